@@ -1,0 +1,232 @@
+/*
+ * pbm.h - C ABI of the reduced-Newton MG-MINRES library for the variable-thickness-sheet (VTS)
+ * minimum-compliance problem solved by the penalty-barrier multiplier (PBM) method.
+ *
+ * Paper: M. Brune, M. Kocvara, "On barrier and modified barrier multigrid methods for 3d topology
+ * optimization" (arXiv:1904.06556).
+ *
+ * Conventions shared by every call
+ *   - Grids are structured nx x ny x nz arrays of cubes of edge h (Section 6) with trilinear (Q1)
+ *     displacements and one density per element.
+ *       node id  = i + (nx+1) * (j + (ny+1) * k),   0 <= i <= nx, 0 <= j <= ny, 0 <= k <= nz
+ *       dof      = 3 * node + c,                     c = 0, 1, 2  (x, y, z displacement)
+ *       element  = i + nx * (j + ny * k)
+ *       local node of an element: a = ix + 2 iy + 4 iz at node (i+ix, j+iy, k+iz); local dof 3a + c.
+ *     Displacement vectors hold every node (n = 3 (nx+1)(ny+1)(nz+1) entries). Supported
+ *     (Dirichlet) dofs are eliminated: their rows and columns of K(rho) and S are those of the
+ *     identity, and every right-hand side must be zero there.
+ *   - Vectors of the reduced Newton system (eq. (system)) have n + 1 entries: the n displacement
+ *     dofs followed by the scalar alpha.
+ *   - Every pointer argument named *_dev is a device pointer to memory the CALLER owns and keeps
+ *     alive until the work on `stream` has finished; the library never frees it. Arrays are dense
+ *     and contiguous (no strides); double pointers must be 8-byte aligned, float pointers 4-byte.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream. Calls
+ *     enqueue work and return without synchronising, except where a call returns host scalars or
+ *     says otherwise. Calls on one grid handle must not run concurrently from several host threads.
+ *   - Every call returns an int status: PBM_OK (0) or a negative error code. On error nothing is
+ *     guaranteed about the outputs, and pbm_last_error() gives a one-line message (per host
+ *     thread). A CUDA error during a call is reported as PBM_ECUDA.
+ *   - All work runs on the CUDA device that is current when the grid is created; the library
+ *     makes that device current itself on every call.
+ */
+#ifndef PBM_H
+#define PBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pbm_grid pbm_grid; /* opaque handle: grid, multigrid hierarchy and workspace */
+
+enum pbm_status {
+    PBM_OK = 0,
+    PBM_EINVAL = -1,       /* invalid argument (sizes, null pointers, unsupported combination)  */
+    PBM_ENOMEM = -2,       /* device or host allocation failed                                  */
+    PBM_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed                       */
+    PBM_EBREAKDOWN = -4,   /* MINRES: v^T M^{-1} v < 0, the preconditioner is not SPD           */
+    PBM_ENOTCONV = -5,     /* iteration limit reached before the tolerance                      */
+    PBM_ETIMEOUT = -6,     /* a bounded device-side wait gave up                                */
+    PBM_ELINESEARCH = -7,  /* Armijo backtracking failed                                        */
+    PBM_ENONFINITE = -8,   /* a NaN or Inf was found in an input or a reduction                 */
+    PBM_ESTATE = -9        /* call out of order (e.g. S applied before pbm_set_state)           */
+};
+
+enum pbm_support {         /* Section 6: supports of the two test problems                       */
+    PBM_CANTILEVER = 0,    /* every node of the face x = 0 fixed in all directions              */
+    PBM_BRIDGE_CORNERS = 1,/* the four corner nodes of the bottom face z = 0 fixed               */
+    PBM_BRIDGE_EDGES = 2,  /* the two bottom edges {x = 0, z = 0} and {x = nx, z = 0} fixed      */
+    PBM_FREE = 3           /* no support (K singular; for operator tests only)                  */
+};
+
+enum pbm_precision {
+    PBM_FP64 = 0,          /* every operator, smoother, transfer and Krylov vector in FP64      */
+    PBM_MIXED = 1          /* FP32 operator / smoother / transfers / inner Krylov vectors inside
+                              an FP64 iterative refinement; FP64 dots, scalars and coarsest solve */
+};
+
+enum pbm_op {
+    PBM_OP_K = 0,          /* K(rho) of eq. (1), rho from pbm_set_density                        */
+    PBM_OP_S = 1           /* reduced Newton matrix S of eq. (S), from pbm_set_state             */
+};
+
+typedef struct pbm_grid_desc {
+    int nx, ny, nz;        /* fine elements per direction, >= 1                                   */
+    int levels;            /* multigrid levels >= 1; nx, ny, nz divisible by 2^(levels-1)       */
+    int support;           /* enum pbm_support                                                   */
+    int precision;         /* enum pbm_precision                                                 */
+    double E, nu;          /* isotropic material, E > 0, -1 < nu < 0.5                          */
+    double h;              /* fine element edge > 0                                             */
+    int pre_sweeps;        /* damped-Jacobi sweeps before / after the coarse correction          */
+    int post_sweeps;
+    double jacobi_theta;   /* Jacobi weight on level k is theta / lambda_k (lambda_k: Lanczos
+                              estimate of lambda_max(D_k^{-1} A_k)); 0 < theta < 2               */
+    int lanczos_steps;     /* Lanczos steps of that estimate, 2..64                              */
+    double inner_rtol;     /* PBM_MIXED: relative tolerance of each inner (FP32) MINRES solve    */
+} pbm_grid_desc;
+
+typedef struct pbm_grid_info {
+    int levels;
+    int nx[16], ny[16], nz[16];   /* per level, 0 = finest                                       */
+    int64_t n[16];                /* 3 * nodes per level                                        */
+    int64_t m[16];                /* elements per level                                          */
+    int64_t n_free;               /* free displacement dofs of the fine level (the paper's n)    */
+    double omega[16];             /* current Jacobi weights (0 until an operator is set up)      */
+    double lambda_max[16];        /* current Lanczos estimates                                   */
+    int64_t device_bytes;         /* device memory held by the handle                            */
+} pbm_grid_info;
+
+/* Newton state of the dual VTS problem (eq. (aug_lagr)): variables xi = (u, alpha, nu_lo, nu_up),
+ * multipliers (rho, mu_lo, mu_up), penalties (p, q_lo, q_up; scalars, as Algorithm 1 updates them
+ * uniformly) and the problem data V, rho_lo, rho_up. */
+typedef struct pbm_state {
+    double* u_dev;         /* n, zero on supported dofs                                          */
+    double* nu_lo_dev;     /* m                                                                  */
+    double* nu_up_dev;     /* m                                                                  */
+    double* rho_dev;       /* m, > 0                                                             */
+    double* mu_lo_dev;     /* m, > 0                                                             */
+    double* mu_up_dev;     /* m, > 0                                                             */
+    double alpha;
+    double p, q_lo, q_up;  /* > 0                                                                */
+    double V, rho_lo, rho_up;
+} pbm_state;
+
+typedef struct pbm_solve_info {
+    int status;            /* same as the return value                                           */
+    int iterations;        /* MINRES iterations (all inner iterations for PBM_MIXED)             */
+    int outer;             /* refinement steps (PBM_MIXED), 1 for PBM_FP64                       */
+    double relres;         /* true ||b - A x||_2 / ||b||_2 at exit, FP64 operator                */
+    double setup_ms;       /* operator hierarchy set-up inside this call (0 if already built)    */
+    double solve_ms;       /* host wall time of the solve                                        */
+} pbm_solve_info;
+
+typedef struct pbm_newton_info {
+    int status;
+    int minres_iterations;
+    int halvings;          /* Armijo step halvings                                               */
+    double kappa;          /* accepted step length                                               */
+    double res_pbm;        /* eq. (resIP) at the state BEFORE the step                           */
+    double slope;          /* grad L^T dxi (must be < 0)                                         */
+    double lagrangian_old, lagrangian_new;
+    double minres_relres;
+} pbm_newton_info;
+
+/* Fills `d` with defaults: FP64, E = 1, nu = 0.3, h = 1, 2 + 2 sweeps, theta = 1.2, 10 Lanczos
+ * steps, inner_rtol = 1e-4. */
+int pbm_default_desc(pbm_grid_desc* d, int nx, int ny, int nz, int levels, int support);
+
+/* Builds the grid and its level hierarchy (Section 6: regular 8-way refinement of a coarse mesh,
+ * here read from the fine grid down), the element matrix K_e of Section 5.2 / eq. (1) (Q1,
+ * isotropic, exact integration), the supports, and allocates every device buffer the solves need.
+ * Errors: PBM_EINVAL (sizes not divisible, levels > 16, coarsest grid with more than 1500 dofs,
+ * bad material), PBM_ENOMEM. */
+int pbm_create_grid(const pbm_grid_desc* d, pbm_grid** out);
+
+/* Releases every buffer of the handle. Waits for the device work the handle enqueued. */
+int pbm_destroy_grid(pbm_grid* g);
+
+/* One-line description of the last error on this host thread ("" if none). */
+const char* pbm_last_error(void);
+
+/* Sizes, current Jacobi weights and memory of the handle (host struct). */
+int pbm_grid_info_get(const pbm_grid* g, pbm_grid_info* out);
+
+enum pbm_map {
+    PBM_MAP_FIXED_DOFS = 0,    /* uint8[n_level]: 1 where the dof is supported                    */
+    PBM_MAP_ELEM_NODES = 1,    /* int32[m_level * 8]: node ids of every element, local order a    */
+    PBM_MAP_PROLONG = 2,       /* level >= 1: for every node of level-1 (the finer grid), 8 int32
+                                  coarse parent node ids then 8 double weights, packed as
+                                  int32[nodes_fine*8] followed by double[nodes_fine*8]; unused
+                                  slots have id -1 and weight 0; supports are NOT applied         */
+    PBM_MAP_KE = 3             /* double[576]: element matrix of the level (row-major 24 x 24)    */
+};
+/* Copies an integer map or table of `level` into host memory `host_dst` (caller-allocated, sized
+ * as listed above). Synchronous. Errors: PBM_EINVAL. */
+int pbm_get_maps(const pbm_grid* g, int level, int which, void* host_dst);
+
+/* rho_dev: m FP64 element densities (eq. (1)). Copied into the handle (the caller may free it
+ * after the stream has passed this call); marks the K(rho) hierarchy stale. Checks that every
+ * value is finite and >= 0 (this synchronises `stream`): PBM_ENONFINITE / PBM_EINVAL. */
+int pbm_set_density(pbm_grid* g, const double* rho_dev, void* stream);
+
+/* y = K(w) x on the fine level, eq. (1): K(w) = sum_i w_i K_i with supported rows/columns the
+ * identity. w_dev: m element weights (NULL = the density set by pbm_set_density); x_dev, y_dev:
+ * n. x and y must not overlap. FP64 throughout. */
+int pbm_apply_K(pbm_grid* g, const double* w_dev, const double* x_dev, double* y_dev, void* stream);
+
+/* Same operator in FP32 (the kernel the mixed path runs); w_dev must not be NULL. */
+int pbm_apply_K_f32(pbm_grid* g, const float* w_dev, const float* x_dev, float* y_dev, void* stream);
+
+/* Sets the Newton state and builds what S needs (Section 3.2): the per-element factors rho', rho'',
+ * mu''_lo, mu''_up, the Schur weights d_i = 1/(1/rho'' + 1/mu''_lo + 1/mu''_up) and rhs weights
+ * eps_i, then the Galerkin hierarchy of S (Section 5.1: A_{k-1} = P^T A_k P, identity on alpha),
+ * the Jacobi diagonals, weights and the coarsest factorisation. The state's arrays are read
+ * during this call only (on `stream`). Synchronises `stream` (host reads the Lanczos scalars).
+ * Errors: PBM_EINVAL (null array), PBM_ENONFINITE (non-finite or non-positive factor). */
+int pbm_set_state(pbm_grid* g, const pbm_state* st, void* stream);
+
+/* y = S x, eq. (S) in closed form: S = [K(rho'), 0; 0, 0] + sum_i d_i g_i g_i^T, g_i = [K_i u; -1],
+ * supported rows/columns the identity. x_dev, y_dev: n + 1 FP64, no overlap. Needs pbm_set_state. */
+int pbm_apply_S(pbm_grid* g, const double* x_dev, double* y_dev, void* stream);
+
+/* Right-hand side of the reduced system, eq. (system): rhs = [f - K(rho' - eps) u ;
+ * -V + sum_i (rho'_i - eps_i)], zero on supported dofs. f_dev: n (zero on supported dofs);
+ * rhs_dev: n + 1. If norms_host is not NULL it receives {||res_1||_2, res_2, ||res_3||_2} of
+ * eq. (lagr_grad_a) at the state (res_1 on free dofs), which synchronises `stream`. */
+int pbm_reduced_rhs(pbm_grid* g, const double* f_dev, double* rhs_dev, double* norms_host, void* stream);
+
+/* x = M^{-1} b: one V-cycle (Section 5.1; correction scheme, damped-Jacobi smoothing, restriction
+ * P^T, 27-point prolongation, identity transfer of alpha, exact coarsest solve) for the operator
+ * `op`. Vectors have n + 1 entries for PBM_OP_S and n for PBM_OP_K. For PBM_OP_K the K(rho)
+ * hierarchy is built first if stale (synchronises `stream`). */
+int pbm_vcycle(pbm_grid* g, int op, const double* b_dev, double* x_dev, void* stream);
+
+/* Solves A x = b, A = K(rho) or S, by MINRES preconditioned with one V-cycle (Section 5) until the
+ * true residual satisfies ||b - A x||_2 <= rtol ||b||_2 (eq. (cgstop), 2-norm over all entries) or
+ * maxit iterations. x_dev is the initial guess on entry (pass zeros for none) and the solution on
+ * exit. PBM_MIXED grids run FP64 iterative refinement around FP32 inner solves of relative
+ * tolerance desc.inner_rtol. Synchronises `stream`. info may be NULL. Errors: PBM_ENOTCONV,
+ * PBM_EBREAKDOWN, PBM_ESTATE. */
+int pbm_minres_solve(pbm_grid* g, int op, const double* b_dev, double* x_dev, double rtol, int maxit,
+                     pbm_solve_info* info, void* stream);
+
+/* One Newton step of Algorithm 2 on the augmented Lagrangian: builds S and its rhs at `st`,
+ * solves the reduced system to relative residual eps_mr, recovers (dnu_lo, dnu_up) by
+ * eq. (deltanu), backtracks (Armijo, c1 = 1e-4, halving, at most 30 halvings) and updates
+ * st->u_dev, st->alpha, st->nu_lo_dev, st->nu_up_dev in place. f_dev: n load vector. Synchronises.
+ * Errors: PBM_ELINESEARCH (no acceptable step; state unchanged), PBM_ENOTCONV, PBM_EBREAKDOWN. */
+int pbm_newton_step(pbm_grid* g, pbm_state* st, const double* f_dev, double eps_mr, pbm_newton_info* info,
+                    void* stream);
+
+/* Per-element compliances c_i = 1/2 u^T K_i u (the constraint terms of the dual, eq. (dual), and
+ * minus the derivative of 1/2 f^T u w.r.t. rho_i at equilibrium). u_dev: n (masked internally);
+ * c_dev: m. If f_dev and fTu_host are both non-NULL, *fTu_host receives f^T u (synchronises). */
+int pbm_compliance_grad(pbm_grid* g, const double* u_dev, double* c_dev, const double* f_dev, double* fTu_host,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PBM_H */

@@ -1,0 +1,208 @@
+"""GB300-native reduced-Newton MG-MINRES solver for the PBM method on 3D variable-thickness-sheet problems.
+
+`Grid` wraps one handle of the C library (include/pbm.h). Vectors are torch CUDA tensors:
+displacements (n = 3 (nx+1)(ny+1)(nz+1), float64), element arrays (m = nx ny nz, float64), and the
+reduced-system vectors (n + 1, float64, alpha last). The library runs every step in its own kernels;
+this module only passes pointers, sizes and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib
+from ._lib import PbmError, SolveInfo, NewtonInfo  # noqa: F401
+
+__all__ = ["Grid", "PbmError", "lib"]
+
+_LIB = None
+
+
+def lib() -> C.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = _lib.load()
+    return _LIB
+
+
+def _ptr(t: torch.Tensor | None, dtype=torch.float64, n: int | None = None, name: str = "tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} entries, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Grid:
+    """A structured grid with its multigrid hierarchy (see pbm_create_grid)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, levels: int, support: str = "cantilever",
+                 precision: str = "fp64", E: float = 1.0, nu: float = 0.3, h: float = 1.0, pre_sweeps: int = 2,
+                 post_sweeps: int = 2, jacobi_theta: float = 1.2, lanczos_steps: int = 10,
+                 inner_rtol: float = 1e-4):
+        self._L = lib()
+        d = _lib.GridDesc()
+        self._check(self._L.pbm_default_desc(C.byref(d), nx, ny, nz, levels, _lib.SUPPORTS[support]))
+        d.precision = _lib.PRECISIONS[precision]
+        d.E, d.nu, d.h = E, nu, h
+        d.pre_sweeps, d.post_sweeps = pre_sweeps, post_sweeps
+        d.jacobi_theta, d.lanczos_steps, d.inner_rtol = jacobi_theta, lanczos_steps, inner_rtol
+        self.desc = d
+        h_ = C.c_void_p()
+        self._h = None
+        self._check(self._L.pbm_create_grid(C.byref(d), C.byref(h_)))
+        self._h = h_
+        self.nx, self.ny, self.nz, self.levels = nx, ny, nz, levels
+        self.nnode = (nx + 1) * (ny + 1) * (nz + 1)
+        self.n = 3 * self.nnode
+        self.m = nx * ny * nz
+        self._keep = []
+
+    # --------------------------------------------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != 0:
+            raise PbmError(rc, self._L.pbm_last_error().decode())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._L.pbm_destroy_grid(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --------------------------------------------------------------------------------------------
+    def info(self) -> dict:
+        gi = _lib.GridInfo()
+        self._check(self._L.pbm_grid_info_get(self._h, C.byref(gi)))
+        L = gi.levels
+        return dict(levels=L, dims=[(gi.nx[k], gi.ny[k], gi.nz[k]) for k in range(L)], n=list(gi.n[:L]),
+                    m=list(gi.m[:L]), n_free=gi.n_free, omega=list(gi.omega[:L]), lambda_max=list(gi.lambda_max[:L]),
+                    device_bytes=gi.device_bytes)
+
+    def maps(self, level: int, which: str):
+        import numpy as np
+        nx, ny, nz = self.nx >> level, self.ny >> level, self.nz >> level
+        nn = (nx + 1) * (ny + 1) * (nz + 1)
+        if which == "fixed_dofs":
+            out = np.zeros(3 * nn, dtype=np.uint8)
+        elif which == "elem_nodes":
+            out = np.zeros((nx * ny * nz, 8), dtype=np.int32)
+        elif which == "prolong":
+            nnf = (2 * nx + 1) * (2 * ny + 1) * (2 * nz + 1)
+            buf = np.zeros(nnf * 8 * 4 + nnf * 8 * 8, dtype=np.uint8)
+            self._check(self._L.pbm_get_maps(self._h, level, _lib.MAPS[which], buf.ctypes.data_as(C.c_void_p)))
+            ids = buf[: nnf * 32].view(np.int32).reshape(nnf, 8)
+            wts = buf[nnf * 32:].view(np.float64).reshape(nnf, 8)
+            return ids, wts
+        elif which == "Ke":
+            out = np.zeros((24, 24), dtype=np.float64)
+        else:
+            raise ValueError(which)
+        self._check(self._L.pbm_get_maps(self._h, level, _lib.MAPS[which], out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    # --------------------------------------------------------------------------------------------
+    def set_density(self, rho: torch.Tensor):
+        self._check(self._L.pbm_set_density(self._h, _ptr(rho, n=self.m, name="rho"), _stream()))
+
+    def apply_K(self, x: torch.Tensor, w: torch.Tensor | None = None, out: torch.Tensor | None = None):
+        y = torch.empty_like(x) if out is None else out
+        self._check(self._L.pbm_apply_K(self._h, _ptr(w, n=self.m, name="w"), _ptr(x, n=self.n, name="x"),
+                                        _ptr(y, n=self.n, name="y"), _stream()))
+        return y
+
+    def apply_K_f32(self, x: torch.Tensor, w: torch.Tensor, out: torch.Tensor | None = None):
+        y = torch.empty_like(x) if out is None else out
+        f = torch.float32
+        self._check(self._L.pbm_apply_K_f32(self._h, _ptr(w, f, self.m, "w"), _ptr(x, f, self.n, "x"),
+                                            _ptr(y, f, self.n, "y"), _stream()))
+        return y
+
+    def _state(self, st: dict) -> _lib.State:
+        s = _lib.State()
+        for key in ("u", "nu_lo", "nu_up", "rho", "mu_lo", "mu_up"):
+            t = st[key]
+            setattr(s, key + "_dev", _ptr(t, n=self.n if key == "u" else self.m, name=key))
+        for key in ("alpha", "p", "q_lo", "q_up", "V", "rho_lo", "rho_up"):
+            setattr(s, key, float(st[key]))
+        return s
+
+    def set_state(self, st: dict):
+        """st: u (n), nu_lo, nu_up, rho, mu_lo, mu_up (m) CUDA float64 tensors; alpha, p, q_lo, q_up, V, rho_lo,
+        rho_up floats."""
+        s = self._state(st)
+        self._check(self._L.pbm_set_state(self._h, C.byref(s), _stream()))
+
+    def apply_S(self, x: torch.Tensor, out: torch.Tensor | None = None):
+        y = torch.empty_like(x) if out is None else out
+        self._check(self._L.pbm_apply_S(self._h, _ptr(x, n=self.n + 1, name="x"), _ptr(y, n=self.n + 1, name="y"),
+                                        _stream()))
+        return y
+
+    def reduced_rhs(self, f: torch.Tensor, norms: bool = False):
+        rhs = torch.empty(self.n + 1, dtype=torch.float64, device=f.device)
+        nrm = (C.c_double * 3)()
+        self._check(self._L.pbm_reduced_rhs(self._h, _ptr(f, n=self.n, name="f"), _ptr(rhs, n=self.n + 1),
+                                            nrm if norms else None, _stream()))
+        return (rhs, tuple(nrm)) if norms else rhs
+
+    def vcycle(self, op: str, b: torch.Tensor):
+        x = torch.empty_like(b)
+        n = self.n + (1 if op == "S" else 0)
+        self._check(self._L.pbm_vcycle(self._h, _lib.OPS[op], _ptr(b, n=n, name="b"), _ptr(x, n=n), _stream()))
+        return x
+
+    def minres_solve(self, op: str, b: torch.Tensor, rtol: float = 1e-8, maxit: int = 500,
+                     x0: torch.Tensor | None = None, check: bool = True):
+        n = self.n + (1 if op == "S" else 0)
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        inf = _lib.SolveInfo()
+        rc = self._L.pbm_minres_solve(self._h, _lib.OPS[op], _ptr(b, n=n, name="b"), _ptr(x, n=n), float(rtol),
+                                      int(maxit), C.byref(inf), _stream())
+        info = {k: getattr(inf, k) for k, _ in _lib.SolveInfo._fields_}
+        if check:
+            self._check(rc)
+        info["rc"] = rc
+        return x, info
+
+    def newton_step(self, st: dict, f: torch.Tensor, eps_mr: float, check: bool = True):
+        """One Newton step of Algorithm 2; updates st['u'], st['nu_lo'], st['nu_up'] in place and st['alpha']."""
+        s = self._state(st)
+        inf = _lib.NewtonInfo()
+        rc = self._L.pbm_newton_step(self._h, C.byref(s), _ptr(f, n=self.n, name="f"), float(eps_mr), C.byref(inf),
+                                     _stream())
+        info = {k: getattr(inf, k) for k, _ in _lib.NewtonInfo._fields_}
+        info["rc"] = rc
+        if check:
+            self._check(rc)
+        st["alpha"] = s.alpha
+        return info
+
+    def compliance_grad(self, u: torch.Tensor, f: torch.Tensor | None = None):
+        c = torch.empty(self.m, dtype=torch.float64, device=u.device)
+        fTu = C.c_double(0.0)
+        self._check(self._L.pbm_compliance_grad(self._h, _ptr(u, n=self.n, name="u"), _ptr(c, n=self.m),
+                                                _ptr(f, n=self.n, name="f"), C.byref(fTu) if f is not None else None,
+                                                _stream()))
+        return (c, fTu.value) if f is not None else c

@@ -1,0 +1,548 @@
+// Operator applications on a structured grid: K(w) x, S x (eq. (S)), explicit coarse Galerkin
+// operators, their Jacobi diagonals, and fused residual / damped-Jacobi epilogues.
+//
+// All of them share one "marching" kernel. A CTA of 32 x BY threads covers 31 x (BY - 1) node
+// columns of the grid and walks up a chunk of node planes in z. Thread (tx, ty) computes the
+// element whose upper corner (in x and y) is its own node column, one element layer per step:
+//   * the node values of the plane just above are staged in shared memory (with a one-node halo
+//     in -x and -y, loaded by the first row / column of threads);
+//   * the element result is split into its 4 bottom and 4 top corners: the top corners are kept in
+//     registers and added to the next layer's bottom corners (same element column), so each node
+//     plane is completed after two element layers;
+//   * the 4 elements around a node column exchange their corner sums through shared memory and the
+//     owning thread writes the node once: no atomics, and a fixed summation order (deterministic).
+// Elements on CTA borders are computed twice (by the two CTAs that share them); the alpha-row sum
+// counts each element once. Every launch finishes with a last-block-done reduction of the per-CTA
+// partial sums in a fixed order.
+#include "pbm_internal.h"
+
+namespace pbm {
+
+enum Kind { K_FINE_K = 0, K_FINE_S = 1, K_FINE_DIAG_K = 2, K_FINE_DIAG_S = 3, K_COARSE = 4, K_COARSE_DIAG = 5 };
+
+template <class T>
+struct MarchParams {
+    int nx, ny, nz, support, DZ;
+    int64_t n, m;
+    const T* x;        // gathered input (n (+1))
+    const T* u;        // second gathered vector (fine S: u; fine diag S: u)
+    const T* w;        // element weights (fine)
+    const T* d;        // Schur weights (fine S)
+    const T* A;        // coarse element matrices (upper triangle, entry-major)
+    const T* bord;     // coarse alpha border (n)
+    double s_alpha;    // coarse S_alpha,alpha
+    T* y;
+    const T* b;
+    const T* diag;
+    const double* omega;
+    int mode;
+    int with_alpha;
+    int dot_slot;
+    double Kdiag;
+    KeHatT<T> K;
+    double* partials;  // 2 * nblocks
+    DevScalars* sc;
+};
+
+template <class T>
+__device__ __forceinline__ T ldv(const T* p, int64_t i) { return __ldg(p + i); }
+
+// deterministic block reduction of two values; result valid in thread 0
+template <int NT>
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
+    const int lane = (threadIdx.x + blockDim.x * threadIdx.y) & 31;
+    const int wid = (threadIdx.x + blockDim.x * threadIdx.y) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        sh[2 * wid] = a;
+        sh[2 * wid + 1] = b;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        constexpr int NW = NT / 32;
+        a = lane < NW ? sh[2 * lane] : 0.0;
+        b = lane < NW ? sh[2 * lane + 1] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+    }
+}
+
+template <class T, int BY, int KIND>
+__global__ void __launch_bounds__(32 * BY) k_march(MarchParams<T> P) {
+    constexpr int BX = 32;
+    constexpr int NT = BX * BY;
+    constexpr bool GX = (KIND == K_FINE_K || KIND == K_FINE_S || KIND == K_COARSE);
+    constexpr bool GU = (KIND == K_FINE_S || KIND == K_FINE_DIAG_S);
+    constexpr bool DIAG = (KIND == K_FINE_DIAG_K || KIND == K_FINE_DIAG_S || KIND == K_COARSE_DIAG);
+    __shared__ T sx[GX ? 2 : 1][3][BY + 1][BX + 1];
+    __shared__ T su[GU ? 2 : 1][3][BY + 1][BX + 1];
+    __shared__ T sacc[3][3][BY][BX];
+    __shared__ double sred[2 * NT / 32];
+    __shared__ bool s_last;
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const int X0 = blockIdx.x * (BX - 1), Y0 = blockIdx.y * (BY - 1);
+    const int ex = X0 - 1 + tx, ey = Y0 - 1 + ty;
+    const int Ix = X0 + tx, Iy = Y0 + ty;
+    const bool owner = (tx < BX - 1) && (ty < BY - 1) && Ix <= nx && Iy <= ny;
+    const bool ecol = ex >= 0 && ex < nx && ey >= 0 && ey < ny;
+    const bool designated = ecol && tx >= 1 && ty >= 1;
+    const int kz0 = blockIdx.z * P.DZ;
+    const int kz1 = min(kz0 + P.DZ, nz + 1);
+    const int64_t sxn = nx + 1, sxy = int64_t(nx + 1) * (ny + 1);
+
+    T xa = T(0);
+    if (GX && P.with_alpha) xa = P.x[P.n];
+    const double om = (!DIAG && P.mode == EPI_JACOBI) ? *P.omega : 0.0;
+
+    auto fetch = [&](const T* v, int i, int j, int k, T* out3, bool& fixed) {
+        fixed = false;
+        if (i < 0 || i > nx || j < 0 || j > ny || k < 0 || k > nz) {
+            out3[0] = out3[1] = out3[2] = T(0);
+            return;
+        }
+        fixed = node_fixed(P.support, nx, ny, nz, i, j, k);
+        const int64_t nd = 3 * (i + sxn * j + sxy * k);
+        out3[0] = ldv(v, nd);
+        out3[1] = ldv(v, nd + 1);
+        out3[2] = ldv(v, nd + 2);
+    };
+    // stage plane `pl` of vector v into buffer s[(pl & 1)], masked; own node unmasked into own3
+    auto stage = [&](const T* v, T (*s)[3][BY + 1][BX + 1], int pl, T* own3) {
+        const int bf = pl & 1;
+        T t3[3];
+        bool fx;
+        fetch(v, Ix, Iy, pl, t3, fx);
+        own3[0] = t3[0];
+        own3[1] = t3[1];
+        own3[2] = t3[2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s[bf][c][ty + 1][tx + 1] = fx ? T(0) : t3[c];
+        if (tx == 0) {
+            fetch(v, Ix - 1, Iy, pl, t3, fx);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s[bf][c][ty + 1][0] = fx ? T(0) : t3[c];
+        }
+        if (ty == 0) {
+            fetch(v, Ix, Iy - 1, pl, t3, fx);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s[bf][c][0][tx + 1] = fx ? T(0) : t3[c];
+        }
+        if (tx == 0 && ty == 0) {
+            fetch(v, Ix - 1, Iy - 1, pl, t3, fx);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s[bf][c][0][0] = fx ? T(0) : t3[c];
+        }
+    };
+
+    T xown[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+    T uown[3];
+    if (GX) stage(P.x, sx, kz0 - 1, xown[(kz0 - 1) & 1]);
+    if (GU) stage(P.u, su, kz0 - 1, uown);
+
+    T carry[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) carry[a][0] = carry[a][1] = carry[a][2] = T(0);
+    double part_alpha = 0.0, part_dot = 0.0;
+
+    for (int k = kz0 - 1; k < kz1; ++k) {
+        // stage the plane above this element layer
+        if (GX) stage(P.x, sx, k + 1, xown[(k + 1) & 1]);
+        if (GU) stage(P.u, su, k + 1, uown);
+        __syncthreads();
+
+        T ye[3][8];
+        const bool ev = ecol && k >= 0 && k < nz;
+        if (ev) {
+            const int64_t e = ex + int64_t(nx) * (ey + int64_t(ny) * k);
+            T xe[3][8], ue[3][8];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                const int ix = a & 1, iy = (a >> 1) & 1, iz = (a >> 2) & 1;
+                const int bf = (k + iz) & 1;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (GX) xe[c][a] = sx[bf][c][ty + iy][tx + ix];
+                    if (GU) ue[c][a] = su[bf][c][ty + iy][tx + ix];
+                }
+            }
+            if (KIND == K_FINE_K) {
+                const T we = ldv(P.w, e);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) wht_fwd(xe[c]);
+                khat_apply(P.K, xe, ye);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) ye[c][q] *= we;
+                    wht_out(ye[c]);
+                }
+            } else if (KIND == K_FINE_S) {
+                const T we = ldv(P.w, e), de = ldv(P.d, e);
+                T W[3][8];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) wht_fwd(ue[c]);
+                khat_apply(P.K, ue, W);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) wht_fwd(xe[c]);
+                T dot = T(0);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int q = 1; q < 8; ++q) dot += W[c][q] * xe[c][q];
+                // H^T Y . H^{-1}: in the transformed basis u . v = (H u) . (H^{-T} v); with
+                // v = H^T V this is U . V, so w_e . x_e = (H^T W) . x_e = W . (H x_e) = W . X
+                const T t = de * (dot - xa);
+                khat_apply(P.K, xe, ye);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) ye[c][q] = we * ye[c][q] + t * W[c][q];
+                    wht_out(ye[c]);
+                }
+                if (designated && k >= kz0) part_alpha -= double(t);
+            } else if (KIND == K_FINE_DIAG_K) {
+                const T we = ldv(P.w, e);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) ye[c][a] = we * T(P.Kdiag);
+            } else if (KIND == K_FINE_DIAG_S) {
+                const T we = ldv(P.w, e), de = ldv(P.d, e);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) wht_fwd(ue[c]);
+                khat_apply(P.K, ue, ye);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    wht_out(ye[c]);
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) ye[c][a] = we * T(P.Kdiag) + de * ye[c][a] * ye[c][a];
+                }
+                if (designated && k >= kz0) part_alpha += double(de);
+            } else if (KIND == K_COARSE) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) ye[c][a] = T(0);
+                const T* Ae = P.A + e;
+                const int64_t m = P.m;
+#pragma unroll
+                for (int i = 0; i < 24; ++i) {
+#pragma unroll
+                    for (int j = i; j < 24; ++j) {
+                        const T a = ldv(Ae, int64_t(tri_index(i, j)) * m);
+                        ye[i % 3][i / 3] += a * xe[j % 3][j / 3];
+                        if (i != j) ye[j % 3][j / 3] += a * xe[i % 3][i / 3];
+                    }
+                }
+            } else {  // K_COARSE_DIAG
+                const T* Ae = P.A + e;
+                const int64_t m = P.m;
+#pragma unroll
+                for (int i = 0; i < 24; ++i) ye[i % 3][i / 3] = ldv(Ae, int64_t(tri_index(i, i)) * m);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int a = 0; a < 8; ++a) ye[c][a] = T(0);
+        }
+
+        // bottom corners complete node plane k (together with the layer below); top corners carry
+        T acc[4][3];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                acc[a][c] = carry[a][c] + ye[c][a];
+                carry[a][c] = ye[c][a + 4];
+            }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sacc[a][c][ty][tx] = acc[a][c];
+        __syncthreads();
+
+        if (owner && k >= kz0 && k <= nz) {
+            T yv[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                yv[c] = acc[3][c] + sacc[2][c][ty][tx + 1] + sacc[1][c][ty + 1][tx] + sacc[0][c][ty + 1][tx + 1];
+            const int64_t nd = 3 * (Ix + sxn * Iy + sxy * k);
+            const bool fixed = node_fixed(P.support, nx, ny, nz, Ix, Iy, k);
+            const T* xo = xown[k & 1];
+            if (DIAG) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) P.y[nd + c] = fixed ? T(1) : yv[c];
+            } else {
+                if (KIND == K_COARSE && P.with_alpha) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const T bc = ldv(P.bord, nd + c);
+                        yv[c] += bc * xa;
+                        part_alpha += double(bc) * double(xo[c]);
+                    }
+                }
+                if (fixed) {
+                    yv[0] = xo[0];
+                    yv[1] = xo[1];
+                    yv[2] = xo[2];
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    T o;
+                    if (P.mode == EPI_APPLY) {
+                        o = yv[c];
+                        part_dot += double(o) * double(xo[c]);
+                    } else if (P.mode == EPI_RESID) {
+                        o = ldv(P.b, nd + c) - yv[c];
+                        part_dot += double(o) * double(o);
+                    } else {
+                        const T bb = ldv(P.b, nd + c);
+                        o = xo[c] + T(om) * (bb - yv[c]) / ldv(P.diag, nd + c);
+                        part_dot += double(o) * double(bb);
+                    }
+                    P.y[nd + c] = o;
+                }
+            }
+        }
+    }
+
+    // per-CTA partials, then the last CTA reduces them in order and finishes the alpha entry
+    block_sum2<NT>(part_alpha, part_dot, sred);
+    const int nblk = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (tx == 0 && ty == 0) {
+        P.partials[bid] = part_alpha;
+        P.partials[nblk + bid] = part_dot;
+        __threadfence();
+        const unsigned t = atomicAdd(&P.sc->counter[0], 1u);
+        s_last = (t == unsigned(nblk - 1));
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double sa = 0.0, sd = 0.0;
+    const int tid = tx + BX * ty;
+    for (int i = tid; i < nblk; i += NT) {
+        sa += ((volatile double*)P.partials)[i];
+        sd += ((volatile double*)P.partials)[nblk + i];
+    }
+    block_sum2<NT>(sa, sd, sred);
+    if (tid == 0) {
+        P.sc->counter[0] = 0u;
+        const int64_t n = P.n;
+        if (DIAG) {
+            if (P.with_alpha) P.y[n] = T(KIND == K_COARSE_DIAG ? P.s_alpha : (KIND == K_FINE_DIAG_S ? sa : 1.0));
+        } else {
+            if (P.with_alpha) {
+                double ya = sa;
+                if (KIND == K_COARSE) ya += P.s_alpha * double(xa);
+                double o;
+                if (P.mode == EPI_APPLY) {
+                    o = ya;
+                    sd += o * double(xa);
+                } else if (P.mode == EPI_RESID) {
+                    o = double(P.b[n]) - ya;
+                    sd += o * o;
+                } else {
+                    const double bb = double(P.b[n]);
+                    o = double(xa) + om * (bb - ya) / double(P.diag[n]);
+                    sd += o * bb;
+                }
+                P.y[n] = T(o);
+            }
+            if (P.dot_slot >= 0) P.sc->red[P.dot_slot] = sd;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// launch helpers
+// ------------------------------------------------------------------------------------------------
+constexpr int BY_ = 8;
+
+static dim3 march_grid(const Geom& g, int& DZ) {
+    const int gx = (g.nx + 1 + 30) / 31;
+    const int gy = (g.ny + 1 + BY_ - 2) / (BY_ - 1);
+    const int planes = g.nz + 1;
+    // aim for about 4 CTAs per SM, chunks of at least 4 planes
+    const int want = 152 * 4;
+    int chunks = (want + gx * gy - 1) / (gx * gy);
+    chunks = std::max(1, std::min(chunks, (planes + 3) / 4));
+    DZ = (planes + chunks - 1) / chunks;
+    chunks = (planes + DZ - 1) / DZ;
+    return dim3(gx, gy, chunks);
+}
+
+template <class T>
+static void fill_khat(KeHatT<T>& out, const KeHat& K) {
+    for (int c = 0; c < 3; ++c)
+        for (int q = 0; q < 8; ++q) out.dg[c][q] = T(K.dg[c][q]);
+    for (int b = 0; b < 2; ++b) {
+        out.lam4[b] = T(K.lam4[b]);
+        out.mu4[b] = T(K.mu4[b]);
+    }
+}
+
+template <class T>
+static MarchParams<T> base_params(pbm_grid* g, int k) {
+    MarchParams<T> P{};
+    const Geom& G = g->L[k].g;
+    P.nx = G.nx;
+    P.ny = G.ny;
+    P.nz = G.nz;
+    P.support = G.support;
+    P.n = G.n();
+    P.m = G.m();
+    P.partials = g->partials;
+    P.sc = g->sc;
+    P.dot_slot = -1;
+    P.Kdiag = g->Kdiag;
+    fill_khat(P.K, g->kehat);
+    return P;
+}
+
+template <class T, int KIND>
+static void run(pbm_grid* g, int k, MarchParams<T>& P, cudaStream_t st, const char* what) {
+    int DZ = 1;
+    dim3 grid = march_grid(g->L[k].g, DZ);
+    P.DZ = DZ;
+    if (int(grid.x * grid.y * grid.z) > g->max_blocks) fail(PBM_EINVAL, "grid too large for the partials buffer");
+    k_march<T, BY_, KIND><<<grid, dim3(32, BY_), 0, st>>>(P);
+    PBM_LAUNCH(what);
+}
+
+template <class T>
+static void set_epi(MarchParams<T>& P, const ApplyArgs& a) {
+    P.x = (const T*)a.x;
+    P.y = (T*)a.y;
+    P.b = (const T*)a.b;
+    P.diag = (const T*)a.diag;
+    P.omega = a.omega;
+    P.mode = a.mode;
+    P.with_alpha = a.with_alpha ? 1 : 0;
+    P.dot_slot = a.dot_slot;
+}
+
+void launch_fine(pbm_grid* g, bool fp32, const void* w, const void* d, const void* u, const ApplyArgs& a,
+                 cudaStream_t st) {
+    if (fp32) {
+        auto P = base_params<float>(g, 0);
+        set_epi(P, a);
+        P.w = (const float*)w;
+        P.d = (const float*)d;
+        P.u = (const float*)u;
+        if (u) run<float, K_FINE_S>(g, 0, P, st, "fine S f32");
+        else run<float, K_FINE_K>(g, 0, P, st, "fine K f32");
+    } else {
+        auto P = base_params<double>(g, 0);
+        set_epi(P, a);
+        P.w = (const double*)w;
+        P.d = (const double*)d;
+        P.u = (const double*)u;
+        if (u) run<double, K_FINE_S>(g, 0, P, st, "fine S f64");
+        else run<double, K_FINE_K>(g, 0, P, st, "fine K f64");
+    }
+}
+
+void launch_coarse(pbm_grid* g, int k, bool fp32, const ApplyArgs& a, cudaStream_t st) {
+    Level& L = g->L[k];
+    if (fp32) {
+        auto P = base_params<float>(g, k);
+        set_epi(P, a);
+        P.A = L.A32;
+        P.bord = L.bord32;
+        P.s_alpha = g->s_alpha;
+        run<float, K_COARSE>(g, k, P, st, "coarse f32");
+    } else {
+        auto P = base_params<double>(g, k);
+        set_epi(P, a);
+        P.A = L.A64;
+        P.bord = L.bord64;
+        P.s_alpha = g->s_alpha;
+        run<double, K_COARSE>(g, k, P, st, "coarse f64");
+    }
+}
+
+void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st) {
+    Level& L = g->L[k];
+    auto P = base_params<double>(g, k);
+    P.mode = EPI_APPLY;
+    P.with_alpha = 1;
+    P.y = L.diag64;
+    P.s_alpha = g->s_alpha;
+    if (k == 0) {
+        P.w = op_s ? g->w64 : g->rho;
+        if (op_s) {
+            P.d = g->d64;
+            P.u = g->u64;
+            run<double, K_FINE_DIAG_S>(g, 0, P, st, "fine diag S");
+        } else {
+            run<double, K_FINE_DIAG_K>(g, 0, P, st, "fine diag K");
+        }
+    } else {
+        P.A = L.A64;
+        if (!op_s) P.s_alpha = 1.0;
+        run<double, K_COARSE_DIAG>(g, k, P, st, "coarse diag");
+    }
+    if (L.diag32) launch_cast(L.diag64, false, L.diag32, true, L.g.n() + 1, st);
+}
+
+// ------------------------------------------------------------------------------------------------
+// per-element bilinear forms u_e^T K_e v_e with supported dofs masked (fine level)
+// ------------------------------------------------------------------------------------------------
+__global__ void k_elem_energy(int nx, int ny, int nz, int support, const double* __restrict__ u,
+                              const double* __restrict__ v, double* __restrict__ out, KeHatT<double> K) {
+    const int64_t m = int64_t(nx) * ny * nz;
+    const int64_t sxn = nx + 1, sxy = int64_t(nx + 1) * (ny + 1);
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
+        const int i = int(e % nx);
+        const int j = int((e / nx) % ny);
+        const int k = int(e / (int64_t(nx) * ny));
+        double U[3][8], X[3][8], W[3][8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const int ii = i + (a & 1), jj = j + ((a >> 1) & 1), kk = k + ((a >> 2) & 1);
+            const bool fx = node_fixed(support, nx, ny, nz, ii, jj, kk);
+            const int64_t nd = 3 * (ii + sxn * jj + sxy * kk);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                U[c][a] = fx ? 0.0 : u[nd + c];
+                X[c][a] = fx ? 0.0 : v[nd + c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            wht_fwd(U[c]);
+            wht_fwd(X[c]);
+        }
+        khat_apply(K, U, W);
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int q = 1; q < 8; ++q) s += W[c][q] * X[c][q];
+        out[e] = s;
+    }
+}
+
+void launch_elem_energy(pbm_grid* g, const double* u, const double* v, double* out, cudaStream_t st) {
+    const Geom& G = g->L[0].g;
+    KeHatT<double> K;
+    fill_khat(K, g->kehat);
+    const int64_t m = G.m();
+    int blocks = int(std::min<int64_t>((m + 255) / 256, 152 * 16));
+    k_elem_energy<<<blocks, 256, 0, st>>>(G.nx, G.ny, G.nz, G.support, u, v ? v : u, out, K);
+    PBM_LAUNCH("elem energy");
+}
+
+}  // namespace pbm

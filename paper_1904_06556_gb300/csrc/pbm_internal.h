@@ -1,0 +1,273 @@
+// Internal declarations of the reduced-Newton MG-MINRES library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "pbm.h"
+
+namespace pbm {
+
+// ------------------------------------------------------------------------------------------------
+// error handling
+// ------------------------------------------------------------------------------------------------
+struct Error {
+    int code;
+    std::string msg;
+};
+void set_error(const std::string& msg);
+[[noreturn]] void fail(int code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+#define PBM_CUDA(x) ::pbm::check_cuda((x), #x)
+#define PBM_LAUNCH(what) ::pbm::check_cuda(cudaGetLastError(), what)
+
+// ------------------------------------------------------------------------------------------------
+// geometry of one level (structured grid of cubes)
+// ------------------------------------------------------------------------------------------------
+struct Geom {
+    int nx, ny, nz;      // elements
+    int support;         // enum pbm_support
+    int64_t nnode() const { return int64_t(nx + 1) * (ny + 1) * (nz + 1); }
+    int64_t n() const { return 3 * nnode(); }
+    int64_t m() const { return int64_t(nx) * ny * nz; }
+};
+
+// Is node (i, j, k) of a level supported? The supports of the coarse levels are those of the same
+// physical faces/corners/edges, so every level uses the same rule on its own node coordinates.
+__host__ __device__ inline bool node_fixed(int support, int nx, int ny, int nz, int i, int j, int k) {
+    (void)nz;
+    switch (support) {
+        case PBM_CANTILEVER: return i == 0;
+        case PBM_BRIDGE_CORNERS: return k == 0 && (i == 0 || i == nx) && (j == 0 || j == ny);
+        case PBM_BRIDGE_EDGES: return k == 0 && (i == 0 || i == nx);
+        default: return false;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// element matrix of the fine level in the (sum, difference) tensor basis
+//
+// With H1 = [[1, 1], [-1, 1]] acting on the two nodal values along one direction and H = H1 (x) H1
+// (x) H1 on the 8 nodal values of one displacement component, the Q1 element matrix factors as
+//     K_e x = H^T Khat H x,
+// because each 1D integral matrix (int N'N', int NN, int N'N, int NN') maps the sum / difference
+// coefficients onto a single coefficient. Khat couples pattern q of output component c with at most
+// three input coefficients:
+//   diagonal:          dg[c][q] * X_c[q]
+//   for d != c, r the third direction:
+//     q_c = 1, q_d = 0:  lam4[q_r] * X_d[q with bit c cleared and bit d set]
+//     q_d = 1, q_c = 0:  mu4[q_r]  * X_d[q with bit d cleared and bit c set]
+// lam4[b] = h lambda m(b) / 4, mu4[b] = h mu m(b) / 4, m(0) = 1/4, m(1) = 1/12, and
+// dg[c][q] = h [ (lambda + mu) q_c m(q_a) m(q_b) + mu sum_{k: q_k = 1} prod_{j != k} m(q_j) ].
+// ------------------------------------------------------------------------------------------------
+struct KeHat {
+    double dg[3][8];
+    double lam4[2];
+    double mu4[2];
+};
+
+template <class T>
+struct KeHatT {
+    T dg[3][8];
+    T lam4[2];
+    T mu4[2];
+};
+
+// per-component forward transform X = H v (index bits: 0 = x, 1 = y, 2 = z)
+template <class T>
+__device__ __forceinline__ void wht_fwd(T* v) {
+#pragma unroll
+    for (int s = 1; s < 8; s <<= 1) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if ((i & s) == 0) {
+                T a = v[i], b = v[i + s];
+                v[i] = a + b;
+                v[i + s] = b - a;
+            }
+        }
+    }
+}
+
+// per-component output transform y = H^T Y
+template <class T>
+__device__ __forceinline__ void wht_out(T* v) {
+#pragma unroll
+    for (int s = 1; s < 8; s <<= 1) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if ((i & s) == 0) {
+                T a = v[i], b = v[i + s];
+                v[i] = a - b;
+                v[i + s] = a + b;
+            }
+        }
+    }
+}
+
+// Y = Khat X on transformed coefficients X[c][q]. The DC pattern q = 0 is zero on output and never
+// read (rigid translations are in the kernel of K_e).
+template <class T>
+__device__ __forceinline__ void khat_apply(const KeHatT<T>& K, const T (&X)[3][8], T (&Y)[3][8]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        Y[c][0] = T(0);
+#pragma unroll
+        for (int q = 1; q < 8; ++q) {
+            T acc = K.dg[c][q] * X[c][q];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (d == c) continue;
+                const int r = 3 - c - d;
+                const int br = (q >> r) & 1;
+                const int qc = (q >> c) & 1, qd = (q >> d) & 1;
+                if (qc == 1 && qd == 0) acc += K.lam4[br] * X[d][(q & ~(1 << c)) | (1 << d)];
+                if (qd == 1 && qc == 0) acc += K.mu4[br] * X[d][(q & ~(1 << d)) | (1 << c)];
+            }
+            Y[c][q] = acc;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// one multigrid level
+// ------------------------------------------------------------------------------------------------
+struct Level {
+    Geom g;
+    double h = 1.0;
+    // coarse levels: element matrices, upper triangle (i <= j) of the 24 x 24 matrix, entry-major
+    // (entry t of element e at [t * m + e]); index of (i, j) is tri_index(i, j)
+    double* A64 = nullptr;
+    float* A32 = nullptr;
+    // alpha border of S on this level (n entries; b_0 = -sum_i d_i K_i u, b_{k+1} = P^T b_k)
+    double* bord64 = nullptr;
+    float* bord32 = nullptr;
+    // Jacobi diagonal, n + 1 entries (last = alpha)
+    double* diag64 = nullptr;
+    float* diag32 = nullptr;
+    // V-cycle work vectors, n + 1 entries each
+    double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *t64 = nullptr;
+    float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr, *t32 = nullptr;
+    double omega = 0.0, lambda_max = 0.0;
+};
+
+constexpr int NTRI = 300;  // entries of the upper triangle of a 24 x 24 matrix
+__host__ __device__ inline int tri_index(int i, int j) {  // i <= j
+    return i * 24 - (i * (i - 1)) / 2 + (j - i);
+}
+
+// device scalar block used by the reductions, Lanczos and MINRES
+struct DevScalars {
+    double red[64];        // reduction outputs (slot per use)
+    double lz_a[64], lz_b[64];
+    double mr[32];         // MINRES scalar state
+    unsigned int counter[64];  // last-block-done counters (one per reduction slot)
+    int flags[8];
+};
+
+}  // namespace pbm
+
+// ------------------------------------------------------------------------------------------------
+// the handle
+// ------------------------------------------------------------------------------------------------
+struct pbm_grid {
+    pbm_grid_desc desc;
+    int device = 0;
+    int levels = 1;
+    std::vector<pbm::Level> L;
+    pbm::KeHat kehat;                 // fine level, h-scaled
+    double Ke[576];                   // fine-level element matrix (row-major), FP64
+    double Kdiag;                     // K_e[i][i] (all equal for the isotropic cube)
+    double G[8][576];                 // P_c^T K_e P_c for the 8 children (coarse local dofs)
+    double* G_dev = nullptr;          // 8 x NTRI upper triangles, [c][t]
+    // fine-level element data
+    double* rho = nullptr;            // density (m)
+    double* w64 = nullptr;            // element weights of the current operator (rho or rho')
+    double* d64 = nullptr;            // Schur weights d_i
+    double* eps64 = nullptr;          // rhs weights eps_i
+    double* aux64 = nullptr;          // 8 m: 5 coefficient rows (rho'', mu''_lo, mu''_up, dL/dnu_lo,
+                                      // dL/dnu_up), u^T K_e u, u^T K_e du, du^T K_e du
+    double* wr64 = nullptr;           // rho' - eps (rhs weights)
+    float* rho32 = nullptr;
+    float* w32 = nullptr;
+    float* d32 = nullptr;
+    double* u64 = nullptr;            // masked displacement of the Newton state (n)
+    float* u32 = nullptr;
+    double* what = nullptr;           // P_c^T (K_e u_e) for every fine element, [24][m]
+    double* nwt = nullptr;            // Newton step buffers: dz (n + 1), r (n), dnu_lo (m), dnu_up (m)
+    double s_alpha = 0.0;             // S_alpha,alpha = sum_i d_i
+    // coarsest level: dense inverse of the bordered matrix, (nc+1)^2 FP64
+    int nc = 0;
+    double* cinv = nullptr;
+    double* cwork = nullptr;
+    // reductions
+    double* partials = nullptr;       // per-block partial sums
+    int max_blocks = 0;
+    pbm::DevScalars* sc = nullptr;
+    pbm::DevScalars* sc_host = nullptr;  // pinned mirror
+    // Krylov work vectors (n + 1 of the finest level)
+    double* kv64[10] = {};
+    float* kv32[10] = {};
+    // operator state: 0 = none, 1 = K(rho) hierarchy current, 2 = S hierarchy current
+    int op_ready = 0;
+    bool rho_set = false;
+    bool state_set = false;
+    double alpha = 0.0, V = 0.0;      // of the current state
+    double sum_rho1 = 0.0, sum_wr = 0.0, gl2 = 0.0;   // reductions of the coefficient kernel
+    int64_t bytes = 0;
+};
+
+namespace pbm {
+
+void* dalloc(pbm_grid* g, size_t bytes);
+void dfree(void* p);
+
+// ---- kernels (launch wrappers), apply.cu ----
+enum EpiMode { EPI_APPLY = 0, EPI_RESID = 1, EPI_JACOBI = 2 };
+
+struct ApplyArgs {
+    // input vector (n (+1)), output (n (+1)); b and diag for RESID / JACOBI
+    const void* x;
+    void* y;
+    const void* b;
+    const void* diag;
+    const double* omega;   // device scalar (JACOBI)
+    int mode;
+    bool with_alpha;       // vectors carry the alpha entry (operator S)
+    int dot_slot;          // >= 0: accumulate sum(y_out . x) (APPLY) or ||y_out||^2 (RESID) or
+                           // sum(y_out . b) (JACOBI) into sc->red[dot_slot]
+};
+
+// fine level: K(w) (u == nullptr) or S (u, d given; w = rho')
+void launch_fine(pbm_grid* g, bool fp32, const void* w, const void* d, const void* u, const ApplyArgs& a,
+                 cudaStream_t st);
+// coarse level k >= 1: explicit element matrices (+ border for S)
+void launch_coarse(pbm_grid* g, int k, bool fp32, const ApplyArgs& a, cudaStream_t st);
+// Jacobi diagonal of a level (S or K), written to L[k].diag64 / diag32 (n + 1, last = alpha)
+void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st);
+// per-element c_e = 1/2 u_e^T K_e u_e (masked u), FP64
+void launch_elem_energy(pbm_grid* g, const double* u, const double* v, double* out, cudaStream_t st);
+
+// ---- multigrid, mg.cu ----
+void launch_restrict(pbm_grid* g, int k, bool fp32, const void* rf, void* bc, bool with_alpha, double scale,
+                     cudaStream_t st);
+void launch_prolong_add(pbm_grid* g, int k, bool fp32, const void* xc, void* xf, bool with_alpha, cudaStream_t st);
+void launch_build_what(pbm_grid* g, cudaStream_t st);
+void launch_build_level1(pbm_grid* g, bool op_s, cudaStream_t st);
+void launch_build_coarser(pbm_grid* g, int k, cudaStream_t st);
+void launch_coarse_to_f32(pbm_grid* g, int k, cudaStream_t st);
+void build_coarsest(pbm_grid* g, bool op_s, cudaStream_t st);
+void launch_coarsest_solve(pbm_grid* g, bool fp32, const void* b, void* x, bool with_alpha, cudaStream_t st);
+
+// ---- vectors and reductions, krylov.cu ----
+void vec_zero(void* p, size_t bytes, cudaStream_t st);
+void launch_scale_diag_first(pbm_grid* g, int k, bool fp32, const void* b, void* x, bool with_alpha,
+                             cudaStream_t st);                    // x = omega D^-1 b
+void launch_cast(const void* src, bool src32, void* dst, bool dst32, int64_t n, cudaStream_t st);
+void launch_dot(pbm_grid* g, bool fp32, const void* a, const void* b, int64_t n, int slot, cudaStream_t st);
+double read_slot(pbm_grid* g, int slot, cudaStream_t st);
+
+}  // namespace pbm

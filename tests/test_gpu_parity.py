@@ -1,0 +1,290 @@
+"""GPU parity: every call of the C ABI against the CPU oracle on the same seeded inputs.
+
+Tolerances: integer maps and interpolation weights bit-exact; FP64 operator applications within 1e-12
+relative (norm-wise; only summation order differs); FP32 applications within 2e-6; solves to the
+protocol of the reduced system (GPU FP64 MINRES driven to 1e-13, compared with the oracle's direct
+solve: displacement error <= 1e-10 relative, compliance <= 1e-8).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic
+from oracle import fem, pbm, solvers
+
+pytestmark = pytest.mark.gpu
+
+SUP = {"cantilever": "cantilever", "bridge_corners": "bridge_corners", "bridge_edges": "bridge_edges"}
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    return t.detach().double().cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1904_06556_gb300 import build
+    build.build()
+    import paper_1904_06556_gb300 as p
+    return p
+
+
+def make_problem(nx, ny, nz, bc, seed, u_scale=0.5, load="end_edge"):
+    g = fem.Grid(nx, ny, nz, bc)
+    f = synthetic.load_vector(nx, ny, nz, load)
+    d = synthetic.random_state(nx, ny, nz, seed, u_scale=u_scale, fixed_dofs=g.fixed_dofs())
+    pb = pbm.Problem(g, f, d["V"], d["rho_lo"], d["rho_up"])
+    return pb, pbm.State.from_dict(d), d
+
+
+def state_dev(d):
+    out = {k: dev(d[k]) for k in ("u", "nu_lo", "nu_up", "rho", "mu_lo", "mu_up")}
+    out.update({k: float(d[k]) for k in ("alpha", "p", "q_lo", "q_up", "V", "rho_lo", "rho_up")})
+    return out
+
+
+# ------------------------------------------------------------------------------------------------
+# integer maps and element matrices
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dims,bc,levels", [((8, 4, 4), "cantilever", 3), ((16, 8, 8), "bridge_corners", 3),
+                                            ((4, 2, 2), "bridge_edges", 2), ((6, 4, 2), "cantilever", 2)])
+def test_maps_bit_exact(pkg, dims, bc, levels):
+    G = pkg.Grid(*dims, levels, bc)
+    for k in range(levels):
+        og = fem.Grid(dims[0] >> k, dims[1] >> k, dims[2] >> k, bc, 2.0 ** k)
+        assert np.array_equal(G.maps(k, "fixed_dofs").astype(bool), og.fixed_dofs())
+        assert np.array_equal(G.maps(k, "elem_nodes").astype(np.int64), og.elem_nodes())
+        assert np.allclose(G.maps(k, "Ke"), fem.element_stiffness(1.0, 0.3, 2.0 ** k), rtol=0, atol=1e-15 * 2 ** k)
+        if k >= 1:
+            ids, wts = G.maps(k, "prolong")
+            fine = fem.Grid(dims[0] >> (k - 1), dims[1] >> (k - 1), dims[2] >> (k - 1), "free")
+            P = fem.prolongation(fine).toarray()           # unmasked on a free grid
+            nnf = fine.nnode
+            Q = np.zeros((nnf, P.shape[1] // 3))
+            for fn in range(nnf):
+                for s in range(8):
+                    if ids[fn, s] >= 0:
+                        Q[fn, ids[fn, s]] += wts[fn, s]
+            assert np.array_equal(Q, P[0::3, 0::3])        # weights exactly {1, 1/2, 1/4, 1/8}
+    info = G.info()
+    assert info["n_free"] == fem.Grid(*dims, bc).n_free()
+
+
+# ------------------------------------------------------------------------------------------------
+# K(w) x
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dims,bc", [((2, 2, 2), "cantilever"), ((6, 4, 2), "bridge_corners"),
+                                     ((34, 10, 6), "cantilever"), ((64, 16, 8), "bridge_edges"),
+                                     ((40, 22, 12), "bridge_corners")])
+def test_apply_K_fp64(pkg, dims, bc):
+    G = pkg.Grid(*dims, 2, bc)
+    g = fem.Grid(*dims, bc)
+    rng = np.random.default_rng(sum(dims))
+    w = rng.uniform(1e-3, 1.0, g.m)
+    x = rng.standard_normal(g.n)
+    ref = fem.apply_K_elementwise(g, w, fem.element_stiffness(), x)
+    y = host(G.apply_K(dev(x), dev(w)))
+    assert rel(y, ref) < 1e-13
+    G.set_density(dev(w))
+    y2 = host(G.apply_K(dev(x)))
+    assert np.array_equal(y, y2)                       # deterministic: same bits on a second call
+
+
+@pytest.mark.parametrize("dims,bc", [((34, 10, 6), "cantilever"), ((64, 32, 32), "cantilever")])
+def test_apply_K_fp32(pkg, dims, bc):
+    G = pkg.Grid(*dims, 2, bc)
+    g = fem.Grid(*dims, bc)
+    rng = np.random.default_rng(7)
+    w = rng.uniform(1e-3, 1.0, g.m)
+    x = rng.standard_normal(g.n)
+    ref = fem.apply_K_elementwise(g, w, fem.element_stiffness(), x)
+    y = host(G.apply_K_f32(dev(x, torch.float32), dev(w, torch.float32)))
+    assert rel(y, ref) < 2e-6
+
+
+# ------------------------------------------------------------------------------------------------
+# S, rhs, compliances
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dims,bc,seed,us", [((8, 4, 4), "cantilever", 0, 0.5), ((16, 8, 8), "bridge_corners", 3, 0.2),
+                                             ((34, 10, 6), "cantilever", 5, 1.0)])
+def test_apply_S_rhs_and_compliance(pkg, dims, bc, seed, us):
+    pb, st, d = make_problem(*dims, bc, seed, us)
+    G = pkg.Grid(*dims, 2, bc)
+    G.set_state(state_dev(d))
+    cf = pbm.coeffs(pb, st)
+    assert np.any(cf.s < -0.5) and np.any(cf.s >= -0.5)  # both branches of phi
+    x = np.random.default_rng(seed + 1).standard_normal(pb.n + 1)
+    y = host(G.apply_S(dev(x)))
+    ref = pbm.apply_S_elementwise(pb, st, cf, x)
+    assert rel(y, ref) < 1e-12
+    rhs, norms = G.reduced_rhs(dev(pb.f), norms=True)
+    assert rel(host(rhs), pbm.rhs_closed(pb, st, cf)) < 1e-12
+    gu, ga, gl, _ = pbm.gradient(pb, st, cf)
+    assert abs(norms[0] - np.linalg.norm(gu)) < 1e-12 * max(1.0, np.linalg.norm(gu))
+    assert abs(norms[1] - ga) < 1e-10 * max(1.0, abs(ga))
+    assert abs(norms[2] - np.linalg.norm(gl)) < 1e-12 * np.linalg.norm(gl)
+    c, fTu = G.compliance_grad(dev(d["u"]), dev(pb.f))
+    assert rel(host(c), pbm.compliances(pb, st.u)) < 1e-12
+    assert abs(fTu - pb.f @ pbm.masked(pb, st.u)) < 1e-12 * max(1.0, abs(fTu))
+
+
+# ------------------------------------------------------------------------------------------------
+# V-cycle: same hierarchy definition as the oracle (Galerkin, theta / lambda_max Jacobi, exact coarse)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dims,bc,levels", [((8, 4, 4), "cantilever", 3), ((16, 8, 8), "bridge_corners", 3),
+                                            ((16, 8, 8), "cantilever", 4)])
+def test_vcycle_S_matches_oracle(pkg, dims, bc, levels):
+    pb, st, d = make_problem(*dims, bc, 2, 0.4)
+    G = pkg.Grid(*dims, levels, bc)
+    G.set_state(state_dev(d))
+    S = pbm.assemble_S(pb, st)
+    h = solvers.Hierarchy(pb.grid, S, levels, has_alpha=True)
+    info = G.info()
+    assert np.allclose(info["omega"][:levels - 1], h.omega, rtol=1e-10)
+    b = np.random.default_rng(4).standard_normal(pb.n + 1)
+    b[pb.fixed] = 0.0
+    x = host(G.vcycle("S", dev(b)))
+    assert rel(x, h.vcycle(b)) < 1e-10
+
+
+@pytest.mark.parametrize("dims,bc,levels", [((8, 4, 4), "cantilever", 3), ((16, 8, 8), "bridge_corners", 4)])
+def test_vcycle_K_matches_oracle(pkg, dims, bc, levels):
+    g = fem.Grid(*dims, bc)
+    rho = synthetic.density_uniform_rescaled(g.m, 0.3, 1)
+    G = pkg.Grid(*dims, levels, bc)
+    G.set_density(dev(rho))
+    K = fem.assemble_K(g, rho, fem.element_stiffness())
+    h = solvers.Hierarchy(g, K, levels, has_alpha=False)
+    b = np.random.default_rng(5).standard_normal(g.n)
+    b[g.fixed_dofs()] = 0.0
+    x = host(G.vcycle("K", dev(b)))
+    assert np.allclose(G.info()["omega"][:levels - 1], h.omega, rtol=1e-10)
+    assert rel(x, h.vcycle(b)) < 1e-10
+
+
+# ------------------------------------------------------------------------------------------------
+# MINRES solves against the oracle's direct solve
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dims,bc,levels", [((16, 8, 8), "cantilever", 3), ((16, 8, 8), "bridge_corners", 3)])
+def test_minres_S_fp64_matches_direct(pkg, dims, bc, levels):
+    pb, st, d = make_problem(*dims, bc, 1, 0.5)
+    G = pkg.Grid(*dims, levels, bc)
+    G.set_state(state_dev(d))
+    cf = pbm.coeffs(pb, st)
+    rhs = pbm.rhs_closed(pb, st, cf)
+    ref = solvers.direct_solve(pbm.assemble_S(pb, st, cf), rhs)
+    x, info = G.minres_solve("S", dev(rhs), rtol=1e-13, maxit=400)
+    assert info["relres"] <= 1e-13
+    assert rel(host(x), ref) < 1e-10
+    # the GPU's own rhs gives the same solution
+    x2, _ = G.minres_solve("S", G.reduced_rhs(dev(pb.f)), rtol=1e-13, maxit=400)
+    assert rel(host(x2), ref) < 1e-10
+
+
+def test_minres_K_equilibrium_and_compliance(pkg):
+    nx, ny, nz = 16, 8, 8
+    g = fem.Grid(nx, ny, nz, "cantilever")
+    rho = np.full(g.m, 0.3)
+    f = synthetic.load_vector(nx, ny, nz, "end_edge")
+    G = pkg.Grid(nx, ny, nz, 3, "cantilever")
+    G.set_density(dev(rho))
+    K = fem.assemble_K(g, rho, fem.element_stiffness())
+    u_ref = solvers.direct_solve(K, f)
+    u, info = G.minres_solve("K", dev(f), rtol=1e-13, maxit=400)
+    assert rel(host(u), u_ref) < 1e-10
+    _, fTu = G.compliance_grad(u, dev(f))
+    assert abs(fTu - f @ u_ref) <= 1e-8 * abs(f @ u_ref)
+
+
+@pytest.mark.parametrize("dims,bc,levels", [((16, 8, 8), "cantilever", 3), ((16, 8, 8), "bridge_corners", 3)])
+def test_minres_S_mixed_precision(pkg, dims, bc, levels):
+    pb, st, d = make_problem(*dims, bc, 1, 0.5)
+    G = pkg.Grid(*dims, levels, bc, precision="mixed")
+    G.set_state(state_dev(d))
+    cf = pbm.coeffs(pb, st)
+    rhs = pbm.rhs_closed(pb, st, cf)
+    ref = solvers.direct_solve(pbm.assemble_S(pb, st, cf), rhs)
+    x, info = G.minres_solve("S", dev(rhs), rtol=1e-10, maxit=400)
+    assert info["relres"] <= 1e-10 and info["outer"] >= 2
+    assert rel(host(x), ref) < 1e-7
+
+
+def test_minres_zero_rhs_and_state_errors(pkg):
+    G = pkg.Grid(8, 4, 4, 2, "cantilever")
+    from paper_1904_06556_gb300 import PbmError
+    with pytest.raises(PbmError, match="PBM_ESTATE"):
+        G.apply_S(torch.zeros(G.n + 1, dtype=torch.float64, device="cuda"))
+    with pytest.raises(PbmError, match="PBM_ESTATE"):
+        G.minres_solve("K", torch.zeros(G.n, dtype=torch.float64, device="cuda"))
+    G.set_density(torch.full((G.m,), 0.5, dtype=torch.float64, device="cuda"))
+    x, info = G.minres_solve("K", torch.zeros(G.n, dtype=torch.float64, device="cuda"))
+    assert torch.count_nonzero(x) == 0 and info["iterations"] == 0
+    bad = torch.full((G.m,), 0.5, dtype=torch.float64, device="cuda")
+    bad[3] = float("nan")
+    with pytest.raises(PbmError, match="PBM_ENONFINITE"):
+        G.set_density(bad)
+
+
+# ------------------------------------------------------------------------------------------------
+# Newton step (Algorithm 2) against the oracle's step with a direct solve
+# ------------------------------------------------------------------------------------------------
+def test_newton_step_matches_oracle(pkg):
+    nx, ny, nz = 8, 4, 4
+    g = fem.Grid(nx, ny, nz, "cantilever")
+    f = synthetic.load_vector(nx, ny, nz, "end_edge")
+    pb = pbm.Problem(g, f, 0.3 * g.m, 1e-3, 1.0)
+    m = g.m
+    st = pbm.State(np.zeros(g.n), 1.0, np.ones(m), np.ones(m), np.full(m, 0.3), np.ones(m), np.ones(m))
+    # one oracle Newton iteration with a direct solve
+    ref, _, _ = pbm.newton(pb, st, eps_nwt=0.0, eps_mr=None, max_iter=1)
+    G = pkg.Grid(nx, ny, nz, 3, "cantilever")
+    d = dict(u=st.u, nu_lo=st.nu_lo, nu_up=st.nu_up, rho=st.rho, mu_lo=st.mu_lo, mu_up=st.mu_up, alpha=st.alpha,
+             p=1.0, q_lo=1.0, q_up=1.0, V=pb.V, rho_lo=pb.rho_lo, rho_up=pb.rho_up)
+    sd = state_dev(d)
+    info = G.newton_step(sd, dev(f), eps_mr=1e-13)
+    assert info["slope"] < 0 and info["lagrangian_new"] < info["lagrangian_old"]
+    assert abs(info["res_pbm"] - pbm.res_pbm(pb, st)) < 1e-10 * pbm.res_pbm(pb, st)
+    assert rel(host(sd["u"]), ref.u) < 1e-9
+    assert abs(sd["alpha"] - ref.alpha) < 1e-9 * abs(ref.alpha)
+    assert rel(host(sd["nu_lo"]), ref.nu_lo) < 1e-9
+    assert rel(host(sd["nu_up"]), ref.nu_up) < 1e-9
+
+
+# ------------------------------------------------------------------------------------------------
+# full-size case of the single-solve workload (64 x 32 x 32 cantilever, 5 levels)
+# ------------------------------------------------------------------------------------------------
+def test_full_size_cant64_apply_and_solve_residual(pkg):
+    w = synthetic.WORKLOADS["cant64"]
+    g = fem.Grid(w.nx, w.ny, w.nz, w.bc)
+    rho = synthetic.density_for(w)
+    f = synthetic.load_vector(w.nx, w.ny, w.nz, w.loads[0])
+    G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc)
+    G.set_density(dev(rho))
+    Ke = fem.element_stiffness()
+    x = np.random.default_rng(0).standard_normal(g.n)
+    assert rel(host(G.apply_K(dev(x))), fem.apply_K_elementwise(g, rho, Ke, x)) < 1e-13
+    u, info = G.minres_solve("K", dev(f), rtol=1e-8, maxit=500)
+    # residual computed by the oracle's assembled matrix (a property that holds at any size)
+    K = fem.assemble_K(g, rho, Ke)
+    r = f - K @ host(u)
+    assert np.linalg.norm(r) <= 1.01e-8 * np.linalg.norm(f)
+    # S at the synthetic state of this workload
+    d = synthetic.synthetic_state(w, host(u))
+    pb = pbm.Problem(g, f, d["V"], d["rho_lo"], d["rho_up"])
+    st = pbm.State.from_dict(d)
+    G.set_state(state_dev(d))
+    cf = pbm.coeffs(pb, st)
+    xs = np.random.default_rng(1).standard_normal(g.n + 1)
+    assert rel(host(G.apply_S(dev(xs))), pbm.apply_S_elementwise(pb, st, cf, xs)) < 1e-12
+    rhs = pbm.rhs_closed(pb, st, cf)
+    dz, info = G.minres_solve("S", dev(rhs), rtol=1e-8, maxit=500)
+    S = pbm.assemble_S(pb, st, cf)
+    assert np.linalg.norm(rhs - S @ host(dz)) <= 1.01e-8 * np.linalg.norm(rhs)
