@@ -1,0 +1,486 @@
+#!/usr/bin/env python3
+"""Throughput of the reduced-Newton MG-MINRES solve of the PBM method (Brune & Kocvara, arXiv:1904.06556).
+
+One step is one complete reduced Newton system of the synthetic workload, every row of the hot path:
+  * Newton state set-up (per-element coefficients rho', rho'', mu'', d, eps; the alpha border; the Galerkin
+    coarse operators of S on every level; Jacobi diagonals; Lanczos estimates of the Jacobi weights; the
+    Cholesky inverse of the coarsest bordered matrix),
+  * the right-hand side of eq. (system),
+  * MINRES preconditioned by one V-cycle per iteration, until the true 2-norm relative residual is at most rtol.
+
+Default workload (single-GPU): the 64 x 32 x 32 cantilever in FP64 (5-level V-cycle, rtol 1e-8), densities
+U[1e-3, 1] from seed 0 rescaled to mean 0.3, multipliers and penalties 1, and u the equilibrium displacement
+of K(rho) u = f (computed before timing by the library's own K solve). The JSON line reports whole-job solves
+per second (device-resident inputs, L2 flushed between steps), the same measured end to end through the C ABI
+with the inputs copied from pinned host memory and the solution copied back every step, the roofline of the
+fine-level S kernel (timed live by the library with CUDA events on its launch stream), the clocks sampled
+during the timed region and the CPU oracle's time for the same system.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cant64|bridge128]
+                  [--precision fp64|mixed]
+
+`--impl reference` times the CPU oracle (oracle/, numpy/scipy) on the host cores for the same workload and
+metric. With N > 1 (torchrun) every rank solves its own replica of the workload (weak scaling; the solve itself
+is not partitioned across GPUs).
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import hashlib  # noqa: E402
+import json  # noqa: E402
+import re  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import threading  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synthetic  # noqa: E402
+
+METRIC = "reduced-Newton MG-MINRES solve time & K(ρ)u GB/s; FP32-mixed vs FP64"
+UNIT = "reduced-Newton solves/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PROFILE_DIR = os.path.join(ROOT, "profiles")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1904_06556_gb300", "csrc", f) for f in ("apply.cu", "pbm_internal.h")]
+# FP64 issue rate of GB300 derived from the nominal 1.25 TFLOP/s (FMA = 2 flops), 152 SMs, 2070 MHz:
+# 1.25e12 / (2 * 152 * 2.07e9) = 2 FP64 instructions per clock per SM, i.e. 629 G FP64 operations/s.
+FP64_OPS_PEAK = 2.0 * 152 * 2.07e9
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload_desc(w, precision):
+    return {"workload": f"{w.name}: {w.nx}x{w.ny}x{w.nz} Q1 hex {w.bc}, {precision}, single reduced-Newton solve",
+            "grid": [w.nx, w.ny, w.nz], "support": w.bc, "load": w.loads[0], "density": w.density,
+            "volume_fraction": w.vf, "levels": w.levels, "rtol": w.rtol, "precision": precision,
+            "n_dofs": w.n, "m_elements": w.m,
+            "l2": "flushed: a 256 MiB buffer is written between timed steps (outside the step's events)"}
+
+
+# ------------------------------------------------------------------------------------------------------------
+# distributed plumbing
+# ------------------------------------------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.lines: list[str] = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------------------
+# roofline helpers
+# ------------------------------------------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name: str):
+    """DRAM bytes per launch of the named kernel from the committed ncu summary under profiles/, if it was taken
+    on the current kernel source (its `kernel_source_sha` line matches); else None."""
+    path = os.path.join(PROFILE_DIR, name)
+    try:
+        with open(path) as fh:
+            txt = fh.read()
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
+    m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m_sha or not m_tr or m_sha.group(1) != kernel_hash():
+        return None
+    return float(m_tr.group(1))
+
+
+# ------------------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1904_06556_gb300 as pkg
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    w = synthetic.WORKLOADS[args.workload]
+    precision = args.precision
+
+    def t64(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+    # ---- inputs (untimed): density, load, equilibrium displacement, synthetic Newton state ----
+    rho = synthetic.density_for(w)
+    f_h = synthetic.load_vector(w.nx, w.ny, w.nz, w.loads[0])
+    G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=precision)
+    f = t64(f_h)
+    G.set_density(t64(rho))
+    u, uinfo = G.minres_solve("K", f, rtol=1e-10, maxit=3000, check=False)
+    if not uinfo["relres"] <= 1e-8:
+        raise RuntimeError(f"equilibrium solve of the input state failed: {uinfo}")
+    st_h = synthetic.synthetic_state(w, np.zeros(w.n))
+    sd = {k: t64(st_h[k]) for k in ("nu_lo", "nu_up", "rho", "mu_lo", "mu_up")}
+    sd["u"] = u
+    sd.update({k: float(st_h[k]) for k in ("alpha", "p", "q_lo", "q_up", "V", "rho_lo", "rho_up")})
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > 2 x L2
+    last = {}
+
+    def step():
+        G.set_state(sd)
+        rhs = G.reduced_rhs(f)
+        x, info = G.minres_solve("S", rhs, rtol=w.rtol, maxit=1000)
+        last["info"] = info
+        return x
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    G.profile(True)
+    G.profile_read("S")
+    G.profile_read("K")
+    n0 = pkg.kernel_launches()
+    iters = []
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        iters.append(last["info"]["iterations"])
+    torch.cuda.synchronize()
+    launches = pkg.kernel_launches() - n0
+    prof = G.profile_read("S")
+    G.profile(False)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+    relres = last["info"]["relres"]
+
+    # ---- end to end through the C ABI: pinned host inputs in, solution out, every step ----
+    host_in = {k: torch.as_tensor(np.ascontiguousarray(st_h[k] if k != "u" else u.cpu().numpy()),
+                                  dtype=torch.float64).pin_memory() for k in ("u", "nu_lo", "nu_up", "rho", "mu_lo",
+                                                                             "mu_up")}
+    host_in["f"] = torch.as_tensor(f_h, dtype=torch.float64).pin_memory()
+    host_out = torch.empty(w.n + 1, dtype=torch.float64).pin_memory()
+    dev_in = {k: torch.empty_like(v, device=dev) for k, v in host_in.items()}
+    sd_e2e = {k: dev_in[k] for k in ("u", "nu_lo", "nu_up", "rho", "mu_lo", "mu_up")}
+    sd_e2e.update({k: sd[k] for k in ("alpha", "p", "q_lo", "q_up", "V", "rho_lo", "rho_up")})
+    h2d = sum(v.numel() * 8 for v in host_in.values())
+    d2h = host_out.numel() * 8
+
+    def step_e2e():
+        for k, v in host_in.items():
+            dev_in[k].copy_(v, non_blocking=True)
+        G.set_state(sd_e2e)
+        rhs = G.reduced_rhs(dev_in["f"])
+        x, _ = G.minres_solve("S", rhs, rtol=w.rtol, maxit=1000)
+        host_out.copy_(x, non_blocking=True)
+
+    step_e2e()
+    torch.cuda.synchronize()
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        ev2[i][0].record(stream)
+        step_e2e()
+        ev2[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = float(sum(a.elapsed_time(b) for a, b in ev2))
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * args.steps / (e2e_ms / 1e3)
+
+    # ---- standalone K(rho) u applies at the workload size (metric's second half), L2 flushed and warm ----
+    kapply = k_apply_rates(G, w, rho, dev, flush)
+
+    # ---- roofline of the fine-level S kernel ----
+    peaks, peak_src = measured_peaks()
+    avg_ms = prof["total_ms"] / max(prof["launches"], 1)
+    if precision == "fp64":
+        achieved = prof["flops"] / (prof["total_ms"] / 1e3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_OPS_PEAK / 1e9, "unit": "G FP64 op/s",
+                "frac": achieved / (FP64_OPS_PEAK / 1e9),
+                "peak_source": "derived: nominal 1.25 TFLOP/s FP64 = 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz",
+                "kernel": "k_march<double, 8, K_FINE_S> (fine-level S apply with fused residual/Jacobi epilogues)"}
+        hbm = prof["bytes"] / (prof["total_ms"] / 1e3) / 1e9
+        roof["hbm_achieved_gbs"] = hbm
+        roof["hbm_frac_of_measured"] = hbm / peaks["hbm_gbs"]
+    else:
+        achieved = prof["bytes"] / (prof["total_ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{peak_src} (MEASURED_PEAKS hbm_gbs)",
+                "kernel": "k_march<float, 8, K_FINE_S> (fine-level S apply with fused residual/Jacobi epilogues)"}
+    roof.update({"launches": prof["launches"], "avg_launch_us": avg_ms * 1e3,
+                 "bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
+                 "ops_per_launch": prof["flops"] / max(prof["launches"], 1)})
+    tr = profiled_traffic(f"fine_S_apply_{precision}_{w.name}.md")
+    roof["traffic"] = tr
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32+f64",
+        "data": "synthetic (seeded; shapes of the paper's cantilever example, Section 6)",
+        "config": workload_desc(w, precision),
+        "solve": {"minres_iterations": iters[-1], "true_relres": relres,
+                  "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
+                  "equilibrium_u_relres": uinfo["relres"]},
+        "k_apply": kapply,
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_ms / args.steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_budget_s)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def k_apply_rates(G, w, rho, dev, flush):
+    """Standalone fine-level K(rho) x in FP64 and FP32 at the workload size: algorithmic GB/s = (2n + m) b /
+    kernel time, with the L2 flushed before every launch and warm (back to back)."""
+    import torch
+    n, m = w.n, w.m
+    x64 = torch.randn(n, dtype=torch.float64, device=dev)
+    w64 = torch.as_tensor(rho, dtype=torch.float64, device=dev)
+    y64 = torch.empty_like(x64)
+    x32, w32 = x64.float(), w64.float()
+    y32 = torch.empty_like(x32)
+    res = {}
+    for name, fn, b in (("fp64", lambda: G.apply_K(x64, w64, out=y64), 8),
+                        ("fp32", lambda: G.apply_K_f32(x32, w32, out=y32), 4)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        cold = []
+        for _ in range(10):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            cold.append(e0.elapsed_time(e1))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(50):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        warm = e0.elapsed_time(e1) / 50
+        byt = (2 * n + m) * b
+        cold_ms = statistics.median(cold)
+        res[name] = {"us_flushed": cold_ms * 1e3, "gbs_flushed": byt / (cold_ms / 1e3) / 1e9,
+                     "us_warm": warm * 1e3, "gbs_warm": byt / (warm / 1e3) / 1e9, "bytes": byt}
+    return res
+
+
+# ------------------------------------------------------------------------------------------------------------
+# the CPU oracle (the cpu_baseline leg and the reference arm)
+# ------------------------------------------------------------------------------------------------------------
+def oracle_inputs(w):
+    from oracle import fem, pbm, solvers
+    g = fem.Grid(w.nx, w.ny, w.nz, w.bc)
+    rho = synthetic.density_for(w)
+    f = synthetic.load_vector(w.nx, w.ny, w.nz, w.loads[0])
+    K = fem.assemble_K(g, rho, fem.element_stiffness(w.E, w.nu))
+    h = solvers.Hierarchy(g, K, w.levels, has_alpha=False)
+    u = solvers.minres(lambda v: K @ v, f, h.vcycle, rtol=1e-12, maxit=2000).x
+    d = synthetic.synthetic_state(w, u)
+    pb = pbm.Problem(g, f, d["V"], d["rho_lo"], d["rho_up"], E=w.E, nu=w.nu)
+    return pb, pbm.State.from_dict(d)
+
+
+def oracle_step(w, pb, st):
+    """One reduced Newton system by the oracle: coefficients, S in CSR, Galerkin hierarchy, rhs, MG-MINRES."""
+    from oracle import pbm, solvers
+    cf = pbm.coeffs(pb, st)
+    S = pbm.assemble_S(pb, st, cf)
+    rhs = pbm.rhs_closed(pb, st, cf)
+    h = solvers.Hierarchy(pb.grid, S, w.levels, has_alpha=True)
+    r = solvers.minres(lambda v: S @ v, rhs, h.vcycle, rtol=w.rtol, maxit=1000)
+    return r
+
+
+def cpu_baseline(w, budget_s):
+    pb, st = oracle_inputs(w)
+    times = []
+    t_all = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        r = oracle_step(w, pb, st)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all + times[-1] > budget_s or len(times) >= 5:
+            break
+    tm = statistics.median(times)
+    return {"value": 1.0 / tm, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{len(times)} complete reduced-Newton system(s) of the same workload by the oracle "
+                       f"(numpy/scipy CSR: coefficients, S assembly, Galerkin hierarchy, rhs, MG-MINRES to "
+                       f"{w.rtol:g}: {r.iters} iterations); median {tm:.2f} s; BLAS/OpenMP threads pinned to 1, "
+                       f"scipy sparse products are single-threaded")}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    w = synthetic.WORKLOADS[args.workload]
+    pb, st = oracle_inputs(w)
+    budget = args.cpu_budget_s * 6
+    t_start = time.perf_counter()
+    for _ in range(min(args.warmup, 1)):
+        oracle_step(w, pb, st)
+    times = []
+    r = None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle_step(w, pb, st)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start + times[-1] > budget:
+            break
+    total = sum(times)
+    value = len(times) / total
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": len(times), "steps_requested": args.steps, "warmup": min(args.warmup, 1),
+           "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+           "config": workload_desc(w, "fp64"),
+           "solve": {"minres_iterations": r.iters, "true_relres": r.relres},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{len(times)} complete reduced-Newton systems of the workload by the oracle"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="cant64", choices=["cant64", "bridge128", "cant32", "cant16"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=30.0)
+    args = ap.parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        raise SystemExit("--steps >= 1 and --warmup >= 0")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

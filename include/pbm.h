@@ -133,6 +133,16 @@ typedef struct pbm_newton_info {
     double minres_relres;
 } pbm_newton_info;
 
+/* Timing of the fine-level operator kernel (K(w) x or S x with any of its fused epilogues: plain
+ * apply, residual b - A x, damped-Jacobi sweep), accumulated per handle while profiling is on. */
+typedef struct pbm_profile_stats {
+    int64_t launches;      /* fine-level operator launches timed                                  */
+    double total_ms;       /* sum of their durations, CUDA events on the launch stream            */
+    double bytes;          /* sum of their algorithmic HBM bytes: every input vector and element
+                              array read once, the output written once                           */
+    double flops;          /* sum of their arithmetic operations (add, mul, FMA each counted 1)  */
+} pbm_profile_stats;
+
 /* Fills `d` with defaults: FP64, E = 1, nu = 0.3, h = 1, 2 + 2 sweeps, theta = 1.2, 10 Lanczos
  * steps, inner_rtol = 1e-4. */
 int pbm_default_desc(pbm_grid_desc* d, int nx, int ny, int nz, int levels, int support);
@@ -225,6 +235,19 @@ int pbm_newton_step(pbm_grid* g, pbm_state* st, const double* f_dev, double eps_
  * c_dev: m. If f_dev and fTu_host are both non-NULL, *fTu_host receives f^T u (synchronises). */
 int pbm_compliance_grad(pbm_grid* g, const double* u_dev, double* c_dev, const double* f_dev, double* fTu_host,
                         void* stream);
+
+/* Number of CUDA kernels this library has launched in the process so far (all handles, all
+ * threads). Lets a caller count the device work of a region of code. Never fails. */
+int64_t pbm_kernel_launches(void);
+
+/* on != 0: from now on, bracket every fine-level operator launch of `g` with a pair of CUDA events
+ * on its stream (adds two event records per launch; off by default). on == 0: stop. */
+int pbm_profile(pbm_grid* g, int on);
+
+/* Copies the statistics of operator `op` (PBM_OP_K: the K(w) kernel, PBM_OP_S: the S kernel)
+ * accumulated since its last read into `out` and resets them. Waits for the recorded events.
+ * Errors: PBM_EINVAL (null argument, unknown operator). */
+int pbm_profile_read(pbm_grid* g, int op, pbm_profile_stats* out);
 
 #ifdef __cplusplus
 }

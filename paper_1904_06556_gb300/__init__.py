@@ -14,7 +14,7 @@ import torch
 from . import _lib
 from ._lib import PbmError, SolveInfo, NewtonInfo  # noqa: F401
 
-__all__ = ["Grid", "PbmError", "lib"]
+__all__ = ["Grid", "PbmError", "lib", "kernel_launches"]
 
 _LIB = None
 
@@ -24,6 +24,11 @@ def lib() -> C.CDLL:
     if _LIB is None:
         _LIB = _lib.load()
     return _LIB
+
+
+def kernel_launches() -> int:
+    """Number of CUDA kernels the library has launched in this process."""
+    return int(lib().pbm_kernel_launches())
 
 
 def _ptr(t: torch.Tensor | None, dtype=torch.float64, n: int | None = None, name: str = "tensor"):
@@ -198,6 +203,17 @@ class Grid:
             self._check(rc)
         st["alpha"] = s.alpha
         return info
+
+    def profile(self, on: bool = True):
+        """Start (or stop) timing every fine-level operator launch with CUDA events on its stream."""
+        self._check(self._L.pbm_profile(self._h, 1 if on else 0))
+
+    def profile_read(self, op: str = "S") -> dict:
+        """Launches, total milliseconds, algorithmic bytes and operations of the fine-level kernel of operator `op`
+        ("K" or "S") since its last read (synchronises)."""
+        ps = _lib.ProfileStats()
+        self._check(self._L.pbm_profile_read(self._h, _lib.OPS[op], C.byref(ps)))
+        return {k: getattr(ps, k) for k, _ in _lib.ProfileStats._fields_}
 
     def compliance_grad(self, u: torch.Tensor, f: torch.Tensor | None = None):
         c = torch.empty(self.m, dtype=torch.float64, device=u.device)

@@ -45,6 +45,10 @@ class State(C.Structure):
                 ("rho_up", C.c_double)]
 
 
+class ProfileStats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("total_ms", C.c_double), ("bytes", C.c_double), ("flops", C.c_double)]
+
+
 class SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("outer", C.c_int), ("relres", C.c_double),
                 ("setup_ms", C.c_double), ("solve_ms", C.c_double)]
@@ -86,6 +90,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pbm_minres_solve": (i, [vp, i, vp, vp, d, i, C.POINTER(SolveInfo), vp]),
         "pbm_newton_step": (i, [vp, C.POINTER(State), vp, d, C.POINTER(NewtonInfo), vp]),
         "pbm_compliance_grad": (i, [vp, vp, vp, vp, C.POINTER(C.c_double), vp]),
+        "pbm_kernel_launches": (C.c_int64, []),
+        "pbm_profile": (i, [vp, i]),
+        "pbm_profile_read": (i, [vp, i, C.POINTER(ProfileStats)]),
     }
     for name, (res, args) in sig.items():
         if hasattr(lib, name):

@@ -411,14 +411,41 @@ static MarchParams<T> base_params(pbm_grid* g, int k) {
     return P;
 }
 
+// Algorithmic cost of one fine-level operator launch, for the profiling statistics. Bytes: every
+// input vector / element array read once and the output written once. Operations (add, mul and FMA
+// each counted once) per element: forward transforms 3 x 24, Khat 45 (21 products + 24 couplings),
+// output transform 3 x 24, corner accumulation 21; K(w) scales 24 coefficients; S adds the transform
+// and Khat of u (117), the dot W.X (21), t_e (2) and the combination w Y + t W (48 instead of 24).
+// Per node epilogue: apply 3 (dot), residual 6, Jacobi 15.
+template <int KIND>
+static void fine_cost(const Geom& G, int mode, int esize, double& bytes, double& flops) {
+    const double n = double(G.n()), m = double(G.m()), nn = double(G.nnode());
+    const bool s = KIND == K_FINE_S;
+    double vec = 2.0 * n + (s ? n : 0.0), elem = m * (s ? 2.0 : 1.0);
+    if (mode == EPI_RESID) vec += n;
+    if (mode == EPI_JACOBI) vec += 2.0 * n;
+    bytes = double(esize) * (vec + elem);
+    const double per_elem = s ? (72 + 45 + 72 + 45 + 21 + 2 + 48 + 72 + 21) : (72 + 45 + 24 + 72 + 21);
+    const double per_node = mode == EPI_JACOBI ? 15.0 : (mode == EPI_RESID ? 6.0 : 3.0);
+    flops = m * per_elem + nn * per_node;
+}
+
 template <class T, int KIND>
 static void run(pbm_grid* g, int k, MarchParams<T>& P, cudaStream_t st, const char* what) {
     int DZ = 1;
     dim3 grid = march_grid(g->L[k].g, DZ);
     P.DZ = DZ;
     if (int(grid.x * grid.y * grid.z) > g->max_blocks) fail(PBM_EINVAL, "grid too large for the partials buffer");
+    constexpr bool fine_op = (KIND == K_FINE_K || KIND == K_FINE_S);
+    const bool prof = fine_op && k == 0 && g->prof_on;
+    if (prof) prof_begin(g, st);
     k_march<T, BY_, KIND><<<grid, dim3(32, BY_), 0, st>>>(P);
     PBM_LAUNCH(what);
+    if (prof) {
+        double bytes = 0.0, flops = 0.0;
+        fine_cost<KIND>(g->L[k].g, P.mode, int(sizeof(T)), bytes, flops);
+        prof_end(g, st, KIND == K_FINE_S ? PBM_OP_S : PBM_OP_K, bytes, flops);
+    }
 }
 
 template <class T>

@@ -3,6 +3,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <limits>
 
 #include "pbm_internal.h"
@@ -27,6 +28,50 @@ void launch_axpy(double* y, const double* x, double kappa, int64_t n, cudaStream
 void launch_scale(const double* a, double* b, double s, int64_t n, cudaStream_t st);
 
 static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ------------------------------------------------------------------------------------------------
+// profiling of the fine-level operator kernel: an event pair per launch, folded on read
+// ------------------------------------------------------------------------------------------------
+void prof_fold(pbm_grid* g) {
+    if (g->prof_used == 0) return;
+    PBM_CUDA(cudaEventSynchronize(g->prof_ev[2 * g->prof_used - 1]));
+    for (size_t i = 0; i < g->prof_used; ++i) {
+        float ms = 0.0f;
+        PBM_CUDA(cudaEventElapsedTime(&ms, g->prof_ev[2 * i], g->prof_ev[2 * i + 1]));
+        g->prof[g->prof_op[i]].total_ms += double(ms);
+    }
+    g->prof_used = 0;
+}
+
+void prof_begin(pbm_grid* g, cudaStream_t st) {
+    if (!g->prof_on) return;
+    if (g->prof_used * 2 == g->prof_ev.size()) {
+        if (g->prof_ev.size() >= 2 * 4096) {
+            prof_fold(g);  // pool full: wait for the recorded launches and reuse the events
+        } else {
+            for (int i = 0; i < 2 * 256; ++i) {
+                cudaEvent_t e;
+                PBM_CUDA(cudaEventCreate(&e));
+                g->prof_ev.push_back(e);
+            }
+            g->prof_op.resize(g->prof_ev.size() / 2);
+        }
+    }
+    PBM_CUDA(cudaEventRecord(g->prof_ev[2 * g->prof_used], st));
+}
+
+void prof_end(pbm_grid* g, cudaStream_t st, int op, double bytes, double flops) {
+    if (!g->prof_on) return;
+    PBM_CUDA(cudaEventRecord(g->prof_ev[2 * g->prof_used + 1], st));
+    g->prof_op[g->prof_used] = op;
+    ++g->prof_used;
+    g->prof[op].launches += 1;
+    g->prof[op].bytes += bytes;
+    g->prof[op].flops += flops;
+}
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 void fail(int code, const std::string& msg) { throw Error{code, msg}; }
@@ -344,6 +389,7 @@ int pbm_destroy_grid(pbm_grid* g) {
     dfree(g->cwork);
     dfree(g->partials);
     dfree(g->sc);
+    for (cudaEvent_t e : g->prof_ev) cudaEventDestroy(e);
     if (g->sc_host) cudaFreeHost(g->sc_host);
     delete g;
     return PBM_OK;
@@ -718,6 +764,27 @@ int pbm_newton_step(pbm_grid* g, pbm_state* s, const double* f_dev, double eps_m
     }
     set_error("");
     return PBM_OK;
+}
+
+int64_t pbm_kernel_launches(void) { return int64_t(g_launches.load(std::memory_order_relaxed)); }
+
+int pbm_profile(pbm_grid* g, int on) {
+    PBM_TRY
+    if (!g) fail(PBM_EINVAL, "null grid");
+    set_device(g);
+    g->prof_on = on != 0;
+    PBM_CATCH
+}
+
+int pbm_profile_read(pbm_grid* g, int op, pbm_profile_stats* out) {
+    PBM_TRY
+    if (!g || !out) fail(PBM_EINVAL, "null argument");
+    if (op != PBM_OP_K && op != PBM_OP_S) fail(PBM_EINVAL, "unknown operator");
+    set_device(g);
+    prof_fold(g);
+    *out = g->prof[op];
+    g->prof[op] = pbm_profile_stats{};
+    PBM_CATCH
 }
 
 int pbm_compliance_grad(pbm_grid* g, const double* u_dev, double* c_dev, const double* f_dev, double* fTu_host,

@@ -21,8 +21,9 @@ struct Error {
 void set_error(const std::string& msg);
 [[noreturn]] void fail(int code, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what);
+void count_launch();  // process-wide counter of the kernels this library launched
 #define PBM_CUDA(x) ::pbm::check_cuda((x), #x)
-#define PBM_LAUNCH(what) ::pbm::check_cuda(cudaGetLastError(), what)
+#define PBM_LAUNCH(what) (::pbm::count_launch(), ::pbm::check_cuda(cudaGetLastError(), what))
 
 // ------------------------------------------------------------------------------------------------
 // geometry of one level (structured grid of cubes)
@@ -218,6 +219,13 @@ struct pbm_grid {
     double alpha = 0.0, V = 0.0;      // of the current state
     double sum_rho1 = 0.0, sum_wr = 0.0, gl2 = 0.0;   // reductions of the coefficient kernel
     int64_t bytes = 0;
+    // optional timing of the fine-level operator kernel (pbm_profile): CUDA event pairs recorded on
+    // the launch stream around every fine apply, folded into the totals when read
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;      // 2 per recorded launch
+    size_t prof_used = 0;
+    pbm_profile_stats prof[2] = {};        // [PBM_OP_K], [PBM_OP_S]
+    std::vector<int> prof_op;              // operator of every recorded launch
 };
 
 namespace pbm {
@@ -250,6 +258,10 @@ void launch_coarse(pbm_grid* g, int k, bool fp32, const ApplyArgs& a, cudaStream
 void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st);
 // per-element c_e = 1/2 u_e^T K_e u_e (masked u), FP64
 void launch_elem_energy(pbm_grid* g, const double* u, const double* v, double* out, cudaStream_t st);
+// profiling hooks around one fine-level operator launch (no-ops unless g->prof_on)
+void prof_begin(pbm_grid* g, cudaStream_t st);
+void prof_end(pbm_grid* g, cudaStream_t st, int op, double bytes, double flops);
+void prof_fold(pbm_grid* g);
 
 // ---- multigrid, mg.cu ----
 void launch_restrict(pbm_grid* g, int k, bool fp32, const void* rf, void* bc, bool with_alpha, double scale,

@@ -86,7 +86,7 @@ void vcycle(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, void* x, in
         oth = t;
     }
     // residual, restriction, coarse correction, prolongation
-    level_apply(g, k, fp32, op_s, args(x, r, EPI_RESID), st);
+    level_apply(g, k, fp32, op_s, args(x, r, EPI_RESID, b), st);
     Level& C = g->L[k + 1];
     void* bc = fp32 ? (void*)C.b32 : (void*)C.b64;
     void* xc = fp32 ? (void*)C.x32 : (void*)C.x64;
