@@ -198,12 +198,16 @@ def run_ours(args):
     # ---- inputs (untimed): density, load, equilibrium displacement, synthetic Newton state ----
     rho = synthetic.density_for(w)
     f_h = synthetic.load_vector(w.nx, w.ny, w.nz, w.loads[0])
-    G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=precision)
     f = t64(f_h)
-    G.set_density(t64(rho))
-    u, uinfo = G.minres_solve("K", f, rtol=1e-10, maxit=3000, check=False)
-    if not uinfo["relres"] <= 1e-8:
+    # the input displacement: equilibrium of K(rho) u = f by the library's FP64 K solve, to the
+    # workload's tolerance (untimed; the 4-corner bridge levels off near 1e-8 in FP64)
+    with pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision="fp64") as G64:
+        G64.set_density(t64(rho))
+        u, uinfo = G64.minres_solve("K", f, rtol=w.rtol, maxit=2000, check=False)
+    if not uinfo["relres"] <= 1e-6:
         raise RuntimeError(f"equilibrium solve of the input state failed: {uinfo}")
+    G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=precision)
+    G.set_density(t64(rho))
     st_h = synthetic.synthetic_state(w, np.zeros(w.n))
     sd = {k: t64(st_h[k]) for k in ("nu_lo", "nu_up", "rho", "mu_lo", "mu_up")}
     sd["u"] = u
@@ -230,9 +234,6 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    G.profile(True)
-    G.profile_read("S")
-    G.profile_read("K")
     n0 = pkg.kernel_launches()
     iters = []
     for i in range(args.steps):
@@ -243,12 +244,23 @@ def run_ours(args):
         iters.append(last["info"]["iterations"])
     torch.cuda.synchronize()
     launches = pkg.kernel_launches() - n0
-    prof = G.profile_read("S")
-    G.profile(False)
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+
+    # ---- the same steps again with every fine-level S launch bracketed by CUDA events on its stream
+    # (pbm_profile): the roofline's kernel durations. Profiled solves launch eagerly, because an
+    # event pair cannot bracket a kernel inside the captured MINRES graph; the kernels are the same.
+    G.profile(True)
+    G.profile_read("S")
+    G.profile_read("K")
+    for i in range(args.steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    prof = G.profile_read("S")
+    G.profile(False)
     total_ms = float(sum(step_ms))
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -307,7 +319,8 @@ def run_ours(args):
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_OPS_PEAK / 1e9, "unit": "G FP64 op/s",
                 "frac": achieved / (FP64_OPS_PEAK / 1e9),
                 "peak_source": "derived: nominal 1.25 TFLOP/s FP64 = 2 FP64 ops/clk/SM x 152 SMs x 2070 MHz",
-                "kernel": "k_march<double, 8, K_FINE_S> (fine-level S apply with fused residual/Jacobi epilogues)"}
+                "kernel": ("fine-level S operator: k_cols_fine<double, S> (element columns) + k_nodes<double> "
+                           "(node sums with the fused residual / Jacobi / dot epilogues), timed as one launch pair")}
         hbm = prof["bytes"] / (prof["total_ms"] / 1e3) / 1e9
         roof["hbm_achieved_gbs"] = hbm
         roof["hbm_frac_of_measured"] = hbm / peaks["hbm_gbs"]

@@ -30,10 +30,11 @@ struct MarchParams {
     const T* d;        // Schur weights (fine S)
     const T* A;        // coarse element matrices (upper triangle, entry-major)
     const T* bord;     // coarse alpha border (n)
-    double s_alpha;    // coarse S_alpha,alpha
+    double s_alpha;    // coarse S_alpha,alpha of the diagonal kinds (set-up)
+    const double* s_alpha_dev;  // coarse S_alpha,alpha of the applies (device scalar)
     T* y;
     const T* b;
-    const T* diag;
+    const T* diag;     // inverse Jacobi diagonal (JACOBI)
     const double* omega;
     int mode;
     int with_alpha;
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(32 * BY) k_march(MarchParams<T> P) {
                         part_dot += double(o) * double(o);
                     } else {
                         const T bb = ldv(P.b, nd + c);
-                        o = xo[c] + T(om) * (bb - yv[c]) / ldv(P.diag, nd + c);
+                        o = xo[c] + T(om) * ((bb - yv[c]) * ldv(P.diag, nd + c));
                         part_dot += double(o) * double(bb);
                     }
                     P.y[nd + c] = o;
@@ -345,7 +346,7 @@ __global__ void __launch_bounds__(32 * BY) k_march(MarchParams<T> P) {
         } else {
             if (P.with_alpha) {
                 double ya = sa;
-                if (KIND == K_COARSE) ya += P.s_alpha * double(xa);
+                if (KIND == K_COARSE) ya += *P.s_alpha_dev * double(xa);
                 double o;
                 if (P.mode == EPI_APPLY) {
                     o = ya;
@@ -355,7 +356,7 @@ __global__ void __launch_bounds__(32 * BY) k_march(MarchParams<T> P) {
                     sd += o * o;
                 } else {
                     const double bb = double(P.b[n]);
-                    o = double(xa) + om * (bb - ya) / double(P.diag[n]);
+                    o = double(xa) + om * ((bb - ya) * double(P.diag[n]));
                     sd += o * bb;
                 }
                 P.y[n] = T(o);
@@ -411,41 +412,14 @@ static MarchParams<T> base_params(pbm_grid* g, int k) {
     return P;
 }
 
-// Algorithmic cost of one fine-level operator launch, for the profiling statistics. Bytes: every
-// input vector / element array read once and the output written once. Operations (add, mul and FMA
-// each counted once) per element: forward transforms 3 x 24, Khat 45 (21 products + 24 couplings),
-// output transform 3 x 24, corner accumulation 21; K(w) scales 24 coefficients; S adds the transform
-// and Khat of u (117), the dot W.X (21), t_e (2) and the combination w Y + t W (48 instead of 24).
-// Per node epilogue: apply 3 (dot), residual 6, Jacobi 15.
-template <int KIND>
-static void fine_cost(const Geom& G, int mode, int esize, double& bytes, double& flops) {
-    const double n = double(G.n()), m = double(G.m()), nn = double(G.nnode());
-    const bool s = KIND == K_FINE_S;
-    double vec = 2.0 * n + (s ? n : 0.0), elem = m * (s ? 2.0 : 1.0);
-    if (mode == EPI_RESID) vec += n;
-    if (mode == EPI_JACOBI) vec += 2.0 * n;
-    bytes = double(esize) * (vec + elem);
-    const double per_elem = s ? (72 + 45 + 72 + 45 + 21 + 2 + 48 + 72 + 21) : (72 + 45 + 24 + 72 + 21);
-    const double per_node = mode == EPI_JACOBI ? 15.0 : (mode == EPI_RESID ? 6.0 : 3.0);
-    flops = m * per_elem + nn * per_node;
-}
-
 template <class T, int KIND>
 static void run(pbm_grid* g, int k, MarchParams<T>& P, cudaStream_t st, const char* what) {
     int DZ = 1;
     dim3 grid = march_grid(g->L[k].g, DZ);
     P.DZ = DZ;
     if (int(grid.x * grid.y * grid.z) > g->max_blocks) fail(PBM_EINVAL, "grid too large for the partials buffer");
-    constexpr bool fine_op = (KIND == K_FINE_K || KIND == K_FINE_S);
-    const bool prof = fine_op && k == 0 && g->prof_on;
-    if (prof) prof_begin(g, st);
     k_march<T, BY_, KIND><<<grid, dim3(32, BY_), 0, st>>>(P);
     PBM_LAUNCH(what);
-    if (prof) {
-        double bytes = 0.0, flops = 0.0;
-        fine_cost<KIND>(g->L[k].g, P.mode, int(sizeof(T)), bytes, flops);
-        prof_end(g, st, KIND == K_FINE_S ? PBM_OP_S : PBM_OP_K, bytes, flops);
-    }
 }
 
 template <class T>
@@ -460,44 +434,29 @@ static void set_epi(MarchParams<T>& P, const ApplyArgs& a) {
     P.dot_slot = a.dot_slot;
 }
 
+// Operator applications run in the two-pass column kernels (colpass.cu); FP64 reads the W_e table,
+// FP32 recomputes W_e from u. The marching kernel above builds the Jacobi diagonals.
 void launch_fine(pbm_grid* g, bool fp32, const void* w, const void* d, const void* u, const ApplyArgs& a,
                  cudaStream_t st) {
-    if (fp32) {
-        auto P = base_params<float>(g, 0);
-        set_epi(P, a);
-        P.w = (const float*)w;
-        P.d = (const float*)d;
-        P.u = (const float*)u;
-        if (u) run<float, K_FINE_S>(g, 0, P, st, "fine S f32");
-        else run<float, K_FINE_K>(g, 0, P, st, "fine K f32");
-    } else {
-        auto P = base_params<double>(g, 0);
-        set_epi(P, a);
-        P.w = (const double*)w;
-        P.d = (const double*)d;
-        P.u = (const double*)u;
-        if (u) run<double, K_FINE_S>(g, 0, P, st, "fine S f64");
-        else run<double, K_FINE_K>(g, 0, P, st, "fine K f64");
+    const bool s = u != nullptr;
+    if (g->prof_on) prof_begin(g, st);
+    if (fp32)
+        cols_fine<float>(g, (const float*)w, s ? (const float*)d : nullptr, nullptr, s ? (const float*)u : nullptr, a,
+                         st);
+    else
+        cols_fine<double>(g, (const double*)w, s ? (const double*)d : nullptr, s ? g->what_hat : nullptr, nullptr, a,
+                          st);
+    if (g->prof_on) {
+        double bytes = 0.0, flops = 0.0;
+        cols_cost(g->L[0].g, s, fp32, a.mode, fp32 ? 4 : 8, bytes, flops);
+        prof_end(g, st, s ? PBM_OP_S : PBM_OP_K, bytes, flops);
     }
 }
 
 void launch_coarse(pbm_grid* g, int k, bool fp32, const ApplyArgs& a, cudaStream_t st) {
     Level& L = g->L[k];
-    if (fp32) {
-        auto P = base_params<float>(g, k);
-        set_epi(P, a);
-        P.A = L.A32;
-        P.bord = L.bord32;
-        P.s_alpha = g->s_alpha;
-        run<float, K_COARSE>(g, k, P, st, "coarse f32");
-    } else {
-        auto P = base_params<double>(g, k);
-        set_epi(P, a);
-        P.A = L.A64;
-        P.bord = L.bord64;
-        P.s_alpha = g->s_alpha;
-        run<double, K_COARSE>(g, k, P, st, "coarse f64");
-    }
+    if (fp32) cols_coarse<float>(g, k, L.A32, L.bord32, a, st);
+    else cols_coarse<double>(g, k, L.A64, L.bord64, a, st);
 }
 
 void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st) {
@@ -521,7 +480,8 @@ void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st) {
         if (!op_s) P.s_alpha = 1.0;
         run<double, K_COARSE_DIAG>(g, k, P, st, "coarse diag");
     }
-    if (L.diag32) launch_cast(L.diag64, false, L.diag32, true, L.g.n() + 1, st);
+    launch_inverse(L.diag64, L.idiag64, L.g.n() + 1, st);
+    if (L.idiag32) launch_cast(L.idiag64, false, L.idiag32, true, L.g.n() + 1, st);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -31,6 +31,8 @@ static thread_local std::string g_last_error;
 static std::atomic<long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch_add(int64_t delta) { g_launches.fetch_add((long long)delta, std::memory_order_relaxed); }
+int64_t launch_count() { return int64_t(g_launches.load(std::memory_order_relaxed)); }
 
 // ------------------------------------------------------------------------------------------------
 // profiling of the fine-level operator kernel: an event pair per launch, folded on read
@@ -126,7 +128,7 @@ static void element_matrix(double E, double nu, double h, double* K) {
                 }
 }
 
-static void element_hat(double E, double nu, double h, KeHat& K) {
+void element_hat(double E, double nu, double h, KeHat& K) {
     const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
     const double mu = E / (2.0 * (1.0 + nu));
     auto mm = [](int bit) { return bit ? 1.0 / 12.0 : 0.25; };
@@ -290,13 +292,15 @@ int pbm_create_grid(const pbm_grid_desc* d, pbm_grid** out) {
         }
         L.bord64 = (double*)dalloc(g, sizeof(double) * nk);
         L.diag64 = (double*)dalloc(g, sizeof(double) * nk);
+        L.idiag64 = (double*)dalloc(g, sizeof(double) * nk);
+        L.sdiag64 = (double*)dalloc(g, sizeof(double) * nk);
         L.x64 = (double*)dalloc(g, sizeof(double) * nk);
         L.b64 = (double*)dalloc(g, sizeof(double) * nk);
         L.r64 = (double*)dalloc(g, sizeof(double) * nk);
         L.t64 = (double*)dalloc(g, sizeof(double) * nk);
         if (mixed) {
             L.bord32 = (float*)dalloc(g, sizeof(float) * nk);
-            L.diag32 = (float*)dalloc(g, sizeof(float) * nk);
+            L.idiag32 = (float*)dalloc(g, sizeof(float) * nk);
             L.x32 = (float*)dalloc(g, sizeof(float) * nk);
             L.b32 = (float*)dalloc(g, sizeof(float) * nk);
             L.r32 = (float*)dalloc(g, sizeof(float) * nk);
@@ -312,6 +316,12 @@ int pbm_create_grid(const pbm_grid_desc* d, pbm_grid** out) {
     g->wr64 = (double*)dalloc(g, sizeof(double) * m);
     g->u64 = (double*)dalloc(g, sizeof(double) * (n + 1));
     g->what = (double*)dalloc(g, sizeof(double) * 24 * m);
+    g->what_hat = (double*)dalloc(g, sizeof(double) * 21 * m);
+    {
+        const int64_t ncol = int64_t(d->nx) * d->ny;
+        g->qa = dalloc(g, sizeof(double) * 12 * ncol * (d->nz + 1));
+        g->qb = dalloc(g, sizeof(double) * 12 * ncol * d->nz);
+    }
     g->nwt = (double*)dalloc(g, sizeof(double) * (2 * n + 1 + 2 * m));
     PBM_CUDA(cudaMemset(g->u64, 0, sizeof(double) * (n + 1)));
     if (mixed) {
@@ -320,14 +330,14 @@ int pbm_create_grid(const pbm_grid_desc* d, pbm_grid** out) {
         g->d32 = (float*)dalloc(g, sizeof(float) * m);
         g->u32 = (float*)dalloc(g, sizeof(float) * (n + 1));
     }
-    for (int i = 0; i < 10; ++i) {
+    for (int i = 0; i < 12; ++i) {
         g->kv64[i] = (double*)dalloc(g, sizeof(double) * (n + 1));
         if (mixed) g->kv32[i] = (float*)dalloc(g, sizeof(float) * (n + 1));
     }
     g->nc = int(g->L[d->levels - 1].g.n());
     const size_t N = size_t(g->nc) + 1;
     g->cinv = (double*)dalloc(g, sizeof(double) * N * N);
-    g->cwork = (double*)dalloc(g, sizeof(double) * N * N);
+    g->cwork = (double*)dalloc(g, sizeof(double) * (2 * N * N + N));   // L, L^{-1}, 1 / diag(L)
     g->max_blocks = 1 << 16;
     g->partials = (double*)dalloc(g, sizeof(double) * 8 * size_t(g->max_blocks));
     g->sc = (DevScalars*)dalloc(g, sizeof(DevScalars));
@@ -357,7 +367,9 @@ int pbm_destroy_grid(pbm_grid* g) {
         dfree(L.bord64);
         dfree(L.bord32);
         dfree(L.diag64);
-        dfree(L.diag32);
+        dfree(L.idiag64);
+        dfree(L.sdiag64);
+        dfree(L.idiag32);
         dfree(L.x64);
         dfree(L.b64);
         dfree(L.r64);
@@ -380,11 +392,17 @@ int pbm_destroy_grid(pbm_grid* g) {
     dfree(g->u64);
     dfree(g->u32);
     dfree(g->what);
+    dfree(g->what_hat);
+    dfree(g->qa);
+    dfree(g->qb);
     dfree(g->nwt);
-    for (int i = 0; i < 10; ++i) {
+    for (int i = 0; i < 12; ++i) {
         dfree(g->kv64[i]);
         dfree(g->kv32[i]);
     }
+    for (cudaGraphExec_t e : g->mr_graph)
+        if (e) cudaGraphExecDestroy(e);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     dfree(g->cinv);
     dfree(g->cwork);
     dfree(g->partials);
@@ -539,6 +557,7 @@ int pbm_set_state(pbm_grid* g, const pbm_state* s, void* stream) {
     PBM_CUDA(cudaStreamSynchronize(st));
     if (g->sc_host->red[12] != 0.0) fail(PBM_ENONFINITE, "non-finite or non-positive Newton coefficients");
     g->s_alpha = g->sc_host->red[8];
+    PBM_CUDA(cudaMemcpyAsync(&g->sc->salpha, &g->sc->red[8], sizeof(double), cudaMemcpyDeviceToDevice, st));
     g->sum_rho1 = g->sc_host->red[9];
     g->sum_wr = g->sc_host->red[10];
     g->gl2 = g->sc_host->red[11];

@@ -1,0 +1,604 @@
+// Two-pass operator application: element columns, then nodes.
+//
+// Pass 1 gives every thread one element column (i, j) and a chunk of L element layers of it (the
+// coarse levels use L = 1 and split each element's 24 rows over eight threads). For each layer it
+// forms the element's contribution to the 8 corner nodes and writes, per node plane, the 4 corner
+// values of the column ("plane quads") to scratch:
+//   QA[k]  plane k as bottom face of layer k (plus, inside a chunk, the top face of layer k - 1),
+//   QB[c]  the top face of the last layer of chunk c (plane min((c + 1) L, nz)).
+// Pass 2 gives every thread one node, sums the quads of the (up to) four columns around it in a
+// fixed order and applies the epilogue (plain apply, residual b - A x, damped-Jacobi sweep), the
+// dot products of the Krylov solvers and, for S, the alpha row. No element is computed twice, no
+// atomics are used and the summation order is fixed, so results are bit-reproducible.
+//
+// On the fine level the element matrix is applied in the factored form K_e = H^T Khat H (see
+// pbm_internal.h). The forward transform is split: the xy part of each node plane's quad is
+// computed once and shared by the two element layers that touch the plane, the z part is per
+// element; the inverse transform runs the z part per element, adds the top face of the layer below
+// (same thread), and the xy part once per plane. For S the transformed vector W_e = Khat H u_e is
+// read from a table built at set-up (pbm_set_state), so the rank-one term costs a dot product and
+// an axpy of 21 coefficients:  Y_e = rho'_e Khat X_e + t_e W_e,  t_e = d_e (W_e . X_e - x_alpha).
+//
+// This is the FP64 path: GB300 issues about two FP64 operations per clock per SM, so the FP64
+// operator is bound by the FP64 pipe, not by HBM; the split removes the halo elements that a
+// tiled single pass recomputes and lets every SM take an equal share of the columns.
+#include "pbm_internal.h"
+
+namespace pbm {
+
+constexpr int CB = 128;   // threads per pass-1 CTA
+constexpr int NB2 = 256;  // threads per pass-2 CTA
+
+template <class T>
+struct ColArgs {
+    int nx, ny, nz, support, L, nchunk;
+    int64_t n, m, ncol;
+    const T* x;        // gathered vector (n (+1))
+    const T* w;        // element weights (fine)
+    const T* d;        // Schur weights (fine S)
+    const T* what;     // 21 x m transformed K_e u_e (fine S, table mode), row r = 7 c + q - 1
+    const T* u;        // displacement (fine S, recompute mode)
+    const T* A;        // coarse element matrices (300 x m, upper triangle, entry-major)
+    KeHatT<T> K;
+    T* QA;
+    T* QB;
+    double* apart;     // per-CTA partial sums of -t_e (fine S)
+};
+
+template <class T>
+struct NodeArgs {
+    int nx, ny, nz, support, L;
+    int64_t n, ncol;
+    const T* QA;
+    const T* QB;
+    const T* x;
+    T* y;
+    const T* b;
+    const T* idiag;        // inverse Jacobi diagonal (JACOBI)
+    const double* omega;   // device scalar (JACOBI)
+    const T* bord;         // coarse alpha border (n) or nullptr
+    const double* s_alpha; // coarse S_alpha,alpha (device scalar)
+    int with_alpha;
+    int mode;
+    int dot_slot;
+    const double* apart;   // pass-1 partials (fine S) or nullptr
+    int napart;
+    double* partials;      // 2 * gridDim.x
+    DevScalars* sc;
+};
+
+// forward xy transform of the masked node quad (i .. i+1, j .. j+1) of plane k of vector v
+template <class T>
+__device__ __forceinline__ void load_quad(const ColArgs<T>& P, const T* __restrict__ vec, int i, int j, int k,
+                                          T (&Q)[3][4]) {
+    const int64_t sxn = P.nx + 1, sxy = int64_t(P.nx + 1) * (P.ny + 1);
+    T v[3][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int ii = i + (a & 1), jj = j + (a >> 1);
+        const bool fx = node_fixed(P.support, P.nx, P.ny, P.nz, ii, jj, k);
+        const int64_t nd = 3 * (ii + sxn * jj + sxy * k);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c][a] = fx ? T(0) : __ldg(vec + nd + c);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T s0 = v[c][0] + v[c][1], d0 = v[c][1] - v[c][0];
+        const T s1 = v[c][2] + v[c][3], d1 = v[c][3] - v[c][2];
+        Q[c][0] = s0 + s1;
+        Q[c][1] = d0 + d1;
+        Q[c][2] = s1 - s0;
+        Q[c][3] = d1 - d0;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void load_quad(const ColArgs<T>& P, int i, int j, int k, T (&Q)[3][4]) {
+    load_quad(P, P.x, i, j, k, Q);
+}
+
+// inverse xy transform of a transformed plane quad, stored as nodal corner values
+template <class T>
+__device__ __forceinline__ void store_quad(T* Q, int64_t slot, int64_t ncol, int64_t col, const T (&V)[3][4]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T a0 = V[c][0] - V[c][1], a1 = V[c][0] + V[c][1];
+        const T a2 = V[c][2] - V[c][3], a3 = V[c][2] + V[c][3];
+        T* q = Q + (slot * 12 + c) * ncol + col;
+        q[0] = a0 - a2;           // corner 0 (i,   j)
+        q[3 * ncol] = a1 - a3;    // corner 1 (i+1, j)
+        q[6 * ncol] = a0 + a2;    // corner 2 (i,   j+1)
+        q[9 * ncol] = a1 + a3;    // corner 3 (i+1, j+1)
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ double cta_sum1(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NT / 32; ++w) s += sh[w];
+    return s;
+}
+
+// ------------------------------------------------------------------------------------------------
+// pass 1, fine level: K(w) x (S = false) or the S operator (S = true)
+// ------------------------------------------------------------------------------------------------
+// MODE 0: K(w) x. MODE 1: S with W_e read from the table (FP64). MODE 2: S with W_e recomputed
+// from the plane quads of u (FP32: the recomputation costs ALU the FP32 pipe has to spare, the
+// table would cost 21 values per element of HBM traffic).
+template <class T, int MODE>
+__global__ void __launch_bounds__(CB) k_cols_fine(ColArgs<T> P) {
+    constexpr bool S = MODE != 0;
+    __shared__ double sh[CB / 32];
+    const int64_t tid = blockIdx.x * int64_t(CB) + threadIdx.x;
+    double apart = 0.0;
+    if (tid < P.ncol * P.nchunk) {
+        const int64_t col = tid % P.ncol;
+        const int chunk = int(tid / P.ncol);
+        const int i = int(col % P.nx), j = int(col / P.nx);
+        const int k0 = chunk * P.L, k1 = min(k0 + P.L, P.nz);
+        const T xa = S ? P.x[P.n] : T(0);
+        T Qlo[3][4], Qhi[3][4], carry[3][4];
+        T Ulo[3][4], Uhi[3][4];
+        load_quad(P, i, j, k0, Qlo);
+        if (MODE == 2) load_quad(P, P.u, i, j, k0, Ulo);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) carry[c][q] = T(0);
+        for (int k = k0; k < k1; ++k) {
+            load_quad(P, i, j, k + 1, Qhi);
+            if (MODE == 2) load_quad(P, P.u, i, j, k + 1, Uhi);
+            const int64_t e = col + P.ncol * k;
+            T X[3][8], Y[3][8];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    X[c][q] = Qlo[c][q] + Qhi[c][q];
+                    X[c][q + 4] = Qhi[c][q] - Qlo[c][q];
+                }
+            khat_apply(P.K, X, Y);
+            const T we = __ldg(P.w + e);
+            if (S) {
+                T Wt[3][8];
+                if (MODE == 2) {
+                    T U[3][8];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            U[c][q] = Ulo[c][q] + Uhi[c][q];
+                            U[c][q + 4] = Uhi[c][q] - Ulo[c][q];
+                            Ulo[c][q] = Uhi[c][q];
+                        }
+                    khat_apply(P.K, U, Wt);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        Wt[c][0] = T(0);
+#pragma unroll
+                        for (int q = 1; q < 8; ++q) Wt[c][q] = __ldg(P.what + int64_t(7 * c + q - 1) * P.m + e);
+                    }
+                }
+                T dot = T(0);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int q = 1; q < 8; ++q) dot += Wt[c][q] * X[c][q];
+                const T t = __ldg(P.d + e) * (dot - xa);
+                apart -= double(t);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int q = 1; q < 8; ++q) Y[c][q] = we * Y[c][q] + t * Wt[c][q];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int q = 1; q < 8; ++q) Y[c][q] *= we;
+            }
+            // z part of the inverse transform: bottom face (plane k) and top face (plane k + 1)
+            T Bq[3][4];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    Bq[c][q] = carry[c][q] + (Y[c][q] - Y[c][q + 4]);
+                    carry[c][q] = Y[c][q] + Y[c][q + 4];
+                    Qlo[c][q] = Qhi[c][q];
+                }
+            store_quad(P.QA, k, P.ncol, col, Bq);
+        }
+        store_quad(P.QB, chunk, P.ncol, col, carry);
+    }
+    if (S) {
+        const double s = cta_sum1<CB>(apart, sh);
+        if (threadIdx.x == 0) P.apart[blockIdx.x] = s;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// pass 1, coarse levels: explicit element matrices. Thread (e, a) forms the 3 rows of local node a
+// of element e (72 FMAs): FP64 work per thread stays short, so the small coarse levels are not
+// limited by one thread's chain of dependent FP64 instructions. Threads of one warp share a, so
+// the matrix reads (entry-major) are coalesced over consecutive elements.
+// ------------------------------------------------------------------------------------------------
+template <class T, int A>
+__device__ __forceinline__ void coarse_node_rows(const T* __restrict__ Ae, int64_t m, const T (&xe)[24], T (&y)[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int r = 3 * A + c;
+        T acc = T(0);
+#pragma unroll
+        for (int s = 0; s < 24; ++s) {
+            const int t = r <= s ? tri_index(r, s) : tri_index(s, r);
+            acc += __ldg(Ae + int64_t(t) * m) * xe[s];
+        }
+        y[c] = acc;
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(CB) k_cols_coarse(ColArgs<T> P) {
+    const int64_t tid = blockIdx.x * int64_t(CB) + threadIdx.x;
+    if (tid >= 8 * P.m) return;
+    const int a = int(tid / P.m);
+    const int64_t e = tid - a * P.m;
+    const int64_t col = e % P.ncol;
+    const int k = int(e / P.ncol);
+    const int i = int(col % P.nx), j = int(col / P.nx);
+    const int64_t sxn = P.nx + 1, sxy = int64_t(P.nx + 1) * (P.ny + 1);
+    T xe[24];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int ii = i + (b & 1), jj = j + ((b >> 1) & 1), kk = k + (b >> 2);
+        const bool fx = node_fixed(P.support, P.nx, P.ny, P.nz, ii, jj, kk);
+        const int64_t nd = 3 * (ii + sxn * jj + sxy * kk);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xe[3 * b + c] = fx ? T(0) : __ldg(P.x + nd + c);
+    }
+    T y[3];
+    switch (a) {
+        case 0: coarse_node_rows<T, 0>(P.A + e, P.m, xe, y); break;
+        case 1: coarse_node_rows<T, 1>(P.A + e, P.m, xe, y); break;
+        case 2: coarse_node_rows<T, 2>(P.A + e, P.m, xe, y); break;
+        case 3: coarse_node_rows<T, 3>(P.A + e, P.m, xe, y); break;
+        case 4: coarse_node_rows<T, 4>(P.A + e, P.m, xe, y); break;
+        case 5: coarse_node_rows<T, 5>(P.A + e, P.m, xe, y); break;
+        case 6: coarse_node_rows<T, 6>(P.A + e, P.m, xe, y); break;
+        default: coarse_node_rows<T, 7>(P.A + e, P.m, xe, y); break;
+    }
+    // bottom nodes (a < 4) go to QA[k], top nodes to QB[k]; corner a & 3
+    T* Q = (a < 4 ? P.QA : P.QB) + (int64_t(k) * 12 + 3 * (a & 3)) * P.ncol + col;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Q[c * P.ncol] = y[c];
+}
+
+// ------------------------------------------------------------------------------------------------
+// pass 2: node sums, epilogue, dots, alpha row
+// ------------------------------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(NB2) k_nodes(NodeArgs<T> P) {
+    __shared__ double sh[NB2 / 32];
+    __shared__ bool s_last;
+    const int nx = P.nx, ny = P.ny, nz = P.nz, L = P.L;
+    const int64_t nn = P.n / 3;
+    const int64_t sx = nx + 1, sxy = int64_t(nx + 1) * (ny + 1);
+    const T xa = P.with_alpha ? P.x[P.n] : T(0);
+    const double om = P.mode == EPI_JACOBI ? *P.omega : 0.0;
+    double pd = 0.0, pa = 0.0;
+    for (int64_t nd = blockIdx.x * int64_t(NB2) + threadIdx.x; nd < nn; nd += int64_t(gridDim.x) * NB2) {
+        const int I = int(nd % sx), J = int((nd / sx) % (ny + 1)), K = int(nd / sxy);
+        const bool hasA = K < nz;
+        const bool hasB = K > 0 && (K % L == 0 || K == nz);
+        const int64_t oa = int64_t(K) * 12 * P.ncol, ob = int64_t(K > 0 ? (K - 1) / L : 0) * 12 * P.ncol;
+        T s[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int dj = 1; dj >= 0; --dj)
+#pragma unroll
+            for (int di = 1; di >= 0; --di) {
+                const int ii = I - di, jj = J - dj;
+                if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) continue;
+                const int64_t col = ii + int64_t(nx) * jj;
+                const int a = di + 2 * dj;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int64_t r = int64_t(3 * a + c) * P.ncol + col;
+                    if (hasA) s[c] += P.QA[oa + r];
+                    if (hasB) s[c] += P.QB[ob + r];
+                }
+            }
+        const int64_t d0 = 3 * nd;
+        const bool fixed = node_fixed(P.support, nx, ny, nz, I, J, K);
+        T xo[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xo[c] = P.x[d0 + c];
+        if (P.bord) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const T bc = P.bord[d0 + c];
+                s[c] += bc * xa;
+                pa += double(bc) * double(xo[c]);
+            }
+        }
+        if (fixed) {
+            s[0] = xo[0];
+            s[1] = xo[1];
+            s[2] = xo[2];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            T o;
+            if (P.mode == EPI_APPLY) {
+                o = s[c];
+                pd += double(o) * double(xo[c]);
+            } else if (P.mode == EPI_RESID) {
+                o = P.b[d0 + c] - s[c];
+                pd += double(o) * double(o);
+            } else {
+                const T bb = P.b[d0 + c];
+                o = xo[c] + T(om) * ((bb - s[c]) * P.idiag[d0 + c]);
+                pd += double(o) * double(bb);
+            }
+            P.y[d0 + c] = o;
+        }
+    }
+    // per-CTA partials, then the last CTA finishes the alpha entry and the dot in a fixed order
+    const double bd = cta_sum1<NB2>(pd, sh);
+    __syncthreads();
+    const double ba = cta_sum1<NB2>(pa, sh);
+    const int nblk = gridDim.x;
+    if (threadIdx.x == 0) {
+        P.partials[blockIdx.x] = bd;
+        P.partials[nblk + blockIdx.x] = ba;
+        __threadfence();
+        s_last = atomicAdd(&P.sc->counter[0], 1u) == unsigned(nblk - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // every thread of the last CTA sums a fixed strided subset; the CTA sum has a fixed tree order
+    double td = 0.0, ta = 0.0;
+    for (int q = threadIdx.x; q < nblk; q += NB2) {
+        td += ((volatile double*)P.partials)[q];
+        ta += ((volatile double*)P.partials)[nblk + q];
+    }
+    if (P.apart)
+        for (int q = threadIdx.x; q < P.napart; q += NB2) ta += ((volatile const double*)P.apart)[q];
+    __syncthreads();
+    double sd = cta_sum1<NB2>(td, sh);
+    __syncthreads();
+    double sa = cta_sum1<NB2>(ta, sh);
+    if (threadIdx.x != 0) return;
+    P.sc->counter[0] = 0u;
+    if (P.with_alpha) {
+        const int64_t n = P.n;
+        const double ya = sa + (P.bord ? *P.s_alpha * double(xa) : 0.0);
+        double o;
+        if (P.mode == EPI_APPLY) {
+            o = ya;
+            sd += o * double(xa);
+        } else if (P.mode == EPI_RESID) {
+            o = double(P.b[n]) - ya;
+            sd += o * o;
+        } else {
+            const double bb = double(P.b[n]);
+            o = double(xa) + om * ((bb - ya) * double(P.idiag[n]));
+            sd += o * bb;
+        }
+        P.y[n] = T(o);
+    }
+    if (P.dot_slot >= 0) P.sc->red[P.dot_slot] = sd;
+}
+
+// ------------------------------------------------------------------------------------------------
+// launch wrappers
+// ------------------------------------------------------------------------------------------------
+// chunk length of the fine pass: the longest of 8, 4, 2, 1 layers that still gives every SM
+// sub-partition (152 x 4) at least two warps of columns
+static int fine_chunk(const Geom& G) {
+    const int64_t ncol = int64_t(G.nx) * G.ny;
+    const int64_t want = 152LL * 4 * 32 * 2;
+    for (int L = 8; L > 1; L >>= 1)
+        if (ncol * ((G.nz + L - 1) / L) >= want) return L;
+    return 1;
+}
+
+template <class T>
+static void node_pass(const ColEnv& env, const Geom& G, const ApplyArgs& a, int L, const T* bord,
+                      const double* s_alpha, const double* apart, int napart, int64_t off, cudaStream_t st) {
+    NodeArgs<T> N{};
+    N.nx = G.nx;
+    N.ny = G.ny;
+    N.nz = G.nz;
+    N.support = G.support;
+    N.L = L;
+    N.n = G.n();
+    N.ncol = int64_t(G.nx) * G.ny;
+    N.QA = (const T*)env.qa;
+    N.QB = (const T*)env.qb;
+    N.x = (const T*)a.x;
+    N.y = (T*)a.y;
+    N.b = (const T*)a.b;
+    N.idiag = (const T*)a.diag;
+    N.omega = a.omega;
+    N.bord = a.with_alpha ? bord : nullptr;
+    N.s_alpha = s_alpha;
+    N.with_alpha = a.with_alpha ? 1 : 0;
+    N.mode = a.mode;
+    N.dot_slot = a.dot_slot;
+    N.apart = apart;
+    N.napart = napart;
+    N.partials = env.partials + off;
+    N.sc = env.sc;
+    const int64_t nn = G.nnode();
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nn + NB2 - 1) / NB2, 152 * 8)));
+    if (off + 2 * blocks > env.partials_len) fail(PBM_EINVAL, "grid too large for the partials buffer");
+    k_nodes<T><<<blocks, NB2, 0, st>>>(N);
+    PBM_LAUNCH("node pass");
+}
+
+template <class T>
+static void fill_khat_t(KeHatT<T>& out, const KeHat& K) {
+    for (int c = 0; c < 3; ++c)
+        for (int q = 0; q < 8; ++q) out.dg[c][q] = T(K.dg[c][q]);
+    for (int b = 0; b < 2; ++b) {
+        out.lam4[b] = T(K.lam4[b]);
+        out.mu4[b] = T(K.mu4[b]);
+    }
+}
+
+// Algorithmic cost of one fine-level operator application by the column passes (profiling
+// statistics). Bytes: every input vector and element array read once, the output written once
+// (the quad scratch is not algorithmic). Operations (add, mul, FMA each counted once) per element:
+// xy transforms of the plane quads 24 (L + 1) / L in and out, z transforms 24 in and out, Khat 45,
+// scaling by the weight 21, carry 12 (L - 1) / L; S adds the dot W.X 21, t_e 2 and the axpy t W 21,
+// and, when W_e is recomputed from u, the transforms and Khat of u.
+// Per node: 12 quad sums plus the epilogue (apply 3, residual 6, Jacobi 12).
+void cols_cost(const Geom& G, bool op_s, bool recompute_w, int mode, int esize, double& bytes, double& flops) {
+    const double n = double(G.n()), m = double(G.m()), nn = double(G.nnode());
+    double vec = 2.0 * n + (op_s ? n : 0.0), elem = m * (op_s ? 2.0 : 1.0);
+    if (mode == EPI_RESID) vec += n;
+    if (mode == EPI_JACOBI) vec += 2.0 * n;
+    bytes = double(esize) * (vec + elem);
+    const double L = double(fine_chunk(G));
+    double per_elem = 2.0 * 24.0 * (L + 1.0) / L + 48.0 + 45.0 + 21.0 + 12.0 * (L - 1.0) / L;
+    if (op_s) per_elem += 44.0;
+    if (op_s && recompute_w) per_elem += 24.0 * (L + 1.0) / L + 24.0 + 45.0;   // quads, z part and Khat of u
+    const double per_node = 12.0 + (mode == EPI_JACOBI ? 12.0 : (mode == EPI_RESID ? 6.0 : 3.0));
+    flops = m * per_elem + nn * per_node;
+}
+
+template <class T>
+void cols_fine_env(const ColEnv& env, const Geom& G, const KeHat& kh, const T* w, const T* d, const T* what,
+                   const T* u, const ApplyArgs& a, cudaStream_t st) {
+    ColArgs<T> P{};
+    P.nx = G.nx;
+    P.ny = G.ny;
+    P.nz = G.nz;
+    P.support = G.support;
+    P.L = fine_chunk(G);
+    P.nchunk = (G.nz + P.L - 1) / P.L;
+    P.n = G.n();
+    P.m = G.m();
+    P.ncol = int64_t(G.nx) * G.ny;
+    P.x = (const T*)a.x;
+    P.w = w;
+    P.d = d;
+    P.what = what;
+    P.u = u;
+    fill_khat_t(P.K, kh);
+    P.QA = (T*)env.qa;
+    P.QB = (T*)env.qb;
+    P.apart = env.partials;
+    const int64_t threads = P.ncol * P.nchunk;
+    const int blocks = int((threads + CB - 1) / CB);
+    const bool s = d != nullptr;
+    if (s && blocks > env.partials_len / 2) fail(PBM_EINVAL, "grid too large for the partials buffer");
+    if (s && what) k_cols_fine<T, 1><<<blocks, CB, 0, st>>>(P);
+    else if (s) k_cols_fine<T, 2><<<blocks, CB, 0, st>>>(P);
+    else k_cols_fine<T, 0><<<blocks, CB, 0, st>>>(P);
+    PBM_LAUNCH("fine column pass");
+    node_pass<T>(env, G, a, P.L, (const T*)nullptr, nullptr, s ? env.partials : nullptr, s ? blocks : 0,
+                 s ? blocks : 0, st);
+}
+
+int64_t cols_scratch_entries(const Geom& G) {
+    const int64_t ncol = int64_t(G.nx) * G.ny;
+    const int L = fine_chunk(G);
+    return 12 * ncol * (G.nz + 1) + 12 * ncol * ((G.nz + L - 1) / L);
+}
+
+static ColEnv env_of(pbm_grid* g) {
+    ColEnv e;
+    e.qa = g->qa;
+    e.qb = g->qb;
+    e.partials = g->partials;
+    e.partials_len = int64_t(8) * g->max_blocks;
+    e.sc = g->sc;
+    return e;
+}
+
+template <class T>
+void cols_fine(pbm_grid* g, const T* w, const T* d, const T* what, const T* u, const ApplyArgs& a, cudaStream_t st) {
+    cols_fine_env<T>(env_of(g), g->L[0].g, g->kehat, w, d, what, u, a, st);
+}
+
+template <class T>
+void cols_coarse(pbm_grid* g, int k, const T* A, const T* bord, const ApplyArgs& a, cudaStream_t st) {
+    const Geom& G = g->L[k].g;
+    const ColEnv env = env_of(g);
+    ColArgs<T> P{};
+    P.nx = G.nx;
+    P.ny = G.ny;
+    P.nz = G.nz;
+    P.support = G.support;
+    P.L = 1;
+    P.nchunk = G.nz;
+    P.n = G.n();
+    P.m = G.m();
+    P.ncol = int64_t(G.nx) * G.ny;
+    P.x = (const T*)a.x;
+    P.A = A;
+    P.QA = (T*)env.qa;
+    P.QB = (T*)env.qb;
+    const int blocks = int((8 * P.m + CB - 1) / CB);
+    k_cols_coarse<T><<<blocks, CB, 0, st>>>(P);
+    PBM_LAUNCH("coarse column pass");
+    node_pass<T>(env, G, a, 1, bord, &g->sc->salpha, nullptr, 0, 0, st);
+}
+
+template void cols_fine<double>(pbm_grid*, const double*, const double*, const double*, const double*,
+                                const ApplyArgs&, cudaStream_t);
+template void cols_fine<float>(pbm_grid*, const float*, const float*, const float*, const float*, const ApplyArgs&,
+                               cudaStream_t);
+template void cols_coarse<double>(pbm_grid*, int, const double*, const double*, const ApplyArgs&, cudaStream_t);
+template void cols_coarse<float>(pbm_grid*, int, const float*, const float*, const ApplyArgs&, cudaStream_t);
+template void cols_fine_env<double>(const ColEnv&, const Geom&, const KeHat&, const double*, const double*,
+                                    const double*, const double*, const ApplyArgs&, cudaStream_t);
+
+// ------------------------------------------------------------------------------------------------
+// W_e = Khat H u_e (21 coefficients per element, FP64) for the fine S pass
+// ------------------------------------------------------------------------------------------------
+__global__ void k_what_hat(int nx, int ny, int nz, int support, const double* __restrict__ u,
+                           double* __restrict__ wh, KeHatT<double> K) {
+    const int64_t m = int64_t(nx) * ny * nz;
+    const int64_t sxn = nx + 1, sxy = int64_t(nx + 1) * (ny + 1);
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
+        const int i = int(e % nx), j = int((e / nx) % ny), k = int(e / (int64_t(nx) * ny));
+        double U[3][8], W[3][8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const int ii = i + (a & 1), jj = j + ((a >> 1) & 1), kk = k + (a >> 2);
+            const bool fx = node_fixed(support, nx, ny, nz, ii, jj, kk);
+            const int64_t nd = 3 * (ii + sxn * jj + sxy * kk);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) U[c][a] = fx ? 0.0 : u[nd + c];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) wht_fwd(U[c]);
+        khat_apply(K, U, W);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int q = 1; q < 8; ++q) wh[int64_t(7 * c + q - 1) * m + e] = W[c][q];
+    }
+}
+
+void launch_what_hat(pbm_grid* g, cudaStream_t st) {
+    const Geom& G = g->L[0].g;
+    KeHatT<double> K;
+    fill_khat_t(K, g->kehat);
+    const int64_t m = G.m();
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((m + 127) / 128, 152 * 16)));
+    k_what_hat<<<blocks, 128, 0, st>>>(G.nx, G.ny, G.nz, G.support, g->u64, g->what_hat, K);
+    PBM_LAUNCH("what hat");
+}
+
+}  // namespace pbm

@@ -68,13 +68,26 @@ void launch_cast(const void* src, bool src32, void* dst, bool dst32, int64_t n, 
 
 void vec_zero(void* p, size_t bytes, cudaStream_t st) { PBM_CUDA(cudaMemsetAsync(p, 0, bytes, st)); }
 
-// x = omega D^{-1} b
+// x = omega D^{-1} b (idiag = D^{-1})
 template <class T>
-__global__ void k_first_jacobi(const T* __restrict__ b, const T* __restrict__ diag, const double* __restrict__ om,
+__global__ void k_first_jacobi(const T* __restrict__ b, const T* __restrict__ idiag, const double* __restrict__ om,
                                T* __restrict__ x, int64_t n) {
-    const double w = *om;
+    const T w = T(*om);
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-        x[i] = T(w * double(b[i]) / double(diag[i]));
+        x[i] = w * (b[i] * idiag[i]);
+}
+
+__global__ void k_inverse(const double* __restrict__ x, double* __restrict__ y, int64_t n, int sq) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        y[i] = sq ? 1.0 / sqrt(x[i]) : 1.0 / x[i];
+}
+void launch_inverse(const double* x, double* y, int64_t n, cudaStream_t st) {
+    k_inverse<<<VG, VB, 0, st>>>(x, y, n, 0);
+    PBM_LAUNCH("inverse");
+}
+void launch_inverse_sqrt(const double* x, double* y, int64_t n, cudaStream_t st) {
+    k_inverse<<<VG, VB, 0, st>>>(x, y, n, 1);
+    PBM_LAUNCH("inverse sqrt");
 }
 
 void launch_scale_diag_first(pbm_grid* g, int k, bool fp32, const void* b, void* x, bool with_alpha,
@@ -82,8 +95,8 @@ void launch_scale_diag_first(pbm_grid* g, int k, bool fp32, const void* b, void*
     Level& L = g->L[k];
     const int64_t n = L.g.n() + (with_alpha ? 1 : 0);
     const double* om = &g->sc->mr[16 + k];
-    if (fp32) k_first_jacobi<float><<<VG, VB, 0, st>>>((const float*)b, L.diag32, om, (float*)x, n);
-    else k_first_jacobi<double><<<VG, VB, 0, st>>>((const double*)b, L.diag64, om, (double*)x, n);
+    if (fp32) k_first_jacobi<float><<<VG, VB, 0, st>>>((const float*)b, L.idiag32, om, (float*)x, n);
+    else k_first_jacobi<double><<<VG, VB, 0, st>>>((const double*)b, L.idiag64, om, (double*)x, n);
     PBM_LAUNCH("first jacobi");
 }
 
@@ -121,15 +134,90 @@ double read_slot(pbm_grid* g, int slot, cudaStream_t st) {
 //   2 r_k == 0), 14 beta_next
 //   reduction slots: red[0] = A z . z, red[1] = v_next . z_next, red[2] = ||r||^2, red[3] = misc
 // ------------------------------------------------------------------------------------------------
+// The per-launch scalars (quotients of beta) are formed once per CTA by thread 0: FP64 division is
+// a long instruction sequence on GB300, so no vector kernel divides per entry.
+// Fixed-role variants: the Lanczos step writes v_next and shifts (v_prev, v_cur) <- (v_cur, v_next)
+// in place; the update shifts the directions and z. Buffer roles never change between
+// iterations, so every iteration is the same sequence of launches.
 template <class T>
-__global__ void k_mr_lanczos(const T* __restrict__ Az, const T* __restrict__ vcur, T* __restrict__ vprev_next,
-                             int64_t n, double* mr, const double* red) {
-    const double beta = mr[1], bprev = mr[0];
-    const double a = red[0] / (beta * beta);
-    const double c1 = 1.0 / beta, c2 = a / beta, c3 = bprev > 0.0 ? beta / bprev : 0.0;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-        vprev_next[i] = T(c1 * double(Az[i]) - c2 * double(vcur[i]) - c3 * double(vprev_next[i]));
-    if (blockIdx.x == 0 && threadIdx.x == 0) mr[8] = a;
+__global__ void k_mr_lanczos2(const T* __restrict__ Az, T* __restrict__ v0, T* __restrict__ v1, int64_t n,
+                              double* mr, const double* red) {
+    __shared__ double cs[4];
+    if (threadIdx.x == 0) {
+        const double beta = mr[1], bprev = mr[0];
+        const double ib = 1.0 / beta;
+        const double a = red[0] * ib * ib;
+        cs[0] = ib;
+        cs[1] = a * ib;
+        cs[2] = bprev > 0.0 ? beta / bprev : 0.0;
+        cs[3] = a;
+    }
+    __syncthreads();
+    const double c1 = cs[0], c2 = cs[1], c3 = cs[2];
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const T vc = v1[i];
+        v1[i] = T(c1 * double(Az[i]) - c2 * double(vc) - c3 * double(v0[i]));
+        v0[i] = vc;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) mr[8] = cs[3];
+}
+
+template <class T>
+__global__ void k_mr_update2(T* __restrict__ zc, const T* __restrict__ zn, T* __restrict__ d1, T* __restrict__ d2,
+                             T* __restrict__ x, int64_t n, const double* mr) {
+    __shared__ double cs[2];
+    if (threadIdx.x == 0) {
+        cs[0] = 1.0 / mr[0];
+        cs[1] = 1.0 / mr[12];
+    }
+    __syncthreads();
+    const double e = mr[10], f = mr[11], step = mr[9];
+    const double ib = cs[0], ir = cs[1];
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const double dp = double(d1[i]);
+        const double dn = (double(zc[i]) * ib - e * double(d2[i]) - f * dp) * ir;
+        d2[i] = T(dp);
+        d1[i] = T(dn);
+        x[i] = T(double(x[i]) + step * dn);
+        zc[i] = zn[i];
+    }
+}
+
+// dst = (double) src, red = dst . other (FP32 preconditioner output into FP64 MINRES vectors)
+__global__ void k_cast_dot(const float* __restrict__ src, double* __restrict__ dst, const double* __restrict__ other,
+                           int64_t n, double* partials, unsigned* counter, double* out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const double v = double(src[i]);
+        dst[i] = v;
+        s += v * other[i];
+    }
+    double tot;
+    if (finish_sum(s, partials, counter, &tot, sh)) *out = tot;
+}
+
+void mr_lanczos2(pbm_grid* g, bool fp32, const void* Az, void* v0, void* v1, int64_t n, cudaStream_t st) {
+    if (fp32)
+        k_mr_lanczos2<float><<<VG, VB, 0, st>>>((const float*)Az, (float*)v0, (float*)v1, n, g->sc->mr, g->sc->red);
+    else
+        k_mr_lanczos2<double><<<VG, VB, 0, st>>>((const double*)Az, (double*)v0, (double*)v1, n, g->sc->mr,
+                                                 g->sc->red);
+    PBM_LAUNCH("mr lanczos");
+}
+void mr_update2(pbm_grid* g, bool fp32, void* zc, const void* zn, void* d1, void* d2, void* x, int64_t n,
+                cudaStream_t st) {
+    if (fp32)
+        k_mr_update2<float><<<VG, VB, 0, st>>>((float*)zc, (const float*)zn, (float*)d1, (float*)d2, (float*)x, n,
+                                               g->sc->mr);
+    else
+        k_mr_update2<double><<<VG, VB, 0, st>>>((double*)zc, (const double*)zn, (double*)d1, (double*)d2, (double*)x,
+                                                n, g->sc->mr);
+    PBM_LAUNCH("mr update");
+}
+void cast_dot(pbm_grid* g, const float* src, double* dst, const double* other, int64_t n, int slot, cudaStream_t st) {
+    k_cast_dot<<<VG, VB, 0, st>>>(src, dst, other, n, g->partials, &g->sc->counter[1], &g->sc->red[slot]);
+    PBM_LAUNCH("cast dot");
 }
 
 __global__ void k_mr_scalars(double* mr, const double* red) {
@@ -172,20 +260,6 @@ __global__ void k_mr_scalars(double* mr, const double* red) {
     mr[5] = sn;
 }
 
-// d_new = (z / beta_old - e d_prev2 - f d_prev) / r  (written over d_prev2), x += step * d_new
-template <class T>
-__global__ void k_mr_update(const T* __restrict__ z, T* __restrict__ dprev2_new, const T* __restrict__ dprev,
-                            T* __restrict__ x, int64_t n, const double* mr) {
-    const double bold = mr[0];  // beta_cur of this iteration (already shifted into beta_prev)
-    const double e = mr[10], f = mr[11], r = mr[12], step = mr[9];
-    const double ib = 1.0 / bold, ir = 1.0 / r;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        const double dn = (double(z[i]) * ib - e * double(dprev2_new[i]) - f * double(dprev[i])) * ir;
-        dprev2_new[i] = T(dn);
-        x[i] = T(double(x[i]) + step * dn);
-    }
-}
-
 __global__ void k_mr_init(double* mr, const double* red) {
     const double vz = red[1];
     for (int i = 0; i < 16; ++i) mr[i] = 0.0;
@@ -201,15 +275,6 @@ __global__ void k_mr_init(double* mr, const double* red) {
     mr[7] = b;
 }
 
-void mr_lanczos(pbm_grid* g, bool fp32, const void* Az, const void* vcur, void* vprev_next, int64_t n, cudaStream_t st) {
-    if (fp32)
-        k_mr_lanczos<float><<<VG, VB, 0, st>>>((const float*)Az, (const float*)vcur, (float*)vprev_next, n, g->sc->mr,
-                                               g->sc->red);
-    else
-        k_mr_lanczos<double><<<VG, VB, 0, st>>>((const double*)Az, (const double*)vcur, (double*)vprev_next, n,
-                                                g->sc->mr, g->sc->red);
-    PBM_LAUNCH("mr lanczos");
-}
 void mr_scalars(pbm_grid* g, cudaStream_t st) {
     k_mr_scalars<<<1, 1, 0, st>>>(g->sc->mr, g->sc->red);
     PBM_LAUNCH("mr scalars");
@@ -218,45 +283,36 @@ void mr_init(pbm_grid* g, cudaStream_t st) {
     k_mr_init<<<1, 1, 0, st>>>(g->sc->mr, g->sc->red);
     PBM_LAUNCH("mr init");
 }
-void mr_update(pbm_grid* g, bool fp32, const void* z, void* d2, const void* d1, void* x, int64_t n, cudaStream_t st) {
-    if (fp32)
-        k_mr_update<float><<<VG, VB, 0, st>>>((const float*)z, (float*)d2, (const float*)d1, (float*)x, n, g->sc->mr);
-    else
-        k_mr_update<double><<<VG, VB, 0, st>>>((const double*)z, (double*)d2, (const double*)d1, (double*)x, n,
-                                               g->sc->mr);
-    PBM_LAUNCH("mr update");
-}
-
-// x64 += (double) d32 (iterative refinement correction)
-__global__ void k_add_f32(double* __restrict__ x, const float* __restrict__ d, int64_t n) {
+// x64 += sign * (double) d32 (iterative refinement correction, or its removal)
+__global__ void k_add_f32(double* __restrict__ x, const float* __restrict__ d, int64_t n, double sign) {
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-        x[i] += double(d[i]);
+        x[i] += sign * double(d[i]);
 }
-void add_f32(double* x, const float* d, int64_t n, cudaStream_t st) {
-    k_add_f32<<<VG, VB, 0, st>>>(x, d, n);
+void add_f32(double* x, const float* d, int64_t n, cudaStream_t st, double sign) {
+    k_add_f32<<<VG, VB, 0, st>>>(x, d, n, sign);
     PBM_LAUNCH("add f32");
 }
 
 // ------------------------------------------------------------------------------------------------
 // Lanczos on D^{-1/2} A D^{-1/2}: lz_a[j], lz_b[j] (device), vectors FP64 of length n
 // ------------------------------------------------------------------------------------------------
-// t = s v with s = 1/sqrt(D); start vector v = 1/sqrt(n)
+// t = s v with s = D^{-1/2} (sdiag); start vector v = 1/sqrt(n)
 __global__ void k_lz_start(double* __restrict__ v, double* __restrict__ t, double* __restrict__ vprev,
-                           const double* __restrict__ diag, int64_t n) {
+                           const double* __restrict__ sdiag, int64_t n) {
     const double v0 = 1.0 / sqrt(double(n));
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
         v[i] = v0;
         vprev[i] = 0.0;
-        t[i] = v0 / sqrt(diag[i]);
+        t[i] = v0 * sdiag[i];
     }
 }
 // w = s w (in place), a_j = w . v
-__global__ void k_lz_a(double* __restrict__ w, const double* __restrict__ v, const double* __restrict__ diag, int64_t n,
-                       double* partials, unsigned* counter, double* aj) {
+__global__ void k_lz_a(double* __restrict__ w, const double* __restrict__ v, const double* __restrict__ sdiag,
+                       int64_t n, double* partials, unsigned* counter, double* aj) {
     __shared__ double sh[32];
     double s = 0.0;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        const double wi = w[i] / sqrt(diag[i]);
+        const double wi = w[i] * sdiag[i];
         w[i] = wi;
         s += wi * v[i];
     }
@@ -279,14 +335,19 @@ __global__ void k_lz_b(double* __restrict__ w, const double* __restrict__ v, con
 }
 // vprev = v; v = w / b_j; t = s v
 __global__ void k_lz_next(const double* __restrict__ w, double* __restrict__ v, double* __restrict__ vprev,
-                          double* __restrict__ t, const double* __restrict__ diag, int64_t n, const double* bj) {
-    const double b = *bj;
-    const double ib = b > 0.0 ? 1.0 / b : 0.0;
+                          double* __restrict__ t, const double* __restrict__ sdiag, int64_t n, const double* bj) {
+    __shared__ double ib_s;
+    if (threadIdx.x == 0) {
+        const double b = *bj;
+        ib_s = b > 0.0 ? 1.0 / b : 0.0;
+    }
+    __syncthreads();
+    const double ib = ib_s;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
         vprev[i] = v[i];
         const double vi = w[i] * ib;
         v[i] = vi;
-        t[i] = vi / sqrt(diag[i]);
+        t[i] = vi * sdiag[i];
     }
 }
 

@@ -10,8 +10,9 @@
 //     matrix is rho'_c K_e + d_c w_c w_c^T (w_c = K_e u_c), so the coarse matrix is
 //     sum_c rho'_c G_c + sum_c d_c (P_c^T w_c)(P_c^T w_c)^T with the 8 fixed G_c = P_c^T K_e P_c.
 //     The coarse alpha border is b_{k-1} = P^T b_k and S_alpha,alpha is unchanged.
-//   * coarsest level: the bordered matrix is assembled densely, factorised by Cholesky in one
-//     CTA, and inverted explicitly; each V-cycle then applies the inverse (a dense mat-vec).
+//   * coarsest level: the bordered matrix is assembled densely and factorised by Cholesky in one
+//     CTA; L^{-1} (a warp per column) and the explicit inverse L^{-T} L^{-1} (a thread per entry)
+//     are spread over the GPU; each V-cycle then applies the inverse (a dense mat-vec).
 #include "pbm_internal.h"
 
 namespace pbm {
@@ -30,7 +31,8 @@ __host__ __device__ inline double pc_weight(int c, int a, int A) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// restriction b_c = P^T r_f (+ alpha copy), times `scale`
+// restriction b_c = P^T r_f (+ alpha copy), times `scale`. One thread per (coarse node, component);
+// the 27 weights 1/2^(number of odd offsets) are compile-time constants of the unrolled loops.
 // ------------------------------------------------------------------------------------------------
 template <class T>
 __global__ void k_restrict(int nxf, int nyf, int nzf, int support, const T* __restrict__ rf, T* __restrict__ bc,
@@ -38,35 +40,33 @@ __global__ void k_restrict(int nxf, int nyf, int nzf, int support, const T* __re
     const int nxc = nxf / 2, nyc = nyf / 2, nzc = nzf / 2;
     const int64_t nnc = int64_t(nxc + 1) * (nyc + 1) * (nzc + 1);
     const int64_t sxf = nxf + 1, sxyf = int64_t(nxf + 1) * (nyf + 1);
-    for (int64_t cn = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; cn < nnc; cn += int64_t(gridDim.x) * blockDim.x) {
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < 3 * nnc; t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t cn = t / 3;
+        const int c = int(t - 3 * cn);
         const int I = int(cn % (nxc + 1));
         const int J = int((cn / (nxc + 1)) % (nyc + 1));
         const int K = int(cn / (int64_t(nxc + 1) * (nyc + 1)));
-        double acc[3] = {0.0, 0.0, 0.0};
+        double acc = 0.0;
         if (!node_fixed(support, nxc, nyc, nzc, I, J, K)) {
+#pragma unroll
             for (int dz = -1; dz <= 1; ++dz) {
                 const int kf = 2 * K + dz;
-                if (kf < 0 || kf > nzf) continue;
+#pragma unroll
                 for (int dy = -1; dy <= 1; ++dy) {
                     const int jf = 2 * J + dy;
-                    if (jf < 0 || jf > nyf) continue;
 #pragma unroll
                     for (int dx = -1; dx <= 1; ++dx) {
                         const int if_ = 2 * I + dx;
-                        if (if_ < 0 || if_ > nxf) continue;
+                        if (if_ < 0 || if_ > nxf || jf < 0 || jf > nyf || kf < 0 || kf > nzf) continue;
                         if (node_fixed(support, nxf, nyf, nzf, if_, jf, kf)) continue;
-                        const double w = (dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0);
-                        const int64_t f = 3 * (if_ + sxf * jf + sxyf * kf);
-                        acc[0] += w * double(rf[f]);
-                        acc[1] += w * double(rf[f + 1]);
-                        acc[2] += w * double(rf[f + 2]);
+                        constexpr double half = 0.5;
+                        const double w = (dx ? half : 1.0) * (dy ? half : 1.0) * (dz ? half : 1.0);
+                        acc += w * double(rf[3 * (if_ + sxf * jf + sxyf * kf) + c]);
                     }
                 }
             }
         }
-        bc[3 * cn] = T(scale * acc[0]);
-        bc[3 * cn + 1] = T(scale * acc[1]);
-        bc[3 * cn + 2] = T(scale * acc[2]);
+        bc[t] = T(scale * acc);
     }
     if (with_alpha && blockIdx.x == 0 && threadIdx.x == 0) {
         const int64_t nf = 3 * int64_t(nxf + 1) * (nyf + 1) * (nzf + 1);
@@ -78,19 +78,20 @@ void launch_restrict(pbm_grid* g, int k, bool fp32, const void* rf, void* bc, bo
                      cudaStream_t st) {
     // k: the fine level of the pair (k -> k+1)
     const Geom& F = g->L[k].g;
-    const int64_t nnc = g->L[k + 1].g.nnode();
-    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nnc + 255) / 256, 152 * 8)));
+    const int64_t nt = 3 * g->L[k + 1].g.nnode();
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nt + 127) / 128, 152 * 16)));
     if (fp32)
-        k_restrict<float><<<blocks, 256, 0, st>>>(F.nx, F.ny, F.nz, F.support, (const float*)rf, (float*)bc,
+        k_restrict<float><<<blocks, 128, 0, st>>>(F.nx, F.ny, F.nz, F.support, (const float*)rf, (float*)bc,
                                                   with_alpha, scale);
     else
-        k_restrict<double><<<blocks, 256, 0, st>>>(F.nx, F.ny, F.nz, F.support, (const double*)rf, (double*)bc,
+        k_restrict<double><<<blocks, 128, 0, st>>>(F.nx, F.ny, F.nz, F.support, (const double*)rf, (double*)bc,
                                                    with_alpha, scale);
     PBM_LAUNCH("restrict");
 }
 
 // ------------------------------------------------------------------------------------------------
-// prolongation x_f += P x_c (+ alpha)
+// prolongation x_f += P x_c (+ alpha). One thread per (fine node, component): the up to 8 coarse
+// parents share the weight 1/2^(number of odd fine coordinates), built from its exponent bits.
 // ------------------------------------------------------------------------------------------------
 template <class T>
 __global__ void k_prolong_add(int nxf, int nyf, int nzf, int support, const T* __restrict__ xc, T* __restrict__ xf,
@@ -98,27 +99,24 @@ __global__ void k_prolong_add(int nxf, int nyf, int nzf, int support, const T* _
     const int nxc = nxf / 2, nyc = nyf / 2, nzc = nzf / 2;
     const int64_t nnf = int64_t(nxf + 1) * (nyf + 1) * (nzf + 1);
     const int64_t sxc = nxc + 1, sxyc = int64_t(nxc + 1) * (nyc + 1);
-    for (int64_t fn = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; fn < nnf; fn += int64_t(gridDim.x) * blockDim.x) {
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < 3 * nnf; t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t fn = t / 3;
+        const int c = int(t - 3 * fn);
         const int I = int(fn % (nxf + 1));
         const int J = int((fn / (nxf + 1)) % (nyf + 1));
         const int K = int(fn / (int64_t(nxf + 1) * (nyf + 1)));
         if (node_fixed(support, nxf, nyf, nzf, I, J, K)) continue;
-        double acc[3] = {0.0, 0.0, 0.0};
         const int i0 = I >> 1, i1 = (I + 1) >> 1, j0 = J >> 1, j1 = (J + 1) >> 1, k0 = K >> 1, k1 = (K + 1) >> 1;
-        const double wx = (I & 1) ? 0.5 : 1.0, wy = (J & 1) ? 0.5 : 1.0, wz = (K & 1) ? 0.5 : 1.0;
+        double acc = 0.0;
         for (int kc = k0; kc <= k1; ++kc)
             for (int jc = j0; jc <= j1; ++jc)
                 for (int ic = i0; ic <= i1; ++ic) {
                     if (node_fixed(support, nxc, nyc, nzc, ic, jc, kc)) continue;
-                    const double w = wx * wy * wz;
-                    const int64_t c = 3 * (ic + sxc * jc + sxyc * kc);
-                    acc[0] += w * double(xc[c]);
-                    acc[1] += w * double(xc[c + 1]);
-                    acc[2] += w * double(xc[c + 2]);
+                    acc += double(xc[3 * (ic + sxc * jc + sxyc * kc) + c]);
                 }
-        xf[3 * fn] += T(acc[0]);
-        xf[3 * fn + 1] += T(acc[1]);
-        xf[3 * fn + 2] += T(acc[2]);
+        const int nodd = (I & 1) + (J & 1) + (K & 1);
+        const double w = __longlong_as_double(static_cast<long long>(1023 - nodd) << 52);  // 2^-nodd
+        xf[t] += T(w * acc);
     }
     if (with_alpha && blockIdx.x == 0 && threadIdx.x == 0) {
         const int64_t nc = 3 * int64_t(nxc + 1) * (nyc + 1) * (nzc + 1);
@@ -128,8 +126,8 @@ __global__ void k_prolong_add(int nxf, int nyf, int nzf, int support, const T* _
 
 void launch_prolong_add(pbm_grid* g, int k, bool fp32, const void* xc, void* xf, bool with_alpha, cudaStream_t st) {
     const Geom& F = g->L[k].g;
-    const int64_t nnf = F.nnode();
-    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nnf + 255) / 256, 152 * 8)));
+    const int64_t nt = 3 * F.nnode();
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nt + 255) / 256, 152 * 16)));
     if (fp32)
         k_prolong_add<float><<<blocks, 256, 0, st>>>(F.nx, F.ny, F.nz, F.support, (const float*)xc, (float*)xf,
                                                      with_alpha);
@@ -239,42 +237,100 @@ void launch_build_level1(pbm_grid* g, bool op_s, cudaStream_t st) {
 
 // ------------------------------------------------------------------------------------------------
 // level k+1 from level k: sum_c P_c^T A_c P_c
+//
+// P_c acts on the node index only and is a tensor product of one 2 x 2 interpolation per axis
+// (child bit 0: rows (1, 0), (1/2, 1/2); child bit 1: rows (1/2, 1/2), (0, 1)). So each 8 x 8 block
+// A_ij (displacement components i, j) of a child matrix is transformed on its own, B_ij = P^T A_ij
+// P, by three one-dimensional passes on each side. A group of 8 lanes holds the 8 children of one
+// coarse element and one block (i <= j); the lanes sum their results with shuffles and each writes
+// 8 of the 64 entries into the coarse upper triangle (every triangle entry is written once: an
+// entry (r, s), r <= s, belongs to block (r % 3, s % 3) if r % 3 <= s % 3, else to the transposed
+// position of block (s % 3, r % 3)).
 // ------------------------------------------------------------------------------------------------
-__global__ void k_build_coarser(int nxf, int nyf, int nzf, const double* __restrict__ Af, double* __restrict__ Ac) {
+__device__ __forceinline__ void interp_pair(double& v0, double& v1, int cb) {
+    const double h = 0.5 * (cb ? v0 : v1);
+    const double sum = (cb ? v1 : v0) + h;
+    v0 = cb ? h : sum;
+    v1 = cb ? sum : h;
+}
+
+__device__ __forceinline__ void interp8(double (&v)[8], int c) {
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const int cb = (c >> ax) & 1;
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            if (!((b >> ax) & 1)) interp_pair(v[b], v[b | (1 << ax)], cb);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_build_coarser(int nxf, int nyf, int nzf, const double* __restrict__ Af,
+                                                       double* __restrict__ Ac) {
     const int nxc = nxf / 2, nyc = nyf / 2, nzc = nzf / 2;
     const int64_t mc = int64_t(nxc) * nyc * nzc, mf = int64_t(nxf) * nyf * nzf;
-    const int t = blockIdx.y;
-    const int I = c_tri_i[t], J = c_tri_j[t];
-    const int AI = I / 3, ci = I % 3, AJ = J / 3, cj = J % 3;
-    for (int64_t E = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; E < mc; E += int64_t(gridDim.x) * blockDim.x) {
-        const int ex = int(E % nxc);
-        const int ey = int((E / nxc) % nyc);
-        const int ez = int(E / (int64_t(nxc) * nyc));
-        double acc = 0.0;
-        for (int c = 0; c < 8; ++c) {
-            const int64_t e = (2 * ex + (c & 1)) + int64_t(nxf) * ((2 * ey + ((c >> 1) & 1)) + int64_t(nyf) * (2 * ez + (c >> 2)));
-            for (int a = 0; a < 8; ++a) {
-                const double wa = pc_weight(c, a, AI);
-                if (wa == 0.0) continue;
-                const int r = 3 * a + ci;
-                for (int b = 0; b < 8; ++b) {
-                    const double wb = pc_weight(c, b, AJ);
-                    if (wb == 0.0) continue;
-                    const int s = 3 * b + cj;
-                    const int tt = r <= s ? tri_index(r, s) : tri_index(s, r);
-                    acc += wa * wb * Af[tt * mf + e];
-                }
-            }
+    const int64_t tid = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int c = int(tid & 7);
+    const int64_t grp = tid >> 3;
+    const int blk = int(grp % 6);
+    int64_t E = grp / 6;
+    const bool live = E < mc;
+    if (!live) E = mc - 1;   // keep the lane in the shuffles
+    const int bi = blk < 3 ? 0 : (blk < 5 ? 1 : 2);
+    const int bj = blk < 3 ? blk : (blk < 5 ? blk - 2 : 2);
+    const int ex = int(E % nxc), ey = int((E / nxc) % nyc), ez = int(E / (int64_t(nxc) * nyc));
+    const int64_t e = (2 * ex + (c & 1)) + int64_t(nxf) * ((2 * ey + ((c >> 1) & 1)) + int64_t(nyf) * (2 * ez + (c >> 2)));
+    double M[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int r = 3 * a + bi, q = 3 * b + bj;
+            const int t = r <= q ? tri_index(r, q) : tri_index(q, r);
+            M[a][b] = Af[int64_t(t) * mf + e];
         }
-        Ac[t * mc + E] = acc;
+    // right: rows, left: columns
+#pragma unroll
+    for (int a = 0; a < 8; ++a) interp8(M[a], c);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        double col[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) col[a] = M[a][b];
+        interp8(col, c);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) M[a][b] = col[a];
+    }
+    // sum over the 8 children (lanes of the group), fixed order
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            double v = M[a][b];
+            v += __shfl_xor_sync(0xffffffffu, v, 1, 8);
+            v += __shfl_xor_sync(0xffffffffu, v, 2, 8);
+            v += __shfl_xor_sync(0xffffffffu, v, 4, 8);
+            M[a][b] = v;
+        }
+    if (!live) return;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        // lane c writes row A = a of the block when a == c (8 entries each)
+        if (a != c) continue;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            if (bi == bj && b < a) continue;
+            const int r = 3 * a + bi, q = 3 * b + bj;
+            const int t = r <= q ? tri_index(r, q) : tri_index(q, r);
+            Ac[int64_t(t) * mc + E] = M[a][b];
+        }
     }
 }
 
 void launch_build_coarser(pbm_grid* g, int k, cudaStream_t st) {
     const Geom& F = g->L[k].g;
     const int64_t mc = g->L[k + 1].g.m();
-    dim3 grid(unsigned(std::max<int64_t>(1, std::min<int64_t>((mc + 127) / 128, 64))), NTRI);
-    k_build_coarser<<<grid, 128, 0, st>>>(F.nx, F.ny, F.nz, g->L[k].A64, g->L[k + 1].A64);
+    const int64_t threads = mc * 48;
+    k_build_coarser<<<int((threads + 127) / 128), 128, 0, st>>>(F.nx, F.ny, F.nz, g->L[k].A64, g->L[k + 1].A64);
     PBM_LAUNCH("build coarser");
 }
 
@@ -299,15 +355,19 @@ void upload_tri_tables() {
 }
 
 // ------------------------------------------------------------------------------------------------
-// coarsest level: dense assembly, Cholesky, explicit inverse (one CTA)
+// coarsest level: dense assembly and Cholesky (one CTA), then L^{-1} (a warp per column) and the
+// explicit inverse L^{-T} L^{-1} (one thread per entry) spread over many SMs
 // ------------------------------------------------------------------------------------------------
-__global__ void k_coarsest_factor(int nx, int ny, int nz, int support, const double* __restrict__ A,
-                                  const double* __restrict__ bord, double s_alpha, int op_s, double* __restrict__ M,
-                                  double* __restrict__ Inv, int* flag) {
+__global__ void __launch_bounds__(1024) k_coarsest_factor(int nx, int ny, int nz, int support, const double* __restrict__ A,
+                                  const double* __restrict__ bord, double s_alpha, int op_s, double* __restrict__ Mg,
+                                  double* __restrict__ Dinv, int* flag, int use_smem) {
+    extern __shared__ double smem[];
+    double* M = use_smem ? smem : Mg;   // the factorisation runs in shared memory when N^2 fits
     const int64_t m = int64_t(nx) * ny * nz;
     const int n = 3 * (nx + 1) * (ny + 1) * (nz + 1);
     const int N = n + 1;
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
     for (int i = tid; i < N * N; i += nt) M[i] = 0.0;
     __syncthreads();
     const int sx = nx + 1, sxy = (nx + 1) * (ny + 1);
@@ -356,43 +416,64 @@ __global__ void k_coarsest_factor(int nx, int ny, int nz, int support, const dou
     }
     if (tid == 0) M[n * N + n] = op_s ? s_alpha : 1.0;
     __syncthreads();
-    // Cholesky (lower, in place)
-    __shared__ double piv;
+    // Cholesky (lower, in place); the reciprocal of each pivot replaces N - j divisions
+    __shared__ double ipiv;
     for (int j = 0; j < N; ++j) {
         if (tid == 0) {
             const double a = M[j * N + j];
             if (!(a > 0.0)) *flag = 1;
-            piv = a > 0.0 ? sqrt(a) : 1.0;
+            const double piv = a > 0.0 ? sqrt(a) : 1.0;
             M[j * N + j] = piv;
+            ipiv = 1.0 / piv;
         }
         __syncthreads();
-        for (int i = j + 1 + tid; i < N; i += nt) M[i * N + j] /= piv;
+        const double ip = ipiv;
+        for (int i = j + 1 + tid; i < N; i += nt) M[i * N + j] *= ip;
         __syncthreads();
-        const int rem = N - j - 1;
-        for (int t = tid; t < rem * rem; t += nt) {
-            const int i = j + 1 + t / rem, k = j + 1 + t % rem;
-            if (k <= i) M[i * N + k] -= M[i * N + j] * M[k * N + j];
+        // trailing update of the lower triangle: a warp per row, lanes over the columns
+        for (int i = j + 1 + wid; i < N; i += nw) {
+            const double lij = M[i * N + j];
+            for (int k = j + 1 + lane; k <= i; k += 32) M[i * N + k] -= lij * M[k * N + j];
         }
         __syncthreads();
     }
-    // Inv := L^{-1} (column by column, forward substitution), stored in the upper part of Inv rows
-    for (int col = tid; col < N; col += nt) {
-        for (int i = 0; i < N; ++i) {
-            double s = (i == col) ? 1.0 : 0.0;
-            for (int k = col; k < i; ++k) s -= M[i * N + k] * Inv[k * N + col];
-            Inv[i * N + col] = (i < col) ? 0.0 : s / M[i * N + i];
-        }
-    }
-    __syncthreads();
-    // A^{-1} = L^{-T} L^{-1}: entry (r, c) = sum_k Linv[k][r] Linv[k][c], k >= max(r, c); store in M
-    for (int t = tid; t < N * N; t += nt) {
-        const int r = t / N, c = t % N;
+    // reciprocals of the diagonal of L for the substitutions
+    for (int i = tid; i < N; i += nt) Dinv[i] = 1.0 / M[i * N + i];
+    if (use_smem)
+        for (int i = tid; i < N * N; i += nt) Mg[i] = M[i];
+}
+
+constexpr int COARSEST_SMEM_N = 160;   // shared-memory factorisation up to N = 160 (200 KB)
+
+// column c of L^{-1} by forward substitution, one warp per column (lanes split the dot products)
+__global__ void k_coarsest_linv(int N, const double* __restrict__ M, const double* __restrict__ Dinv,
+                                double* __restrict__ Linv) {
+    const int lane = threadIdx.x & 31;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (col >= N) return;
+    for (int i = 0; i < col; ++i)
+        if (lane == 0) Linv[i * N + col] = 0.0;
+    for (int i = col; i < N; ++i) {
         double s = 0.0;
-        for (int k = (r > c ? r : c); k < N; ++k) s += Inv[k * N + r] * Inv[k * N + c];
-        M[t] = s;
+        for (int k = col + lane; k < i; k += 32) s += M[i * N + k] * Linv[k * N + col];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const double v = ((i == col ? 1.0 : 0.0) - s) * Dinv[i];
+        if (lane == 0) Linv[i * N + col] = v;
+        __syncwarp();
     }
-    __syncthreads();
-    for (int t = tid; t < N * N; t += nt) Inv[t] = M[t];
+}
+
+// A^{-1} = L^{-T} L^{-1}: entry (r, c) = sum_{k >= max(r, c)} Linv[k][r] Linv[k][c], symmetric
+__global__ void k_coarsest_inv(int N, const double* __restrict__ Linv, double* __restrict__ Inv) {
+    const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (t >= int64_t(N) * N) return;
+    const int r = int(t / N), c = int(t % N);
+    if (c < r) return;
+    double s = 0.0;
+    for (int k = c; k < N; ++k) s += Linv[k * N + r] * Linv[k * N + c];
+    Inv[r * N + c] = s;
+    Inv[c * N + r] = s;
 }
 
 void build_coarsest(pbm_grid* g, bool op_s, cudaStream_t st) {
@@ -400,9 +481,27 @@ void build_coarsest(pbm_grid* g, bool op_s, cudaStream_t st) {
     Level& L = g->L[kc];
     PBM_CUDA(cudaMemsetAsync(&g->sc->flags[0], 0, sizeof(int), st));
     if (kc == 0) fail(PBM_EINVAL, "a single-level hierarchy has no coarse operator (use levels >= 2)");
-    k_coarsest_factor<<<1, 512, 0, st>>>(L.g.nx, L.g.ny, L.g.nz, L.g.support, L.A64, L.bord64, g->s_alpha, op_s ? 1 : 0,
-                                         g->cwork, g->cinv, &g->sc->flags[0]);
+    const int N = g->nc + 1;
+    double* M = g->cwork;
+    double* Linv = g->cwork + size_t(N) * N;
+    double* Dinv = g->cwork + 2 * size_t(N) * N;
+    const bool sm = N <= COARSEST_SMEM_N;
+    const size_t smem = sm ? sizeof(double) * size_t(N) * N : 0;
+    if (sm) {
+        static bool attr_done[64] = {};
+        if (!attr_done[g->device & 63]) {
+            PBM_CUDA(cudaFuncSetAttribute(k_coarsest_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(sizeof(double) * COARSEST_SMEM_N * COARSEST_SMEM_N)));
+            attr_done[g->device & 63] = true;
+        }
+    }
+    k_coarsest_factor<<<1, 1024, smem, st>>>(L.g.nx, L.g.ny, L.g.nz, L.g.support, L.A64, L.bord64, g->s_alpha,
+                                             op_s ? 1 : 0, M, Dinv, &g->sc->flags[0], sm ? 1 : 0);
     PBM_LAUNCH("coarsest factor");
+    k_coarsest_linv<<<(N * 32 + 127) / 128, 128, 0, st>>>(N, M, Dinv, Linv);
+    PBM_LAUNCH("coarsest L inverse");
+    k_coarsest_inv<<<int((int64_t(N) * N + 255) / 256), 256, 0, st>>>(N, Linv, g->cinv);
+    PBM_LAUNCH("coarsest inverse");
 }
 
 // x = Inv b on the coarsest level (warp per row, FP64 accumulation)

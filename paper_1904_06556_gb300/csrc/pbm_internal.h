@@ -22,6 +22,8 @@ void set_error(const std::string& msg);
 [[noreturn]] void fail(int code, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what);
 void count_launch();  // process-wide counter of the kernels this library launched
+void count_launch_add(int64_t delta);
+int64_t launch_count();
 #define PBM_CUDA(x) ::pbm::check_cuda((x), #x)
 #define PBM_LAUNCH(what) (::pbm::count_launch(), ::pbm::check_cuda(cudaGetLastError(), what))
 
@@ -69,6 +71,9 @@ struct KeHat {
     double lam4[2];
     double mu4[2];
 };
+
+// the factors of the isotropic Q1 cube of edge h (capi.cu)
+void element_hat(double E, double nu, double h, KeHat& K);
 
 template <class T>
 struct KeHatT {
@@ -146,9 +151,11 @@ struct Level {
     // alpha border of S on this level (n entries; b_0 = -sum_i d_i K_i u, b_{k+1} = P^T b_k)
     double* bord64 = nullptr;
     float* bord32 = nullptr;
-    // Jacobi diagonal, n + 1 entries (last = alpha)
+    // Jacobi diagonal, its inverse and its inverse square root (Lanczos), n + 1 entries (last = alpha)
     double* diag64 = nullptr;
-    float* diag32 = nullptr;
+    double* idiag64 = nullptr;
+    double* sdiag64 = nullptr;
+    float* idiag32 = nullptr;
     // V-cycle work vectors, n + 1 entries each
     double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *t64 = nullptr;
     float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr, *t32 = nullptr;
@@ -167,6 +174,8 @@ struct DevScalars {
     double mr[32];         // MINRES scalar state
     unsigned int counter[64];  // last-block-done counters (one per reduction slot)
     int flags[8];
+    double salpha;         // S_alpha,alpha = sum_i d_i of the current state (coarse S applies)
+    double ctl[8];         // graph-resident MINRES loop control: target, iteration budget, count, exit
 };
 
 }  // namespace pbm
@@ -198,6 +207,9 @@ struct pbm_grid {
     double* u64 = nullptr;            // masked displacement of the Newton state (n)
     float* u32 = nullptr;
     double* what = nullptr;           // P_c^T (K_e u_e) for every fine element, [24][m]
+    double* what_hat = nullptr;       // Khat H u_e for every fine element, [21][m] (FP64 S pass)
+    void* qa = nullptr;               // plane-quad scratch of the column passes, 12 (nz + 1) nx ny
+    void* qb = nullptr;               // chunk-top quads, 12 nz nx ny (entries of the FP64 size)
     double* nwt = nullptr;            // Newton step buffers: dz (n + 1), r (n), dnu_lo (m), dnu_up (m)
     double s_alpha = 0.0;             // S_alpha,alpha = sum_i d_i
     // coarsest level: dense inverse of the bordered matrix, (nc+1)^2 FP64
@@ -209,9 +221,9 @@ struct pbm_grid {
     int max_blocks = 0;
     pbm::DevScalars* sc = nullptr;
     pbm::DevScalars* sc_host = nullptr;  // pinned mirror
-    // Krylov work vectors (n + 1 of the finest level)
-    double* kv64[10] = {};
-    float* kv32[10] = {};
+    // Krylov work vectors (n + 1 of the finest level); [10] holds the MINRES iterate
+    double* kv64[12] = {};
+    float* kv32[12] = {};
     // operator state: 0 = none, 1 = K(rho) hierarchy current, 2 = S hierarchy current
     int op_ready = 0;
     bool rho_set = false;
@@ -225,6 +237,11 @@ struct pbm_grid {
     std::vector<cudaEvent_t> prof_ev;      // 2 per recorded launch
     size_t prof_used = 0;
     pbm_profile_stats prof[2] = {};        // [PBM_OP_K], [PBM_OP_S]
+    // MINRES iterations captured as CUDA graphs (a WHILE node around one iteration), per
+    // (vector precision, operator, FP32 preconditioner); built on first use, kept until destroy
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t mr_graph[8] = {};
+    int64_t mr_graph_kernels[8] = {};      // kernels in one iteration of each graph (launch counting)
     std::vector<int> prof_op;              // operator of every recorded launch
 };
 
@@ -256,6 +273,30 @@ void launch_fine(pbm_grid* g, bool fp32, const void* w, const void* d, const voi
 void launch_coarse(pbm_grid* g, int k, bool fp32, const ApplyArgs& a, cudaStream_t st);
 // Jacobi diagonal of a level (S or K), written to L[k].diag64 / diag32 (n + 1, last = alpha)
 void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st);
+// two-pass column kernels (colpass.cu). ColEnv names the scratch the passes use: the plane-quad
+// buffers (cols_scratch_entries() entries of the vector type), the per-CTA partial sums and the
+// device scalar block (last-CTA counter, reduction slots).
+struct ColEnv {
+    void* qa = nullptr;
+    void* qb = nullptr;
+    double* partials = nullptr;
+    int64_t partials_len = 0;
+    DevScalars* sc = nullptr;
+};
+int64_t cols_scratch_entries(const Geom& G);
+template <class T>
+void cols_fine_env(const ColEnv& env, const Geom& G, const KeHat& kh, const T* w, const T* d, const T* what,
+                   const T* u, const ApplyArgs& a, cudaStream_t st);
+// fine level: K(w) x (d == nullptr) or S (d given; W_e from `what` if given, else recomputed from u)
+template <class T>
+void cols_fine(pbm_grid* g, const T* w, const T* d, const T* what, const T* u, const ApplyArgs& a, cudaStream_t st);
+template <class T>
+void cols_coarse(pbm_grid* g, int k, const T* A, const T* bord, const ApplyArgs& a, cudaStream_t st);
+void launch_what_hat(pbm_grid* g, cudaStream_t st);
+void cols_cost(const Geom& G, bool op_s, bool recompute_w, int mode, int esize, double& bytes, double& flops);
+// y = 1 / x and y = 1 / sqrt(x) (n entries)
+void launch_inverse(const double* x, double* y, int64_t n, cudaStream_t st);
+void launch_inverse_sqrt(const double* x, double* y, int64_t n, cudaStream_t st);
 // per-element c_e = 1/2 u_e^T K_e u_e (masked u), FP64
 void launch_elem_energy(pbm_grid* g, const double* u, const double* v, double* out, cudaStream_t st);
 // profiling hooks around one fine-level operator launch (no-ops unless g->prof_on)

@@ -4,16 +4,19 @@
 // only sequences launches and reads back scalars.
 #include <chrono>
 #include <cmath>
+#include <limits>
 
 #include "pbm_internal.h"
 
 namespace pbm {
 
-void mr_lanczos(pbm_grid* g, bool fp32, const void* Az, const void* vcur, void* vprev_next, int64_t n, cudaStream_t st);
 void mr_scalars(pbm_grid* g, cudaStream_t st);
 void mr_init(pbm_grid* g, cudaStream_t st);
-void mr_update(pbm_grid* g, bool fp32, const void* z, void* d2, const void* d1, void* x, int64_t n, cudaStream_t st);
-void add_f32(double* x, const float* d, int64_t n, cudaStream_t st);
+void add_f32(double* x, const float* d, int64_t n, cudaStream_t st, double sign);
+void mr_lanczos2(pbm_grid* g, bool fp32, const void* Az, void* v0, void* v1, int64_t n, cudaStream_t st);
+void mr_update2(pbm_grid* g, bool fp32, void* zc, const void* zn, void* d1, void* d2, void* x, int64_t n,
+                cudaStream_t st);
+void cast_dot(pbm_grid* g, const float* src, double* dst, const double* other, int64_t n, int slot, cudaStream_t st);
 void lz_start(pbm_grid* g, double* v, double* t, double* vprev, const double* diag, int64_t n, cudaStream_t st);
 void lz_a(pbm_grid* g, double* w, const double* v, const double* diag, int64_t n, int j, cudaStream_t st);
 void lz_b(pbm_grid* g, double* w, const double* v, const double* vprev, int64_t n, int j, cudaStream_t st);
@@ -67,7 +70,7 @@ void vcycle(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, void* x, in
     }
     void* t = fp32 ? (void*)L.t32 : (void*)L.t64;
     void* r = fp32 ? (void*)L.r32 : (void*)L.r64;
-    const void* D = fp32 ? (const void*)L.diag32 : (const void*)L.diag64;
+    const void* D = fp32 ? (const void*)L.idiag32 : (const void*)L.idiag64;
     const double* om = &g->sc->mr[16 + k];
     const int pre = g->desc.pre_sweeps, post = g->desc.post_sweeps;
     // pre-smoothing from x = 0: the first sweep is x = omega D^-1 b; arrange the ping-pong so that
@@ -143,12 +146,13 @@ static void lanczos_level(pbm_grid* g, int k, bool op_s, cudaStream_t st) {
     double* t = g->kv64[8];
     double* w = g->kv64[9];
     const int steps = g->desc.lanczos_steps;
-    lz_start(g, v, t, vp, L.diag64, nv, st);
+    launch_inverse_sqrt(L.diag64, L.sdiag64, nv, st);
+    lz_start(g, v, t, vp, L.sdiag64, nv, st);
     for (int j = 0; j < steps; ++j) {
         level_apply(g, k, false, op_s, args(t, w, EPI_APPLY), st);
-        lz_a(g, w, v, L.diag64, nv, j, st);
+        lz_a(g, w, v, L.sdiag64, nv, j, st);
         lz_b(g, w, v, vp, nv, j, st);
-        lz_next(g, w, v, vp, t, L.diag64, nv, j, st);
+        lz_next(g, w, v, vp, t, L.sdiag64, nv, j, st);
     }
     PBM_CUDA(cudaMemcpyAsync(g->sc_host->lz_a, g->sc->lz_a, sizeof(double) * steps, cudaMemcpyDeviceToHost, st));
     PBM_CUDA(cudaMemcpyAsync(g->sc_host->lz_b, g->sc->lz_b, sizeof(double) * steps, cudaMemcpyDeviceToHost, st));
@@ -182,6 +186,7 @@ void setup_hierarchy(pbm_grid* g, bool op_s, cudaStream_t st) {
         // alpha border of the fine level: b_0 = -sum_i d_i K_i u (restricted below with scale -1)
         launch_fine(g, false, g->d64, nullptr, nullptr, args(g->u64, F.bord64, EPI_APPLY), st);
         launch_build_what(g, st);
+        launch_what_hat(g, st);
     } else {
         // K(w): what is not needed (d = 0); keep u zero so that nothing stale is used
     }
@@ -218,6 +223,14 @@ void setup_hierarchy(pbm_grid* g, bool op_s, cudaStream_t st) {
 
 // ------------------------------------------------------------------------------------------------
 // MINRES (x holds the initial guess); returns status
+//
+// Vectors in the precision `fp32` (FP32 only for the inner solves of the mixed path), scalars in
+// FP64 on the device. With pc32 (FP64 vectors only) the preconditioner is the FP32 V-cycle: the
+// Lanczos vector is rounded to FP32, cycled, and widened back with the dot product fused.
+// When the recurrence's residual estimate reaches the target the true residual is computed
+// (check_true); if it is above rtol the target is tightened and the iteration continues, unless
+// the true residual has not halved since the previous check (stagnation: returns PBM_ENOTCONV
+// with the current iterate, which the caller may restart from).
 // ------------------------------------------------------------------------------------------------
 struct MrResult {
     int status = PBM_OK;
@@ -225,12 +238,111 @@ struct MrResult {
     double relres = 0.0;
 };
 
+static void precondition(pbm_grid* g, bool fp32, bool pc32, bool op_s, const void* v, void* z, int64_t nv,
+                         cudaStream_t st) {
+    if (!pc32) {
+        vcycle(g, 0, fp32, op_s, v, z, 1, st);
+        return;
+    }
+    Level& F = g->L[0];
+    launch_cast(v, false, F.b32, true, nv, st);
+    vcycle(g, 0, true, op_s, F.b32, F.x32, -1, st);
+    cast_dot(g, F.x32, (double*)z, (const double*)v, nv, 1, st);
+}
+
+// ---- MINRES loop control on the device (graph mode) ----------------------------------------------
+// ctl[0] target on the residual estimate, ctl[1] iteration budget, ctl[2] iterations done,
+// ctl[3] exit reason: 1 breakdown, 2 lucky (beta = 0 or r = 0), 3 estimate below target, 4 budget
+__global__ void k_mr_ctl(double* ctl, double target, double budget) {
+    ctl[0] = target;
+    ctl[1] = budget;
+    ctl[2] = 0.0;
+    ctl[3] = 0.0;
+}
+
+__device__ __forceinline__ int mr_exit_reason(const double* mr, double target, double it, double budget) {
+    if (mr[13] == 1.0) return 1;
+    if (mr[13] == 2.0 || mr[1] == 0.0) return 2;
+    if (fabs(mr[6]) <= target * mr[7]) return 3;
+    if (it >= budget) return 4;
+    return 0;
+}
+
+// the WHILE condition of the captured loop: continue while no exit reason holds (at most ctl[1]
+// iterations per graph launch, so the loop always ends)
+__global__ void k_mr_check(const double* mr, double* ctl, cudaGraphConditionalHandle h) {
+    const double it = ctl[2] + 1.0;
+    ctl[2] = it;
+    const int r = mr_exit_reason(mr, ctl[0], it, ctl[1]);
+    ctl[3] = double(r);
+    cudaGraphSetConditional(h, r == 0 ? 1u : 0u);
+}
+
+// one MINRES iteration on fixed buffers V = {V0, V1, Zc, Zn, D1, D2, AZ}, iterate X
+static void mr_iteration(pbm_grid* g, bool fp32, bool pc32, bool op_s, void* const* V, void* X, int64_t nv,
+                         cudaStream_t st) {
+    level_apply(g, 0, fp32, op_s, args(V[2], V[6], EPI_APPLY, nullptr, nullptr, nullptr, 0), st);
+    mr_lanczos2(g, fp32, V[6], V[0], V[1], nv, st);
+    precondition(g, fp32, pc32, op_s, V[1], V[3], nv, st);
+    mr_scalars(g, st);
+    mr_update2(g, fp32, V[2], V[3], V[4], V[5], X, nv, st);
+}
+
+// the captured loop for (fp32, op_s, pc32); built on first use
+static cudaGraphExec_t mr_graph(pbm_grid* g, bool fp32, bool pc32, bool op_s, void* const* V, void* X, int64_t nv,
+                                int64_t& kernels) {
+    const int key = (fp32 ? 1 : 0) | (op_s ? 2 : 0) | (pc32 ? 4 : 0);
+    kernels = g->mr_graph_kernels[key];
+    if (g->mr_graph[key]) return g->mr_graph[key];
+    if (!g->cap_stream) PBM_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    const cudaStream_t cs = g->cap_stream;
+    cudaGraph_t graph = nullptr;
+    PBM_CUDA(cudaGraphCreate(&graph, 0));
+    const int64_t before = launch_count();
+    try {
+        cudaGraphConditionalHandle h;
+        PBM_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        PBM_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        PBM_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        try {
+            mr_iteration(g, fp32, pc32, op_s, V, X, nv, cs);
+            k_mr_check<<<1, 1, 0, cs>>>(g->sc->mr, g->sc->ctl, h);
+            PBM_LAUNCH("mr check");
+        } catch (...) {
+            cudaGraph_t dummy = nullptr;
+            cudaStreamEndCapture(cs, &dummy);
+            throw;
+        }
+        PBM_CUDA(cudaStreamEndCapture(cs, &body));
+        cudaGraphExec_t ex = nullptr;
+        PBM_CUDA(cudaGraphInstantiate(&ex, graph, 0));
+        g->mr_graph[key] = ex;
+    } catch (...) {
+        cudaGraphDestroy(graph);
+        count_launch_add(before - launch_count());
+        throw;
+    }
+    cudaGraphDestroy(graph);
+    // captured launches did not run: count them when the graph executes
+    kernels = launch_count() - before;
+    g->mr_graph_kernels[key] = kernels;
+    count_launch_add(-kernels);
+    return g->mr_graph[key];
+}
+
 static MrResult minres(pbm_grid* g, bool fp32, bool op_s, const void* b, void* x, double rtol, int maxit,
-                       bool check_true, cudaStream_t st) {
+                       bool check_true, cudaStream_t st, bool pc32 = false) {
     MrResult res;
     const int64_t nv = g->L[0].g.n() + (op_s ? 1 : 0);
-    void* const* pool = fp32 ? (void* const*)g->kv32 : (void* const*)g->kv64;
-    void *vp = pool[0], *vc = pool[1], *z = pool[2], *z2 = pool[3], *dp = pool[4], *dp2 = pool[5], *Az = pool[6];
+    void* const* V = fp32 ? (void* const*)g->kv32 : (void* const*)g->kv64;
+    void* X = V[10];
     const size_t bytes = nv * esz(fp32);
     launch_dot(g, fp32, b, b, nv, 3, st);
     const double bnorm = std::sqrt(read_slot(g, 3, st));
@@ -238,61 +350,84 @@ static MrResult minres(pbm_grid* g, bool fp32, bool op_s, const void* b, void* x
         vec_zero(x, bytes, st);
         return res;
     }
-    level_apply(g, 0, fp32, op_s, args(x, vc, EPI_RESID, b, nullptr, nullptr, 2), st);
-    vcycle(g, 0, fp32, op_s, vc, z, 1, st);
+    PBM_CUDA(cudaMemcpyAsync(X, x, bytes, cudaMemcpyDeviceToDevice, st));
+    auto finish = [&]() { PBM_CUDA(cudaMemcpyAsync(x, X, bytes, cudaMemcpyDeviceToDevice, st)); };
+    level_apply(g, 0, fp32, op_s, args(X, V[1], EPI_RESID, b, nullptr, nullptr, 2), st);
+    precondition(g, fp32, pc32, op_s, V[1], V[2], nv, st);
     mr_init(g, st);
-    vec_zero(vp, bytes, st);
-    vec_zero(dp, bytes, st);
-    vec_zero(dp2, bytes, st);
+    vec_zero(V[0], bytes, st);
+    vec_zero(V[4], bytes, st);
+    vec_zero(V[5], bytes, st);
     double target = rtol;
-    auto read_mr = [&]() {
-        PBM_CUDA(cudaMemcpyAsync(g->sc_host->mr, g->sc->mr, sizeof(double) * 16, cudaMemcpyDeviceToHost, st));
+    double last_check = std::numeric_limits<double>::infinity();
+    double* mr = g->sc_host->mr;
+    double* ctl = g->sc_host->ctl;
+    auto read_state = [&](bool with_ctl) {
+        PBM_CUDA(cudaMemcpyAsync(mr, g->sc->mr, sizeof(double) * 16, cudaMemcpyDeviceToHost, st));
+        if (with_ctl) PBM_CUDA(cudaMemcpyAsync(ctl, g->sc->ctl, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
         PBM_CUDA(cudaStreamSynchronize(st));
     };
-    read_mr();
-    if (g->sc_host->mr[13] != 0.0) {
+    read_state(false);
+    if (mr[13] != 0.0) {
         res.status = PBM_EBREAKDOWN;
+        finish();
         return res;
     }
-    const double r0 = std::sqrt(g->sc_host->red[2]);
-    (void)r0;
-    for (int it = 1; it <= maxit; ++it) {
-        level_apply(g, 0, fp32, op_s, args(z, Az, EPI_APPLY, nullptr, nullptr, nullptr, 0), st);
-        mr_lanczos(g, fp32, Az, vc, vp, nv, st);
-        vcycle(g, 0, fp32, op_s, vp, z2, 1, st);
-        mr_scalars(g, st);
-        mr_update(g, fp32, z, dp2, dp, x, nv, st);
-        std::swap(vp, vc);
-        std::swap(dp2, dp);
-        std::swap(z, z2);
-        res.iters = it;
-        read_mr();
-        const double* mr = g->sc_host->mr;
-        if (mr[13] == 1.0) {
-            res.status = PBM_EBREAKDOWN;
-            break;
+    // the graph cannot hold the profiling event pairs: profiled solves launch eagerly
+    const bool graph = !g->prof_on;
+    while (res.iters < maxit) {
+        int reason = 0;
+        const int budget = maxit - res.iters;
+        if (graph) {
+            int64_t kernels = 0;
+            cudaGraphExec_t ex = mr_graph(g, fp32, pc32, op_s, V, X, nv, kernels);
+            k_mr_ctl<<<1, 1, 0, st>>>(g->sc->ctl, target, double(budget));
+            PBM_LAUNCH("mr ctl");
+            PBM_CUDA(cudaGraphLaunch(ex, st));
+            read_state(true);
+            res.iters += int(ctl[2]);
+            count_launch_add(kernels * int64_t(ctl[2]));
+            reason = int(ctl[3]);
+        } else {
+            mr_iteration(g, fp32, pc32, op_s, V, X, nv, st);
+            read_state(false);
+            res.iters += 1;
+            reason = mr[13] == 1.0 ? 1 : (mr[13] == 2.0 || mr[1] == 0.0) ? 2
+                   : (std::fabs(mr[6]) <= target * mr[7]) ? 3 : (res.iters >= maxit ? 4 : 0);
         }
-        const bool lucky = (mr[13] == 2.0) || mr[1] == 0.0;
-        if (std::fabs(mr[6]) <= target * mr[7] || lucky) {
-            if (!check_true) return res;
-            level_apply(g, 0, fp32, op_s, args(x, Az, EPI_RESID, b, nullptr, nullptr, 2), st);
-            res.relres = std::sqrt(read_slot(g, 2, st)) / bnorm;
-            if (res.relres <= rtol || lucky) {
-                res.status = res.relres <= rtol ? PBM_OK : PBM_ENOTCONV;
+        if (reason == 1) {
+            res.status = PBM_EBREAKDOWN;
+            finish();
+            return res;
+        }
+        if (reason == 2 || reason == 3) {
+            if (!check_true) {
+                finish();
                 return res;
             }
+            level_apply(g, 0, fp32, op_s, args(X, V[6], EPI_RESID, b, nullptr, nullptr, 2), st);
+            res.relres = std::sqrt(read_slot(g, 2, st)) / bnorm;
+            if (res.relres <= rtol) {
+                finish();
+                return res;
+            }
+            if (reason == 2 || !(res.relres < 0.5 * last_check)) {
+                res.status = PBM_ENOTCONV;
+                finish();
+                return res;
+            }
+            last_check = res.relres;
             target = target * 0.5 * rtol / res.relres;
         }
     }
-    if (res.status == PBM_OK) {
-        if (check_true) {
-            level_apply(g, 0, fp32, op_s, args(x, Az, EPI_RESID, b, nullptr, nullptr, 2), st);
-            res.relres = std::sqrt(read_slot(g, 2, st)) / bnorm;
-            res.status = res.relres <= rtol ? PBM_OK : PBM_ENOTCONV;
-        } else {
-            res.status = PBM_ENOTCONV;
-        }
+    if (check_true) {
+        level_apply(g, 0, fp32, op_s, args(X, V[6], EPI_RESID, b, nullptr, nullptr, 2), st);
+        res.relres = std::sqrt(read_slot(g, 2, st)) / bnorm;
+        res.status = res.relres <= rtol ? PBM_OK : PBM_ENOTCONV;
+    } else {
+        res.status = PBM_ENOTCONV;
     }
+    finish();
     return res;
 }
 
@@ -303,6 +438,14 @@ static double true_relres(pbm_grid* g, bool op_s, const double* b, const double*
     return std::sqrt(read_slot(g, 2, st)) / bnorm;
 }
 
+// Mixed precision (PBM_MIXED), two stages:
+//  1. FP64 iterative refinement around inner MINRES solves of the residual equation that run
+//     entirely in FP32 (operator, V-cycle, vectors; FP64 scalars) to desc.inner_rtol. Each step must
+//     at least halve the FP64 residual; a step that does not is undone and the solve moves on.
+//  2. FP64 MINRES (FP64 vectors and operator) preconditioned by the FP32 V-cycle, restarted from
+//     the current iterate (residual replacement) while the true residual keeps halving. It needs
+//     only the preconditioner to be accurate to FP32, so it also converges where the FP32
+//     operator is too inexact for stage 1 (condition number near 1 / FP32 epsilon).
 int solve(pbm_grid* g, bool op_s, const double* b, double* x, double rtol, int maxit, pbm_solve_info* info,
           cudaStream_t st) {
     auto t0 = std::chrono::steady_clock::now();
@@ -315,8 +458,7 @@ int solve(pbm_grid* g, bool op_s, const double* b, double* x, double rtol, int m
         inf.outer = 1;
         inf.relres = r.relres;
     } else {
-        // FP64 iterative refinement around FP32 MG-MINRES solves of the residual equation
-        double* r64 = g->kv64[0];
+        double* r64 = g->kv64[7];
         float* r32 = g->kv32[7];
         float* dx32 = g->kv32[8];
         launch_dot(g, false, b, b, nv, 3, st);
@@ -325,31 +467,45 @@ int solve(pbm_grid* g, bool op_s, const double* b, double* x, double rtol, int m
         if (bnorm == 0.0) {
             vec_zero(x, nv * sizeof(double), st);
         } else {
-            int total = 0;
+            int total = 0, outer = 0;
             double rel = true_relres(g, op_s, b, x, r64, bnorm, st);
-            int outer = 0;
-            while (rel > rtol) {
-                if (total >= maxit || outer >= 60) {
-                    inf.status = PBM_ENOTCONV;
-                    break;
-                }
+            bool robust = false;
+            while (rel > rtol && !robust) {
+                if (total >= maxit || outer >= 60) break;
                 ++outer;
                 launch_cast(r64, false, r32, true, nv, st);
                 vec_zero(dx32, nv * sizeof(float), st);
                 MrResult ir = minres(g, true, op_s, r32, dx32, g->desc.inner_rtol, maxit - total, false, st);
                 total += ir.iters;
                 if (ir.status == PBM_EBREAKDOWN) {
+                    robust = true;
+                    break;
+                }
+                add_f32(x, dx32, nv, st, 1.0);
+                const double prev = rel;
+                rel = true_relres(g, op_s, b, x, r64, bnorm, st);
+                if (!(rel < 0.5 * prev)) {
+                    if (!(rel < prev)) {
+                        add_f32(x, dx32, nv, st, -1.0);
+                        rel = prev;
+                    }
+                    robust = true;
+                }
+            }
+            double last = std::numeric_limits<double>::infinity();
+            while (rel > rtol && robust && total < maxit) {
+                ++outer;
+                MrResult r = minres(g, false, op_s, b, x, rtol, maxit - total, true, st, true);
+                total += r.iters;
+                rel = r.relres;
+                if (r.status == PBM_EBREAKDOWN) {
                     inf.status = PBM_EBREAKDOWN;
                     break;
                 }
-                add_f32(x, dx32, nv, st);
-                const double prev = rel;
-                rel = true_relres(g, op_s, b, x, r64, bnorm, st);
-                if (!(rel < prev)) {  // no progress: stop rather than loop
-                    inf.status = PBM_ENOTCONV;
-                    break;
-                }
+                if (r.status == PBM_OK || !(rel < 0.5 * last)) break;
+                last = rel;
             }
+            if (inf.status == PBM_OK && rel > rtol) inf.status = PBM_ENOTCONV;
             inf.iterations = total;
             inf.outer = outer;
             inf.relres = rel;

@@ -232,6 +232,37 @@ def test_minres_S_mixed_precision(pkg, dims, bc, levels):
     assert rel(host(x), ref) < 1e-7
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_minres_K_bridge_bumps(pkg, precision):
+    """The four-corner bridge with a Gaussian-bump density (contrast 1e3) is the ill-conditioned case: the mixed
+    path must still reach the tolerance (its FP64-operator stage takes over when FP32 refinement stalls)."""
+    nx, ny, nz, lv = 32, 16, 16, 4
+    g = fem.Grid(nx, ny, nz, "bridge_corners")
+    rho = synthetic.density_bumps(nx, ny, nz, 0.2, 0)
+    f = synthetic.load_vector(nx, ny, nz, "top_traction")
+    K = fem.assemble_K(g, rho, fem.element_stiffness())
+    u_ref = solvers.direct_solve(K, f)
+    G = pkg.Grid(nx, ny, nz, lv, "bridge_corners", precision=precision)
+    G.set_density(dev(rho))
+    u, info = G.minres_solve("K", dev(f), rtol=1e-8, maxit=3000)
+    assert info["relres"] <= 1e-8
+    r = f - K @ host(u)
+    assert np.linalg.norm(r) <= 1.01e-8 * np.linalg.norm(f)
+    assert rel(host(u), u_ref) < 1e-5
+
+
+def test_minres_stagnation_returns_notconv(pkg):
+    """A tolerance below what FP64 can reach on the bridge ends with PBM_ENOTCONV and the best iterate, not after
+    maxit iterations."""
+    nx, ny, nz, lv = 32, 16, 16, 4
+    rho = synthetic.density_bumps(nx, ny, nz, 0.2, 0)
+    f = synthetic.load_vector(nx, ny, nz, "top_traction")
+    G = pkg.Grid(nx, ny, nz, lv, "bridge_corners")
+    G.set_density(dev(rho))
+    u, info = G.minres_solve("K", dev(f), rtol=1e-17, maxit=5000, check=False)
+    assert info["rc"] == -5 and info["iterations"] < 1000 and info["relres"] < 1e-9
+
+
 def test_minres_zero_rhs_and_state_errors(pkg):
     G = pkg.Grid(8, 4, 4, 2, "cantilever")
     from paper_1904_06556_gb300 import PbmError
