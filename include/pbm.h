@@ -249,6 +249,25 @@ int pbm_profile(pbm_grid* g, int on);
  * Errors: PBM_EINVAL (null argument, unknown operator). */
 int pbm_profile_read(pbm_grid* g, int op, pbm_profile_stats* out);
 
+/* y = K(w) x, exactly as pbm_apply_K computes it (FP64, supported rows and columns the identity),
+ * for callers that cannot allocate device memory and so cannot create a grid handle: code running
+ * while a CUDA graph is being captured, loops that must not allocate after start-up, or hosts whose
+ * own allocator owns all device memory. The paper has no counterpart; this is an interface for
+ * such callers. The call allocates nothing (no cudaMalloc, cudaFree or allocating library routine):
+ * the scratch of its kernels is one fixed 32 MiB array in the library's device code, which every
+ * GPU that loads the library holds until the process exits.
+ *   nx, ny, nz, support, E, nu, h: the grid as in pbm_grid_desc (no multigrid levels are needed).
+ *   w_dev: m FP64 element weights; x_dev, y_dev: n FP64 entries, caller-owned, not overlapping.
+ *   stream: as elsewhere (work is enqueued, nothing synchronises).
+ * The first call on a device looks up the array's device address on that device; make that first
+ * call before any stream capture. Every call shares the array and finds it as the previous call
+ * left it, so calls whose work overlaps on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.
+ * Errors: PBM_EINVAL (null pointer, bad sizes or material, or a grid whose scratch exceeds the
+ * array: roughly more than 170,000 elements), PBM_ECUDA. */
+int pbm_apply_K_noalloc(int nx, int ny, int nz, int support, double E, double nu, double h, const double* w_dev,
+                        const double* x_dev, double* y_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

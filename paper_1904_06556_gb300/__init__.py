@@ -14,7 +14,7 @@ import torch
 from . import _lib
 from ._lib import PbmError, SolveInfo, NewtonInfo  # noqa: F401
 
-__all__ = ["Grid", "PbmError", "lib", "kernel_launches"]
+__all__ = ["Grid", "PbmError", "lib", "kernel_launches", "apply_K_noalloc"]
 
 _LIB = None
 
@@ -29,6 +29,20 @@ def lib() -> C.CDLL:
 def kernel_launches() -> int:
     """Number of CUDA kernels the library has launched in this process."""
     return int(lib().pbm_kernel_launches())
+
+
+def apply_K_noalloc(nx: int, ny: int, nz: int, support: str, x: torch.Tensor, w: torch.Tensor,
+                    out: torch.Tensor | None = None, E: float = 1.0, nu: float = 0.3, h: float = 1.0) -> torch.Tensor:
+    """y = K(w) x like Grid.apply_K, for callers that cannot allocate device memory (pbm_apply_K_noalloc): no grid
+    handle, and the library allocates nothing. Pass `out` to avoid the allocation of the result tensor too."""
+    L = lib()
+    n, m = 3 * (nx + 1) * (ny + 1) * (nz + 1), nx * ny * nz
+    y = torch.empty_like(x) if out is None else out
+    rc = L.pbm_apply_K_noalloc(nx, ny, nz, _lib.SUPPORTS[support], float(E), float(nu), float(h),
+                               _ptr(w, n=m, name="w"), _ptr(x, n=n, name="x"), _ptr(y, n=n, name="y"), _stream())
+    if rc != 0:
+        raise PbmError(rc, L.pbm_last_error().decode())
+    return y
 
 
 def _ptr(t: torch.Tensor | None, dtype=torch.float64, n: int | None = None, name: str = "tensor"):

@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pbm_newton_step": (i, [vp, C.POINTER(State), vp, d, C.POINTER(NewtonInfo), vp]),
         "pbm_compliance_grad": (i, [vp, vp, vp, vp, C.POINTER(C.c_double), vp]),
         "pbm_kernel_launches": (C.c_int64, []),
+        "pbm_apply_K_noalloc": (i, [i, i, i, i, d, d, d, vp, vp, vp, vp]),
         "pbm_profile": (i, [vp, i]),
         "pbm_profile_read": (i, [vp, i, C.POINTER(ProfileStats)]),
     }
