@@ -216,10 +216,16 @@ def run_ours(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > 2 x L2
     last = {}
 
+    ph = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
     def step():
+        ph[0].record(stream)
         G.set_state(sd)
+        ph[1].record(stream)
         rhs = G.reduced_rhs(f)
+        ph[2].record(stream)
         x, info = G.minres_solve("S", rhs, rtol=w.rtol, maxit=1000)
+        ph[3].record(stream)
         last["info"] = info
         return x
 
@@ -248,6 +254,8 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    phases = {"set_state_ms": ph[0].elapsed_time(ph[1]), "rhs_ms": ph[1].elapsed_time(ph[2]),
+              "minres_ms": ph[2].elapsed_time(ph[3])}
 
     # ---- the same steps again with every fine-level S launch bracketed by CUDA events on its stream
     # (pbm_profile): the roofline's kernel durations. Profiled solves launch eagerly, because an
@@ -341,7 +349,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32+f64",
         "data": "synthetic (seeded; shapes of the paper's cantilever example, Section 6)",
         "config": workload_desc(w, precision),
-        "solve": {"minres_iterations": iters[-1], "true_relres": relres,
+        "solve": {"minres_iterations": iters[-1], "true_relres": relres, "phases_last_step": phases,
+                  "mixed_outer_steps": last["info"]["outer"], "fine_chunk": G.info()["fine_chunk"],
                   "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
                   "equilibrium_u_relres": uinfo["relres"]},
         "k_apply": kapply,
@@ -356,6 +365,97 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_batch(args):
+    """Batching workload: 12 design instances of uneven size (3 each of 32x16x16, 48x24x24, 64x32x32 and 96x48x48
+    cantilevers, densities U[1e-3, 1] rescaled to mean 0.3, seeds 0..11), each with 4 load cases (end point load,
+    distributed end load, top-face traction, torsion couple): 48 reduced-Newton systems. One step = the set-up of every
+    system (pbm_set_state), its right-hand side and the solve of all 48 systems, batched (one launch per stage for all
+    systems, graph-captured MINRES) or one by one; reports systems per second for both."""
+    import torch
+
+    import paper_1904_06556_gb300 as pkg
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    precision = args.precision
+
+    def t64(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+    grids, states, fs = [], [], []
+    for w in synthetic.BATCH_WORKLOADS:
+        rho = synthetic.density_for(w)
+        with pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision="fp64") as G64:
+            G64.set_density(t64(rho))
+            for load in w.loads:
+                f = t64(synthetic.load_vector(w.nx, w.ny, w.nz, load))
+                u, inf = G64.minres_solve("K", f, rtol=w.rtol, maxit=2000, check=False)
+                st_h = synthetic.synthetic_state(w, np.zeros(w.n))
+                sd = {k: t64(st_h[k]) for k in ("nu_lo", "nu_up", "rho", "mu_lo", "mu_up")}
+                sd["u"] = u
+                sd.update({k: float(st_h[k]) for k in ("alpha", "p", "q_lo", "q_up", "V", "rho_lo", "rho_up")})
+                G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=precision)
+                grids.append(G)
+                states.append(sd)
+                fs.append(f)
+    B = pkg.Batch(grids, "S")
+    rtol = synthetic.BATCH_WORKLOADS[0].rtol
+    stream = torch.cuda.current_stream()
+    last = {}
+
+    def setup():
+        rhs = []
+        for G, sd, f in zip(grids, states, fs):
+            G.set_state(sd)
+            rhs.append(G.reduced_rhs(f))
+        return rhs
+
+    def step_batched():
+        rhs = setup()
+        xs, infos = B.minres_solve(rhs, rtol=rtol, maxit=2000)
+        last["b"] = infos
+
+    def step_single():
+        rhs = setup()
+        infos = []
+        for G, r in zip(grids, rhs):
+            _, inf = G.minres_solve("S", r, rtol=rtol, maxit=2000)
+            infos.append(inf)
+        last["s"] = infos
+
+    res = {}
+    for name, fn in (("batched", step_batched), ("one_by_one", step_single)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = pkg.kernel_launches()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[name] = {"ms_per_step": ms, "systems_per_s": len(grids) / (ms / 1e3),
+                     "gpu_launches_per_step": (pkg.kernel_launches() - n0) / args.steps}
+    ib, i1 = last["b"], last["s"]
+    out = {"metric": METRIC + " (batching workload)", "value": res["batched"]["systems_per_s"],
+           "unit": "reduced-Newton systems/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": res["batched"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed" else "f64",
+           "data": "synthetic (seeded; 12 cantilever instances x 4 load cases)",
+           "config": {"workload": "batch48: 3 each of 32x16x16, 48x24x24, 64x32x32, 96x48x48 cantilevers, "
+                                  "4 load cases each", "systems": len(grids), "precision": precision, "rtol": rtol},
+           "batched": res["batched"], "one_by_one": res["one_by_one"],
+           "speedup_vs_one_by_one": res["one_by_one"]["ms_per_step"] / res["batched"]["ms_per_step"],
+           "iterations_batched": [x["iterations"] for x in ib], "iterations_one_by_one": [x["iterations"] for x in i1],
+           "max_relres_batched": max(x["relres"] for x in ib)}
+    B.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -482,7 +582,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="cant64", choices=["cant64", "bridge128", "cant32", "cant16"])
+    ap.add_argument("--workload", default="cant64", choices=["cant64", "bridge128", "cant32", "cant16", "batch48"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=30.0)
@@ -491,6 +591,8 @@ def main():
         raise SystemExit("--steps >= 1 and --warmup >= 0")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch48":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -96,6 +96,9 @@ typedef struct pbm_grid_info {
     double omega[16];             /* current Jacobi weights (0 until an operator is set up)      */
     double lambda_max[16];        /* current Lanczos estimates                                   */
     int64_t device_bytes;         /* device memory held by the handle                            */
+    int fine_chunk[4];            /* element layers per thread of the fine operator's column pass,
+                                     chosen by timing at creation: FP64 K, FP64 S, FP32 K, FP32 S
+                                     (0 where the precision is not used)                         */
 } pbm_grid_info;
 
 /* Newton state of the dual VTS problem (eq. (aug_lagr)): variables xi = (u, alpha, nu_lo, nu_up),
@@ -230,6 +233,42 @@ int pbm_minres_solve(pbm_grid* g, int op, const double* b_dev, double* x_dev, do
 int pbm_newton_step(pbm_grid* g, pbm_state* st, const double* f_dev, double eps_mr, pbm_newton_info* info,
                     void* stream);
 
+/* Parameters of Algorithm 1 (PBM outer loop). pbm_default_pbm_params gives the paper's values
+ * (Section 3.3, Section 5.3): eps_pbm 1e-5, beta = gamma = 0.3, p_min 1e-8, eps_nwt 1 and its
+ * floor 1e-3, eps_mr = 1e-4 sqrt(n) (eps_mr <= 0 selects it) reduced tenfold down to eps_mr_min
+ * whenever a Newton step reduces res_PBM by less than 10 percent. */
+typedef struct pbm_pbm_params {
+    double eps_pbm;        /* stop when |delta / d| < eps_pbm (duality gap over dual objective)  */
+    double beta;           /* multiplier safeguard: beta x <= x+ <= x / beta, 0 < beta < 1       */
+    double gamma;          /* penalty reduction p+ = max(gamma p, p_min), 0 < gamma < 1          */
+    double p_min;
+    double eps_nwt, eps_nwt_min;  /* Newton tolerance on res_PBM and its floor                   */
+    double eps_mr, eps_mr_min;    /* MINRES relative tolerance (<= 0: 1e-4 sqrt(n)) and floor    */
+    int max_outer, max_newton;    /* outer iterations; Newton steps per Newton loop              */
+} pbm_pbm_params;
+
+typedef struct pbm_pbm_info {
+    int status;
+    int outer, newton, minres;    /* outer iterations, Newton steps, MINRES iterations in total */
+    double gap_ratio;             /* |delta / d| at the end of the last outer iteration         */
+    double compliance;            /* 1/2 f^T u at exit                                           */
+    double volume;                /* sum rho at exit                                              */
+    double eps_mr;                /* MINRES tolerance in use at exit                              */
+} pbm_pbm_info;
+
+int pbm_default_pbm_params(pbm_pbm_params* p);
+
+/* Algorithm 1: the PBM method for the VTS problem (eq. (1)) in its dual form, from the state *st
+ * (for the paper's initial point: u = 0, alpha = 1, nu = e, rho = V/m, mu = e, p = q = 1). Each
+ * outer iteration runs Newton steps (Algorithm 2, pbm_newton_step) until res_PBM < eps_nwt, then
+ * evaluates the duality gap delta (eq. (gap)) and d, stops when |delta / d| < eps_pbm, else updates
+ * the multipliers (rho, mu_lo, mu_up with the beta safeguard), the penalties and eps_nwt. The run
+ * ends with a Newton loop at 10 eps_pbm and a final density update. st is updated in place; st->rho
+ * holds the optimal densities on exit. Synchronises. Errors: PBM_ENOTCONV (max_outer or max_newton
+ * reached), PBM_ELINESEARCH, PBM_EBREAKDOWN, PBM_EINVAL. */
+int pbm_solve(pbm_grid* g, pbm_state* st, const double* f_dev, const pbm_pbm_params* prm, pbm_pbm_info* info,
+              void* stream);
+
 /* Per-element compliances c_i = 1/2 u^T K_i u (the constraint terms of the dual, eq. (dual), and
  * minus the derivative of 1/2 f^T u w.r.t. rho_i at equilibrium). u_dev: n (masked internally);
  * c_dev: m. If f_dev and fTu_host are both non-NULL, *fTu_host receives f^T u (synchronises). */
@@ -248,6 +287,30 @@ int pbm_profile(pbm_grid* g, int on);
  * accumulated since its last read into `out` and resets them. Waits for the recorded events.
  * Errors: PBM_EINVAL (null argument, unknown operator). */
 int pbm_profile_read(pbm_grid* g, int op, pbm_profile_stats* out);
+
+/* ---- batched solves --------------------------------------------------------------------------
+ * A batch advances several independent systems (grid handles of any sizes, FP64 or all mixed, with
+ * the same smoothing sweeps) together: every stage of the MINRES iteration and the V-cycle is one
+ * launch over all systems' work, and the iteration runs as a CUDA-graph loop until every system has
+ * finished. This is the benchmark spec's batching of design instances and load cases; each system keeps
+ * its own hierarchy, scratch and scalars, so the results equal those of separate solves up to the
+ * iteration at which each system stops. */
+typedef struct pbm_batch pbm_batch;
+
+/* grids: n handles on one device. op: PBM_OP_K or PBM_OP_S (every system's operator must be set up
+ * before each solve: pbm_set_density + a solve or pbm_vcycle for K, pbm_set_state for S). The
+ * batch stores the grids' buffer addresses: destroy it before any of its grids. Errors: PBM_EINVAL
+ * (mixed precisions, different sweeps, a repeated grid), PBM_ENOMEM. */
+int pbm_batch_create(pbm_grid* const* grids, int n, int op, pbm_batch** out);
+int pbm_batch_destroy(pbm_batch* b);
+
+/* Solves A_s x_s = b_s for every system s (b_dev[s], x_dev[s]: device vectors of that system's
+ * length, x the initial guess on entry) to the true relative residual rtol, as pbm_minres_solve does
+ * for one system (mixed grids: FP64 refinement around batched FP32 inner solves, with the
+ * single-system FP32-preconditioned FP64 stage for any system the refinement cannot finish).
+ * infos: n results or NULL. Synchronises. Returns the first non-OK status of any system. */
+int pbm_batch_minres_solve(pbm_batch* b, const double* const* b_dev, double* const* x_dev, double rtol, int maxit,
+                           pbm_solve_info* infos, void* stream);
 
 /* y = K(w) x, exactly as pbm_apply_K computes it (FP64, supported rows and columns the identity),
  * for callers that cannot allocate device memory and so cannot create a grid handle: code running

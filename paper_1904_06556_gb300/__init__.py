@@ -14,7 +14,7 @@ import torch
 from . import _lib
 from ._lib import PbmError, SolveInfo, NewtonInfo  # noqa: F401
 
-__all__ = ["Grid", "PbmError", "lib", "kernel_launches", "apply_K_noalloc"]
+__all__ = ["Grid", "Batch", "PbmError", "lib", "kernel_launches", "apply_K_noalloc"]
 
 _LIB = None
 
@@ -117,7 +117,7 @@ class Grid:
         L = gi.levels
         return dict(levels=L, dims=[(gi.nx[k], gi.ny[k], gi.nz[k]) for k in range(L)], n=list(gi.n[:L]),
                     m=list(gi.m[:L]), n_free=gi.n_free, omega=list(gi.omega[:L]), lambda_max=list(gi.lambda_max[:L]),
-                    device_bytes=gi.device_bytes)
+                    device_bytes=gi.device_bytes, fine_chunk=list(gi.fine_chunk))
 
     def maps(self, level: int, which: str):
         import numpy as np
@@ -229,6 +229,36 @@ class Grid:
         self._check(self._L.pbm_profile_read(self._h, _lib.OPS[op], C.byref(ps)))
         return {k: getattr(ps, k) for k, _ in _lib.ProfileStats._fields_}
 
+    def pbm_solve(self, st: dict, f: torch.Tensor, check: bool = True, **params):
+        """Algorithm 1 from the state `st` (updated in place; st['rho'] holds the densities on exit). Keyword
+        arguments override the paper's parameters (eps_pbm, beta, gamma, p_min, eps_nwt, eps_nwt_min, eps_mr,
+        eps_mr_min, max_outer, max_newton)."""
+        prm = _lib.PbmParams()
+        self._check(self._L.pbm_default_pbm_params(C.byref(prm)))
+        for k, v in params.items():
+            if not hasattr(prm, k):
+                raise TypeError(f"unknown PBM parameter {k}")
+            setattr(prm, k, v)
+        s = self._state(st)
+        inf = _lib.PbmInfo()
+        rc = self._L.pbm_solve(self._h, C.byref(s), _ptr(f, n=self.n, name="f"), C.byref(prm), C.byref(inf),
+                               _stream())
+        info = {k: getattr(inf, k) for k, _ in _lib.PbmInfo._fields_}
+        info["rc"] = rc
+        if check:
+            self._check(rc)
+        for k in ("alpha", "p", "q_lo", "q_up"):
+            st[k] = getattr(s, k)
+        return info
+
+    @staticmethod
+    def initial_state(n: int, m: int, V: float, rho_lo: float, rho_up: float, device="cuda") -> dict:
+        """The paper's initial point of Algorithm 1: u = 0, alpha = 1, nu = e, rho = V/m, mu = e, p = q = 1."""
+        f64 = dict(dtype=torch.float64, device=device)
+        return dict(u=torch.zeros(n, **f64), nu_lo=torch.ones(m, **f64), nu_up=torch.ones(m, **f64),
+                    rho=torch.full((m,), V / m, **f64), mu_lo=torch.ones(m, **f64), mu_up=torch.ones(m, **f64),
+                    alpha=1.0, p=1.0, q_lo=1.0, q_up=1.0, V=V, rho_lo=rho_lo, rho_up=rho_up)
+
     def compliance_grad(self, u: torch.Tensor, f: torch.Tensor | None = None):
         c = torch.empty(self.m, dtype=torch.float64, device=u.device)
         fTu = C.c_double(0.0)
@@ -236,3 +266,46 @@ class Grid:
                                                 _ptr(f, n=self.n, name="f"), C.byref(fTu) if f is not None else None,
                                                 _stream()))
         return (c, fTu.value) if f is not None else c
+
+
+class Batch:
+    """Several grids solved together, one launch per stage for all of them (see pbm_batch_create)."""
+
+    def __init__(self, grids: list, op: str = "S"):
+        self._L = lib()
+        self.grids = list(grids)
+        self.op = op
+        arr = (C.c_void_p * len(self.grids))(*[g._h.value for g in self.grids])
+        h = C.c_void_p()
+        rc = self._L.pbm_batch_create(arr, len(self.grids), _lib.OPS[op], C.byref(h))
+        if rc != 0:
+            raise PbmError(rc, self._L.pbm_last_error().decode())
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._L.pbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def minres_solve(self, bs: list, rtol: float = 1e-8, maxit: int = 1000, x0s: list | None = None,
+                     check: bool = True):
+        """Solves every system; returns (list of solutions, list of info dicts)."""
+        ns = len(self.grids)
+        xs = [torch.zeros_like(b) if x0s is None else x0s[i].clone() for i, b in enumerate(bs)]
+        for g, b, x in zip(self.grids, bs, xs):
+            n = g.n + (1 if self.op == "S" else 0)
+            _ptr(b, n=n, name="b"), _ptr(x, n=n, name="x")
+        barr = (C.c_void_p * ns)(*[b.data_ptr() for b in bs])
+        xarr = (C.c_void_p * ns)(*[x.data_ptr() for x in xs])
+        infos = (_lib.SolveInfo * ns)()
+        rc = self._L.pbm_batch_minres_solve(self._h, barr, xarr, float(rtol), int(maxit), infos, _stream())
+        out = [{k: getattr(inf, k) for k, _ in _lib.SolveInfo._fields_} for inf in infos]
+        if check and rc != 0:
+            raise PbmError(rc, self._L.pbm_last_error().decode())
+        return xs, out

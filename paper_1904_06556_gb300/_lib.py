@@ -35,7 +35,7 @@ class GridDesc(C.Structure):
 class GridInfo(C.Structure):
     _fields_ = [("levels", C.c_int), ("nx", C.c_int * 16), ("ny", C.c_int * 16), ("nz", C.c_int * 16),
                 ("n", C.c_int64 * 16), ("m", C.c_int64 * 16), ("n_free", C.c_int64), ("omega", C.c_double * 16),
-                ("lambda_max", C.c_double * 16), ("device_bytes", C.c_int64)]
+                ("lambda_max", C.c_double * 16), ("device_bytes", C.c_int64), ("fine_chunk", C.c_int * 4)]
 
 
 class State(C.Structure):
@@ -47,6 +47,18 @@ class State(C.Structure):
 
 class ProfileStats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("total_ms", C.c_double), ("bytes", C.c_double), ("flops", C.c_double)]
+
+
+class PbmParams(C.Structure):
+    _fields_ = [("eps_pbm", C.c_double), ("beta", C.c_double), ("gamma", C.c_double), ("p_min", C.c_double),
+                ("eps_nwt", C.c_double), ("eps_nwt_min", C.c_double), ("eps_mr", C.c_double),
+                ("eps_mr_min", C.c_double), ("max_outer", C.c_int), ("max_newton", C.c_int)]
+
+
+class PbmInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("outer", C.c_int), ("newton", C.c_int), ("minres", C.c_int),
+                ("gap_ratio", C.c_double), ("compliance", C.c_double), ("volume", C.c_double),
+                ("eps_mr", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -91,6 +103,11 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pbm_newton_step": (i, [vp, C.POINTER(State), vp, d, C.POINTER(NewtonInfo), vp]),
         "pbm_compliance_grad": (i, [vp, vp, vp, vp, C.POINTER(C.c_double), vp]),
         "pbm_kernel_launches": (C.c_int64, []),
+        "pbm_batch_create": (i, [C.POINTER(vp), i, i, C.POINTER(vp)]),
+        "pbm_batch_destroy": (i, [vp]),
+        "pbm_batch_minres_solve": (i, [vp, C.POINTER(vp), C.POINTER(vp), d, i, C.POINTER(SolveInfo), vp]),
+        "pbm_default_pbm_params": (i, [C.POINTER(PbmParams)]),
+        "pbm_solve": (i, [vp, C.POINTER(State), vp, C.POINTER(PbmParams), C.POINTER(PbmInfo), vp]),
         "pbm_apply_K_noalloc": (i, [i, i, i, i, d, d, d, vp, vp, vp, vp]),
         "pbm_profile": (i, [vp, i]),
         "pbm_profile_read": (i, [vp, i, C.POINTER(ProfileStats)]),

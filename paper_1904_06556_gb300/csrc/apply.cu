@@ -448,7 +448,7 @@ void launch_fine(pbm_grid* g, bool fp32, const void* w, const void* d, const voi
                           st);
     if (g->prof_on) {
         double bytes = 0.0, flops = 0.0;
-        cols_cost(g->L[0].g, s, fp32, a.mode, fp32 ? 4 : 8, bytes, flops);
+        cols_cost(g->L[0].g, fine_L(g, fp32, s), s, fp32, a.mode, fp32 ? 4 : 8, bytes, flops);
         prof_end(g, st, s ? PBM_OP_S : PBM_OP_K, bytes, flops);
     }
 }

@@ -12,7 +12,8 @@ namespace pbm {
 
 void upload_tri_tables();
 void setup_hierarchy(pbm_grid* g, bool op_s, cudaStream_t st);
-void vcycle(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, void* x, int dot_slot, cudaStream_t st);
+void vcycle(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, void* x, int dot_slot, cudaStream_t st,
+            bool first_done = false);
 int solve(pbm_grid* g, bool op_s, const double* b, double* x, double rtol, int maxit, pbm_solve_info* info,
           cudaStream_t st);
 void launch_coeffs(pbm_grid* g, const pbm_state* s, const double* c2, double* coef, cudaStream_t st);
@@ -26,6 +27,8 @@ void launch_lagr_terms(pbm_grid* g, double kappa, const double* c2u, const doubl
                        cudaStream_t st);
 void launch_axpy(double* y, const double* x, double kappa, int64_t n, cudaStream_t st);
 void launch_scale(const double* a, double* b, double s, int64_t n, cudaStream_t st);
+void launch_mult_update(pbm_grid* g, const double* c2, pbm_state* s, double beta, bool only_rho, cudaStream_t st);
+void launch_gap_sums(pbm_grid* g, const double* c2, const pbm_state* s, int slot, cudaStream_t st);
 
 static thread_local std::string g_last_error;
 static std::atomic<long long> g_launches{0};
@@ -241,6 +244,9 @@ int pbm_create_grid(const pbm_grid_desc* d, pbm_grid** out) {
     const int64_t nc_dofs = 3LL * (d->nx / f + 1) * (d->ny / f + 1) * (d->nz / f + 1);
     if (d->levels >= 2 && nc_dofs > 1500) fail(PBM_EINVAL, "coarsest grid too large (more than 1500 dofs): add levels");
     if (d->levels < 2) fail(PBM_EINVAL, "at least 2 levels are needed (the V-cycle ends in an exact coarse solve)");
+    if (3.0 * (d->nx + 1.0) * (d->ny + 1.0) * (d->nz + 1.0) >= 2147483647.0 ||
+        8.0 * double(d->nx) * d->ny * d->nz >= 2147483647.0)
+        fail(PBM_EINVAL, "grid too large: the kernels index nodes and elements with 32-bit integers");
 
     g = new pbm_grid();
     g->desc = *d;
@@ -345,6 +351,8 @@ int pbm_create_grid(const pbm_grid_desc* d, pbm_grid** out) {
     PBM_CUDA(cudaMallocHost((void**)&g->sc_host, sizeof(DevScalars)));
     std::memset(g->sc_host, 0, sizeof(DevScalars));
     PBM_CUDA(cudaDeviceSynchronize());
+    autotune_fine(g);
+    PBM_CUDA(cudaDeviceSynchronize());
     *out = g;
     g = nullptr;
     }
@@ -434,6 +442,10 @@ int pbm_grid_info_get(const pbm_grid* g, pbm_grid_info* out) {
             for (int i = 0; i <= F.nx; ++i) fixed += node_fixed(F.support, F.nx, F.ny, F.nz, i, j, k) ? 1 : 0;
     out->n_free = F.n() - 3 * fixed;
     out->device_bytes = g->bytes;
+    out->fine_chunk[0] = fine_L(g, false, false);
+    out->fine_chunk[1] = fine_L(g, false, true);
+    out->fine_chunk[2] = g->desc.precision == PBM_MIXED ? fine_L(g, true, false) : 0;
+    out->fine_chunk[3] = g->desc.precision == PBM_MIXED ? fine_L(g, true, true) : 0;
     PBM_CATCH
 }
 
@@ -678,15 +690,16 @@ int pbm_minres_solve(pbm_grid* g, int op, const double* b_dev, double* x_dev, do
     PBM_CATCH
 }
 
-int pbm_newton_step(pbm_grid* g, pbm_state* s, const double* f_dev, double eps_mr, pbm_newton_info* info,
-                    void* stream) {
-    pbm_newton_info inf{};
+// One Newton step of Algorithm 2 (see pbm_newton_step). With eps_stop > 0 the step is not taken
+// when res_PBM at the current state is already below eps_stop (*stepped = false). Returns the MINRES
+// status of the step (PBM_OK or PBM_ENOTCONV); throws on every other error.
+// With res_prev >= 0 the MINRES tolerance adapts before the solve (Section 5.3): if res_PBM has not
+// fallen below 0.9 res_prev, *eps_mr = max(*eps_mr / 10, eps_mr_min).
+static int newton_core(pbm_grid* g, pbm_state* s, const double* f_dev, double* eps_mr_io, double eps_stop,
+                       pbm_newton_info& inf, void* stream, bool* stepped, double res_prev = -1.0,
+                       double eps_mr_min = 0.0) {
     int rc_solve = PBM_OK;
-    PBM_TRY
-    if (!g || !f_dev) fail(PBM_EINVAL, "null argument");
-    check_state(s);
-    if (!(eps_mr > 0.0)) fail(PBM_EINVAL, "eps_mr must be > 0");
-    set_device(g);
+    *stepped = false;
     const cudaStream_t st = S(stream);
     const int64_t n = g->L[0].g.n(), m = g->L[0].g.m();
     int rc = pbm_set_state(g, s, stream);
@@ -703,6 +716,9 @@ int pbm_newton_step(pbm_grid* g, pbm_state* s, const double* f_dev, double eps_m
     const double fnorm = std::sqrt(read_slot(g, 20, st));
     const double rho_n = std::sqrt(double(m)) * (std::fabs(s->rho_lo) + std::fabs(s->rho_up));
     inf.res_pbm = norms[0] / fnorm + std::fabs(norms[1]) / s->V + norms[2] / rho_n;
+    if (eps_stop > 0.0 && inf.res_pbm < eps_stop) return PBM_OK;
+    if (res_prev >= 0.0 && inf.res_pbm > 0.9 * res_prev) *eps_mr_io = std::max(0.1 * *eps_mr_io, eps_mr_min);
+    const double eps_mr = *eps_mr_io;
     // reduced Newton system S dz = rhs (eq. (system))
     PBM_CUDA(cudaMemsetAsync(dz, 0, sizeof(double) * (n + 1), st));
     pbm_solve_info si{};
@@ -768,11 +784,134 @@ int pbm_newton_step(pbm_grid* g, pbm_state* s, const double* f_dev, double eps_m
     launch_axpy(s->nu_up_dev, dup, kappa, m, st);
     s->alpha += kappa * dalpha;
     PBM_CUDA(cudaStreamSynchronize(st));
+    *stepped = true;
+    return rc_solve;
+}
+
+int pbm_newton_step(pbm_grid* g, pbm_state* s, const double* f_dev, double eps_mr, pbm_newton_info* info,
+                    void* stream) {
+    pbm_newton_info inf{};
+    int rc_solve = PBM_OK;
+    PBM_TRY
+    if (!g || !f_dev) fail(PBM_EINVAL, "null argument");
+    check_state(s);
+    if (!(eps_mr > 0.0)) fail(PBM_EINVAL, "eps_mr must be > 0");
+    set_device(g);
+    bool stepped = false;
+    double eps_mr_v = eps_mr;
+    rc_solve = newton_core(g, s, f_dev, &eps_mr_v, -1.0, inf, stream, &stepped);
     inf.status = rc_solve;
     if (info) *info = inf;
     if (rc_solve != PBM_OK) {
         set_error("Newton step taken with an inexact solve (MINRES did not reach eps_mr)");
         return rc_solve;
+    }
+    }
+    catch (const Error& e) {
+        set_error(e.msg);
+        inf.status = e.code;
+        if (info) *info = inf;
+        return e.code;
+    }
+    set_error("");
+    return PBM_OK;
+}
+
+int pbm_default_pbm_params(pbm_pbm_params* p) {
+    if (!p) {
+        set_error("null argument");
+        return PBM_EINVAL;
+    }
+    p->eps_pbm = 1e-5;
+    p->beta = 0.3;
+    p->gamma = 0.3;
+    p->p_min = 1e-8;
+    p->eps_nwt = 1.0;
+    p->eps_nwt_min = 1e-3;
+    p->eps_mr = 0.0;
+    p->eps_mr_min = 1e-9;
+    p->max_outer = 100;
+    p->max_newton = 100;
+    set_error("");
+    return PBM_OK;
+}
+
+int pbm_solve(pbm_grid* g, pbm_state* s, const double* f_dev, const pbm_pbm_params* prm, pbm_pbm_info* info,
+              void* stream) {
+    pbm_pbm_info inf{};
+    PBM_TRY
+    if (!g || !f_dev || !prm) fail(PBM_EINVAL, "null argument");
+    check_state(s);
+    if (!(prm->beta > 0.0 && prm->beta < 1.0) || !(prm->gamma > 0.0 && prm->gamma < 1.0) || !(prm->p_min > 0.0) ||
+        !(prm->eps_pbm > 0.0) || !(prm->eps_nwt > 0.0) || !(prm->eps_nwt_min > 0.0) || prm->max_outer < 1 ||
+        prm->max_newton < 1)
+        fail(PBM_EINVAL, "invalid PBM parameters");
+    set_device(g);
+    const cudaStream_t st = S(stream);
+    const int64_t n = g->L[0].g.n(), m = g->L[0].g.m();
+    double eps_nwt = prm->eps_nwt;
+    double eps_mr = prm->eps_mr > 0.0 ? prm->eps_mr : 1e-4 * std::sqrt(double(g->L[0].g.n()));
+    eps_mr = std::min(eps_mr, 0.5);
+    double* c2 = g->aux64 + 5 * m;
+    // Newton loop of Algorithm 2 to res_PBM < eps, adapting eps_MR (Section 5.3): when a step does not
+    // reduce res_PBM below 0.9 of the previous value, eps_MR = max(eps_MR / 10, eps_mr_min)
+    auto newton_loop = [&](double eps) {
+        double res_prev = -1.0;
+        for (int it = 0; it < prm->max_newton; ++it) {
+            pbm_newton_info ni{};
+            bool stepped = false;
+            const int rc = newton_core(g, s, f_dev, &eps_mr, eps, ni, stream, &stepped, res_prev, prm->eps_mr_min);
+            (void)rc;   // an inexact solve still gives a descent step; the Newton loop goes on
+            if (!stepped) return;
+            inf.newton += 1;
+            inf.minres += ni.minres_iterations;
+            res_prev = ni.res_pbm;
+        }
+        fail(PBM_ENOTCONV, "Newton loop reached max_newton steps");
+    };
+    // duality gap (eq. gap) and dual objective at the current state
+    auto gap_ratio = [&](double& gap, double& dual) {
+        launch_mask_copy(g, s->u_dev, g->u64, st);
+        launch_elem_energy(g, g->u64, nullptr, c2, st);
+        launch_gap_sums(g, c2, s, 30, st);
+        launch_dot(g, false, f_dev, g->u64, n, 34, st);
+        PBM_CUDA(cudaMemcpyAsync(&g->sc_host->red[30], &g->sc->red[30], sizeof(double) * 5, cudaMemcpyDeviceToHost, st));
+        PBM_CUDA(cudaStreamSynchronize(st));
+        const double* R = g->sc_host->red;
+        const double fTu = R[34];
+        gap = -0.5 * fTu + s->alpha * s->V - R[30];
+        dual = s->alpha * s->V - fTu - s->rho_lo * R[31] + s->rho_up * R[32];
+        inf.compliance = 0.5 * fTu;
+        inf.volume = R[33];
+        return std::fabs(gap / dual);
+    };
+    double ratio = std::numeric_limits<double>::infinity();
+    for (int outer = 1; outer <= prm->max_outer; ++outer) {
+        inf.outer = outer;
+        newton_loop(eps_nwt);
+        double gap = 0.0, dual = 0.0;
+        ratio = gap_ratio(gap, dual);
+        inf.gap_ratio = ratio;
+        if (ratio < prm->eps_pbm) break;
+        launch_mult_update(g, c2, s, prm->beta, false, st);
+        s->p = std::max(prm->gamma * s->p, prm->p_min);
+        s->q_lo = std::max(prm->gamma * s->q_lo, prm->p_min);
+        s->q_up = std::max(prm->gamma * s->q_up, prm->p_min);
+        eps_nwt = std::max(std::min(100.0 * ratio, eps_nwt), prm->eps_nwt_min);
+    }
+    // final Newton loop at 10 eps_PBM and the final density update of Algorithm 1
+    newton_loop(10.0 * prm->eps_pbm);
+    launch_mask_copy(g, s->u_dev, g->u64, st);
+    launch_elem_energy(g, g->u64, nullptr, c2, st);
+    launch_mult_update(g, c2, s, prm->beta, true, st);
+    double gap = 0.0, dual = 0.0;
+    (void)gap_ratio(gap, dual);
+    inf.eps_mr = eps_mr;
+    inf.status = ratio < prm->eps_pbm ? PBM_OK : PBM_ENOTCONV;
+    if (info) *info = inf;
+    if (inf.status != PBM_OK) {
+        set_error("PBM reached max_outer iterations");
+        return inf.status;
     }
     }
     catch (const Error& e) {

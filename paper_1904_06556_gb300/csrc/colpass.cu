@@ -29,44 +29,6 @@ namespace pbm {
 constexpr int CB = 128;   // threads per pass-1 CTA
 constexpr int NB2 = 256;  // threads per pass-2 CTA
 
-template <class T>
-struct ColArgs {
-    int nx, ny, nz, support, L, nchunk;
-    int64_t n, m, ncol;
-    const T* x;        // gathered vector (n (+1))
-    const T* w;        // element weights (fine)
-    const T* d;        // Schur weights (fine S)
-    const T* what;     // 21 x m transformed K_e u_e (fine S, table mode), row r = 7 c + q - 1
-    const T* u;        // displacement (fine S, recompute mode)
-    const T* A;        // coarse element matrices (300 x m, upper triangle, entry-major)
-    KeHatT<T> K;
-    T* QA;
-    T* QB;
-    double* apart;     // per-CTA partial sums of -t_e (fine S)
-};
-
-template <class T>
-struct NodeArgs {
-    int nx, ny, nz, support, L;
-    int64_t n, ncol;
-    const T* QA;
-    const T* QB;
-    const T* x;
-    T* y;
-    const T* b;
-    const T* idiag;        // inverse Jacobi diagonal (JACOBI)
-    const double* omega;   // device scalar (JACOBI)
-    const T* bord;         // coarse alpha border (n) or nullptr
-    const double* s_alpha; // coarse S_alpha,alpha (device scalar)
-    int with_alpha;
-    int mode;
-    int dot_slot;
-    const double* apart;   // pass-1 partials (fine S) or nullptr
-    int napart;
-    double* partials;      // 2 * gridDim.x
-    DevScalars* sc;
-};
-
 // forward xy transform of the masked node quad (i .. i+1, j .. j+1) of plane k of vector v
 template <class T>
 __device__ __forceinline__ void load_quad(const ColArgs<T>& P, const T* __restrict__ vec, int i, int j, int k,
@@ -132,15 +94,18 @@ __device__ __forceinline__ double cta_sum1(double v, double* sh) {
 // from the plane quads of u (FP32: the recomputation costs ALU the FP32 pipe has to spare, the
 // table would cost 21 values per element of HBM traffic).
 template <class T, int MODE>
-__global__ void __launch_bounds__(CB) k_cols_fine(ColArgs<T> P) {
+__device__ __forceinline__ void cols_fine_body(const ColArgs<T>& P, unsigned blk) {
     constexpr bool S = MODE != 0;
     __shared__ double sh[CB / 32];
-    const int64_t tid = blockIdx.x * int64_t(CB) + threadIdx.x;
-    double apart = 0.0;
+    const int64_t tid = blk * int64_t(CB) + threadIdx.x;
+    T apartT = T(0);
     if (tid < P.ncol * P.nchunk) {
-        const int64_t col = tid % P.ncol;
-        const int chunk = int(tid / P.ncol);
-        const int i = int(col % P.nx), j = int(col / P.nx);
+        const unsigned ncol = unsigned(P.ncol), nxu = unsigned(P.nx);
+        const unsigned chunk_u = unsigned(tid) / ncol;
+        const unsigned colu = unsigned(tid) - chunk_u * ncol;
+        const int64_t col = colu;
+        const int chunk = int(chunk_u);
+        const int j = int(colu / nxu), i = int(colu - unsigned(j) * nxu);
         const int k0 = chunk * P.L, k1 = min(k0 + P.L, P.nz);
         const T xa = S ? P.x[P.n] : T(0);
         T Qlo[3][4], Qhi[3][4], carry[3][4];
@@ -192,7 +157,7 @@ __global__ void __launch_bounds__(CB) k_cols_fine(ColArgs<T> P) {
 #pragma unroll
                     for (int q = 1; q < 8; ++q) dot += Wt[c][q] * X[c][q];
                 const T t = __ldg(P.d + e) * (dot - xa);
-                apart -= double(t);
+                apartT -= t;
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -218,9 +183,21 @@ __global__ void __launch_bounds__(CB) k_cols_fine(ColArgs<T> P) {
         store_quad(P.QB, chunk, P.ncol, col, carry);
     }
     if (S) {
-        const double s = cta_sum1<CB>(apart, sh);
-        if (threadIdx.x == 0) P.apart[blockIdx.x] = s;
+        const double s = cta_sum1<CB>(double(apartT), sh);
+        if (threadIdx.x == 0) P.apart[blk] = s;
     }
+}
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(CB) k_cols_fine(ColArgs<T> P) {
+    cols_fine_body<T, MODE>(P, blockIdx.x);
+}
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(CB) k_cols_fine_b(const ColArgs<T>* __restrict__ A, BatchMap M) {
+    const int s = batch_system(M, blockIdx.x);
+    if (!batch_active(M, s)) return;
+    cols_fine_body<T, MODE>(A[s], blockIdx.x - M.first[s]);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -245,14 +222,16 @@ __device__ __forceinline__ void coarse_node_rows(const T* __restrict__ Ae, int64
 }
 
 template <class T>
-__global__ void __launch_bounds__(CB) k_cols_coarse(ColArgs<T> P) {
-    const int64_t tid = blockIdx.x * int64_t(CB) + threadIdx.x;
-    if (tid >= 8 * P.m) return;
-    const int a = int(tid / P.m);
-    const int64_t e = tid - a * P.m;
-    const int64_t col = e % P.ncol;
-    const int k = int(e / P.ncol);
-    const int i = int(col % P.nx), j = int(col / P.nx);
+__device__ __forceinline__ void cols_coarse_body(const ColArgs<T>& P, unsigned blk) {
+    const unsigned tid = blk * CB + threadIdx.x;
+    const unsigned mu = unsigned(P.m), ncol = unsigned(P.ncol), nxu = unsigned(P.nx);
+    if (tid >= 8 * mu) return;
+    const int a = int(tid / mu);
+    const unsigned eu = tid - unsigned(a) * mu;
+    const unsigned ku = eu / ncol, colu = eu - ku * ncol;
+    const int64_t e = eu, col = colu;
+    const int k = int(ku);
+    const int j = int(colu / nxu), i = int(colu - unsigned(j) * nxu);
     const int64_t sxn = P.nx + 1, sxy = int64_t(P.nx + 1) * (P.ny + 1);
     T xe[24];
 #pragma unroll
@@ -280,21 +259,39 @@ __global__ void __launch_bounds__(CB) k_cols_coarse(ColArgs<T> P) {
     for (int c = 0; c < 3; ++c) Q[c * P.ncol] = y[c];
 }
 
+template <class T>
+__global__ void __launch_bounds__(CB) k_cols_coarse(ColArgs<T> P) {
+    cols_coarse_body<T>(P, blockIdx.x);
+}
+
+template <class T>
+__global__ void __launch_bounds__(CB) k_cols_coarse_b(const ColArgs<T>* __restrict__ A, BatchMap M) {
+    const int s = batch_system(M, blockIdx.x);
+    if (!batch_active(M, s)) return;
+    cols_coarse_body<T>(A[s], blockIdx.x - M.first[s]);
+}
+
 // ------------------------------------------------------------------------------------------------
 // pass 2: node sums, epilogue, dots, alpha row
 // ------------------------------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(NB2) k_nodes(NodeArgs<T> P) {
+__device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, unsigned nblk) {
     __shared__ double sh[NB2 / 32];
     __shared__ bool s_last;
     const int nx = P.nx, ny = P.ny, nz = P.nz, L = P.L;
-    const int64_t nn = P.n / 3;
-    const int64_t sx = nx + 1, sxy = int64_t(nx + 1) * (ny + 1);
+    // node counts stay below 2^31 (checked at grid creation): 32-bit index arithmetic
+    const unsigned nn = unsigned(P.n / 3);
+    const unsigned sx = unsigned(nx + 1), sy = unsigned(ny + 1);
     const T xa = P.with_alpha ? P.x[P.n] : T(0);
     const double om = P.mode == EPI_JACOBI ? *P.omega : 0.0;
-    double pd = 0.0, pa = 0.0;
-    for (int64_t nd = blockIdx.x * int64_t(NB2) + threadIdx.x; nd < nn; nd += int64_t(gridDim.x) * NB2) {
-        const int I = int(nd % sx), J = int((nd / sx) % (ny + 1)), K = int(nd / sxy);
+    const T omT = T(om);
+    // per-thread partial sums in the vector type (no FP64 work per entry in the FP32 kernels), the
+    // dot product only when the launch asks for it
+    const bool want_dot = P.dot_slot >= 0;
+    T pdT = T(0), paT = T(0);
+    for (unsigned nd = blk * NB2 + threadIdx.x; nd < nn; nd += nblk * NB2) {
+        const unsigned r = nd / sx;
+        const int I = int(nd - r * sx), J = int(r % sy), K = int(r / sy);
         const bool hasA = K < nz;
         const bool hasB = K > 0 && (K % L == 0 || K == nz);
         const int64_t oa = int64_t(K) * 12 * P.ncol, ob = int64_t(K > 0 ? (K - 1) / L : 0) * 12 * P.ncol;
@@ -314,7 +311,7 @@ __global__ void __launch_bounds__(NB2) k_nodes(NodeArgs<T> P) {
                     if (hasB) s[c] += P.QB[ob + r];
                 }
             }
-        const int64_t d0 = 3 * nd;
+        const int64_t d0 = 3 * int64_t(nd);
         const bool fixed = node_fixed(P.support, nx, ny, nz, I, J, K);
         T xo[3];
 #pragma unroll
@@ -324,7 +321,7 @@ __global__ void __launch_bounds__(NB2) k_nodes(NodeArgs<T> P) {
             for (int c = 0; c < 3; ++c) {
                 const T bc = P.bord[d0 + c];
                 s[c] += bc * xa;
-                pa += double(bc) * double(xo[c]);
+                paT += bc * xo[c];
             }
         }
         if (fixed) {
@@ -337,35 +334,37 @@ __global__ void __launch_bounds__(NB2) k_nodes(NodeArgs<T> P) {
             T o;
             if (P.mode == EPI_APPLY) {
                 o = s[c];
-                pd += double(o) * double(xo[c]);
+                if (want_dot) pdT += o * xo[c];
             } else if (P.mode == EPI_RESID) {
                 o = P.b[d0 + c] - s[c];
-                pd += double(o) * double(o);
+                if (want_dot) pdT += o * o;
             } else {
                 const T bb = P.b[d0 + c];
-                o = xo[c] + T(om) * ((bb - s[c]) * P.idiag[d0 + c]);
-                pd += double(o) * double(bb);
+                o = xo[c] + omT * ((bb - s[c]) * P.idiag[d0 + c]);
+                if (want_dot) pdT += o * bb;
             }
             P.y[d0 + c] = o;
         }
     }
+    const double pd = double(pdT), pa = double(paT);
     // per-CTA partials, then the last CTA finishes the alpha entry and the dot in a fixed order
+    // (skipped when the launch needs neither: smoothing sweeps and residuals of K inside the V-cycle)
+    if (P.dot_slot < 0 && !P.with_alpha) return;
     const double bd = cta_sum1<NB2>(pd, sh);
     __syncthreads();
     const double ba = cta_sum1<NB2>(pa, sh);
-    const int nblk = gridDim.x;
     if (threadIdx.x == 0) {
-        P.partials[blockIdx.x] = bd;
-        P.partials[nblk + blockIdx.x] = ba;
+        P.partials[blk] = bd;
+        P.partials[nblk + blk] = ba;
         __threadfence();
-        s_last = atomicAdd(&P.sc->counter[0], 1u) == unsigned(nblk - 1);
+        s_last = atomicAdd(&P.sc->counter[0], 1u) == nblk - 1;
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     // every thread of the last CTA sums a fixed strided subset; the CTA sum has a fixed tree order
     double td = 0.0, ta = 0.0;
-    for (int q = threadIdx.x; q < nblk; q += NB2) {
+    for (int q = threadIdx.x; q < int(nblk); q += NB2) {
         td += ((volatile double*)P.partials)[q];
         ta += ((volatile double*)P.partials)[nblk + q];
     }
@@ -397,6 +396,18 @@ __global__ void __launch_bounds__(NB2) k_nodes(NodeArgs<T> P) {
     if (P.dot_slot >= 0) P.sc->red[P.dot_slot] = sd;
 }
 
+template <class T>
+__global__ void __launch_bounds__(NB2) k_nodes(NodeArgs<T> P) {
+    nodes_body<T>(P, blockIdx.x, gridDim.x);
+}
+
+template <class T>
+__global__ void __launch_bounds__(NB2) k_nodes_b(const NodeArgs<T>* __restrict__ A, BatchMap M) {
+    const int s = batch_system(M, blockIdx.x);
+    if (!batch_active(M, s)) return;
+    nodes_body<T>(A[s], blockIdx.x - M.first[s], M.first[s + 1] - M.first[s]);
+}
+
 // ------------------------------------------------------------------------------------------------
 // launch wrappers
 // ------------------------------------------------------------------------------------------------
@@ -411,8 +422,8 @@ static int fine_chunk(const Geom& G) {
 }
 
 template <class T>
-static void node_pass(const ColEnv& env, const Geom& G, const ApplyArgs& a, int L, const T* bord,
-                      const double* s_alpha, const double* apart, int napart, int64_t off, cudaStream_t st) {
+NodeArgs<T> make_node_args(const ColEnv& env, const Geom& G, const ApplyArgs& a, int L, const T* bord,
+                           const double* s_alpha, const double* apart, int napart, int64_t off, int* blocks_out) {
     NodeArgs<T> N{};
     N.nx = G.nx;
     N.ny = G.ny;
@@ -440,6 +451,15 @@ static void node_pass(const ColEnv& env, const Geom& G, const ApplyArgs& a, int 
     const int64_t nn = G.nnode();
     const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nn + NB2 - 1) / NB2, 152 * 8)));
     if (off + 2 * blocks > env.partials_len) fail(PBM_EINVAL, "grid too large for the partials buffer");
+    *blocks_out = blocks;
+    return N;
+}
+
+template <class T>
+static void node_pass(const ColEnv& env, const Geom& G, const ApplyArgs& a, int L, const T* bord,
+                      const double* s_alpha, const double* apart, int napart, int64_t off, cudaStream_t st) {
+    int blocks = 0;
+    NodeArgs<T> N = make_node_args<T>(env, G, a, L, bord, s_alpha, apart, napart, off, &blocks);
     k_nodes<T><<<blocks, NB2, 0, st>>>(N);
     PBM_LAUNCH("node pass");
 }
@@ -461,13 +481,13 @@ static void fill_khat_t(KeHatT<T>& out, const KeHat& K) {
 // scaling by the weight 21, carry 12 (L - 1) / L; S adds the dot W.X 21, t_e 2 and the axpy t W 21,
 // and, when W_e is recomputed from u, the transforms and Khat of u.
 // Per node: 12 quad sums plus the epilogue (apply 3, residual 6, Jacobi 12).
-void cols_cost(const Geom& G, bool op_s, bool recompute_w, int mode, int esize, double& bytes, double& flops) {
+void cols_cost(const Geom& G, int Lc, bool op_s, bool recompute_w, int mode, int esize, double& bytes, double& flops) {
     const double n = double(G.n()), m = double(G.m()), nn = double(G.nnode());
     double vec = 2.0 * n + (op_s ? n : 0.0), elem = m * (op_s ? 2.0 : 1.0);
     if (mode == EPI_RESID) vec += n;
     if (mode == EPI_JACOBI) vec += 2.0 * n;
     bytes = double(esize) * (vec + elem);
-    const double L = double(fine_chunk(G));
+    const double L = double(Lc > 0 ? Lc : fine_chunk(G));
     double per_elem = 2.0 * 24.0 * (L + 1.0) / L + 48.0 + 45.0 + 21.0 + 12.0 * (L - 1.0) / L;
     if (op_s) per_elem += 44.0;
     if (op_s && recompute_w) per_elem += 24.0 * (L + 1.0) / L + 24.0 + 45.0;   // quads, z part and Khat of u
@@ -476,19 +496,19 @@ void cols_cost(const Geom& G, bool op_s, bool recompute_w, int mode, int esize, 
 }
 
 template <class T>
-void cols_fine_env(const ColEnv& env, const Geom& G, const KeHat& kh, const T* w, const T* d, const T* what,
-                   const T* u, const ApplyArgs& a, cudaStream_t st) {
+ColArgs<T> make_fine_args(const ColEnv& env, const Geom& G, const KeHat& kh, const T* w, const T* d, const T* what,
+                          const T* u, const void* x, int* blocks_out) {
     ColArgs<T> P{};
     P.nx = G.nx;
     P.ny = G.ny;
     P.nz = G.nz;
     P.support = G.support;
-    P.L = fine_chunk(G);
+    P.L = env.L > 0 ? env.L : fine_chunk(G);
     P.nchunk = (G.nz + P.L - 1) / P.L;
     P.n = G.n();
     P.m = G.m();
     P.ncol = int64_t(G.nx) * G.ny;
-    P.x = (const T*)a.x;
+    P.x = (const T*)x;
     P.w = w;
     P.d = d;
     P.what = what;
@@ -499,8 +519,17 @@ void cols_fine_env(const ColEnv& env, const Geom& G, const KeHat& kh, const T* w
     P.apart = env.partials;
     const int64_t threads = P.ncol * P.nchunk;
     const int blocks = int((threads + CB - 1) / CB);
+    if (d && blocks > env.partials_len / 2) fail(PBM_EINVAL, "grid too large for the partials buffer");
+    *blocks_out = blocks;
+    return P;
+}
+
+template <class T>
+void cols_fine_env(const ColEnv& env, const Geom& G, const KeHat& kh, const T* w, const T* d, const T* what,
+                   const T* u, const ApplyArgs& a, cudaStream_t st) {
+    int blocks = 0;
+    const ColArgs<T> P = make_fine_args<T>(env, G, kh, w, d, what, u, a.x, &blocks);
     const bool s = d != nullptr;
-    if (s && blocks > env.partials_len / 2) fail(PBM_EINVAL, "grid too large for the partials buffer");
     if (s && what) k_cols_fine<T, 1><<<blocks, CB, 0, st>>>(P);
     else if (s) k_cols_fine<T, 2><<<blocks, CB, 0, st>>>(P);
     else k_cols_fine<T, 0><<<blocks, CB, 0, st>>>(P);
@@ -515,7 +544,7 @@ int64_t cols_scratch_entries(const Geom& G) {
     return 12 * ncol * (G.nz + 1) + 12 * ncol * ((G.nz + L - 1) / L);
 }
 
-static ColEnv env_of(pbm_grid* g) {
+ColEnv env_of(pbm_grid* g) {
     ColEnv e;
     e.qa = g->qa;
     e.qb = g->qb;
@@ -525,15 +554,83 @@ static ColEnv env_of(pbm_grid* g) {
     return e;
 }
 
-template <class T>
-void cols_fine(pbm_grid* g, const T* w, const T* d, const T* what, const T* u, const ApplyArgs& a, cudaStream_t st) {
-    cols_fine_env<T>(env_of(g), g->L[0].g, g->kehat, w, d, what, u, a, st);
+int fine_L(const pbm_grid* g, bool fp32, bool op_s) {
+    const int L = g->fineL[fp32 ? 1 : 0][op_s ? 1 : 0];
+    return L > 0 ? L : fine_chunk(g->L[0].g);
 }
 
 template <class T>
-void cols_coarse(pbm_grid* g, int k, const T* A, const T* bord, const ApplyArgs& a, cudaStream_t st) {
-    const Geom& G = g->L[k].g;
-    const ColEnv env = env_of(g);
+void cols_fine(pbm_grid* g, const T* w, const T* d, const T* what, const T* u, const ApplyArgs& a, cudaStream_t st) {
+    ColEnv env = env_of(g);
+    env.L = fine_L(g, sizeof(T) == 4, d != nullptr);
+    cols_fine_env<T>(env, g->L[0].g, g->kehat, w, d, what, u, a, st);
+}
+
+// Autotuner of the fine column pass: L trades the balance of columns over the SM sub-partitions
+// (short chunks, more threads) against the plane transforms shared inside a chunk (long chunks).
+// Each candidate is timed with CUDA events on zeroed inputs (the kernels' cost does not depend on
+// the values) and the fastest is kept per (precision, operator).
+void autotune_fine(pbm_grid* g) {
+    const Geom& G = g->L[0].g;
+    const int64_t n = G.n(), m = G.m();
+    const bool mixed = g->desc.precision == PBM_MIXED;
+    PBM_CUDA(cudaMemset(g->kv64[0], 0, sizeof(double) * (n + 1)));
+    PBM_CUDA(cudaMemset(g->w64, 0, sizeof(double) * m));
+    PBM_CUDA(cudaMemset(g->d64, 0, sizeof(double) * m));
+    PBM_CUDA(cudaMemset(g->what_hat, 0, sizeof(double) * 21 * m));
+    if (mixed) {
+        PBM_CUDA(cudaMemset(g->kv32[0], 0, sizeof(float) * (n + 1)));
+        PBM_CUDA(cudaMemset(g->w32, 0, sizeof(float) * m));
+        PBM_CUDA(cudaMemset(g->d32, 0, sizeof(float) * m));
+        PBM_CUDA(cudaMemset(g->u32, 0, sizeof(float) * (n + 1)));
+    }
+    cudaEvent_t e0, e1;
+    PBM_CUDA(cudaEventCreate(&e0));
+    PBM_CUDA(cudaEventCreate(&e1));
+    try {
+        for (int p = 0; p < (mixed ? 2 : 1); ++p)
+            for (int op = 0; op < 2; ++op) {
+                ApplyArgs a{};
+                a.x = p ? (const void*)g->kv32[0] : (const void*)g->kv64[0];
+                a.y = p ? (void*)g->kv32[1] : (void*)g->kv64[1];
+                a.mode = EPI_APPLY;
+                a.with_alpha = op == 1;
+                a.dot_slot = -1;
+                float best = 3.4e38f;
+                int bestL = 0;
+                for (int L = 1; L <= 8; L *= 2) {
+                    if (L > 1 && L > G.nz) break;
+                    g->fineL[p][op] = L;
+                    for (int rep = 0; rep < 4; ++rep) {
+                        if (rep == 1) PBM_CUDA(cudaEventRecord(e0, 0));
+                        if (p)
+                            cols_fine<float>(g, g->w32, op ? g->d32 : nullptr, nullptr, op ? g->u32 : nullptr, a, 0);
+                        else
+                            cols_fine<double>(g, g->w64, op ? g->d64 : nullptr, op ? g->what_hat : nullptr, nullptr, a,
+                                              0);
+                    }
+                    PBM_CUDA(cudaEventRecord(e1, 0));
+                    PBM_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.0f;
+                    PBM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (ms < best) {
+                        best = ms;
+                        bestL = L;
+                    }
+                }
+                g->fineL[p][op] = bestL;
+            }
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
+
+template <class T>
+ColArgs<T> make_coarse_args(const ColEnv& env, const Geom& G, const T* A, const void* x, int* blocks_out) {
     ColArgs<T> P{};
     P.nx = G.nx;
     P.ny = G.ny;
@@ -544,15 +641,55 @@ void cols_coarse(pbm_grid* g, int k, const T* A, const T* bord, const ApplyArgs&
     P.n = G.n();
     P.m = G.m();
     P.ncol = int64_t(G.nx) * G.ny;
-    P.x = (const T*)a.x;
+    P.x = (const T*)x;
     P.A = A;
     P.QA = (T*)env.qa;
     P.QB = (T*)env.qb;
-    const int blocks = int((8 * P.m + CB - 1) / CB);
+    *blocks_out = int((8 * P.m + CB - 1) / CB);
+    return P;
+}
+
+template <class T>
+void cols_coarse(pbm_grid* g, int k, const T* A, const T* bord, const ApplyArgs& a, cudaStream_t st) {
+    const Geom& G = g->L[k].g;
+    const ColEnv env = env_of(g);
+    int blocks = 0;
+    const ColArgs<T> P = make_coarse_args<T>(env, G, A, a.x, &blocks);
     k_cols_coarse<T><<<blocks, CB, 0, st>>>(P);
     PBM_LAUNCH("coarse column pass");
     node_pass<T>(env, G, a, 1, bord, &g->sc->salpha, nullptr, 0, 0, st);
 }
+
+// ---- batched launches (one launch over the systems of a batch) ----
+template <class T>
+void launch_cols_fine_b(const ColArgs<T>* dA, const BatchMap& M, int mode, int total_blocks, cudaStream_t st) {
+    if (mode == 1) k_cols_fine_b<T, 1><<<total_blocks, CB, 0, st>>>(dA, M);
+    else if (mode == 2) k_cols_fine_b<T, 2><<<total_blocks, CB, 0, st>>>(dA, M);
+    else k_cols_fine_b<T, 0><<<total_blocks, CB, 0, st>>>(dA, M);
+    PBM_LAUNCH("batched fine column pass");
+}
+template <class T>
+void launch_cols_coarse_b(const ColArgs<T>* dA, const BatchMap& M, int total_blocks, cudaStream_t st) {
+    k_cols_coarse_b<T><<<total_blocks, CB, 0, st>>>(dA, M);
+    PBM_LAUNCH("batched coarse column pass");
+}
+template <class T>
+void launch_nodes_b(const NodeArgs<T>* dA, const BatchMap& M, int total_blocks, cudaStream_t st) {
+    k_nodes_b<T><<<total_blocks, NB2, 0, st>>>(dA, M);
+    PBM_LAUNCH("batched node pass");
+}
+#define PBM_INST_BATCH(T)                                                                                         \
+    template void launch_cols_fine_b<T>(const ColArgs<T>*, const BatchMap&, int, int, cudaStream_t);           \
+    template void launch_cols_coarse_b<T>(const ColArgs<T>*, const BatchMap&, int, cudaStream_t);              \
+    template void launch_nodes_b<T>(const NodeArgs<T>*, const BatchMap&, int, cudaStream_t);                   \
+    template ColArgs<T> make_fine_args<T>(const ColEnv&, const Geom&, const KeHat&, const T*, const T*, const T*, \
+                                          const T*, const void*, int*);                                         \
+    template ColArgs<T> make_coarse_args<T>(const ColEnv&, const Geom&, const T*, const void*, int*);          \
+    template NodeArgs<T> make_node_args<T>(const ColEnv&, const Geom&, const ApplyArgs&, int, const T*,         \
+                                           const double*, const double*, int, int64_t, int*);
+PBM_INST_BATCH(double)
+PBM_INST_BATCH(float)
+#undef PBM_INST_BATCH
 
 template void cols_fine<double>(pbm_grid*, const double*, const double*, const double*, const double*,
                                 const ApplyArgs&, cudaStream_t);

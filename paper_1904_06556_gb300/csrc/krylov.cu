@@ -70,11 +70,17 @@ void vec_zero(void* p, size_t bytes, cudaStream_t st) { PBM_CUDA(cudaMemsetAsync
 
 // x = omega D^{-1} b (idiag = D^{-1})
 template <class T>
+__device__ __forceinline__ void first_jacobi_body(const T* __restrict__ b, const T* __restrict__ idiag,
+                                                  const double* __restrict__ om, T* __restrict__ x, int64_t n,
+                                                  unsigned blk, unsigned nblk) {
+    const T w = T(*om);
+    for (int64_t i = blk * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(nblk) * blockDim.x)
+        x[i] = w * (b[i] * idiag[i]);
+}
+template <class T>
 __global__ void k_first_jacobi(const T* __restrict__ b, const T* __restrict__ idiag, const double* __restrict__ om,
                                T* __restrict__ x, int64_t n) {
-    const T w = T(*om);
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-        x[i] = w * (b[i] * idiag[i]);
+    first_jacobi_body<T>(b, idiag, om, x, n, blockIdx.x, gridDim.x);
 }
 
 __global__ void k_inverse(const double* __restrict__ x, double* __restrict__ y, int64_t n, int sq) {
@@ -104,11 +110,11 @@ template <class T>
 __global__ void k_dot(const T* __restrict__ a, const T* __restrict__ b, int64_t n, double* partials, unsigned* counter,
                       double* out) {
     __shared__ double sh[32];
-    double s = 0.0;
+    T st = T(0);   // per-thread sum in the vector type, CTA and grid sums in FP64
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-        s += double(a[i]) * double(b[i]);
+        st += a[i] * b[i];
     double tot;
-    if (finish_sum(s, partials, counter, &tot, sh)) *out = tot;
+    if (finish_sum(double(st), partials, counter, &tot, sh)) *out = tot;
 }
 
 void launch_dot(pbm_grid* g, bool fp32, const void* a, const void* b, int64_t n, int slot, cudaStream_t st) {
@@ -140,8 +146,9 @@ double read_slot(pbm_grid* g, int slot, cudaStream_t st) {
 // in place; the update shifts the directions and z. Buffer roles never change between
 // iterations, so every iteration is the same sequence of launches.
 template <class T>
-__global__ void k_mr_lanczos2(const T* __restrict__ Az, T* __restrict__ v0, T* __restrict__ v1, int64_t n,
-                              double* mr, const double* red) {
+__device__ __forceinline__ void mr_lanczos2_body(const T* __restrict__ Az, T* __restrict__ v0, T* __restrict__ v1,
+                                                 int64_t n, double* mr, const double* red, unsigned blk,
+                                                 unsigned nblk) {
     __shared__ double cs[4];
     if (threadIdx.x == 0) {
         const double beta = mr[1], bprev = mr[0];
@@ -153,34 +160,45 @@ __global__ void k_mr_lanczos2(const T* __restrict__ Az, T* __restrict__ v0, T* _
         cs[3] = a;
     }
     __syncthreads();
-    const double c1 = cs[0], c2 = cs[1], c3 = cs[2];
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const T c1 = T(cs[0]), c2 = T(cs[1]), c3 = T(cs[2]);   // vector arithmetic in the vector type
+    for (int64_t i = blk * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(nblk) * blockDim.x) {
         const T vc = v1[i];
-        v1[i] = T(c1 * double(Az[i]) - c2 * double(vc) - c3 * double(v0[i]));
+        v1[i] = c1 * Az[i] - c2 * vc - c3 * v0[i];
         v0[i] = vc;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) mr[8] = cs[3];
+    if (blk == 0 && threadIdx.x == 0) mr[8] = cs[3];
+}
+template <class T>
+__global__ void k_mr_lanczos2(const T* __restrict__ Az, T* __restrict__ v0, T* __restrict__ v1, int64_t n,
+                              double* mr, const double* red) {
+    mr_lanczos2_body<T>(Az, v0, v1, n, mr, red, blockIdx.x, gridDim.x);
 }
 
 template <class T>
-__global__ void k_mr_update2(T* __restrict__ zc, const T* __restrict__ zn, T* __restrict__ d1, T* __restrict__ d2,
-                             T* __restrict__ x, int64_t n, const double* mr) {
+__device__ __forceinline__ void mr_update2_body(T* __restrict__ zc, const T* __restrict__ zn, T* __restrict__ d1,
+                                                T* __restrict__ d2, T* __restrict__ x, int64_t n, const double* mr,
+                                                unsigned blk, unsigned nblk) {
     __shared__ double cs[2];
     if (threadIdx.x == 0) {
         cs[0] = 1.0 / mr[0];
         cs[1] = 1.0 / mr[12];
     }
     __syncthreads();
-    const double e = mr[10], f = mr[11], step = mr[9];
-    const double ib = cs[0], ir = cs[1];
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        const double dp = double(d1[i]);
-        const double dn = (double(zc[i]) * ib - e * double(d2[i]) - f * dp) * ir;
-        d2[i] = T(dp);
-        d1[i] = T(dn);
-        x[i] = T(double(x[i]) + step * dn);
+    const T e = T(mr[10]), f = T(mr[11]), step = T(mr[9]);
+    const T ib = T(cs[0]), ir = T(cs[1]);
+    for (int64_t i = blk * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(nblk) * blockDim.x) {
+        const T dp = d1[i];
+        const T dn = (zc[i] * ib - e * d2[i] - f * dp) * ir;
+        d2[i] = dp;
+        d1[i] = dn;
+        x[i] = x[i] + step * dn;
         zc[i] = zn[i];
     }
+}
+template <class T>
+__global__ void k_mr_update2(T* __restrict__ zc, const T* __restrict__ zn, T* __restrict__ d1, T* __restrict__ d2,
+                             T* __restrict__ x, int64_t n, const double* mr) {
+    mr_update2_body<T>(zc, zn, d1, d2, x, n, mr, blockIdx.x, gridDim.x);
 }
 
 // dst = (double) src, red = dst . other (FP32 preconditioner output into FP64 MINRES vectors)
@@ -220,7 +238,7 @@ void cast_dot(pbm_grid* g, const float* src, double* dst, const double* other, i
     PBM_LAUNCH("cast dot");
 }
 
-__global__ void k_mr_scalars(double* mr, const double* red) {
+__device__ void mr_scalars_body(double* mr, const double* red) {
     const double vz = red[1];
     if (!(vz >= 0.0)) {
         mr[13] = 1.0;
@@ -260,7 +278,9 @@ __global__ void k_mr_scalars(double* mr, const double* red) {
     mr[5] = sn;
 }
 
-__global__ void k_mr_init(double* mr, const double* red) {
+__global__ void k_mr_scalars(double* mr, const double* red) { mr_scalars_body(mr, red); }
+
+__device__ void mr_init_body(double* mr, const double* red) {
     const double vz = red[1];
     for (int i = 0; i < 16; ++i) mr[i] = 0.0;
     mr[2] = 1.0;
@@ -273,6 +293,50 @@ __global__ void k_mr_init(double* mr, const double* red) {
     mr[1] = b;
     mr[6] = b;
     mr[7] = b;
+}
+__global__ void k_mr_init(double* mr, const double* red) { mr_init_body(mr, red); }
+
+// ---- batched vector and scalar stages of MINRES (one launch over the systems of a batch) ----
+template <class T>
+__global__ void k_vec_b(const VecArgs<T>* __restrict__ A, BatchMap M) {
+    const int s = batch_system(M, blockIdx.x);
+    if (!batch_active(M, s)) return;
+    const VecArgs<T>& P = A[s];
+    const unsigned blk = blockIdx.x - M.first[s], nblk = M.first[s + 1] - M.first[s];
+    switch (P.op) {
+        case VOP_FIRST_JACOBI: first_jacobi_body<T>(P.a, P.f, P.om, P.b, P.n, blk, nblk); break;
+        case VOP_LANCZOS2: mr_lanczos2_body<T>(P.a, P.b, P.c, P.n, P.mr, P.red, blk, nblk); break;
+        case VOP_UPDATE2: mr_update2_body<T>(P.b, P.a, P.c, P.d, P.e, P.n, P.mr, blk, nblk); break;
+        case VOP_ZERO:
+            for (int64_t i = blk * int64_t(blockDim.x) + threadIdx.x; i < P.n; i += int64_t(nblk) * blockDim.x)
+                P.b[i] = T(0);
+            break;
+        default:  // VOP_COPY
+            for (int64_t i = blk * int64_t(blockDim.x) + threadIdx.x; i < P.n; i += int64_t(nblk) * blockDim.x)
+                P.b[i] = P.a[i];
+            break;
+    }
+}
+template <class T>
+void launch_vec_b(const VecArgs<T>* dA, const BatchMap& M, int total_blocks, cudaStream_t st) {
+    k_vec_b<T><<<total_blocks, VB, 0, st>>>(dA, M);
+    PBM_LAUNCH("batched vector stage");
+}
+template void launch_vec_b<double>(const VecArgs<double>*, const BatchMap&, int, cudaStream_t);
+template void launch_vec_b<float>(const VecArgs<float>*, const BatchMap&, int, cudaStream_t);
+
+// one thread per system: SOP_INIT (MINRES start from red[1] = v . M^-1 v), SOP_SCALARS (Givens step)
+__global__ void k_scal_b(DevScalars* const* __restrict__ sc, int nsys, int op) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    DevScalars* S = sc[s];
+    if (S->flags[1] == 0) return;
+    if (op == SOP_INIT) mr_init_body(S->mr, S->red);
+    else mr_scalars_body(S->mr, S->red);
+}
+void launch_scal_b(DevScalars* const* d_sc, int nsys, int op, cudaStream_t st) {
+    k_scal_b<<<(nsys + 63) / 64, 64, 0, st>>>(d_sc, nsys, op);
+    PBM_LAUNCH("batched scalar stage");
 }
 
 void mr_scalars(pbm_grid* g, cudaStream_t st) {
@@ -306,27 +370,15 @@ __global__ void k_lz_start(double* __restrict__ v, double* __restrict__ t, doubl
         t[i] = v0 * sdiag[i];
     }
 }
-// w = s w (in place), a_j = w . v
-__global__ void k_lz_a(double* __restrict__ w, const double* __restrict__ v, const double* __restrict__ sdiag,
-                       int64_t n, double* partials, unsigned* counter, double* aj) {
-    __shared__ double sh[32];
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        const double wi = w[i] * sdiag[i];
-        w[i] = wi;
-        s += wi * v[i];
-    }
-    double tot;
-    if (finish_sum(s, partials, counter, &tot, sh)) *aj = tot;
-}
-// w -= a_j v + b_{j-1} vprev; b_j = ||w||
-__global__ void k_lz_b(double* __restrict__ w, const double* __restrict__ v, const double* __restrict__ vprev, int64_t n,
-                       const double* aj, const double* bjm1, double* partials, unsigned* counter, double* bj) {
+// w = s y - a_j v - b_{j-1} vprev (y = A s v, a_j = y . s v from the operator's fused dot); b_j = ||w||
+__global__ void k_lz_b(double* __restrict__ w, const double* __restrict__ v, const double* __restrict__ vprev,
+                       const double* __restrict__ sdiag, int64_t n, const double* aj, const double* bjm1,
+                       double* partials, unsigned* counter, double* bj) {
     __shared__ double sh[32];
     const double a = *aj, b = bjm1 ? *bjm1 : 0.0;
     double s = 0.0;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        const double wi = w[i] - a * v[i] - b * vprev[i];
+        const double wi = sdiag[i] * w[i] - a * v[i] - b * vprev[i];
         w[i] = wi;
         s += wi * wi;
     }
@@ -355,13 +407,10 @@ void lz_start(pbm_grid* g, double* v, double* t, double* vprev, const double* di
     k_lz_start<<<VG, VB, 0, st>>>(v, t, vprev, diag, n);
     PBM_LAUNCH("lz start");
 }
-void lz_a(pbm_grid* g, double* w, const double* v, const double* diag, int64_t n, int j, cudaStream_t st) {
-    k_lz_a<<<VG, VB, 0, st>>>(w, v, diag, n, g->partials, &g->sc->counter[2], &g->sc->lz_a[j]);
-    PBM_LAUNCH("lz a");
-}
-void lz_b(pbm_grid* g, double* w, const double* v, const double* vprev, int64_t n, int j, cudaStream_t st) {
-    k_lz_b<<<VG, VB, 0, st>>>(w, v, vprev, n, &g->sc->lz_a[j], j > 0 ? &g->sc->lz_b[j - 1] : nullptr, g->partials,
-                              &g->sc->counter[2], &g->sc->lz_b[j]);
+void lz_b(pbm_grid* g, double* w, const double* v, const double* vprev, const double* sdiag, int64_t n, int j,
+          cudaStream_t st) {
+    k_lz_b<<<VG, VB, 0, st>>>(w, v, vprev, sdiag, n, &g->sc->lz_a[j], j > 0 ? &g->sc->lz_b[j - 1] : nullptr,
+                              g->partials, &g->sc->counter[2], &g->sc->lz_b[j]);
     PBM_LAUNCH("lz b");
 }
 void lz_next(pbm_grid* g, const double* w, double* v, double* vprev, double* t, const double* diag, int64_t n, int j,

@@ -34,19 +34,30 @@ __host__ __device__ inline double pc_weight(int c, int a, int A) {
 // restriction b_c = P^T r_f (+ alpha copy), times `scale`. One thread per (coarse node, component);
 // the 27 weights 1/2^(number of odd offsets) are compile-time constants of the unrolled loops.
 // ------------------------------------------------------------------------------------------------
+// With xfirst given, the same pass also writes the coarse level's first damped-Jacobi sweep from
+// zero, xfirst = omega D^{-1} b_c (idiag = D^{-1} of the coarse level, omega its device weight).
+
 template <class T>
-__global__ void k_restrict(int nxf, int nyf, int nzf, int support, const T* __restrict__ rf, T* __restrict__ bc,
-                           int with_alpha, double scale) {
+__device__ __forceinline__ void restrict_body(const RestrictArgs<T>& P, unsigned blk, unsigned nblk) {
+    const int nxf = P.nxf, nyf = P.nyf, nzf = P.nzf, support = P.support, with_alpha = P.with_alpha;
+    const T* __restrict__ rf = P.rf;
+    T* __restrict__ bc = P.bc;
+    T* __restrict__ xfirst = P.xfirst;
+    const T* __restrict__ idiag = P.idiag;
+    const double scale = P.scale;
+    const double* om = P.om;
     const int nxc = nxf / 2, nyc = nyf / 2, nzc = nzf / 2;
-    const int64_t nnc = int64_t(nxc + 1) * (nyc + 1) * (nzc + 1);
+    const unsigned nnc = unsigned(nxc + 1) * unsigned(nyc + 1) * unsigned(nzc + 1);
     const int64_t sxf = nxf + 1, sxyf = int64_t(nxf + 1) * (nyf + 1);
-    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < 3 * nnc; t += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t cn = t / 3;
-        const int c = int(t - 3 * cn);
-        const int I = int(cn % (nxc + 1));
-        const int J = int((cn / (nxc + 1)) % (nyc + 1));
-        const int K = int(cn / (int64_t(nxc + 1) * (nyc + 1)));
-        double acc = 0.0;
+    const double w_first = xfirst ? *om : 0.0;
+    for (unsigned t = blk * blockDim.x + threadIdx.x; t < 3 * nnc; t += nblk * blockDim.x) {
+        const unsigned cn = t / 3u;
+        const int c = int(t - 3u * cn);
+        const unsigned r = cn / unsigned(nxc + 1);
+        const int I = int(cn - r * unsigned(nxc + 1));
+        const int J = int(r % unsigned(nyc + 1));
+        const int K = int(r / unsigned(nyc + 1));
+        T acc = T(0);   // accumulated in the vector type (no FP64 work per entry for FP32)
         if (!node_fixed(support, nxc, nyc, nzc, I, J, K)) {
 #pragma unroll
             for (int dz = -1; dz <= 1; ++dz) {
@@ -59,33 +70,52 @@ __global__ void k_restrict(int nxf, int nyf, int nzf, int support, const T* __re
                         const int if_ = 2 * I + dx;
                         if (if_ < 0 || if_ > nxf || jf < 0 || jf > nyf || kf < 0 || kf > nzf) continue;
                         if (node_fixed(support, nxf, nyf, nzf, if_, jf, kf)) continue;
-                        constexpr double half = 0.5;
-                        const double w = (dx ? half : 1.0) * (dy ? half : 1.0) * (dz ? half : 1.0);
-                        acc += w * double(rf[3 * (if_ + sxf * jf + sxyf * kf) + c]);
+                        const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
+                        acc += w * rf[3 * (if_ + sxf * jf + sxyf * kf) + c];
                     }
                 }
             }
         }
-        bc[t] = T(scale * acc);
+        const T bv = T(scale) * acc;
+        bc[t] = bv;
+        if (xfirst) xfirst[t] = T(w_first) * (bv * idiag[t]);
     }
-    if (with_alpha && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (with_alpha && blk == 0 && threadIdx.x == 0) {
         const int64_t nf = 3 * int64_t(nxf + 1) * (nyf + 1) * (nzf + 1);
-        bc[3 * nnc] = T(scale * double(rf[nf]));
+        const T bv = T(scale * double(rf[nf]));
+        bc[3 * int64_t(nnc)] = bv;
+        if (xfirst) xfirst[3 * int64_t(nnc)] = T(w_first) * (bv * idiag[3 * int64_t(nnc)]);
     }
 }
 
+template <class T>
+__global__ void k_restrict(RestrictArgs<T> P) {
+    restrict_body<T>(P, blockIdx.x, gridDim.x);
+}
+template <class T>
+__global__ void k_restrict_b(const RestrictArgs<T>* __restrict__ A, BatchMap M) {
+    const int s = batch_system(M, blockIdx.x);
+    if (!batch_active(M, s)) return;
+    restrict_body<T>(A[s], blockIdx.x - M.first[s], M.first[s + 1] - M.first[s]);
+}
+
 void launch_restrict(pbm_grid* g, int k, bool fp32, const void* rf, void* bc, bool with_alpha, double scale,
-                     cudaStream_t st) {
+                     cudaStream_t st, void* xfirst) {
     // k: the fine level of the pair (k -> k+1)
     const Geom& F = g->L[k].g;
-    const int64_t nt = 3 * g->L[k + 1].g.nnode();
+    Level& C = g->L[k + 1];
+    const int64_t nt = 3 * C.g.nnode();
     const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nt + 127) / 128, 152 * 16)));
+    const double* om = &g->sc->mr[16 + k + 1];
     if (fp32)
-        k_restrict<float><<<blocks, 128, 0, st>>>(F.nx, F.ny, F.nz, F.support, (const float*)rf, (float*)bc,
-                                                  with_alpha, scale);
+        k_restrict<float><<<blocks, 128, 0, st>>>(RestrictArgs<float>{F.nx, F.ny, F.nz, F.support, with_alpha ? 1 : 0,
+                                                                      (const float*)rf, (float*)bc, scale,
+                                                                      (float*)xfirst, C.idiag32, om});
     else
-        k_restrict<double><<<blocks, 128, 0, st>>>(F.nx, F.ny, F.nz, F.support, (const double*)rf, (double*)bc,
-                                                   with_alpha, scale);
+        k_restrict<double><<<blocks, 128, 0, st>>>(RestrictArgs<double>{F.nx, F.ny, F.nz, F.support,
+                                                                        with_alpha ? 1 : 0, (const double*)rf,
+                                                                        (double*)bc, scale, (double*)xfirst,
+                                                                        C.idiag64, om});
     PBM_LAUNCH("restrict");
 }
 
@@ -93,35 +123,50 @@ void launch_restrict(pbm_grid* g, int k, bool fp32, const void* rf, void* bc, bo
 // prolongation x_f += P x_c (+ alpha). One thread per (fine node, component): the up to 8 coarse
 // parents share the weight 1/2^(number of odd fine coordinates), built from its exponent bits.
 // ------------------------------------------------------------------------------------------------
+
 template <class T>
-__global__ void k_prolong_add(int nxf, int nyf, int nzf, int support, const T* __restrict__ xc, T* __restrict__ xf,
-                              int with_alpha) {
+__device__ __forceinline__ void prolong_body(const ProlongArgs<T>& P, unsigned blk, unsigned nblk) {
+    const int nxf = P.nxf, nyf = P.nyf, nzf = P.nzf, support = P.support, with_alpha = P.with_alpha;
+    const T* __restrict__ xc = P.xc;
+    T* __restrict__ xf = P.xf;
     const int nxc = nxf / 2, nyc = nyf / 2, nzc = nzf / 2;
     const int64_t nnf = int64_t(nxf + 1) * (nyf + 1) * (nzf + 1);
     const int64_t sxc = nxc + 1, sxyc = int64_t(nxc + 1) * (nyc + 1);
-    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < 3 * nnf; t += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t fn = t / 3;
-        const int c = int(t - 3 * fn);
-        const int I = int(fn % (nxf + 1));
-        const int J = int((fn / (nxf + 1)) % (nyf + 1));
-        const int K = int(fn / (int64_t(nxf + 1) * (nyf + 1)));
+    for (unsigned t = blk * blockDim.x + threadIdx.x; t < 3u * unsigned(nnf); t += nblk * blockDim.x) {
+        const unsigned fn = t / 3u;
+        const int c = int(t - 3u * fn);
+        const unsigned r = fn / unsigned(nxf + 1);
+        const int I = int(fn - r * unsigned(nxf + 1));
+        const int J = int(r % unsigned(nyf + 1));
+        const int K = int(r / unsigned(nyf + 1));
         if (node_fixed(support, nxf, nyf, nzf, I, J, K)) continue;
         const int i0 = I >> 1, i1 = (I + 1) >> 1, j0 = J >> 1, j1 = (J + 1) >> 1, k0 = K >> 1, k1 = (K + 1) >> 1;
-        double acc = 0.0;
+        T acc = T(0);
         for (int kc = k0; kc <= k1; ++kc)
             for (int jc = j0; jc <= j1; ++jc)
                 for (int ic = i0; ic <= i1; ++ic) {
                     if (node_fixed(support, nxc, nyc, nzc, ic, jc, kc)) continue;
-                    acc += double(xc[3 * (ic + sxc * jc + sxyc * kc) + c]);
+                    acc += xc[3 * (ic + sxc * jc + sxyc * kc) + c];
                 }
         const int nodd = (I & 1) + (J & 1) + (K & 1);
-        const double w = __longlong_as_double(static_cast<long long>(1023 - nodd) << 52);  // 2^-nodd
-        xf[t] += T(w * acc);
+        const T w = T(__longlong_as_double(static_cast<long long>(1023 - nodd) << 52));  // 2^-nodd, exact
+        xf[t] += w * acc;
     }
-    if (with_alpha && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (with_alpha && blk == 0 && threadIdx.x == 0) {
         const int64_t nc = 3 * int64_t(nxc + 1) * (nyc + 1) * (nzc + 1);
         xf[3 * nnf] += xc[nc];
     }
+}
+
+template <class T>
+__global__ void k_prolong_add(ProlongArgs<T> P) {
+    prolong_body<T>(P, blockIdx.x, gridDim.x);
+}
+template <class T>
+__global__ void k_prolong_add_b(const ProlongArgs<T>* __restrict__ A, BatchMap M) {
+    const int s = batch_system(M, blockIdx.x);
+    if (!batch_active(M, s)) return;
+    prolong_body<T>(A[s], blockIdx.x - M.first[s], M.first[s + 1] - M.first[s]);
 }
 
 void launch_prolong_add(pbm_grid* g, int k, bool fp32, const void* xc, void* xf, bool with_alpha, cudaStream_t st) {
@@ -129,11 +174,13 @@ void launch_prolong_add(pbm_grid* g, int k, bool fp32, const void* xc, void* xf,
     const int64_t nt = 3 * F.nnode();
     const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nt + 255) / 256, 152 * 16)));
     if (fp32)
-        k_prolong_add<float><<<blocks, 256, 0, st>>>(F.nx, F.ny, F.nz, F.support, (const float*)xc, (float*)xf,
-                                                     with_alpha);
+        k_prolong_add<float><<<blocks, 256, 0, st>>>(ProlongArgs<float>{F.nx, F.ny, F.nz, F.support,
+                                                                        with_alpha ? 1 : 0, (const float*)xc,
+                                                                        (float*)xf});
     else
-        k_prolong_add<double><<<blocks, 256, 0, st>>>(F.nx, F.ny, F.nz, F.support, (const double*)xc, (double*)xf,
-                                                      with_alpha);
+        k_prolong_add<double><<<blocks, 256, 0, st>>>(ProlongArgs<double>{F.nx, F.ny, F.nz, F.support,
+                                                                          with_alpha ? 1 : 0, (const double*)xc,
+                                                                          (double*)xf});
     PBM_LAUNCH("prolong");
 }
 
@@ -505,11 +552,15 @@ void build_coarsest(pbm_grid* g, bool op_s, cudaStream_t st) {
 }
 
 // x = Inv b on the coarsest level (warp per row, FP64 accumulation)
+
 template <class T>
-__global__ void k_coarsest_solve(int N, int n_vec, const double* __restrict__ Inv, const T* __restrict__ b,
-                                 T* __restrict__ x) {
+__device__ __forceinline__ void coarsest_solve_body(const CoarsestArgs<T>& P, unsigned blk) {
+    const int N = P.N, n_vec = P.n_vec;
+    const double* __restrict__ Inv = P.Inv;
+    const T* __restrict__ b = P.b;
+    T* __restrict__ x = P.x;
     const int lane = threadIdx.x & 31;
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int row = int((blk * blockDim.x + threadIdx.x) >> 5);
     if (row >= n_vec) return;
     double s = 0.0;
     for (int c = lane; c < n_vec; c += 32) s += Inv[row * N + c] * double(b[c]);
@@ -518,13 +569,75 @@ __global__ void k_coarsest_solve(int N, int n_vec, const double* __restrict__ In
     if (lane == 0) x[row] = T(s);
 }
 
+template <class T>
+__global__ void k_coarsest_solve(CoarsestArgs<T> P) {
+    coarsest_solve_body<T>(P, blockIdx.x);
+}
+template <class T>
+__global__ void k_coarsest_solve_b(const CoarsestArgs<T>* __restrict__ A, BatchMap M) {
+    const int s = batch_system(M, blockIdx.x);
+    if (!batch_active(M, s)) return;
+    coarsest_solve_body<T>(A[s], blockIdx.x - M.first[s]);
+}
+
 void launch_coarsest_solve(pbm_grid* g, bool fp32, const void* b, void* x, bool with_alpha, cudaStream_t st) {
     const int N = g->nc + 1;
     const int nv = with_alpha ? N : N - 1;
     const int blocks = (nv * 32 + 255) / 256;
-    if (fp32) k_coarsest_solve<float><<<blocks, 256, 0, st>>>(N, nv, g->cinv, (const float*)b, (float*)x);
-    else k_coarsest_solve<double><<<blocks, 256, 0, st>>>(N, nv, g->cinv, (const double*)b, (double*)x);
+    if (fp32) k_coarsest_solve<float><<<blocks, 256, 0, st>>>(CoarsestArgs<float>{N, nv, g->cinv, (const float*)b, (float*)x});
+    else k_coarsest_solve<double><<<blocks, 256, 0, st>>>(CoarsestArgs<double>{N, nv, g->cinv, (const double*)b, (double*)x});
     PBM_LAUNCH("coarsest solve");
 }
+
+template <class T>
+RestrictArgs<T> make_restrict_args(pbm_grid* g, int k, const void* rf, void* bc, bool with_alpha, double scale,
+                                   void* xfirst, int* blocks_out) {
+    const Geom& F = g->L[k].g;
+    Level& C = g->L[k + 1];
+    const int64_t nt = 3 * C.g.nnode();
+    *blocks_out = int(std::max<int64_t>(1, std::min<int64_t>((nt + 127) / 128, 152 * 16)));
+    const T* idiag = sizeof(T) == 4 ? (const T*)(const void*)C.idiag32 : (const T*)(const void*)C.idiag64;
+    return RestrictArgs<T>{F.nx, F.ny, F.nz, F.support, with_alpha ? 1 : 0, (const T*)rf, (T*)bc, scale,
+                           (T*)xfirst, idiag, &g->sc->mr[16 + k + 1]};
+}
+template <class T>
+ProlongArgs<T> make_prolong_args(pbm_grid* g, int k, const void* xc, void* xf, bool with_alpha, int* blocks_out) {
+    const Geom& F = g->L[k].g;
+    const int64_t nt = 3 * F.nnode();
+    *blocks_out = int(std::max<int64_t>(1, std::min<int64_t>((nt + 255) / 256, 152 * 16)));
+    return ProlongArgs<T>{F.nx, F.ny, F.nz, F.support, with_alpha ? 1 : 0, (const T*)xc, (T*)xf};
+}
+template <class T>
+CoarsestArgs<T> make_coarsest_args(pbm_grid* g, const void* b, void* x, bool with_alpha, int* blocks_out) {
+    const int N = g->nc + 1;
+    const int nv = with_alpha ? N : N - 1;
+    *blocks_out = (nv * 32 + 255) / 256;
+    return CoarsestArgs<T>{N, nv, g->cinv, (const T*)b, (T*)x};
+}
+template <class T>
+void launch_restrict_b(const RestrictArgs<T>* dA, const BatchMap& M, int total_blocks, cudaStream_t st) {
+    k_restrict_b<T><<<total_blocks, 128, 0, st>>>(dA, M);
+    PBM_LAUNCH("batched restrict");
+}
+template <class T>
+void launch_prolong_b(const ProlongArgs<T>* dA, const BatchMap& M, int total_blocks, cudaStream_t st) {
+    k_prolong_add_b<T><<<total_blocks, 256, 0, st>>>(dA, M);
+    PBM_LAUNCH("batched prolong");
+}
+template <class T>
+void launch_coarsest_b(const CoarsestArgs<T>* dA, const BatchMap& M, int total_blocks, cudaStream_t st) {
+    k_coarsest_solve_b<T><<<total_blocks, 256, 0, st>>>(dA, M);
+    PBM_LAUNCH("batched coarsest solve");
+}
+#define PBM_INST_MG(T)                                                                                          \
+    template RestrictArgs<T> make_restrict_args<T>(pbm_grid*, int, const void*, void*, bool, double, void*, int*); \
+    template ProlongArgs<T> make_prolong_args<T>(pbm_grid*, int, const void*, void*, bool, int*);               \
+    template CoarsestArgs<T> make_coarsest_args<T>(pbm_grid*, const void*, void*, bool, int*);                  \
+    template void launch_restrict_b<T>(const RestrictArgs<T>*, const BatchMap&, int, cudaStream_t);             \
+    template void launch_prolong_b<T>(const ProlongArgs<T>*, const BatchMap&, int, cudaStream_t);               \
+    template void launch_coarsest_b<T>(const CoarsestArgs<T>*, const BatchMap&, int, cudaStream_t);
+PBM_INST_MG(double)
+PBM_INST_MG(float)
+#undef PBM_INST_MG
 
 }  // namespace pbm

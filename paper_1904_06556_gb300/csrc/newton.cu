@@ -219,4 +219,49 @@ void launch_scale(const double* a, double* b, double s, int64_t n, cudaStream_t 
     PBM_LAUNCH("scale");
 }
 
+// Algorithm 1 multiplier update with the safeguard beta x <= x+ <= x / beta (ibeta = 1 / beta):
+//   rho+ = rho phi'(s), mu_lo+ = mu_lo phi'(-nu_lo / q_lo), mu_up+ = mu_up phi'(-nu_up / q_up),
+// s = (c - alpha + nu_lo - nu_up) / p, c = u^T K_e u / 2 (c2 holds u^T K_e u).
+__global__ void k_mult_update(int64_t m, const double* __restrict__ c2, double* __restrict__ rho,
+                              double* __restrict__ mul, double* __restrict__ muu, const double* __restrict__ nul,
+                              const double* __restrict__ nuu, double alpha, double p, double ql, double qu,
+                              double beta, double ibeta, int only_rho) {
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
+        const double s = (0.5 * c2[e] - alpha + nul[e] - nuu[e]) / p;
+        const double r = rho[e];
+        rho[e] = fmin(fmax(r * dphi_pb(s), beta * r), r * ibeta);
+        if (only_rho) continue;
+        const double a = mul[e], b = muu[e];
+        mul[e] = fmin(fmax(a * dphi_pb(-nul[e] / ql), beta * a), a * ibeta);
+        muu[e] = fmin(fmax(b * dphi_pb(-nuu[e] / qu), beta * b), b * ibeta);
+    }
+}
+void launch_mult_update(pbm_grid* g, const double* c2, pbm_state* s, double beta, bool only_rho, cudaStream_t st) {
+    k_mult_update<<<NG, NB, 0, st>>>(g->L[0].g.m(), c2, s->rho_dev, s->mu_lo_dev, s->mu_up_dev, s->nu_lo_dev,
+                                     s->nu_up_dev, s->alpha, s->p, s->q_lo, s->q_up, beta, 1.0 / beta,
+                                     only_rho ? 1 : 0);
+    PBM_LAUNCH("multiplier update");
+}
+
+// sums of the duality gap (eq. gap) and the dual objective: out[0] = sum min(rho_lo a, rho_up a),
+// a = alpha - c_e; out[1] = sum nu_lo; out[2] = sum nu_up; out[3] = sum rho
+__global__ void k_gap_sums(int64_t m, const double* __restrict__ c2, double alpha, double rho_lo, double rho_up,
+                           const double* __restrict__ nul, const double* __restrict__ nuu,
+                           const double* __restrict__ rho, double* partials, unsigned* counter, double* out) {
+    double acc[4] = {0, 0, 0, 0};
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
+        const double a = alpha - 0.5 * c2[e];
+        acc[0] += fmin(rho_lo * a, rho_up * a);
+        acc[1] += nul[e];
+        acc[2] += nuu[e];
+        acc[3] += rho[e];
+    }
+    finish_multi<4>(acc, partials, counter, out);
+}
+void launch_gap_sums(pbm_grid* g, const double* c2, const pbm_state* s, int slot, cudaStream_t st) {
+    k_gap_sums<<<NG, NB, 0, st>>>(g->L[0].g.m(), c2, s->alpha, s->rho_lo, s->rho_up, s->nu_lo_dev, s->nu_up_dev,
+                                  s->rho_dev, g->partials, &g->sc->counter[3], &g->sc->red[slot]);
+    PBM_LAUNCH("gap sums");
+}
+
 }  // namespace pbm

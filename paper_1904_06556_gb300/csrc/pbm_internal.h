@@ -241,6 +241,7 @@ struct pbm_grid {
     // (vector precision, operator, FP32 preconditioner); built on first use, kept until destroy
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t mr_graph[8] = {};
+    int fineL[2][2] = {};                  // autotuned chunk length [fp32][op_s] of the fine column pass
     int64_t mr_graph_kernels[8] = {};      // kernels in one iteration of each graph (launch counting)
     std::vector<int> prof_op;              // operator of every recorded launch
 };
@@ -273,10 +274,133 @@ void launch_fine(pbm_grid* g, bool fp32, const void* w, const void* d, const voi
 void launch_coarse(pbm_grid* g, int k, bool fp32, const ApplyArgs& a, cudaStream_t st);
 // Jacobi diagonal of a level (S or K), written to L[k].diag64 / diag32 (n + 1, last = alpha)
 void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st);
+// ------------------------------------------------------------------------------------------------
+// batched launches: one launch covers several systems (grid handles); first[s] is the first CTA of
+// system s (first[nsys] = total CTAs), sc[s] its scalar block; flags[1] == 0 marks a system whose
+// solve is finished (its CTAs return at once)
+// ------------------------------------------------------------------------------------------------
+struct BatchMap {
+    const int* first;
+    DevScalars* const* sc;
+    int nsys;
+};
+__device__ __forceinline__ int batch_system(const BatchMap& M, unsigned b) {
+    int lo = 0, hi = M.nsys - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (unsigned(M.first[mid]) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ bool batch_active(const BatchMap& M, int s) { return M.sc[s]->flags[1] != 0; }
+
+// ---- launch arguments of the operator, transfer and coarse-solve kernels (single and batched) ----
+template <class T>
+struct ColArgs {
+    int nx, ny, nz, support, L, nchunk;
+    int64_t n, m, ncol;
+    const T* x;        // gathered vector (n (+1))
+    const T* w;        // element weights (fine)
+    const T* d;        // Schur weights (fine S)
+    const T* what;     // 21 x m transformed K_e u_e (fine S, table mode), row r = 7 c + q - 1
+    const T* u;        // displacement (fine S, recompute mode)
+    const T* A;        // coarse element matrices (300 x m, upper triangle, entry-major)
+    KeHatT<T> K;
+    T* QA;
+    T* QB;
+    double* apart;     // per-CTA partial sums of -t_e (fine S)
+};
+
+template <class T>
+struct NodeArgs {
+    int nx, ny, nz, support, L;
+    int64_t n, ncol;
+    const T* QA;
+    const T* QB;
+    const T* x;
+    T* y;
+    const T* b;
+    const T* idiag;        // inverse Jacobi diagonal (JACOBI)
+    const double* omega;   // device scalar (JACOBI)
+    const T* bord;         // coarse alpha border (n) or nullptr
+    const double* s_alpha; // coarse S_alpha,alpha (device scalar)
+    int with_alpha;
+    int mode;
+    int dot_slot;
+    const double* apart;   // pass-1 partials (fine S) or nullptr
+    int napart;
+    double* partials;      // 2 * gridDim.x
+    DevScalars* sc;
+};
+
+template <class T>
+struct RestrictArgs {
+    int nxf, nyf, nzf, support, with_alpha;
+    const T* rf;
+    T* bc;
+    double scale;
+    T* xfirst;
+    const T* idiag;
+    const double* om;
+};
+
+template <class T>
+struct ProlongArgs {
+    int nxf, nyf, nzf, support, with_alpha;
+    const T* xc;
+    T* xf;
+};
+
+template <class T>
+struct CoarsestArgs {
+    int N, n_vec;
+    const double* Inv;
+    const T* b;
+    T* x;
+};
+
+// batched MINRES vector stages (krylov.cu): FIRST_JACOBI b = om f a (a input, f inverse diagonal);
+// LANCZOS2 a = A z, b = v_prev, c = v_cur; UPDATE2 a = z_next, b = z, c = d_prev, d = d_prev2, e = x;
+// ZERO b; COPY b = a
+enum VecOp { VOP_FIRST_JACOBI = 0, VOP_LANCZOS2 = 1, VOP_UPDATE2 = 2, VOP_ZERO = 3, VOP_COPY = 4 };
+enum ScalOp { SOP_INIT = 0, SOP_SCALARS = 1 };
+template <class T>
+struct VecArgs {
+    int op;
+    int64_t n;
+    const T* a;
+    T* b;
+    T* c;
+    T* d;
+    T* e;
+    const T* f;
+    double* mr;
+    const double* red;
+    const double* om;
+};
+template <class T>
+void launch_vec_b(const VecArgs<T>* dA, const BatchMap& M, int total_blocks, cudaStream_t st);
+void launch_scal_b(DevScalars* const* d_sc, int nsys, int op, cudaStream_t st);
+template <class T>
+RestrictArgs<T> make_restrict_args(pbm_grid* g, int k, const void* rf, void* bc, bool with_alpha, double scale,
+                                   void* xfirst, int* blocks_out);
+template <class T>
+ProlongArgs<T> make_prolong_args(pbm_grid* g, int k, const void* xc, void* xf, bool with_alpha, int* blocks_out);
+template <class T>
+CoarsestArgs<T> make_coarsest_args(pbm_grid* g, const void* b, void* x, bool with_alpha, int* blocks_out);
+template <class T>
+void launch_restrict_b(const RestrictArgs<T>* dA, const BatchMap& M, int total_blocks, cudaStream_t st);
+template <class T>
+void launch_prolong_b(const ProlongArgs<T>* dA, const BatchMap& M, int total_blocks, cudaStream_t st);
+template <class T>
+void launch_coarsest_b(const CoarsestArgs<T>* dA, const BatchMap& M, int total_blocks, cudaStream_t st);
+
 // two-pass column kernels (colpass.cu). ColEnv names the scratch the passes use: the plane-quad
 // buffers (cols_scratch_entries() entries of the vector type), the per-CTA partial sums and the
 // device scalar block (last-CTA counter, reduction slots).
 struct ColEnv {
+    int L = 0;                 // chunk length of the fine column pass (0: the default rule)
     void* qa = nullptr;
     void* qb = nullptr;
     double* partials = nullptr;
@@ -284,6 +408,22 @@ struct ColEnv {
     DevScalars* sc = nullptr;
 };
 int64_t cols_scratch_entries(const Geom& G);
+ColEnv env_of(pbm_grid* g);
+// argument builders shared by the single and the batched launches (blocks_out: CTAs of the launch)
+template <class T>
+ColArgs<T> make_fine_args(const ColEnv& env, const Geom& G, const KeHat& kh, const T* w, const T* d, const T* what,
+                          const T* u, const void* x, int* blocks_out);
+template <class T>
+ColArgs<T> make_coarse_args(const ColEnv& env, const Geom& G, const T* A, const void* x, int* blocks_out);
+template <class T>
+NodeArgs<T> make_node_args(const ColEnv& env, const Geom& G, const ApplyArgs& a, int L, const T* bord,
+                           const double* s_alpha, const double* apart, int napart, int64_t off, int* blocks_out);
+template <class T>
+void launch_cols_fine_b(const ColArgs<T>* dA, const BatchMap& M, int mode, int total_blocks, cudaStream_t st);
+template <class T>
+void launch_cols_coarse_b(const ColArgs<T>* dA, const BatchMap& M, int total_blocks, cudaStream_t st);
+template <class T>
+void launch_nodes_b(const NodeArgs<T>* dA, const BatchMap& M, int total_blocks, cudaStream_t st);
 template <class T>
 void cols_fine_env(const ColEnv& env, const Geom& G, const KeHat& kh, const T* w, const T* d, const T* what,
                    const T* u, const ApplyArgs& a, cudaStream_t st);
@@ -293,7 +433,11 @@ void cols_fine(pbm_grid* g, const T* w, const T* d, const T* what, const T* u, c
 template <class T>
 void cols_coarse(pbm_grid* g, int k, const T* A, const T* bord, const ApplyArgs& a, cudaStream_t st);
 void launch_what_hat(pbm_grid* g, cudaStream_t st);
-void cols_cost(const Geom& G, bool op_s, bool recompute_w, int mode, int esize, double& bytes, double& flops);
+void cols_cost(const Geom& G, int L, bool op_s, bool recompute_w, int mode, int esize, double& bytes, double& flops);
+// chunk length the handle uses for the fine column pass of (precision, operator)
+int fine_L(const pbm_grid* g, bool fp32, bool op_s);
+// times the candidate chunk lengths of the fine column pass and keeps the fastest (grid creation)
+void autotune_fine(pbm_grid* g);
 // y = 1 / x and y = 1 / sqrt(x) (n entries)
 void launch_inverse(const double* x, double* y, int64_t n, cudaStream_t st);
 void launch_inverse_sqrt(const double* x, double* y, int64_t n, cudaStream_t st);
@@ -305,8 +449,9 @@ void prof_end(pbm_grid* g, cudaStream_t st, int op, double bytes, double flops);
 void prof_fold(pbm_grid* g);
 
 // ---- multigrid, mg.cu ----
+// b_c = scale P^T r_f; if xfirst is given also xfirst = omega_{k+1} D_{k+1}^{-1} b_c (first Jacobi sweep)
 void launch_restrict(pbm_grid* g, int k, bool fp32, const void* rf, void* bc, bool with_alpha, double scale,
-                     cudaStream_t st);
+                     cudaStream_t st, void* xfirst = nullptr);
 void launch_prolong_add(pbm_grid* g, int k, bool fp32, const void* xc, void* xf, bool with_alpha, cudaStream_t st);
 void launch_build_what(pbm_grid* g, cudaStream_t st);
 void launch_build_level1(pbm_grid* g, bool op_s, cudaStream_t st);

@@ -18,8 +18,8 @@ void mr_update2(pbm_grid* g, bool fp32, void* zc, const void* zn, void* d1, void
                 cudaStream_t st);
 void cast_dot(pbm_grid* g, const float* src, double* dst, const double* other, int64_t n, int slot, cudaStream_t st);
 void lz_start(pbm_grid* g, double* v, double* t, double* vprev, const double* diag, int64_t n, cudaStream_t st);
-void lz_a(pbm_grid* g, double* w, const double* v, const double* diag, int64_t n, int j, cudaStream_t st);
-void lz_b(pbm_grid* g, double* w, const double* v, const double* vprev, int64_t n, int j, cudaStream_t st);
+void lz_b(pbm_grid* g, double* w, const double* v, const double* vprev, const double* sdiag, int64_t n, int j,
+          cudaStream_t st);
 void lz_next(pbm_grid* g, const double* w, double* v, double* vprev, double* t, const double* diag, int64_t n, int j,
              cudaStream_t st);
 
@@ -60,7 +60,10 @@ static size_t esz(bool fp32) { return fp32 ? sizeof(float) : sizeof(double); }
 // ------------------------------------------------------------------------------------------------
 // V-cycle: x = M^{-1} b on level k (x overwritten). If dot_slot >= 0, red[dot_slot] = x . b.
 // ------------------------------------------------------------------------------------------------
-void vcycle(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, void* x, int dot_slot, cudaStream_t st) {
+// first_done: the caller already wrote the first pre-smoothing sweep omega D^{-1} b into the buffer
+// the sweep sequence starts from (x for an odd number of pre-sweeps, else the level's t)
+void vcycle(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, void* x, int dot_slot, cudaStream_t st,
+            bool first_done = false) {
     Level& L = g->L[k];
     const int64_t nv = L.g.n() + (op_s ? 1 : 0);
     if (k == g->levels - 1) {
@@ -78,7 +81,7 @@ void vcycle(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, void* x, in
     void* cur = (pre % 2 == 1) ? x : t;
     void* oth = (cur == x) ? t : x;
     if (pre >= 1) {
-        launch_scale_diag_first(g, k, fp32, b, cur, op_s, st);
+        if (!first_done) launch_scale_diag_first(g, k, fp32, b, cur, op_s, st);
         for (int s = 1; s < pre; ++s) {
             level_apply(g, k, fp32, op_s, args(cur, oth, EPI_JACOBI, b, D, om), st);
             std::swap(cur, oth);
@@ -93,8 +96,13 @@ void vcycle(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, void* x, in
     Level& C = g->L[k + 1];
     void* bc = fp32 ? (void*)C.b32 : (void*)C.b64;
     void* xc = fp32 ? (void*)C.x32 : (void*)C.x64;
-    launch_restrict(g, k, fp32, r, bc, op_s, 1.0, st);
-    vcycle(g, k + 1, fp32, op_s, bc, xc, -1, st);
+    // the restriction also writes the coarse level's first smoothing sweep, unless that level is the
+    // coarsest (exact solve)
+    const bool fuse = (k + 1 < g->levels - 1) && pre >= 1;
+    void* xfirst = nullptr;
+    if (fuse) xfirst = (pre % 2 == 1) ? xc : (fp32 ? (void*)C.t32 : (void*)C.t64);
+    launch_restrict(g, k, fp32, r, bc, op_s, 1.0, st, xfirst);
+    vcycle(g, k + 1, fp32, op_s, bc, xc, -1, st, fuse);
     launch_prolong_add(g, k, fp32, xc, x, op_s, st);
     // post-smoothing
     cur = x;
@@ -148,10 +156,12 @@ static void lanczos_level(pbm_grid* g, int k, bool op_s, cudaStream_t st) {
     const int steps = g->desc.lanczos_steps;
     launch_inverse_sqrt(L.diag64, L.sdiag64, nv, st);
     lz_start(g, v, t, vp, L.sdiag64, nv, st);
+    // a_j = (A t) . t with t = D^{-1/2} v is the operator launch's fused dot product
+    const int slot = 40;
     for (int j = 0; j < steps; ++j) {
-        level_apply(g, k, false, op_s, args(t, w, EPI_APPLY), st);
-        lz_a(g, w, v, L.sdiag64, nv, j, st);
-        lz_b(g, w, v, vp, nv, j, st);
+        level_apply(g, k, false, op_s, args(t, w, EPI_APPLY, nullptr, nullptr, nullptr, slot), st);
+        PBM_CUDA(cudaMemcpyAsync(&g->sc->lz_a[j], &g->sc->red[slot], sizeof(double), cudaMemcpyDeviceToDevice, st));
+        lz_b(g, w, v, vp, L.sdiag64, nv, j, st);
         lz_next(g, w, v, vp, t, L.sdiag64, nv, j, st);
     }
     PBM_CUDA(cudaMemcpyAsync(g->sc_host->lz_a, g->sc->lz_a, sizeof(double) * steps, cudaMemcpyDeviceToHost, st));

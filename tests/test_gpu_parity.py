@@ -337,3 +337,113 @@ def test_full_size_cant64_apply_and_solve_residual(pkg):
     dz, info = G.minres_solve("S", dev(rhs), rtol=1e-8, maxit=500)
     S = pbm.assemble_S(pb, st, cf)
     assert np.linalg.norm(rhs - S @ host(dz)) <= 1.01e-8 * np.linalg.norm(rhs)
+
+
+# ------------------------------------------------------------------------------------------------
+# Algorithm 1 (PBM outer loop) on the GPU
+# ------------------------------------------------------------------------------------------------
+def _pbm_gpu_state(G, pb):
+    return G.initial_state(pb.n, pb.m, pb.V, pb.rho_lo, pb.rho_up)
+
+
+def test_pbm_solve_matches_oracle_algorithm1(pkg):
+    """Same parameters, near-exact inner solves on both sides (oracle: direct, GPU: MG-MINRES to 1e-11): the
+    outer/Newton iteration counts agree and the optimal densities coincide."""
+    nx, ny, nz = 8, 4, 4
+    g = fem.Grid(nx, ny, nz, "cantilever")
+    f = synthetic.load_vector(nx, ny, nz, "end_edge")
+    pb = pbm.Problem(g, f, 0.3 * g.m, 1e-3, 1.0)
+    ref = pbm.pbm(pb, eps_pbm=1e-6)
+    G = pkg.Grid(nx, ny, nz, 2, "cantilever")
+    st = _pbm_gpu_state(G, pb)
+    info = G.pbm_solve(st, dev(pb.f), eps_pbm=1e-6, eps_mr=1e-11, eps_mr_min=1e-11)
+    assert info["outer"] == ref.outer and info["newton"] == ref.newton
+    assert np.max(np.abs(host(st["rho"]) - ref.state.rho)) < 1e-7
+    comp_ref = 0.5 * pb.f @ pbm.masked(pb, ref.state.u)
+    assert abs(info["compliance"] - comp_ref) < 1e-8 * comp_ref
+    assert abs(st["alpha"] - ref.state.alpha) < 1e-8 * abs(ref.state.alpha)
+
+
+def test_pbm_solve_cant16_paper_parameters(pkg):
+    """The 16x8x8 cantilever run with the paper's parameters (adaptive eps_MR from 1e-4 sqrt(n)): the result
+    satisfies what Theorem 1 and Section 6 fix, checked with the oracle's own operators."""
+    w = synthetic.WORKLOADS["cant16"]
+    g = fem.Grid(w.nx, w.ny, w.nz, w.bc)
+    f = synthetic.load_vector(w.nx, w.ny, w.nz, w.loads[0])
+    pb = pbm.Problem(g, f, w.V, w.rho_lo, w.rho_up)
+    G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc)
+    st = _pbm_gpu_state(G, pb)
+    info = G.pbm_solve(st, dev(pb.f), eps_pbm=1e-5)
+    rho = host(st["rho"])
+    assert info["gap_ratio"] < 1e-5
+    assert abs(rho.sum() - pb.V) / pb.V <= 1e-3
+    assert rho.min() >= pb.rho_lo * (1 - 1e-6) and rho.max() <= pb.rho_up * (1 + 1e-6)
+    # the density's own equilibrium compliance (oracle direct solve) matches the dual's 1/2 f^T u
+    K = fem.assemble_K(g, rho, fem.element_stiffness())
+    u_rho = solvers.direct_solve(K, pb.f)
+    comp_rho = 0.5 * pb.f @ u_rho
+    assert abs(comp_rho - info["compliance"]) < 1e-3 * comp_rho
+    # KKT: c_e = alpha where the density is clearly between its bounds (elements next to a bound meet it only
+    # to the PBM tolerance)
+    c = pbm.compliances(pb, host(st["u"]))
+    inner = (rho > 10 * pb.rho_lo) & (rho < 0.9 * pb.rho_up)
+    assert inner.sum() > 10
+    assert np.all(np.abs(c[inner] - st["alpha"]) < 1e-3 * st["alpha"])
+    assert 2 <= info["outer"] <= 40 and info["newton"] >= info["outer"]
+
+
+# ------------------------------------------------------------------------------------------------
+# batched solves: systems of uneven size and depth advanced by one launch per stage
+# ------------------------------------------------------------------------------------------------
+BATCH_CASES = [((8, 4, 4), 2, "cantilever", 0), ((16, 8, 8), 3, "cantilever", 1),
+               ((16, 8, 8), 3, "bridge_corners", 2), ((24, 12, 12), 3, "cantilever", 3),
+               ((32, 16, 16), 4, "cantilever", 4)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_S_solves_equal_single_solves(pkg, precision):
+    grids, bs, refs, probs = [], [], [], []
+    for dims, lv, bc, seed in BATCH_CASES:
+        pb, st, d = make_problem(*dims, bc, seed, 0.5)
+        G = pkg.Grid(*dims, lv, bc, precision=precision)
+        G.set_state(state_dev(d))
+        rhs = dev(pbm.rhs_closed(pb, st, pbm.coeffs(pb, st)))
+        x1, i1 = G.minres_solve("S", rhs, rtol=1e-10, maxit=500)
+        grids.append(G)
+        bs.append(rhs)
+        refs.append((x1, i1))
+        probs.append((pb, st))
+    B = pkg.Batch(grids, "S")
+    xs, infos = B.minres_solve(bs, rtol=1e-10, maxit=500)
+    for x, inf, (x1, i1), (pb, st) in zip(xs, infos, refs, probs):
+        assert inf["relres"] <= 1e-10
+        if precision == "fp64":
+            # the batched kernels do each system's arithmetic exactly as the single launches do
+            assert inf["iterations"] == i1["iterations"]
+            assert torch.equal(x, x1)
+        else:
+            assert rel(host(x), host(x1)) < 1e-7
+    # the residuals, measured by the oracle's assembled operators
+    for x, b, (pb, st) in zip(xs, bs, probs):
+        S = pbm.assemble_S(pb, st)
+        assert np.linalg.norm(host(b) - S @ host(x)) <= 1.01e-10 * np.linalg.norm(host(b))
+    B.close()
+
+
+def test_batch_K_solves_equal_single_solves(pkg):
+    grids, fs, refs = [], [], []
+    for dims, lv, bc, seed in BATCH_CASES[:4]:
+        g = fem.Grid(*dims, bc)
+        rho = synthetic.density_uniform_rescaled(g.m, 0.3, seed)
+        G = pkg.Grid(*dims, lv, bc)
+        G.set_density(dev(rho))
+        f = dev(synthetic.load_vector(*dims, "end_edge"))
+        u1, i1 = G.minres_solve("K", f, rtol=1e-10, maxit=500)
+        grids.append(G)
+        fs.append(f)
+        refs.append((u1, i1))
+    B = pkg.Batch(grids, "K")
+    us, infos = B.minres_solve(fs, rtol=1e-10, maxit=500)
+    for u, inf, (u1, i1) in zip(us, infos, refs):
+        assert inf["iterations"] == i1["iterations"] and torch.equal(u, u1)
+    B.close()
