@@ -52,7 +52,7 @@ METRIC = "reduced-Newton MG-MINRES solve time & K(ρ)u GB/s; FP32-mixed vs FP64"
 UNIT = "reduced-Newton solves/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 PROFILE_DIR = os.path.join(ROOT, "profiles")
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_1904_06556_gb300", "csrc", f) for f in ("apply.cu", "pbm_internal.h")]
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1904_06556_gb300", "csrc", f) for f in ("colpass.cu", "pbm_internal.h")]
 # FP64 issue rate of GB300 derived from the nominal 1.25 TFLOP/s (FMA = 2 flops), 152 SMs, 2070 MHz:
 # 1.25e12 / (2 * 152 * 2.07e9) = 2 FP64 instructions per clock per SM, i.e. 629 G FP64 operations/s.
 FP64_OPS_PEAK = 2.0 * 152 * 2.07e9
@@ -336,7 +336,9 @@ def run_ours(args):
         achieved = prof["bytes"] / (prof["total_ms"] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{peak_src} (MEASURED_PEAKS hbm_gbs)",
-                "kernel": "k_march<float, 8, K_FINE_S> (fine-level S apply with fused residual/Jacobi epilogues)"}
+                "kernel": ("fine-level S operator: k_cols_fine<float, 2> (element columns, W_e recomputed from u) + "
+                           "k_nodes<float> (node sums with the fused residual / Jacobi / dot epilogues), timed as one "
+                           "launch pair")}
     roof.update({"launches": prof["launches"], "avg_launch_us": avg_ms * 1e3,
                  "bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
                  "ops_per_launch": prof["flops"] / max(prof["launches"], 1)})
