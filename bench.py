@@ -353,6 +353,7 @@ def run_ours(args):
         "config": workload_desc(w, precision),
         "solve": {"minres_iterations": iters[-1], "true_relres": relres, "phases_last_step": phases,
                   "mixed_outer_steps": last["info"]["outer"], "fine_chunk": G.info()["fine_chunk"],
+                  "fp32_tile_K_S": G.info()["fp32_tile"],
                   "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
                   "equilibrium_u_relres": uinfo["relres"]},
         "k_apply": kapply,

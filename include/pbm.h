@@ -72,6 +72,12 @@ enum pbm_op {
     PBM_OP_S = 1           /* reduced Newton matrix S of eq. (S), from pbm_set_state             */
 };
 
+enum pbm_epilogue {        /* what a fused operator launch writes (pbm_apply_fine_f32)           */
+    PBM_EPI_APPLY = 0,     /* y = A x                                                            */
+    PBM_EPI_RESID = 1,     /* y = b - A x                                                        */
+    PBM_EPI_JACOBI = 2     /* y = x + omega D^{-1} (b - A x), one damped-Jacobi sweep             */
+};
+
 typedef struct pbm_grid_desc {
     int nx, ny, nz;        /* fine elements per direction, >= 1                                   */
     int levels;            /* multigrid levels >= 1; nx, ny, nz divisible by 2^(levels-1)       */
@@ -98,7 +104,10 @@ typedef struct pbm_grid_info {
     int64_t device_bytes;         /* device memory held by the handle                            */
     int fine_chunk[4];            /* element layers per thread of the fine operator's column pass,
                                      chosen by timing at creation: FP64 K, FP64 S, FP32 K, FP32 S
-                                     (0 where the precision is not used)                         */
+                                     (FP32: batched solves; 0 where the precision is not used)    */
+    int fp32_tile[2][5];          /* plan of the single-pass FP32 fine operator, for K and for S:
+                                     {TX, TY, DZ} node columns x node columns x planes per CTA,
+                                     threads per CTA, plan index (pbm_set_fp32_plan)               */
 } pbm_grid_info;
 
 /* Newton state of the dual VTS problem (eq. (aug_lagr)): variables xi = (u, alpha, nu_lo, nu_up),
@@ -191,6 +200,35 @@ int pbm_apply_K(pbm_grid* g, const double* w_dev, const double* x_dev, double* y
 
 /* Same operator in FP32 (the kernel the mixed path runs); w_dev must not be NULL. */
 int pbm_apply_K_f32(pbm_grid* g, const float* w_dev, const float* x_dev, float* y_dev, void* stream);
+
+/* One FP32 fine-level application of the operator `op` (PBM_OP_K: K(rho) of eq. (1) with the density
+ * of pbm_set_density; PBM_OP_S: S of eq. (S) at the state of pbm_set_state) with one of the fused
+ * epilogues the mixed-precision V-cycle uses (Section 5.1):
+ *   PBM_EPI_APPLY  y = A x                       dot: y . x
+ *   PBM_EPI_RESID  y = b - A x                   dot: y . y
+ *   PBM_EPI_JACOBI y = x + omega_0 D_0^{-1} (b - A x), omega_0 and D_0 the fine level's Jacobi weight
+ *                  and diagonal of the current hierarchy (pbm_grid_info_get, pbm_get_diag)   dot: y . b
+ * Only for PBM_MIXED grids, whose FP32 copies of the operator data are made when the operator's
+ * hierarchy is set up (pbm_set_state for S; a K solve or pbm_vcycle for K): PBM_ESTATE otherwise.
+ * x_dev, b_dev (NULL for APPLY), y_dev: FP32 device vectors of n (K) or n + 1 (S) entries, y not
+ * overlapping x or b. dot_host: NULL, or receives the epilogue's FP64-reduced dot product (this
+ * synchronises `stream`). Errors: PBM_EINVAL, PBM_ESTATE. */
+int pbm_apply_fine_f32(pbm_grid* g, int op, int epilogue, const float* x_dev, const float* b_dev, float* y_dev,
+                       double* dot_host, void* stream);
+
+/* Tile plans of the single-pass FP32 fine operator (CTA size, register budget, TX x TY node columns
+ * by DZ planes per CTA; listed by pbm_grid_info_get's fp32_tile). pbm_create_grid times every plan
+ * on PBM_MIXED grids and keeps the fastest per operator; pbm_set_fp32_plan overrides that choice
+ * for `op` (PBM_OP_K or PBM_OP_S) with plan 0 <= plan < pbm_fp32_plan_count(). Every plan computes
+ * the same operator; only the reduction order of the dot products and alpha row depends on it.
+ * Errors: PBM_EINVAL. */
+int pbm_fp32_plan_count(void);
+int pbm_set_fp32_plan(pbm_grid* g, int op, int plan);
+
+/* Copies the Jacobi diagonal of level `level` of the current hierarchy (K or S, the last one set
+ * up) into diag_dev: n_level + 1 FP64 entries (the last is the alpha entry of S, 1 for K);
+ * supported dofs hold 1. Errors: PBM_EINVAL, PBM_ESTATE (no hierarchy). */
+int pbm_get_diag(const pbm_grid* g, int level, double* diag_dev, void* stream);
 
 /* Sets the Newton state and builds what S needs (Section 3.2): the per-element factors rho', rho'',
  * mu''_lo, mu''_up, the Schur weights d_i = 1/(1/rho'' + 1/mu''_lo + 1/mu''_up) and rhs weights

@@ -45,6 +45,11 @@ def apply_K_noalloc(nx: int, ny: int, nz: int, support: str, x: torch.Tensor, w:
     return y
 
 
+def fp32_plan_count() -> int:
+    """Number of tile plans of the single-pass FP32 fine operator (pbm_fp32_plan_count)."""
+    return int(lib().pbm_fp32_plan_count())
+
+
 def _ptr(t: torch.Tensor | None, dtype=torch.float64, n: int | None = None, name: str = "tensor"):
     if t is None:
         return None
@@ -117,7 +122,8 @@ class Grid:
         L = gi.levels
         return dict(levels=L, dims=[(gi.nx[k], gi.ny[k], gi.nz[k]) for k in range(L)], n=list(gi.n[:L]),
                     m=list(gi.m[:L]), n_free=gi.n_free, omega=list(gi.omega[:L]), lambda_max=list(gi.lambda_max[:L]),
-                    device_bytes=gi.device_bytes, fine_chunk=list(gi.fine_chunk))
+                    device_bytes=gi.device_bytes, fine_chunk=list(gi.fine_chunk),
+                    fp32_tile=[list(gi.fp32_tile[0]), list(gi.fp32_tile[1])])
 
     def maps(self, level: int, which: str):
         import numpy as np
@@ -157,6 +163,30 @@ class Grid:
         self._check(self._L.pbm_apply_K_f32(self._h, _ptr(w, f, self.m, "w"), _ptr(x, f, self.n, "x"),
                                             _ptr(y, f, self.n, "y"), _stream()))
         return y
+
+    def apply_fine_f32(self, op: str, epilogue: str, x: torch.Tensor, b: torch.Tensor | None = None,
+                       out: torch.Tensor | None = None, dot: bool = False):
+        """One FP32 fine-level application of K or S with a fused epilogue (pbm_apply_fine_f32); returns
+        (y, dot) where dot is the epilogue's reduced dot product (or None)."""
+        f = torch.float32
+        n = self.n + (1 if op == "S" else 0)
+        y = out if out is not None else torch.empty(n, dtype=f, device=x.device)
+        d = C.c_double(0.0)
+        self._check(self._L.pbm_apply_fine_f32(self._h, _lib.OPS[op], _lib.EPILOGUES[epilogue], _ptr(x, f, n, "x"),
+                                               _ptr(b, f, n, "b") if b is not None else None, _ptr(y, f, n, "y"),
+                                               C.byref(d) if dot else None, _stream()))
+        return y, (d.value if dot else None)
+
+    def set_fp32_plan(self, op: str, plan: int):
+        """Overrides the autotuned tile plan of the FP32 fine operator for op (pbm_set_fp32_plan)."""
+        self._check(self._L.pbm_set_fp32_plan(self._h, _lib.OPS[op], int(plan)))
+
+    def diag(self, level: int = 0) -> torch.Tensor:
+        """Jacobi diagonal (n_level + 1 FP64 entries) of a level of the current hierarchy (pbm_get_diag)."""
+        nl = int(self.info()["n"][level]) + 1
+        out = torch.empty(nl, dtype=torch.float64, device="cuda")
+        self._check(self._L.pbm_get_diag(self._h, level, _ptr(out, n=nl, name="diag"), _stream()))
+        return out
 
     def _state(self, st: dict) -> _lib.State:
         s = _lib.State()

@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "PBM_OK", -1: "PBM_EINVAL", -2: "PBM_ENOMEM", -3: "PBM_ECUDA"
 SUPPORTS = {"cantilever": 0, "bridge_corners": 1, "bridge_edges": 2, "free": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 OPS = {"K": 0, "S": 1}
+EPILOGUES = {"apply": 0, "resid": 1, "jacobi": 2}
 MAPS = {"fixed_dofs": 0, "elem_nodes": 1, "prolong": 2, "Ke": 3}
 
 
@@ -35,7 +36,8 @@ class GridDesc(C.Structure):
 class GridInfo(C.Structure):
     _fields_ = [("levels", C.c_int), ("nx", C.c_int * 16), ("ny", C.c_int * 16), ("nz", C.c_int * 16),
                 ("n", C.c_int64 * 16), ("m", C.c_int64 * 16), ("n_free", C.c_int64), ("omega", C.c_double * 16),
-                ("lambda_max", C.c_double * 16), ("device_bytes", C.c_int64), ("fine_chunk", C.c_int * 4)]
+                ("lambda_max", C.c_double * 16), ("device_bytes", C.c_int64), ("fine_chunk", C.c_int * 4),
+                ("fp32_tile", (C.c_int * 5) * 2)]
 
 
 class State(C.Structure):
@@ -95,6 +97,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pbm_set_density": (i, [vp, vp, vp]),
         "pbm_apply_K": (i, [vp, vp, vp, vp, vp]),
         "pbm_apply_K_f32": (i, [vp, vp, vp, vp, vp]),
+        "pbm_apply_fine_f32": (i, [vp, i, i, vp, vp, vp, C.POINTER(C.c_double), vp]),
+        "pbm_get_diag": (i, [vp, i, vp, vp]),
+        "pbm_fp32_plan_count": (i, []),
+        "pbm_set_fp32_plan": (i, [vp, i, i]),
         "pbm_set_state": (i, [vp, C.POINTER(State), vp]),
         "pbm_apply_S": (i, [vp, vp, vp, vp]),
         "pbm_reduced_rhs": (i, [vp, vp, vp, C.POINTER(C.c_double), vp]),

@@ -434,15 +434,17 @@ static void set_epi(MarchParams<T>& P, const ApplyArgs& a) {
     P.dot_slot = a.dot_slot;
 }
 
-// Operator applications run in the two-pass column kernels (colpass.cu); FP64 reads the W_e table,
-// FP32 recomputes W_e from u. The marching kernel above builds the Jacobi diagonals.
+// Fine-level operator applications: FP64 runs the two-pass column kernels (colpass.cu) with the
+// W_e table, FP32 the single-pass kernel (fused.cu) that recomputes W_e from u. The marching kernel
+// above builds the Jacobi diagonals.
 void launch_fine(pbm_grid* g, bool fp32, const void* w, const void* d, const void* u, const ApplyArgs& a,
                  cudaStream_t st) {
     const bool s = u != nullptr;
     if (g->prof_on) prof_begin(g, st);
     if (fp32)
-        cols_fine<float>(g, (const float*)w, s ? (const float*)d : nullptr, nullptr, s ? (const float*)u : nullptr, a,
-                         st);
+        fused_fine_f32(fused_plan(g->L[0].g, g->fusedP[s ? 1 : 0]), g->sc, g->partials, int64_t(8) * g->max_blocks,
+                       g->L[0].g, g->kehat, (const float*)w, s ? (const float*)d : nullptr,
+                       s ? (const float*)u : nullptr, a, st);
     else
         cols_fine<double>(g, (const double*)w, s ? (const double*)d : nullptr, s ? g->what_hat : nullptr, nullptr, a,
                           st);

@@ -351,6 +351,7 @@ int pbm_create_grid(const pbm_grid_desc* d, pbm_grid** out) {
     PBM_CUDA(cudaMallocHost((void**)&g->sc_host, sizeof(DevScalars)));
     std::memset(g->sc_host, 0, sizeof(DevScalars));
     PBM_CUDA(cudaDeviceSynchronize());
+    g->fusedP[0] = g->fusedP[1] = fused_default_plan(g->L[0].g);
     autotune_fine(g);
     PBM_CUDA(cudaDeviceSynchronize());
     *out = g;
@@ -446,6 +447,14 @@ int pbm_grid_info_get(const pbm_grid* g, pbm_grid_info* out) {
     out->fine_chunk[1] = fine_L(g, false, true);
     out->fine_chunk[2] = g->desc.precision == PBM_MIXED ? fine_L(g, true, false) : 0;
     out->fine_chunk[3] = g->desc.precision == PBM_MIXED ? fine_L(g, true, true) : 0;
+    for (int op = 0; op < 2; ++op) {
+        const FusedPlan fp = fused_plan(F, g->fusedP[op]);
+        out->fp32_tile[op][0] = fp.TX;
+        out->fp32_tile[op][1] = fp.TY;
+        out->fp32_tile[op][2] = fp.DZ;
+        out->fp32_tile[op][3] = fused_threads(fp);
+        out->fp32_tile[op][4] = g->fusedP[op];
+    }
     PBM_CATCH
 }
 
@@ -544,6 +553,53 @@ int pbm_apply_K_f32(pbm_grid* g, const float* w_dev, const float* x_dev, float* 
     a.mode = EPI_APPLY;
     a.dot_slot = -1;
     launch_fine(g, true, w_dev, nullptr, nullptr, a, S(stream));
+    PBM_CATCH
+}
+
+int pbm_apply_fine_f32(pbm_grid* g, int op, int epilogue, const float* x_dev, const float* b_dev, float* y_dev,
+                       double* dot_host, void* stream) {
+    PBM_TRY
+    if (!g || !x_dev || !y_dev) fail(PBM_EINVAL, "null argument");
+    if (op != PBM_OP_K && op != PBM_OP_S) fail(PBM_EINVAL, "unknown operator");
+    if (epilogue < PBM_EPI_APPLY || epilogue > PBM_EPI_JACOBI) fail(PBM_EINVAL, "unknown epilogue");
+    if (epilogue != PBM_EPI_APPLY && !b_dev) fail(PBM_EINVAL, "the residual and Jacobi epilogues need b");
+    if (g->desc.precision != PBM_MIXED) fail(PBM_ESTATE, "FP32 operators need a PBM_MIXED grid");
+    if (g->op_ready != (op == PBM_OP_S ? 2 : 1)) fail(PBM_ESTATE, "the operator's hierarchy is not set up");
+    set_device(g);
+    const cudaStream_t st = S(stream);
+    ApplyArgs a{};
+    a.x = x_dev;
+    a.y = y_dev;
+    a.b = b_dev;
+    a.diag = g->L[0].idiag32;
+    a.omega = &g->sc->mr[16];
+    a.mode = epilogue;
+    a.dot_slot = dot_host ? 56 : -1;
+    level_apply(g, 0, true, op == PBM_OP_S, a, st);
+    if (dot_host) *dot_host = read_slot(g, 56, st);
+    PBM_CATCH
+}
+
+int pbm_fp32_plan_count(void) { return fused_num_plans(); }
+
+int pbm_set_fp32_plan(pbm_grid* g, int op, int plan) {
+    PBM_TRY
+    if (!g) fail(PBM_EINVAL, "null grid");
+    if (op != PBM_OP_K && op != PBM_OP_S) fail(PBM_EINVAL, "unknown operator");
+    if (plan < 0 || plan >= fused_num_plans()) fail(PBM_EINVAL, "plan out of range");
+    g->fusedP[op == PBM_OP_S ? 1 : 0] = plan;
+    PBM_CATCH
+}
+
+int pbm_get_diag(const pbm_grid* g, int level, double* diag_dev, void* stream) {
+    PBM_TRY
+    if (!g || !diag_dev) fail(PBM_EINVAL, "null argument");
+    if (level < 0 || level >= g->levels) fail(PBM_EINVAL, "level out of range");
+    if (g->op_ready == 0) fail(PBM_ESTATE, "no hierarchy has been set up");
+    set_device(const_cast<pbm_grid*>(g));
+    const Level& L = g->L[level];
+    PBM_CUDA(cudaMemcpyAsync(diag_dev, L.diag64, sizeof(double) * (L.g.n() + 1), cudaMemcpyDeviceToDevice,
+                             S(stream)));
     PBM_CATCH
 }
 

@@ -569,7 +569,8 @@ void cols_fine(pbm_grid* g, const T* w, const T* d, const T* what, const T* u, c
 // Autotuner of the fine column pass: L trades the balance of columns over the SM sub-partitions
 // (short chunks, more threads) against the plane transforms shared inside a chunk (long chunks).
 // Each candidate is timed with CUDA events on zeroed inputs (the kernels' cost does not depend on
-// the values) and the fastest is kept per (precision, operator).
+// the values) and the fastest is kept per (precision, operator). For mixed-precision grids the tile
+// plans of the single-pass FP32 operator (fused.cu) are timed the same way.
 void autotune_fine(pbm_grid* g) {
     const Geom& G = g->L[0].g;
     const int64_t n = G.n(), m = G.m();
@@ -619,6 +620,35 @@ void autotune_fine(pbm_grid* g) {
                     }
                 }
                 g->fineL[p][op] = bestL;
+            }
+        // tile plan of the single-pass FP32 operator
+        if (mixed)
+            for (int op = 0; op < 2; ++op) {
+                ApplyArgs a{};
+                a.x = g->kv32[0];
+                a.y = g->kv32[1];
+                a.mode = EPI_APPLY;
+                a.with_alpha = op == 1;
+                a.dot_slot = -1;
+                float best = 3.4e38f;
+                int bestP = 0;
+                for (int c = 0; c < fused_num_plans(); ++c) {
+                    const FusedPlan fp = fused_plan(G, c);
+                    for (int rep = 0; rep < 4; ++rep) {
+                        if (rep == 1) PBM_CUDA(cudaEventRecord(e0, 0));
+                        fused_fine_f32(fp, g->sc, g->partials, int64_t(8) * g->max_blocks, G, g->kehat, g->w32,
+                                       op ? g->d32 : nullptr, op ? g->u32 : nullptr, a, 0);
+                    }
+                    PBM_CUDA(cudaEventRecord(e1, 0));
+                    PBM_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.0f;
+                    PBM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (ms < best) {
+                        best = ms;
+                        bestP = c;
+                    }
+                }
+                g->fusedP[op] = bestP;
             }
     } catch (...) {
         cudaEventDestroy(e0);

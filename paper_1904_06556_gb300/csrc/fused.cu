@@ -1,0 +1,491 @@
+// Single-pass FP32 fine-level operator: K(w) x and the S operator of eq. (S), with the fused apply /
+// residual / damped-Jacobi epilogues (Section 5.1) and the Krylov dot products.
+//
+// In FP32 the operator is bound by memory traffic, not by arithmetic, so this kernel trades a little
+// recomputation for traffic: every CTA owns a TX x TY tile of node columns and marches up a chunk of
+// DZ node planes. It computes the (TX + 1) x (TY + 1) element columns around its tile, so the
+// elements on tile borders are computed by two CTAs (and the element layer below a chunk by two
+// chunks), and nothing but the inputs and the output goes through global memory:
+//   * the node plane above the current element layer (x, and u for S) is staged in shared memory
+//     with a one-node halo; the global loads of the plane after it are issued before the element
+//     arithmetic of the current layer (software prefetch into registers);
+//   * one thread per element column applies K_e = H^T Khat H (the factored element matrix, see
+//     pbm_internal.h): the xy part of the transform of each plane is shared by the two layers that
+//     touch it, and the top face of every element stays in registers until the next layer adds its
+//     bottom face;
+//   * the four element columns around a node exchange their corner values through shared memory;
+//     the thread that owns the node sums them in a fixed order and applies the epilogue.
+// The alpha row of S counts every element once (in the CTA and chunk that own its upper corner
+// node). Per-CTA partial sums of the dot product and of the alpha row are finished by the last CTA
+// in a fixed order, so results are bit-reproducible for a given tile plan.
+#include <algorithm>
+
+#include "pbm_internal.h"
+
+namespace pbm {
+
+constexpr int FSLOT = 4;   // staging slots per thread: 3 (TX + 2)(TY + 2) <= FSLOT * NT
+
+struct FusedArgs {
+    int nx, ny, nz, support;
+    int TX, TY, DZ, gx, gy;
+    int64_t n;
+    const float* x;
+    const float* u;       // displacement (S)
+    const float* w;       // element weights
+    const float* d;       // Schur weights (S)
+    float* y;
+    const float* b;
+    const float* idiag;
+    const double* omega;
+    int mode, with_alpha, dot_slot;
+    KeHatT<float> K;
+    double* partials;     // 2 * gridDim.x
+    DevScalars* sc;
+};
+
+// transformed xy quad of the element column at staged coordinates (lx, ly) of a staged plane,
+// supported nodes masked
+__device__ __forceinline__ void fused_quad(const float* __restrict__ s, int RW, int lx, int ly, const bool (&fx)[4],
+                                           float (&Q)[3][4]) {
+    float v[3][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const float* p = s + (ly + (a >> 1)) * RW + 3 * (lx + (a & 1));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c][a] = fx[a] ? 0.0f : p[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float s0 = v[c][0] + v[c][1], d0 = v[c][1] - v[c][0];
+        const float s1 = v[c][2] + v[c][3], d1 = v[c][3] - v[c][2];
+        Q[c][0] = s0 + s1;
+        Q[c][1] = d0 + d1;
+        Q[c][2] = s1 - s0;
+        Q[c][3] = d1 - d0;
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ double fused_cta_sum(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NT / 32; ++w) s += sh[w];
+    __syncthreads();
+    return s;
+}
+
+// MODE 0: K(w) x. MODE 2: S x with W_e = Khat H u_e recomputed from the staged u. NT threads per
+// CTA, MINB resident CTAs per SM requested from the register allocator.
+template <int MODE, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
+    constexpr bool S = MODE == 2;
+    extern __shared__ float4 fused_smem4[];
+    float* smem = reinterpret_cast<float*>(fused_smem4);
+    __shared__ double sred[NT / 32];
+    __shared__ bool s_last;
+
+    const int TX = P.TX, TY = P.TY, EX = TX + 1, EY = TY + 1;
+    const int RW = 3 * (TX + 2);           // floats per staged row
+    const int SF = RW * (TY + 2);          // floats per staged plane: TY + 2 rows
+    const int EC = EX * EY;
+    float* sx = smem;                      // 2 planes of x
+    float* su = smem + 2 * SF;             // 2 planes of u (S)
+    float* sq = smem + (S ? 4 : 2) * SF;   // 12 x EC corner values of the element columns
+
+    const int t = threadIdx.x;
+    const int nx = P.nx, ny = P.ny, nz = P.nz, support = P.support;
+    const int bx = int(blockIdx.x % unsigned(P.gx));
+    const int rest = int(blockIdx.x / unsigned(P.gx));
+    const int by = rest % P.gy, bz = rest / P.gy;
+    const int X0 = bx * TX, Y0 = by * TY;
+    const int kz0 = bz * P.DZ, kz1 = min(kz0 + P.DZ, nz + 1);
+    const int64_t plane = 3 * int64_t(nx + 1) * (ny + 1);
+
+    // staging slots: flat index f = t + s NT of the staged plane, row f / RW, float f % RW
+    int gofs[FSLOT];
+#pragma unroll
+    for (int s = 0; s < FSLOT; ++s) {
+        const int f = t + s * NT;
+        gofs[s] = -2;
+        if (f < SF) {
+            const int row = f / RW, o = f - row * RW;
+            const int gxn = X0 - 1 + o / 3, gyn = Y0 - 1 + row;
+            gofs[s] = (gxn >= 0 && gxn <= nx && gyn >= 0 && gyn <= ny) ? 3 * (gxn + (nx + 1) * gyn) + o % 3 : -1;
+        }
+    }
+    float px[FSLOT], pu[FSLOT];
+    auto fetch = [&](int k) {
+        const float* xs = P.x + int64_t(k) * plane;
+        const float* us = S ? P.u + int64_t(k) * plane : nullptr;
+#pragma unroll
+        for (int s = 0; s < FSLOT; ++s) {
+            px[s] = gofs[s] >= 0 ? __ldg(xs + gofs[s]) : 0.0f;
+            if (S) pu[s] = gofs[s] >= 0 ? __ldg(us + gofs[s]) : 0.0f;
+        }
+    };
+    auto stage = [&](int k) {
+        float* dx = sx + (k & 1) * SF;
+        float* du = su + (k & 1) * SF;
+#pragma unroll
+        for (int s = 0; s < FSLOT; ++s)
+            if (gofs[s] != -2) {
+                dx[t + s * NT] = px[s];
+                if (S) du[t + s * NT] = pu[s];
+            }
+    };
+
+    // element-column role
+    const int lx = t % EX, ly = t / EX;
+    const int ex = X0 - 1 + lx, ey = Y0 - 1 + ly;
+    const bool ecol = t < EC && ex >= 0 && ex < nx && ey >= 0 && ey < ny;
+    const bool designated = ecol && lx < TX && ly < TY;
+    // owner role
+    const int ox = t % TX, oy = t / TX;
+    const int I = X0 + ox, J = Y0 + oy;
+    const bool owner = t < TX * TY && I <= nx && J <= ny;
+
+    const float xa = S ? P.x[P.n] : 0.0f;
+    const double om = P.mode == EPI_JACOBI ? *P.omega : 0.0;
+    const float omF = float(om);
+    const bool want_dot = P.dot_slot >= 0;
+    float pdT = 0.0f, paT = 0.0f;
+
+    auto corner_mask = [&](int k, bool (&fx)[4]) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) fx[a] = node_fixed(support, nx, ny, nz, ex + (a & 1), ey + (a >> 1), k);
+    };
+
+    const int kstart = max(kz0 - 1, 0);
+    float Qlo[3][4], Ulo[3][4], carry[3][4];
+    // element weights of the current layer, loaded one layer ahead
+    const int64_t e0 = ex + int64_t(nx) * (ey + int64_t(ny) * kstart), elayer = int64_t(nx) * ny;
+    float wn = 0.0f, dn = 0.0f;
+    if (ecol && kstart < nz) {
+        wn = __ldg(P.w + e0);
+        if (S) dn = __ldg(P.d + e0);
+    }
+    fetch(kstart);
+    stage(kstart);
+    if (kstart + 1 <= nz) fetch(kstart + 1);
+    __syncthreads();
+    if (ecol) {
+        bool fx[4];
+        corner_mask(kstart, fx);
+        fused_quad(sx + (kstart & 1) * SF, RW, lx, ly, fx, Qlo);
+        if (S) fused_quad(su + (kstart & 1) * SF, RW, lx, ly, fx, Ulo);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) carry[c][q] = 0.0f;
+
+    for (int k = kstart; k < kz1; ++k) {
+        const bool layer = k < nz;
+        if (layer) stage(k + 1);
+        __syncthreads();  // (a) plane k + 1 staged
+        if (layer && k + 2 <= nz && k + 1 < kz1) fetch(k + 2);
+        const float we = wn, de = dn;
+        if (ecol && k + 1 < nz && k + 1 < kz1) {
+            wn = __ldg(P.w + e0 + (k + 1 - kstart) * elayer);
+            if (S) dn = __ldg(P.d + e0 + (k + 1 - kstart) * elayer);
+        }
+        float xo[3] = {0.0f, 0.0f, 0.0f};
+        if (owner && k >= kz0) {
+            const float* p = sx + (k & 1) * SF + (oy + 1) * RW + 3 * (ox + 1);
+            xo[0] = p[0];
+            xo[1] = p[1];
+            xo[2] = p[2];
+        }
+        float Bq[3][4];
+        if (ecol && layer) {
+            bool fx[4];
+            corner_mask(k + 1, fx);
+            float Qhi[3][4];
+            fused_quad(sx + ((k + 1) & 1) * SF, RW, lx, ly, fx, Qhi);
+            float X[3][8], Y[3][8];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    X[c][q] = Qlo[c][q] + Qhi[c][q];
+                    X[c][q + 4] = Qhi[c][q] - Qlo[c][q];
+                    Qlo[c][q] = Qhi[c][q];
+                }
+            if (S) {
+                float Uhi[3][4], U[3][8], Wt[3][8];
+                fused_quad(su + ((k + 1) & 1) * SF, RW, lx, ly, fx, Uhi);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        U[c][q] = Ulo[c][q] + Uhi[c][q];
+                        U[c][q + 4] = Uhi[c][q] - Ulo[c][q];
+                        Ulo[c][q] = Uhi[c][q];
+                    }
+                khat_apply(P.K, U, Wt);
+                float dot = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int q = 1; q < 8; ++q) dot += Wt[c][q] * X[c][q];
+                const float te = de * (dot - xa);
+                if (designated && k + 1 >= kz0 && k + 1 < kz1) paT -= te;   // counted where its top plane is owned
+                khat_apply(P.K, X, Y);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int q = 1; q < 8; ++q) Y[c][q] = we * Y[c][q] + te * Wt[c][q];
+            } else {
+                khat_apply(P.K, X, Y);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int q = 1; q < 8; ++q) Y[c][q] *= we;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    Bq[c][q] = carry[c][q] + (Y[c][q] - Y[c][q + 4]);
+                    carry[c][q] = Y[c][q] + Y[c][q + 4];
+                }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    Bq[c][q] = carry[c][q];
+                    carry[c][q] = 0.0f;
+                }
+        }
+        if (k < kz0) continue;  // the layer below the chunk: only its top face is kept
+        // inverse xy transform: the element column's values at its 4 corners of plane k
+        if (t < EC) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float a0 = Bq[c][0] - Bq[c][1], a1 = Bq[c][0] + Bq[c][1];
+                const float a2 = Bq[c][2] - Bq[c][3], a3 = Bq[c][2] + Bq[c][3];
+                sq[(0 * 3 + c) * EC + t] = a0 - a2;
+                sq[(1 * 3 + c) * EC + t] = a1 - a3;
+                sq[(2 * 3 + c) * EC + t] = a0 + a2;
+                sq[(3 * 3 + c) * EC + t] = a1 + a3;
+            }
+        }
+        __syncthreads();  // (b) corner values of plane k complete
+        if (owner) {
+            float s[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int dj = 1; dj >= 0; --dj)
+#pragma unroll
+                for (int di = 1; di >= 0; --di) {
+                    // element column (ox + 1 - di, oy + 1 - dj); the node is its corner (di, dj)
+                    const int le = (oy + 1 - dj) * EX + (ox + 1 - di);
+                    const int a = di + 2 * dj;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) s[c] += sq[(a * 3 + c) * EC + le];
+                }
+            const int64_t d0 = 3 * (I + int64_t(nx + 1) * (J + int64_t(ny + 1) * k));
+            if (node_fixed(support, nx, ny, nz, I, J, k)) {
+                s[0] = xo[0];
+                s[1] = xo[1];
+                s[2] = xo[2];
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float o;
+                if (P.mode == EPI_APPLY) {
+                    o = s[c];
+                    if (want_dot) pdT += o * xo[c];
+                } else if (P.mode == EPI_RESID) {
+                    o = __ldg(P.b + d0 + c) - s[c];
+                    if (want_dot) pdT += o * o;
+                } else {
+                    const float bb = __ldg(P.b + d0 + c);
+                    o = xo[c] + omF * ((bb - s[c]) * __ldg(P.idiag + d0 + c));
+                    if (want_dot) pdT += o * bb;
+                }
+                P.y[d0 + c] = o;
+            }
+        }
+    }
+
+    // per-CTA partials; the last CTA finishes the dot and the alpha entry in a fixed order
+    if (!want_dot && !P.with_alpha) return;
+    const unsigned nblk = gridDim.x, blk = blockIdx.x;
+    const double bd = fused_cta_sum<NT>(double(pdT), sred);
+    const double ba = fused_cta_sum<NT>(double(paT), sred);
+    if (t == 0) {
+        P.partials[blk] = bd;
+        P.partials[nblk + blk] = ba;
+        __threadfence();
+        s_last = atomicAdd(&P.sc->counter[0], 1u) == nblk - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double td = 0.0, ta = 0.0;
+    for (int q = t; q < int(nblk); q += NT) {
+        td += ((volatile double*)P.partials)[q];
+        ta += ((volatile double*)P.partials)[nblk + q];
+    }
+    double sd = fused_cta_sum<NT>(td, sred);
+    const double sa = fused_cta_sum<NT>(ta, sred);
+    if (t != 0) return;
+    P.sc->counter[0] = 0u;
+    if (P.with_alpha) {
+        const int64_t n = P.n;
+        double o;
+        if (P.mode == EPI_APPLY) {
+            o = sa;
+            sd += o * double(xa);
+        } else if (P.mode == EPI_RESID) {
+            o = double(P.b[n]) - sa;
+            sd += o * o;
+        } else {
+            const double bb = double(P.b[n]);
+            o = double(xa) + om * ((bb - sa) * double(P.idiag[n]));
+            sd += o * bb;
+        }
+        P.y[n] = float(o);
+    }
+    if (want_dot) P.sc->red[P.dot_slot] = sd;
+}
+
+// ------------------------------------------------------------------------------------------------
+// tile plans
+// ------------------------------------------------------------------------------------------------
+// Kernel variants: threads per CTA and the resident CTAs per SM asked of the register allocator.
+static const int kFusedVariants[][2] = {{256, 1}, {256, 2}, {128, 3}, {128, 4}, {256, 3}, {128, 6}};
+constexpr int kFusedNumVariants = int(sizeof(kFusedVariants) / sizeof(kFusedVariants[0]));
+// Candidate owner tiles (TX x TY node columns) per CTA size: (TX + 1)(TY + 1) element columns must
+// fit the CTA's threads and the staged plane, 3 (TX + 2)(TY + 2) floats, its staging slots.
+static const int kTiles256[][2] = {{31, 7}, {15, 15}, {26, 8}, {21, 10}, {43, 4}, {63, 3}};
+static const int kTiles128[][2] = {{15, 7}, {31, 3}, {20, 5}, {24, 4}, {7, 15}, {10, 10}};
+constexpr int kFusedNumTiles = 6;
+
+// Candidate c: variant c / kFusedNumTiles, tile c % kFusedNumTiles of that variant's CTA size.
+FusedPlan fused_plan(const Geom& G, int cand) {
+    FusedPlan p{};
+    const int tile = cand % kFusedNumTiles;
+    p.var = cand / kFusedNumTiles;
+    const int nt = kFusedVariants[p.var][0], per_sm = kFusedVariants[p.var][1];
+    p.TX = nt == 256 ? kTiles256[tile][0] : kTiles128[tile][0];
+    p.TY = nt == 256 ? kTiles256[tile][1] : kTiles128[tile][1];
+    p.gx = (G.nx + 1 + p.TX - 1) / p.TX;
+    p.gy = (G.ny + 1 + p.TY - 1) / p.TY;
+    const int planes = G.nz + 1;
+    const int tiles = p.gx * p.gy;
+    // chunk length: with per_sm resident CTAs per SM a launch takes about waves x (DZ + 1) plane
+    // steps; take the shortest, then the fewest CTAs
+    double best = 1e300;
+    p.DZ = planes;
+    for (int dz = std::max(1, std::min(planes, 2)); dz <= planes; ++dz) {
+        const int gz = (planes + dz - 1) / dz;
+        if (dz > 1 && (planes + dz - 2) / (dz - 1) == gz && dz != planes) continue;  // same split, shorter dz
+        const double waves = double((int64_t(tiles) * gz + 152 * per_sm - 1) / (152 * per_sm));
+        const double cost = waves * (dz + 1);
+        if (cost < best - 1e-9) {
+            best = cost;
+            p.DZ = dz;
+        }
+    }
+    p.gz = (planes + p.DZ - 1) / p.DZ;
+    return p;
+}
+
+int fused_num_plans() { return kFusedNumVariants * kFusedNumTiles; }
+
+int fused_blocks(const FusedPlan& p) { return p.gx * p.gy * p.gz; }
+
+int fused_threads(const FusedPlan& p) { return kFusedVariants[p.var][0]; }
+
+// plan used until the autotuner has timed the candidates (and for grids it does not tune): fewest
+// plane steps per SM (waves x (DZ + 1) / resident CTAs), then fewest element columns computed
+int fused_default_plan(const Geom& G) {
+    int best = 0;
+    double bc = 1e300;
+    for (int c = 0; c < fused_num_plans(); ++c) {
+        const FusedPlan p = fused_plan(G, c);
+        const int per_sm = kFusedVariants[p.var][1];
+        const int blocks = fused_blocks(p);
+        const double waves = double((blocks + 152 * per_sm - 1) / (152 * per_sm));
+        const double cols = double(p.gx) * (p.TX + 1) * p.gy * (p.TY + 1);
+        const double cost = waves * (p.DZ + 1) / per_sm * 1e9 + cols * (p.DZ + 1) / p.DZ;
+        if (cost < bc) {
+            bc = cost;
+            best = c;
+        }
+    }
+    return best;
+}
+
+static size_t fused_smem_bytes(const FusedPlan& p, bool s) {
+    const int SF = 3 * (p.TX + 2) * (p.TY + 2);
+    const int EC = (p.TX + 1) * (p.TY + 1);
+    return sizeof(float) * (size_t((s ? 4 : 2) * SF) + size_t(12 * EC));
+}
+
+template <int MODE>
+static void fused_launch(const FusedPlan& p, int blocks, size_t smem, const FusedArgs& P, cudaStream_t st) {
+    switch (p.var) {
+        case 0: k_fused_f32<MODE, 256, 1><<<blocks, 256, smem, st>>>(P); break;
+        case 1: k_fused_f32<MODE, 256, 2><<<blocks, 256, smem, st>>>(P); break;
+        case 2: k_fused_f32<MODE, 128, 3><<<blocks, 128, smem, st>>>(P); break;
+        case 3: k_fused_f32<MODE, 128, 4><<<blocks, 128, smem, st>>>(P); break;
+        case 4: k_fused_f32<MODE, 256, 3><<<blocks, 256, smem, st>>>(P); break;
+        default: k_fused_f32<MODE, 128, 6><<<blocks, 128, smem, st>>>(P); break;
+    }
+}
+
+void fused_fine_f32(const FusedPlan& p, DevScalars* sc, double* partials, int64_t partials_len, const Geom& G,
+                    const KeHat& kh, const float* w, const float* d, const float* u, const ApplyArgs& a,
+                    cudaStream_t st) {
+    const bool s = d != nullptr;
+    const int nt = fused_threads(p);
+    if ((p.TX + 1) * (p.TY + 1) > nt || 3 * (p.TX + 2) * (p.TY + 2) > FSLOT * nt)
+        fail(PBM_EINVAL, "fused operator: tile does not fit the CTA");
+    const int blocks = fused_blocks(p);
+    if (2 * int64_t(blocks) > partials_len) fail(PBM_EINVAL, "grid too large for the partials buffer");
+    FusedArgs P{};
+    P.nx = G.nx;
+    P.ny = G.ny;
+    P.nz = G.nz;
+    P.support = G.support;
+    P.TX = p.TX;
+    P.TY = p.TY;
+    P.DZ = p.DZ;
+    P.gx = p.gx;
+    P.gy = p.gy;
+    P.n = G.n();
+    P.x = (const float*)a.x;
+    P.u = u;
+    P.w = w;
+    P.d = d;
+    P.y = (float*)a.y;
+    P.b = (const float*)a.b;
+    P.idiag = (const float*)a.diag;
+    P.omega = a.omega;
+    P.mode = a.mode;
+    P.with_alpha = (s && a.with_alpha) ? 1 : 0;
+    P.dot_slot = a.dot_slot;
+    for (int c = 0; c < 3; ++c)
+        for (int q = 0; q < 8; ++q) P.K.dg[c][q] = float(kh.dg[c][q]);
+    for (int b = 0; b < 2; ++b) {
+        P.K.lam4[b] = float(kh.lam4[b]);
+        P.K.mu4[b] = float(kh.mu4[b]);
+    }
+    P.partials = partials;
+    P.sc = sc;
+    const size_t smem = fused_smem_bytes(p, s);
+    if (s) fused_launch<2>(p, blocks, smem, P, st);
+    else fused_launch<0>(p, blocks, smem, P, st);
+    PBM_LAUNCH("fused FP32 fine operator");
+}
+
+}  // namespace pbm

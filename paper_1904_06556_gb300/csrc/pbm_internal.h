@@ -242,6 +242,7 @@ struct pbm_grid {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t mr_graph[8] = {};
     int fineL[2][2] = {};                  // autotuned chunk length [fp32][op_s] of the fine column pass
+    int fusedP[2] = {};                    // autotuned tile plan [op_s] of the single-pass FP32 operator
     int64_t mr_graph_kernels[8] = {};      // kernels in one iteration of each graph (launch counting)
     std::vector<int> prof_op;              // operator of every recorded launch
 };
@@ -270,6 +271,8 @@ struct ApplyArgs {
 // fine level: K(w) (u == nullptr) or S (u, d given; w = rho')
 void launch_fine(pbm_grid* g, bool fp32, const void* w, const void* d, const void* u, const ApplyArgs& a,
                  cudaStream_t st);
+// operator of level k (fine: K(rho) or S from the handle's data; coarse: the Galerkin matrices)
+void level_apply(pbm_grid* g, int k, bool fp32, bool op_s, const ApplyArgs& a0, cudaStream_t st);
 // coarse level k >= 1: explicit element matrices (+ border for S)
 void launch_coarse(pbm_grid* g, int k, bool fp32, const ApplyArgs& a, cudaStream_t st);
 // Jacobi diagonal of a level (S or K), written to L[k].diag64 / diag32 (n + 1, last = alpha)
@@ -433,6 +436,19 @@ void cols_fine(pbm_grid* g, const T* w, const T* d, const T* what, const T* u, c
 template <class T>
 void cols_coarse(pbm_grid* g, int k, const T* A, const T* bord, const ApplyArgs& a, cudaStream_t st);
 void launch_what_hat(pbm_grid* g, cudaStream_t st);
+// single-pass FP32 fine operator (fused.cu): tile plan of candidate `cand` for a grid, and the launch
+struct FusedPlan {
+    int TX, TY, DZ, gx, gy, gz;
+    int var;   // kernel variant (threads per CTA, resident CTAs per SM)
+};
+FusedPlan fused_plan(const Geom& G, int cand);
+int fused_num_plans();
+int fused_default_plan(const Geom& G);
+int fused_blocks(const FusedPlan& p);
+int fused_threads(const FusedPlan& p);
+void fused_fine_f32(const FusedPlan& p, DevScalars* sc, double* partials, int64_t partials_len, const Geom& G,
+                    const KeHat& kh, const float* w, const float* d, const float* u, const ApplyArgs& a,
+                    cudaStream_t st);
 void cols_cost(const Geom& G, int L, bool op_s, bool recompute_w, int mode, int esize, double& bytes, double& flops);
 // chunk length the handle uses for the fine column pass of (precision, operator)
 int fine_L(const pbm_grid* g, bool fp32, bool op_s);

@@ -123,6 +123,93 @@ def test_apply_K_fp32(pkg, dims, bc):
     assert rel(y, ref) < 2e-6
 
 
+def _f32(a):
+    """The FP32 rounding of an FP64 array, in FP64 (the inputs the FP32 kernels actually see)."""
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def _check_epilogues(G, op, A_apply, diag, x, b, tol):
+    """The three fused epilogues of one FP32 fine-level launch against the oracle's operator `A_apply`
+    (FP64, applied to the FP32-rounded inputs) and the dots they reduce."""
+    xr, br = _f32(x), _f32(b)
+    omega = G.info()["omega"][0]
+    ax = A_apply(xr)
+    y, dot = G.apply_fine_f32(op, "apply", dev(x, torch.float32), dot=True)
+    y = host(y)
+    assert rel(y, ax) < tol
+    assert abs(dot - y @ xr) <= 1e-5 * np.abs(y * xr).sum()
+    y2, _ = G.apply_fine_f32(op, "apply", dev(x, torch.float32))
+    assert np.array_equal(host(y2), y)                     # deterministic
+    r, dot = G.apply_fine_f32(op, "resid", dev(x, torch.float32), dev(b, torch.float32), dot=True)
+    r = host(r)
+    assert rel(r, br - ax) < tol
+    assert abs(dot - r @ r) <= 1e-5 * (r @ r)
+    j, dot = G.apply_fine_f32(op, "jacobi", dev(x, torch.float32), dev(b, torch.float32), dot=True)
+    j = host(j)
+    assert rel(j, xr + omega * (br - ax) / diag) < tol
+    assert abs(dot - j @ br) <= 1e-5 * np.abs(j * br).sum()
+
+
+@pytest.mark.parametrize("dims,bc", [((8, 4, 4), "cantilever"), ((34, 10, 6), "bridge_corners"),
+                                     ((64, 20, 12), "cantilever")])
+def test_fused_fp32_K_epilogues_and_jacobi_diagonal(pkg, dims, bc):
+    """The single-pass FP32 operator (several CTA tiles and chunks, ragged edges) with each fused
+    epilogue, and the Jacobi diagonal of K (bit-level FP64 set-up) against the oracle's CSR K."""
+    g = fem.Grid(*dims, bc)
+    rng = np.random.default_rng(sum(dims))
+    rho = rng.uniform(1e-3, 1.0, g.m)
+    G = pkg.Grid(*dims, levels_for(*dims), bc, precision="mixed")
+    G.set_density(dev(rho))
+    G.vcycle("K", dev(rng.standard_normal(g.n)))          # builds the K(rho) hierarchy
+    K = fem.assemble_K(g, rho, fem.element_stiffness())
+    dg = host(G.diag(0))
+    assert rel(dg[:g.n], K.diagonal()) < 1e-13
+    _check_epilogues(G, "K", lambda v: K @ v, K.diagonal(), rng.standard_normal(g.n), rng.standard_normal(g.n),
+                     2e-6)
+
+
+@pytest.mark.parametrize("dims,bc,seed", [((8, 4, 4), "cantilever", 0), ((34, 10, 6), "bridge_corners", 3),
+                                          ((64, 20, 12), "cantilever", 4)])
+def test_fused_fp32_S_epilogues_and_jacobi_diagonal(pkg, dims, bc, seed):
+    """The same for S of eq. (S): the rank-one terms recomputed from u in every launch, the alpha row
+    counted once per element across CTA tiles and chunks, and the Jacobi diagonal of S."""
+    pb, st, d = make_problem(*dims, bc, seed, 0.5)
+    G = pkg.Grid(*dims, levels_for(*dims), bc, precision="mixed")
+    G.set_state(state_dev(d))
+    cf = pbm.coeffs(pb, st)
+    S = pbm.assemble_S(pb, st, cf)
+    dg = host(G.diag(0))
+    assert rel(dg, S.diagonal()) < 1e-12
+    rng = np.random.default_rng(seed + 7)
+    _check_epilogues(G, "S", lambda v: pbm.apply_S_elementwise(pb, st, cf, v), S.diagonal(),
+                     rng.standard_normal(pb.n + 1), rng.standard_normal(pb.n + 1), 1e-5)
+
+
+@pytest.mark.parametrize("dims,bc,seed", [((34, 10, 6), "bridge_corners", 9), ((64, 20, 12), "cantilever", 10)])
+def test_fused_fp32_every_tile_plan(pkg, dims, bc, seed):
+    """Every tile plan of the FP32 operator (CTA sizes, tiles, chunk lengths) gives the oracle's K x and
+    S x, including the alpha row assembled from per-CTA partial sums."""
+    pb, st, d = make_problem(*dims, bc, seed, 0.5)
+    G = pkg.Grid(*dims, levels_for(*dims), bc, precision="mixed")
+    G.set_state(state_dev(d))
+    cf = pbm.coeffs(pb, st)
+    x = np.random.default_rng(seed).standard_normal(pb.n + 1)
+    ref = pbm.apply_S_elementwise(pb, st, cf, _f32(x))
+    for plan in range(pkg.fp32_plan_count()):
+        G.set_fp32_plan("S", plan)
+        y, _ = G.apply_fine_f32("S", "apply", dev(x, torch.float32))
+        assert rel(host(y), ref) < 1e-5, plan
+    g = fem.Grid(*dims, bc)
+    K = fem.assemble_K(g, d["rho"], fem.element_stiffness())
+    G.set_density(dev(d["rho"]))
+    G.vcycle("K", dev(pb.f))
+    refk = K @ _f32(x[:g.n])
+    for plan in range(pkg.fp32_plan_count()):
+        G.set_fp32_plan("K", plan)
+        y, _ = G.apply_fine_f32("K", "apply", dev(x[:g.n], torch.float32))
+        assert rel(host(y), refk) < 2e-6, plan
+
+
 # ------------------------------------------------------------------------------------------------
 # S, rhs, compliances
 # ------------------------------------------------------------------------------------------------
