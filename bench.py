@@ -52,7 +52,9 @@ METRIC = "reduced-Newton MG-MINRES solve time & K(ρ)u GB/s; FP32-mixed vs FP64"
 UNIT = "reduced-Newton solves/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 PROFILE_DIR = os.path.join(ROOT, "profiles")
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_1904_06556_gb300", "csrc", f) for f in ("colpass.cu", "pbm_internal.h")]
+# sources of the fine-level S kernels whose ncu traffic a committed profile may quote, per precision
+KERNEL_SOURCES = {p: [os.path.join(ROOT, "paper_1904_06556_gb300", "csrc", f) for f in (src, "pbm_internal.h")]
+                  for p, src in (("fp64", "colpass.cu"), ("mixed", "fused.cu"))}
 # FP64 issue rate of GB300 derived from the nominal 1.25 TFLOP/s (FMA = 2 flops), 152 SMs, 2070 MHz:
 # 1.25e12 / (2 * 152 * 2.07e9) = 2 FP64 instructions per clock per SM, i.e. 629 G FP64 operations/s.
 FP64_OPS_PEAK = 2.0 * 152 * 2.07e9
@@ -149,15 +151,15 @@ def measured_peaks():
         return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
 
 
-def kernel_hash() -> str:
+def kernel_hash(precision: str) -> str:
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in KERNEL_SOURCES[precision]:
         with open(p, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name: str):
+def profiled_traffic(name: str, precision: str):
     """DRAM bytes per launch of the named kernel from the committed ncu summary under profiles/, if it was taken
     on the current kernel source (its `kernel_source_sha` line matches); else None."""
     path = os.path.join(PROFILE_DIR, name)
@@ -168,7 +170,7 @@ def profiled_traffic(name: str):
         return None
     m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
     m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not m_sha or not m_tr or m_sha.group(1) != kernel_hash():
+    if not m_sha or not m_tr or m_sha.group(1) != kernel_hash(precision):
         return None
     return float(m_tr.group(1))
 
@@ -336,13 +338,12 @@ def run_ours(args):
         achieved = prof["bytes"] / (prof["total_ms"] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{peak_src} (MEASURED_PEAKS hbm_gbs)",
-                "kernel": ("fine-level S operator: k_cols_fine<float, 2> (element columns, W_e recomputed from u) + "
-                           "k_nodes<float> (node sums with the fused residual / Jacobi / dot epilogues), timed as one "
-                           "launch pair")}
+                "kernel": ("fine-level S operator: k_fused_f32<2, threads, CTAs per SM> (single pass: element "
+                           "columns with W_e recomputed from u, node sums, fused residual / Jacobi / dot epilogues)")}
     roof.update({"launches": prof["launches"], "avg_launch_us": avg_ms * 1e3,
                  "bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
                  "ops_per_launch": prof["flops"] / max(prof["launches"], 1)})
-    tr = profiled_traffic(f"fine_S_apply_{precision}_{w.name}.md")
+    tr = profiled_traffic(f"fine_S_apply_{precision}_{w.name}.md", precision)
     roof["traffic"] = tr
 
     out = {
@@ -459,6 +460,62 @@ def run_batch(args):
            "iterations_batched": [x["iterations"] for x in ib], "iterations_one_by_one": [x["iterations"] for x in i1],
            "max_relres_batched": max(x["relres"] for x in ib)}
     B.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_pbm(args):
+    """A complete PBM run (Algorithm 1, pbm_solve) from the paper's initial point on the workload's grid: the
+    large full-PBM workload (256 x 128 x 128 cantilever, distributed end load, vf 0.15, 7 levels) or any other
+    grid. Reports the total time, the outer / Newton / MINRES counts, the compliance and the fine-level
+    K(rho) x roofline at that size; with --compare-fp64 the same run with the FP64 path and the relative
+    difference of the compliances. Rank 0 only (replicas otherwise do the same run)."""
+    import torch
+
+    import paper_1904_06556_gb300 as pkg
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synthetic.WORKLOADS[args.workload]
+    f = torch.as_tensor(synthetic.load_vector(w.nx, w.ny, w.nz, w.loads[0]), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def one_run(precision):
+        with pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=precision) as G:
+            st = G.initial_state(w.n, w.m, w.V, w.rho_lo, w.rho_up, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = G.pbm_solve(st, f, check=False)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            rho = st["rho"]
+            kap = k_apply_rates(G, w, rho.cpu().numpy(), dev, flush) if precision == args.precision else None
+        return secs, info, kap, float(rho.sum().item())
+
+    secs, info, kap, vol = one_run(args.precision)
+    peaks, peak_src = measured_peaks()
+    out = {"metric": METRIC + " (full PBM run)", "value": secs, "unit": "s per PBM run", "n_gpus": world,
+           "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+           "data": "synthetic (seeded; the paper's cantilever example, Section 6)",
+           "config": dict(workload_desc(w, args.precision),
+                          workload=f"{w.name}: {w.nx}x{w.ny}x{w.nz} Q1 hex {w.bc}, {args.precision}, complete PBM "
+                                   f"run from the paper's initial point (eps_pbm 1e-5)"),
+           "pbm": {k: info[k] for k in ("rc", "status", "outer", "newton", "minres", "gap_ratio", "compliance",
+                                        "volume", "eps_mr")},
+           "volume_fraction_final": vol / w.m,
+           "k_apply": kap,
+           "k_apply_roofline_fp32": {"bound": "hbm", "achieved": kap["fp32"]["gbs_flushed"],
+                                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                     "frac": kap["fp32"]["gbs_flushed"] / peaks["hbm_gbs"],
+                                     "peak_source": peak_src}}
+    if args.compare_fp64:
+        s64, i64, _, _ = one_run("fp64" if args.precision == "mixed" else "mixed")
+        out["other_precision"] = {"seconds": s64, "outer": i64["outer"], "newton": i64["newton"],
+                                  "minres": i64["minres"], "compliance": i64["compliance"],
+                                  "compliance_rel_diff": abs(info["compliance"] - i64["compliance"]) /
+                                  abs(i64["compliance"])}
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -585,7 +642,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="cant64", choices=["cant64", "bridge128", "cant32", "cant16", "batch48"])
+    ap.add_argument("--workload", default="cant64",
+                    choices=["cant64", "bridge128", "cant32", "cant16", "cant256", "batch48"])
+    ap.add_argument("--pbm", action="store_true", help="time one complete PBM run (Algorithm 1) on the workload")
+    ap.add_argument("--compare-fp64", action="store_true", help="with --pbm: also run the other precision")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=30.0)
@@ -596,6 +656,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch48":
         run_batch(args)
+    elif args.pbm:
+        run_pbm(args)
     else:
         run_ours(args)
 

@@ -156,10 +156,21 @@ static void lanczos_level(pbm_grid* g, int k, bool op_s, cudaStream_t st) {
     const int steps = g->desc.lanczos_steps;
     launch_inverse_sqrt(L.diag64, L.sdiag64, nv, st);
     lz_start(g, v, t, vp, L.sdiag64, nv, st);
-    // a_j = (A t) . t with t = D^{-1/2} v is the operator launch's fused dot product
+    // a_j = (A t) . t with t = D^{-1/2} v is the operator launch's fused dot product. Mixed grids
+    // apply the FP32 operators the smoother will use (the weight is an estimate; the Lanczos
+    // vectors and scalars stay FP64); FP64 grids the FP64 ones.
+    const bool op32 = g->desc.precision == PBM_MIXED;
+    float* t32 = op32 ? g->kv32[7] : nullptr;
+    float* w32 = op32 ? g->kv32[8] : nullptr;
     const int slot = 40;
     for (int j = 0; j < steps; ++j) {
-        level_apply(g, k, false, op_s, args(t, w, EPI_APPLY, nullptr, nullptr, nullptr, slot), st);
+        if (op32) {
+            launch_cast(t, false, t32, true, nv, st);
+            level_apply(g, k, true, op_s, args(t32, w32, EPI_APPLY, nullptr, nullptr, nullptr, slot), st);
+            launch_cast(w32, true, w, false, nv, st);
+        } else {
+            level_apply(g, k, false, op_s, args(t, w, EPI_APPLY, nullptr, nullptr, nullptr, slot), st);
+        }
         PBM_CUDA(cudaMemcpyAsync(&g->sc->lz_a[j], &g->sc->red[slot], sizeof(double), cudaMemcpyDeviceToDevice, st));
         lz_b(g, w, v, vp, L.sdiag64, nv, j, st);
         lz_next(g, w, v, vp, t, L.sdiag64, nv, j, st);
