@@ -520,6 +520,59 @@ def run_pbm(args):
         print(json.dumps(out), flush=True)
 
 
+def run_plans(args):
+    """Times every tile plan of the single-pass FP32 operator (pbm_set_fp32_plan) on the workload's grid, K and S
+    with the apply epilogue: median of 20 launches with the L2 flushed before each (CUDA events). Prints one JSON
+    line per plan and operator."""
+    import torch
+
+    import paper_1904_06556_gb300 as pkg
+
+    _, rank, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synthetic.WORKLOADS[args.workload]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision="mixed")
+    G.set_density(torch.as_tensor(synthetic.density_for(w), dtype=torch.float64, device=dev))
+    G.vcycle("K", torch.zeros(w.n, dtype=torch.float64, device=dev))
+    x = torch.randn(w.n + 1, dtype=torch.float32, device=dev)
+
+    def med_us(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(20):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) * 1e3)
+        return statistics.median(ts)
+
+    st_h = synthetic.synthetic_state(w, np.zeros(w.n))
+    sd = {k: torch.as_tensor(st_h[k], dtype=torch.float64, device=dev) for k in ("nu_lo", "nu_up", "rho", "mu_lo",
+                                                                                   "mu_up")}
+    sd["u"] = 1e-2 * torch.randn(w.n, dtype=torch.float64, device=dev)
+    sd.update({k: float(st_h[k]) for k in ("alpha", "p", "q_lo", "q_up", "V", "rho_lo", "rho_up")})
+    peaks, _ = measured_peaks()
+    for op, nv, byt in (("K", w.n, (2 * w.n + w.m) * 4), ("S", w.n + 1, (3 * w.n + 2 * w.m) * 4)):
+        if op == "S":
+            G.set_state(sd)
+        for plan in range(pkg.fp32_plan_count()):
+            G.set_fp32_plan(op, plan)
+            us = med_us(lambda: G.apply_fine_f32(op, "apply", x[:nv]))
+            tile = G.info()["fp32_tile"][0 if op == "K" else 1]
+            print(json.dumps({"workload": w.name, "op": op, "plan": plan, "tile_TX_TY_DZ_threads": tile[:4],
+                              "us_flushed": us, "gbs": byt / us / 1e3, "frac_of_hbm": byt / us / 1e3 /
+                              peaks["hbm_gbs"]}), flush=True)
+    G.close()
+
+
 def k_apply_rates(G, w, rho, dev, flush):
     """Standalone fine-level K(rho) x in FP64 and FP32 at the workload size: algorithmic GB/s = (2n + m) b /
     kernel time, with the L2 flushed before every launch and warm (back to back)."""
@@ -646,6 +699,8 @@ def main():
                     choices=["cant64", "bridge128", "cant32", "cant16", "cant256", "batch48"])
     ap.add_argument("--pbm", action="store_true", help="time one complete PBM run (Algorithm 1) on the workload")
     ap.add_argument("--compare-fp64", action="store_true", help="with --pbm: also run the other precision")
+    ap.add_argument("--fp32-plans", action="store_true",
+                    help="time every tile plan of the FP32 fine operator on the workload's grid")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=30.0)
@@ -658,6 +713,8 @@ def main():
         run_batch(args)
     elif args.pbm:
         run_pbm(args)
+    elif args.fp32_plans:
+        run_plans(args)
     else:
         run_ours(args)
 

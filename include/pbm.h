@@ -317,8 +317,10 @@ int pbm_compliance_grad(pbm_grid* g, const double* u_dev, double* c_dev, const d
  * threads). Lets a caller count the device work of a region of code. Never fails. */
 int64_t pbm_kernel_launches(void);
 
-/* on != 0: from now on, bracket every fine-level operator launch of `g` with a pair of CUDA events
- * on its stream (adds two event records per launch; off by default). on == 0: stop. */
+/* on != 0: from now on, bracket every fine-level operator launch of `g` in its working precision
+ * (FP64 grids: the FP64 kernels; PBM_MIXED grids: the FP32 kernels of the inner solves, not the
+ * FP64 residual applies of the refinement) with a pair of CUDA events on its stream (two event
+ * records per launch; off by default). on == 0: stop. */
 int pbm_profile(pbm_grid* g, int on);
 
 /* Copies the statistics of operator `op` (PBM_OP_K: the K(w) kernel, PBM_OP_S: the S kernel)
@@ -330,8 +332,7 @@ int pbm_profile_read(pbm_grid* g, int op, pbm_profile_stats* out);
  * A batch advances several independent systems (grid handles of any sizes, FP64 or all mixed, with
  * the same smoothing sweeps) together: every stage of the MINRES iteration and the V-cycle is one
  * launch over all systems' work, and the iteration runs as a CUDA-graph loop until every system has
- * finished. This is the benchmark spec's batching of design instances and load cases; each system keeps
- * its own hierarchy, scratch and scalars, so the results equal those of separate solves up to the
+ * finished: many design instances and load cases solved together. Each system keeps its own hierarchy, scratch and scalars, so the results equal those of separate solves up to the
  * iteration at which each system stops. */
 typedef struct pbm_batch pbm_batch;
 

@@ -3,7 +3,7 @@
 Written from Section 3 of the paper. Variables xi = (u, alpha, nu_lo, nu_up); multipliers (rho, mu_lo, mu_up);
 penalties p, q_lo, q_up (scalars: they start at 1 and are updated uniformly, Algorithm 1).
 
-Readings of the paper taken here (each one is listed in the design doc):
+Readings of the paper taken here, where it is silent or inconsistent (the CUDA path takes the same ones):
   * tau_hat = -1/2 in eq. (103.1) (the "pure logarithmic branch" the paper says it uses).
   * The nu-gradient signs are derived from the augmented Lagrangian eq. (aug_lagr) itself:
         dL/dnu_lo_i = -rho_lo_i + rho'_i - mu'_lo_i,     dL/dnu_up_i = rho_up_i - rho'_i - mu'_up_i

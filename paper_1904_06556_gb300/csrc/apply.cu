@@ -440,7 +440,9 @@ static void set_epi(MarchParams<T>& P, const ApplyArgs& a) {
 void launch_fine(pbm_grid* g, bool fp32, const void* w, const void* d, const void* u, const ApplyArgs& a,
                  cudaStream_t st) {
     const bool s = u != nullptr;
-    if (g->prof_on) prof_begin(g, st);
+    // profiling times the operator kernel of the grid's working precision (FP32 on mixed grids)
+    const bool prof = g->prof_on && fp32 == (g->desc.precision == PBM_MIXED);
+    if (prof) prof_begin(g, st);
     if (fp32)
         fused_fine_f32(fused_plan(g->L[0].g, g->fusedP[s ? 1 : 0]), g->sc, g->partials, int64_t(8) * g->max_blocks,
                        g->L[0].g, g->kehat, (const float*)w, s ? (const float*)d : nullptr,
@@ -448,7 +450,7 @@ void launch_fine(pbm_grid* g, bool fp32, const void* w, const void* d, const voi
     else
         cols_fine<double>(g, (const double*)w, s ? (const double*)d : nullptr, s ? g->what_hat : nullptr, nullptr, a,
                           st);
-    if (g->prof_on) {
+    if (prof) {
         double bytes = 0.0, flops = 0.0;
         cols_cost(g->L[0].g, fine_L(g, fp32, s), s, fp32, a.mode, fp32 ? 4 : 8, bytes, flops);
         prof_end(g, st, s ? PBM_OP_S : PBM_OP_K, bytes, flops);

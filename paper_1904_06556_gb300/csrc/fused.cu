@@ -44,16 +44,16 @@ struct FusedArgs {
     DevScalars* sc;
 };
 
-// transformed xy quad of the element column at staged coordinates (lx, ly) of a staged plane,
-// supported nodes masked
-__device__ __forceinline__ void fused_quad(const float* __restrict__ s, int RW, int lx, int ly, const bool (&fx)[4],
-                                           float (&Q)[3][4]) {
+// transformed xy quad of the element column at staged coordinates (lx, ly) of a staged plane
+// (nodes as float4, supported nodes already zero)
+__device__ __forceinline__ void fused_quad(const float4* __restrict__ s, int NW, int lx, int ly, float (&Q)[3][4]) {
     float v[3][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        const float* p = s + (ly + (a >> 1)) * RW + 3 * (lx + (a & 1));
-#pragma unroll
-        for (int c = 0; c < 3; ++c) v[c][a] = fx[a] ? 0.0f : p[c];
+        const float4 p = s[(ly + (a >> 1)) * NW + lx + (a & 1)];
+        v[0][a] = p.x;
+        v[1][a] = p.y;
+        v[2][a] = p.z;
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -80,23 +80,30 @@ __device__ __forceinline__ double fused_cta_sum(double v, double* sh) {
     return s;
 }
 
+// Support of node (i, j) as two bits: bit 0 fixed on planes k >= 1, bit 1 fixed on plane 0. Every
+// support of node_fixed depends on the plane only through k == 0.
+__device__ __forceinline__ int fixed_bits(int support, int nx, int ny, int nz, int i, int j) {
+    return (node_fixed(support, nx, ny, nz, i, j, 1) ? 1 : 0) | (node_fixed(support, nx, ny, nz, i, j, 0) ? 2 : 0);
+}
+
 // MODE 0: K(w) x. MODE 2: S x with W_e = Khat H u_e recomputed from the staged u. NT threads per
 // CTA, MINB resident CTAs per SM requested from the register allocator.
 template <int MODE, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
     constexpr bool S = MODE == 2;
     extern __shared__ float4 fused_smem4[];
-    float* smem = reinterpret_cast<float*>(fused_smem4);
     __shared__ double sred[NT / 32];
     __shared__ bool s_last;
 
     const int TX = P.TX, TY = P.TY, EX = TX + 1, EY = TY + 1;
-    const int RW = 3 * (TX + 2);           // floats per staged row
-    const int SF = RW * (TY + 2);          // floats per staged plane: TY + 2 rows
+    const int NW = TX + 2;                 // staged nodes per row
+    const int SN = NW * (TY + 2);          // staged nodes per plane (float4 each, w unused)
+    const int RW = 3 * NW;                 // floats per row of the global plane
+    const int SF = RW * (TY + 2);          // floats staged per plane
     const int EC = EX * EY;
-    float* sx = smem;                      // 2 planes of x
-    float* su = smem + 2 * SF;             // 2 planes of u (S)
-    float* sq = smem + (S ? 4 : 2) * SF;   // 12 x EC corner values of the element columns
+    float4* sx = fused_smem4;              // 2 planes of x
+    float4* su = fused_smem4 + 2 * SN;     // 2 planes of u (S)
+    float4* sq = fused_smem4 + (S ? 4 : 2) * SN;   // 4 x EC corner values of the element columns
 
     const int t = threadIdx.x;
     const int nx = P.nx, ny = P.ny, nz = P.nz, support = P.support;
@@ -107,16 +114,23 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
     const int kz0 = bz * P.DZ, kz1 = min(kz0 + P.DZ, nz + 1);
     const int64_t plane = 3 * int64_t(nx + 1) * (ny + 1);
 
-    // staging slots: flat index f = t + s NT of the staged plane, row f / RW, float f % RW
-    int gofs[FSLOT];
+    // staging slots: float f = t + s NT of the staged plane (row f / RW, float f % RW of the row),
+    // its offset in the global plane, its place in shared memory and the support bits of its node
+    int gofs[FSLOT], sidx[FSLOT];
+    int fbits = 0;
 #pragma unroll
     for (int s = 0; s < FSLOT; ++s) {
         const int f = t + s * NT;
         gofs[s] = -2;
+        sidx[s] = 0;
         if (f < SF) {
             const int row = f / RW, o = f - row * RW;
-            const int gxn = X0 - 1 + o / 3, gyn = Y0 - 1 + row;
-            gofs[s] = (gxn >= 0 && gxn <= nx && gyn >= 0 && gyn <= ny) ? 3 * (gxn + (nx + 1) * gyn) + o % 3 : -1;
+            const int lxn = o / 3, c = o - 3 * lxn;
+            const int gxn = X0 - 1 + lxn, gyn = Y0 - 1 + row;
+            const bool in = gxn >= 0 && gxn <= nx && gyn >= 0 && gyn <= ny;
+            gofs[s] = in ? 3 * (gxn + (nx + 1) * gyn) + c : -1;
+            sidx[s] = 4 * (row * NW + lxn) + c;
+            if (in) fbits |= fixed_bits(support, nx, ny, nz, gxn, gyn) << (2 * s);
         }
     }
     float px[FSLOT], pu[FSLOT];
@@ -129,14 +143,18 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
             if (S) pu[s] = gofs[s] >= 0 ? __ldg(us + gofs[s]) : 0.0f;
         }
     };
+    // writes the fetched plane k into its buffer, supported nodes zero (the masked vectors the element
+    // matrices act on)
     auto stage = [&](int k) {
-        float* dx = sx + (k & 1) * SF;
-        float* du = su + (k & 1) * SF;
+        float* dx = reinterpret_cast<float*>(sx + (k & 1) * SN);
+        float* du = reinterpret_cast<float*>(su + (k & 1) * SN);
+        const int sh = k == 0 ? 1 : 0;
 #pragma unroll
         for (int s = 0; s < FSLOT; ++s)
             if (gofs[s] != -2) {
-                dx[t + s * NT] = px[s];
-                if (S) du[t + s * NT] = pu[s];
+                const bool fx = (fbits >> (2 * s + sh)) & 1;
+                dx[sidx[s]] = fx ? 0.0f : px[s];
+                if (S) du[sidx[s]] = fx ? 0.0f : pu[s];
             }
     };
 
@@ -149,17 +167,13 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
     const int ox = t % TX, oy = t / TX;
     const int I = X0 + ox, J = Y0 + oy;
     const bool owner = t < TX * TY && I <= nx && J <= ny;
+    const int obits = owner ? fixed_bits(support, nx, ny, nz, I, J) : 0;
 
     const float xa = S ? P.x[P.n] : 0.0f;
     const double om = P.mode == EPI_JACOBI ? *P.omega : 0.0;
     const float omF = float(om);
     const bool want_dot = P.dot_slot >= 0;
     float pdT = 0.0f, paT = 0.0f;
-
-    auto corner_mask = [&](int k, bool (&fx)[4]) {
-#pragma unroll
-        for (int a = 0; a < 4; ++a) fx[a] = node_fixed(support, nx, ny, nz, ex + (a & 1), ey + (a >> 1), k);
-    };
 
     const int kstart = max(kz0 - 1, 0);
     float Qlo[3][4], Ulo[3][4], carry[3][4];
@@ -175,10 +189,8 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
     if (kstart + 1 <= nz) fetch(kstart + 1);
     __syncthreads();
     if (ecol) {
-        bool fx[4];
-        corner_mask(kstart, fx);
-        fused_quad(sx + (kstart & 1) * SF, RW, lx, ly, fx, Qlo);
-        if (S) fused_quad(su + (kstart & 1) * SF, RW, lx, ly, fx, Ulo);
+        fused_quad(sx + (kstart & 1) * SN, NW, lx, ly, Qlo);
+        if (S) fused_quad(su + (kstart & 1) * SN, NW, lx, ly, Ulo);
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -195,19 +207,18 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
             wn = __ldg(P.w + e0 + (k + 1 - kstart) * elayer);
             if (S) dn = __ldg(P.d + e0 + (k + 1 - kstart) * elayer);
         }
-        float xo[3] = {0.0f, 0.0f, 0.0f};
+        // the owner's own x on plane k: staged (masked) unless the node is supported
+        float4 xo4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const bool ofixed = (obits >> (k == 0 ? 1 : 0)) & 1;
+        const int64_t d0 = 3 * (I + int64_t(nx + 1) * (J + int64_t(ny + 1) * k));
         if (owner && k >= kz0) {
-            const float* p = sx + (k & 1) * SF + (oy + 1) * RW + 3 * (ox + 1);
-            xo[0] = p[0];
-            xo[1] = p[1];
-            xo[2] = p[2];
+            if (ofixed) xo4 = make_float4(__ldg(P.x + d0), __ldg(P.x + d0 + 1), __ldg(P.x + d0 + 2), 0.0f);
+            else xo4 = sx[(k & 1) * SN + (oy + 1) * NW + ox + 1];
         }
         float Bq[3][4];
         if (ecol && layer) {
-            bool fx[4];
-            corner_mask(k + 1, fx);
             float Qhi[3][4];
-            fused_quad(sx + ((k + 1) & 1) * SF, RW, lx, ly, fx, Qhi);
+            fused_quad(sx + ((k + 1) & 1) * SN, NW, lx, ly, Qhi);
             float X[3][8], Y[3][8];
 #pragma unroll
             for (int c = 0; c < 3; ++c)
@@ -219,7 +230,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
                 }
             if (S) {
                 float Uhi[3][4], U[3][8], Wt[3][8];
-                fused_quad(su + ((k + 1) & 1) * SF, RW, lx, ly, fx, Uhi);
+                fused_quad(su + ((k + 1) & 1) * SN, NW, lx, ly, Uhi);
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -267,15 +278,18 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
         if (k < kz0) continue;  // the layer below the chunk: only its top face is kept
         // inverse xy transform: the element column's values at its 4 corners of plane k
         if (t < EC) {
+            float o[4][3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const float a0 = Bq[c][0] - Bq[c][1], a1 = Bq[c][0] + Bq[c][1];
                 const float a2 = Bq[c][2] - Bq[c][3], a3 = Bq[c][2] + Bq[c][3];
-                sq[(0 * 3 + c) * EC + t] = a0 - a2;
-                sq[(1 * 3 + c) * EC + t] = a1 - a3;
-                sq[(2 * 3 + c) * EC + t] = a0 + a2;
-                sq[(3 * 3 + c) * EC + t] = a1 + a3;
+                o[0][c] = a0 - a2;
+                o[1][c] = a1 - a3;
+                o[2][c] = a0 + a2;
+                o[3][c] = a1 + a3;
             }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) sq[a * EC + t] = make_float4(o[a][0], o[a][1], o[a][2], 0.0f);
         }
         __syncthreads();  // (b) corner values of plane k complete
         if (owner) {
@@ -285,13 +299,13 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
 #pragma unroll
                 for (int di = 1; di >= 0; --di) {
                     // element column (ox + 1 - di, oy + 1 - dj); the node is its corner (di, dj)
-                    const int le = (oy + 1 - dj) * EX + (ox + 1 - di);
-                    const int a = di + 2 * dj;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) s[c] += sq[(a * 3 + c) * EC + le];
+                    const float4 v = sq[(di + 2 * dj) * EC + (oy + 1 - dj) * EX + (ox + 1 - di)];
+                    s[0] += v.x;
+                    s[1] += v.y;
+                    s[2] += v.z;
                 }
-            const int64_t d0 = 3 * (I + int64_t(nx + 1) * (J + int64_t(ny + 1) * k));
-            if (node_fixed(support, nx, ny, nz, I, J, k)) {
+            const float xo[3] = {xo4.x, xo4.y, xo4.z};
+            if (ofixed) {
                 s[0] = xo[0];
                 s[1] = xo[1];
                 s[2] = xo[2];
@@ -426,9 +440,9 @@ int fused_default_plan(const Geom& G) {
 }
 
 static size_t fused_smem_bytes(const FusedPlan& p, bool s) {
-    const int SF = 3 * (p.TX + 2) * (p.TY + 2);
+    const int SN = (p.TX + 2) * (p.TY + 2);
     const int EC = (p.TX + 1) * (p.TY + 1);
-    return sizeof(float) * (size_t((s ? 4 : 2) * SF) + size_t(12 * EC));
+    return sizeof(float4) * (size_t((s ? 4 : 2) * SN) + size_t(4 * EC));
 }
 
 template <int MODE>
