@@ -216,6 +216,13 @@ int pbm_apply_K_f32(pbm_grid* g, const float* w_dev, const float* x_dev, float* 
 int pbm_apply_fine_f32(pbm_grid* g, int op, int epilogue, const float* x_dev, const float* b_dev, float* y_dev,
                        double* dot_host, void* stream);
 
+/* The same on level `level` of the current hierarchy (0 = fine; level >= 1: the FP32 copy of the
+ * Galerkin operator A_level = P^T A_(level-1) P of Section 5.1, with the alpha border for S, and
+ * that level's Jacobi weight and diagonal). Vectors have n_level (+ 1 for S) entries. Errors as
+ * above, and PBM_EINVAL for a level out of range. */
+int pbm_apply_level_f32(pbm_grid* g, int level, int op, int epilogue, const float* x_dev, const float* b_dev,
+                        float* y_dev, double* dot_host, void* stream);
+
 /* Tile plans of the single-pass FP32 fine operator (CTA size, register budget, TX x TY node columns
  * by DZ planes per CTA; listed by pbm_grid_info_get's fp32_tile). pbm_create_grid times every plan
  * on PBM_MIXED grids and keeps the fastest per operator; pbm_set_fp32_plan overrides that choice

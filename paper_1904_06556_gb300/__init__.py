@@ -91,6 +91,7 @@ class Grid:
         self.nnode = (nx + 1) * (ny + 1) * (nz + 1)
         self.n = 3 * self.nnode
         self.m = nx * ny * nz
+        self._level_n = [3 * ((nx >> k) + 1) * ((ny >> k) + 1) * ((nz >> k) + 1) for k in range(levels)]
         self._keep = []
 
     # --------------------------------------------------------------------------------------------
@@ -177,13 +178,25 @@ class Grid:
                                                C.byref(d) if dot else None, _stream()))
         return y, (d.value if dot else None)
 
+    def apply_level_f32(self, level: int, op: str, epilogue: str, x: torch.Tensor, b: torch.Tensor | None = None,
+                        out: torch.Tensor | None = None, dot: bool = False):
+        """pbm_apply_level_f32: one FP32 application of level `level`'s operator with a fused epilogue."""
+        f = torch.float32
+        n = self._level_n[level] + (1 if op == "S" else 0)
+        y = out if out is not None else torch.empty(n, dtype=f, device=x.device)
+        d = C.c_double(0.0)
+        self._check(self._L.pbm_apply_level_f32(self._h, level, _lib.OPS[op], _lib.EPILOGUES[epilogue],
+                                                _ptr(x, f, n, "x"), _ptr(b, f, n, "b") if b is not None else None,
+                                                _ptr(y, f, n, "y"), C.byref(d) if dot else None, _stream()))
+        return y, (d.value if dot else None)
+
     def set_fp32_plan(self, op: str, plan: int):
         """Overrides the autotuned tile plan of the FP32 fine operator for op (pbm_set_fp32_plan)."""
         self._check(self._L.pbm_set_fp32_plan(self._h, _lib.OPS[op], int(plan)))
 
     def diag(self, level: int = 0) -> torch.Tensor:
         """Jacobi diagonal (n_level + 1 FP64 entries) of a level of the current hierarchy (pbm_get_diag)."""
-        nl = int(self.info()["n"][level]) + 1
+        nl = self._level_n[level] + 1
         out = torch.empty(nl, dtype=torch.float64, device="cuda")
         self._check(self._L.pbm_get_diag(self._h, level, _ptr(out, n=nl, name="diag"), _stream()))
         return out

@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pbm_apply_K": (i, [vp, vp, vp, vp, vp]),
         "pbm_apply_K_f32": (i, [vp, vp, vp, vp, vp]),
         "pbm_apply_fine_f32": (i, [vp, i, i, vp, vp, vp, C.POINTER(C.c_double), vp]),
+        "pbm_apply_level_f32": (i, [vp, i, i, i, vp, vp, vp, C.POINTER(C.c_double), vp]),
         "pbm_get_diag": (i, [vp, i, vp, vp]),
         "pbm_fp32_plan_count": (i, []),
         "pbm_set_fp32_plan": (i, [vp, i, i]),

@@ -437,10 +437,13 @@ int pbm_grid_info_get(const pbm_grid* g, pbm_grid_info* out) {
         out->lambda_max[k] = g->L[k].lambda_max;
     }
     const Geom& F = g->L[0].g;
+    // supported nodes: every support lies on the faces x = 0 and x = nx, so only those are visited
     int64_t fixed = 0;
     for (int k = 0; k <= F.nz; ++k)
-        for (int j = 0; j <= F.ny; ++j)
-            for (int i = 0; i <= F.nx; ++i) fixed += node_fixed(F.support, F.nx, F.ny, F.nz, i, j, k) ? 1 : 0;
+        for (int j = 0; j <= F.ny; ++j) {
+            fixed += node_fixed(F.support, F.nx, F.ny, F.nz, 0, j, k) ? 1 : 0;
+            if (F.nx > 0) fixed += node_fixed(F.support, F.nx, F.ny, F.nz, F.nx, j, k) ? 1 : 0;
+        }
     out->n_free = F.n() - 3 * fixed;
     out->device_bytes = g->bytes;
     out->fine_chunk[0] = fine_L(g, false, false);
@@ -558,8 +561,14 @@ int pbm_apply_K_f32(pbm_grid* g, const float* w_dev, const float* x_dev, float* 
 
 int pbm_apply_fine_f32(pbm_grid* g, int op, int epilogue, const float* x_dev, const float* b_dev, float* y_dev,
                        double* dot_host, void* stream) {
+    return pbm_apply_level_f32(g, 0, op, epilogue, x_dev, b_dev, y_dev, dot_host, stream);
+}
+
+int pbm_apply_level_f32(pbm_grid* g, int level, int op, int epilogue, const float* x_dev, const float* b_dev,
+                        float* y_dev, double* dot_host, void* stream) {
     PBM_TRY
     if (!g || !x_dev || !y_dev) fail(PBM_EINVAL, "null argument");
+    if (level < 0 || level >= g->levels) fail(PBM_EINVAL, "level out of range");
     if (op != PBM_OP_K && op != PBM_OP_S) fail(PBM_EINVAL, "unknown operator");
     if (epilogue < PBM_EPI_APPLY || epilogue > PBM_EPI_JACOBI) fail(PBM_EINVAL, "unknown epilogue");
     if (epilogue != PBM_EPI_APPLY && !b_dev) fail(PBM_EINVAL, "the residual and Jacobi epilogues need b");
@@ -571,11 +580,11 @@ int pbm_apply_fine_f32(pbm_grid* g, int op, int epilogue, const float* x_dev, co
     a.x = x_dev;
     a.y = y_dev;
     a.b = b_dev;
-    a.diag = g->L[0].idiag32;
-    a.omega = &g->sc->mr[16];
+    a.diag = g->L[level].idiag32;
+    a.omega = &g->sc->mr[16 + level];
     a.mode = epilogue;
     a.dot_slot = dot_host ? 56 : -1;
-    level_apply(g, 0, true, op == PBM_OP_S, a, st);
+    level_apply(g, level, true, op == PBM_OP_S, a, st);
     if (dot_host) *dot_host = read_slot(g, 56, st);
     PBM_CATCH
 }

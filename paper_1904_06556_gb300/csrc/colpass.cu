@@ -650,6 +650,44 @@ void autotune_fine(pbm_grid* g) {
                 }
                 g->fusedP[op] = bestP;
             }
+        // plans of the single-pass FP32 coarse operator, per level that is ever applied
+        if (mixed)
+            for (int k = 1; k + 1 < g->levels; ++k) {
+                const Level& L = g->L[k];
+                PBM_CUDA(cudaMemset(L.A32, 0, sizeof(float) * NTRI * L.g.m()));
+                PBM_CUDA(cudaMemset(L.bord32, 0, sizeof(float) * (L.g.n() + 1)));
+                for (int op = 0; op < 2; ++op) {
+                    ApplyArgs a{};
+                    a.x = g->kv32[0];
+                    a.y = g->kv32[1];
+                    a.mode = EPI_APPLY;
+                    a.with_alpha = op == 1;
+                    a.dot_slot = -1;
+                    float best = 3.4e38f;
+                    int bestP = -1;
+                    // candidate -1: the two column passes
+                    for (int c = -1; c < fused_coarse_num_plans(); ++c) {
+                        for (int rep = 0; rep < 4; ++rep) {
+                            if (rep == 1) PBM_CUDA(cudaEventRecord(e0, 0));
+                            if (c < 0)
+                                cols_coarse<float>(g, k, L.A32, L.bord32, a, 0);
+                            else
+                                fused_coarse_f32(fused_coarse_plan(L.g, c), g->sc, g->partials,
+                                                 int64_t(8) * g->max_blocks, L.g, L.A32, L.bord32, &g->sc->salpha, a,
+                                                 0);
+                        }
+                        PBM_CUDA(cudaEventRecord(e1, 0));
+                        PBM_CUDA(cudaEventSynchronize(e1));
+                        float ms = 0.0f;
+                        PBM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                        if (ms < best) {
+                            best = ms;
+                            bestP = c;
+                        }
+                    }
+                    g->coarseP[op][k] = bestP;
+                }
+            }
     } catch (...) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);

@@ -372,6 +372,257 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
 }
 
 // ------------------------------------------------------------------------------------------------
+// FP32 coarse levels: the same marching tile, with the stored Galerkin element matrices
+// ------------------------------------------------------------------------------------------------
+// Four threads per element column, one per xy corner q of the element: thread q forms the rows of
+// local node q (bottom face, plane k) and of local node q + 4 (top face, plane k + 1), 144 FMAs per
+// layer, reading the upper triangle (entry-major, A[t m + e]) of the 24 x 24 matrix. Its top rows
+// are its carry into the next layer's bottom rows (the same xy corner). The coarse S adds the alpha
+// border: y_u += b x_alpha, y_alpha = b . x + S_aa x_alpha.
+struct CoarseArgs {
+    int nx, ny, nz, support;
+    int TX, TY, DZ, gx, gy;
+    int64_t n, m;
+    const float* A;
+    const float* x;
+    float* y;
+    const float* b;
+    const float* idiag;
+    const double* omega;
+    const float* bord;       // alpha border (S) or nullptr
+    const double* s_alpha;   // S_alpha,alpha (S)
+    int mode, with_alpha, dot_slot;
+    double* partials;
+    DevScalars* sc;
+};
+
+constexpr int CSLOT = 2;   // staging slots per thread: 3 (TX + 2)(TY + 2) <= CSLOT * NT
+
+template <int Q>
+__device__ __forceinline__ void coarse_rows6(const float* __restrict__ Ae, int64_t m, const float (&xe)[24],
+                                             float (&yb)[3], float (&yt)[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int rb = 3 * Q + c, rt = 3 * (Q + 4) + c;
+        float ab = 0.0f, at = 0.0f;
+#pragma unroll
+        for (int s = 0; s < 24; ++s) {
+            const int tb = rb <= s ? tri_index(rb, s) : tri_index(s, rb);
+            const int tt = rt <= s ? tri_index(rt, s) : tri_index(s, rt);
+            ab = fmaf(__ldg(Ae + int64_t(tb) * m), xe[s], ab);
+            at = fmaf(__ldg(Ae + int64_t(tt) * m), xe[s], at);
+        }
+        yb[c] = ab;
+        yt[c] = at;
+    }
+}
+
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
+    extern __shared__ float4 fused_smem4[];
+    __shared__ double sred[NT / 32];
+    __shared__ bool s_last;
+
+    const int TX = P.TX, TY = P.TY, EX = TX + 1, EY = TY + 1;
+    const int NW = TX + 2;
+    const int SN = NW * (TY + 2);
+    const int RW = 3 * NW;
+    const int SF = RW * (TY + 2);
+    const int EC = EX * EY;
+    float4* sx = fused_smem4;
+    float4* sq = fused_smem4 + 2 * SN;
+
+    const int t = threadIdx.x;
+    const int nx = P.nx, ny = P.ny, nz = P.nz, support = P.support;
+    const int bx = int(blockIdx.x % unsigned(P.gx));
+    const int rest = int(blockIdx.x / unsigned(P.gx));
+    const int by = rest % P.gy, bz = rest / P.gy;
+    const int X0 = bx * TX, Y0 = by * TY;
+    const int kz0 = bz * P.DZ, kz1 = min(kz0 + P.DZ, nz + 1);
+    const int64_t plane = 3 * int64_t(nx + 1) * (ny + 1);
+
+    int gofs[CSLOT], sidx[CSLOT];
+    int fbits = 0;
+#pragma unroll
+    for (int s = 0; s < CSLOT; ++s) {
+        const int f = t + s * NT;
+        gofs[s] = -2;
+        sidx[s] = 0;
+        if (f < SF) {
+            const int row = f / RW, o = f - row * RW;
+            const int lxn = o / 3, c = o - 3 * lxn;
+            const int gxn = X0 - 1 + lxn, gyn = Y0 - 1 + row;
+            const bool in = gxn >= 0 && gxn <= nx && gyn >= 0 && gyn <= ny;
+            gofs[s] = in ? 3 * (gxn + (nx + 1) * gyn) + c : -1;
+            sidx[s] = 4 * (row * NW + lxn) + c;
+            if (in) fbits |= fixed_bits(support, nx, ny, nz, gxn, gyn) << (2 * s);
+        }
+    }
+    float px[CSLOT];
+    auto fetch = [&](int k) {
+        const float* xs = P.x + int64_t(k) * plane;
+#pragma unroll
+        for (int s = 0; s < CSLOT; ++s) px[s] = gofs[s] >= 0 ? __ldg(xs + gofs[s]) : 0.0f;
+    };
+    auto stage = [&](int k) {
+        float* dx = reinterpret_cast<float*>(sx + (k & 1) * SN);
+        const int sh = k == 0 ? 1 : 0;
+#pragma unroll
+        for (int s = 0; s < CSLOT; ++s)
+            if (gofs[s] != -2) dx[sidx[s]] = ((fbits >> (2 * s + sh)) & 1) ? 0.0f : px[s];
+    };
+
+    // element-column role: corner q of element column col
+    const int q = t / EC, col = t - q * EC;
+    const int lx = col % EX, ly = col / EX;
+    const int ex = X0 - 1 + lx, ey = Y0 - 1 + ly;
+    const bool ecol = q < 4 && ex >= 0 && ex < nx && ey >= 0 && ey < ny;
+    // owner role
+    const int ox = t % TX, oy = t / TX;
+    const int I = X0 + ox, J = Y0 + oy;
+    const bool owner = t < TX * TY && I <= nx && J <= ny;
+    const int obits = owner ? fixed_bits(support, nx, ny, nz, I, J) : 0;
+
+    const float xa = P.with_alpha ? P.x[P.n] : 0.0f;
+    const double om = P.mode == EPI_JACOBI ? *P.omega : 0.0;
+    const float omF = float(om);
+    const bool want_dot = P.dot_slot >= 0;
+    float pdT = 0.0f, paT = 0.0f;
+
+    const int kstart = max(kz0 - 1, 0);
+    const int64_t elayer = int64_t(nx) * ny;
+    const int64_t e0 = ex + int64_t(nx) * ey;
+    float carry[3] = {0.0f, 0.0f, 0.0f};
+    fetch(kstart);
+    stage(kstart);
+    if (kstart + 1 <= nz) fetch(kstart + 1);
+
+    for (int k = kstart; k < kz1; ++k) {
+        const bool layer = k < nz;
+        if (layer) stage(k + 1);
+        __syncthreads();  // (a) planes k and k + 1 staged
+        if (layer && k + 2 <= nz && k + 1 < kz1) fetch(k + 2);
+        float4 xo4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const bool ofixed = (obits >> (k == 0 ? 1 : 0)) & 1;
+        const int64_t d0 = 3 * (I + int64_t(nx + 1) * (J + int64_t(ny + 1) * k));
+        if (owner && k >= kz0) {
+            if (ofixed) xo4 = make_float4(__ldg(P.x + d0), __ldg(P.x + d0 + 1), __ldg(P.x + d0 + 2), 0.0f);
+            else xo4 = sx[(k & 1) * SN + (oy + 1) * NW + ox + 1];
+        }
+        float yb[3] = {0.0f, 0.0f, 0.0f}, yt[3] = {0.0f, 0.0f, 0.0f};
+        if (ecol && layer) {
+            float xe[24];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                const float4 v = sx[((k + (a >> 2)) & 1) * SN + (ly + ((a >> 1) & 1)) * NW + lx + (a & 1)];
+                xe[3 * a] = v.x;
+                xe[3 * a + 1] = v.y;
+                xe[3 * a + 2] = v.z;
+            }
+            const float* Ae = P.A + e0 + int64_t(k) * elayer;
+            switch (q) {
+                case 0: coarse_rows6<0>(Ae, P.m, xe, yb, yt); break;
+                case 1: coarse_rows6<1>(Ae, P.m, xe, yb, yt); break;
+                case 2: coarse_rows6<2>(Ae, P.m, xe, yb, yt); break;
+                default: coarse_rows6<3>(Ae, P.m, xe, yb, yt); break;
+            }
+        }
+        float ob[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ob[c] = carry[c] + yb[c];
+            carry[c] = yt[c];
+        }
+        if (k < kz0) continue;
+        if (q < 4) sq[q * EC + col] = make_float4(ob[0], ob[1], ob[2], 0.0f);
+        __syncthreads();  // (b) corner values of plane k complete
+        if (owner) {
+            float s3[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int dj = 1; dj >= 0; --dj)
+#pragma unroll
+                for (int di = 1; di >= 0; --di) {
+                    const float4 v = sq[(di + 2 * dj) * EC + (oy + 1 - dj) * EX + (ox + 1 - di)];
+                    s3[0] += v.x;
+                    s3[1] += v.y;
+                    s3[2] += v.z;
+                }
+            const float xo[3] = {xo4.x, xo4.y, xo4.z};
+            if (P.bord) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float bc = __ldg(P.bord + d0 + c);
+                    s3[c] += bc * xa;
+                    paT += bc * xo[c];
+                }
+            }
+            if (ofixed) {
+                s3[0] = xo[0];
+                s3[1] = xo[1];
+                s3[2] = xo[2];
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float o;
+                if (P.mode == EPI_APPLY) {
+                    o = s3[c];
+                    if (want_dot) pdT += o * xo[c];
+                } else if (P.mode == EPI_RESID) {
+                    o = __ldg(P.b + d0 + c) - s3[c];
+                    if (want_dot) pdT += o * o;
+                } else {
+                    const float bb = __ldg(P.b + d0 + c);
+                    o = xo[c] + omF * ((bb - s3[c]) * __ldg(P.idiag + d0 + c));
+                    if (want_dot) pdT += o * bb;
+                }
+                P.y[d0 + c] = o;
+            }
+        }
+    }
+
+    if (!want_dot && !P.with_alpha) return;
+    const unsigned nblk = gridDim.x, blk = blockIdx.x;
+    const double bd = fused_cta_sum<NT>(double(pdT), sred);
+    const double ba = fused_cta_sum<NT>(double(paT), sred);
+    if (t == 0) {
+        P.partials[blk] = bd;
+        P.partials[nblk + blk] = ba;
+        __threadfence();
+        s_last = atomicAdd(&P.sc->counter[0], 1u) == nblk - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double td = 0.0, ta = 0.0;
+    for (int i = t; i < int(nblk); i += NT) {
+        td += ((volatile double*)P.partials)[i];
+        ta += ((volatile double*)P.partials)[nblk + i];
+    }
+    double sd = fused_cta_sum<NT>(td, sred);
+    const double sa = fused_cta_sum<NT>(ta, sred);
+    if (t != 0) return;
+    P.sc->counter[0] = 0u;
+    if (P.with_alpha) {
+        const int64_t n = P.n;
+        const double ya = sa + (P.bord ? *P.s_alpha * double(xa) : 0.0);
+        double o;
+        if (P.mode == EPI_APPLY) {
+            o = ya;
+            sd += o * double(xa);
+        } else if (P.mode == EPI_RESID) {
+            o = double(P.b[n]) - ya;
+            sd += o * o;
+        } else {
+            const double bb = double(P.b[n]);
+            o = double(xa) + om * ((bb - ya) * double(P.idiag[n]));
+            sd += o * bb;
+        }
+        P.y[n] = float(o);
+    }
+    if (want_dot) P.sc->red[P.dot_slot] = sd;
+}
+
+// ------------------------------------------------------------------------------------------------
 // tile plans
 // ------------------------------------------------------------------------------------------------
 // Kernel variants: threads per CTA and the resident CTAs per SM asked of the register allocator.
@@ -500,6 +751,84 @@ void fused_fine_f32(const FusedPlan& p, DevScalars* sc, double* partials, int64_
     if (s) fused_launch<2>(p, blocks, smem, P, st);
     else fused_launch<0>(p, blocks, smem, P, st);
     PBM_LAUNCH("fused FP32 fine operator");
+}
+
+// ---- coarse-level plans: CTA size, resident CTAs per SM, owner tile (4 (TX+1)(TY+1) = threads) ----
+static const int kCoarsePlans[][4] = {{256, 2, 7, 7}, {256, 2, 15, 3}, {128, 4, 7, 3}, {128, 4, 3, 7},
+                                      {256, 1, 7, 7}, {128, 2, 7, 3}};
+constexpr int kCoarseNumPlans = int(sizeof(kCoarsePlans) / sizeof(kCoarsePlans[0]));
+
+int fused_coarse_num_plans() { return kCoarseNumPlans; }
+
+FusedPlan fused_coarse_plan(const Geom& G, int cand) {
+    FusedPlan p{};
+    p.var = cand;
+    const int per_sm = kCoarsePlans[cand][1];
+    p.TX = kCoarsePlans[cand][2];
+    p.TY = kCoarsePlans[cand][3];
+    p.gx = (G.nx + 1 + p.TX - 1) / p.TX;
+    p.gy = (G.ny + 1 + p.TY - 1) / p.TY;
+    const int planes = G.nz + 1;
+    const int tiles = p.gx * p.gy;
+    double best = 1e300;
+    p.DZ = planes;
+    for (int dz = std::max(1, std::min(planes, 2)); dz <= planes; ++dz) {
+        const int gz = (planes + dz - 1) / dz;
+        if (dz > 1 && (planes + dz - 2) / (dz - 1) == gz && dz != planes) continue;
+        const double waves = double((int64_t(tiles) * gz + 152 * per_sm - 1) / (152 * per_sm));
+        const double cost = waves * (dz + 1);
+        if (cost < best - 1e-9) {
+            best = cost;
+            p.DZ = dz;
+        }
+    }
+    p.gz = (planes + p.DZ - 1) / p.DZ;
+    return p;
+}
+
+void fused_coarse_f32(const FusedPlan& p, DevScalars* sc, double* partials, int64_t partials_len, const Geom& G,
+                      const float* A, const float* bord, const double* s_alpha, const ApplyArgs& a,
+                      cudaStream_t st) {
+    const int nt = kCoarsePlans[p.var][0];
+    if (4 * (p.TX + 1) * (p.TY + 1) != nt || 3 * (p.TX + 2) * (p.TY + 2) > CSLOT * nt || p.TX * p.TY > nt)
+        fail(PBM_EINVAL, "fused coarse operator: tile does not fit the CTA");
+    const int blocks = p.gx * p.gy * p.gz;
+    if (2 * int64_t(blocks) > partials_len) fail(PBM_EINVAL, "grid too large for the partials buffer");
+    CoarseArgs P{};
+    P.nx = G.nx;
+    P.ny = G.ny;
+    P.nz = G.nz;
+    P.support = G.support;
+    P.TX = p.TX;
+    P.TY = p.TY;
+    P.DZ = p.DZ;
+    P.gx = p.gx;
+    P.gy = p.gy;
+    P.n = G.n();
+    P.m = G.m();
+    P.A = A;
+    P.x = (const float*)a.x;
+    P.y = (float*)a.y;
+    P.b = (const float*)a.b;
+    P.idiag = (const float*)a.diag;
+    P.omega = a.omega;
+    P.bord = a.with_alpha ? bord : nullptr;
+    P.s_alpha = s_alpha;
+    P.mode = a.mode;
+    P.with_alpha = a.with_alpha ? 1 : 0;
+    P.dot_slot = a.dot_slot;
+    P.partials = partials;
+    P.sc = sc;
+    const size_t smem = sizeof(float4) * (size_t(2 * (p.TX + 2) * (p.TY + 2)) + size_t(4 * (p.TX + 1) * (p.TY + 1)));
+    switch (p.var) {
+        case 0:
+        case 1: k_fused_coarse_f32<256, 2><<<blocks, 256, smem, st>>>(P); break;
+        case 2:
+        case 3: k_fused_coarse_f32<128, 4><<<blocks, 128, smem, st>>>(P); break;
+        case 4: k_fused_coarse_f32<256, 1><<<blocks, 256, smem, st>>>(P); break;
+        default: k_fused_coarse_f32<128, 2><<<blocks, 128, smem, st>>>(P); break;
+    }
+    PBM_LAUNCH("fused FP32 coarse operator");
 }
 
 }  // namespace pbm

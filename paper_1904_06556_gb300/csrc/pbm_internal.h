@@ -243,6 +243,8 @@ struct pbm_grid {
     cudaGraphExec_t mr_graph[8] = {};
     int fineL[2][2] = {};                  // autotuned chunk length [fp32][op_s] of the fine column pass
     int fusedP[2] = {};                    // autotuned tile plan [op_s] of the single-pass FP32 operator
+    int coarseP[2][16] = {};               // autotuned FP32 coarse operator [op_s][level]: -1 two passes,
+                                           // >= 0 plan of the single pass
     int64_t mr_graph_kernels[8] = {};      // kernels in one iteration of each graph (launch counting)
     std::vector<int> prof_op;              // operator of every recorded launch
 };
@@ -449,6 +451,12 @@ int fused_threads(const FusedPlan& p);
 void fused_fine_f32(const FusedPlan& p, DevScalars* sc, double* partials, int64_t partials_len, const Geom& G,
                     const KeHat& kh, const float* w, const float* d, const float* u, const ApplyArgs& a,
                     cudaStream_t st);
+// single-pass FP32 coarse-level operator (stored Galerkin matrices; fused.cu)
+int fused_coarse_num_plans();
+FusedPlan fused_coarse_plan(const Geom& G, int cand);
+void fused_coarse_f32(const FusedPlan& p, DevScalars* sc, double* partials, int64_t partials_len, const Geom& G,
+                      const float* A, const float* bord, const double* s_alpha, const ApplyArgs& a,
+                      cudaStream_t st);
 void cols_cost(const Geom& G, int L, bool op_s, bool recompute_w, int mode, int esize, double& bytes, double& flops);
 // chunk length the handle uses for the fine column pass of (precision, operator)
 int fine_L(const pbm_grid* g, bool fp32, bool op_s);

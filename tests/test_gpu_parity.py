@@ -210,6 +210,41 @@ def test_fused_fp32_every_tile_plan(pkg, dims, bc, seed):
         assert rel(host(y), refk) < 2e-6, plan
 
 
+@pytest.mark.parametrize("dims,bc,levels,op", [((16, 8, 8), "bridge_corners", 3, "S"), ((32, 16, 16), "cantilever", 4, "S"),
+                                              ((32, 16, 16), "cantilever", 4, "K")])
+def test_fused_fp32_coarse_levels_match_oracle_galerkin(pkg, dims, bc, levels, op):
+    """The single-pass FP32 coarse operator (stored Galerkin matrices, alpha border for S) with each epilogue on
+    every coarse level, and the FP64 Jacobi diagonals of those levels, against the oracle's CSR Galerkin
+    hierarchy A_k = P^T A_(k-1) P."""
+    pb, st, d = make_problem(*dims, bc, 6, 0.5)
+    G = pkg.Grid(*dims, levels, bc, precision="mixed")
+    if op == "S":
+        G.set_state(state_dev(d))
+        A0 = pbm.assemble_S(pb, st)
+    else:
+        G.set_density(dev(d["rho"]))
+        G.vcycle("K", dev(pb.f))
+        A0 = fem.assemble_K(pb.grid, d["rho"], fem.element_stiffness())
+    h = solvers.Hierarchy(pb.grid, A0, levels, has_alpha=(op == "S"))
+    rng = np.random.default_rng(sum(dims) + levels)
+    for k in range(1, levels):
+        Ak = h.A[k]
+        nk = Ak.shape[0]
+        assert rel(host(G.diag(k))[:nk], Ak.diagonal()) < 1e-12
+        x, b = rng.standard_normal(nk), rng.standard_normal(nk)
+        xr, br = _f32(x), _f32(b)
+        omega = G.info()["omega"][k]
+        y, dot = G.apply_level_f32(k, op, "apply", dev(x, torch.float32), dot=True)
+        y = host(y)
+        assert rel(y, Ak @ xr) < 1e-5, k
+        assert abs(dot - y @ xr) <= 1e-5 * np.abs(y * xr).sum()
+        r, _ = G.apply_level_f32(k, op, "resid", dev(x, torch.float32), dev(b, torch.float32))
+        assert rel(host(r), br - Ak @ xr) < 1e-5, k
+        if k < levels - 1:
+            j, _ = G.apply_level_f32(k, op, "jacobi", dev(x, torch.float32), dev(b, torch.float32))
+            assert rel(host(j), xr + omega * (br - Ak @ xr) / Ak.diagonal()) < 1e-5, k
+
+
 # ------------------------------------------------------------------------------------------------
 # S, rhs, compliances
 # ------------------------------------------------------------------------------------------------
