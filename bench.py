@@ -79,6 +79,22 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(ms: float, device) -> float:
+    """The largest of every rank's timed total (the job's time); the value itself with one process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, total_ms: float) -> float:
+    """Systems per second of the whole job: every rank solves `steps` systems (replicas, weak scaling)."""
+    return world * steps / (total_ms / 1e3)
+
+
 # ------------------------------------------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ------------------------------------------------------------------------------------------------------------
@@ -271,12 +287,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     prof = G.profile_read("S")
     G.profile(False)
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(sum(step_ms)), dev)
+    value = whole_job_rate(world, args.steps, total_ms)
     relres = last["info"]["relres"]
 
     # ---- end to end through the C ABI: pinned host inputs in, solution out, every step ----
@@ -311,12 +323,8 @@ def run_ours(args):
         step_e2e()
         ev2[i][1].record(stream)
     torch.cuda.synchronize()
-    e2e_ms = float(sum(a.elapsed_time(b) for a, b in ev2))
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * args.steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in ev2)), dev)
+    e2e_value = whole_job_rate(world, args.steps, e2e_ms)
 
     # ---- standalone K(rho) u applies at the workload size (metric's second half), L2 flushed and warm ----
     kapply = k_apply_rates(G, w, rho, dev, flush)
