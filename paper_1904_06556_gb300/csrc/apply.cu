@@ -444,9 +444,8 @@ void launch_fine(pbm_grid* g, bool fp32, const void* w, const void* d, const voi
     const bool prof = g->prof_on && fp32 == (g->desc.precision == PBM_MIXED);
     if (prof) prof_begin(g, st);
     if (fp32)
-        fused_fine_f32(fused_plan(g->L[0].g, g->fusedP[s ? 1 : 0]), g->sc, g->partials, int64_t(8) * g->max_blocks,
-                       g->L[0].g, g->kehat, (const float*)w, s ? (const float*)d : nullptr,
-                       s ? (const float*)u : nullptr, a, st);
+        fused_fine_f32(fused_plan(g->L[0].g, g->fusedP[s ? 1 : 0]), red_set(g, a.rset), g->L[0].g, g->kehat,
+                       (const float*)w, s ? (const float*)d : nullptr, s ? (const float*)u : nullptr, a, st);
     else
         cols_fine<double>(g, (const double*)w, s ? (const double*)d : nullptr, s ? g->what_hat : nullptr, nullptr, a,
                           st);
@@ -466,8 +465,8 @@ void launch_coarse(pbm_grid* g, int k, bool fp32, const ApplyArgs& a, cudaStream
     Level& L = g->L[k];
     const int plan = g->coarseP[a.with_alpha ? 1 : 0][k];
     if (fp32 && plan >= 0)
-        fused_coarse_f32(fused_coarse_plan(L.g, plan), g->sc, g->partials, int64_t(8) * g->max_blocks, L.g, L.A32,
-                         L.bord32, &g->sc->salpha, a, st);
+        fused_coarse_f32(fused_coarse_plan(L.g, plan), red_set(g, a.rset), L.g, L.A32, L.bord32, &g->sc->salpha, a,
+                         st);
     else if (fp32)
         cols_coarse<float>(g, k, L.A32, L.bord32, a, st);
     else

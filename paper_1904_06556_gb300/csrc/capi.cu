@@ -295,6 +295,9 @@ int pbm_create_grid(const pbm_grid_desc* d, pbm_grid** out) {
         if (k >= 1) {
             L.A64 = (double*)dalloc(g, sizeof(double) * NTRI * mk);
             if (mixed) L.A32 = (float*)dalloc(g, sizeof(float) * NTRI * mk);
+            const size_t nq = size_t(12) * size_t(L.g.nx) * size_t(L.g.ny) * size_t(L.g.nz + 1);
+            L.qa = dalloc(g, sizeof(double) * nq);
+            L.qb = dalloc(g, sizeof(double) * nq);
         }
         L.bord64 = (double*)dalloc(g, sizeof(double) * nk);
         L.diag64 = (double*)dalloc(g, sizeof(double) * nk);
@@ -345,7 +348,7 @@ int pbm_create_grid(const pbm_grid_desc* d, pbm_grid** out) {
     g->cinv = (double*)dalloc(g, sizeof(double) * N * N);
     g->cwork = (double*)dalloc(g, sizeof(double) * (2 * N * N + N));   // L, L^{-1}, 1 / diag(L)
     g->max_blocks = 1 << 16;
-    g->partials = (double*)dalloc(g, sizeof(double) * 8 * size_t(g->max_blocks));
+    g->partials = (double*)dalloc(g, sizeof(double) * size_t(8 + 2 * (kRedSets - 1)) * size_t(g->max_blocks));
     g->sc = (DevScalars*)dalloc(g, sizeof(DevScalars));
     PBM_CUDA(cudaMemset(g->sc, 0, sizeof(DevScalars)));
     PBM_CUDA(cudaMallocHost((void**)&g->sc_host, sizeof(DevScalars)));
@@ -373,6 +376,8 @@ int pbm_destroy_grid(pbm_grid* g) {
     for (auto& L : g->L) {
         dfree(L.A64);
         dfree(L.A32);
+        dfree(L.qa);
+        dfree(L.qb);
         dfree(L.bord64);
         dfree(L.bord32);
         dfree(L.diag64);
@@ -412,6 +417,10 @@ int pbm_destroy_grid(pbm_grid* g) {
     for (cudaGraphExec_t e : g->mr_graph)
         if (e) cudaGraphExecDestroy(e);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    for (auto& sst : g->side)
+        if (sst) cudaStreamDestroy(sst);
+    for (auto& ev : g->side_ev)
+        if (ev) cudaEventDestroy(ev);
     dfree(g->cinv);
     dfree(g->cwork);
     dfree(g->partials);

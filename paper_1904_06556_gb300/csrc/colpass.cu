@@ -357,7 +357,7 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
         P.partials[blk] = bd;
         P.partials[nblk + blk] = ba;
         __threadfence();
-        s_last = atomicAdd(&P.sc->counter[0], 1u) == nblk - 1;
+        s_last = atomicAdd(P.counter, 1u) == nblk - 1;
     }
     __syncthreads();
     if (!s_last) return;
@@ -375,7 +375,7 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
     __syncthreads();
     double sa = cta_sum1<NB2>(ta, sh);
     if (threadIdx.x != 0) return;
-    P.sc->counter[0] = 0u;
+    *P.counter = 0u;
     if (P.with_alpha) {
         const int64_t n = P.n;
         const double ya = sa + (P.bord ? *P.s_alpha * double(xa) : 0.0);
@@ -448,6 +448,7 @@ NodeArgs<T> make_node_args(const ColEnv& env, const Geom& G, const ApplyArgs& a,
     N.napart = napart;
     N.partials = env.partials + off;
     N.sc = env.sc;
+    N.counter = env.counter ? env.counter : &env.sc->counter[0];
     const int64_t nn = G.nnode();
     const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nn + NB2 - 1) / NB2, 152 * 8)));
     if (off + 2 * blocks > env.partials_len) fail(PBM_EINVAL, "grid too large for the partials buffer");
@@ -544,14 +545,34 @@ int64_t cols_scratch_entries(const Geom& G) {
     return 12 * ncol * (G.nz + 1) + 12 * ncol * ((G.nz + L - 1) / L);
 }
 
-ColEnv env_of(pbm_grid* g) {
+ColEnv env_of(pbm_grid* g, int rset) {
+    const RedSet r = red_set(g, rset);
     ColEnv e;
     e.qa = g->qa;
     e.qb = g->qb;
-    e.partials = g->partials;
-    e.partials_len = int64_t(8) * g->max_blocks;
-    e.sc = g->sc;
+    e.partials = r.partials;
+    e.partials_len = r.len;
+    e.sc = r.sc;
+    e.counter = r.counter;
     return e;
+}
+
+// Set 0: the first 8 max_blocks doubles of the partials buffer and counter[0]; set r > 0: 2 max_blocks
+// doubles each after them and counter[32 + r].
+RedSet red_set(pbm_grid* g, int rset) {
+    if (rset < 0 || rset >= kRedSets) fail(PBM_EINVAL, "reduction set out of range");
+    RedSet r;
+    r.sc = g->sc;
+    if (rset == 0) {
+        r.partials = g->partials;
+        r.len = int64_t(8) * g->max_blocks;
+        r.counter = &g->sc->counter[0];
+    } else {
+        r.partials = g->partials + int64_t(8 + 2 * (rset - 1)) * g->max_blocks;
+        r.len = int64_t(2) * g->max_blocks;
+        r.counter = &g->sc->counter[32 + rset];
+    }
+    return r;
 }
 
 int fine_L(const pbm_grid* g, bool fp32, bool op_s) {
@@ -561,7 +582,7 @@ int fine_L(const pbm_grid* g, bool fp32, bool op_s) {
 
 template <class T>
 void cols_fine(pbm_grid* g, const T* w, const T* d, const T* what, const T* u, const ApplyArgs& a, cudaStream_t st) {
-    ColEnv env = env_of(g);
+    ColEnv env = env_of(g, a.rset);
     env.L = fine_L(g, sizeof(T) == 4, d != nullptr);
     cols_fine_env<T>(env, g->L[0].g, g->kehat, w, d, what, u, a, st);
 }
@@ -636,8 +657,8 @@ void autotune_fine(pbm_grid* g) {
                     const FusedPlan fp = fused_plan(G, c);
                     for (int rep = 0; rep < 4; ++rep) {
                         if (rep == 1) PBM_CUDA(cudaEventRecord(e0, 0));
-                        fused_fine_f32(fp, g->sc, g->partials, int64_t(8) * g->max_blocks, G, g->kehat, g->w32,
-                                       op ? g->d32 : nullptr, op ? g->u32 : nullptr, a, 0);
+                        fused_fine_f32(fp, red_set(g, 0), G, g->kehat, g->w32, op ? g->d32 : nullptr,
+                                       op ? g->u32 : nullptr, a, 0);
                     }
                     PBM_CUDA(cudaEventRecord(e1, 0));
                     PBM_CUDA(cudaEventSynchronize(e1));
@@ -672,9 +693,8 @@ void autotune_fine(pbm_grid* g) {
                             if (c < 0)
                                 cols_coarse<float>(g, k, L.A32, L.bord32, a, 0);
                             else
-                                fused_coarse_f32(fused_coarse_plan(L.g, c), g->sc, g->partials,
-                                                 int64_t(8) * g->max_blocks, L.g, L.A32, L.bord32, &g->sc->salpha, a,
-                                                 0);
+                                fused_coarse_f32(fused_coarse_plan(L.g, c), red_set(g, 0), L.g, L.A32, L.bord32,
+                                                 &g->sc->salpha, a, 0);
                         }
                         PBM_CUDA(cudaEventRecord(e1, 0));
                         PBM_CUDA(cudaEventSynchronize(e1));
@@ -720,7 +740,11 @@ ColArgs<T> make_coarse_args(const ColEnv& env, const Geom& G, const T* A, const 
 template <class T>
 void cols_coarse(pbm_grid* g, int k, const T* A, const T* bord, const ApplyArgs& a, cudaStream_t st) {
     const Geom& G = g->L[k].g;
-    const ColEnv env = env_of(g);
+    ColEnv env = env_of(g, a.rset);
+    if (g->L[k].qa) {
+        env.qa = g->L[k].qa;
+        env.qb = g->L[k].qb;
+    }
     int blocks = 0;
     const ColArgs<T> P = make_coarse_args<T>(env, G, A, a.x, &blocks);
     k_cols_coarse<T><<<blocks, CB, 0, st>>>(P);

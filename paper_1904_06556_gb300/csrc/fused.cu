@@ -42,6 +42,7 @@ struct FusedArgs {
     KeHatT<float> K;
     double* partials;     // 2 * gridDim.x
     DevScalars* sc;
+    unsigned int* counter;   // last-CTA counter
 };
 
 // transformed xy quad of the element column at staged coordinates (lx, ly) of a staged plane
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
         P.partials[blk] = bd;
         P.partials[nblk + blk] = ba;
         __threadfence();
-        s_last = atomicAdd(&P.sc->counter[0], 1u) == nblk - 1;
+        s_last = atomicAdd(P.counter, 1u) == nblk - 1;
     }
     __syncthreads();
     if (!s_last) return;
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
     double sd = fused_cta_sum<NT>(td, sred);
     const double sa = fused_cta_sum<NT>(ta, sred);
     if (t != 0) return;
-    P.sc->counter[0] = 0u;
+    *P.counter = 0u;
     if (P.with_alpha) {
         const int64_t n = P.n;
         double o;
@@ -394,6 +395,7 @@ struct CoarseArgs {
     int mode, with_alpha, dot_slot;
     double* partials;
     DevScalars* sc;
+    unsigned int* counter;
 };
 
 constexpr int CSLOT = 2;   // staging slots per thread: 3 (TX + 2)(TY + 2) <= CSLOT * NT
@@ -588,7 +590,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
         P.partials[blk] = bd;
         P.partials[nblk + blk] = ba;
         __threadfence();
-        s_last = atomicAdd(&P.sc->counter[0], 1u) == nblk - 1;
+        s_last = atomicAdd(P.counter, 1u) == nblk - 1;
     }
     __syncthreads();
     if (!s_last) return;
@@ -601,7 +603,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
     double sd = fused_cta_sum<NT>(td, sred);
     const double sa = fused_cta_sum<NT>(ta, sred);
     if (t != 0) return;
-    P.sc->counter[0] = 0u;
+    *P.counter = 0u;
     if (P.with_alpha) {
         const int64_t n = P.n;
         const double ya = sa + (P.bord ? *P.s_alpha * double(xa) : 0.0);
@@ -708,15 +710,14 @@ static void fused_launch(const FusedPlan& p, int blocks, size_t smem, const Fuse
     }
 }
 
-void fused_fine_f32(const FusedPlan& p, DevScalars* sc, double* partials, int64_t partials_len, const Geom& G,
-                    const KeHat& kh, const float* w, const float* d, const float* u, const ApplyArgs& a,
-                    cudaStream_t st) {
+void fused_fine_f32(const FusedPlan& p, const RedSet& r, const Geom& G, const KeHat& kh, const float* w,
+                    const float* d, const float* u, const ApplyArgs& a, cudaStream_t st) {
     const bool s = d != nullptr;
     const int nt = fused_threads(p);
     if ((p.TX + 1) * (p.TY + 1) > nt || 3 * (p.TX + 2) * (p.TY + 2) > FSLOT * nt)
         fail(PBM_EINVAL, "fused operator: tile does not fit the CTA");
     const int blocks = fused_blocks(p);
-    if (2 * int64_t(blocks) > partials_len) fail(PBM_EINVAL, "grid too large for the partials buffer");
+    if (2 * int64_t(blocks) > r.len) fail(PBM_EINVAL, "grid too large for the partials buffer");
     FusedArgs P{};
     P.nx = G.nx;
     P.ny = G.ny;
@@ -745,8 +746,9 @@ void fused_fine_f32(const FusedPlan& p, DevScalars* sc, double* partials, int64_
         P.K.lam4[b] = float(kh.lam4[b]);
         P.K.mu4[b] = float(kh.mu4[b]);
     }
-    P.partials = partials;
-    P.sc = sc;
+    P.partials = r.partials;
+    P.sc = r.sc;
+    P.counter = r.counter;
     const size_t smem = fused_smem_bytes(p, s);
     if (s) fused_launch<2>(p, blocks, smem, P, st);
     else fused_launch<0>(p, blocks, smem, P, st);
@@ -786,14 +788,13 @@ FusedPlan fused_coarse_plan(const Geom& G, int cand) {
     return p;
 }
 
-void fused_coarse_f32(const FusedPlan& p, DevScalars* sc, double* partials, int64_t partials_len, const Geom& G,
-                      const float* A, const float* bord, const double* s_alpha, const ApplyArgs& a,
-                      cudaStream_t st) {
+void fused_coarse_f32(const FusedPlan& p, const RedSet& r, const Geom& G, const float* A, const float* bord,
+                      const double* s_alpha, const ApplyArgs& a, cudaStream_t st) {
     const int nt = kCoarsePlans[p.var][0];
     if (4 * (p.TX + 1) * (p.TY + 1) != nt || 3 * (p.TX + 2) * (p.TY + 2) > CSLOT * nt || p.TX * p.TY > nt)
         fail(PBM_EINVAL, "fused coarse operator: tile does not fit the CTA");
     const int blocks = p.gx * p.gy * p.gz;
-    if (2 * int64_t(blocks) > partials_len) fail(PBM_EINVAL, "grid too large for the partials buffer");
+    if (2 * int64_t(blocks) > r.len) fail(PBM_EINVAL, "grid too large for the partials buffer");
     CoarseArgs P{};
     P.nx = G.nx;
     P.ny = G.ny;
@@ -817,8 +818,9 @@ void fused_coarse_f32(const FusedPlan& p, DevScalars* sc, double* partials, int6
     P.mode = a.mode;
     P.with_alpha = a.with_alpha ? 1 : 0;
     P.dot_slot = a.dot_slot;
-    P.partials = partials;
-    P.sc = sc;
+    P.partials = r.partials;
+    P.sc = r.sc;
+    P.counter = r.counter;
     const size_t smem = sizeof(float4) * (size_t(2 * (p.TX + 2) * (p.TY + 2)) + size_t(4 * (p.TX + 1) * (p.TY + 1)));
     switch (p.var) {
         case 0:

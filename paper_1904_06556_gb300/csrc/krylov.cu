@@ -407,10 +407,12 @@ void lz_start(pbm_grid* g, double* v, double* t, double* vprev, const double* di
     k_lz_start<<<VG, VB, 0, st>>>(v, t, vprev, diag, n);
     PBM_LAUNCH("lz start");
 }
-void lz_b(pbm_grid* g, double* w, const double* v, const double* vprev, const double* sdiag, int64_t n, int j,
-          cudaStream_t st) {
-    k_lz_b<<<VG, VB, 0, st>>>(w, v, vprev, sdiag, n, &g->sc->lz_a[j], j > 0 ? &g->sc->lz_b[j - 1] : nullptr,
-                              g->partials, &g->sc->counter[2], &g->sc->lz_b[j]);
+// j: coefficient index in sc->lz_a / lz_b; rset: reduction set of the stream (0: counter[2])
+void lz_b(pbm_grid* g, double* w, const double* v, const double* vprev, const double* sdiag, int64_t n, int j0,
+          int j, int rset, cudaStream_t st) {
+    const RedSet r = red_set(g, rset);
+    k_lz_b<<<VG, VB, 0, st>>>(w, v, vprev, sdiag, n, &g->sc->lz_a[j0 + j], j > 0 ? &g->sc->lz_b[j0 + j - 1] : nullptr,
+                              r.partials, rset == 0 ? &g->sc->counter[2] : r.counter, &g->sc->lz_b[j0 + j]);
     PBM_LAUNCH("lz b");
 }
 void lz_next(pbm_grid* g, const double* w, double* v, double* vprev, double* t, const double* diag, int64_t n, int j,

@@ -160,6 +160,10 @@ struct Level {
     double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *t64 = nullptr;
     float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr, *t32 = nullptr;
     double omega = 0.0, lambda_max = 0.0;
+    // coarse levels: plane-quad scratch of this level's two-pass applies (12 (nz + 1) nx ny entries of
+    // the FP64 size each), so that different levels can be applied on concurrent streams
+    void* qa = nullptr;
+    void* qb = nullptr;
 };
 
 constexpr int NTRI = 300;  // entries of the upper triangle of a 24 x 24 matrix
@@ -170,7 +174,7 @@ __host__ __device__ inline int tri_index(int i, int j) {  // i <= j
 // device scalar block used by the reductions, Lanczos and MINRES
 struct DevScalars {
     double red[64];        // reduction outputs (slot per use)
-    double lz_a[64], lz_b[64];
+    double lz_a[128], lz_b[128];   // Lanczos coefficients, steps x level
     double mr[32];         // MINRES scalar state
     unsigned int counter[64];  // last-block-done counters (one per reduction slot)
     int flags[8];
@@ -247,6 +251,10 @@ struct pbm_grid {
                                            // >= 0 plan of the single pass
     int64_t mr_graph_kernels[8] = {};      // kernels in one iteration of each graph (launch counting)
     std::vector<int> prof_op;              // operator of every recorded launch
+    // set-up streams: the coarsest factorisation and the Lanczos estimates of the coarse levels run
+    // beside the fine level's (created on first use)
+    cudaStream_t side[8] = {};
+    cudaEvent_t side_ev[9] = {};
 };
 
 namespace pbm {
@@ -268,7 +276,20 @@ struct ApplyArgs {
     bool with_alpha;       // vectors carry the alpha entry (operator S)
     int dot_slot;          // >= 0: accumulate sum(y_out . x) (APPLY) or ||y_out||^2 (RESID) or
                            // sum(y_out . b) (JACOBI) into sc->red[dot_slot]
+    int rset = 0;          // reduction set: launches that may run concurrently on different streams
+                           // use different sets (partial sums and last-CTA counter, see red_set)
 };
+
+// Scratch of the cross-CTA reductions of one launch: per-CTA partial sums and the last-CTA counter.
+// Set 0 is the default of every solve; sets 1 .. kRedSets - 1 serve concurrent set-up streams.
+constexpr int kRedSets = 9;
+struct RedSet {
+    DevScalars* sc;
+    double* partials;
+    int64_t len;            // doubles available at `partials`
+    unsigned int* counter;
+};
+RedSet red_set(pbm_grid* g, int rset);
 
 // fine level: K(w) (u == nullptr) or S (u, d given; w = rho')
 void launch_fine(pbm_grid* g, bool fp32, const void* w, const void* d, const void* u, const ApplyArgs& a,
@@ -337,6 +358,7 @@ struct NodeArgs {
     int napart;
     double* partials;      // 2 * gridDim.x
     DevScalars* sc;
+    unsigned int* counter; // last-CTA counter
 };
 
 template <class T>
@@ -411,9 +433,10 @@ struct ColEnv {
     double* partials = nullptr;
     int64_t partials_len = 0;
     DevScalars* sc = nullptr;
+    unsigned int* counter = nullptr;   // last-CTA counter (nullptr: &sc->counter[0])
 };
 int64_t cols_scratch_entries(const Geom& G);
-ColEnv env_of(pbm_grid* g);
+ColEnv env_of(pbm_grid* g, int rset = 0);
 // argument builders shared by the single and the batched launches (blocks_out: CTAs of the launch)
 template <class T>
 ColArgs<T> make_fine_args(const ColEnv& env, const Geom& G, const KeHat& kh, const T* w, const T* d, const T* what,
@@ -448,15 +471,13 @@ int fused_num_plans();
 int fused_default_plan(const Geom& G);
 int fused_blocks(const FusedPlan& p);
 int fused_threads(const FusedPlan& p);
-void fused_fine_f32(const FusedPlan& p, DevScalars* sc, double* partials, int64_t partials_len, const Geom& G,
-                    const KeHat& kh, const float* w, const float* d, const float* u, const ApplyArgs& a,
-                    cudaStream_t st);
+void fused_fine_f32(const FusedPlan& p, const RedSet& r, const Geom& G, const KeHat& kh, const float* w,
+                    const float* d, const float* u, const ApplyArgs& a, cudaStream_t st);
 // single-pass FP32 coarse-level operator (stored Galerkin matrices; fused.cu)
 int fused_coarse_num_plans();
 FusedPlan fused_coarse_plan(const Geom& G, int cand);
-void fused_coarse_f32(const FusedPlan& p, DevScalars* sc, double* partials, int64_t partials_len, const Geom& G,
-                      const float* A, const float* bord, const double* s_alpha, const ApplyArgs& a,
-                      cudaStream_t st);
+void fused_coarse_f32(const FusedPlan& p, const RedSet& r, const Geom& G, const float* A, const float* bord,
+                      const double* s_alpha, const ApplyArgs& a, cudaStream_t st);
 void cols_cost(const Geom& G, int L, bool op_s, bool recompute_w, int mode, int esize, double& bytes, double& flops);
 // chunk length the handle uses for the fine column pass of (precision, operator)
 int fine_L(const pbm_grid* g, bool fp32, bool op_s);

@@ -18,8 +18,8 @@ void mr_update2(pbm_grid* g, bool fp32, void* zc, const void* zn, void* d1, void
                 cudaStream_t st);
 void cast_dot(pbm_grid* g, const float* src, double* dst, const double* other, int64_t n, int slot, cudaStream_t st);
 void lz_start(pbm_grid* g, double* v, double* t, double* vprev, const double* diag, int64_t n, cudaStream_t st);
-void lz_b(pbm_grid* g, double* w, const double* v, const double* vprev, const double* sdiag, int64_t n, int j,
-          cudaStream_t st);
+void lz_b(pbm_grid* g, double* w, const double* v, const double* vprev, const double* sdiag, int64_t n, int j0,
+          int j, int rset, cudaStream_t st);
 void lz_next(pbm_grid* g, const double* w, double* v, double* vprev, double* t, const double* diag, int64_t n, int j,
              cudaStream_t st);
 
@@ -146,42 +146,55 @@ static double tridiag_max_eig(const std::vector<double>& a, const std::vector<do
     return hi;
 }
 
-static void lanczos_level(pbm_grid* g, int k, bool op_s, cudaStream_t st) {
+// Lanczos estimate of lambda_max(D^{-1} A) on level k, enqueued on `st` with reduction set `rset`:
+// the coefficients go to sc->lz_a / lz_b from index k * steps; lanczos_finish reads them on the host.
+// Every level has its own vectors (its V-cycle work vectors), reduction slot and set, so the levels
+// can run on concurrent streams.
+static void lanczos_issue(pbm_grid* g, int k, bool op_s, int rset, cudaStream_t st) {
     Level& L = g->L[k];
     const int64_t nv = L.g.n() + (op_s ? 1 : 0);
-    double* v = g->kv64[6];
-    double* vp = g->kv64[7];
-    double* t = g->kv64[8];
-    double* w = g->kv64[9];
+    double* v = L.x64;
+    double* vp = L.b64;
+    double* t = L.r64;
+    double* w = L.t64;
     const int steps = g->desc.lanczos_steps;
+    const int j0 = k * steps;
     launch_inverse_sqrt(L.diag64, L.sdiag64, nv, st);
     lz_start(g, v, t, vp, L.sdiag64, nv, st);
     // a_j = (A t) . t with t = D^{-1/2} v is the operator launch's fused dot product. Mixed grids
     // apply the FP32 operators the smoother will use (the weight is an estimate; the Lanczos
     // vectors and scalars stay FP64); FP64 grids the FP64 ones.
     const bool op32 = g->desc.precision == PBM_MIXED;
-    float* t32 = op32 ? g->kv32[7] : nullptr;
-    float* w32 = op32 ? g->kv32[8] : nullptr;
-    const int slot = 40;
+    float* t32 = op32 ? L.x32 : nullptr;
+    float* w32 = op32 ? L.t32 : nullptr;
+    const int slot = 40 + k;
     for (int j = 0; j < steps; ++j) {
+        ApplyArgs a = args(op32 ? (const void*)t32 : (const void*)t, op32 ? (void*)w32 : (void*)w, EPI_APPLY, nullptr,
+                           nullptr, nullptr, slot);
+        a.rset = rset;
         if (op32) {
             launch_cast(t, false, t32, true, nv, st);
-            level_apply(g, k, true, op_s, args(t32, w32, EPI_APPLY, nullptr, nullptr, nullptr, slot), st);
+            level_apply(g, k, true, op_s, a, st);
             launch_cast(w32, true, w, false, nv, st);
         } else {
-            level_apply(g, k, false, op_s, args(t, w, EPI_APPLY, nullptr, nullptr, nullptr, slot), st);
+            level_apply(g, k, false, op_s, a, st);
         }
-        PBM_CUDA(cudaMemcpyAsync(&g->sc->lz_a[j], &g->sc->red[slot], sizeof(double), cudaMemcpyDeviceToDevice, st));
-        lz_b(g, w, v, vp, L.sdiag64, nv, j, st);
-        lz_next(g, w, v, vp, t, L.sdiag64, nv, j, st);
+        PBM_CUDA(cudaMemcpyAsync(&g->sc->lz_a[j0 + j], &g->sc->red[slot], sizeof(double), cudaMemcpyDeviceToDevice,
+                                 st));
+        lz_b(g, w, v, vp, L.sdiag64, nv, j0, j, rset, st);
+        lz_next(g, w, v, vp, t, L.sdiag64, nv, j0 + j, st);
     }
-    PBM_CUDA(cudaMemcpyAsync(g->sc_host->lz_a, g->sc->lz_a, sizeof(double) * steps, cudaMemcpyDeviceToHost, st));
-    PBM_CUDA(cudaMemcpyAsync(g->sc_host->lz_b, g->sc->lz_b, sizeof(double) * steps, cudaMemcpyDeviceToHost, st));
-    PBM_CUDA(cudaStreamSynchronize(st));
+}
+
+// host side, after the coefficients of level k are in sc_host: the largest Ritz value and the weight
+static void lanczos_finish(pbm_grid* g, int k) {
+    Level& L = g->L[k];
+    const int steps = g->desc.lanczos_steps;
+    const int j0 = k * steps;
     std::vector<double> a, b;
     for (int j = 0; j < steps; ++j) {
-        a.push_back(g->sc_host->lz_a[j]);
-        const double bj = g->sc_host->lz_b[j];
+        a.push_back(g->sc_host->lz_a[j0 + j]);
+        const double bj = g->sc_host->lz_b[j0 + j];
         if (!(bj > 0.0) || j == steps - 1) break;
         b.push_back(bj);
     }
@@ -220,7 +233,6 @@ void setup_hierarchy(pbm_grid* g, bool op_s, cudaStream_t st) {
             if (op_s) launch_restrict(g, k, false, g->L[k].bord64, g->L[k + 1].bord64, false, 1.0, st);
         }
         for (int k = 1; k < nl; ++k) launch_diag(g, k, op_s, st);
-        build_coarsest(g, op_s, st);
     }
     if (mixed) {
         if (op_s) {
@@ -233,11 +245,38 @@ void setup_hierarchy(pbm_grid* g, bool op_s, cudaStream_t st) {
         }
         for (int k = 1; k < nl; ++k) launch_coarse_to_f32(g, k, st);
     }
-    for (int k = 0; k + 1 < nl; ++k) lanczos_level(g, k, op_s, st);
-    upload_omegas(g, st);
-    // coarsest factorisation status
+    // The coarsest factorisation and the Lanczos estimates of the coarse levels run on side streams
+    // beside the fine level's Lanczos (each level with its own vectors, reduction set and slot), then
+    // one synchronisation reads every level's coefficients and the factorisation status.
+    const int steps = g->desc.lanczos_steps;
+    if (steps * std::max(1, nl - 1) > 128) fail(PBM_EINVAL, "lanczos_steps x levels exceeds 128");
+    for (int i = 0; i < nl; ++i) {
+        if (i < 8 && !g->side[i]) PBM_CUDA(cudaStreamCreateWithFlags(&g->side[i], cudaStreamNonBlocking));
+        if (!g->side_ev[i]) PBM_CUDA(cudaEventCreateWithFlags(&g->side_ev[i], cudaEventDisableTiming));
+    }
+    if (!g->side_ev[8]) PBM_CUDA(cudaEventCreateWithFlags(&g->side_ev[8], cudaEventDisableTiming));
+    cudaEvent_t fork = g->side_ev[8];
+    PBM_CUDA(cudaEventRecord(fork, st));
+    if (nl >= 2) {
+        PBM_CUDA(cudaStreamWaitEvent(g->side[0], fork, 0));
+        build_coarsest(g, op_s, g->side[0]);
+        PBM_CUDA(cudaEventRecord(g->side_ev[0], g->side[0]));
+    }
+    for (int k = 1; k + 1 < nl; ++k) {
+        PBM_CUDA(cudaStreamWaitEvent(g->side[k], fork, 0));
+        lanczos_issue(g, k, op_s, k, g->side[k]);
+        PBM_CUDA(cudaEventRecord(g->side_ev[k], g->side[k]));
+    }
+    if (nl >= 2) lanczos_issue(g, 0, op_s, 0, st);
+    for (int k = 0; k + 1 < nl; ++k) PBM_CUDA(cudaStreamWaitEvent(st, g->side_ev[k], 0));
+    PBM_CUDA(cudaMemcpyAsync(g->sc_host->lz_a, g->sc->lz_a, sizeof(double) * steps * std::max(1, nl - 1),
+                             cudaMemcpyDeviceToHost, st));
+    PBM_CUDA(cudaMemcpyAsync(g->sc_host->lz_b, g->sc->lz_b, sizeof(double) * steps * std::max(1, nl - 1),
+                             cudaMemcpyDeviceToHost, st));
     PBM_CUDA(cudaMemcpyAsync(g->sc_host->flags, g->sc->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     PBM_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k + 1 < nl; ++k) lanczos_finish(g, k);
+    upload_omegas(g, st);
     if (nl >= 2 && g->sc_host->flags[0] != 0) fail(PBM_ENONFINITE, "coarsest matrix is not positive definite");
     g->op_ready = op_s ? 2 : 1;
 }
