@@ -43,6 +43,7 @@ struct MarchParams {
     KeHatT<T> K;
     double* partials;  // 2 * nblocks
     DevScalars* sc;
+    unsigned int* counter;  // last-CTA counter
 };
 
 template <class T>
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(32 * BY) k_march(MarchParams<T> P) {
         P.partials[bid] = part_alpha;
         P.partials[nblk + bid] = part_dot;
         __threadfence();
-        const unsigned t = atomicAdd(&P.sc->counter[0], 1u);
+        const unsigned t = atomicAdd(P.counter, 1u);
         s_last = (t == unsigned(nblk - 1));
     }
     __syncthreads();
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(32 * BY) k_march(MarchParams<T> P) {
     }
     block_sum2<NT>(sa, sd, sred);
     if (tid == 0) {
-        P.sc->counter[0] = 0u;
+        *P.counter = 0u;
         const int64_t n = P.n;
         if (DIAG) {
             if (P.with_alpha) P.y[n] = T(KIND == K_COARSE_DIAG ? P.s_alpha : (KIND == K_FINE_DIAG_S ? sa : 1.0));
@@ -395,8 +396,9 @@ static void fill_khat(KeHatT<T>& out, const KeHat& K) {
 }
 
 template <class T>
-static MarchParams<T> base_params(pbm_grid* g, int k) {
+static MarchParams<T> base_params(pbm_grid* g, int k, int rset = 0) {
     MarchParams<T> P{};
+    const RedSet r = red_set(g, rset);
     const Geom& G = g->L[k].g;
     P.nx = G.nx;
     P.ny = G.ny;
@@ -404,8 +406,9 @@ static MarchParams<T> base_params(pbm_grid* g, int k) {
     P.support = G.support;
     P.n = G.n();
     P.m = G.m();
-    P.partials = g->partials;
+    P.partials = r.partials;
     P.sc = g->sc;
+    P.counter = r.counter;
     P.dot_slot = -1;
     P.Kdiag = g->Kdiag;
     fill_khat(P.K, g->kehat);
@@ -418,6 +421,7 @@ static void run(pbm_grid* g, int k, MarchParams<T>& P, cudaStream_t st, const ch
     dim3 grid = march_grid(g->L[k].g, DZ);
     P.DZ = DZ;
     if (int(grid.x * grid.y * grid.z) > g->max_blocks) fail(PBM_EINVAL, "grid too large for the partials buffer");
+    // (every reduction set holds at least 2 max_blocks partial sums)
     k_march<T, BY_, KIND><<<grid, dim3(32, BY_), 0, st>>>(P);
     PBM_LAUNCH(what);
 }
@@ -473,9 +477,9 @@ void launch_coarse(pbm_grid* g, int k, bool fp32, const ApplyArgs& a, cudaStream
         cols_coarse<double>(g, k, L.A64, L.bord64, a, st);
 }
 
-void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st) {
+void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st, int rset) {
     Level& L = g->L[k];
-    auto P = base_params<double>(g, k);
+    auto P = base_params<double>(g, k, rset);
     P.mode = EPI_APPLY;
     P.with_alpha = 1;
     P.y = L.diag64;

@@ -253,8 +253,8 @@ struct pbm_grid {
     std::vector<int> prof_op;              // operator of every recorded launch
     // set-up streams: the coarsest factorisation and the Lanczos estimates of the coarse levels run
     // beside the fine level's (created on first use)
-    cudaStream_t side[8] = {};
-    cudaEvent_t side_ev[9] = {};
+    cudaStream_t side[16] = {};
+    cudaEvent_t side_ev[18] = {};          // [k]: level k's stream done, [16]: fork, [17]: Galerkin chain done
 };
 
 namespace pbm {
@@ -282,7 +282,7 @@ struct ApplyArgs {
 
 // Scratch of the cross-CTA reductions of one launch: per-CTA partial sums and the last-CTA counter.
 // Set 0 is the default of every solve; sets 1 .. kRedSets - 1 serve concurrent set-up streams.
-constexpr int kRedSets = 9;
+constexpr int kRedSets = 16;
 struct RedSet {
     DevScalars* sc;
     double* partials;
@@ -299,7 +299,7 @@ void level_apply(pbm_grid* g, int k, bool fp32, bool op_s, const ApplyArgs& a0, 
 // coarse level k >= 1: explicit element matrices (+ border for S)
 void launch_coarse(pbm_grid* g, int k, bool fp32, const ApplyArgs& a, cudaStream_t st);
 // Jacobi diagonal of a level (S or K), written to L[k].diag64 / diag32 (n + 1, last = alpha)
-void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st);
+void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st, int rset = 0);
 // ------------------------------------------------------------------------------------------------
 // batched launches: one launch covers several systems (grid handles); first[s] is the first CTA of
 // system s (first[nsys] = total CTAs), sc[s] its scalar block; flags[1] == 0 marks a system whose

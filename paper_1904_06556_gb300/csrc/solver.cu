@@ -216,59 +216,61 @@ void setup_hierarchy(pbm_grid* g, bool op_s, cudaStream_t st) {
     const bool mixed = g->desc.precision == PBM_MIXED;
     const int nl = g->levels;
     Level& F = g->L[0];
+    const int steps = g->desc.lanczos_steps;
+    if (steps * std::max(1, nl - 1) > 128) fail(PBM_EINVAL, "lanczos_steps x levels exceeds 128");
+    if (nl > 16) fail(PBM_EINVAL, "more than 16 levels");
+    for (int i = 0; i < 18; ++i) {
+        if (i < 16 && !g->side[i]) PBM_CUDA(cudaStreamCreateWithFlags(&g->side[i], cudaStreamNonBlocking));
+        if (!g->side_ev[i]) PBM_CUDA(cudaEventCreateWithFlags(&g->side_ev[i], cudaEventDisableTiming));
+    }
+    // fine-level data: alpha border b_0 = -sum_i d_i K_i u, the tables of the Galerkin products and of
+    // the S pass, the Jacobi diagonal, and the FP32 copies of mixed grids
     if (op_s) {
-        // alpha border of the fine level: b_0 = -sum_i d_i K_i u (restricted below with scale -1)
         launch_fine(g, false, g->d64, nullptr, nullptr, args(g->u64, F.bord64, EPI_APPLY), st);
         launch_build_what(g, st);
         launch_what_hat(g, st);
-    } else {
-        // K(w): what is not needed (d = 0); keep u zero so that nothing stale is used
     }
     launch_diag(g, 0, op_s, st);
-    if (nl >= 2) {
-        launch_build_level1(g, op_s, st);
-        if (op_s) launch_restrict(g, 0, false, F.bord64, g->L[1].bord64, false, -1.0, st);
-        for (int k = 1; k + 1 < nl; ++k) {
-            launch_build_coarser(g, k, st);
-            if (op_s) launch_restrict(g, k, false, g->L[k].bord64, g->L[k + 1].bord64, false, 1.0, st);
-        }
-        for (int k = 1; k < nl; ++k) launch_diag(g, k, op_s, st);
-    }
     if (mixed) {
         if (op_s) {
             launch_cast(g->w64, false, g->w32, true, F.g.m(), st);
             launch_cast(g->d64, false, g->d32, true, F.g.m(), st);
             launch_cast(g->u64, false, g->u32, true, F.g.n(), st);
-        }
-        else {
+        } else {
             launch_cast(g->rho, false, g->rho32, true, F.g.m(), st);
         }
-        for (int k = 1; k < nl; ++k) launch_coarse_to_f32(g, k, st);
     }
-    // The coarsest factorisation and the Lanczos estimates of the coarse levels run on side streams
-    // beside the fine level's Lanczos (each level with its own vectors, reduction set and slot), then
-    // one synchronisation reads every level's coefficients and the factorisation status.
-    const int steps = g->desc.lanczos_steps;
-    if (steps * std::max(1, nl - 1) > 128) fail(PBM_EINVAL, "lanczos_steps x levels exceeds 128");
-    for (int i = 0; i < nl; ++i) {
-        if (i < 8 && !g->side[i]) PBM_CUDA(cudaStreamCreateWithFlags(&g->side[i], cudaStreamNonBlocking));
-        if (!g->side_ev[i]) PBM_CUDA(cudaEventCreateWithFlags(&g->side_ev[i], cudaEventDisableTiming));
-    }
-    if (!g->side_ev[8]) PBM_CUDA(cudaEventCreateWithFlags(&g->side_ev[8], cudaEventDisableTiming));
-    cudaEvent_t fork = g->side_ev[8];
+    // From here three kinds of work overlap: the fine level's Lanczos estimate on `st`; the Galerkin
+    // chain of the coarse levels on side[1], followed there by level 1's Lanczos; once the chain is
+    // done, the coarsest factorisation on side[0] and the Lanczos of levels 2 .. nl - 2 on side[k].
+    // Each stream has its own reduction set, vectors and slots; one synchronisation reads everything.
+    cudaEvent_t fork = g->side_ev[16], chain = g->side_ev[17];
     PBM_CUDA(cudaEventRecord(fork, st));
     if (nl >= 2) {
-        PBM_CUDA(cudaStreamWaitEvent(g->side[0], fork, 0));
+        const cudaStream_t sg = g->side[1];
+        PBM_CUDA(cudaStreamWaitEvent(sg, fork, 0));
+        launch_build_level1(g, op_s, sg);
+        if (op_s) launch_restrict(g, 0, false, F.bord64, g->L[1].bord64, false, -1.0, sg);
+        for (int k = 1; k + 1 < nl; ++k) {
+            launch_build_coarser(g, k, sg);
+            if (op_s) launch_restrict(g, k, false, g->L[k].bord64, g->L[k + 1].bord64, false, 1.0, sg);
+        }
+        for (int k = 1; k < nl; ++k) launch_diag(g, k, op_s, sg, 1);
+        if (mixed)
+            for (int k = 1; k < nl; ++k) launch_coarse_to_f32(g, k, sg);
+        PBM_CUDA(cudaEventRecord(chain, sg));
+        PBM_CUDA(cudaStreamWaitEvent(g->side[0], chain, 0));
         build_coarsest(g, op_s, g->side[0]);
         PBM_CUDA(cudaEventRecord(g->side_ev[0], g->side[0]));
+        for (int k = 1; k + 1 < nl; ++k) {
+            if (k > 1) PBM_CUDA(cudaStreamWaitEvent(g->side[k], chain, 0));
+            lanczos_issue(g, k, op_s, k, g->side[k]);
+            PBM_CUDA(cudaEventRecord(g->side_ev[k], g->side[k]));
+        }
+        lanczos_issue(g, 0, op_s, 0, st);
+        for (int k = 0; k + 1 < nl; ++k) PBM_CUDA(cudaStreamWaitEvent(st, g->side_ev[k], 0));
+        if (nl == 2) PBM_CUDA(cudaStreamWaitEvent(st, chain, 0));
     }
-    for (int k = 1; k + 1 < nl; ++k) {
-        PBM_CUDA(cudaStreamWaitEvent(g->side[k], fork, 0));
-        lanczos_issue(g, k, op_s, k, g->side[k]);
-        PBM_CUDA(cudaEventRecord(g->side_ev[k], g->side[k]));
-    }
-    if (nl >= 2) lanczos_issue(g, 0, op_s, 0, st);
-    for (int k = 0; k + 1 < nl; ++k) PBM_CUDA(cudaStreamWaitEvent(st, g->side_ev[k], 0));
     PBM_CUDA(cudaMemcpyAsync(g->sc_host->lz_a, g->sc->lz_a, sizeof(double) * steps * std::max(1, nl - 1),
                              cudaMemcpyDeviceToHost, st));
     PBM_CUDA(cudaMemcpyAsync(g->sc_host->lz_b, g->sc->lz_b, sizeof(double) * steps * std::max(1, nl - 1),
