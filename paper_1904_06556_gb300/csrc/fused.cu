@@ -88,23 +88,23 @@ __device__ __forceinline__ int fixed_bits(int support, int nx, int ny, int nz, i
 }
 
 // MODE 0: K(w) x. MODE 2: S x with W_e = Khat H u_e recomputed from the staged u. NT threads per
-// CTA, MINB resident CTAs per SM requested from the register allocator.
-template <int MODE, int NT, int MINB>
+// CTA, MINB resident CTAs per SM requested from the register allocator, an owner tile of TX x TY
+// node columns (compile-time, so that every shared-memory offset is a constant).
+template <int MODE, int NT, int MINB, int TX, int TY>
 __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
     constexpr bool S = MODE == 2;
-    extern __shared__ float4 fused_smem4[];
+    constexpr int EX = TX + 1, EY = TY + 1;
+    constexpr int NW = TX + 2;             // staged nodes per row
+    constexpr int SN = NW * (TY + 2);      // staged nodes per plane (float4 each, w unused)
+    constexpr int RW = 3 * NW;             // floats per row of the global plane
+    constexpr int SF = RW * (TY + 2);      // floats staged per plane
+    constexpr int EC = EX * EY;
+    static_assert(EC <= NT && TX * TY <= NT && SF <= FSLOT * NT, "tile does not fit the CTA");
+    __shared__ float4 sx[2][SN];           // 2 planes of x
+    __shared__ float4 su[S ? 2 : 1][S ? SN : 1];   // 2 planes of u (S)
+    __shared__ float4 sq[4][EC];           // corner values of the element columns
     __shared__ double sred[NT / 32];
     __shared__ bool s_last;
-
-    const int TX = P.TX, TY = P.TY, EX = TX + 1, EY = TY + 1;
-    const int NW = TX + 2;                 // staged nodes per row
-    const int SN = NW * (TY + 2);          // staged nodes per plane (float4 each, w unused)
-    const int RW = 3 * NW;                 // floats per row of the global plane
-    const int SF = RW * (TY + 2);          // floats staged per plane
-    const int EC = EX * EY;
-    float4* sx = fused_smem4;              // 2 planes of x
-    float4* su = fused_smem4 + 2 * SN;     // 2 planes of u (S)
-    float4* sq = fused_smem4 + (S ? 4 : 2) * SN;   // 4 x EC corner values of the element columns
 
     const int t = threadIdx.x;
     const int nx = P.nx, ny = P.ny, nz = P.nz, support = P.support;
@@ -144,12 +144,12 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
             if (S) pu[s] = gofs[s] >= 0 ? __ldg(us + gofs[s]) : 0.0f;
         }
     };
-    // writes the fetched plane k into its buffer, supported nodes zero (the masked vectors the element
-    // matrices act on)
-    auto stage = [&](int k) {
-        float* dx = reinterpret_cast<float*>(sx + (k & 1) * SN);
-        float* du = reinterpret_cast<float*>(su + (k & 1) * SN);
-        const int sh = k == 0 ? 1 : 0;
+    // writes the fetched plane into buffer `buf`, supported nodes zero (the masked vectors the element
+    // matrices act on); first: the plane is plane 0
+    auto stage = [&](int buf, bool first) {
+        float* dx = reinterpret_cast<float*>(sx[buf]);
+        float* du = reinterpret_cast<float*>(su[S ? buf : 0]);
+        const int sh = first ? 1 : 0;
 #pragma unroll
         for (int s = 0; s < FSLOT; ++s)
             if (gofs[s] != -2) {
@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
     const int I = X0 + ox, J = Y0 + oy;
     const bool owner = t < TX * TY && I <= nx && J <= ny;
     const int obits = owner ? fixed_bits(support, nx, ny, nz, I, J) : 0;
+    const int ooff = (oy + 1) * NW + ox + 1;   // staged node of the owner
 
     const float xa = S ? P.x[P.n] : 0.0f;
     const double om = P.mode == EPI_JACOBI ? *P.omega : 0.0;
@@ -179,19 +180,24 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
     const int kstart = max(kz0 - 1, 0);
     float Qlo[3][4], Ulo[3][4], carry[3][4];
     // element weights of the current layer, loaded one layer ahead
-    const int64_t e0 = ex + int64_t(nx) * (ey + int64_t(ny) * kstart), elayer = int64_t(nx) * ny;
+    const int64_t elayer = int64_t(nx) * ny;
+    const float* wp = P.w + (ex + int64_t(nx) * (ey + int64_t(ny) * kstart));
+    const float* dp = S ? P.d + (ex + int64_t(nx) * (ey + int64_t(ny) * kstart)) : nullptr;
     float wn = 0.0f, dn = 0.0f;
     if (ecol && kstart < nz) {
-        wn = __ldg(P.w + e0);
-        if (S) dn = __ldg(P.d + e0);
+        wn = __ldg(wp);
+        if (S) dn = __ldg(dp);
     }
+    // the owner's dofs on plane k
+    int64_t d0 = 3 * (I + int64_t(nx + 1) * (J + int64_t(ny + 1) * kz0));
+    int cur = 0;                           // buffer of the plane below the current layer
     fetch(kstart);
-    stage(kstart);
+    stage(cur, kstart == 0);
     if (kstart + 1 <= nz) fetch(kstart + 1);
     __syncthreads();
     if (ecol) {
-        fused_quad(sx + (kstart & 1) * SN, NW, lx, ly, Qlo);
-        if (S) fused_quad(su + (kstart & 1) * SN, NW, lx, ly, Ulo);
+        fused_quad(sx[cur], NW, lx, ly, Qlo);
+        if (S) fused_quad(su[S ? cur : 0], NW, lx, ly, Ulo);
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -200,26 +206,30 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
 
     for (int k = kstart; k < kz1; ++k) {
         const bool layer = k < nz;
-        if (layer) stage(k + 1);
+        const int nxt = cur ^ 1;           // buffer of plane k + 1
+        if (layer) stage(nxt, false);
         __syncthreads();  // (a) plane k + 1 staged
         if (layer && k + 2 <= nz && k + 1 < kz1) fetch(k + 2);
         const float we = wn, de = dn;
         if (ecol && k + 1 < nz && k + 1 < kz1) {
-            wn = __ldg(P.w + e0 + (k + 1 - kstart) * elayer);
-            if (S) dn = __ldg(P.d + e0 + (k + 1 - kstart) * elayer);
+            wp += elayer;
+            wn = __ldg(wp);
+            if (S) {
+                dp += elayer;
+                dn = __ldg(dp);
+            }
         }
         // the owner's own x on plane k: staged (masked) unless the node is supported
         float4 xo4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         const bool ofixed = (obits >> (k == 0 ? 1 : 0)) & 1;
-        const int64_t d0 = 3 * (I + int64_t(nx + 1) * (J + int64_t(ny + 1) * k));
         if (owner && k >= kz0) {
             if (ofixed) xo4 = make_float4(__ldg(P.x + d0), __ldg(P.x + d0 + 1), __ldg(P.x + d0 + 2), 0.0f);
-            else xo4 = sx[(k & 1) * SN + (oy + 1) * NW + ox + 1];
+            else xo4 = sx[cur][ooff];
         }
         float Bq[3][4];
         if (ecol && layer) {
             float Qhi[3][4];
-            fused_quad(sx + ((k + 1) & 1) * SN, NW, lx, ly, Qhi);
+            fused_quad(sx[nxt], NW, lx, ly, Qhi);
             float X[3][8], Y[3][8];
 #pragma unroll
             for (int c = 0; c < 3; ++c)
@@ -231,7 +241,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
                 }
             if (S) {
                 float Uhi[3][4], U[3][8], Wt[3][8];
-                fused_quad(su + ((k + 1) & 1) * SN, NW, lx, ly, Uhi);
+                fused_quad(su[S ? nxt : 0], NW, lx, ly, Uhi);
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -276,6 +286,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
                     carry[c][q] = 0.0f;
                 }
         }
+        cur = nxt;
         if (k < kz0) continue;  // the layer below the chunk: only its top face is kept
         // inverse xy transform: the element column's values at its 4 corners of plane k
         if (t < EC) {
@@ -290,7 +301,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
                 o[3][c] = a1 + a3;
             }
 #pragma unroll
-            for (int a = 0; a < 4; ++a) sq[a * EC + t] = make_float4(o[a][0], o[a][1], o[a][2], 0.0f);
+            for (int a = 0; a < 4; ++a) sq[a][t] = make_float4(o[a][0], o[a][1], o[a][2], 0.0f);
         }
         __syncthreads();  // (b) corner values of plane k complete
         if (owner) {
@@ -300,7 +311,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
 #pragma unroll
                 for (int di = 1; di >= 0; --di) {
                     // element column (ox + 1 - di, oy + 1 - dj); the node is its corner (di, dj)
-                    const float4 v = sq[(di + 2 * dj) * EC + (oy + 1 - dj) * EX + (ox + 1 - di)];
+                    const float4 v = sq[di + 2 * dj][(oy + 1 - dj) * EX + (ox + 1 - di)];
                     s[0] += v.x;
                     s[1] += v.y;
                     s[2] += v.z;
@@ -328,6 +339,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
                 P.y[d0 + c] = o;
             }
         }
+        d0 += plane;
     }
 
     // per-CTA partials; the last CTA finishes the dot and the alpha entry in a fixed order
@@ -627,23 +639,25 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
 // ------------------------------------------------------------------------------------------------
 // tile plans
 // ------------------------------------------------------------------------------------------------
-// Kernel variants: threads per CTA and the resident CTAs per SM asked of the register allocator.
-static const int kFusedVariants[][2] = {{256, 1}, {256, 2}, {128, 3}, {128, 4}, {256, 3}, {128, 6}};
-constexpr int kFusedNumVariants = int(sizeof(kFusedVariants) / sizeof(kFusedVariants[0]));
-// Candidate owner tiles (TX x TY node columns) per CTA size: (TX + 1)(TY + 1) element columns must
-// fit the CTA's threads and the staged plane, 3 (TX + 2)(TY + 2) floats, its staging slots.
-static const int kTiles256[][2] = {{31, 7}, {15, 15}, {26, 8}, {21, 10}, {43, 4}, {63, 3}};
-static const int kTiles128[][2] = {{15, 7}, {31, 3}, {20, 5}, {24, 4}, {7, 15}, {10, 10}};
-constexpr int kFusedNumTiles = 6;
+// Plans of the fine kernel: threads per CTA, resident CTAs per SM asked of the register allocator, and
+// the owner tile TX x TY ((TX + 1)(TY + 1) element columns fit the CTA; the staged plane,
+// 3 (TX + 2)(TY + 2) floats, fits its staging slots). The list keeps the shapes that timed best on
+// the grids of the workloads.
+#define PBM_FUSED_PLANS(X)                                                                                  \
+    X(0, 256, 2, 31, 7) X(1, 256, 2, 21, 10) X(2, 256, 2, 26, 8) X(3, 256, 2, 15, 15) X(4, 256, 1, 31, 7)    \
+    X(5, 256, 1, 21, 10) X(6, 128, 4, 15, 7) X(7, 128, 4, 20, 5) X(8, 128, 4, 7, 15) X(9, 128, 4, 24, 4)     \
+    X(10, 128, 3, 15, 7) X(11, 128, 3, 24, 4)
+#define PBM_PLAN_ROW(i, nt, minb, tx, ty) {nt, minb, tx, ty},
+static const int kFusedPlans[][4] = {PBM_FUSED_PLANS(PBM_PLAN_ROW)};
+#undef PBM_PLAN_ROW
+constexpr int kFusedNumPlans = int(sizeof(kFusedPlans) / sizeof(kFusedPlans[0]));
 
-// Candidate c: variant c / kFusedNumTiles, tile c % kFusedNumTiles of that variant's CTA size.
 FusedPlan fused_plan(const Geom& G, int cand) {
     FusedPlan p{};
-    const int tile = cand % kFusedNumTiles;
-    p.var = cand / kFusedNumTiles;
-    const int nt = kFusedVariants[p.var][0], per_sm = kFusedVariants[p.var][1];
-    p.TX = nt == 256 ? kTiles256[tile][0] : kTiles128[tile][0];
-    p.TY = nt == 256 ? kTiles256[tile][1] : kTiles128[tile][1];
+    p.var = cand;
+    const int per_sm = kFusedPlans[cand][1];
+    p.TX = kFusedPlans[cand][2];
+    p.TY = kFusedPlans[cand][3];
     p.gx = (G.nx + 1 + p.TX - 1) / p.TX;
     p.gy = (G.ny + 1 + p.TY - 1) / p.TY;
     const int planes = G.nz + 1;
@@ -666,11 +680,11 @@ FusedPlan fused_plan(const Geom& G, int cand) {
     return p;
 }
 
-int fused_num_plans() { return kFusedNumVariants * kFusedNumTiles; }
+int fused_num_plans() { return kFusedNumPlans; }
 
 int fused_blocks(const FusedPlan& p) { return p.gx * p.gy * p.gz; }
 
-int fused_threads(const FusedPlan& p) { return kFusedVariants[p.var][0]; }
+int fused_threads(const FusedPlan& p) { return kFusedPlans[p.var][0]; }
 
 // plan used until the autotuner has timed the candidates (and for grids it does not tune): fewest
 // plane steps per SM (waves x (DZ + 1) / resident CTAs), then fewest element columns computed
@@ -679,7 +693,7 @@ int fused_default_plan(const Geom& G) {
     double bc = 1e300;
     for (int c = 0; c < fused_num_plans(); ++c) {
         const FusedPlan p = fused_plan(G, c);
-        const int per_sm = kFusedVariants[p.var][1];
+        const int per_sm = kFusedPlans[p.var][1];
         const int blocks = fused_blocks(p);
         const double waves = double((blocks + 152 * per_sm - 1) / (152 * per_sm));
         const double cols = double(p.gx) * (p.TX + 1) * p.gy * (p.TY + 1);
@@ -692,21 +706,14 @@ int fused_default_plan(const Geom& G) {
     return best;
 }
 
-static size_t fused_smem_bytes(const FusedPlan& p, bool s) {
-    const int SN = (p.TX + 2) * (p.TY + 2);
-    const int EC = (p.TX + 1) * (p.TY + 1);
-    return sizeof(float4) * (size_t((s ? 4 : 2) * SN) + size_t(4 * EC));
-}
-
 template <int MODE>
-static void fused_launch(const FusedPlan& p, int blocks, size_t smem, const FusedArgs& P, cudaStream_t st) {
+static void fused_launch(const FusedPlan& p, int blocks, const FusedArgs& P, cudaStream_t st) {
     switch (p.var) {
-        case 0: k_fused_f32<MODE, 256, 1><<<blocks, 256, smem, st>>>(P); break;
-        case 1: k_fused_f32<MODE, 256, 2><<<blocks, 256, smem, st>>>(P); break;
-        case 2: k_fused_f32<MODE, 128, 3><<<blocks, 128, smem, st>>>(P); break;
-        case 3: k_fused_f32<MODE, 128, 4><<<blocks, 128, smem, st>>>(P); break;
-        case 4: k_fused_f32<MODE, 256, 3><<<blocks, 256, smem, st>>>(P); break;
-        default: k_fused_f32<MODE, 128, 6><<<blocks, 128, smem, st>>>(P); break;
+#define PBM_PLAN_CASE(i, nt, minb, tx, ty) \
+    case i: k_fused_f32<MODE, nt, minb, tx, ty><<<blocks, nt, 0, st>>>(P); break;
+        PBM_FUSED_PLANS(PBM_PLAN_CASE)
+#undef PBM_PLAN_CASE
+        default: fail(PBM_EINVAL, "fused operator: unknown plan");
     }
 }
 
@@ -749,9 +756,8 @@ void fused_fine_f32(const FusedPlan& p, const RedSet& r, const Geom& G, const Ke
     P.partials = r.partials;
     P.sc = r.sc;
     P.counter = r.counter;
-    const size_t smem = fused_smem_bytes(p, s);
-    if (s) fused_launch<2>(p, blocks, smem, P, st);
-    else fused_launch<0>(p, blocks, smem, P, st);
+    if (s) fused_launch<2>(p, blocks, P, st);
+    else fused_launch<0>(p, blocks, P, st);
     PBM_LAUNCH("fused FP32 fine operator");
 }
 
