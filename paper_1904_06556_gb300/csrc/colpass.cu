@@ -671,10 +671,16 @@ void autotune_fine(pbm_grid* g) {
                 }
                 g->fusedP[op] = bestP;
             }
-        // plans of the single-pass FP32 coarse operator, per level that is ever applied
+        // plans of the single-pass FP32 coarse operator, per level that is ever applied. Levels of
+        // 32768 elements or more keep the two passes without timing: their element matrices (1.2 KB
+        // per element) dominate and the single pass reads those of its tile halos twice.
         if (mixed)
             for (int k = 1; k + 1 < g->levels; ++k) {
                 const Level& L = g->L[k];
+                if (L.g.m() >= 32768) {
+                    g->coarseP[0][k] = g->coarseP[1][k] = -1;
+                    continue;
+                }
                 PBM_CUDA(cudaMemset(L.A32, 0, sizeof(float) * NTRI * L.g.m()));
                 PBM_CUDA(cudaMemset(L.bord32, 0, sizeof(float) * (L.g.n() + 1)));
                 for (int op = 0; op < 2; ++op) {
