@@ -229,3 +229,19 @@ def random_state(nx: int, ny: int, nz: int, seed: int, u_scale: float = 1.0, p: 
     return dict(u=u, alpha=float(rng.uniform(0.5, 2.0)), nu_lo=rng.uniform(0.0, 2.0, m),
                 nu_up=rng.uniform(0.0, 2.0, m), rho=rng.uniform(1e-3, 1.0, m), mu_lo=rng.uniform(0.2, 2.0, m),
                 mu_up=rng.uniform(0.2, 2.0, m), p=p, q_lo=q, q_up=q, V=0.3 * m, rho_lo=1e-3, rho_up=1.0)
+
+
+def ip_random_state(nx: int, ny: int, nz: int, seed: int, fixed_dofs: np.ndarray | None = None, u_scale: float = 0.5,
+                    rho_lo: float = 1e-3, rho_up: float = 1.0) -> dict:
+    """A strictly feasible random point of the interior-point method for operator tests: rho inside (rho_lo, rho_up),
+    nu_lo, nu_up > 0, u with zeros on `fixed_dofs`, and barrier parameters r, s."""
+    rng = np.random.default_rng(seed)
+    m, n = elem_count(nx, ny, nz), dof_count(nx, ny, nz)
+    u = rng.standard_normal(n) * u_scale
+    if fixed_dofs is not None:
+        u[fixed_dofs] = 0.0
+    rho = rho_lo + (rho_up - rho_lo) * rng.uniform(0.05, 0.95, m)
+    return dict(u=u, alpha=float(rng.uniform(-1.0, 1.0)), rho=rho, nu_lo=rng.uniform(0.1, 2.0, m),
+                nu_up=rng.uniform(0.1, 2.0, m), V=0.3 * m, rho_lo=rho_lo, rho_up=rho_up,
+                r=float(rng.uniform(0.01, 0.1)), s=float(rng.uniform(0.01, 0.1)))
+

@@ -111,7 +111,8 @@ def test_apply_K_fp64(pkg, dims, bc):
     assert np.array_equal(y, y2)                       # deterministic: same bits on a second call
 
 
-@pytest.mark.parametrize("dims,bc", [((34, 10, 6), "cantilever"), ((64, 32, 32), "cantilever")])
+@pytest.mark.parametrize("dims,bc", [((34, 10, 6), "cantilever"), ((64, 32, 32), "cantilever"), ((2, 2, 2), "bridge_edges"),
+                                     ((2, 2, 4), "free"), ((36, 4, 2), "bridge_edges")])
 def test_apply_K_fp32(pkg, dims, bc):
     G = pkg.Grid(*dims, levels_for(*dims), bc)
     g = fem.Grid(*dims, bc)
@@ -151,7 +152,7 @@ def _check_epilogues(G, op, A_apply, diag, x, b, tol):
 
 
 @pytest.mark.parametrize("dims,bc", [((8, 4, 4), "cantilever"), ((34, 10, 6), "bridge_corners"),
-                                     ((64, 20, 12), "cantilever")])
+                                     ((64, 20, 12), "cantilever"), ((18, 6, 4), "bridge_edges")])
 def test_fused_fp32_K_epilogues_and_jacobi_diagonal(pkg, dims, bc):
     """The single-pass FP32 operator (several CTA tiles and chunks, ragged edges) with each fused
     epilogue, and the Jacobi diagonal of K (bit-level FP64 set-up) against the oracle's CSR K."""
@@ -169,7 +170,7 @@ def test_fused_fp32_K_epilogues_and_jacobi_diagonal(pkg, dims, bc):
 
 
 @pytest.mark.parametrize("dims,bc,seed", [((8, 4, 4), "cantilever", 0), ((34, 10, 6), "bridge_corners", 3),
-                                          ((64, 20, 12), "cantilever", 4)])
+                                          ((64, 20, 12), "cantilever", 4), ((18, 6, 4), "bridge_edges", 8)])
 def test_fused_fp32_S_epilogues_and_jacobi_diagonal(pkg, dims, bc, seed):
     """The same for S of eq. (S): the rank-one terms recomputed from u in every launch, the alpha row
     counted once per element across CTA tiles and chunks, and the Jacobi diagonal of S."""
