@@ -270,6 +270,49 @@ int pbm_vcycle(pbm_grid* g, int op, const double* b_dev, double* x_dev, void* st
 int pbm_minres_solve(pbm_grid* g, int op, const double* b_dev, double* x_dev, double rtol, int maxit,
                      pbm_solve_info* info, void* stream);
 
+/* ---- interior-point Newton system (Section 4.1) ----------------------------------------------
+ * The primal-dual interior-point method's Newton step on the perturbed KKT system of eq. (1)
+ * (barrier parameters r, s), reduced by two Schur complements to eq. (S_IP):
+ *   S_IP = [K(rho), 0; 0, 0] + sum_i d_i [K_i u; 1][K_i u; 1]^T,
+ *   d_i = 1 / (nu_lo_i / (rho_i - rho_lo) + nu_up_i / (rho_up - rho_i)).
+ * It has the structure of the PBM matrix S (the alpha border has the opposite sign), so the same
+ * operator kernels, Galerkin hierarchy and MG-MINRES solve it. The right-hand side and the
+ * recovered increments are those of the Newton step J dz = -res with J the Jacobian eq. (gradres):
+ *   rhs = [f - K(rho + d c) u ; V - sum(rho + d c)],  c_i = res_3 - res_4/(rho_i - rho_lo) + res_5/(rho_up - rho_i),
+ *   drho = d (K_i u . du + dalpha + c),  dnu_up by the form of eq. (Delta_onu),  dnu_lo by eq. (Delta_unu),
+ * with res_3 = 1/2 u^T K_i u + alpha + nu_lo - nu_up, res_4 = nu_lo (rho - rho_lo) - r,
+ * res_5 = nu_up (rho_up - rho) - s. Supported dofs are eliminated as everywhere. */
+typedef struct pbm_ip_state {
+    const double* u_dev;      /* n: displacement (supported dofs ignored)                           */
+    double alpha;             /* volume multiplier                                                    */
+    const double* rho_dev;    /* m: densities, strictly rho_lo < rho_i < rho_up                       */
+    const double* nu_lo_dev;  /* m: bound multipliers, > 0                                            */
+    const double* nu_up_dev;  /* m: > 0                                                               */
+    double V, rho_lo, rho_up; /* volume bound and density bounds                                      */
+    double r, s;              /* barrier parameters of the lower and upper bounds, > 0                */
+} pbm_ip_state;
+
+/* Sets the interior-point state: the per-element coefficients above and the Galerkin hierarchy,
+ * Jacobi diagonals, weights and coarsest factorisation of S_IP. The state's arrays are read during
+ * this call only. Replaces any PBM state of the grid (pbm_set_state replaces this one). Synchronises
+ * `stream`. Errors: PBM_EINVAL (null array, a point that is not strictly feasible, r or s <= 0). */
+int pbm_ip_set_state(pbm_grid* g, const pbm_ip_state* st, void* stream);
+
+/* y = S_IP x (n + 1 FP64 entries each, alpha last; supported rows and columns the identity). */
+int pbm_ip_apply_S(pbm_grid* g, const double* x_dev, double* y_dev, void* stream);
+
+/* rhs (n + 1) of the reduced system at the state; f_dev: n load vector. */
+int pbm_ip_reduced_rhs(pbm_grid* g, const double* f_dev, double* rhs_dev, void* stream);
+
+/* Solves S_IP dz = rhs by MG-MINRES as pbm_minres_solve does (true relative residual <= rtol;
+ * dz_dev holds the initial guess on entry). Synchronises. Errors as pbm_minres_solve. */
+int pbm_ip_solve(pbm_grid* g, const double* rhs_dev, double* dz_dev, double rtol, int maxit, pbm_solve_info* info,
+                 void* stream);
+
+/* The density and multiplier increments (m entries each) from the reduced solution dz = [du; dalpha]. */
+int pbm_ip_recover(pbm_grid* g, const double* dz_dev, double* drho_dev, double* dnu_lo_dev, double* dnu_up_dev,
+                   void* stream);
+
 /* One Newton step of Algorithm 2 on the augmented Lagrangian: builds S and its rhs at `st`,
  * solves the reduced system to relative residual eps_mr, recovers (dnu_lo, dnu_up) by
  * eq. (deltanu), backtracks (Armijo, c1 = 1e-4, halving, at most 30 halvings) and updates

@@ -190,6 +190,44 @@ class Grid:
                                                 _ptr(y, f, n, "y"), C.byref(d) if dot else None, _stream()))
         return y, (d.value if dot else None)
 
+    # ---- interior-point Newton system (pbm_ip_*) ----
+    def ip_set_state(self, st: dict):
+        """st: u (n), rho, nu_lo, nu_up (m) FP64 CUDA tensors; alpha, V, rho_lo, rho_up, r, s floats."""
+        s = _lib.IPState(_ptr(st["u"], n=self.n, name="u").value, float(st["alpha"]),
+                         _ptr(st["rho"], n=self.m, name="rho").value, _ptr(st["nu_lo"], n=self.m, name="nu_lo").value,
+                         _ptr(st["nu_up"], n=self.m, name="nu_up").value, float(st["V"]), float(st["rho_lo"]),
+                         float(st["rho_up"]), float(st["r"]), float(st["s"]))
+        self._check(self._L.pbm_ip_set_state(self._h, C.byref(s), _stream()))
+
+    def ip_apply_S(self, x: torch.Tensor, out: torch.Tensor | None = None):
+        y = out if out is not None else torch.empty(self.n + 1, dtype=torch.float64, device=x.device)
+        self._check(self._L.pbm_ip_apply_S(self._h, _ptr(x, n=self.n + 1, name="x"), _ptr(y, n=self.n + 1, name="y"),
+                                           _stream()))
+        return y
+
+    def ip_reduced_rhs(self, f: torch.Tensor):
+        rhs = torch.empty(self.n + 1, dtype=torch.float64, device=f.device)
+        self._check(self._L.pbm_ip_reduced_rhs(self._h, _ptr(f, n=self.n, name="f"), _ptr(rhs, n=self.n + 1),
+                                               _stream()))
+        return rhs
+
+    def ip_solve(self, rhs: torch.Tensor, rtol: float = 1e-8, maxit: int = 500, x0: torch.Tensor | None = None,
+                 check: bool = True):
+        dz = x0.clone() if x0 is not None else torch.zeros(self.n + 1, dtype=torch.float64, device=rhs.device)
+        inf = _lib.SolveInfo()
+        rc = self._L.pbm_ip_solve(self._h, _ptr(rhs, n=self.n + 1, name="rhs"), _ptr(dz, n=self.n + 1),
+                                  float(rtol), int(maxit), C.byref(inf), _stream())
+        if check:
+            self._check(rc)
+        return dz, {k: getattr(inf, k) for k, _ in _lib.SolveInfo._fields_}
+
+    def ip_recover(self, dz: torch.Tensor):
+        """(drho, dnu_lo, dnu_up) from the reduced solution dz (pbm_ip_recover)."""
+        out = [torch.empty(self.m, dtype=torch.float64, device=dz.device) for _ in range(3)]
+        self._check(self._L.pbm_ip_recover(self._h, _ptr(dz, n=self.n + 1, name="dz"), *[_ptr(t) for t in out],
+                                           _stream()))
+        return tuple(out)
+
     def set_fp32_plan(self, op: str, plan: int):
         """Overrides the autotuned tile plan of the FP32 fine operator for op (pbm_set_fp32_plan)."""
         self._check(self._L.pbm_set_fp32_plan(self._h, _lib.OPS[op], int(plan)))

@@ -47,6 +47,12 @@ class State(C.Structure):
                 ("rho_up", C.c_double)]
 
 
+class IPState(C.Structure):
+    _fields_ = [("u_dev", C.c_void_p), ("alpha", C.c_double), ("rho_dev", C.c_void_p), ("nu_lo_dev", C.c_void_p),
+                ("nu_up_dev", C.c_void_p), ("V", C.c_double), ("rho_lo", C.c_double), ("rho_up", C.c_double),
+                ("r", C.c_double), ("s", C.c_double)]
+
+
 class ProfileStats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("total_ms", C.c_double), ("bytes", C.c_double), ("flops", C.c_double)]
 
@@ -101,6 +107,11 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pbm_apply_level_f32": (i, [vp, i, i, i, vp, vp, vp, C.POINTER(C.c_double), vp]),
         "pbm_get_diag": (i, [vp, i, vp, vp]),
         "pbm_fp32_plan_count": (i, []),
+        "pbm_ip_set_state": (i, [vp, C.POINTER(IPState), vp]),
+        "pbm_ip_apply_S": (i, [vp, vp, vp, vp]),
+        "pbm_ip_reduced_rhs": (i, [vp, vp, vp, vp]),
+        "pbm_ip_solve": (i, [vp, vp, vp, d, i, C.POINTER(SolveInfo), vp]),
+        "pbm_ip_recover": (i, [vp, vp, vp, vp, vp, vp]),
         "pbm_set_fp32_plan": (i, [vp, i, i]),
         "pbm_set_state": (i, [vp, C.POINTER(State), vp]),
         "pbm_apply_S": (i, [vp, vp, vp, vp]),

@@ -29,6 +29,9 @@ void launch_axpy(double* y, const double* x, double kappa, int64_t n, cudaStream
 void launch_scale(const double* a, double* b, double s, int64_t n, cudaStream_t st);
 void launch_mult_update(pbm_grid* g, const double* c2, pbm_state* s, double beta, bool only_rho, cudaStream_t st);
 void launch_gap_sums(pbm_grid* g, const double* c2, const pbm_state* s, int slot, cudaStream_t st);
+void launch_ip_coeffs(pbm_grid* g, const pbm_ip_state* s, const double* c2, double* coef, cudaStream_t st);
+void launch_ip_recover(pbm_grid* g, const double* wdu, const double* da, const double* coef, double rho_lo,
+                       double rho_up, double* drho, double* dnl, double* dnu, cudaStream_t st);
 
 static thread_local std::string g_last_error;
 static std::atomic<long long> g_launches{0};
@@ -416,6 +419,7 @@ int pbm_destroy_grid(pbm_grid* g) {
     }
     for (cudaGraphExec_t e : g->mr_graph)
         if (e) cudaGraphExecDestroy(e);
+    dfree(g->ip_work);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     for (auto& sst : g->side)
         if (sst) cudaStreamDestroy(sst);
@@ -650,7 +654,134 @@ int pbm_set_state(pbm_grid* g, const pbm_state* s, void* stream) {
     g->alpha = s->alpha;
     g->V = s->V;
     g->state_set = true;
+    g->ip_set = false;
     setup_hierarchy(g, true, st);
+    PBM_CATCH
+}
+
+// ------------------------------------------------------------------------------------------------
+// interior-point Newton system (Section 4.1). S_IP = Jf S Jf with Jf = diag(I, -1) and S the PBM-form
+// operator (border -1) built from w = rho and the weights d: the applies and the solve flip the
+// sign of the alpha entry around the PBM-form kernels.
+// ------------------------------------------------------------------------------------------------
+static double* ip_work(pbm_grid* g) {
+    if (!g->ip_work) g->ip_work = (double*)dalloc(g, sizeof(double) * 2 * size_t(g->L[0].g.n() + 1));
+    return g->ip_work;
+}
+
+int pbm_ip_set_state(pbm_grid* g, const pbm_ip_state* s, void* stream) {
+    PBM_TRY
+    if (!g || !s || !s->u_dev || !s->rho_dev || !s->nu_lo_dev || !s->nu_up_dev) fail(PBM_EINVAL, "null argument");
+    if (!(s->r > 0.0) || !(s->s > 0.0)) fail(PBM_EINVAL, "barrier parameters must be > 0");
+    if (!(s->rho_up > s->rho_lo)) fail(PBM_EINVAL, "rho_up must exceed rho_lo");
+    set_device(g);
+    const cudaStream_t st = S(stream);
+    const int64_t m = g->L[0].g.m();
+    ip_work(g);
+    launch_mask_copy(g, s->u_dev, g->u64, st);
+    double* c2 = g->aux64 + 5 * m;
+    launch_elem_energy(g, g->u64, nullptr, c2, st);
+    launch_ip_coeffs(g, s, c2, g->aux64, st);
+    PBM_CUDA(cudaMemcpyAsync(&g->sc_host->red[8], &g->sc->red[8], sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
+    PBM_CUDA(cudaStreamSynchronize(st));
+    if (g->sc_host->red[10] != 0.0) fail(PBM_EINVAL, "interior-point state not strictly feasible or not finite");
+    g->s_alpha = g->sc_host->red[8];
+    PBM_CUDA(cudaMemcpyAsync(&g->sc->salpha, &g->sc->red[8], sizeof(double), cudaMemcpyDeviceToDevice, st));
+    g->alpha = s->alpha;
+    g->V = s->V;
+    g->ip_rho_lo = s->rho_lo;
+    g->ip_rho_up = s->rho_up;
+    g->state_set = false;
+    g->ip_set = true;
+    setup_hierarchy(g, true, st);
+    PBM_CATCH
+}
+
+static void require_ip(const pbm_grid* g) {
+    if (!g->ip_set) fail(PBM_ESTATE, "pbm_ip_set_state has not been called");
+}
+
+int pbm_ip_apply_S(pbm_grid* g, const double* x_dev, double* y_dev, void* stream) {
+    PBM_TRY
+    if (!g || !x_dev || !y_dev) fail(PBM_EINVAL, "null argument");
+    require_ip(g);
+    set_device(g);
+    const cudaStream_t st = S(stream);
+    const int64_t n = g->L[0].g.n();
+    double* xf = ip_work(g);
+    PBM_CUDA(cudaMemcpyAsync(xf, x_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    set_entry(xf, n, x_dev + n, -1.0, 0.0, st);
+    ApplyArgs a{};
+    a.x = xf;
+    a.y = y_dev;
+    a.mode = EPI_APPLY;
+    a.with_alpha = true;
+    a.dot_slot = -1;
+    launch_fine(g, false, g->w64, g->d64, g->u64, a, st);
+    set_entry(y_dev, n, y_dev + n, -1.0, 0.0, st);
+    PBM_CATCH
+}
+
+int pbm_ip_reduced_rhs(pbm_grid* g, const double* f_dev, double* rhs_dev, void* stream) {
+    PBM_TRY
+    if (!g || !f_dev || !rhs_dev) fail(PBM_EINVAL, "null argument");
+    require_ip(g);
+    set_device(g);
+    const cudaStream_t st = S(stream);
+    const int64_t n = g->L[0].g.n();
+    // rhs_u = f - K(rho + d c) u (supported rows: f - u = 0); rhs_alpha = V - sum(rho + d c)
+    ApplyArgs a{};
+    a.x = g->u64;
+    a.y = rhs_dev;
+    a.b = f_dev;
+    a.mode = EPI_RESID;
+    a.dot_slot = -1;
+    launch_fine(g, false, g->wr64, nullptr, nullptr, a, st);
+    set_entry(rhs_dev, n, &g->sc->red[9], -1.0, g->V, st);
+    PBM_CATCH
+}
+
+int pbm_ip_solve(pbm_grid* g, const double* rhs_dev, double* dz_dev, double rtol, int maxit, pbm_solve_info* info,
+                 void* stream) {
+    PBM_TRY
+    if (!g || !rhs_dev || !dz_dev) fail(PBM_EINVAL, "null argument");
+    if (!(rtol > 0.0) || maxit < 1) fail(PBM_EINVAL, "rtol must be > 0 and maxit >= 1");
+    require_ip(g);
+    set_device(g);
+    const cudaStream_t st = S(stream);
+    const int64_t n = g->L[0].g.n();
+    auto t0 = std::chrono::steady_clock::now();
+    if (g->op_ready != 2) setup_hierarchy(g, true, st);
+    const double setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    // the PBM-form system S (Jf dz) = Jf rhs
+    double* bf = ip_work(g) + (n + 1);
+    PBM_CUDA(cudaMemcpyAsync(bf, rhs_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    set_entry(bf, n, rhs_dev + n, -1.0, 0.0, st);
+    set_entry(dz_dev, n, dz_dev + n, -1.0, 0.0, st);
+    pbm_solve_info inf{};
+    const int rc = solve(g, true, bf, dz_dev, rtol, maxit, &inf, st);
+    set_entry(dz_dev, n, dz_dev + n, -1.0, 0.0, st);
+    inf.setup_ms = setup_ms;
+    if (info) *info = inf;
+    if (rc != PBM_OK) {
+        set_error(rc == PBM_EBREAKDOWN ? "MINRES breakdown: preconditioner not positive definite"
+                                       : "MINRES did not reach the tolerance");
+        return rc;
+    }
+    PBM_CATCH
+}
+
+int pbm_ip_recover(pbm_grid* g, const double* dz_dev, double* drho_dev, double* dnu_lo_dev, double* dnu_up_dev,
+                   void* stream) {
+    PBM_TRY
+    if (!g || !dz_dev || !drho_dev || !dnu_lo_dev || !dnu_up_dev) fail(PBM_EINVAL, "null argument");
+    require_ip(g);
+    set_device(g);
+    const cudaStream_t st = S(stream);
+    const int64_t m = g->L[0].g.m(), n = g->L[0].g.n();
+    double* wdu = g->aux64 + 6 * m;
+    launch_elem_energy(g, g->u64, dz_dev, wdu, st);
+    launch_ip_recover(g, wdu, dz_dev + n, g->aux64, g->ip_rho_lo, g->ip_rho_up, drho_dev, dnu_lo_dev, dnu_up_dev, st);
     PBM_CATCH
 }
 

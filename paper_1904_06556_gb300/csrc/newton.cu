@@ -265,3 +265,84 @@ void launch_gap_sums(pbm_grid* g, const double* c2, const pbm_state* s, int slot
 }
 
 }  // namespace pbm
+
+// ------------------------------------------------------------------------------------------------
+// Interior-point Newton system (Section 4.1). With c2 = u_e^T K_e u_e per element:
+//   res_3 = c2/2 + alpha + nu_lo - nu_up,  res_4 = nu_lo (rho - rho_lo) - r,  res_5 = nu_up (rho_up - rho) - s,
+//   d = 1 / (nu_lo / (rho - rho_lo) + nu_up / (rho_up - rho)),
+//   c = res_3 - res_4 / (rho - rho_lo) + res_5 / (rho_up - rho)        (from J dz = -res, eq. (gradres)),
+// so that S_IP = [K(rho), 0; 0, 0] + sum_i d_i [K_i u; 1][K_i u; 1]^T (eq. (S_IP)) and the right-hand side is
+// [f - K(rho + d c) u ; V - sum(rho + d c)].
+// ------------------------------------------------------------------------------------------------
+namespace pbm {
+
+// outputs: w = rho, d, wr = rho + d c, coef rows c, res_3, res_4, res_5, nu_lo - nu_up;
+// sums: 0 sum d, 1 sum (rho + d c), 2 #elements not strictly feasible or not finite
+__global__ void k_ip_coeffs(int64_t m, const double* __restrict__ c2, const double* __restrict__ rho,
+                            const double* __restrict__ nul, const double* __restrict__ nuu, double alpha, double rho_lo,
+                            double rho_up, double r, double s, double* __restrict__ w, double* __restrict__ d,
+                            double* __restrict__ wr, double* __restrict__ coef, double* partials, unsigned* counter,
+                            double* out) {
+    double acc[3] = {0, 0, 0};
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
+        const double re = rho[e], nl = nul[e], nu = nuu[e];
+        const double gl = re - rho_lo, gu = rho_up - re;
+        const double r3 = 0.5 * c2[e] + alpha + nl - nu;
+        const double r4 = nl * gl - r;
+        const double r5 = nu * gu - s;
+        const double de = 1.0 / (nl / gl + nu / gu);
+        const double ce = r3 - r4 / gl + r5 / gu;
+        w[e] = re;
+        d[e] = de;
+        wr[e] = re + de * ce;
+        coef[e] = ce;
+        coef[m + e] = r3;
+        coef[2 * m + e] = r4;
+        coef[3 * m + e] = r5;
+        coef[4 * m + e] = nl - nu;
+        acc[0] += de;
+        acc[1] += re + de * ce;
+        const bool ok = gl > 0.0 && gu > 0.0 && nl > 0.0 && nu > 0.0 && isfinite(de) && isfinite(ce) && de > 0.0;
+        acc[2] += ok ? 0.0 : 1.0;
+    }
+    finish_multi<3>(acc, partials, counter, out);
+}
+
+void launch_ip_coeffs(pbm_grid* g, const pbm_ip_state* s, const double* c2, double* coef, cudaStream_t st) {
+    const int64_t m = g->L[0].g.m();
+    k_ip_coeffs<<<NG, NB, 0, st>>>(m, c2, s->rho_dev, s->nu_lo_dev, s->nu_up_dev, s->alpha, s->rho_lo, s->rho_up, s->r,
+                                   s->s, g->w64, g->d64, g->wr64, coef, g->partials, &g->sc->counter[3],
+                                   &g->sc->red[8]);
+    PBM_LAUNCH("ip coeffs");
+}
+
+// increments from the reduced solution: wdu = u_e^T K_e du_e, da = dz[n];
+//   drho = d (wdu + da + c),
+//   dnu_up = ((rho - rho_lo)(wdu + da + res_3) - (nu_lo - nu_up) drho - res_4 - res_5) / (rho_up - rho_lo),
+//   dnu_lo = dnu_up - wdu - da - res_3
+__global__ void k_ip_recover(int64_t m, const double* __restrict__ wdu, const double* __restrict__ da_p,
+                             const double* __restrict__ rho, const double* __restrict__ d,
+                             const double* __restrict__ coef, double rho_lo, double rho_up, double* __restrict__ drho,
+                             double* __restrict__ dnl, double* __restrict__ dnu) {
+    const double da = *da_p;
+    const double inv = 1.0 / (rho_up - rho_lo);
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
+        const double ce = coef[e], r3 = coef[m + e], r4 = coef[2 * m + e], r5 = coef[3 * m + e];
+        const double ndiff = coef[4 * m + e];
+        const double q = wdu[e] + da;
+        const double dr = d[e] * (q + ce);
+        const double du_ = ((rho[e] - rho_lo) * (q + r3) - ndiff * dr - r4 - r5) * inv;
+        drho[e] = dr;
+        dnu[e] = du_;
+        dnl[e] = du_ - q - r3;
+    }
+}
+
+void launch_ip_recover(pbm_grid* g, const double* wdu, const double* da, const double* coef, double rho_lo,
+                       double rho_up, double* drho, double* dnl, double* dnu, cudaStream_t st) {
+    const int64_t m = g->L[0].g.m();
+    k_ip_recover<<<NG, NB, 0, st>>>(m, wdu, da, g->w64, g->d64, coef, rho_lo, rho_up, drho, dnl, dnu);
+    PBM_LAUNCH("ip recover");
+}
+
+}  // namespace pbm

@@ -231,7 +231,10 @@ struct pbm_grid {
     // operator state: 0 = none, 1 = K(rho) hierarchy current, 2 = S hierarchy current
     int op_ready = 0;
     bool rho_set = false;
-    bool state_set = false;
+    bool state_set = false;           // a PBM state (pbm_set_state) defines S
+    bool ip_set = false;              // an interior-point state (pbm_ip_set_state) defines S
+    double ip_rho_lo = 0.0, ip_rho_up = 1.0;
+    double* ip_work = nullptr;        // 2 (n + 1): interior-point right-hand side and operand copies
     double alpha = 0.0, V = 0.0;      // of the current state
     double sum_rho1 = 0.0, sum_wr = 0.0, gl2 = 0.0;   // reductions of the coefficient kernel
     int64_t bytes = 0;

@@ -273,6 +273,45 @@ def test_apply_S_rhs_and_compliance(pkg, dims, bc, seed, us):
 
 
 # ------------------------------------------------------------------------------------------------
+# interior-point Newton system (Section 4.1)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dims,bc,levels,precision", [((8, 4, 4), "cantilever", 2, "fp64"),
+                                                      ((16, 8, 8), "bridge_corners", 3, "fp64"),
+                                                      ((16, 8, 8), "cantilever", 3, "mixed")])
+def test_ip_newton_system_matches_oracle(pkg, dims, bc, levels, precision):
+    from oracle import ip
+    g = fem.Grid(*dims, bc)
+    d = synthetic.ip_random_state(*dims, 21, fixed_dofs=g.fixed_dofs())
+    pb = pbm.Problem(g, synthetic.load_vector(*dims, "end_edge"), d["V"], d["rho_lo"], d["rho_up"])
+    st = ip.state_from_dict(d)
+    cf = ip.coeffs(pb, st, d["r"], d["s"])
+    G = pkg.Grid(*dims, levels, bc, precision=precision)
+    sd = {k: dev(d[k]) for k in ("u", "rho", "nu_lo", "nu_up")}
+    sd.update({k: d[k] for k in ("alpha", "V", "rho_lo", "rho_up", "r", "s")})
+    G.ip_set_state(sd)
+    x = np.random.default_rng(3).standard_normal(pb.n + 1)
+    assert rel(host(G.ip_apply_S(dev(x))), ip.apply_S(pb, st, cf, x)) < 1e-12
+    rhs = G.ip_reduced_rhs(dev(pb.f))
+    rhs_ref = ip.rhs(pb, st, d["r"], d["s"], cf)
+    assert rel(host(rhs), rhs_ref) < 1e-12
+    rtol, tol = (1e-12, 1e-9) if precision == "fp64" else (1e-10, 1e-7)
+    dz, info = G.ip_solve(rhs, rtol=rtol, maxit=500)
+    S = ip.assemble_S(pb, st, cf)
+    ref = solvers.direct_solve(S, rhs_ref)
+    assert info["relres"] <= rtol
+    assert rel(host(dz), ref) < tol
+    drho, dnl, dnu = (host(t) for t in G.ip_recover(dz))
+    rr, rl, ru = ip.recover(pb, st, cf, host(dz))
+    for a, b in ((drho, rr), (dnl, rl), (dnu, ru)):
+        assert rel(a, b) < 1e-12
+    if pb.m <= 128:       # the full Newton step of the unreduced system, dense
+        fu, fa, frho, fnl, fnu = ip.newton_full(pb, st, d["r"], d["s"])
+        assert rel(host(dz)[:pb.n], fu) < tol and abs(host(dz)[pb.n] - fa) < tol * max(1.0, abs(fa))
+        for a, b in ((drho, frho), (dnl, fnl), (dnu, fnu)):
+            assert rel(a, b) < tol
+
+
+# ------------------------------------------------------------------------------------------------
 # V-cycle: same hierarchy definition as the oracle (Galerkin, theta / lambda_max Jacobi, exact coarse)
 # ------------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("dims,bc,levels", [((8, 4, 4), "cantilever", 3), ((16, 8, 8), "bridge_corners", 3),
