@@ -472,6 +472,68 @@ def run_batch(args):
         print(json.dumps(out), flush=True)
 
 
+def run_ip(args):
+    """Interior-point Newton systems (Section 4.1) on the workload's grid: state set-up (coefficients, Galerkin
+    hierarchy of S_IP), right-hand side, MG-MINRES to the workload's tolerance and the recovery of the density and
+    multiplier increments, at a strictly feasible synthetic point (rho from the density recipe, nu_lo = nu_up = 1,
+    alpha = 1, r = s = 1e-2, u the equilibrium displacement). Device-resident inputs, L2 flushed between steps."""
+    import torch
+
+    import paper_1904_06556_gb300 as pkg
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synthetic.WORKLOADS[args.workload]
+
+    def t64(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+    rho = np.clip(synthetic.density_for(w), 2 * w.rho_lo, 0.99 * w.rho_up)
+    f = t64(synthetic.load_vector(w.nx, w.ny, w.nz, w.loads[0]))
+    with pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision="fp64") as G64:
+        G64.set_density(t64(rho))
+        u, _ = G64.minres_solve("K", f, rtol=w.rtol, maxit=2000, check=False)
+    G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=args.precision)
+    sd = dict(u=u, rho=t64(rho), nu_lo=t64(np.ones(w.m)), nu_up=t64(np.ones(w.m)), alpha=1.0, V=float(rho.sum()),
+              rho_lo=w.rho_lo, rho_up=w.rho_up, r=1e-2, s=1e-2)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    last = {}
+
+    def step():
+        G.ip_set_state(sd)
+        rhs = G.ip_reduced_rhs(f)
+        dz, info = G.ip_solve(rhs, rtol=w.rtol, maxit=1000)
+        G.ip_recover(dz)
+        last["info"] = info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    total_ms = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in ev)), dev)
+    out = {"metric": METRIC + " (interior-point Newton system)", "value": whole_job_rate(world, args.steps, total_ms),
+           "unit": "interior-point Newton systems/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+           "data": "synthetic (seeded; strictly feasible interior point on the workload's grid)",
+           "config": dict(workload_desc(w, args.precision),
+                          workload=f"{w.name}: {w.nx}x{w.ny}x{w.nz} Q1 hex {w.bc}, {args.precision}, one "
+                                   f"interior-point Newton system (set-up, rhs, MG-MINRES, recovery)"),
+           "solve": {"minres_iterations": last["info"]["iterations"], "true_relres": last["info"]["relres"],
+                     "outer": last["info"]["outer"]}}
+    G.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def run_pbm(args):
     """A complete PBM run (Algorithm 1, pbm_solve) from the paper's initial point on the workload's grid: the
     large full-PBM workload (256 x 128 x 128 cantilever, distributed end load, vf 0.15, 7 levels) or any other
@@ -706,6 +768,7 @@ def main():
     ap.add_argument("--workload", default="cant64",
                     choices=["cant64", "bridge128", "cant32", "cant16", "cant256", "batch48"])
     ap.add_argument("--pbm", action="store_true", help="time one complete PBM run (Algorithm 1) on the workload")
+    ap.add_argument("--ip", action="store_true", help="time interior-point Newton systems (Section 4.1)")
     ap.add_argument("--compare-fp64", action="store_true", help="with --pbm: also run the other precision")
     ap.add_argument("--fp32-plans", action="store_true",
                     help="time every tile plan of the FP32 fine operator on the workload's grid")
@@ -721,6 +784,8 @@ def main():
         run_batch(args)
     elif args.pbm:
         run_pbm(args)
+    elif args.ip:
+        run_ip(args)
     elif args.fp32_plans:
         run_plans(args)
     else:
