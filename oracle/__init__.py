@@ -14,6 +14,8 @@ Modules
              right-hand side (eq. system), the recovery of the nu-step (eq. deltanu), the duality gap (eq. gap),
              Newton (Algorithm 2) and the outer PBM loop (Algorithm 1).
   solvers  : preconditioned MINRES (Paige-Saunders), a Galerkin V-cycle on CSR (Section 5.1), direct solves.
+  doc      : the damped optimality-criteria method (Algorithm DOC): equilibrium solve and the bisection of the
+             volume multiplier.
   ip       : the primal-dual interior-point method's Newton system (Section 4.1): perturbed KKT residual, its
              Jacobian (eq. gradres), the reduced matrix (eq. S_IP), its right-hand side and the recovery of the
              density and multiplier increments (eqs. Delta_rho, Delta_onu, Delta_unu).
