@@ -270,6 +270,49 @@ int pbm_vcycle(pbm_grid* g, int op, const double* b_dev, double* x_dev, void* st
 int pbm_minres_solve(pbm_grid* g, int op, const double* b_dev, double* x_dev, double rtol, int maxit,
                      pbm_solve_info* info, void* stream);
 
+/* ---- damped optimality criteria (Section 4.2, Algorithm DOC) ---------------------------------
+ * One DOC iteration: the equilibrium displacement u of K(rho) u = f by MG-MINRES to the true
+ * relative residual eps_mr (the paper uses 1e-4), then the volume multiplier alpha by bisection on
+ * [0, 10^4]: each trial density is rho_i^+ = min(max(rho_i (u^T K_i u)^q / alpha, rho_lo), rho_up),
+ * the lower end moves up while sum(rho^+) > V and the upper end down otherwise, until
+ * (hi - lo)/(hi + lo) <= tau_alpha; rho^+ is the last trial's density. */
+typedef struct pbm_doc_params {
+    double V, rho_lo, rho_up;  /* volume bound and density bounds                                     */
+    double q;                  /* damping exponent (the paper: 1/2)                                  */
+    double eps_doc;            /* stop when ||rho^+ - rho||_inf <= eps_doc (pbm_doc_solve)            */
+    double tau_alpha;          /* bisection tolerance (<= 0: eps_doc / 10)                            */
+    double eps_mr;             /* MINRES tolerance of the equilibrium solves                          */
+    int maxit;                 /* MINRES iterations per solve                                         */
+    int max_iter;              /* DOC iterations (pbm_doc_solve)                                      */
+} pbm_doc_params;
+
+typedef struct pbm_doc_info {
+    int status;
+    int iterations;            /* DOC iterations done                                                 */
+    int minres;                /* MINRES iterations, summed                                           */
+    int trials;                /* bisection trials of the last iteration                              */
+    double alpha;              /* volume multiplier of the last trial                                 */
+    double change;             /* ||rho^+ - rho||_inf of the last iteration                           */
+    double compliance;         /* f^T u of the last equilibrium solve                                 */
+    double minres_relres;      /* true relative residual of the last solve                            */
+} pbm_doc_info;
+
+/* Defaults: q = 1/2, eps_doc = 1e-3, tau_alpha = eps_doc / 10, eps_mr = 1e-4, maxit = 500,
+ * max_iter = 1000; V, rho_lo, rho_up are the caller's. */
+int pbm_default_doc_params(pbm_doc_params* p);
+
+/* One DOC iteration from the densities rho_dev (m, FP64, in/out: rho^+ on return) and the
+ * displacement u_dev (n, in: initial guess of the solve, out: u of K(rho) u = f). f_dev: n load.
+ * Synchronises. Errors: PBM_EINVAL, PBM_ENOTCONV (solve or bisection), PBM_EBREAKDOWN. */
+int pbm_doc_step(pbm_grid* g, double* rho_dev, const double* f_dev, double* u_dev, const pbm_doc_params* p,
+                 pbm_doc_info* info, void* stream);
+
+/* Algorithm DOC: iterations of pbm_doc_step until ||rho^+ - rho||_inf <= eps_doc (rho_dev then holds
+ * the last density, whose change was below the tolerance) or max_iter. Errors: as pbm_doc_step, and
+ * PBM_ENOTCONV when max_iter is reached. */
+int pbm_doc_solve(pbm_grid* g, double* rho_dev, const double* f_dev, double* u_dev, const pbm_doc_params* p,
+                  pbm_doc_info* info, void* stream);
+
 /* ---- interior-point Newton system (Section 4.1) ----------------------------------------------
  * The primal-dual interior-point method's Newton step on the perturbed KKT system of eq. (1)
  * (barrier parameters r, s), reduced by two Schur complements to eq. (S_IP):

@@ -190,6 +190,39 @@ class Grid:
                                                 _ptr(y, f, n, "y"), C.byref(d) if dot else None, _stream()))
         return y, (d.value if dot else None)
 
+    # ---- damped optimality criteria (pbm_doc_*) ----
+    def _doc_params(self, V, rho_lo, rho_up, **kw):
+        p = _lib.DocParams()
+        self._check(self._L.pbm_default_doc_params(C.byref(p)))
+        p.V, p.rho_lo, p.rho_up = float(V), float(rho_lo), float(rho_up)
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown DOC parameter {k}")
+            setattr(p, k, v)
+        return p
+
+    def doc_step(self, rho: torch.Tensor, f: torch.Tensor, u: torch.Tensor, V: float, rho_lo: float, rho_up: float,
+                 **params) -> dict:
+        """One iteration of Algorithm DOC (pbm_doc_step): rho (m) and u (n) FP64 CUDA tensors, updated in place."""
+        p = self._doc_params(V, rho_lo, rho_up, **params)
+        inf = _lib.DocInfo()
+        self._check(self._L.pbm_doc_step(self._h, _ptr(rho, n=self.m, name="rho"), _ptr(f, n=self.n, name="f"),
+                                         _ptr(u, n=self.n, name="u"), C.byref(p), C.byref(inf), _stream()))
+        return {k: getattr(inf, k) for k, _ in _lib.DocInfo._fields_}
+
+    def doc_solve(self, rho: torch.Tensor, f: torch.Tensor, u: torch.Tensor, V: float, rho_lo: float, rho_up: float,
+                  check: bool = True, **params) -> dict:
+        """Algorithm DOC until ||rho+ - rho||_inf <= eps_doc (pbm_doc_solve); rho and u updated in place."""
+        p = self._doc_params(V, rho_lo, rho_up, **params)
+        inf = _lib.DocInfo()
+        rc = self._L.pbm_doc_solve(self._h, _ptr(rho, n=self.m, name="rho"), _ptr(f, n=self.n, name="f"),
+                                   _ptr(u, n=self.n, name="u"), C.byref(p), C.byref(inf), _stream())
+        if check:
+            self._check(rc)
+        out = {k: getattr(inf, k) for k, _ in _lib.DocInfo._fields_}
+        out["rc"] = rc
+        return out
+
     # ---- interior-point Newton system (pbm_ip_*) ----
     def ip_set_state(self, st: dict):
         """st: u (n), rho, nu_lo, nu_up (m) FP64 CUDA tensors; alpha, V, rho_lo, rho_up, r, s floats."""

@@ -53,6 +53,18 @@ class IPState(C.Structure):
                 ("r", C.c_double), ("s", C.c_double)]
 
 
+class DocParams(C.Structure):
+    _fields_ = [("V", C.c_double), ("rho_lo", C.c_double), ("rho_up", C.c_double), ("q", C.c_double),
+                ("eps_doc", C.c_double), ("tau_alpha", C.c_double), ("eps_mr", C.c_double), ("maxit", C.c_int),
+                ("max_iter", C.c_int)]
+
+
+class DocInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("minres", C.c_int), ("trials", C.c_int),
+                ("alpha", C.c_double), ("change", C.c_double), ("compliance", C.c_double),
+                ("minres_relres", C.c_double)]
+
+
 class ProfileStats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("total_ms", C.c_double), ("bytes", C.c_double), ("flops", C.c_double)]
 
@@ -108,6 +120,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pbm_get_diag": (i, [vp, i, vp, vp]),
         "pbm_fp32_plan_count": (i, []),
         "pbm_ip_set_state": (i, [vp, C.POINTER(IPState), vp]),
+        "pbm_default_doc_params": (i, [C.POINTER(DocParams)]),
+        "pbm_doc_step": (i, [vp, vp, vp, vp, C.POINTER(DocParams), C.POINTER(DocInfo), vp]),
+        "pbm_doc_solve": (i, [vp, vp, vp, vp, C.POINTER(DocParams), C.POINTER(DocInfo), vp]),
         "pbm_ip_apply_S": (i, [vp, vp, vp, vp]),
         "pbm_ip_reduced_rhs": (i, [vp, vp, vp, vp]),
         "pbm_ip_solve": (i, [vp, vp, vp, d, i, C.POINTER(SolveInfo), vp]),

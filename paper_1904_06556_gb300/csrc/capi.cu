@@ -30,6 +30,8 @@ void launch_scale(const double* a, double* b, double s, int64_t n, cudaStream_t 
 void launch_mult_update(pbm_grid* g, const double* c2, pbm_state* s, double beta, bool only_rho, cudaStream_t st);
 void launch_gap_sums(pbm_grid* g, const double* c2, const pbm_state* s, int slot, cudaStream_t st);
 void launch_ip_coeffs(pbm_grid* g, const pbm_ip_state* s, const double* c2, double* coef, cudaStream_t st);
+void launch_doc(pbm_grid* g, const double* e, double* rho_inout, double V, double rho_lo, double rho_up, double q,
+                double tau, double* w, cudaStream_t st);
 void launch_ip_recover(pbm_grid* g, const double* wdu, const double* da, const double* coef, double rho_lo,
                        double rho_up, double* drho, double* dnl, double* dnu, cudaStream_t st);
 
@@ -664,6 +666,114 @@ int pbm_set_state(pbm_grid* g, const pbm_state* s, void* stream) {
 // operator (border -1) built from w = rho and the weights d: the applies and the solve flip the
 // sign of the alpha entry around the PBM-form kernels.
 // ------------------------------------------------------------------------------------------------
+// ------------------------------------------------------------------------------------------------
+// damped optimality criteria (Algorithm DOC)
+// ------------------------------------------------------------------------------------------------
+int pbm_default_doc_params(pbm_doc_params* p) {
+    if (!p) return PBM_EINVAL;
+    std::memset(p, 0, sizeof(*p));
+    p->rho_up = 1.0;
+    p->q = 0.5;
+    p->eps_doc = 1e-3;
+    p->tau_alpha = 0.0;
+    p->eps_mr = 1e-4;
+    p->maxit = 500;
+    p->max_iter = 1000;
+    return PBM_OK;
+}
+
+static void doc_iteration(pbm_grid* g, double* rho_dev, const double* f_dev, double* u_dev, const pbm_doc_params* p,
+                          pbm_doc_info* info, cudaStream_t st) {
+    const int64_t m = g->L[0].g.m(), n = g->L[0].g.n();
+    // rho into the handle (checked), then the equilibrium solve on the K(rho) hierarchy
+    PBM_CUDA(cudaMemcpyAsync(g->rho, rho_dev, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+    launch_check_nonneg(g, g->rho, m, 13, st);
+    if (read_slot(g, 13, st) != 0.0) fail(PBM_ENONFINITE, "density has non-finite or negative entries");
+    g->rho_set = true;
+    setup_hierarchy(g, false, st);
+    pbm_solve_info inf{};
+    const int rc = solve(g, false, f_dev, u_dev, p->eps_mr, p->maxit, &inf, st);
+    info->minres += inf.iterations;
+    info->minres_relres = inf.relres;
+    if (rc != PBM_OK) fail(rc, rc == PBM_EBREAKDOWN ? "MINRES breakdown" : "equilibrium solve did not converge");
+    double* e = g->aux64 + 6 * m;
+    double* w = g->aux64 + 7 * m;
+    launch_elem_energy(g, u_dev, nullptr, e, st);
+    const double tau = p->tau_alpha > 0.0 ? p->tau_alpha : 0.1 * p->eps_doc;
+    launch_doc(g, e, rho_dev, p->V, p->rho_lo, p->rho_up, p->q, tau, w, st);
+    launch_dot(g, false, f_dev, u_dev, n, 14, st);
+    PBM_CUDA(cudaMemcpyAsync(&g->sc_host->red[12], &g->sc->red[12], sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
+    PBM_CUDA(cudaMemcpyAsync(&g->sc_host->ctl[0], &g->sc->ctl[0], sizeof(double) * 5, cudaMemcpyDeviceToHost, st));
+    PBM_CUDA(cudaStreamSynchronize(st));
+    info->change = g->sc_host->red[12];
+    info->compliance = g->sc_host->red[14];
+    info->alpha = g->sc_host->ctl[2];
+    info->trials = int(g->sc_host->ctl[3]);
+    info->iterations += 1;
+}
+
+static void check_doc(pbm_grid* g, const double* rho_dev, const double* f_dev, const double* u_dev,
+                      const pbm_doc_params* p) {
+    if (!g || !rho_dev || !f_dev || !u_dev || !p) fail(PBM_EINVAL, "null argument");
+    if (!(p->rho_up > p->rho_lo) || !(p->rho_lo >= 0.0)) fail(PBM_EINVAL, "need 0 <= rho_lo < rho_up");
+    if (!(p->q > 0.0) || !(p->eps_mr > 0.0) || p->maxit < 1) fail(PBM_EINVAL, "need q > 0, eps_mr > 0, maxit >= 1");
+    if (!(p->tau_alpha > 0.0) && !(p->eps_doc > 0.0)) fail(PBM_EINVAL, "need tau_alpha > 0 or eps_doc > 0");
+    if (!(p->V > 0.0)) fail(PBM_EINVAL, "need V > 0");
+}
+
+int pbm_doc_step(pbm_grid* g, double* rho_dev, const double* f_dev, double* u_dev, const pbm_doc_params* p,
+                 pbm_doc_info* info, void* stream) {
+    PBM_TRY
+    check_doc(g, rho_dev, f_dev, u_dev, p);
+    set_device(g);
+    pbm_doc_info inf{};
+    doc_iteration(g, rho_dev, f_dev, u_dev, p, &inf, S(stream));
+    if (info) *info = inf;
+    PBM_CATCH
+}
+
+int pbm_doc_solve(pbm_grid* g, double* rho_dev, const double* f_dev, double* u_dev, const pbm_doc_params* p,
+                  pbm_doc_info* info, void* stream) {
+    pbm_doc_info inf{};
+    int rc = PBM_OK;
+    try {
+        check_doc(g, rho_dev, f_dev, u_dev, p);
+        if (!(p->eps_doc > 0.0) || p->max_iter < 1) fail(PBM_EINVAL, "need eps_doc > 0 and max_iter >= 1");
+        set_device(g);
+        const cudaStream_t st = S(stream);
+        const int64_t m = g->L[0].g.m();
+        double* prev = (double*)dalloc(g, sizeof(double) * m);
+        try {
+            bool done = false;
+            while (!done && inf.iterations < p->max_iter) {
+                // keep rho: Algorithm DOC stops with the density whose update was below the tolerance
+                PBM_CUDA(cudaMemcpyAsync(prev, rho_dev, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+                doc_iteration(g, rho_dev, f_dev, u_dev, p, &inf, st);
+                if (inf.change <= p->eps_doc) {
+                    PBM_CUDA(cudaMemcpyAsync(rho_dev, prev, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+                    PBM_CUDA(cudaStreamSynchronize(st));
+                    done = true;
+                }
+            }
+            if (!done) fail(PBM_ENOTCONV, "DOC did not reach eps_doc in max_iter iterations");
+        } catch (...) {
+            cudaStreamSynchronize(st);
+            dfree(prev);
+            g->bytes -= int64_t(sizeof(double) * m);
+            throw;
+        }
+        dfree(prev);
+        g->bytes -= int64_t(sizeof(double) * m);
+    } catch (const Error& e) {
+        set_error(e.msg);
+        rc = e.code;
+    }
+    inf.status = rc;
+    if (info) *info = inf;
+    if (rc == PBM_OK) set_error("");
+    return rc;
+}
+
 static double* ip_work(pbm_grid* g) {
     if (!g->ip_work) g->ip_work = (double*)dalloc(g, sizeof(double) * 2 * size_t(g->L[0].g.n() + 1));
     return g->ip_work;

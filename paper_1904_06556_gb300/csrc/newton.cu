@@ -346,3 +346,123 @@ void launch_ip_recover(pbm_grid* g, const double* wdu, const double* da, const d
 }
 
 }  // namespace pbm
+
+// ------------------------------------------------------------------------------------------------
+// Damped optimality-criteria step (Algorithm DOC, Section 4.2): with e_i = u^T K_i u the trial density
+// of a volume multiplier alpha is rho_i^+ = min(max(w_i / alpha, rho_lo), rho_up), w_i = rho_i e_i^q.
+// The bisection state lives on the device (ctl[0] lo, ctl[1] hi, ctl[2] alpha of the last trial,
+// ctl[3] trials, ctl[4] done), so the trials run as consecutive launches without host round trips.
+// ------------------------------------------------------------------------------------------------
+namespace pbm {
+
+__global__ void k_doc_weights(int64_t m, const double* __restrict__ rho, const double* __restrict__ e, double q,
+                              double* __restrict__ w, double* ctl, double alpha_hi) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m; i += int64_t(gridDim.x) * blockDim.x)
+        w[i] = rho[i] * pow(e[i], q);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl[0] = 0.0;
+        ctl[1] = alpha_hi;
+        ctl[2] = 0.0;
+        ctl[3] = 0.0;
+        ctl[4] = 0.0;
+    }
+}
+
+// one trial: if the interval is still wide, alpha = its midpoint, the sum of the trial densities, and the last
+// CTA moves one end of the interval (every CTA reads the interval before any CTA can reach the update)
+__global__ void k_doc_trial(int64_t m, const double* __restrict__ w, double V, double rho_lo, double rho_up,
+                            double tau, double* ctl, double* partials, unsigned* counter) {
+    __shared__ double sh[NB / 32];
+    __shared__ bool last;
+    const double lo = ctl[0], hi = ctl[1];
+    if (ctl[4] != 0.0) return;
+    if ((hi - lo) / (hi + lo) <= tau) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl[4] = 1.0;
+        return;
+    }
+    const double alpha = 0.5 * (hi + lo);
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m; i += int64_t(gridDim.x) * blockDim.x)
+        s += fmin(fmax(w[i] / alpha, rho_lo), rho_up);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int k = 0; k < NB / 32; ++k) b += sh[k];
+        partials[blockIdx.x] = b;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double tot = 0.0;
+    for (unsigned k = 0; k < gridDim.x; ++k) tot += ((volatile double*)partials)[k];
+    ctl[2] = alpha;
+    ctl[3] += 1.0;
+    if (tot > V) ctl[0] = alpha;
+    else ctl[1] = alpha;
+    *counter = 0u;
+}
+
+// rho^+ from the last trial's alpha (rho unchanged if no trial ran); out[0] = ||rho^+ - rho||_inf
+__global__ void k_doc_update(int64_t m, const double* __restrict__ w, const double* ctl, double rho_lo,
+                             double rho_up, const double* __restrict__ rho, double* __restrict__ rho_new,
+                             double* partials, unsigned* counter, double* out) {
+    __shared__ double sh[NB / 32];
+    __shared__ bool last;
+    const bool none = ctl[3] == 0.0;
+    const double alpha = ctl[2];
+    double mx = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m; i += int64_t(gridDim.x) * blockDim.x) {
+        const double r = none ? rho[i] : fmin(fmax(w[i] / alpha, rho_lo), rho_up);
+        mx = fmax(mx, fabs(r - rho[i]));
+        rho_new[i] = r;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int k = 0; k < NB / 32; ++k) b = fmax(b, sh[k]);
+        partials[blockIdx.x] = b;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double tot = 0.0;
+    for (unsigned k = 0; k < gridDim.x; ++k) tot = fmax(tot, ((volatile double*)partials)[k]);
+    *out = tot;
+    *counter = 0u;
+}
+
+void launch_doc(pbm_grid* g, const double* e, double* rho_inout, double V, double rho_lo, double rho_up, double q,
+                double tau, double* w, cudaStream_t st) {
+    const int64_t m = g->L[0].g.m();
+    double* ctl = &g->sc->ctl[0];   // reused: the MINRES loop is not running
+    k_doc_weights<<<NG, NB, 0, st>>>(m, g->rho, e, q, w, ctl, 1e4);
+    PBM_LAUNCH("doc weights");
+    // trials in batches; the host looks at the done flag after each batch
+    for (int batch = 0; batch < 8; ++batch) {
+        for (int t = 0; t < 16; ++t) {
+            k_doc_trial<<<NG, NB, 0, st>>>(m, w, V, rho_lo, rho_up, tau, ctl, g->partials, &g->sc->counter[3]);
+            PBM_LAUNCH("doc trial");
+        }
+        PBM_CUDA(cudaMemcpyAsync(&g->sc_host->ctl[0], ctl, sizeof(double) * 5, cudaMemcpyDeviceToHost, st));
+        PBM_CUDA(cudaStreamSynchronize(st));
+        if (g->sc_host->ctl[4] != 0.0) break;
+    }
+    if (g->sc_host->ctl[4] == 0.0) fail(PBM_ENOTCONV, "DOC bisection did not close its interval in 128 trials");
+    k_doc_update<<<NG, NB, 0, st>>>(m, w, ctl, rho_lo, rho_up, g->rho, rho_inout, g->partials, &g->sc->counter[3],
+                                    &g->sc->red[12]);
+    PBM_LAUNCH("doc update");
+}
+
+}  // namespace pbm

@@ -273,6 +273,48 @@ def test_apply_S_rhs_and_compliance(pkg, dims, bc, seed, us):
 
 
 # ------------------------------------------------------------------------------------------------
+# damped optimality criteria (Algorithm DOC)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dims,bc,levels", [((8, 4, 4), "cantilever", 2), ((16, 8, 8), "bridge_corners", 3)])
+def test_doc_step_matches_oracle(pkg, dims, bc, levels):
+    from oracle import doc
+    import scipy.sparse.linalg as sla
+    g = fem.Grid(*dims, bc)
+    f = synthetic.load_vector(*dims, "end_edge" if bc == "cantilever" else "top_traction")
+    rho = synthetic.density_uniform_rescaled(g.m, 0.3, 5)
+    V = 0.3 * g.m
+    pb = pbm.Problem(g, f, V, 1e-3, 1.0)
+    u_ref = sla.spsolve(fem.assemble_K(g, rho, pb.Ke).tocsc(), pb.f)
+    rho_ref, alpha_ref, trials_ref = doc.density_update(rho, doc.energies(pb, u_ref), V, 1e-3, 1.0, 0.5, 1e-5)
+    G = pkg.Grid(*dims, levels, bc)
+    r, u = dev(rho), torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    info = G.doc_step(r, dev(pb.f), u, V, 1e-3, 1.0, tau_alpha=1e-5, eps_mr=1e-12, maxit=400)
+    assert rel(host(u), u_ref) < 1e-9
+    assert info["trials"] == trials_ref
+    assert abs(info["alpha"] - alpha_ref) <= 1e-9 * alpha_ref
+    assert rel(host(r), rho_ref) < 1e-9
+    assert abs(info["change"] - np.abs(rho_ref - rho).max()) <= 1e-9
+    assert abs(info["compliance"] - pb.f @ u_ref) <= 1e-9 * abs(pb.f @ u_ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_doc_solve_matches_oracle(pkg, precision):
+    from oracle import doc
+    nx, ny, nz = 8, 4, 4
+    g = fem.Grid(nx, ny, nz, "cantilever")
+    f = synthetic.load_vector(nx, ny, nz, "end_edge")
+    V = 0.3 * g.m
+    pb = pbm.Problem(g, f, V, 1e-3, 1.0)
+    ref = doc.doc(pb, np.full(g.m, V / g.m), q=0.5, eps_doc=1e-3)
+    assert ref.converged
+    G = pkg.Grid(nx, ny, nz, 2, "cantilever", precision=precision)
+    r, u = dev(np.full(g.m, V / g.m)), torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    info = G.doc_solve(r, dev(pb.f), u, V, 1e-3, 1.0, eps_doc=1e-3, eps_mr=1e-10)
+    assert info["rc"] == 0 and info["iterations"] == ref.iterations
+    assert np.abs(host(r) - ref.rho).max() < 1e-6
+
+
+# ------------------------------------------------------------------------------------------------
 # interior-point Newton system (Section 4.1)
 # ------------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("dims,bc,levels,precision", [((8, 4, 4), "cantilever", 2, "fp64"),
