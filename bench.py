@@ -534,6 +534,47 @@ def run_ip(args):
         print(json.dumps(out), flush=True)
 
 
+def run_doc(args):
+    """A complete run of Algorithm DOC (pbm_doc_solve) from the uniform density V/m with the paper's settings
+    (q = 1/2, eps_DOC = 1e-3, tau_alpha = eps_DOC / 10, MINRES to 1e-4): total time, DOC and MINRES iterations and
+    the final compliance; with --compare-fp64 the other precision too."""
+    import torch
+
+    import paper_1904_06556_gb300 as pkg
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synthetic.WORKLOADS[args.workload]
+    f = torch.as_tensor(synthetic.load_vector(w.nx, w.ny, w.nz, w.loads[0]), dtype=torch.float64, device=dev)
+
+    def one_run(precision):
+        with pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=precision) as G:
+            rho = torch.full((w.m,), w.V / w.m, dtype=torch.float64, device=dev)
+            u = torch.zeros(w.n, dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = G.doc_solve(rho, f, u, w.V, w.rho_lo, w.rho_up, check=False, eps_doc=1e-3, eps_mr=1e-4)
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0, info
+
+    secs, info = one_run(args.precision)
+    out = {"metric": METRIC + " (complete DOC run)", "value": secs, "unit": "s per DOC run", "n_gpus": world,
+           "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+           "data": "synthetic (seeded; the paper's cantilever example, Section 6)",
+           "config": dict(workload_desc(w, args.precision),
+                          workload=f"{w.name}: {w.nx}x{w.ny}x{w.nz} Q1 hex {w.bc}, {args.precision}, complete DOC "
+                                   f"run (q 1/2, eps_DOC 1e-3, MINRES 1e-4)"),
+           "doc": info}
+    if args.compare_fp64:
+        s2, i2 = one_run("fp64" if args.precision == "mixed" else "mixed")
+        out["other_precision"] = {"seconds": s2, "iterations": i2["iterations"], "minres": i2["minres"],
+                                  "compliance": i2["compliance"]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def run_pbm(args):
     """A complete PBM run (Algorithm 1, pbm_solve) from the paper's initial point on the workload's grid: the
     large full-PBM workload (256 x 128 x 128 cantilever, distributed end load, vf 0.15, 7 levels) or any other
@@ -769,6 +810,7 @@ def main():
                     choices=["cant64", "bridge128", "cant32", "cant16", "cant256", "batch48"])
     ap.add_argument("--pbm", action="store_true", help="time one complete PBM run (Algorithm 1) on the workload")
     ap.add_argument("--ip", action="store_true", help="time interior-point Newton systems (Section 4.1)")
+    ap.add_argument("--doc", action="store_true", help="time one complete run of Algorithm DOC")
     ap.add_argument("--compare-fp64", action="store_true", help="with --pbm: also run the other precision")
     ap.add_argument("--fp32-plans", action="store_true",
                     help="time every tile plan of the FP32 fine operator on the workload's grid")
@@ -786,6 +828,8 @@ def main():
         run_pbm(args)
     elif args.ip:
         run_ip(args)
+    elif args.doc:
+        run_doc(args)
     elif args.fp32_plans:
         run_plans(args)
     else:
