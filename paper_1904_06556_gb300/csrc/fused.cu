@@ -26,6 +26,50 @@ namespace pbm {
 
 constexpr int FSLOT = 4;   // staging slots per thread: 3 (TX + 2)(TY + 2) <= FSLOT * NT
 
+// The element arithmetic keeps displacement components x and y of a coefficient as one float2 and
+// runs it with the paired FP32 instructions (one instruction for two operations), component z alone.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Khat of pbm_internal.h with the diagonal of components x, y as pairs
+struct KeHat2 {
+    float2 dg01[8];
+    float dg2[8];
+    float lam4[2];
+    float mu4[2];
+};
+
+// Y = Khat X on (x, y) pairs and z: the diagonal in pairs, the couplings per component
+__device__ __forceinline__ void khat_apply2(const KeHat2& K, const float2 (&X01)[8], const float (&X2)[8],
+                                            float2 (&Y01)[8], float (&Y2)[8]) {
+    auto get = [&](int d, int i) -> float { return d == 0 ? X01[i].x : (d == 1 ? X01[i].y : X2[i]); };
+#pragma unroll
+    for (int q = 1; q < 8; ++q) {
+        Y01[q] = mul2(K.dg01[q], X01[q]);
+        Y2[q] = K.dg2[q] * X2[q];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float acc = c == 0 ? Y01[q].x : (c == 1 ? Y01[q].y : Y2[q]);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (d == c) continue;
+                const int r = 3 - c - d;
+                const int br = (q >> r) & 1;
+                const int qc = (q >> c) & 1, qd = (q >> d) & 1;
+                if (qc == 1 && qd == 0) acc = fmaf(K.lam4[br], get(d, (q & ~(1 << c)) | (1 << d)), acc);
+                if (qd == 1 && qc == 0) acc = fmaf(K.mu4[br], get(d, (q & ~(1 << d)) | (1 << c)), acc);
+            }
+            if (c == 0) Y01[q].x = acc;
+            else if (c == 1) Y01[q].y = acc;
+            else Y2[q] = acc;
+        }
+    }
+    Y01[0] = make_float2(0.0f, 0.0f);
+    Y2[0] = 0.0f;
+}
+
 struct FusedArgs {
     int nx, ny, nz, support;
     int TX, TY, DZ, gx, gy;
@@ -39,32 +83,36 @@ struct FusedArgs {
     const float* idiag;
     const double* omega;
     int mode, with_alpha, dot_slot;
-    KeHatT<float> K;
+    KeHat2 K;
     double* partials;     // 2 * gridDim.x
     DevScalars* sc;
     unsigned int* counter;   // last-CTA counter
 };
 
-// transformed xy quad of the element column at staged coordinates (lx, ly) of a staged plane
-// (nodes as float4, supported nodes already zero)
-__device__ __forceinline__ void fused_quad(const float4* __restrict__ s, int NW, int lx, int ly, float (&Q)[3][4]) {
-    float v[3][4];
+// transformed xy quad of the element column at staged coordinates (lx, ly) of a staged plane (nodes
+// as float4, supported nodes already zero), components (x, y) paired
+__device__ __forceinline__ void fused_quad2(const float4* __restrict__ s, int NW, int lx, int ly, float2 (&Q01)[4],
+                                            float (&Q2)[4]) {
+    float2 v01[4];
+    float v2[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const float4 p = s[(ly + (a >> 1)) * NW + lx + (a & 1)];
-        v[0][a] = p.x;
-        v[1][a] = p.y;
-        v[2][a] = p.z;
+        v01[a] = make_float2(p.x, p.y);
+        v2[a] = p.z;
     }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float s0 = v[c][0] + v[c][1], d0 = v[c][1] - v[c][0];
-        const float s1 = v[c][2] + v[c][3], d1 = v[c][3] - v[c][2];
-        Q[c][0] = s0 + s1;
-        Q[c][1] = d0 + d1;
-        Q[c][2] = s1 - s0;
-        Q[c][3] = d1 - d0;
-    }
+    const float2 s0 = add2(v01[0], v01[1]), d0 = sub2(v01[1], v01[0]);
+    const float2 s1 = add2(v01[2], v01[3]), d1 = sub2(v01[3], v01[2]);
+    Q01[0] = add2(s0, s1);
+    Q01[1] = add2(d0, d1);
+    Q01[2] = sub2(s1, s0);
+    Q01[3] = sub2(d1, d0);
+    const float t0 = v2[0] + v2[1], e0 = v2[1] - v2[0];
+    const float t1 = v2[2] + v2[3], e1 = v2[3] - v2[2];
+    Q2[0] = t0 + t1;
+    Q2[1] = e0 + e1;
+    Q2[2] = t1 - t0;
+    Q2[3] = e1 - e0;
 }
 
 template <int NT>
@@ -178,7 +226,10 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
     float pdT = 0.0f, paT = 0.0f;
 
     const int kstart = max(kz0 - 1, 0);
-    float Qlo[3][4], Ulo[3][4], carry[3][4];
+    // per element column: xy-transformed quads of the plane below (x, and u for S) and the top face of the
+    // previous layer, components (x, y) paired and z alone
+    float2 Qlo01[4], Ulo01[4], carry01[4];
+    float Qlo2[4], Ulo2[4], carry2[4];
     // element weights of the current layer, loaded one layer ahead
     const int64_t elayer = int64_t(nx) * ny;
     const float* wp = P.w + (ex + int64_t(nx) * (ey + int64_t(ny) * kstart));
@@ -196,13 +247,14 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
     if (kstart + 1 <= nz) fetch(kstart + 1);
     __syncthreads();
     if (ecol) {
-        fused_quad(sx[cur], NW, lx, ly, Qlo);
-        if (S) fused_quad(su[S ? cur : 0], NW, lx, ly, Ulo);
+        fused_quad2(sx[cur], NW, lx, ly, Qlo01, Qlo2);
+        if (S) fused_quad2(su[S ? cur : 0], NW, lx, ly, Ulo01, Ulo2);
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) carry[c][q] = 0.0f;
+    for (int q = 0; q < 4; ++q) {
+        carry01[q] = make_float2(0.0f, 0.0f);
+        carry2[q] = 0.0f;
+    }
 
     for (int k = kstart; k < kz1; ++k) {
         const bool layer = k < nz;
@@ -226,96 +278,106 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
             if (ofixed) xo4 = make_float4(__ldg(P.x + d0), __ldg(P.x + d0 + 1), __ldg(P.x + d0 + 2), 0.0f);
             else xo4 = sx[cur][ooff];
         }
-        float Bq[3][4];
+        float2 Bq01[4];
+        float Bq2[4];
         if (ecol && layer) {
-            float Qhi[3][4];
-            fused_quad(sx[nxt], NW, lx, ly, Qhi);
-            float X[3][8], Y[3][8];
+            float2 Qhi01[4];
+            float Qhi2[4];
+            fused_quad2(sx[nxt], NW, lx, ly, Qhi01, Qhi2);
+            float2 X01[8], Y01[8];
+            float X2[8], Y2[8];
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
+            for (int q = 0; q < 4; ++q) {
+                X01[q] = add2(Qlo01[q], Qhi01[q]);
+                X01[q + 4] = sub2(Qhi01[q], Qlo01[q]);
+                X2[q] = Qlo2[q] + Qhi2[q];
+                X2[q + 4] = Qhi2[q] - Qlo2[q];
+                Qlo01[q] = Qhi01[q];
+                Qlo2[q] = Qhi2[q];
+            }
+            if (S) {
+                float2 Uhi01[4], U01[8], W01[8];
+                float Uhi2[4], U2[8], W2[8];
+                fused_quad2(su[S ? nxt : 0], NW, lx, ly, Uhi01, Uhi2);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    X[c][q] = Qlo[c][q] + Qhi[c][q];
-                    X[c][q + 4] = Qhi[c][q] - Qlo[c][q];
-                    Qlo[c][q] = Qhi[c][q];
+                    U01[q] = add2(Ulo01[q], Uhi01[q]);
+                    U01[q + 4] = sub2(Uhi01[q], Ulo01[q]);
+                    U2[q] = Ulo2[q] + Uhi2[q];
+                    U2[q + 4] = Uhi2[q] - Ulo2[q];
+                    Ulo01[q] = Uhi01[q];
+                    Ulo2[q] = Uhi2[q];
                 }
-            if (S) {
-                float Uhi[3][4], U[3][8], Wt[3][8];
-                fused_quad(su[S ? nxt : 0], NW, lx, ly, Uhi);
+                khat_apply2(P.K, U01, U2, W01, W2);
+                float2 dot01 = make_float2(0.0f, 0.0f);
+                float dot2 = 0.0f;
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        U[c][q] = Ulo[c][q] + Uhi[c][q];
-                        U[c][q + 4] = Uhi[c][q] - Ulo[c][q];
-                        Ulo[c][q] = Uhi[c][q];
-                    }
-                khat_apply(P.K, U, Wt);
-                float dot = 0.0f;
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-#pragma unroll
-                    for (int q = 1; q < 8; ++q) dot += Wt[c][q] * X[c][q];
-                const float te = de * (dot - xa);
+                for (int q = 1; q < 8; ++q) {
+                    dot01 = fma2(W01[q], X01[q], dot01);
+                    dot2 = fmaf(W2[q], X2[q], dot2);
+                }
+                const float te = de * ((dot01.x + dot01.y + dot2) - xa);
                 if (designated && k + 1 >= kz0 && k + 1 < kz1) paT -= te;   // counted where its top plane is owned
-                khat_apply(P.K, X, Y);
+                khat_apply2(P.K, X01, X2, Y01, Y2);
+                const float2 we2 = make_float2(we, we), te2 = make_float2(te, te);
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-#pragma unroll
-                    for (int q = 1; q < 8; ++q) Y[c][q] = we * Y[c][q] + te * Wt[c][q];
+                for (int q = 1; q < 8; ++q) {
+                    Y01[q] = fma2(te2, W01[q], mul2(we2, Y01[q]));
+                    Y2[q] = fmaf(te, W2[q], we * Y2[q]);
+                }
             } else {
-                khat_apply(P.K, X, Y);
+                khat_apply2(P.K, X01, X2, Y01, Y2);
+                const float2 we2 = make_float2(we, we);
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-#pragma unroll
-                    for (int q = 1; q < 8; ++q) Y[c][q] *= we;
+                for (int q = 1; q < 8; ++q) {
+                    Y01[q] = mul2(we2, Y01[q]);
+                    Y2[q] *= we;
+                }
             }
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    Bq[c][q] = carry[c][q] + (Y[c][q] - Y[c][q + 4]);
-                    carry[c][q] = Y[c][q] + Y[c][q + 4];
-                }
+            for (int q = 0; q < 4; ++q) {
+                Bq01[q] = add2(carry01[q], sub2(Y01[q], Y01[q + 4]));
+                carry01[q] = add2(Y01[q], Y01[q + 4]);
+                Bq2[q] = carry2[q] + (Y2[q] - Y2[q + 4]);
+                carry2[q] = Y2[q] + Y2[q + 4];
+            }
         } else {
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    Bq[c][q] = carry[c][q];
-                    carry[c][q] = 0.0f;
-                }
+            for (int q = 0; q < 4; ++q) {
+                Bq01[q] = carry01[q];
+                Bq2[q] = carry2[q];
+                carry01[q] = make_float2(0.0f, 0.0f);
+                carry2[q] = 0.0f;
+            }
         }
         cur = nxt;
         if (k < kz0) continue;  // the layer below the chunk: only its top face is kept
         // inverse xy transform: the element column's values at its 4 corners of plane k
         if (t < EC) {
-            float o[4][3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float a0 = Bq[c][0] - Bq[c][1], a1 = Bq[c][0] + Bq[c][1];
-                const float a2 = Bq[c][2] - Bq[c][3], a3 = Bq[c][2] + Bq[c][3];
-                o[0][c] = a0 - a2;
-                o[1][c] = a1 - a3;
-                o[2][c] = a0 + a2;
-                o[3][c] = a1 + a3;
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a) sq[a][t] = make_float4(o[a][0], o[a][1], o[a][2], 0.0f);
+            const float2 a0 = sub2(Bq01[0], Bq01[1]), a1 = add2(Bq01[0], Bq01[1]);
+            const float2 a2 = sub2(Bq01[2], Bq01[3]), a3 = add2(Bq01[2], Bq01[3]);
+            const float b0 = Bq2[0] - Bq2[1], b1 = Bq2[0] + Bq2[1];
+            const float b2 = Bq2[2] - Bq2[3], b3 = Bq2[2] + Bq2[3];
+            const float2 o0 = sub2(a0, a2), o1 = sub2(a1, a3), o2 = add2(a0, a2), o3 = add2(a1, a3);
+            sq[0][t] = make_float4(o0.x, o0.y, b0 - b2, 0.0f);
+            sq[1][t] = make_float4(o1.x, o1.y, b1 - b3, 0.0f);
+            sq[2][t] = make_float4(o2.x, o2.y, b0 + b2, 0.0f);
+            sq[3][t] = make_float4(o3.x, o3.y, b1 + b3, 0.0f);
         }
         __syncthreads();  // (b) corner values of plane k complete
         if (owner) {
-            float s[3] = {0.0f, 0.0f, 0.0f};
+            float2 s01 = make_float2(0.0f, 0.0f);
+            float s2 = 0.0f;
 #pragma unroll
             for (int dj = 1; dj >= 0; --dj)
 #pragma unroll
                 for (int di = 1; di >= 0; --di) {
                     // element column (ox + 1 - di, oy + 1 - dj); the node is its corner (di, dj)
                     const float4 v = sq[di + 2 * dj][(oy + 1 - dj) * EX + (ox + 1 - di)];
-                    s[0] += v.x;
-                    s[1] += v.y;
-                    s[2] += v.z;
+                    s01 = add2(s01, make_float2(v.x, v.y));
+                    s2 += v.z;
                 }
+            float s[3] = {s01.x, s01.y, s2};
             const float xo[3] = {xo4.x, xo4.y, xo4.z};
             if (ofixed) {
                 s[0] = xo[0];
@@ -747,8 +809,10 @@ void fused_fine_f32(const FusedPlan& p, const RedSet& r, const Geom& G, const Ke
     P.mode = a.mode;
     P.with_alpha = (s && a.with_alpha) ? 1 : 0;
     P.dot_slot = a.dot_slot;
-    for (int c = 0; c < 3; ++c)
-        for (int q = 0; q < 8; ++q) P.K.dg[c][q] = float(kh.dg[c][q]);
+    for (int q = 0; q < 8; ++q) {
+        P.K.dg01[q] = make_float2(float(kh.dg[0][q]), float(kh.dg[1][q]));
+        P.K.dg2[q] = float(kh.dg[2][q]);
+    }
     for (int b = 0; b < 2; ++b) {
         P.K.lam4[b] = float(kh.lam4[b]);
         P.K.mu4[b] = float(kh.mu4[b]);
