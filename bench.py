@@ -52,8 +52,8 @@ METRIC = "reduced-Newton MG-MINRES solve time & K(ρ)u GB/s; FP32-mixed vs FP64"
 UNIT = "reduced-Newton solves/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 PROFILE_DIR = os.path.join(ROOT, "profiles")
-# sources of the fine-level S kernels whose ncu traffic a committed profile may quote, per precision
-KERNEL_SOURCES = {p: [os.path.join(ROOT, "paper_1904_06556_gb300", "csrc", f) for f in (src, "pbm_internal.h")]
+# source of the fine-level S kernel whose ncu traffic a committed profile may quote, per precision
+KERNEL_SOURCES = {p: [os.path.join(ROOT, "paper_1904_06556_gb300", "csrc", src)]
                   for p, src in (("fp64", "colpass.cu"), ("mixed", "fused.cu"))}
 # FP64 issue rate of GB300 derived from the nominal 1.25 TFLOP/s (FMA = 2 flops), 152 SMs, 2070 MHz:
 # 1.25e12 / (2 * 152 * 2.07e9) = 2 FP64 instructions per clock per SM, i.e. 629 G FP64 operations/s.
