@@ -190,6 +190,7 @@ __device__ __forceinline__ void cols_fine_body(const ColArgs<T>& P, unsigned blk
 
 template <class T, int MODE>
 __global__ void __launch_bounds__(CB) k_cols_fine(ColArgs<T> P) {
+    pdl_wait();
     cols_fine_body<T, MODE>(P, blockIdx.x);
 }
 
@@ -261,6 +262,7 @@ __device__ __forceinline__ void cols_coarse_body(const ColArgs<T>& P, unsigned b
 
 template <class T>
 __global__ void __launch_bounds__(CB) k_cols_coarse(ColArgs<T> P) {
+    pdl_wait();
     cols_coarse_body<T>(P, blockIdx.x);
 }
 
@@ -398,6 +400,7 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
 
 template <class T>
 __global__ void __launch_bounds__(NB2) k_nodes(NodeArgs<T> P) {
+    pdl_wait();
     nodes_body<T>(P, blockIdx.x, gridDim.x);
 }
 
@@ -461,7 +464,7 @@ static void node_pass(const ColEnv& env, const Geom& G, const ApplyArgs& a, int 
                       const double* s_alpha, const double* apart, int napart, int64_t off, cudaStream_t st) {
     int blocks = 0;
     NodeArgs<T> N = make_node_args<T>(env, G, a, L, bord, s_alpha, apart, napart, off, &blocks);
-    k_nodes<T><<<blocks, NB2, 0, st>>>(N);
+    launch_pdl(k_nodes<T>, dim3(blocks), dim3(NB2), 0, st, N);
     PBM_LAUNCH("node pass");
 }
 
@@ -531,9 +534,9 @@ void cols_fine_env(const ColEnv& env, const Geom& G, const KeHat& kh, const T* w
     int blocks = 0;
     const ColArgs<T> P = make_fine_args<T>(env, G, kh, w, d, what, u, a.x, &blocks);
     const bool s = d != nullptr;
-    if (s && what) k_cols_fine<T, 1><<<blocks, CB, 0, st>>>(P);
-    else if (s) k_cols_fine<T, 2><<<blocks, CB, 0, st>>>(P);
-    else k_cols_fine<T, 0><<<blocks, CB, 0, st>>>(P);
+    if (s && what) launch_pdl(k_cols_fine<T, 1>, dim3(blocks), dim3(CB), 0, st, P);
+    else if (s) launch_pdl(k_cols_fine<T, 2>, dim3(blocks), dim3(CB), 0, st, P);
+    else launch_pdl(k_cols_fine<T, 0>, dim3(blocks), dim3(CB), 0, st, P);
     PBM_LAUNCH("fine column pass");
     node_pass<T>(env, G, a, P.L, (const T*)nullptr, nullptr, s ? env.partials : nullptr, s ? blocks : 0,
                  s ? blocks : 0, st);
@@ -753,7 +756,7 @@ void cols_coarse(pbm_grid* g, int k, const T* A, const T* bord, const ApplyArgs&
     }
     int blocks = 0;
     const ColArgs<T> P = make_coarse_args<T>(env, G, A, a.x, &blocks);
-    k_cols_coarse<T><<<blocks, CB, 0, st>>>(P);
+    launch_pdl(k_cols_coarse<T>, dim3(blocks), dim3(CB), 0, st, P);
     PBM_LAUNCH("coarse column pass");
     node_pass<T>(env, G, a, 1, bord, &g->sc->salpha, nullptr, 0, 0, st);
 }

@@ -140,6 +140,7 @@ __device__ __forceinline__ int fixed_bits(int support, int nx, int ny, int nz, i
 // node columns (compile-time, so that every shared-memory offset is a constant).
 template <int MODE, int NT, int MINB, int TX, int TY>
 __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
+    pdl_wait();
     constexpr bool S = MODE == 2;
     constexpr int EX = TX + 1, EY = TY + 1;
     constexpr int NW = TX + 2;             // staged nodes per row
@@ -495,6 +496,7 @@ __device__ __forceinline__ void coarse_rows6(const float* __restrict__ Ae, int64
 
 template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
+    pdl_wait();
     extern __shared__ float4 fused_smem4[];
     __shared__ double sred[NT / 32];
     __shared__ bool s_last;
@@ -772,7 +774,7 @@ template <int MODE>
 static void fused_launch(const FusedPlan& p, int blocks, const FusedArgs& P, cudaStream_t st) {
     switch (p.var) {
 #define PBM_PLAN_CASE(i, nt, minb, tx, ty) \
-    case i: k_fused_f32<MODE, nt, minb, tx, ty><<<blocks, nt, 0, st>>>(P); break;
+    case i: launch_pdl(k_fused_f32<MODE, nt, minb, tx, ty>, dim3(blocks), dim3(nt), 0, st, P); break;
         PBM_FUSED_PLANS(PBM_PLAN_CASE)
 #undef PBM_PLAN_CASE
         default: fail(PBM_EINVAL, "fused operator: unknown plan");
@@ -894,11 +896,11 @@ void fused_coarse_f32(const FusedPlan& p, const RedSet& r, const Geom& G, const 
     const size_t smem = sizeof(float4) * (size_t(2 * (p.TX + 2) * (p.TY + 2)) + size_t(4 * (p.TX + 1) * (p.TY + 1)));
     switch (p.var) {
         case 0:
-        case 1: k_fused_coarse_f32<256, 2><<<blocks, 256, smem, st>>>(P); break;
+        case 1: launch_pdl(k_fused_coarse_f32<256, 2>, dim3(blocks), dim3(256), smem, st, P); break;
         case 2:
-        case 3: k_fused_coarse_f32<128, 4><<<blocks, 128, smem, st>>>(P); break;
-        case 4: k_fused_coarse_f32<256, 1><<<blocks, 256, smem, st>>>(P); break;
-        default: k_fused_coarse_f32<128, 2><<<blocks, 128, smem, st>>>(P); break;
+        case 3: launch_pdl(k_fused_coarse_f32<128, 4>, dim3(blocks), dim3(128), smem, st, P); break;
+        case 4: launch_pdl(k_fused_coarse_f32<256, 1>, dim3(blocks), dim3(256), smem, st, P); break;
+        default: launch_pdl(k_fused_coarse_f32<128, 2>, dim3(blocks), dim3(128), smem, st, P); break;
     }
     PBM_LAUNCH("fused FP32 coarse operator");
 }

@@ -54,15 +54,16 @@ __device__ bool finish_sum(double part, double* partials, unsigned* counter, dou
 // ------------------------------------------------------------------------------------------------
 template <class S, class D>
 __global__ void k_cast(const S* __restrict__ a, D* __restrict__ b, int64_t n) {
+    pdl_wait();
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
         b[i] = D(a[i]);
 }
 
 void launch_cast(const void* src, bool src32, void* dst, bool dst32, int64_t n, cudaStream_t st) {
-    if (src32 && !dst32) k_cast<float, double><<<VG, VB, 0, st>>>((const float*)src, (double*)dst, n);
-    else if (!src32 && dst32) k_cast<double, float><<<VG, VB, 0, st>>>((const double*)src, (float*)dst, n);
-    else if (src32) k_cast<float, float><<<VG, VB, 0, st>>>((const float*)src, (float*)dst, n);
-    else k_cast<double, double><<<VG, VB, 0, st>>>((const double*)src, (double*)dst, n);
+    if (src32 && !dst32) launch_pdl(k_cast<float, double>, dim3(VG), dim3(VB), 0, st, (const float*)src, (double*)dst, n);
+    else if (!src32 && dst32) launch_pdl(k_cast<double, float>, dim3(VG), dim3(VB), 0, st, (const double*)src, (float*)dst, n);
+    else if (src32) launch_pdl(k_cast<float, float>, dim3(VG), dim3(VB), 0, st, (const float*)src, (float*)dst, n);
+    else launch_pdl(k_cast<double, double>, dim3(VG), dim3(VB), 0, st, (const double*)src, (double*)dst, n);
     PBM_LAUNCH("cast");
 }
 
@@ -80,6 +81,7 @@ __device__ __forceinline__ void first_jacobi_body(const T* __restrict__ b, const
 template <class T>
 __global__ void k_first_jacobi(const T* __restrict__ b, const T* __restrict__ idiag, const double* __restrict__ om,
                                T* __restrict__ x, int64_t n) {
+    pdl_wait();
     first_jacobi_body<T>(b, idiag, om, x, n, blockIdx.x, gridDim.x);
 }
 
@@ -101,14 +103,15 @@ void launch_scale_diag_first(pbm_grid* g, int k, bool fp32, const void* b, void*
     Level& L = g->L[k];
     const int64_t n = L.g.n() + (with_alpha ? 1 : 0);
     const double* om = &g->sc->mr[16 + k];
-    if (fp32) k_first_jacobi<float><<<VG, VB, 0, st>>>((const float*)b, L.idiag32, om, (float*)x, n);
-    else k_first_jacobi<double><<<VG, VB, 0, st>>>((const double*)b, L.idiag64, om, (double*)x, n);
+    if (fp32) launch_pdl(k_first_jacobi<float>, dim3(VG), dim3(VB), 0, st, (const float*)b, L.idiag32, om, (float*)x, n);
+    else launch_pdl(k_first_jacobi<double>, dim3(VG), dim3(VB), 0, st, (const double*)b, L.idiag64, om, (double*)x, n);
     PBM_LAUNCH("first jacobi");
 }
 
 template <class T>
 __global__ void k_dot(const T* __restrict__ a, const T* __restrict__ b, int64_t n, double* partials, unsigned* counter,
                       double* out) {
+    pdl_wait();
     __shared__ double sh[32];
     T st = T(0);   // per-thread sum in the vector type, CTA and grid sums in FP64
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
@@ -119,10 +122,10 @@ __global__ void k_dot(const T* __restrict__ a, const T* __restrict__ b, int64_t 
 
 void launch_dot(pbm_grid* g, bool fp32, const void* a, const void* b, int64_t n, int slot, cudaStream_t st) {
     if (fp32)
-        k_dot<float><<<VG, VB, 0, st>>>((const float*)a, (const float*)b, n, g->partials, &g->sc->counter[1],
+        launch_pdl(k_dot<float>, dim3(VG), dim3(VB), 0, st, (const float*)a, (const float*)b, n, g->partials, &g->sc->counter[1],
                                         &g->sc->red[slot]);
     else
-        k_dot<double><<<VG, VB, 0, st>>>((const double*)a, (const double*)b, n, g->partials, &g->sc->counter[1],
+        launch_pdl(k_dot<double>, dim3(VG), dim3(VB), 0, st, (const double*)a, (const double*)b, n, g->partials, &g->sc->counter[1],
                                          &g->sc->red[slot]);
     PBM_LAUNCH("dot");
 }
@@ -171,6 +174,7 @@ __device__ __forceinline__ void mr_lanczos2_body(const T* __restrict__ Az, T* __
 template <class T>
 __global__ void k_mr_lanczos2(const T* __restrict__ Az, T* __restrict__ v0, T* __restrict__ v1, int64_t n,
                               double* mr, const double* red) {
+    pdl_wait();
     mr_lanczos2_body<T>(Az, v0, v1, n, mr, red, blockIdx.x, gridDim.x);
 }
 
@@ -198,12 +202,14 @@ __device__ __forceinline__ void mr_update2_body(T* __restrict__ zc, const T* __r
 template <class T>
 __global__ void k_mr_update2(T* __restrict__ zc, const T* __restrict__ zn, T* __restrict__ d1, T* __restrict__ d2,
                              T* __restrict__ x, int64_t n, const double* mr) {
+    pdl_wait();
     mr_update2_body<T>(zc, zn, d1, d2, x, n, mr, blockIdx.x, gridDim.x);
 }
 
 // dst = (double) src, red = dst . other (FP32 preconditioner output into FP64 MINRES vectors)
 __global__ void k_cast_dot(const float* __restrict__ src, double* __restrict__ dst, const double* __restrict__ other,
                            int64_t n, double* partials, unsigned* counter, double* out) {
+    pdl_wait();
     __shared__ double sh[32];
     double s = 0.0;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
@@ -217,24 +223,24 @@ __global__ void k_cast_dot(const float* __restrict__ src, double* __restrict__ d
 
 void mr_lanczos2(pbm_grid* g, bool fp32, const void* Az, void* v0, void* v1, int64_t n, cudaStream_t st) {
     if (fp32)
-        k_mr_lanczos2<float><<<VG, VB, 0, st>>>((const float*)Az, (float*)v0, (float*)v1, n, g->sc->mr, g->sc->red);
+        launch_pdl(k_mr_lanczos2<float>, dim3(VG), dim3(VB), 0, st, (const float*)Az, (float*)v0, (float*)v1, n, g->sc->mr, g->sc->red);
     else
-        k_mr_lanczos2<double><<<VG, VB, 0, st>>>((const double*)Az, (double*)v0, (double*)v1, n, g->sc->mr,
+        launch_pdl(k_mr_lanczos2<double>, dim3(VG), dim3(VB), 0, st, (const double*)Az, (double*)v0, (double*)v1, n, g->sc->mr,
                                                  g->sc->red);
     PBM_LAUNCH("mr lanczos");
 }
 void mr_update2(pbm_grid* g, bool fp32, void* zc, const void* zn, void* d1, void* d2, void* x, int64_t n,
                 cudaStream_t st) {
     if (fp32)
-        k_mr_update2<float><<<VG, VB, 0, st>>>((float*)zc, (const float*)zn, (float*)d1, (float*)d2, (float*)x, n,
+        launch_pdl(k_mr_update2<float>, dim3(VG), dim3(VB), 0, st, (float*)zc, (const float*)zn, (float*)d1, (float*)d2, (float*)x, n,
                                                g->sc->mr);
     else
-        k_mr_update2<double><<<VG, VB, 0, st>>>((double*)zc, (const double*)zn, (double*)d1, (double*)d2, (double*)x,
+        launch_pdl(k_mr_update2<double>, dim3(VG), dim3(VB), 0, st, (double*)zc, (const double*)zn, (double*)d1, (double*)d2, (double*)x,
                                                 n, g->sc->mr);
     PBM_LAUNCH("mr update");
 }
 void cast_dot(pbm_grid* g, const float* src, double* dst, const double* other, int64_t n, int slot, cudaStream_t st) {
-    k_cast_dot<<<VG, VB, 0, st>>>(src, dst, other, n, g->partials, &g->sc->counter[1], &g->sc->red[slot]);
+    launch_pdl(k_cast_dot, dim3(VG), dim3(VB), 0, st, src, dst, other, n, g->partials, &g->sc->counter[1], &g->sc->red[slot]);
     PBM_LAUNCH("cast dot");
 }
 
@@ -278,7 +284,8 @@ __device__ void mr_scalars_body(double* mr, const double* red) {
     mr[5] = sn;
 }
 
-__global__ void k_mr_scalars(double* mr, const double* red) { mr_scalars_body(mr, red); }
+__global__ void k_mr_scalars(double* mr, const double* red) {
+    pdl_wait(); mr_scalars_body(mr, red); }
 
 __device__ void mr_init_body(double* mr, const double* red) {
     const double vz = red[1];
@@ -294,7 +301,8 @@ __device__ void mr_init_body(double* mr, const double* red) {
     mr[6] = b;
     mr[7] = b;
 }
-__global__ void k_mr_init(double* mr, const double* red) { mr_init_body(mr, red); }
+__global__ void k_mr_init(double* mr, const double* red) {
+    pdl_wait(); mr_init_body(mr, red); }
 
 // ---- batched vector and scalar stages of MINRES (one launch over the systems of a batch) ----
 template <class T>
@@ -340,20 +348,21 @@ void launch_scal_b(DevScalars* const* d_sc, int nsys, int op, cudaStream_t st) {
 }
 
 void mr_scalars(pbm_grid* g, cudaStream_t st) {
-    k_mr_scalars<<<1, 1, 0, st>>>(g->sc->mr, g->sc->red);
+    launch_pdl(k_mr_scalars, dim3(1), dim3(1), 0, st, g->sc->mr, g->sc->red);
     PBM_LAUNCH("mr scalars");
 }
 void mr_init(pbm_grid* g, cudaStream_t st) {
-    k_mr_init<<<1, 1, 0, st>>>(g->sc->mr, g->sc->red);
+    launch_pdl(k_mr_init, dim3(1), dim3(1), 0, st, g->sc->mr, g->sc->red);
     PBM_LAUNCH("mr init");
 }
 // x64 += sign * (double) d32 (iterative refinement correction, or its removal)
 __global__ void k_add_f32(double* __restrict__ x, const float* __restrict__ d, int64_t n, double sign) {
+    pdl_wait();
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
         x[i] += sign * double(d[i]);
 }
 void add_f32(double* x, const float* d, int64_t n, cudaStream_t st, double sign) {
-    k_add_f32<<<VG, VB, 0, st>>>(x, d, n, sign);
+    launch_pdl(k_add_f32, dim3(VG), dim3(VB), 0, st, x, d, n, sign);
     PBM_LAUNCH("add f32");
 }
 

@@ -90,6 +90,7 @@ __device__ __forceinline__ void restrict_body(const RestrictArgs<T>& P, unsigned
 
 template <class T>
 __global__ void k_restrict(RestrictArgs<T> P) {
+    pdl_wait();
     restrict_body<T>(P, blockIdx.x, gridDim.x);
 }
 template <class T>
@@ -108,11 +109,11 @@ void launch_restrict(pbm_grid* g, int k, bool fp32, const void* rf, void* bc, bo
     const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nt + 127) / 128, 152 * 16)));
     const double* om = &g->sc->mr[16 + k + 1];
     if (fp32)
-        k_restrict<float><<<blocks, 128, 0, st>>>(RestrictArgs<float>{F.nx, F.ny, F.nz, F.support, with_alpha ? 1 : 0,
+        launch_pdl(k_restrict<float>, dim3(blocks), dim3(128), 0, st, RestrictArgs<float>{F.nx, F.ny, F.nz, F.support, with_alpha ? 1 : 0,
                                                                       (const float*)rf, (float*)bc, scale,
                                                                       (float*)xfirst, C.idiag32, om});
     else
-        k_restrict<double><<<blocks, 128, 0, st>>>(RestrictArgs<double>{F.nx, F.ny, F.nz, F.support,
+        launch_pdl(k_restrict<double>, dim3(blocks), dim3(128), 0, st, RestrictArgs<double>{F.nx, F.ny, F.nz, F.support,
                                                                         with_alpha ? 1 : 0, (const double*)rf,
                                                                         (double*)bc, scale, (double*)xfirst,
                                                                         C.idiag64, om});
@@ -160,6 +161,7 @@ __device__ __forceinline__ void prolong_body(const ProlongArgs<T>& P, unsigned b
 
 template <class T>
 __global__ void k_prolong_add(ProlongArgs<T> P) {
+    pdl_wait();
     prolong_body<T>(P, blockIdx.x, gridDim.x);
 }
 template <class T>
@@ -174,11 +176,11 @@ void launch_prolong_add(pbm_grid* g, int k, bool fp32, const void* xc, void* xf,
     const int64_t nt = 3 * F.nnode();
     const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nt + 255) / 256, 152 * 16)));
     if (fp32)
-        k_prolong_add<float><<<blocks, 256, 0, st>>>(ProlongArgs<float>{F.nx, F.ny, F.nz, F.support,
+        launch_pdl(k_prolong_add<float>, dim3(blocks), dim3(256), 0, st, ProlongArgs<float>{F.nx, F.ny, F.nz, F.support,
                                                                         with_alpha ? 1 : 0, (const float*)xc,
                                                                         (float*)xf});
     else
-        k_prolong_add<double><<<blocks, 256, 0, st>>>(ProlongArgs<double>{F.nx, F.ny, F.nz, F.support,
+        launch_pdl(k_prolong_add<double>, dim3(blocks), dim3(256), 0, st, ProlongArgs<double>{F.nx, F.ny, F.nz, F.support,
                                                                           with_alpha ? 1 : 0, (const double*)xc,
                                                                           (double*)xf});
     PBM_LAUNCH("prolong");
@@ -571,6 +573,7 @@ __device__ __forceinline__ void coarsest_solve_body(const CoarsestArgs<T>& P, un
 
 template <class T>
 __global__ void k_coarsest_solve(CoarsestArgs<T> P) {
+    pdl_wait();
     coarsest_solve_body<T>(P, blockIdx.x);
 }
 template <class T>
@@ -584,8 +587,8 @@ void launch_coarsest_solve(pbm_grid* g, bool fp32, const void* b, void* x, bool 
     const int N = g->nc + 1;
     const int nv = with_alpha ? N : N - 1;
     const int blocks = (nv * 32 + 255) / 256;
-    if (fp32) k_coarsest_solve<float><<<blocks, 256, 0, st>>>(CoarsestArgs<float>{N, nv, g->cinv, (const float*)b, (float*)x});
-    else k_coarsest_solve<double><<<blocks, 256, 0, st>>>(CoarsestArgs<double>{N, nv, g->cinv, (const double*)b, (double*)x});
+    if (fp32) launch_pdl(k_coarsest_solve<float>, dim3(blocks), dim3(256), 0, st, CoarsestArgs<float>{N, nv, g->cinv, (const float*)b, (float*)x});
+    else launch_pdl(k_coarsest_solve<double>, dim3(blocks), dim3(256), 0, st, CoarsestArgs<double>{N, nv, g->cinv, (const double*)b, (double*)x});
     PBM_LAUNCH("coarsest solve");
 }
 

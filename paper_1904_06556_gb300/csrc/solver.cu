@@ -316,6 +316,7 @@ static void precondition(pbm_grid* g, bool fp32, bool pc32, bool op_s, const voi
 // ctl[0] target on the residual estimate, ctl[1] iteration budget, ctl[2] iterations done,
 // ctl[3] exit reason: 1 breakdown, 2 lucky (beta = 0 or r = 0), 3 estimate below target, 4 budget
 __global__ void k_mr_ctl(double* ctl, double target, double budget) {
+    pdl_wait();
     ctl[0] = target;
     ctl[1] = budget;
     ctl[2] = 0.0;
@@ -333,6 +334,7 @@ __device__ __forceinline__ int mr_exit_reason(const double* mr, double target, d
 // the WHILE condition of the captured loop: continue while no exit reason holds (at most ctl[1]
 // iterations per graph launch, so the loop always ends)
 __global__ void k_mr_check(const double* mr, double* ctl, cudaGraphConditionalHandle h) {
+    pdl_wait();
     const double it = ctl[2] + 1.0;
     ctl[2] = it;
     const int r = mr_exit_reason(mr, ctl[0], it, ctl[1]);
@@ -375,7 +377,7 @@ static cudaGraphExec_t mr_graph(pbm_grid* g, bool fp32, bool pc32, bool op_s, vo
         PBM_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         try {
             mr_iteration(g, fp32, pc32, op_s, V, X, nv, cs);
-            k_mr_check<<<1, 1, 0, cs>>>(g->sc->mr, g->sc->ctl, h);
+            launch_pdl(k_mr_check, dim3(1), dim3(1), 0, cs, g->sc->mr, g->sc->ctl, h);
             PBM_LAUNCH("mr check");
         } catch (...) {
             cudaGraph_t dummy = nullptr;
@@ -443,7 +445,7 @@ static MrResult minres(pbm_grid* g, bool fp32, bool op_s, const void* b, void* x
         if (graph) {
             int64_t kernels = 0;
             cudaGraphExec_t ex = mr_graph(g, fp32, pc32, op_s, V, X, nv, kernels);
-            k_mr_ctl<<<1, 1, 0, st>>>(g->sc->ctl, target, double(budget));
+            launch_pdl(k_mr_ctl, dim3(1), dim3(1), 0, st, g->sc->ctl, target, double(budget));
             PBM_LAUNCH("mr ctl");
             PBM_CUDA(cudaGraphLaunch(ex, st));
             read_state(true);
