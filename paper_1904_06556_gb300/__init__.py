@@ -182,8 +182,9 @@ class Grid:
                         out: torch.Tensor | None = None, dot: bool = False):
         """pbm_apply_level_f32: one FP32 application of level `level`'s operator with a fused epilogue."""
         f = torch.float32
-        n = self._level_n[level] + (1 if op == "S" else 0)
-        y = out if out is not None else torch.empty(n, dtype=f, device=x.device)
+        # a level out of range is left to the library to reject (PBM_EINVAL)
+        n = self._level_n[level] + (1 if op == "S" else 0) if 0 <= level < len(self._level_n) else None
+        y = out if out is not None else torch.empty(n if n is not None else x.numel(), dtype=f, device=x.device)
         d = C.c_double(0.0)
         self._check(self._L.pbm_apply_level_f32(self._h, level, _lib.OPS[op], _lib.EPILOGUES[epilogue],
                                                 _ptr(x, f, n, "x"), _ptr(b, f, n, "b") if b is not None else None,

@@ -483,6 +483,38 @@ def test_minres_zero_rhs_and_state_errors(pkg):
         G.set_density(bad)
 
 
+def test_error_statuses_of_the_fp32_ip_and_doc_entry_points(pkg):
+    """Out-of-order calls and invalid arguments of the newer entry points return their documented statuses and
+    leave the handle usable."""
+    from paper_1904_06556_gb300 import PbmError
+    f64 = dict(dtype=torch.float64, device="cuda")
+    G = pkg.Grid(8, 4, 4, 2, "cantilever", precision="mixed")
+    x32 = torch.zeros(G.n + 1, dtype=torch.float32, device="cuda")
+    with pytest.raises(PbmError, match="PBM_ESTATE"):          # no hierarchy yet
+        G.apply_fine_f32("S", "apply", x32)
+    with pytest.raises(PbmError, match="PBM_ESTATE"):
+        G.diag(0)
+    with pytest.raises(PbmError, match="PBM_EINVAL"):          # plan out of range
+        G.set_fp32_plan("K", pkg.fp32_plan_count())
+    with pytest.raises(PbmError, match="PBM_ESTATE"):          # interior-point calls before pbm_ip_set_state
+        G.ip_reduced_rhs(torch.zeros(G.n, **f64))
+    st = dict(u=torch.zeros(G.n, **f64), rho=torch.full((G.m,), 0.5, **f64), nu_lo=torch.ones(G.m, **f64),
+              nu_up=torch.ones(G.m, **f64), alpha=1.0, V=0.5 * G.m, rho_lo=1e-3, rho_up=1.0, r=1e-2, s=1e-2)
+    bad = dict(st, rho=torch.full((G.m,), 1.5, **f64))        # outside (rho_lo, rho_up)
+    with pytest.raises(PbmError, match="PBM_EINVAL"):
+        G.ip_set_state(bad)
+    with pytest.raises(PbmError, match="PBM_EINVAL"):
+        G.ip_set_state(dict(st, r=0.0))
+    G.ip_set_state(st)                                        # the handle still works
+    with pytest.raises(PbmError, match="PBM_ESTATE"):          # a PBM call on an interior-point state
+        G.apply_S(torch.zeros(G.n + 1, **f64))
+    with pytest.raises(PbmError, match="PBM_EINVAL"):          # DOC with an empty bound interval
+        G.doc_step(torch.full((G.m,), 0.5, **f64), torch.zeros(G.n, **f64), torch.zeros(G.n, **f64), 0.5 * G.m, 1.0,
+                   1.0)
+    with pytest.raises(PbmError, match="PBM_EINVAL"):          # a level out of range
+        G.apply_level_f32(5, "K", "apply", torch.zeros(3, dtype=torch.float32, device="cuda"))
+
+
 # ------------------------------------------------------------------------------------------------
 # Newton step (Algorithm 2) against the oracle's step with a direct solve
 # ------------------------------------------------------------------------------------------------
