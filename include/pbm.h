@@ -228,8 +228,13 @@ int pbm_apply_level_f32(pbm_grid* g, int level, int op, int epilogue, const floa
  * on PBM_MIXED grids and keeps the fastest per operator; pbm_set_fp32_plan overrides that choice
  * for `op` (PBM_OP_K or PBM_OP_S) with plan 0 <= plan < pbm_fp32_plan_count(). Every plan computes
  * the same operator; only the reduction order of the dot products and alpha row depends on it.
- * Errors: PBM_EINVAL. */
+ * Plan pbm_fp32_tc_plan() (the last) runs the element contraction K_e x_e of every element layer
+ * on the tensor cores (tcgen05 MMA, TF32 operands split into a rounded high part and the FP32
+ * remainder, FP32 accumulation: products as accurate as FP32 arithmetic); the others run the
+ * factored element matrix on the CUDA cores. A wait of the tensor-core plan that gives up (after
+ * one second) leaves a NaN in y[0]. Errors: PBM_EINVAL. */
 int pbm_fp32_plan_count(void);
+int pbm_fp32_tc_plan(void);
 int pbm_set_fp32_plan(pbm_grid* g, int op, int plan);
 
 /* Copies the Jacobi diagonal of level `level` of the current hierarchy (K or S, the last one set

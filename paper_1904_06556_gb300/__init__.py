@@ -50,6 +50,11 @@ def fp32_plan_count() -> int:
     return int(lib().pbm_fp32_plan_count())
 
 
+def fp32_tc_plan() -> int:
+    """The plan that runs the element contraction on the tensor cores (pbm_fp32_tc_plan)."""
+    return int(lib().pbm_fp32_tc_plan())
+
+
 def _ptr(t: torch.Tensor | None, dtype=torch.float64, n: int | None = None, name: str = "tensor"):
     if t is None:
         return None

@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pbm_apply_level_f32": (i, [vp, i, i, i, vp, vp, vp, C.POINTER(C.c_double), vp]),
         "pbm_get_diag": (i, [vp, i, vp, vp]),
         "pbm_fp32_plan_count": (i, []),
+        "pbm_fp32_tc_plan": (i, []),
         "pbm_ip_set_state": (i, [vp, C.POINTER(IPState), vp]),
         "pbm_default_doc_params": (i, [C.POINTER(DocParams)]),
         "pbm_doc_step": (i, [vp, vp, vp, vp, C.POINTER(DocParams), C.POINTER(DocInfo), vp]),

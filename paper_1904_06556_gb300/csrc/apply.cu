@@ -448,8 +448,8 @@ void launch_fine(pbm_grid* g, bool fp32, const void* w, const void* d, const voi
     const bool prof = g->prof_on && fp32 == (g->desc.precision == PBM_MIXED);
     if (prof) prof_begin(g, st);
     if (fp32)
-        fused_fine_f32(fused_plan(g->L[0].g, g->fusedP[s ? 1 : 0]), red_set(g, a.rset), g->L[0].g, g->kehat,
-                       (const float*)w, s ? (const float*)d : nullptr, s ? (const float*)u : nullptr, a, st);
+        fused_fine_f32(fused_plan(g->L[0].g, g->fusedP[s ? 1 : 0], s), red_set(g, a.rset), g->L[0].g, g->kehat,
+                       g->tc, (const float*)w, s ? (const float*)d : nullptr, s ? (const float*)u : nullptr, a, st);
     else
         cols_fine<double>(g, (const double*)w, s ? (const double*)d : nullptr, s ? g->what_hat : nullptr, nullptr, a,
                           st);

@@ -291,6 +291,13 @@ int pbm_create_grid(const pbm_grid_desc* d, pbm_grid** out) {
     upload_tri_tables();
     g->G_dev = (double*)dalloc(g, sizeof(double) * 8 * NTRI);
     PBM_CUDA(cudaMemcpy(g->G_dev, Gtri.data(), sizeof(double) * 8 * NTRI, cudaMemcpyHostToDevice));
+    {
+        std::vector<float> B;
+        tc_build(g->Ke, B, g->tc.terms, g->tc.scale);
+        g->tcB = (float*)dalloc(g, sizeof(float) * B.size());
+        PBM_CUDA(cudaMemcpy(g->tcB, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice));
+        g->tc.B = g->tcB;
+    }
 
     const Geom& F = g->L[0].g;
     const int64_t n = F.n(), m = F.m();
@@ -399,6 +406,7 @@ int pbm_destroy_grid(pbm_grid* g) {
         dfree(L.t32);
     }
     dfree(g->G_dev);
+    dfree(g->tcB);
     dfree(g->rho);
     dfree(g->w64);
     dfree(g->d64);
@@ -466,7 +474,7 @@ int pbm_grid_info_get(const pbm_grid* g, pbm_grid_info* out) {
     out->fine_chunk[2] = g->desc.precision == PBM_MIXED ? fine_L(g, true, false) : 0;
     out->fine_chunk[3] = g->desc.precision == PBM_MIXED ? fine_L(g, true, true) : 0;
     for (int op = 0; op < 2; ++op) {
-        const FusedPlan fp = fused_plan(F, g->fusedP[op]);
+        const FusedPlan fp = fused_plan(F, g->fusedP[op], op == 1);
         out->fp32_tile[op][0] = fp.TX;
         out->fp32_tile[op][1] = fp.TY;
         out->fp32_tile[op][2] = fp.DZ;
@@ -605,6 +613,8 @@ int pbm_apply_level_f32(pbm_grid* g, int level, int op, int epilogue, const floa
 }
 
 int pbm_fp32_plan_count(void) { return fused_num_plans(); }
+
+int pbm_fp32_tc_plan(void) { return fused_tc_plan(); }
 
 int pbm_set_fp32_plan(pbm_grid* g, int op, int plan) {
     PBM_TRY

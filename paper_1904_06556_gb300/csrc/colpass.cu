@@ -657,10 +657,10 @@ void autotune_fine(pbm_grid* g) {
                 float best = 3.4e38f;
                 int bestP = 0;
                 for (int c = 0; c < fused_num_plans(); ++c) {
-                    const FusedPlan fp = fused_plan(G, c);
+                    const FusedPlan fp = fused_plan(G, c, op == 1);
                     for (int rep = 0; rep < 4; ++rep) {
                         if (rep == 1) PBM_CUDA(cudaEventRecord(e0, 0));
-                        fused_fine_f32(fp, red_set(g, 0), G, g->kehat, g->w32, op ? g->d32 : nullptr,
+                        fused_fine_f32(fp, red_set(g, 0), G, g->kehat, g->tc, g->w32, op ? g->d32 : nullptr,
                                        op ? g->u32 : nullptr, a, 0);
                     }
                     PBM_CUDA(cudaEventRecord(e1, 0));

@@ -129,12 +129,6 @@ __device__ __forceinline__ double fused_cta_sum(double v, double* sh) {
     return s;
 }
 
-// Support of node (i, j) as two bits: bit 0 fixed on planes k >= 1, bit 1 fixed on plane 0. Every
-// support of node_fixed depends on the plane only through k == 0.
-__device__ __forceinline__ int fixed_bits(int support, int nx, int ny, int nz, int i, int j) {
-    return (node_fixed(support, nx, ny, nz, i, j, 1) ? 1 : 0) | (node_fixed(support, nx, ny, nz, i, j, 0) ? 2 : 0);
-}
-
 // MODE 0: K(w) x. MODE 2: S x with W_e = Khat H u_e recomputed from the staged u. NT threads per
 // CTA, MINB resident CTAs per SM requested from the register allocator, an owner tile of TX x TY
 // node columns (compile-time, so that every shared-memory offset is a constant).
@@ -716,7 +710,12 @@ static const int kFusedPlans[][4] = {PBM_FUSED_PLANS(PBM_PLAN_ROW)};
 #undef PBM_PLAN_ROW
 constexpr int kFusedNumPlans = int(sizeof(kFusedPlans) / sizeof(kFusedPlans[0]));
 
-FusedPlan fused_plan(const Geom& G, int cand) {
+FusedPlan fused_plan(const Geom& G, int cand, bool op_s) {
+    if (cand == kFusedNumPlans) {
+        FusedPlan p = tc_plan(G, op_s);
+        p.var = cand;
+        return p;
+    }
     FusedPlan p{};
     p.var = cand;
     const int per_sm = kFusedPlans[cand][1];
@@ -744,18 +743,20 @@ FusedPlan fused_plan(const Geom& G, int cand) {
     return p;
 }
 
-int fused_num_plans() { return kFusedNumPlans; }
+int fused_num_plans() { return kFusedNumPlans + 1; }
+
+int fused_tc_plan() { return kFusedNumPlans; }
 
 int fused_blocks(const FusedPlan& p) { return p.gx * p.gy * p.gz; }
 
-int fused_threads(const FusedPlan& p) { return kFusedPlans[p.var][0]; }
+int fused_threads(const FusedPlan& p) { return p.var == kFusedNumPlans ? 256 : kFusedPlans[p.var][0]; }
 
 // plan used until the autotuner has timed the candidates (and for grids it does not tune): fewest
 // plane steps per SM (waves x (DZ + 1) / resident CTAs), then fewest element columns computed
 int fused_default_plan(const Geom& G) {
     int best = 0;
     double bc = 1e300;
-    for (int c = 0; c < fused_num_plans(); ++c) {
+    for (int c = 0; c < kFusedNumPlans; ++c) {
         const FusedPlan p = fused_plan(G, c);
         const int per_sm = kFusedPlans[p.var][1];
         const int blocks = fused_blocks(p);
@@ -781,8 +782,12 @@ static void fused_launch(const FusedPlan& p, int blocks, const FusedArgs& P, cud
     }
 }
 
-void fused_fine_f32(const FusedPlan& p, const RedSet& r, const Geom& G, const KeHat& kh, const float* w,
-                    const float* d, const float* u, const ApplyArgs& a, cudaStream_t st) {
+void fused_fine_f32(const FusedPlan& p, const RedSet& r, const Geom& G, const KeHat& kh, const TcMatrix& tm,
+                    const float* w, const float* d, const float* u, const ApplyArgs& a, cudaStream_t st) {
+    if (p.var == kFusedNumPlans) {
+        tc_fine_f32(p, r, G, tm, w, d, u, a, st);
+        return;
+    }
     const bool s = d != nullptr;
     const int nt = fused_threads(p);
     if ((p.TX + 1) * (p.TY + 1) > nt || 3 * (p.TX + 2) * (p.TY + 2) > FSLOT * nt)

@@ -77,6 +77,12 @@ __host__ __device__ inline bool node_fixed(int support, int nx, int ny, int nz, 
     }
 }
 
+// Support of node (i, j) as two bits: bit 0 fixed on planes k >= 1, bit 1 fixed on plane 0. Every
+// support of node_fixed depends on the plane only through k == 0.
+__host__ __device__ inline int fixed_bits(int support, int nx, int ny, int nz, int i, int j) {
+    return (node_fixed(support, nx, ny, nz, i, j, 1) ? 1 : 0) | (node_fixed(support, nx, ny, nz, i, j, 0) ? 2 : 0);
+}
+
 // ------------------------------------------------------------------------------------------------
 // element matrix of the fine level in the (sum, difference) tensor basis
 //
@@ -198,6 +204,14 @@ __host__ __device__ inline int tri_index(int i, int j) {  // i <= j
     return i * 24 - (i * (i - 1)) / 2 + (j - i);
 }
 
+// the element matrix as the operand of the tensor-core kernel: hi and lo parts (2 x 1024 floats) of
+// K_e / scale in the MMA layout, and the number of MMA terms (2 when K_e / scale is exact in TF32)
+struct TcMatrix {
+    const float* B = nullptr;
+    int terms = 3;
+    float scale = 1.0f;
+};
+
 // device scalar block used by the reductions, Lanczos and MINRES
 struct DevScalars {
     double red[64];        // reduction outputs (slot per use)
@@ -224,6 +238,8 @@ struct pbm_grid {
     double Kdiag;                     // K_e[i][i] (all equal for the isotropic cube)
     double G[8][576];                 // P_c^T K_e P_c for the 8 children (coarse local dofs)
     double* G_dev = nullptr;          // 8 x NTRI upper triangles, [c][t]
+    float* tcB = nullptr;             // element matrix as the tensor-core operand (2 x 1024 floats)
+    pbm::TcMatrix tc;
     // fine-level element data
     double* rho = nullptr;            // density (m)
     double* w64 = nullptr;            // element weights of the current operator (rho or rho')
@@ -491,18 +507,25 @@ void cols_fine(pbm_grid* g, const T* w, const T* d, const T* what, const T* u, c
 template <class T>
 void cols_coarse(pbm_grid* g, int k, const T* A, const T* bord, const ApplyArgs& a, cudaStream_t st);
 void launch_what_hat(pbm_grid* g, cudaStream_t st);
-// single-pass FP32 fine operator (fused.cu): tile plan of candidate `cand` for a grid, and the launch
+// single-pass FP32 fine operator (fused.cu): tile plan of candidate `cand` for a grid (of the K or the S
+// operator), and the launch. The last plan is the tensor-core kernel (tc.cu).
 struct FusedPlan {
     int TX, TY, DZ, gx, gy, gz;
-    int var;   // kernel variant (threads per CTA, resident CTAs per SM)
+    int var;   // kernel variant (threads per CTA, resident CTAs per SM; tensor cores)
 };
-FusedPlan fused_plan(const Geom& G, int cand);
+FusedPlan fused_plan(const Geom& G, int cand, bool op_s = false);
 int fused_num_plans();
+int fused_tc_plan();
 int fused_default_plan(const Geom& G);
 int fused_blocks(const FusedPlan& p);
 int fused_threads(const FusedPlan& p);
-void fused_fine_f32(const FusedPlan& p, const RedSet& r, const Geom& G, const KeHat& kh, const float* w,
-                    const float* d, const float* u, const ApplyArgs& a, cudaStream_t st);
+void fused_fine_f32(const FusedPlan& p, const RedSet& r, const Geom& G, const KeHat& kh, const TcMatrix& tm,
+                    const float* w, const float* d, const float* u, const ApplyArgs& a, cudaStream_t st);
+// tensor-core variant (tc.cu): operand matrices from K_e (host), plan, launch
+void tc_build(const double* Ke, std::vector<float>& B, int& terms, float& scale);
+FusedPlan tc_plan(const Geom& G, bool op_s);
+void tc_fine_f32(const FusedPlan& p, const RedSet& r, const Geom& G, const TcMatrix& tm, const float* w,
+                 const float* d, const float* u, const ApplyArgs& a, cudaStream_t st);
 // single-pass FP32 coarse-level operator (stored Galerkin matrices; fused.cu)
 int fused_coarse_num_plans();
 FusedPlan fused_coarse_plan(const Geom& G, int cand);

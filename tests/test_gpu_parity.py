@@ -186,6 +186,37 @@ def test_fused_fp32_S_epilogues_and_jacobi_diagonal(pkg, dims, bc, seed):
                      rng.standard_normal(pb.n + 1), rng.standard_normal(pb.n + 1), 1e-5)
 
 
+@pytest.mark.parametrize("dims,bc,op", [((8, 4, 4), "cantilever", "K"), ((34, 10, 6), "bridge_corners", "K"),
+                                        ((64, 20, 12), "cantilever", "K"), ((96, 24, 16), "bridge_edges", "K"),
+                                        ((34, 10, 6), "bridge_corners", "S"), ((64, 20, 12), "cantilever", "S"),
+                                        ((18, 6, 4), "bridge_edges", "S")])
+def test_tensor_core_plan_epilogues(pkg, dims, bc, op):
+    """The tensor-core plan (tcgen05 MMAs on TF32 high / remainder splits, FP32 accumulation) with each
+    fused epilogue against the oracle at the FP32 operator's tolerance: one and several 31 x 7 node
+    tiles with ragged edges, plane chunks, supported nodes on every kind of support."""
+    rng = np.random.default_rng(sum(dims) + 17)
+    if op == "K":
+        g = fem.Grid(*dims, bc)
+        rho = rng.uniform(1e-3, 1.0, g.m)
+        G = pkg.Grid(*dims, levels_for(*dims), bc, precision="mixed")
+        G.set_density(dev(rho))
+        G.vcycle("K", dev(rng.standard_normal(g.n)))
+        G.set_fp32_plan("K", pkg.fp32_tc_plan())
+        assert G.info()["fp32_tile"][0][4] == pkg.fp32_tc_plan()
+        K = fem.assemble_K(g, rho, fem.element_stiffness())
+        _check_epilogues(G, "K", lambda v: K @ v, K.diagonal(), rng.standard_normal(g.n),
+                         rng.standard_normal(g.n), 2e-6)
+    else:
+        pb, st, d = make_problem(*dims, bc, sum(dims), 0.5)
+        G = pkg.Grid(*dims, levels_for(*dims), bc, precision="mixed")
+        G.set_state(state_dev(d))
+        G.set_fp32_plan("S", pkg.fp32_tc_plan())
+        cf = pbm.coeffs(pb, st)
+        S = pbm.assemble_S(pb, st, cf)
+        _check_epilogues(G, "S", lambda v: pbm.apply_S_elementwise(pb, st, cf, v), S.diagonal(),
+                         rng.standard_normal(pb.n + 1), rng.standard_normal(pb.n + 1), 1e-5)
+
+
 @pytest.mark.parametrize("dims,bc,seed", [((34, 10, 6), "bridge_corners", 9), ((64, 20, 12), "cantilever", 10)])
 def test_fused_fp32_every_tile_plan(pkg, dims, bc, seed):
     """Every tile plan of the FP32 operator (CTA sizes, tiles, chunk lengths) gives the oracle's K x and
