@@ -71,10 +71,11 @@ __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t a, uint64_t b, u
         : "memory");
 }
 
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
-                 : "memory");
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
+
+__device__ __forceinline__ uint64_t pack_desc(uint32_t lo, uint32_t hi) { return (uint64_t(hi) << 32) | lo; }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -87,22 +88,26 @@ __device__ __forceinline__ uint64_t gtimer() {
     return t;
 }
 
-// waits for the completion of phase `parity` of an mbarrier, for one second at most
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    const uint32_t a = smem_addr(bar);
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t done;
+    // suspend-time hint 1 ms: the thread sleeps until the phase completes or the hint runs out
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000000;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// waits for the completion of phase `parity` of the mbarrier at shared address a, for one second at
+// most (then false)
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+    if (mbar_try(a, parity)) return true;
     const uint64_t t0 = gtimer();
-    for (int it = 0; it < (1 << 26); ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if ((it & 255) == 255 && gtimer() - t0 > 1000000000ull) break;
-    }
+    while (gtimer() - t0 < 1000000000ull)
+        if (mbar_try(a, parity)) return true;
     return false;
 }
 
@@ -124,11 +129,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// x rounded to the nearest TF32 value (ties away from zero)
+// x rounded to the nearest TF32 value (ties away from zero): half a unit of the 11th significant bit
+// added to the magnitude, the 13 bits below it cleared (finite x far below the FP32 maximum)
 __device__ __forceinline__ float tf32_hi(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 __device__ __forceinline__ void split_store(float4* hi, float4* lo, const float (&v)[3], bool zero) {
@@ -183,9 +187,10 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
     constexpr bool S = MODE == 2;
     constexpr int NV = S ? 2 : 1;                  // staged vectors: x (and u)
     constexpr uint32_t NCOL = S ? 256 : 128;       // 2 buffers x 2 MMA halves x NV x 32 columns
+    constexpr int PL = 2 * SLOTS;                  // float4 per staged plane (hi, lo)
     extern __shared__ float4 tc_sm[];
     float4* stg = tc_sm;                           // [NV][RING][hi, lo][SLOTS]
-    float4* sB = stg + NV * RING * 2 * SLOTS;      // [hi, lo][256]
+    float4* sB = stg + NV * RING * PL;             // [hi, lo][256]
     float4* sq = sB + 2 * (BFLOATS / 4);           // [2][EYT][EXT] row sums of the node exchange
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_slot;
@@ -204,47 +209,55 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
     const int kstart = max(kz0 - 1, 0);
     const int pmax = min(kz1, nz);                 // last node plane the chunk reads
 
-    // staging slots q = t + s NT: node row j, run r, node i of the run; float offset of the node in a
-    // plane (-1 outside the grid, -2 no slot) and its support bits
-    int gofs[PSLOT];
-    int fbits = 0;
+    // staging slots q = t + s NT (node row j, run r, node i of the run): a pointer to the node in the
+    // next plane to fetch, and whether the node is in the grid / supported on plane 0 / on the others
+    const float* gx[PSLOT];
+    const float* gu[PSLOT];
+    unsigned has = 0, in = 0, fix0 = 0, fix1 = 0;
 #pragma unroll
     for (int s = 0; s < PSLOT; ++s) {
         const int q = t + s * NT;
-        gofs[s] = -2;
+        int64_t o = 0;
         if (q < SLOTS) {
+            has |= 1u << s;
             const int j = q / (SEG * 9), rr = q - j * (SEG * 9);
             const int run = rr / 9, i = rr - run * 9;
             const int gxn = X0 - 1 + 8 * run + i, gyn = Y0 - 1 + j;
-            const bool in = gxn >= 0 && gxn <= nx && gyn >= 0 && gyn <= ny;
-            gofs[s] = in ? 3 * (gxn + (nx + 1) * gyn) : -1;
-            if (in) fbits |= fixed_bits(support, nx, ny, nz, gxn, gyn) << (2 * s);
+            if (gxn >= 0 && gxn <= nx && gyn >= 0 && gyn <= ny) {
+                in |= 1u << s;
+                o = 3 * (gxn + int64_t(nx + 1) * gyn);
+                if (node_fixed(support, nx, ny, nz, gxn, gyn, 0)) fix0 |= 1u << s;
+                if (node_fixed(support, nx, ny, nz, gxn, gyn, 1)) fix1 |= 1u << s;
+            }
         }
+        gx[s] = P.x + o + kstart * plane;
+        gu[s] = S ? P.u + o + kstart * plane : nullptr;
     }
     float px[PSLOT][3], pu[PSLOT][3];
-    auto fetch = [&](int k) {
-        const float* xs = P.x + int64_t(k) * plane;
-        const float* us = S ? P.u + int64_t(k) * plane : nullptr;
+    auto fetch = [&]() {   // the next plane, in order
 #pragma unroll
-        for (int s = 0; s < PSLOT; ++s)
+        for (int s = 0; s < PSLOT; ++s) {
+            const bool ok = (in >> s) & 1u;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                px[s][c] = gofs[s] >= 0 ? __ldg(xs + gofs[s] + c) : 0.0f;
-                if (S) pu[s][c] = gofs[s] >= 0 ? __ldg(us + gofs[s] + c) : 0.0f;
+                px[s][c] = ok ? __ldg(gx[s] + c) : 0.0f;
+                if (S) pu[s][c] = ok ? __ldg(gu[s] + c) : 0.0f;
             }
+            gx[s] += plane;
+            if (S) gu[s] += plane;
+        }
     };
     // writes the fetched plane k into its ring slot as hi / lo, supported nodes zero (the masked
     // vectors the element matrices act on)
     auto stage = [&](int k) {
-        const int r = k % RING;
-        const int sh = k == 0 ? 1 : 0;
+        float4* base = stg + (k & (RING - 1)) * PL + t;
+        const unsigned fx = k == 0 ? fix0 : fix1;
 #pragma unroll
         for (int s = 0; s < PSLOT; ++s) {
-            if (gofs[s] == -2) continue;
-            const int q = t + s * NT;
-            const bool fx = (fbits >> (2 * s + sh)) & 1;
-            split_store(&stg[(r * 2 + 0) * SLOTS + q], &stg[(r * 2 + 1) * SLOTS + q], px[s], fx);
-            if (S) split_store(&stg[((RING + r) * 2 + 0) * SLOTS + q], &stg[((RING + r) * 2 + 1) * SLOTS + q], pu[s], fx);
+            if (!((has >> s) & 1u)) continue;
+            const bool z = (fx >> s) & 1u;
+            split_store(base + s * NT, base + s * NT + SLOTS, px[s], z);
+            if (S) split_store(base + RING * PL + s * NT, base + RING * PL + s * NT + SLOTS, pu[s], z);
         }
     };
 
@@ -257,23 +270,28 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
     // owner of node (ex, ey) = local node (lx, ly), lx, ly >= 1
     const int I = ex, J = ey;
     const bool owner = lx >= 1 && ly >= 1 && I <= nx && J <= ny;
-    const int obits = owner ? fixed_bits(support, nx, ny, nz, I, J) : 0;
+    const bool ofix0 = owner && node_fixed(support, nx, ny, nz, I, J, 0);
+    const bool ofix1 = owner && node_fixed(support, nx, ny, nz, I, J, 1);
     const int orun = min(lx >> 3, SEG - 1);
     const int oslot = (ly * SEG + orun) * 9 + (lx - 8 * orun);
     const int eslot = (ly * SEG + (lx >> 3)) * 9 + (lx & 7);   // corner (0, 0) of the element
     const int64_t elayer = int64_t(nx) * ny;
-    const int64_t e0 = ecol ? ex + int64_t(nx) * ey : 0;
+    const float* wp = P.w + (ecol ? ex + int64_t(nx) * ey : 0) + kstart * elayer;
+    const float* dp = S ? P.d + (ecol ? ex + int64_t(nx) * ey : 0) + kstart * elayer : nullptr;
+    float4* const sq_w = sq + ly * EXT + lx;           // this row's sums (buffer 0)
+    const float4* const sq_r = sq + (ly - 1) * EXT + lx;   // the row below (owners)
 
     const float xa = S ? P.x[P.n] : 0.0f;
-    const double om = P.mode == EPI_JACOBI ? *P.omega : 0.0;
+    const int mode = P.mode;
+    const double om = mode == EPI_JACOBI ? *P.omega : 0.0;
     const float omF = float(om);
     const bool want_dot = P.dot_slot >= 0;
     const float ks = P.kscale;
     float pdT = 0.0f, paT = 0.0f;
 
     if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[1])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_addr(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_addr(&mbar[1])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
@@ -285,47 +303,52 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     for (int p = kstart; p <= min(kstart + 2, pmax); ++p) {
-        fetch(p);
+        fetch();
         stage(p);
     }
-    if (kstart + 3 <= pmax) fetch(kstart + 3);
+    if (kstart + 3 <= pmax) fetch();
     float wn = 0.0f, dn = 0.0f;
     if (ecol && kstart < nz) {
-        wn = __ldg(P.w + e0 + kstart * elayer);
-        if (S) dn = __ldg(P.d + e0 + kstart * elayer);
+        wn = __ldg(wp);
+        if (S) dn = __ldg(dp);
     }
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    const uint32_t stg_a = smem_addr(stg), b_a = smem_addr(sB);
+    // descriptor words: start address / 16 in bits 0-13 of the low word, LBO / 16 in bits 16-29; SBO / 16
+    // in bits 0-13 of the high word and the version (bit 46) in its bit 14. A: LBO 16, SBO 144; B: LBO
+    // 128, SBO 1024. Offsets below are in 16-byte units.
+    const uint32_t aLo = (smem_addr(stg) >> 4) | (1u << 16), bLo = (smem_addr(sB) >> 4) | (8u << 16);
+    constexpr uint32_t aHi = 9u | (1u << 14), bHi = 64u | (1u << 14);
+    const bool three = P.terms == 3;
+    const uint32_t mbar0 = smem_addr(&mbar[0]);
 
-    // the MMAs of layer k (node planes k and k + 1) into accumulator buffer buf
+    // the MMAs of MMA half h (element rows 4h .. 4h + 3) of layer k (node planes k and k + 1) into
+    // accumulator buffer buf; the two halves are issued by thread 0 of warps 0 and 4, each of which
+    // commits its own MMAs to the buffer's mbarrier (two arrivals per phase)
+    const int my_half = t == 0 ? 0 : (t == 128 ? 1 : -1);
     auto issue = [&](int k, int buf) {
         tc_fence_after();
+        const uint32_t r0 = uint32_t(k & (RING - 1)) * PL, r1 = uint32_t((k + 1) & (RING - 1)) * PL;
+        const int h = my_half;
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
+        for (int v = 0; v < NV; ++v) {
                 const uint32_t dt = tmem + uint32_t(((buf * 2 + h) * NV + v) * 32);
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {
-                    const int ay = s & 1, az = s >> 1;
-                    const int r = (k + az) % RING;
-                    const uint32_t ahi = stg_a + uint32_t(((v * RING + r) * 2) * SLOTS * 16) +
-                                         uint32_t((4 * h + ay) * SEG * 9 * 16);
-                    const uint32_t alo = ahi + uint32_t(SLOTS * 16);
-                    const uint32_t bhi = b_a + uint32_t(s * 256), blo = bhi + uint32_t(BFLOATS * 4);
-                    tc_mma(dt, tc_desc(ahi, 16, 144), tc_desc(bhi, 128, 1024), s > 0 ? 1u : 0u);
-                    tc_mma(dt, tc_desc(alo, 16, 144), tc_desc(bhi, 128, 1024), 1u);
-                    if (P.terms == 3) tc_mma(dt, tc_desc(ahi, 16, 144), tc_desc(blo, 128, 1024), 1u);
+                    const uint32_t a = aLo + (s >> 1 ? r1 : r0) + uint32_t(v * RING * PL + (4 * h + (s & 1)) * SEG * 9);
+                    const uint32_t b = bLo + uint32_t(s * 16);
+                    tc_mma(dt, pack_desc(a, aHi), pack_desc(b, bHi), s > 0 ? 1u : 0u);
+                    tc_mma(dt, pack_desc(a + SLOTS, aHi), pack_desc(b, bHi), 1u);
+                    if (three) tc_mma(dt, pack_desc(a, aHi), pack_desc(b + 256, bHi), 1u);
                 }
-            }
-        tc_commit(&mbar[buf]);
+        }
+        tc_commit(mbar0 + 8u * uint32_t(buf));
     };
 
-    if (t == 0) issue(kstart, 0);
+    if (my_half >= 0) issue(kstart, 0);
     uint32_t ph = 0;   // bit b: parity of the next completion of mbar[b]
     bool ok = true;
     // top face of the previous layer (corners 4..7 become corners 0..3 of the plane above)
@@ -335,35 +358,40 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) carry[a][c] = 0.0f;
     int64_t d0 = 3 * (I + int64_t(nx + 1) * (J + int64_t(ny + 1) * kz0));
-    const uint32_t lrow = uint32_t(32 * (wid & 3)) << 16;
+    const uint32_t lrow = tmem + (uint32_t(32 * (wid & 3)) << 16) + uint32_t((wid >> 2) * NV * 32);
 
     for (int k = kstart; k < kz1; ++k) {
         const int buf = (k - kstart) & 1;
         const bool layer = k < nz;
-        if (t == 0 && k + 1 < kz1 && k + 1 < nz) issue(k + 1, buf ^ 1);
+        if (my_half >= 0 && k + 1 < kz1 && k + 1 < nz) issue(k + 1, buf ^ 1);
         const float we = wn, de = dn;
         if (ecol && k + 1 < nz && k + 1 < kz1) {
-            wn = __ldg(P.w + e0 + (k + 1) * elayer);
-            if (S) dn = __ldg(P.d + e0 + (k + 1) * elayer);
+            wp += elayer;
+            wn = __ldg(wp);
+            if (S) {
+                dp += elayer;
+                dn = __ldg(dp);
+            }
         }
         float bot[4][3];
         if (layer) {
-            if (!mbar_wait(&mbar[buf], (ph >> buf) & 1u)) ok = false;
+            if (!mbar_wait(mbar0 + 8u * uint32_t(buf), (ph >> buf) & 1u)) ok = false;
             ph ^= 1u << buf;
-            __syncwarp();   // the tensor-memory loads are warp-wide (thread 0 may come from issuing)
+            __syncwarp();   // the tensor-memory loads are warp-wide (lane 0 may come from issuing)
             tc_fence_after();
+            const uint32_t col = lrow + uint32_t(buf * 2 * NV * 32);
             float D[32];
-            tmem_ld32(tmem + lrow + uint32_t(((buf * 2 + (wid >> 2)) * NV) * 32), D);
+            tmem_ld32(col, D);
             float yv[32];
             if (S) {
                 // t_e = d_e (u_e . K_e x_e - x_alpha), u_e from the staged u (hi + lo is exact)
+                const float4* u0 = stg + RING * PL + (k & (RING - 1)) * PL + eslot;
+                const float4* u1 = stg + RING * PL + ((k + 1) & (RING - 1)) * PL + eslot;
                 float dot = 0.0f;
 #pragma unroll
                 for (int a = 0; a < 8; ++a) {
-                    const int r = (k + (a >> 2)) % RING;
-                    const int sl = eslot + ((a >> 1) & 1) * SEG * 9 + (a & 1);
-                    const float4 h = stg[((RING + r) * 2 + 0) * SLOTS + sl];
-                    const float4 l = stg[((RING + r) * 2 + 1) * SLOTS + sl];
+                    const float4* up = ((a >> 2) ? u1 : u0) + ((a >> 1) & 1) * SEG * 9 + (a & 1);
+                    const float4 h = up[0], l = up[SLOTS];
                     dot = fmaf(h.x + l.x, D[4 * a], dot);
                     dot = fmaf(h.y + l.y, D[4 * a + 1], dot);
                     dot = fmaf(h.z + l.z, D[4 * a + 2], dot);
@@ -371,7 +399,7 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
                 const float te = de * (ks * dot - xa);
                 if (designated && k + 1 >= kz0 && k + 1 < kz1) paT -= te;   // counted where its top plane is owned
                 float Du[32];
-                tmem_ld32(tmem + lrow + uint32_t(((buf * 2 + (wid >> 2)) * NV + 1) * 32), Du);
+                tmem_ld32(col + 32u, Du);
                 const float wk = we * ks, tk = te * ks;
 #pragma unroll
                 for (int i = 0; i < 32; ++i) yv[i] = fmaf(wk, D[i], tk * Du[i]);
@@ -398,14 +426,14 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
         }
         // the owner's own x on plane k: staged (masked) unless the node is supported
         float xo[3] = {0.0f, 0.0f, 0.0f};
-        const bool ofixed = (obits >> (k == 0 ? 1 : 0)) & 1;
+        const bool ofixed = k == 0 ? ofix0 : ofix1;
         if (owner && k >= kz0) {
             if (ofixed) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) xo[c] = __ldg(P.x + d0 + c);
             } else {
-                const int r = k % RING;
-                const float4 h = stg[(r * 2 + 0) * SLOTS + oslot], l = stg[(r * 2 + 1) * SLOTS + oslot];
+                const float4* op = stg + (k & (RING - 1)) * PL + oslot;
+                const float4 h = op[0], l = op[SLOTS];
                 xo[0] = h.x + l.x;
                 xo[1] = h.y + l.y;
                 xo[2] = h.z + l.z;
@@ -423,15 +451,15 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
             stage(k + 3);
             fence_async_smem();
         }
-        if (k + 4 <= pmax) fetch(k + 4);
-        if (k >= kz0) sq[(buf * EYT + ly) * EXT + lx] = make_float4(n1[0], n1[1], n1[2], 0.0f);
+        if (k + 4 <= pmax) fetch();
+        if (k >= kz0) sq_w[buf * EYT * EXT] = make_float4(n1[0], n1[1], n1[2], 0.0f);
         if (!ok) s_abort = 1;
         tc_fence_before();
         __syncthreads();
         if (s_abort) break;
         if (k < kz0) continue;
         if (owner) {
-            const float4 o = sq[(buf * EYT + ly - 1) * EXT + lx];
+            const float4 o = sq_r[buf * EYT * EXT];
             float s3[3] = {n0[0] + o.x, n0[1] + o.y, n0[2] + o.z};
             if (ofixed) {
                 s3[0] = xo[0];
@@ -441,10 +469,10 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 float o3;
-                if (P.mode == EPI_APPLY) {
+                if (mode == EPI_APPLY) {
                     o3 = s3[c];
                     if (want_dot) pdT += o3 * xo[c];
-                } else if (P.mode == EPI_RESID) {
+                } else if (mode == EPI_RESID) {
                     o3 = __ldg(P.b + d0 + c) - s3[c];
                     if (want_dot) pdT += o3 * o3;
                 } else {
@@ -462,8 +490,8 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
     // waited for (bounded) first
     if (s_abort) {
         if (wid == 0) {
-            mbar_wait(&mbar[0], ph & 1u);
-            mbar_wait(&mbar[1], (ph >> 1) & 1u);
+            mbar_wait(mbar0, ph & 1u);
+            mbar_wait(mbar0 + 8u, (ph >> 1) & 1u);
         }
         __syncthreads();
     }
@@ -506,10 +534,10 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
     if (P.with_alpha) {
         const int64_t n = P.n;
         double o;
-        if (P.mode == EPI_APPLY) {
+        if (mode == EPI_APPLY) {
             o = sa;
             sd += o * double(xa);
-        } else if (P.mode == EPI_RESID) {
+        } else if (mode == EPI_RESID) {
             o = double(P.b[n]) - sa;
             sd += o * o;
         } else {
