@@ -204,6 +204,33 @@ def apply_K_elementwise(g: Grid, w: np.ndarray, Ke: np.ndarray, x: np.ndarray) -
     return np.where(fixed, x, y)
 
 
+def apply_K_at_nodes(g: Grid, w: np.ndarray, Ke: np.ndarray, x: np.ndarray, nodes: np.ndarray) -> np.ndarray:
+    """Rows of y = K(w) x at the given node ids, shape (len(nodes), 3), each summed from the at most 8 elements
+    around its node: the node is local corner a of element e, and y_node = sum_e w_e (K_e x_e)[3a : 3a + 3] with
+    supported dofs of x zeroed; a supported node keeps y = x. For sampled checks at sizes where the full product
+    is not wanted."""
+    xm = np.where(g.fixed_dofs(), 0.0, x)
+    fixed_n = g.fixed_nodes()
+    off = local_offsets()
+    out = np.zeros((len(nodes), 3))
+    for r, nd in enumerate(np.asarray(nodes, dtype=np.int64)):
+        i = nd % (g.nx + 1)
+        j = (nd // (g.nx + 1)) % (g.ny + 1)
+        k = nd // ((g.nx + 1) * (g.ny + 1))
+        if fixed_n[nd]:
+            out[r] = x[3 * nd:3 * nd + 3]
+            continue
+        for a in range(8):
+            ei, ej, ek = i - off[a, 0], j - off[a, 1], k - off[a, 2]
+            if not (0 <= ei < g.nx and 0 <= ej < g.ny and 0 <= ek < g.nz):
+                continue
+            e = ei + g.nx * (ej + g.ny * ek)
+            xe = np.concatenate([xm[3 * q:3 * q + 3] for q in
+                                 (g.node_id(ei + off[b, 0], ej + off[b, 1], ek + off[b, 2]) for b in range(8))])
+            out[r] += w[e] * (Ke[3 * a:3 * a + 3] @ xe)
+    return out
+
+
 def element_energies(g: Grid, Ke: np.ndarray, u: np.ndarray, v: np.ndarray | None = None) -> np.ndarray:
     """Per-element bilinear forms  u_e^T K_e v_e  (v = u if omitted); u, v full-length nodal vectors."""
     dofs = g.elem_dofs()

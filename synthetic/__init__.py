@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = [
     "Workload", "WORKLOADS", "BATCH_WORKLOADS", "load_vector", "density_uniform_rescaled", "density_bumps",
-    "density_for", "synthetic_state", "random_state", "node_count", "dof_count", "elem_count",
+    "density_for", "synthetic_state", "random_state", "smooth_displacement", "node_count", "dof_count", "elem_count",
 ]
 
 
@@ -215,6 +215,28 @@ def synthetic_state(w: Workload, u: np.ndarray) -> dict:
     return dict(u=np.asarray(u, dtype=np.float64), alpha=1.0, nu_lo=np.ones(m), nu_up=np.ones(m),
                 rho=density_for(w), mu_lo=np.ones(m), mu_up=np.ones(m), p=1.0, q_lo=1.0, q_up=1.0,
                 V=w.V, rho_lo=w.rho_lo, rho_up=w.rho_up)
+
+
+def smooth_displacement(nx: int, ny: int, nz: int, seed: int, amplitude: float = 1.0,
+                        fixed_dofs: np.ndarray | None = None) -> np.ndarray:
+    """A seeded smooth nodal field (length 3 (nx+1)(ny+1)(nz+1)): per component the sum of 4 products of
+    low-frequency sines in x, y and z with random wave numbers (1 to 3 half waves across the box), phases and
+    amplitudes, scaled to max |u| = amplitude and zero on `fixed_dofs`."""
+    rng = np.random.default_rng(seed)
+    k, j, i = np.meshgrid(np.arange(nz + 1) / max(nz, 1), np.arange(ny + 1) / max(ny, 1),
+                          np.arange(nx + 1) / max(nx, 1), indexing="ij")
+    u = np.zeros((k.size, 3))
+    for c in range(3):
+        for _ in range(4):
+            fx, fy, fz = rng.integers(1, 4, size=3)
+            px, py, pz = rng.uniform(0.0, 2.0 * np.pi, size=3)
+            u[:, c] += rng.uniform(0.5, 1.0) * (np.sin(np.pi * fx * i + px) * np.sin(np.pi * fy * j + py)
+                                                * np.sin(np.pi * fz * k + pz)).ravel()
+    u = u.ravel()
+    u *= amplitude / np.abs(u).max()
+    if fixed_dofs is not None:
+        u[fixed_dofs] = 0.0
+    return u
 
 
 def random_state(nx: int, ny: int, nz: int, seed: int, u_scale: float = 1.0, p: float = 1.0, q: float = 1.0,

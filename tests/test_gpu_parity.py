@@ -607,6 +607,72 @@ def test_full_size_cant64_apply_and_solve_residual(pkg):
 
 
 # ------------------------------------------------------------------------------------------------
+# full sizes of the mixed-precision workload (128 x 64 x 64 bridge) and of the large one (256 x 128 x 128)
+# ------------------------------------------------------------------------------------------------
+def test_full_size_bridge128_mixed_applies_and_solve(pkg):
+    """The mixed-precision workload at its full size (1.6 M dofs, 6 levels) in the configuration the bench
+    times: K and S applies in FP64 and with the autotuned FP32 plan against the oracle's matrix-free products on
+    every row, and the mixed S solve to 1e-8 checked by the oracle's residual. The Newton state's displacement is
+    a seeded smooth field (no input comes from the GPU path)."""
+    w = synthetic.WORKLOADS["bridge128"]
+    g = fem.Grid(w.nx, w.ny, w.nz, w.bc)
+    rho = synthetic.density_for(w)
+    f = synthetic.load_vector(w.nx, w.ny, w.nz, w.loads[0])
+    G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision="mixed")
+    G.set_density(dev(rho))
+    Ke = fem.element_stiffness()
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(g.n)
+    assert rel(host(G.apply_K(dev(x))), fem.apply_K_elementwise(g, rho, Ke, x)) < 1e-13
+    G.vcycle("K", dev(f))
+    yk, _ = G.apply_fine_f32("K", "apply", dev(x, torch.float32))
+    assert rel(host(yk), fem.apply_K_elementwise(g, rho, Ke, _f32(x))) < 2e-6
+    u = synthetic.smooth_displacement(w.nx, w.ny, w.nz, 5, 1.0, g.fixed_dofs())
+    d = synthetic.synthetic_state(w, u)
+    pb = pbm.Problem(g, f, d["V"], d["rho_lo"], d["rho_up"])
+    st = pbm.State.from_dict(d)
+    G.set_state(state_dev(d))
+    cf = pbm.coeffs(pb, st)
+    xs = rng.standard_normal(g.n + 1)
+    assert rel(host(G.apply_S(dev(xs))), pbm.apply_S_elementwise(pb, st, cf, xs)) < 1e-12
+    ys, _ = G.apply_fine_f32("S", "apply", dev(xs, torch.float32))
+    assert rel(host(ys), pbm.apply_S_elementwise(pb, st, cf, _f32(xs))) < 1e-5
+    rhs = pbm.rhs_closed(pb, st, cf)
+    dz, info = G.minres_solve("S", dev(rhs), rtol=1e-8, maxit=2000)
+    assert info["outer"] >= 1
+    r = rhs - pbm.apply_S_elementwise(pb, st, cf, host(dz))
+    assert np.linalg.norm(r) <= 1.01e-8 * np.linalg.norm(rhs)
+
+
+def test_full_size_cant256_K_apply_sampled_rows(pkg):
+    """The K(w) x of the large workload (256 x 128 x 128 cantilever, 12.8 M dofs, 7 levels): FP64, the
+    autotuned FP32 plan the bench times and the tensor-core plan, on 3000 random nodes and the nodes of every
+    face, edge and corner kind, against the oracle's row-by-row product (element weights drawn at random so
+    that every element's weight matters)."""
+    w = synthetic.WORKLOADS["cant256"]
+    g = fem.Grid(w.nx, w.ny, w.nz, w.bc)
+    rng = np.random.default_rng(11)
+    rho = rng.uniform(1e-3, 1.0, g.m)
+    G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision="mixed")
+    G.set_density(dev(rho))
+    G.vcycle("K", dev(synthetic.load_vector(w.nx, w.ny, w.nz, w.loads[0])))
+    x = rng.standard_normal(g.n)
+    X, Y, Z = w.nx, w.ny, w.nz
+    special = [g.node_id(i, j, k) for i in (0, 1, X // 2, X - 1, X) for j in (0, 1, Y // 2, Y - 1, Y)
+               for k in (0, 1, Z // 2, Z - 1, Z)]
+    nodes = np.unique(np.concatenate([rng.integers(0, g.nnode, 3000), special]))
+    Ke = fem.element_stiffness()
+    ref64 = fem.apply_K_at_nodes(g, rho, Ke, x, nodes)
+    assert rel(host(G.apply_K(dev(x))).reshape(-1, 3)[nodes], ref64) < 1e-13
+    ref32 = fem.apply_K_at_nodes(g, rho, Ke, _f32(x), nodes)
+    auto = G.info()["fp32_tile"][0][4]
+    for plan in (auto, pkg.fp32_tc_plan()):
+        G.set_fp32_plan("K", plan)
+        y, _ = G.apply_fine_f32("K", "apply", dev(x, torch.float32))
+        assert rel(host(y).reshape(-1, 3)[nodes], ref32) < 2e-6, plan
+
+
+# ------------------------------------------------------------------------------------------------
 # Algorithm 1 (PBM outer loop) on the GPU
 # ------------------------------------------------------------------------------------------------
 def _pbm_gpu_state(G, pb):

@@ -168,6 +168,22 @@ def test_K_symmetric_pd_sparsity_and_matrix_free(bc):
     assert np.allclose(fem.apply_K_elementwise(g, w, Ke, x), K @ x, rtol=1e-13, atol=1e-13)
 
 
+@pytest.mark.parametrize("bc", ["cantilever", "bridge_corners", "bridge_edges"])
+def test_rows_at_nodes_equal_assembled_rows(bc):
+    """The row-by-row product used for sampled checks at full size equals the rows of the assembled K(w) x (the
+    plain definition), on every node of a small grid: interior, faces, edges, corners and supported nodes."""
+    g = fem.Grid(5, 3, 2, bc)
+    rng = np.random.default_rng(4)
+    w = rng.uniform(1e-3, 1.0, g.m)
+    Ke = fem.element_stiffness()
+    x = rng.standard_normal(g.n)
+    ref = (fem.assemble_K(g, w, Ke) @ x).reshape(-1, 3)
+    nodes = np.arange(g.nnode)
+    assert np.allclose(fem.apply_K_at_nodes(g, w, Ke, x, nodes), ref, rtol=1e-13, atol=1e-13)
+    sub = rng.permutation(g.nnode)[:17]
+    assert np.allclose(fem.apply_K_at_nodes(g, w, Ke, x, sub), ref[sub], rtol=1e-13, atol=1e-13)
+
+
 def test_compliance_identity():
     """At equilibrium f^T u = u^T K(rho) u (eq. (1) with K(rho) u = f)."""
     g = fem.Grid(8, 4, 4, "cantilever")
