@@ -78,6 +78,14 @@ enum pbm_epilogue {        /* what a fused operator launch writes (pbm_apply_fin
     PBM_EPI_JACOBI = 2     /* y = x + omega D^{-1} (b - A x), one damped-Jacobi sweep             */
 };
 
+enum pbm_smoother {        /* smoothing of the multigrid V-cycle (Section 5.2; the paper uses Gauss-Seidel) */
+    PBM_SMOOTHER_JACOBI = 0,    /* damped Jacobi x += omega_k D^{-1} (b - A x), omega_k = theta / lambda_k */
+    PBM_SMOOTHER_CHEBYSHEV = 1  /* Chebyshev acceleration of Jacobi (Saad, Iterative Methods, Alg. 12.1) on
+                                   the interval [0.1, 1.1] lambda_k of D^{-1} A: each pass of nu steps damps
+                                   that interval by the Chebyshev polynomial of degree nu; same operator
+                                   applications per step as a Jacobi sweep                              */
+};
+
 typedef struct pbm_grid_desc {
     int nx, ny, nz;        /* fine elements per direction, >= 1                                   */
     int levels;            /* multigrid levels >= 1; nx, ny, nz divisible by 2^(levels-1)       */
@@ -85,12 +93,14 @@ typedef struct pbm_grid_desc {
     int precision;         /* enum pbm_precision                                                 */
     double E, nu;          /* isotropic material, E > 0, -1 < nu < 0.5                          */
     double h;              /* fine element edge > 0                                             */
-    int pre_sweeps;        /* damped-Jacobi sweeps before / after the coarse correction          */
+    int pre_sweeps;        /* smoothing steps before / after the coarse correction (Chebyshev:
+                              at most 9 each)                                                    */
     int post_sweeps;
     double jacobi_theta;   /* Jacobi weight on level k is theta / lambda_k (lambda_k: Lanczos
                               estimate of lambda_max(D_k^{-1} A_k)); 0 < theta < 2               */
     int lanczos_steps;     /* Lanczos steps of that estimate, 2..64                              */
     double inner_rtol;     /* PBM_MIXED: relative tolerance of each inner (FP32) MINRES solve    */
+    int smoother;          /* enum pbm_smoother                                                   */
 } pbm_grid_desc;
 
 typedef struct pbm_grid_info {
@@ -260,10 +270,11 @@ int pbm_apply_S(pbm_grid* g, const double* x_dev, double* y_dev, void* stream);
  * eq. (lagr_grad_a) at the state (res_1 on free dofs), which synchronises `stream`. */
 int pbm_reduced_rhs(pbm_grid* g, const double* f_dev, double* rhs_dev, double* norms_host, void* stream);
 
-/* x = M^{-1} b: one V-cycle (Section 5.1; correction scheme, damped-Jacobi smoothing, restriction
- * P^T, 27-point prolongation, identity transfer of alpha, exact coarsest solve) for the operator
- * `op`. Vectors have n + 1 entries for PBM_OP_S and n for PBM_OP_K. For PBM_OP_K the K(rho)
- * hierarchy is built first if stale (synchronises `stream`). */
+/* x = M^{-1} b: one V-cycle (Section 5.1; correction scheme, the grid's smoothing (damped Jacobi or
+ * Chebyshev, pbm_grid_desc.smoother), restriction P^T, 27-point prolongation, identity transfer of
+ * alpha, exact coarsest solve) for the operator `op`; in FP32 on PBM_MIXED grids (b and x are cast).
+ * Vectors have n + 1 entries for PBM_OP_S and n for PBM_OP_K. For PBM_OP_K the K(rho) hierarchy is
+ * built first if stale (synchronises `stream`). */
 int pbm_vcycle(pbm_grid* g, int op, const double* b_dev, double* x_dev, void* stream);
 
 /* Solves A x = b, A = K(rho) or S, by MINRES preconditioned with one V-cycle (Section 5) until the

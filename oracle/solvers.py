@@ -13,6 +13,11 @@
                     steps on D_k^{-1/2} A_k D_k^{-1/2} from the normalised all-ones vector; theta = 1.2 restates the
                     weight 0.6 relative to the Jacobi stability limit 2 / lambda_max (a fixed 0.6 makes the V-cycle
                     indefinite on these operators, whose lambda_max(D^-1 A) is 3 to 13).
+                    The Chebyshev variant (`smoother="chebyshev"`) replaces each smoothing pass of nu steps by nu
+                    steps of Chebyshev acceleration of the Jacobi iteration (Saad, "Iterative Methods for Sparse
+                    Linear Systems", Algorithm 12.1) on the interval [0.1, 1.1] lambda_k, which damps the upper
+                    part of the spectrum of D_k^{-1} A_k; the interval is a reading (the paper smooths with
+                    Gauss-Seidel and names no polynomial smoother).
   * `direct_solve`— sparse LU (scipy SuperLU) or dense solve.
 """
 from __future__ import annotations
@@ -134,7 +139,11 @@ class Hierarchy:
     """Galerkin hierarchy on CSR matrices. Level 0 is the finest."""
 
     def __init__(self, grid: fem.Grid, A: sp.spmatrix, levels: int, has_alpha: bool, omega: float | None = None,
-                 sweeps: int = 2, post_sweeps: int | None = None, theta: float = 1.2, lanczos_steps: int = 10):
+                 sweeps: int = 2, post_sweeps: int | None = None, theta: float = 1.2, lanczos_steps: int = 10,
+                 smoother: str = "jacobi"):
+        if smoother not in ("jacobi", "chebyshev"):
+            raise ValueError(smoother)
+        self.smoother = smoother
         self.nu1 = sweeps
         self.nu2 = sweeps if post_sweeps is None else post_sweeps
         self.has_alpha = has_alpha
@@ -156,23 +165,53 @@ class Hierarchy:
             self.A.append(Ac)
             self.grids.append(gc)
         self.D = [Ak.diagonal() for Ak in self.A]
-        if omega is None:
+        if omega is None or smoother == "chebyshev":
             self.lmax = [lanczos_lmax(Ak, Dk, lanczos_steps) for Ak, Dk in zip(self.A[:-1], self.D[:-1])]
+        if omega is None:
             self.omega = [theta / lm for lm in self.lmax]
         else:
             self.omega = [omega] * (len(self.A) - 1)
+        if smoother == "chebyshev":
+            # eigenvalue interval [lo, hi] of D^-1 A that the polynomial damps: centre and half width
+            self.cheb = [((0.1 * lm + 1.1 * lm) / 2.0, (1.1 * lm - 0.1 * lm) / 2.0) for lm in self.lmax]
         self.coarse_chol = sla.cho_factor(self.A[-1].toarray(), lower=True)
 
     def vcycle(self, b: np.ndarray, k: int = 0) -> np.ndarray:
         if k == len(self.A) - 1:
             return sla.cho_solve(self.coarse_chol, b)
         A, D, w = self.A[k], self.D[k], self.omega[k]
-        x = w * b / D
-        for _ in range(self.nu1 - 1):
-            x = x + w * (b - A @ x) / D
+        if self.smoother == "chebyshev":
+            x = chebyshev_smooth(A, D, b, np.zeros_like(b), *self.cheb[k], self.nu1)
+        else:
+            x = w * b / D
+            for _ in range(self.nu1 - 1):
+                x = x + w * (b - A @ x) / D
         r = b - A @ x
         xc = self.vcycle(self.P[k].T @ r, k + 1)
         x = x + self.P[k] @ xc
+        if self.smoother == "chebyshev":
+            return chebyshev_smooth(A, D, b, x, *self.cheb[k], self.nu2)
         for _ in range(self.nu2):
             x = x + w * (b - A @ x) / D
         return x
+
+
+def chebyshev_smooth(A, D: np.ndarray, b: np.ndarray, x: np.ndarray, theta: float, delta: float,
+                     steps: int) -> np.ndarray:
+    """`steps` steps of Chebyshev acceleration of the Jacobi iteration for A x = b from x (Saad, Algorithm 12.1,
+    preconditioner D): the eigenvalues of D^-1 A in [theta - delta, theta + delta] are damped by the Chebyshev
+    polynomial of degree `steps` scaled to 1 at zero."""
+    if steps <= 0:
+        return x
+    sigma = theta / delta
+    rho = 1.0 / sigma
+    r = b - A @ x
+    d = r / D / theta
+    x = x + d
+    for _ in range(steps - 1):
+        r = b - A @ x
+        rho_next = 1.0 / (2.0 * sigma - rho)
+        d = rho_next * rho * d + (2.0 * rho_next / delta) * (r / D)
+        x = x + d
+        rho = rho_next
+    return x

@@ -79,7 +79,7 @@ class Grid:
     def __init__(self, nx: int, ny: int, nz: int, levels: int, support: str = "cantilever",
                  precision: str = "fp64", E: float = 1.0, nu: float = 0.3, h: float = 1.0, pre_sweeps: int = 2,
                  post_sweeps: int = 2, jacobi_theta: float = 1.2, lanczos_steps: int = 10,
-                 inner_rtol: float = 1e-4):
+                 inner_rtol: float = 1e-4, smoother: str = "jacobi"):
         self._L = lib()
         d = _lib.GridDesc()
         self._check(self._L.pbm_default_desc(C.byref(d), nx, ny, nz, levels, _lib.SUPPORTS[support]))
@@ -87,6 +87,7 @@ class Grid:
         d.E, d.nu, d.h = E, nu, h
         d.pre_sweeps, d.post_sweeps = pre_sweeps, post_sweeps
         d.jacobi_theta, d.lanczos_steps, d.inner_rtol = jacobi_theta, lanczos_steps, inner_rtol
+        d.smoother = _lib.SMOOTHERS[smoother]
         self.desc = d
         h_ = C.c_void_p()
         self._h = None

@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "PBM_OK", -1: "PBM_EINVAL", -2: "PBM_ENOMEM", -3: "PBM_ECUDA"
                 -9: "PBM_ESTATE"}
 SUPPORTS = {"cantilever": 0, "bridge_corners": 1, "bridge_edges": 2, "free": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+SMOOTHERS = {"jacobi": 0, "chebyshev": 1}
 OPS = {"K": 0, "S": 1}
 EPILOGUES = {"apply": 0, "resid": 1, "jacobi": 2}
 MAPS = {"fixed_dofs": 0, "elem_nodes": 1, "prolong": 2, "Ke": 3}
@@ -30,7 +31,7 @@ class GridDesc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("levels", C.c_int), ("support", C.c_int),
                 ("precision", C.c_int), ("E", C.c_double), ("nu", C.c_double), ("h", C.c_double),
                 ("pre_sweeps", C.c_int), ("post_sweeps", C.c_int), ("jacobi_theta", C.c_double),
-                ("lanczos_steps", C.c_int), ("inner_rtol", C.c_double)]
+                ("lanczos_steps", C.c_int), ("inner_rtol", C.c_double), ("smoother", C.c_int)]
 
 
 class GridInfo(C.Structure):

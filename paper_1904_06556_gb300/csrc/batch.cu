@@ -311,6 +311,12 @@ struct Gen {
             oth[j] = (cur[j] == x) ? t : x;
         }
         auto om = [&](int s) { return (const double*)&b->g[s]->sc->mr[16 + k]; };
+        // Chebyshev smoothing (the batch's grids share the smoother): step sw >= 1 of a pass is EPI_CHEB
+        const bool cheb = b->g[ss[0]]->desc.smoother == PBM_SMOOTHER_CHEBYSHEV;
+        auto coef = [&](int s, int sw, bool pre_pass) {
+            return (cheb && sw >= 1) ? (const double*)&b->g[s]->sc->cheb[k][cheb_slot(sw, pre_pass && sw == 1)] : om(s);
+        };
+        const int mode_cheb = EPI_CHEB;
         if (pre >= 1) {
             if (!first_done) {
                 std::vector<VecArgs<T>> va(ss.size());
@@ -334,8 +340,8 @@ struct Gen {
                     a.y = oth[j];
                     a.b = in[is[j]];
                     a.diag = lv(ss[j], k, 'd');
-                    a.omega = om(ss[j]);
-                    a.mode = EPI_JACOBI;
+                    a.omega = coef(ss[j], sw, true);
+                    a.mode = cheb ? mode_cheb : EPI_JACOBI;
                     a.dot_slot = -1;
                     aa[j] = a;
                 }
@@ -393,8 +399,8 @@ struct Gen {
                 a.y = oth[j];
                 a.b = in[is[j]];
                 a.diag = lv(ss[j], k, 'd');
-                a.omega = om(ss[j]);
-                a.mode = EPI_JACOBI;
+                a.omega = coef(ss[j], sw, false);
+                a.mode = (cheb && sw >= 1) ? mode_cheb : EPI_JACOBI;
                 a.dot_slot = (sw == post - 1) ? dot_slot : -1;
                 aa[j] = a;
             }
@@ -685,7 +691,8 @@ int pbm_batch_create(pbm_grid* const* grids, int n, int op, pbm_batch** out) {
             if (g->device != b->device) fail(PBM_EINVAL, "all grids of a batch must live on one device");
             if ((g->desc.precision == PBM_MIXED) != b->mixed) fail(PBM_EINVAL, "all grids of a batch need one precision");
             if (g->desc.pre_sweeps < 1) fail(PBM_EINVAL, "batched V-cycles need at least one pre-smoothing sweep");
-            if (g->desc.pre_sweeps != grids[0]->desc.pre_sweeps || g->desc.post_sweeps != grids[0]->desc.post_sweeps)
+            if (g->desc.pre_sweeps != grids[0]->desc.pre_sweeps || g->desc.post_sweeps != grids[0]->desc.post_sweeps ||
+                g->desc.smoother != grids[0]->desc.smoother)
                 fail(PBM_EINVAL, "all grids of a batch need the same smoothing sweeps");
             if (g->prof_on) fail(PBM_EINVAL, "profiling must be off for batched solves");
             for (int t = 0; t < s; ++t)

@@ -223,6 +223,7 @@ int pbm_default_desc(pbm_grid_desc* d, int nx, int ny, int nz, int levels, int s
     d->jacobi_theta = 1.2;
     d->lanczos_steps = 10;
     d->inner_rtol = 1e-4;
+    d->smoother = PBM_SMOOTHER_JACOBI;
     set_error("");
     return PBM_OK;
 }
@@ -243,6 +244,9 @@ int pbm_create_grid(const pbm_grid_desc* d, pbm_grid** out) {
         d->post_sweeps > 64)
         fail(PBM_EINVAL, "sweeps must be in 0..64, at least one in total");
     if (!(d->jacobi_theta > 0.0 && d->jacobi_theta < 2.0)) fail(PBM_EINVAL, "jacobi_theta must be in (0, 2)");
+    if (d->smoother != PBM_SMOOTHER_JACOBI && d->smoother != PBM_SMOOTHER_CHEBYSHEV) fail(PBM_EINVAL, "unknown smoother");
+    if (d->smoother == PBM_SMOOTHER_CHEBYSHEV && (d->pre_sweeps > kChebMaxStep + 1 || d->post_sweeps > kChebMaxStep + 1))
+        fail(PBM_EINVAL, "Chebyshev smoothing takes at most 9 steps per pass");
     if (d->lanczos_steps < 2 || d->lanczos_steps > 64) fail(PBM_EINVAL, "lanczos_steps must be in 2..64");
     if (d->precision == PBM_MIXED && !(d->inner_rtol > 0.0 && d->inner_rtol < 1.0))
         fail(PBM_EINVAL, "inner_rtol must be in (0, 1)");

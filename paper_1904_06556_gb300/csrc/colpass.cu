@@ -287,6 +287,10 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
     const T xa = P.with_alpha ? P.x[P.n] : T(0);
     const double om = P.mode == EPI_JACOBI ? *P.omega : 0.0;
     const T omT = T(om);
+    // Chebyshev step coefficients (EPI_CHEB)
+    const double c0 = P.mode == EPI_CHEB ? P.omega[0] : 0.0, c1 = P.mode == EPI_CHEB ? P.omega[1] : 0.0;
+    const double c2 = P.mode == EPI_CHEB ? P.omega[2] : 0.0;
+    const T c0T = T(c0), c1T = T(c1), c2T = T(c2);
     // per-thread partial sums in the vector type (no FP64 work per entry in the FP32 kernels), the
     // dot product only when the launch asks for it
     const bool want_dot = P.dot_slot >= 0;
@@ -340,9 +344,14 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
             } else if (P.mode == EPI_RESID) {
                 o = P.b[d0 + c] - s[c];
                 if (want_dot) pdT += o * o;
-            } else {
+            } else if (P.mode == EPI_JACOBI) {
                 const T bb = P.b[d0 + c];
                 o = xo[c] + omT * ((bb - s[c]) * P.idiag[d0 + c]);
+                if (want_dot) pdT += o * bb;
+            } else {
+                const T bb = P.b[d0 + c];
+                o = c0T * xo[c] + c2T * ((bb - s[c]) * P.idiag[d0 + c]);
+                if (c1 != 0.0) o -= c1T * P.y[d0 + c];
                 if (want_dot) pdT += o * bb;
             }
             P.y[d0 + c] = o;
@@ -388,9 +397,14 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
         } else if (P.mode == EPI_RESID) {
             o = double(P.b[n]) - ya;
             sd += o * o;
-        } else {
+        } else if (P.mode == EPI_JACOBI) {
             const double bb = double(P.b[n]);
             o = double(xa) + om * ((bb - ya) * double(P.idiag[n]));
+            sd += o * bb;
+        } else {
+            const double bb = double(P.b[n]);
+            o = c0 * double(xa) + c2 * ((bb - ya) * double(P.idiag[n]));
+            if (c1 != 0.0) o -= c1 * double(P.y[n]);
             sd += o * bb;
         }
         P.y[n] = T(o);

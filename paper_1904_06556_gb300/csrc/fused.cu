@@ -217,6 +217,10 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
     const float xa = S ? P.x[P.n] : 0.0f;
     const double om = P.mode == EPI_JACOBI ? *P.omega : 0.0;
     const float omF = float(om);
+    // Chebyshev step coefficients (EPI_CHEB)
+    const double c0 = P.mode == EPI_CHEB ? P.omega[0] : 0.0, c1 = P.mode == EPI_CHEB ? P.omega[1] : 0.0;
+    const double c2 = P.mode == EPI_CHEB ? P.omega[2] : 0.0;
+    const float c0F = float(c0), c1F = float(c1), c2F = float(c2);
     const bool want_dot = P.dot_slot >= 0;
     float pdT = 0.0f, paT = 0.0f;
 
@@ -388,9 +392,14 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
                 } else if (P.mode == EPI_RESID) {
                     o = __ldg(P.b + d0 + c) - s[c];
                     if (want_dot) pdT += o * o;
-                } else {
+                } else if (P.mode == EPI_JACOBI) {
                     const float bb = __ldg(P.b + d0 + c);
                     o = xo[c] + omF * ((bb - s[c]) * __ldg(P.idiag + d0 + c));
+                    if (want_dot) pdT += o * bb;
+                } else {
+                    const float bb = __ldg(P.b + d0 + c);
+                    o = c0F * xo[c] + c2F * ((bb - s[c]) * __ldg(P.idiag + d0 + c));
+                    if (c1 != 0.0) o -= c1F * P.y[d0 + c];
                     if (want_dot) pdT += o * bb;
                 }
                 P.y[d0 + c] = o;
@@ -431,9 +440,14 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
         } else if (P.mode == EPI_RESID) {
             o = double(P.b[n]) - sa;
             sd += o * o;
-        } else {
+        } else if (P.mode == EPI_JACOBI) {
             const double bb = double(P.b[n]);
             o = double(xa) + om * ((bb - sa) * double(P.idiag[n]));
+            sd += o * bb;
+        } else {
+            const double bb = double(P.b[n]);
+            o = c0 * double(xa) + c2 * ((bb - sa) * double(P.idiag[n]));
+            if (c1 != 0.0) o -= c1 * double(P.y[n]);
             sd += o * bb;
         }
         P.y[n] = float(o);
@@ -558,6 +572,10 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
     const float xa = P.with_alpha ? P.x[P.n] : 0.0f;
     const double om = P.mode == EPI_JACOBI ? *P.omega : 0.0;
     const float omF = float(om);
+    // Chebyshev step coefficients (EPI_CHEB)
+    const double c0 = P.mode == EPI_CHEB ? P.omega[0] : 0.0, c1 = P.mode == EPI_CHEB ? P.omega[1] : 0.0;
+    const double c2 = P.mode == EPI_CHEB ? P.omega[2] : 0.0;
+    const float c0F = float(c0), c1F = float(c1), c2F = float(c2);
     const bool want_dot = P.dot_slot >= 0;
     float pdT = 0.0f, paT = 0.0f;
 
@@ -642,9 +660,14 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
                 } else if (P.mode == EPI_RESID) {
                     o = __ldg(P.b + d0 + c) - s3[c];
                     if (want_dot) pdT += o * o;
-                } else {
+                } else if (P.mode == EPI_JACOBI) {
                     const float bb = __ldg(P.b + d0 + c);
                     o = xo[c] + omF * ((bb - s3[c]) * __ldg(P.idiag + d0 + c));
+                    if (want_dot) pdT += o * bb;
+                } else {
+                    const float bb = __ldg(P.b + d0 + c);
+                    o = c0F * xo[c] + c2F * ((bb - s3[c]) * __ldg(P.idiag + d0 + c));
+                    if (c1 != 0.0) o -= c1F * P.y[d0 + c];
                     if (want_dot) pdT += o * bb;
                 }
                 P.y[d0 + c] = o;
@@ -684,9 +707,14 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
         } else if (P.mode == EPI_RESID) {
             o = double(P.b[n]) - ya;
             sd += o * o;
-        } else {
+        } else if (P.mode == EPI_JACOBI) {
             const double bb = double(P.b[n]);
             o = double(xa) + om * ((bb - ya) * double(P.idiag[n]));
+            sd += o * bb;
+        } else {
+            const double bb = double(P.b[n]);
+            o = c0 * double(xa) + c2 * ((bb - ya) * double(P.idiag[n]));
+            if (c1 != 0.0) o -= c1 * double(P.y[n]);
             sd += o * bb;
         }
         P.y[n] = float(o);

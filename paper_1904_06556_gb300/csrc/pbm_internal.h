@@ -220,6 +220,7 @@ struct DevScalars {
     unsigned int counter[64];  // last-block-done counters (one per reduction slot)
     int flags[8];
     double salpha;         // S_alpha,alpha = sum_i d_i of the current state (coarse S applies)
+    double cheb[16][4 * 2 * 8];   // per level: Chebyshev step coefficients (c0, c1, c2, 0) at cheb_slot
     double ctl[8];         // graph-resident MINRES loop control: target, iteration budget, count, exit
 };
 
@@ -309,7 +310,13 @@ void* dalloc(pbm_grid* g, size_t bytes);
 void dfree(void* p);
 
 // ---- kernels (launch wrappers), apply.cu ----
-enum EpiMode { EPI_APPLY = 0, EPI_RESID = 1, EPI_JACOBI = 2 };
+// EPI_CHEB: one step of Chebyshev acceleration of Jacobi, y = c0 x - c1 y_prev + c2 D^{-1} (b - A x)
+// with (c0, c1, c2) = (1 + a_s, a_s or 0, b_s) read from ApplyArgs::omega, y_prev the iterate before x,
+// read from y itself before it is overwritten (not read when c1 = 0)
+enum EpiMode { EPI_APPLY = 0, EPI_RESID = 1, EPI_JACOBI = 2, EPI_CHEB = 3 };
+// slot of step s >= 1 (from_zero: the step after a first step taken from x = 0) in DevScalars::cheb[k]
+constexpr int kChebMaxStep = 8;
+inline int cheb_slot(int s, bool from_zero) { return 4 * (2 * (s - 1) + (from_zero ? 1 : 0)); }
 
 struct ApplyArgs {
     // input vector (n (+1)), output (n (+1)); b and diag for RESID / JACOBI

@@ -80,10 +80,17 @@ void vcycle(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, void* x, in
     // the last pre-sweep lands in x
     void* cur = (pre % 2 == 1) ? x : t;
     void* oth = (cur == x) ? t : x;
+    // Chebyshev: step s >= 1 of a pass is EPI_CHEB with that step's coefficients; its previous iterate
+    // is the other ping-pong buffer (zero before the pre-smoothing's second step: c1 = 0 there)
+    const bool cheb = g->desc.smoother == PBM_SMOOTHER_CHEBYSHEV;
+    auto step_mode = [&](int s) { return (cheb && s >= 1) ? EPI_CHEB : EPI_JACOBI; };
+    auto step_coef = [&](int s, bool pre_pass) {
+        return (cheb && s >= 1) ? &g->sc->cheb[k][cheb_slot(s, pre_pass && s == 1)] : om;
+    };
     if (pre >= 1) {
         if (!first_done) launch_scale_diag_first(g, k, fp32, b, cur, op_s, st);
         for (int s = 1; s < pre; ++s) {
-            level_apply(g, k, fp32, op_s, args(cur, oth, EPI_JACOBI, b, D, om), st);
+            level_apply(g, k, fp32, op_s, args(cur, oth, step_mode(s), b, D, step_coef(s, true)), st);
             std::swap(cur, oth);
         }
     } else {
@@ -109,7 +116,8 @@ void vcycle(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, void* x, in
     oth = t;
     for (int s = 0; s < post; ++s) {
         const bool last = (s == post - 1);
-        level_apply(g, k, fp32, op_s, args(cur, oth, EPI_JACOBI, b, D, om, last ? dot_slot : -1), st);
+        level_apply(g, k, fp32, op_s, args(cur, oth, step_mode(s), b, D, step_coef(s, false), last ? dot_slot : -1),
+                    st);
         std::swap(cur, oth);
     }
     if (cur != x) PBM_CUDA(cudaMemcpyAsync(x, cur, nv * esz(fp32), cudaMemcpyDeviceToDevice, st));
@@ -201,12 +209,39 @@ static void lanczos_finish(pbm_grid* g, int k) {
     b.resize(a.size() > 0 ? a.size() - 1 : 0);
     L.lambda_max = tridiag_max_eig(a, b);
     if (!(L.lambda_max > 0.0) || !std::isfinite(L.lambda_max)) fail(PBM_ENONFINITE, "Lanczos estimate is not positive");
-    L.omega = g->desc.jacobi_theta / L.lambda_max;
+    if (g->desc.smoother == PBM_SMOOTHER_CHEBYSHEV) {
+        // Chebyshev acceleration on [lo, hi] = [0.1, 1.1] lambda: centre theta, half width delta; the first
+        // step of a pass is a Jacobi step with weight 1 / theta, step s >= 1 takes
+        // x_{s+1} = x_s + a_s (x_s - x_{s-1}) + b_s D^-1 (b - A x_s) with rho_0 = delta / theta,
+        // rho_s = 1 / (2 theta / delta - rho_{s-1}), a_s = rho_s rho_{s-1}, b_s = 2 rho_s / delta
+        const double lo = 0.1 * L.lambda_max, hi = 1.1 * L.lambda_max;
+        const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+        L.omega = 1.0 / theta;
+        double rho = 1.0 / sigma;
+        double* c = g->sc_host->cheb[k];
+        for (int st = 1; st <= kChebMaxStep; ++st) {
+            const double rn = 1.0 / (2.0 * sigma - rho);
+            const double as = rn * rho, bs = 2.0 * rn / delta;
+            for (int z = 0; z < 2; ++z) {
+                double* e = c + cheb_slot(st, z == 1);
+                e[0] = 1.0 + as;
+                e[1] = z == 1 ? 0.0 : as;
+                e[2] = bs;
+                e[3] = 0.0;
+            }
+            rho = rn;
+        }
+    } else {
+        L.omega = g->desc.jacobi_theta / L.lambda_max;
+    }
 }
 
 static void upload_omegas(pbm_grid* g, cudaStream_t st) {
     for (int k = 0; k < g->levels; ++k) g->sc_host->mr[16 + k] = g->L[k].omega;
     PBM_CUDA(cudaMemcpyAsync(&g->sc->mr[16], &g->sc_host->mr[16], sizeof(double) * 16, cudaMemcpyHostToDevice, st));
+    if (g->desc.smoother == PBM_SMOOTHER_CHEBYSHEV)
+        PBM_CUDA(cudaMemcpyAsync(&g->sc->cheb[0][0], &g->sc_host->cheb[0][0], sizeof(g->sc_host->cheb),
+                                 cudaMemcpyHostToDevice, st));
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -285,6 +285,10 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
     const int mode = P.mode;
     const double om = mode == EPI_JACOBI ? *P.omega : 0.0;
     const float omF = float(om);
+    // Chebyshev step coefficients (EPI_CHEB)
+    const double c0 = mode == EPI_CHEB ? P.omega[0] : 0.0, c1 = mode == EPI_CHEB ? P.omega[1] : 0.0;
+    const double c2 = mode == EPI_CHEB ? P.omega[2] : 0.0;
+    const float c0F = float(c0), c1F = float(c1), c2F = float(c2);
     const bool want_dot = P.dot_slot >= 0;
     const float ks = P.kscale;
     float pdT = 0.0f, paT = 0.0f;
@@ -475,9 +479,14 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
                 } else if (mode == EPI_RESID) {
                     o3 = __ldg(P.b + d0 + c) - s3[c];
                     if (want_dot) pdT += o3 * o3;
-                } else {
+                } else if (mode == EPI_JACOBI) {
                     const float bb = __ldg(P.b + d0 + c);
                     o3 = xo[c] + omF * ((bb - s3[c]) * __ldg(P.idiag + d0 + c));
+                    if (want_dot) pdT += o3 * bb;
+                } else {
+                    const float bb = __ldg(P.b + d0 + c);
+                    o3 = c0F * xo[c] + c2F * ((bb - s3[c]) * __ldg(P.idiag + d0 + c));
+                    if (c1 != 0.0) o3 -= c1F * P.y[d0 + c];
                     if (want_dot) pdT += o3 * bb;
                 }
                 P.y[d0 + c] = o3;
@@ -540,9 +549,14 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
         } else if (mode == EPI_RESID) {
             o = double(P.b[n]) - sa;
             sd += o * o;
-        } else {
+        } else if (mode == EPI_JACOBI) {
             const double bb = double(P.b[n]);
             o = double(xa) + om * ((bb - sa) * double(P.idiag[n]));
+            sd += o * bb;
+        } else {
+            const double bb = double(P.b[n]);
+            o = c0 * double(xa) + c2 * ((bb - sa) * double(P.idiag[n]));
+            if (c1 != 0.0) o -= c1 * double(P.y[n]);
             sd += o * bb;
         }
         P.y[n] = float(o);

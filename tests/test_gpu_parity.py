@@ -387,35 +387,87 @@ def test_ip_newton_system_matches_oracle(pkg, dims, bc, levels, precision):
 # ------------------------------------------------------------------------------------------------
 # V-cycle: same hierarchy definition as the oracle (Galerkin, theta / lambda_max Jacobi, exact coarse)
 # ------------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("dims,bc,levels", [((8, 4, 4), "cantilever", 3), ((16, 8, 8), "bridge_corners", 3),
-                                            ((16, 8, 8), "cantilever", 4)])
-def test_vcycle_S_matches_oracle(pkg, dims, bc, levels):
+def _check_smoother_weights(info, h, levels, smoother):
+    if smoother == "jacobi":
+        assert np.allclose(info["omega"][:levels - 1], h.omega, rtol=1e-10)
+    else:   # Lanczos estimates; the first step of a Chebyshev pass has weight 1 / theta = 1 / (0.6 lambda)
+        assert np.allclose(info["lambda_max"][:levels - 1], h.lmax, rtol=1e-10)
+        assert np.allclose(info["omega"][:levels - 1], [1.0 / c[0] for c in h.cheb], rtol=1e-10)
+
+
+@pytest.mark.parametrize("dims,bc,levels,smoother,sweeps", [((8, 4, 4), "cantilever", 3, "jacobi", 2),
+                                                            ((16, 8, 8), "bridge_corners", 3, "jacobi", 2),
+                                                            ((16, 8, 8), "cantilever", 4, "jacobi", 2),
+                                                            ((16, 8, 8), "bridge_corners", 3, "chebyshev", 2),
+                                                            ((16, 8, 8), "cantilever", 4, "chebyshev", 3)])
+def test_vcycle_S_matches_oracle(pkg, dims, bc, levels, smoother, sweeps):
     pb, st, d = make_problem(*dims, bc, 2, 0.4)
-    G = pkg.Grid(*dims, levels, bc)
+    G = pkg.Grid(*dims, levels, bc, smoother=smoother, pre_sweeps=sweeps, post_sweeps=sweeps)
     G.set_state(state_dev(d))
     S = pbm.assemble_S(pb, st)
-    h = solvers.Hierarchy(pb.grid, S, levels, has_alpha=True)
-    info = G.info()
-    assert np.allclose(info["omega"][:levels - 1], h.omega, rtol=1e-10)
+    h = solvers.Hierarchy(pb.grid, S, levels, has_alpha=True, sweeps=sweeps, smoother=smoother)
+    _check_smoother_weights(G.info(), h, levels, smoother)
     b = np.random.default_rng(4).standard_normal(pb.n + 1)
     b[:pb.n][pb.fixed] = 0.0
     x = host(G.vcycle("S", dev(b)))
     assert rel(x, h.vcycle(b)) < 1e-10
 
 
-@pytest.mark.parametrize("dims,bc,levels", [((8, 4, 4), "cantilever", 3), ((16, 8, 8), "bridge_corners", 4)])
-def test_vcycle_K_matches_oracle(pkg, dims, bc, levels):
+@pytest.mark.parametrize("dims,bc,levels,smoother,sweeps", [((8, 4, 4), "cantilever", 3, "jacobi", 2),
+                                                            ((16, 8, 8), "bridge_corners", 4, "jacobi", 2),
+                                                            ((8, 4, 4), "cantilever", 3, "chebyshev", 2),
+                                                            ((16, 8, 8), "bridge_corners", 4, "chebyshev", 3),
+                                                            ((16, 8, 8), "cantilever", 3, "chebyshev", 1)])
+def test_vcycle_K_matches_oracle(pkg, dims, bc, levels, smoother, sweeps):
     g = fem.Grid(*dims, bc)
     rho = synthetic.density_uniform_rescaled(g.m, 0.3, 1)
-    G = pkg.Grid(*dims, levels, bc)
+    G = pkg.Grid(*dims, levels, bc, smoother=smoother, pre_sweeps=sweeps, post_sweeps=sweeps)
     G.set_density(dev(rho))
     K = fem.assemble_K(g, rho, fem.element_stiffness())
-    h = solvers.Hierarchy(g, K, levels, has_alpha=False)
+    h = solvers.Hierarchy(g, K, levels, has_alpha=False, sweeps=sweeps, smoother=smoother)
     b = np.random.default_rng(5).standard_normal(g.n)
     b[g.fixed_dofs()] = 0.0
     x = host(G.vcycle("K", dev(b)))
-    assert np.allclose(G.info()["omega"][:levels - 1], h.omega, rtol=1e-10)
+    _check_smoother_weights(G.info(), h, levels, smoother)
     assert rel(x, h.vcycle(b)) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_vcycle_chebyshev_fp32_and_solves(pkg, precision):
+    """Chebyshev smoothing in both precisions: on mixed grids the FP32 V-cycle (single-pass fine and coarse
+    kernels, Chebyshev epilogue) agrees with the oracle's to FP32 accuracy; the MINRES solves reach the oracle's
+    direct solution; a batch of Chebyshev grids gives the single solves."""
+    dims, bc, levels = (16, 8, 8), "bridge_corners", 3
+    pb, st, d = make_problem(*dims, bc, 1, 0.5)
+    G = pkg.Grid(*dims, levels, bc, precision=precision, smoother="chebyshev")
+    G.set_state(state_dev(d))
+    cf = pbm.coeffs(pb, st)
+    S = pbm.assemble_S(pb, st, cf)
+    h = solvers.Hierarchy(pb.grid, S, levels, has_alpha=True, smoother="chebyshev")
+    b = np.random.default_rng(9).standard_normal(pb.n + 1)
+    b[:pb.n][pb.fixed] = 0.0
+    xv = host(G.vcycle("S", dev(b)))        # FP32 V-cycle on mixed grids
+    assert rel(xv, h.vcycle(b)) < (1e-4 if precision == "mixed" else 1e-10)
+    rhs = pbm.rhs_closed(pb, st, cf)
+    ref = solvers.direct_solve(S, rhs)
+    x, info = G.minres_solve("S", dev(rhs), rtol=1e-10, maxit=400)
+    assert info["relres"] <= 1e-10
+    assert rel(host(x), ref) < 1e-7
+    G2 = pkg.Grid(8, 4, 4, 2, "cantilever", precision=precision, smoother="chebyshev")
+    pb2, st2, d2 = make_problem(8, 4, 4, "cantilever", 3, 0.5)
+    G2.set_state(state_dev(d2))
+    rhs2 = pbm.rhs_closed(pb2, st2, pbm.coeffs(pb2, st2))
+    y1, _ = G.minres_solve("S", dev(rhs), rtol=1e-10, maxit=400)
+    y2, _ = G2.minres_solve("S", dev(rhs2), rtol=1e-10, maxit=400)
+    B = pkg.Batch([G, G2], "S")
+    ys, infos = B.minres_solve([dev(rhs), dev(rhs2)], rtol=1e-10, maxit=400)
+    for y, yb, inf in zip((y1, y2), ys, infos):
+        assert inf["relres"] <= 1e-10
+        if precision == "fp64":
+            assert torch.equal(y, yb)
+        else:
+            assert rel(host(yb), host(y)) < 1e-7
+    B.close()
 
 
 # ------------------------------------------------------------------------------------------------

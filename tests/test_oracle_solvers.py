@@ -74,6 +74,34 @@ def test_vcycle_is_symmetric_positive_definite(levels):
     assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
 
 
+@pytest.mark.parametrize("levels", [2, 3])
+def test_chebyshev_vcycle_is_symmetric_positive_definite(levels):
+    pb, st, S = _S_problem(nx=8, ny=4, nz=4)
+    h = solvers.Hierarchy(pb.grid, S, levels, has_alpha=True, sweeps=2, smoother="chebyshev")
+    M = _vcycle_matrix(h, S.shape[0])
+    assert np.max(np.abs(M - M.T)) < 1e-10 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+
+
+@pytest.mark.parametrize("steps", [1, 2, 3, 5])
+def test_chebyshev_smoother_error_is_scaled_chebyshev_polynomial(steps):
+    """On A = diag(lambda) with D = I, `steps` steps from x0 leave the error p(lambda) (x0 - x*) with
+    p(lambda) = T_steps((theta - lambda) / delta) / T_steps(theta / delta), T the Chebyshev polynomial of the first
+    kind: the defining property of Chebyshev acceleration (the polynomial of least maximum on the interval
+    [theta - delta, theta + delta] among those with p(0) = 1)."""
+    rng = np.random.default_rng(steps)
+    lam = rng.uniform(0.05, 4.0, 40)
+    A = sp.diags(lam)
+    b = rng.standard_normal(40)
+    x0 = rng.standard_normal(40)
+    theta, delta = 2.0, 1.8
+    x = solvers.chebyshev_smooth(A, np.ones(40), b, x0, theta, delta, steps)
+    xs = b / lam
+    T = lambda t: np.polynomial.chebyshev.chebval(t, [0.0] * steps + [1.0])
+    p = T((theta - lam) / delta) / T(theta / delta)
+    assert np.allclose(x - xs, p * (x0 - xs), rtol=1e-11, atol=1e-12)
+
+
 def test_fixed_weight_06_is_indefinite_on_S():
     """Why the Jacobi weight is scaled by lambda_max: with a fixed 0.6, omega * lambda_max(D^-1 S) > 2 and the
     V-cycle loses definiteness, which MINRES reports as a breakdown."""
