@@ -61,8 +61,9 @@ FP64_OPS_PEAK = 2.0 * 152 * 2.07e9
 FALLBACK_HBM_GBS = 6800.0
 
 
-def workload_desc(w, precision):
+def workload_desc(w, precision, smoother="jacobi"):
     return {"workload": f"{w.name}: {w.nx}x{w.ny}x{w.nz} Q1 hex {w.bc}, {precision}, single reduced-Newton solve",
+            "smoother": smoother,
             "grid": [w.nx, w.ny, w.nz], "support": w.bc, "load": w.loads[0], "density": w.density,
             "volume_fraction": w.vf, "levels": w.levels, "rtol": w.rtol, "precision": precision,
             "n_dofs": w.n, "m_elements": w.m,
@@ -224,7 +225,7 @@ def run_ours(args):
         u, uinfo = G64.minres_solve("K", f, rtol=w.rtol, maxit=2000, check=False)
     if not uinfo["relres"] <= 1e-6:
         raise RuntimeError(f"equilibrium solve of the input state failed: {uinfo}")
-    G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=precision)
+    G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=precision, smoother=args.smoother)
     G.set_density(t64(rho))
     st_h = synthetic.synthetic_state(w, np.zeros(w.n))
     sd = {k: t64(st_h[k]) for k in ("nu_lo", "nu_up", "rho", "mu_lo", "mu_up")}
@@ -359,7 +360,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32+f64",
         "data": "synthetic (seeded; shapes of the paper's cantilever example, Section 6)",
-        "config": workload_desc(w, precision),
+        "config": workload_desc(w, precision, args.smoother),
         "solve": {"minres_iterations": iters[-1], "true_relres": relres, "phases_last_step": phases,
                   "mixed_outer_steps": last["info"]["outer"], "fine_chunk": G.info()["fine_chunk"],
                   "fp32_tile_K_S": G.info()["fp32_tile"],
@@ -373,7 +374,7 @@ def run_ours(args):
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w, args.cpu_budget_s)
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_budget_s, args.smoother)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -411,7 +412,7 @@ def run_batch(args):
                 sd = {k: t64(st_h[k]) for k in ("nu_lo", "nu_up", "rho", "mu_lo", "mu_up")}
                 sd["u"] = u
                 sd.update({k: float(st_h[k]) for k in ("alpha", "p", "q_lo", "q_up", "V", "rho_lo", "rho_up")})
-                G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=precision)
+                G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=precision, smoother=args.smoother)
                 grids.append(G)
                 states.append(sd)
                 fs.append(f)
@@ -494,7 +495,7 @@ def run_ip(args):
     with pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision="fp64") as G64:
         G64.set_density(t64(rho))
         u, _ = G64.minres_solve("K", f, rtol=w.rtol, maxit=2000, check=False)
-    G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=args.precision)
+    G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=args.precision, smoother=args.smoother)
     sd = dict(u=u, rho=t64(rho), nu_lo=t64(np.ones(w.m)), nu_up=t64(np.ones(w.m)), alpha=1.0, V=float(rho.sum()),
               rho_lo=w.rho_lo, rho_up=w.rho_up, r=1e-2, s=1e-2)
     stream = torch.cuda.current_stream()
@@ -549,7 +550,7 @@ def run_doc(args):
     f = torch.as_tensor(synthetic.load_vector(w.nx, w.ny, w.nz, w.loads[0]), dtype=torch.float64, device=dev)
 
     def one_run(precision):
-        with pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=precision) as G:
+        with pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=precision, smoother=args.smoother) as G:
             rho = torch.full((w.m,), w.V / w.m, dtype=torch.float64, device=dev)
             u = torch.zeros(w.n, dtype=torch.float64, device=dev)
             torch.cuda.synchronize()
@@ -593,7 +594,7 @@ def run_pbm(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
     def one_run(precision):
-        with pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=precision) as G:
+        with pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=precision, smoother=args.smoother) as G:
             st = G.initial_state(w.n, w.m, w.V, w.rho_lo, w.rho_up, device=dev)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -739,24 +740,24 @@ def oracle_inputs(w):
     return pb, pbm.State.from_dict(d)
 
 
-def oracle_step(w, pb, st):
+def oracle_step(w, pb, st, smoother="jacobi"):
     """One reduced Newton system by the oracle: coefficients, S in CSR, Galerkin hierarchy, rhs, MG-MINRES."""
     from oracle import pbm, solvers
     cf = pbm.coeffs(pb, st)
     S = pbm.assemble_S(pb, st, cf)
     rhs = pbm.rhs_closed(pb, st, cf)
-    h = solvers.Hierarchy(pb.grid, S, w.levels, has_alpha=True)
+    h = solvers.Hierarchy(pb.grid, S, w.levels, has_alpha=True, smoother=smoother)
     r = solvers.minres(lambda v: S @ v, rhs, h.vcycle, rtol=w.rtol, maxit=1000)
     return r
 
 
-def cpu_baseline(w, budget_s):
+def cpu_baseline(w, budget_s, smoother="jacobi"):
     pb, st = oracle_inputs(w)
     times = []
     t_all = time.perf_counter()
     while True:
         t0 = time.perf_counter()
-        r = oracle_step(w, pb, st)
+        r = oracle_step(w, pb, st, smoother)
         times.append(time.perf_counter() - t0)
         if time.perf_counter() - t_all + times[-1] > budget_s or len(times) >= 5:
             break
@@ -777,12 +778,12 @@ def run_reference(args):
     budget = args.cpu_budget_s * 6
     t_start = time.perf_counter()
     for _ in range(min(args.warmup, 1)):
-        oracle_step(w, pb, st)
+        oracle_step(w, pb, st, args.smoother)
     times = []
     r = None
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        r = oracle_step(w, pb, st)
+        r = oracle_step(w, pb, st, args.smoother)
         times.append(time.perf_counter() - t0)
         if time.perf_counter() - t_start + times[-1] > budget:
             break
@@ -792,7 +793,7 @@ def run_reference(args):
            "steps": len(times), "steps_requested": args.steps, "warmup": min(args.warmup, 1),
            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-           "config": workload_desc(w, "fp64"),
+           "config": workload_desc(w, "fp64", args.smoother),
            "solve": {"minres_iterations": r.iters, "true_relres": r.relres},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"{len(times)} complete reduced-Newton systems of the workload by the oracle"},
@@ -815,6 +816,9 @@ def main():
     ap.add_argument("--fp32-plans", action="store_true",
                     help="time every tile plan of the FP32 fine operator on the workload's grid")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--smoother", default="chebyshev", choices=["jacobi", "chebyshev"],
+                    help="V-cycle smoothing: Chebyshev acceleration of Jacobi (default; fewer MINRES iterations "
+                         "for the same operator applications) or damped Jacobi")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=30.0)
     args = ap.parse_args()
