@@ -15,9 +15,10 @@
                     indefinite on these operators, whose lambda_max(D^-1 A) is 3 to 13).
                     The Chebyshev variant (`smoother="chebyshev"`) replaces each smoothing pass of nu steps by nu
                     steps of Chebyshev acceleration of the Jacobi iteration (Saad, "Iterative Methods for Sparse
-                    Linear Systems", Algorithm 12.1) on the interval [0.1, 1.1] lambda_k, which damps the upper
-                    part of the spectrum of D_k^{-1} A_k; the interval is a reading (the paper smooths with
-                    Gauss-Seidel and names no polynomial smoother).
+                    Linear Systems", Algorithm 12.1) on the interval [0.1, 1.4] lambda_k, which damps the upper
+                    part of the spectrum of D_k^{-1} A_k; every eigenvalue up to (0.1 + 1.4) lambda_k is damped, so
+                    the Lanczos estimate from below may be off by a third. The interval is a reading (the paper
+                    smooths with Gauss-Seidel and names no polynomial smoother).
   * `direct_solve`— sparse LU (scipy SuperLU) or dense solve.
 """
 from __future__ import annotations
@@ -173,7 +174,7 @@ class Hierarchy:
             self.omega = [omega] * (len(self.A) - 1)
         if smoother == "chebyshev":
             # eigenvalue interval [lo, hi] of D^-1 A that the polynomial damps: centre and half width
-            self.cheb = [((0.1 * lm + 1.1 * lm) / 2.0, (1.1 * lm - 0.1 * lm) / 2.0) for lm in self.lmax]
+            self.cheb = [((0.1 * lm + 1.4 * lm) / 2.0, (1.4 * lm - 0.1 * lm) / 2.0) for lm in self.lmax]
         self.coarse_chol = sla.cho_factor(self.A[-1].toarray(), lower=True)
 
     def vcycle(self, b: np.ndarray, k: int = 0) -> np.ndarray:

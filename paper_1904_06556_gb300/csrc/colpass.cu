@@ -285,12 +285,16 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
     const unsigned nn = unsigned(P.n / 3);
     const unsigned sx = unsigned(nx + 1), sy = unsigned(ny + 1);
     const T xa = P.with_alpha ? P.x[P.n] : T(0);
-    const double om = P.mode == EPI_JACOBI ? *P.omega : 0.0;
-    const T omT = T(om);
-    // Chebyshev step coefficients (EPI_CHEB)
-    const double c0 = P.mode == EPI_CHEB ? P.omega[0] : 0.0, c1 = P.mode == EPI_CHEB ? P.omega[1] : 0.0;
-    const double c2 = P.mode == EPI_CHEB ? P.omega[2] : 0.0;
-    const T c0T = T(c0), c1T = T(c1), c2T = T(c2);
+    // epilogue weights, converted once and only in their mode
+    T omT = T(0), c0T = T(0), c1T = T(0), c2T = T(0);
+    bool c1nz = false;
+    if (P.mode == EPI_JACOBI) omT = T(*P.omega);
+    if (P.mode == EPI_CHEB) {
+        c0T = T(P.omega[0]);
+        c1T = T(P.omega[1]);
+        c2T = T(P.omega[2]);
+        c1nz = c1T != T(0);
+    }
     // per-thread partial sums in the vector type (no FP64 work per entry in the FP32 kernels), the
     // dot product only when the launch asks for it
     const bool want_dot = P.dot_slot >= 0;
@@ -351,7 +355,7 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
             } else {
                 const T bb = P.b[d0 + c];
                 o = c0T * xo[c] + c2T * ((bb - s[c]) * P.idiag[d0 + c]);
-                if (c1 != 0.0) o -= c1T * P.y[d0 + c];
+                if (c1nz) o -= c1T * P.y[d0 + c];
                 if (want_dot) pdT += o * bb;
             }
             P.y[d0 + c] = o;
@@ -399,12 +403,12 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
             sd += o * o;
         } else if (P.mode == EPI_JACOBI) {
             const double bb = double(P.b[n]);
-            o = double(xa) + om * ((bb - ya) * double(P.idiag[n]));
+            o = double(xa) + *P.omega * ((bb - ya) * double(P.idiag[n]));
             sd += o * bb;
         } else {
             const double bb = double(P.b[n]);
-            o = c0 * double(xa) + c2 * ((bb - ya) * double(P.idiag[n]));
-            if (c1 != 0.0) o -= c1 * double(P.y[n]);
+            o = P.omega[0] * double(xa) + P.omega[2] * ((bb - ya) * double(P.idiag[n]));
+            if (P.omega[1] != 0.0) o -= P.omega[1] * double(P.y[n]);
             sd += o * bb;
         }
         P.y[n] = T(o);

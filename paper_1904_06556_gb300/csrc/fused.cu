@@ -215,12 +215,16 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
     const int ooff = (oy + 1) * NW + ox + 1;   // staged node of the owner
 
     const float xa = S ? P.x[P.n] : 0.0f;
-    const double om = P.mode == EPI_JACOBI ? *P.omega : 0.0;
-    const float omF = float(om);
-    // Chebyshev step coefficients (EPI_CHEB)
-    const double c0 = P.mode == EPI_CHEB ? P.omega[0] : 0.0, c1 = P.mode == EPI_CHEB ? P.omega[1] : 0.0;
-    const double c2 = P.mode == EPI_CHEB ? P.omega[2] : 0.0;
-    const float c0F = float(c0), c1F = float(c1), c2F = float(c2);
+    // epilogue weights, converted once and only in their mode (no FP64 work in the other modes)
+    float omF = 0.0f, c0F = 0.0f, c1F = 0.0f, c2F = 0.0f;
+    bool c1nz = false;
+    if (P.mode == EPI_JACOBI) omF = float(*P.omega);
+    if (P.mode == EPI_CHEB) {
+        c0F = float(P.omega[0]);
+        c1F = float(P.omega[1]);
+        c2F = float(P.omega[2]);
+        c1nz = c1F != 0.0f;
+    }
     const bool want_dot = P.dot_slot >= 0;
     float pdT = 0.0f, paT = 0.0f;
 
@@ -399,7 +403,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
                 } else {
                     const float bb = __ldg(P.b + d0 + c);
                     o = c0F * xo[c] + c2F * ((bb - s[c]) * __ldg(P.idiag + d0 + c));
-                    if (c1 != 0.0) o -= c1F * P.y[d0 + c];
+                    if (c1nz) o -= c1F * P.y[d0 + c];
                     if (want_dot) pdT += o * bb;
                 }
                 P.y[d0 + c] = o;
@@ -442,12 +446,12 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
             sd += o * o;
         } else if (P.mode == EPI_JACOBI) {
             const double bb = double(P.b[n]);
-            o = double(xa) + om * ((bb - sa) * double(P.idiag[n]));
+            o = double(xa) + *P.omega * ((bb - sa) * double(P.idiag[n]));
             sd += o * bb;
         } else {
             const double bb = double(P.b[n]);
-            o = c0 * double(xa) + c2 * ((bb - sa) * double(P.idiag[n]));
-            if (c1 != 0.0) o -= c1 * double(P.y[n]);
+            o = P.omega[0] * double(xa) + P.omega[2] * ((bb - sa) * double(P.idiag[n]));
+            if (P.omega[1] != 0.0) o -= P.omega[1] * double(P.y[n]);
             sd += o * bb;
         }
         P.y[n] = float(o);
@@ -570,12 +574,16 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
     const int obits = owner ? fixed_bits(support, nx, ny, nz, I, J) : 0;
 
     const float xa = P.with_alpha ? P.x[P.n] : 0.0f;
-    const double om = P.mode == EPI_JACOBI ? *P.omega : 0.0;
-    const float omF = float(om);
-    // Chebyshev step coefficients (EPI_CHEB)
-    const double c0 = P.mode == EPI_CHEB ? P.omega[0] : 0.0, c1 = P.mode == EPI_CHEB ? P.omega[1] : 0.0;
-    const double c2 = P.mode == EPI_CHEB ? P.omega[2] : 0.0;
-    const float c0F = float(c0), c1F = float(c1), c2F = float(c2);
+    // epilogue weights, converted once and only in their mode (no FP64 work in the other modes)
+    float omF = 0.0f, c0F = 0.0f, c1F = 0.0f, c2F = 0.0f;
+    bool c1nz = false;
+    if (P.mode == EPI_JACOBI) omF = float(*P.omega);
+    if (P.mode == EPI_CHEB) {
+        c0F = float(P.omega[0]);
+        c1F = float(P.omega[1]);
+        c2F = float(P.omega[2]);
+        c1nz = c1F != 0.0f;
+    }
     const bool want_dot = P.dot_slot >= 0;
     float pdT = 0.0f, paT = 0.0f;
 
@@ -667,7 +675,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
                 } else {
                     const float bb = __ldg(P.b + d0 + c);
                     o = c0F * xo[c] + c2F * ((bb - s3[c]) * __ldg(P.idiag + d0 + c));
-                    if (c1 != 0.0) o -= c1F * P.y[d0 + c];
+                    if (c1nz) o -= c1F * P.y[d0 + c];
                     if (want_dot) pdT += o * bb;
                 }
                 P.y[d0 + c] = o;
@@ -709,12 +717,12 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
             sd += o * o;
         } else if (P.mode == EPI_JACOBI) {
             const double bb = double(P.b[n]);
-            o = double(xa) + om * ((bb - ya) * double(P.idiag[n]));
+            o = double(xa) + *P.omega * ((bb - ya) * double(P.idiag[n]));
             sd += o * bb;
         } else {
             const double bb = double(P.b[n]);
-            o = c0 * double(xa) + c2 * ((bb - ya) * double(P.idiag[n]));
-            if (c1 != 0.0) o -= c1 * double(P.y[n]);
+            o = P.omega[0] * double(xa) + P.omega[2] * ((bb - ya) * double(P.idiag[n]));
+            if (P.omega[1] != 0.0) o -= P.omega[1] * double(P.y[n]);
             sd += o * bb;
         }
         P.y[n] = float(o);

@@ -210,11 +210,13 @@ static void lanczos_finish(pbm_grid* g, int k) {
     L.lambda_max = tridiag_max_eig(a, b);
     if (!(L.lambda_max > 0.0) || !std::isfinite(L.lambda_max)) fail(PBM_ENONFINITE, "Lanczos estimate is not positive");
     if (g->desc.smoother == PBM_SMOOTHER_CHEBYSHEV) {
-        // Chebyshev acceleration on [lo, hi] = [0.1, 1.1] lambda: centre theta, half width delta; the first
+        // Chebyshev acceleration on [lo, hi] = [0.1, 1.4] lambda: centre theta, half width delta (every
+        // eigenvalue of D^-1 A up to lo + hi = 1.5 lambda is damped, so the estimate from below may be off by a
+        // third, as the Jacobi weight's 2 / theta = 1.67 allows); the first
         // step of a pass is a Jacobi step with weight 1 / theta, step s >= 1 takes
         // x_{s+1} = x_s + a_s (x_s - x_{s-1}) + b_s D^-1 (b - A x_s) with rho_0 = delta / theta,
         // rho_s = 1 / (2 theta / delta - rho_{s-1}), a_s = rho_s rho_{s-1}, b_s = 2 rho_s / delta
-        const double lo = 0.1 * L.lambda_max, hi = 1.1 * L.lambda_max;
+        const double lo = 0.1 * L.lambda_max, hi = 1.4 * L.lambda_max;
         const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
         L.omega = 1.0 / theta;
         double rho = 1.0 / sigma;

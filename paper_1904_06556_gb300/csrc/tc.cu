@@ -283,12 +283,16 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
 
     const float xa = S ? P.x[P.n] : 0.0f;
     const int mode = P.mode;
-    const double om = mode == EPI_JACOBI ? *P.omega : 0.0;
-    const float omF = float(om);
-    // Chebyshev step coefficients (EPI_CHEB)
-    const double c0 = mode == EPI_CHEB ? P.omega[0] : 0.0, c1 = mode == EPI_CHEB ? P.omega[1] : 0.0;
-    const double c2 = mode == EPI_CHEB ? P.omega[2] : 0.0;
-    const float c0F = float(c0), c1F = float(c1), c2F = float(c2);
+    // epilogue weights, converted once and only in their mode (no FP64 work in the other modes)
+    float omF = 0.0f, c0F = 0.0f, c1F = 0.0f, c2F = 0.0f;
+    bool c1nz = false;
+    if (mode == EPI_JACOBI) omF = float(*P.omega);
+    if (mode == EPI_CHEB) {
+        c0F = float(P.omega[0]);
+        c1F = float(P.omega[1]);
+        c2F = float(P.omega[2]);
+        c1nz = c1F != 0.0f;
+    }
     const bool want_dot = P.dot_slot >= 0;
     const float ks = P.kscale;
     float pdT = 0.0f, paT = 0.0f;
@@ -486,7 +490,7 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
                 } else {
                     const float bb = __ldg(P.b + d0 + c);
                     o3 = c0F * xo[c] + c2F * ((bb - s3[c]) * __ldg(P.idiag + d0 + c));
-                    if (c1 != 0.0) o3 -= c1F * P.y[d0 + c];
+                    if (c1nz) o3 -= c1F * P.y[d0 + c];
                     if (want_dot) pdT += o3 * bb;
                 }
                 P.y[d0 + c] = o3;
@@ -551,12 +555,12 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
             sd += o * o;
         } else if (mode == EPI_JACOBI) {
             const double bb = double(P.b[n]);
-            o = double(xa) + om * ((bb - sa) * double(P.idiag[n]));
+            o = double(xa) + *P.omega * ((bb - sa) * double(P.idiag[n]));
             sd += o * bb;
         } else {
             const double bb = double(P.b[n]);
-            o = c0 * double(xa) + c2 * ((bb - sa) * double(P.idiag[n]));
-            if (c1 != 0.0) o -= c1 * double(P.y[n]);
+            o = P.omega[0] * double(xa) + P.omega[2] * ((bb - sa) * double(P.idiag[n]));
+            if (P.omega[1] != 0.0) o -= P.omega[1] * double(P.y[n]);
             sd += o * bb;
         }
         P.y[n] = float(o);
