@@ -508,12 +508,14 @@ void cols_cost(const Geom& G, int Lc, bool op_s, bool recompute_w, int mode, int
     double vec = 2.0 * n + (op_s ? n : 0.0), elem = m * (op_s ? 2.0 : 1.0);
     if (mode == EPI_RESID) vec += n;
     if (mode == EPI_JACOBI) vec += 2.0 * n;
+    if (mode == EPI_CHEB) vec += 3.0 * n;   // b, the inverse diagonal and the previous iterate
     bytes = double(esize) * (vec + elem);
     const double L = double(Lc > 0 ? Lc : fine_chunk(G));
     double per_elem = 2.0 * 24.0 * (L + 1.0) / L + 48.0 + 45.0 + 21.0 + 12.0 * (L - 1.0) / L;
     if (op_s) per_elem += 44.0;
     if (op_s && recompute_w) per_elem += 24.0 * (L + 1.0) / L + 24.0 + 45.0;   // quads, z part and Khat of u
-    const double per_node = 12.0 + (mode == EPI_JACOBI ? 12.0 : (mode == EPI_RESID ? 6.0 : 3.0));
+    const double per_node =
+        12.0 + (mode == EPI_CHEB ? 18.0 : (mode == EPI_JACOBI ? 12.0 : (mode == EPI_RESID ? 6.0 : 3.0)));
     flops = m * per_elem + nn * per_node;
 }
 
