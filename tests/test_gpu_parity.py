@@ -448,6 +448,11 @@ def test_vcycle_chebyshev_fp32_and_solves(pkg, precision):
     b[:pb.n][pb.fixed] = 0.0
     xv = host(G.vcycle("S", dev(b)))        # FP32 V-cycle on mixed grids
     assert rel(xv, h.vcycle(b)) < (1e-4 if precision == "mixed" else 1e-10)
+    if precision == "mixed":   # the same with the fine level on the tensor-core plan (its Chebyshev epilogue)
+        auto = G.info()["fp32_tile"][1][4]
+        G.set_fp32_plan("S", pkg.fp32_tc_plan())
+        assert rel(host(G.vcycle("S", dev(b))), h.vcycle(b)) < 1e-4
+        G.set_fp32_plan("S", auto)
     rhs = pbm.rhs_closed(pb, st, cf)
     ref = solvers.direct_solve(S, rhs)
     x, info = G.minres_solve("S", dev(rhs), rtol=1e-10, maxit=400)
