@@ -157,7 +157,7 @@ typedef struct pbm_newton_info {
 } pbm_newton_info;
 
 /* Timing of the fine-level operator kernel (K(w) x or S x with any of its fused epilogues: plain
- * apply, residual b - A x, damped-Jacobi sweep), accumulated per handle while profiling is on. */
+ * apply, residual b - A x, damped-Jacobi sweep, Chebyshev step), accumulated per handle while profiling is on. */
 typedef struct pbm_profile_stats {
     int64_t launches;      /* fine-level operator launches timed                                  */
     double total_ms;       /* sum of their durations, CUDA events on the launch stream            */
