@@ -31,12 +31,13 @@ def test_default_desc(lib):
     assert (d.nx, d.ny, d.nz, d.levels, d.precision) == (16, 8, 8, 3, 0)
     assert d.E == 1.0 and d.nu == 0.3 and d.pre_sweeps == 2 and d.post_sweeps == 2
     assert d.jacobi_theta == 1.2 and d.lanczos_steps == 10
+    assert d.smoother == _lib.SMOOTHERS["jacobi"]
 
 
 @pytest.mark.parametrize("field,value,msg", [
     ("nx", 15, "divisible"), ("levels", 0, "levels"), ("levels", 1, "at least 2"), ("support", 9, "support"),
     ("precision", 7, "precision"), ("nu", 0.5, "material"), ("E", -1.0, "material"), ("jacobi_theta", 2.5, "theta"),
-    ("lanczos_steps", 1, "lanczos"), ("pre_sweeps", -1, "sweeps"),
+    ("lanczos_steps", 1, "lanczos"), ("pre_sweeps", -1, "sweeps"), ("smoother", 2, "smoother"),
 ])
 def test_invalid_descriptions_rejected(lib, field, value, msg):
     d = _lib.GridDesc()
@@ -45,6 +46,18 @@ def test_invalid_descriptions_rejected(lib, field, value, msg):
     h = C.c_void_p()
     assert lib.pbm_create_grid(C.byref(d), C.byref(h)) == _lib.PBM_EINVAL
     assert msg in lib.pbm_last_error().decode()
+    assert not h.value
+
+
+def test_chebyshev_steps_limit(lib):
+    """A Chebyshev pass takes at most 9 steps (the coefficient table holds 8 after the first)."""
+    d = _lib.GridDesc()
+    lib.pbm_default_desc(C.byref(d), 16, 8, 8, 3, 0)
+    d.smoother = _lib.SMOOTHERS["chebyshev"]
+    d.post_sweeps = 10
+    h = C.c_void_p()
+    assert lib.pbm_create_grid(C.byref(d), C.byref(h)) == _lib.PBM_EINVAL
+    assert "Chebyshev" in lib.pbm_last_error().decode()
     assert not h.value
 
 

@@ -464,6 +464,10 @@ def test_vcycle_chebyshev_fp32_and_solves(pkg, precision):
     rhs2 = pbm.rhs_closed(pb2, st2, pbm.coeffs(pb2, st2))
     y1, _ = G.minres_solve("S", dev(rhs), rtol=1e-10, maxit=400)
     y2, _ = G2.minres_solve("S", dev(rhs2), rtol=1e-10, maxit=400)
+    G3 = pkg.Grid(8, 4, 4, 2, "cantilever", precision=precision)          # damped Jacobi
+    with pytest.raises(pkg.PbmError, match="smoothing"):
+        pkg.Batch([G, G3], "S")
+    G3.close()
     B = pkg.Batch([G, G2], "S")
     ys, infos = B.minres_solve([dev(rhs), dev(rhs2)], rtol=1e-10, maxit=400)
     for y, yb, inf in zip((y1, y2), ys, infos):
