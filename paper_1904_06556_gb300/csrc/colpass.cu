@@ -305,27 +305,41 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
         const bool hasA = K < nz;
         const bool hasB = K > 0 && (K % L == 0 || K == nz);
         const int64_t oa = int64_t(K) * 12 * P.ncol, ob = int64_t(K > 0 ? (K - 1) / L : 0) * 12 * P.ncol;
+        const int64_t d0 = 3 * int64_t(nd);
+        // every load of the node first (the quads of the four columns around it, its x and the
+        // epilogue's operands), then the sums in a fixed order
+        T qa[4][3], qb[4][3];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int dj = 1 - (q >> 1), di = 1 - (q & 1);
+            const int ii = I - di, jj = J - dj;
+            const bool in = ii >= 0 && ii < nx && jj >= 0 && jj < ny;
+            const int64_t col = in ? ii + int64_t(nx) * jj : 0;
+            const int a = di + 2 * dj;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int64_t r = int64_t(3 * a + c) * P.ncol + col;
+                qa[q][c] = (in && hasA) ? __ldg(P.QA + oa + r) : T(0);
+                qb[q][c] = (in && hasB) ? __ldg(P.QB + ob + r) : T(0);
+            }
+        }
+        T xo[3], bv[3] = {T(0), T(0), T(0)}, dv[3] = {T(0), T(0), T(0)}, yp[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            xo[c] = P.x[d0 + c];
+            if (P.mode != EPI_APPLY) bv[c] = __ldg(P.b + d0 + c);
+            if (P.mode >= EPI_JACOBI) dv[c] = __ldg(P.idiag + d0 + c);
+            if (c1nz) yp[c] = P.y[d0 + c];
+        }
         T s[3] = {T(0), T(0), T(0)};
 #pragma unroll
-        for (int dj = 1; dj >= 0; --dj)
+        for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int di = 1; di >= 0; --di) {
-                const int ii = I - di, jj = J - dj;
-                if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) continue;
-                const int64_t col = ii + int64_t(nx) * jj;
-                const int a = di + 2 * dj;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const int64_t r = int64_t(3 * a + c) * P.ncol + col;
-                    if (hasA) s[c] += P.QA[oa + r];
-                    if (hasB) s[c] += P.QB[ob + r];
-                }
+            for (int c = 0; c < 3; ++c) {
+                s[c] += qa[q][c];
+                s[c] += qb[q][c];
             }
-        const int64_t d0 = 3 * int64_t(nd);
         const bool fixed = node_fixed(P.support, nx, ny, nz, I, J, K);
-        T xo[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) xo[c] = P.x[d0 + c];
         if (P.bord) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -346,17 +360,15 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
                 o = s[c];
                 if (want_dot) pdT += o * xo[c];
             } else if (P.mode == EPI_RESID) {
-                o = P.b[d0 + c] - s[c];
+                o = bv[c] - s[c];
                 if (want_dot) pdT += o * o;
             } else if (P.mode == EPI_JACOBI) {
-                const T bb = P.b[d0 + c];
-                o = xo[c] + omT * ((bb - s[c]) * P.idiag[d0 + c]);
-                if (want_dot) pdT += o * bb;
+                o = xo[c] + omT * ((bv[c] - s[c]) * dv[c]);
+                if (want_dot) pdT += o * bv[c];
             } else {
-                const T bb = P.b[d0 + c];
-                o = c0T * xo[c] + c2T * ((bb - s[c]) * P.idiag[d0 + c]);
-                if (c1nz) o -= c1T * P.y[d0 + c];
-                if (want_dot) pdT += o * bb;
+                o = c0T * xo[c] + c2T * ((bv[c] - s[c]) * dv[c]);
+                if (c1nz) o -= c1T * yp[c];
+                if (want_dot) pdT += o * bv[c];
             }
             P.y[d0 + c] = o;
         }
