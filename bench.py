@@ -821,7 +821,7 @@ def main():
     ap.add_argument("--fp32-plans", action="store_true",
                     help="time every tile plan of the FP32 fine operator on the workload's grid")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--smoother", default="chebyshev", choices=["jacobi", "chebyshev"],
+    ap.add_argument("--smoother", default="chebyshev", choices=["jacobi", "chebyshev", "gauss_seidel"],
                     help="V-cycle smoothing: Chebyshev acceleration of Jacobi (default; fewer MINRES iterations "
                          "for the same operator applications) or damped Jacobi")
     ap.add_argument("--no-cpu-baseline", action="store_true")

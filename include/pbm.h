@@ -80,11 +80,16 @@ enum pbm_epilogue {        /* what a fused operator launch writes (pbm_apply_fin
 
 enum pbm_smoother {        /* smoothing of the multigrid V-cycle (Section 5.2; the paper uses Gauss-Seidel) */
     PBM_SMOOTHER_JACOBI = 0,    /* damped Jacobi x += omega_k D^{-1} (b - A x), omega_k = theta / lambda_k */
-    PBM_SMOOTHER_CHEBYSHEV = 1  /* Chebyshev acceleration of Jacobi (Saad, Iterative Methods, Alg. 12.1) on
+    PBM_SMOOTHER_CHEBYSHEV = 1, /* Chebyshev acceleration of Jacobi (Saad, Iterative Methods, Alg. 12.1) on
                                    the interval [0.1, 1.4] lambda_k of D^{-1} A: each pass of nu steps damps
                                    that interval by the Chebyshev polynomial of degree nu (and every
                                    eigenvalue up to 1.5 lambda_k); same operator applications per step as a
                                    Jacobi sweep                                                          */
+    PBM_SMOOTHER_GAUSS_SEIDEL = 2  /* the paper's Gauss-Seidel, made parallel: multicolour sweeps over the 8
+                                   node colours (i mod 2) + 2 (j mod 2) + 4 (k mod 2) (and alpha as a 9th
+                                   for S), x_c += D_c^{-1} (b - A x)_c colour after colour; forward before the
+                                   coarse correction, backward after it. One operator application per colour,
+                                   so 8 (9) per sweep. Not for batched solves.                           */
 };
 
 typedef struct pbm_grid_desc {

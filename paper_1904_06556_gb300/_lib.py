@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "PBM_OK", -1: "PBM_EINVAL", -2: "PBM_ENOMEM", -3: "PBM_ECUDA"
                 -9: "PBM_ESTATE"}
 SUPPORTS = {"cantilever": 0, "bridge_corners": 1, "bridge_edges": 2, "free": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
-SMOOTHERS = {"jacobi": 0, "chebyshev": 1}
+SMOOTHERS = {"jacobi": 0, "chebyshev": 1, "gauss_seidel": 2}
 OPS = {"K": 0, "S": 1}
 EPILOGUES = {"apply": 0, "resid": 1, "jacobi": 2}
 MAPS = {"fixed_dofs": 0, "elem_nodes": 1, "prolong": 2, "Ke": 3}

@@ -691,6 +691,8 @@ int pbm_batch_create(pbm_grid* const* grids, int n, int op, pbm_batch** out) {
             if (g->device != b->device) fail(PBM_EINVAL, "all grids of a batch must live on one device");
             if ((g->desc.precision == PBM_MIXED) != b->mixed) fail(PBM_EINVAL, "all grids of a batch need one precision");
             if (g->desc.pre_sweeps < 1) fail(PBM_EINVAL, "batched V-cycles need at least one pre-smoothing sweep");
+            if (g->desc.smoother == PBM_SMOOTHER_GAUSS_SEIDEL)
+                fail(PBM_EINVAL, "batched V-cycles smooth with Jacobi or Chebyshev, not Gauss-Seidel");
             if (g->desc.pre_sweeps != grids[0]->desc.pre_sweeps || g->desc.post_sweeps != grids[0]->desc.post_sweeps ||
                 g->desc.smoother != grids[0]->desc.smoother)
                 fail(PBM_EINVAL, "all grids of a batch need the same smoothing sweeps");

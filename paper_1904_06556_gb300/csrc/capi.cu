@@ -244,7 +244,9 @@ int pbm_create_grid(const pbm_grid_desc* d, pbm_grid** out) {
         d->post_sweeps > 64)
         fail(PBM_EINVAL, "sweeps must be in 0..64, at least one in total");
     if (!(d->jacobi_theta > 0.0 && d->jacobi_theta < 2.0)) fail(PBM_EINVAL, "jacobi_theta must be in (0, 2)");
-    if (d->smoother != PBM_SMOOTHER_JACOBI && d->smoother != PBM_SMOOTHER_CHEBYSHEV) fail(PBM_EINVAL, "unknown smoother");
+    if (d->smoother != PBM_SMOOTHER_JACOBI && d->smoother != PBM_SMOOTHER_CHEBYSHEV &&
+        d->smoother != PBM_SMOOTHER_GAUSS_SEIDEL)
+        fail(PBM_EINVAL, "unknown smoother");
     if (d->smoother == PBM_SMOOTHER_CHEBYSHEV && (d->pre_sweeps > kChebMaxStep + 1 || d->post_sweeps > kChebMaxStep + 1))
         fail(PBM_EINVAL, "Chebyshev smoothing takes at most 9 steps per pass");
     if (d->lanczos_steps < 2 || d->lanczos_steps > 64) fail(PBM_EINVAL, "lanczos_steps must be in 2..64");

@@ -365,9 +365,12 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
             } else if (P.mode == EPI_JACOBI) {
                 o = xo[c] + omT * ((bv[c] - s[c]) * dv[c]);
                 if (want_dot) pdT += o * bv[c];
-            } else {
+            } else if (P.mode == EPI_CHEB) {
                 o = c0T * xo[c] + c2T * ((bv[c] - s[c]) * dv[c]);
                 if (c1nz) o -= c1T * yp[c];
+                if (want_dot) pdT += o * bv[c];
+            } else {
+                o = (node_colour(I, J, K) == P.mode - EPI_GS0) ? xo[c] + (bv[c] - s[c]) * dv[c] : xo[c];
                 if (want_dot) pdT += o * bv[c];
             }
             P.y[d0 + c] = o;
@@ -417,10 +420,14 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
             const double bb = double(P.b[n]);
             o = double(xa) + *P.omega * ((bb - ya) * double(P.idiag[n]));
             sd += o * bb;
-        } else {
+        } else if (P.mode == EPI_CHEB) {
             const double bb = double(P.b[n]);
             o = P.omega[0] * double(xa) + P.omega[2] * ((bb - ya) * double(P.idiag[n]));
             if (P.omega[1] != 0.0) o -= P.omega[1] * double(P.y[n]);
+            sd += o * bb;
+        } else {
+            const double bb = double(P.b[n]);
+            o = P.mode == EPI_GS0 + 8 ? double(xa) + (bb - ya) * double(P.idiag[n]) : double(xa);
             sd += o * bb;
         }
         P.y[n] = T(o);
@@ -521,6 +528,7 @@ void cols_cost(const Geom& G, int Lc, bool op_s, bool recompute_w, int mode, int
     if (mode == EPI_RESID) vec += n;
     if (mode == EPI_JACOBI) vec += 2.0 * n;
     if (mode == EPI_CHEB) vec += 3.0 * n;   // b, the inverse diagonal and the previous iterate
+    if (mode >= EPI_GS0) vec += 2.0 * n;    // a Gauss-Seidel colour step: b and the inverse diagonal
     bytes = double(esize) * (vec + elem);
     const double L = double(Lc > 0 ? Lc : fine_chunk(G));
     double per_elem = 2.0 * 24.0 * (L + 1.0) / L + 48.0 + 45.0 + 21.0 + 12.0 * (L - 1.0) / L;

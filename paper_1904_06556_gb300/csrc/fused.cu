@@ -369,6 +369,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
         }
         __syncthreads();  // (b) corner values of plane k complete
         if (owner) {
+            const bool gs_upd = node_colour(I, J, k) == P.mode - EPI_GS0;   // Gauss-Seidel colour step
             float2 s01 = make_float2(0.0f, 0.0f);
             float s2 = 0.0f;
 #pragma unroll
@@ -400,10 +401,14 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
                     const float bb = __ldg(P.b + d0 + c);
                     o = xo[c] + omF * ((bb - s[c]) * __ldg(P.idiag + d0 + c));
                     if (want_dot) pdT += o * bb;
-                } else {
+                } else if (P.mode == EPI_CHEB) {
                     const float bb = __ldg(P.b + d0 + c);
                     o = c0F * xo[c] + c2F * ((bb - s[c]) * __ldg(P.idiag + d0 + c));
                     if (c1nz) o -= c1F * P.y[d0 + c];
+                    if (want_dot) pdT += o * bb;
+                } else {
+                    const float bb = __ldg(P.b + d0 + c);
+                    o = gs_upd ? xo[c] + (bb - s[c]) * __ldg(P.idiag + d0 + c) : xo[c];
                     if (want_dot) pdT += o * bb;
                 }
                 P.y[d0 + c] = o;
@@ -448,10 +453,14 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
             const double bb = double(P.b[n]);
             o = double(xa) + *P.omega * ((bb - sa) * double(P.idiag[n]));
             sd += o * bb;
-        } else {
+        } else if (P.mode == EPI_CHEB) {
             const double bb = double(P.b[n]);
             o = P.omega[0] * double(xa) + P.omega[2] * ((bb - sa) * double(P.idiag[n]));
             if (P.omega[1] != 0.0) o -= P.omega[1] * double(P.y[n]);
+            sd += o * bb;
+        } else {
+            const double bb = double(P.b[n]);
+            o = P.mode == EPI_GS0 + 8 ? double(xa) + (bb - sa) * double(P.idiag[n]) : double(xa);
             sd += o * bb;
         }
         P.y[n] = float(o);
@@ -635,6 +644,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
         if (q < 4) sq[q * EC + col] = make_float4(ob[0], ob[1], ob[2], 0.0f);
         __syncthreads();  // (b) corner values of plane k complete
         if (owner) {
+            const bool gs_upd = node_colour(I, J, k) == P.mode - EPI_GS0;   // Gauss-Seidel colour step
             float s3[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
             for (int dj = 1; dj >= 0; --dj)
@@ -672,10 +682,14 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
                     const float bb = __ldg(P.b + d0 + c);
                     o = xo[c] + omF * ((bb - s3[c]) * __ldg(P.idiag + d0 + c));
                     if (want_dot) pdT += o * bb;
-                } else {
+                } else if (P.mode == EPI_CHEB) {
                     const float bb = __ldg(P.b + d0 + c);
                     o = c0F * xo[c] + c2F * ((bb - s3[c]) * __ldg(P.idiag + d0 + c));
                     if (c1nz) o -= c1F * P.y[d0 + c];
+                    if (want_dot) pdT += o * bb;
+                } else {
+                    const float bb = __ldg(P.b + d0 + c);
+                    o = gs_upd ? xo[c] + (bb - s3[c]) * __ldg(P.idiag + d0 + c) : xo[c];
                     if (want_dot) pdT += o * bb;
                 }
                 P.y[d0 + c] = o;
@@ -719,10 +733,14 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
             const double bb = double(P.b[n]);
             o = double(xa) + *P.omega * ((bb - ya) * double(P.idiag[n]));
             sd += o * bb;
-        } else {
+        } else if (P.mode == EPI_CHEB) {
             const double bb = double(P.b[n]);
             o = P.omega[0] * double(xa) + P.omega[2] * ((bb - ya) * double(P.idiag[n]));
             if (P.omega[1] != 0.0) o -= P.omega[1] * double(P.y[n]);
+            sd += o * bb;
+        } else {
+            const double bb = double(P.b[n]);
+            o = P.mode == EPI_GS0 + 8 ? double(xa) + (bb - ya) * double(P.idiag[n]) : double(xa);
             sd += o * bb;
         }
         P.y[n] = float(o);

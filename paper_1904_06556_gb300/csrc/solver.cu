@@ -57,6 +57,50 @@ static ApplyArgs args(const void* x, void* y, int mode, const void* b = nullptr,
 
 static size_t esz(bool fp32) { return fp32 ? sizeof(float) : sizeof(double); }
 
+void vcycle(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, void* x, int dot_slot, cudaStream_t st,
+            bool first_done);
+
+// V-cycle with multicolour Gauss-Seidel smoothing: every sweep is one operator launch per colour (8 node
+// colours, and alpha last for S) with the EPI_GS0 + c epilogue, forward before the coarse correction and
+// backward after it; pre-smoothing starts from x = 0 (no sweep is fused into the restriction)
+static void vcycle_gs(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, void* x, int dot_slot,
+                      cudaStream_t st) {
+    Level& L = g->L[k];
+    const int64_t nv = L.g.n() + (op_s ? 1 : 0);
+    const size_t es = fp32 ? sizeof(float) : sizeof(double);
+    void* t = fp32 ? (void*)L.t32 : (void*)L.t64;
+    void* r = fp32 ? (void*)L.r32 : (void*)L.r64;
+    const void* D = fp32 ? (const void*)L.idiag32 : (const void*)L.idiag64;
+    const int ncol = op_s ? 9 : 8;
+    const int pre = g->desc.pre_sweeps, post = g->desc.post_sweeps;
+    vec_zero(x, nv * es, st);
+    void* cur = x;
+    void* oth = t;
+    for (int sw = 0; sw < pre; ++sw)
+        for (int c = 0; c < ncol; ++c) {
+            level_apply(g, k, fp32, op_s, args(cur, oth, EPI_GS0 + c, b, D), st);
+            std::swap(cur, oth);
+        }
+    if (cur != x) PBM_CUDA(cudaMemcpyAsync(x, cur, nv * es, cudaMemcpyDeviceToDevice, st));
+    level_apply(g, k, fp32, op_s, args(x, r, EPI_RESID, b), st);
+    Level& C = g->L[k + 1];
+    void* bc = fp32 ? (void*)C.b32 : (void*)C.b64;
+    void* xc = fp32 ? (void*)C.x32 : (void*)C.x64;
+    launch_restrict(g, k, fp32, r, bc, op_s, 1.0, st, nullptr);
+    vcycle(g, k + 1, fp32, op_s, bc, xc, -1, st, false);
+    launch_prolong_add(g, k, fp32, xc, x, op_s, st);
+    cur = x;
+    oth = t;
+    for (int sw = 0; sw < post; ++sw)
+        for (int c = ncol - 1; c >= 0; --c) {
+            const bool last = sw == post - 1 && c == 0;
+            level_apply(g, k, fp32, op_s, args(cur, oth, EPI_GS0 + c, b, D, nullptr, last ? dot_slot : -1), st);
+            std::swap(cur, oth);
+        }
+    if (cur != x) PBM_CUDA(cudaMemcpyAsync(x, cur, nv * es, cudaMemcpyDeviceToDevice, st));
+    if (post == 0 && dot_slot >= 0) launch_dot(g, fp32, x, b, nv, dot_slot, st);
+}
+
 // ------------------------------------------------------------------------------------------------
 // V-cycle: x = M^{-1} b on level k (x overwritten). If dot_slot >= 0, red[dot_slot] = x . b.
 // ------------------------------------------------------------------------------------------------
@@ -75,6 +119,10 @@ void vcycle(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, void* x, in
     void* r = fp32 ? (void*)L.r32 : (void*)L.r64;
     const void* D = fp32 ? (const void*)L.idiag32 : (const void*)L.idiag64;
     const double* om = &g->sc->mr[16 + k];
+    if (g->desc.smoother == PBM_SMOOTHER_GAUSS_SEIDEL) {
+        vcycle_gs(g, k, fp32, op_s, b, x, dot_slot, st);
+        return;
+    }
     const int pre = g->desc.pre_sweeps, post = g->desc.post_sweeps;
     // pre-smoothing from x = 0: the first sweep is x = omega D^-1 b; arrange the ping-pong so that
     // the last pre-sweep lands in x

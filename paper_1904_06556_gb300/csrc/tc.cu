@@ -467,6 +467,7 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
         if (s_abort) break;
         if (k < kz0) continue;
         if (owner) {
+            const bool gs_upd = node_colour(I, J, k) == mode - EPI_GS0;   // Gauss-Seidel colour step
             const float4 o = sq_r[buf * EYT * EXT];
             float s3[3] = {n0[0] + o.x, n0[1] + o.y, n0[2] + o.z};
             if (ofixed) {
@@ -487,10 +488,14 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
                     const float bb = __ldg(P.b + d0 + c);
                     o3 = xo[c] + omF * ((bb - s3[c]) * __ldg(P.idiag + d0 + c));
                     if (want_dot) pdT += o3 * bb;
-                } else {
+                } else if (mode == EPI_CHEB) {
                     const float bb = __ldg(P.b + d0 + c);
                     o3 = c0F * xo[c] + c2F * ((bb - s3[c]) * __ldg(P.idiag + d0 + c));
                     if (c1nz) o3 -= c1F * P.y[d0 + c];
+                    if (want_dot) pdT += o3 * bb;
+                } else {
+                    const float bb = __ldg(P.b + d0 + c);
+                    o3 = gs_upd ? xo[c] + (bb - s3[c]) * __ldg(P.idiag + d0 + c) : xo[c];
                     if (want_dot) pdT += o3 * bb;
                 }
                 P.y[d0 + c] = o3;
@@ -557,10 +562,14 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
             const double bb = double(P.b[n]);
             o = double(xa) + *P.omega * ((bb - sa) * double(P.idiag[n]));
             sd += o * bb;
-        } else {
+        } else if (mode == EPI_CHEB) {
             const double bb = double(P.b[n]);
             o = P.omega[0] * double(xa) + P.omega[2] * ((bb - sa) * double(P.idiag[n]));
             if (P.omega[1] != 0.0) o -= P.omega[1] * double(P.y[n]);
+            sd += o * bb;
+        } else {
+            const double bb = double(P.b[n]);
+            o = mode == EPI_GS0 + 8 ? double(xa) + (bb - sa) * double(P.idiag[n]) : double(xa);
             sd += o * bb;
         }
         P.y[n] = float(o);

@@ -37,7 +37,7 @@ def test_default_desc(lib):
 @pytest.mark.parametrize("field,value,msg", [
     ("nx", 15, "divisible"), ("levels", 0, "levels"), ("levels", 1, "at least 2"), ("support", 9, "support"),
     ("precision", 7, "precision"), ("nu", 0.5, "material"), ("E", -1.0, "material"), ("jacobi_theta", 2.5, "theta"),
-    ("lanczos_steps", 1, "lanczos"), ("pre_sweeps", -1, "sweeps"), ("smoother", 2, "smoother"),
+    ("lanczos_steps", 1, "lanczos"), ("pre_sweeps", -1, "sweeps"), ("smoother", 3, "smoother"),
 ])
 def test_invalid_descriptions_rejected(lib, field, value, msg):
     d = _lib.GridDesc()

@@ -390,6 +390,8 @@ def test_ip_newton_system_matches_oracle(pkg, dims, bc, levels, precision):
 def _check_smoother_weights(info, h, levels, smoother):
     if smoother == "jacobi":
         assert np.allclose(info["omega"][:levels - 1], h.omega, rtol=1e-10)
+    elif smoother == "gauss_seidel":   # no weight; the Lanczos estimates are still formed
+        assert np.allclose(info["lambda_max"][:levels - 1], h.lmax, rtol=1e-10)
     else:   # Lanczos estimates; the first step of a Chebyshev pass has weight 1 / theta = 1 / (0.6 lambda)
         assert np.allclose(info["lambda_max"][:levels - 1], h.lmax, rtol=1e-10)
         assert np.allclose(info["omega"][:levels - 1], [1.0 / c[0] for c in h.cheb], rtol=1e-10)
@@ -399,7 +401,9 @@ def _check_smoother_weights(info, h, levels, smoother):
                                                             ((16, 8, 8), "bridge_corners", 3, "jacobi", 2),
                                                             ((16, 8, 8), "cantilever", 4, "jacobi", 2),
                                                             ((16, 8, 8), "bridge_corners", 3, "chebyshev", 2),
-                                                            ((16, 8, 8), "cantilever", 4, "chebyshev", 3)])
+                                                            ((16, 8, 8), "cantilever", 4, "chebyshev", 3),
+                                                            ((16, 8, 8), "bridge_corners", 3, "gauss_seidel", 1),
+                                                            ((8, 4, 4), "cantilever", 2, "gauss_seidel", 2)])
 def test_vcycle_S_matches_oracle(pkg, dims, bc, levels, smoother, sweeps):
     pb, st, d = make_problem(*dims, bc, 2, 0.4)
     G = pkg.Grid(*dims, levels, bc, smoother=smoother, pre_sweeps=sweeps, post_sweeps=sweeps)
@@ -417,7 +421,9 @@ def test_vcycle_S_matches_oracle(pkg, dims, bc, levels, smoother, sweeps):
                                                             ((16, 8, 8), "bridge_corners", 4, "jacobi", 2),
                                                             ((8, 4, 4), "cantilever", 3, "chebyshev", 2),
                                                             ((16, 8, 8), "bridge_corners", 4, "chebyshev", 3),
-                                                            ((16, 8, 8), "cantilever", 3, "chebyshev", 1)])
+                                                            ((16, 8, 8), "cantilever", 3, "chebyshev", 1),
+                                                            ((16, 8, 8), "bridge_edges", 3, "gauss_seidel", 1),
+                                                            ((8, 4, 4), "cantilever", 3, "gauss_seidel", 2)])
 def test_vcycle_K_matches_oracle(pkg, dims, bc, levels, smoother, sweeps):
     g = fem.Grid(*dims, bc)
     rho = synthetic.density_uniform_rescaled(g.m, 0.3, 1)
@@ -430,6 +436,36 @@ def test_vcycle_K_matches_oracle(pkg, dims, bc, levels, smoother, sweeps):
     x = host(G.vcycle("K", dev(b)))
     _check_smoother_weights(G.info(), h, levels, smoother)
     assert rel(x, h.vcycle(b)) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_gauss_seidel_smoother_fp32_and_solves(pkg, precision):
+    """Multicolour Gauss-Seidel smoothing (one launch per colour, alpha as the ninth): the FP32 V-cycle on mixed
+    grids (fine single pass, coarse kernels, and the tensor-core plan) against the oracle's; MINRES solves reach
+    the oracle's direct solution; batches refuse it."""
+    dims, bc, levels = (16, 8, 8), "cantilever", 3
+    pb, st, d = make_problem(*dims, bc, 5, 0.5)
+    G = pkg.Grid(*dims, levels, bc, precision=precision, smoother="gauss_seidel", pre_sweeps=1, post_sweeps=1)
+    G.set_state(state_dev(d))
+    cf = pbm.coeffs(pb, st)
+    S = pbm.assemble_S(pb, st, cf)
+    h = solvers.Hierarchy(pb.grid, S, levels, has_alpha=True, sweeps=1, smoother="gauss_seidel")
+    b = np.random.default_rng(10).standard_normal(pb.n + 1)
+    b[:pb.n][pb.fixed] = 0.0
+    tol = 1e-4 if precision == "mixed" else 1e-10
+    assert rel(host(G.vcycle("S", dev(b))), h.vcycle(b)) < tol
+    if precision == "mixed":
+        auto = G.info()["fp32_tile"][1][4]
+        G.set_fp32_plan("S", pkg.fp32_tc_plan())
+        assert rel(host(G.vcycle("S", dev(b))), h.vcycle(b)) < tol
+        G.set_fp32_plan("S", auto)
+    rhs = pbm.rhs_closed(pb, st, cf)
+    ref = solvers.direct_solve(S, rhs)
+    x, info = G.minres_solve("S", dev(rhs), rtol=1e-10, maxit=400)
+    assert info["relres"] <= 1e-10
+    assert rel(host(x), ref) < 1e-7
+    with pytest.raises(pkg.PbmError, match="Gauss-Seidel"):
+        pkg.Batch([G], "S")
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])

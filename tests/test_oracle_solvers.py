@@ -6,6 +6,7 @@ the V-cycle operator assembled column by column.
 import numpy as np
 import pytest
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 import synthetic
 from oracle import fem, pbm, solvers
@@ -100,6 +101,44 @@ def test_chebyshev_smoother_error_is_scaled_chebyshev_polynomial(steps):
     T = lambda t: np.polynomial.chebyshev.chebval(t, [0.0] * steps + [1.0])
     p = T((theta - lam) / delta) / T(theta / delta)
     assert np.allclose(x - xs, p * (x0 - xs), rtol=1e-11, atol=1e-12)
+
+
+def test_multicolour_gs_sweep_is_sequential_gauss_seidel_in_colour_order():
+    """On an operator with one unknown per node (a scalar 27-point Q1 stencil: nodes of one colour share no element,
+    so a colour has no internal coupling) a multicolour sweep equals the textbook Gauss-Seidel sweep on the
+    unknowns ordered by colour: x + (L + D)^-1 (b - A x), L the strictly lower triangle in that order."""
+    g = fem.Grid(5, 4, 3, "free")
+    n = g.nnode
+    rng = np.random.default_rng(3)
+    rows, cols, vals = [], [], []
+    ijk = g.node_ijk()
+    for e in g.elem_nodes():
+        w = rng.uniform(0.5, 1.5)
+        for a in e:
+            for b_ in e:
+                rows.append(a)
+                cols.append(b_)
+                vals.append(w * (8.0 if a == b_ else -1.0))
+    A = sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr() + sp.identity(n) * 0.1
+    D = A.diagonal()
+    colours = (ijk[:, 0] % 2) + 2 * (ijk[:, 1] % 2) + 4 * (ijk[:, 2] % 2)
+    b = rng.standard_normal(n)
+    x0 = rng.standard_normal(n)
+    x = solvers.multicolour_gs_sweep(A, D, b, x0, colours, range(8))
+    perm = np.argsort(colours, kind="stable")
+    Ap = A[perm][:, perm]
+    LD = sp.tril(Ap, format="csr")
+    xp = x0[perm] + spla.spsolve_triangular(LD, (b - A @ x0)[perm], lower=True)
+    assert np.allclose(x[perm], xp, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_gauss_seidel_vcycle_is_symmetric_positive_definite(levels):
+    pb, st, S = _S_problem(nx=8, ny=4, nz=4)
+    h = solvers.Hierarchy(pb.grid, S, levels, has_alpha=True, sweeps=1, smoother="gauss_seidel")
+    M = _vcycle_matrix(h, S.shape[0])
+    assert np.max(np.abs(M - M.T)) < 1e-10 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
 
 
 def test_fixed_weight_06_is_indefinite_on_S():
