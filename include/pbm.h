@@ -85,11 +85,12 @@ enum pbm_smoother {        /* smoothing of the multigrid V-cycle (Section 5.2; t
                                    that interval by the Chebyshev polynomial of degree nu (and every
                                    eigenvalue up to 1.5 lambda_k); same operator applications per step as a
                                    Jacobi sweep                                                          */
-    PBM_SMOOTHER_GAUSS_SEIDEL = 2  /* the paper's Gauss-Seidel, made parallel: multicolour sweeps over the 8
-                                   node colours (i mod 2) + 2 (j mod 2) + 4 (k mod 2) (and alpha as a 9th
-                                   for S), x_c += D_c^{-1} (b - A x)_c colour after colour; forward before the
-                                   coarse correction, backward after it. One operator application per colour,
-                                   so 8 (9) per sweep. Not for batched solves.                           */
+    PBM_SMOOTHER_GAUSS_SEIDEL = 2  /* the paper's (point) Gauss-Seidel, made parallel: multicolour sweeps over
+                                   24 dof colours 3 ((i mod 2) + 2 (j mod 2) + 4 (k mod 2)) + component (and
+                                   alpha as a 25th for S), x_c += D_c^{-1} (b - A x)_c colour after colour
+                                   (no two dofs of a colour are coupled); forward before the coarse
+                                   correction, backward after it. One operator application per colour, so
+                                   24 (25) per sweep. Not for batched solves.                            */
 };
 
 typedef struct pbm_grid_desc {

@@ -20,10 +20,10 @@
                     the Lanczos estimate from below may be off by a third. The interval is a reading (the paper
                     smooths with Gauss-Seidel and names no polynomial smoother).
                     The Gauss-Seidel variant (`smoother="gauss_seidel"`, the paper's smoother made parallel) sweeps
-                    the 8 node colours c = (i mod 2) + 2 (j mod 2) + 4 (k mod 2) (and, for S, the extra unknown alpha
-                    as a ninth): x_c += D_c^-1 (b - A x)_c, colour after colour. Nodes of one colour share no element,
-                    so the only coupling inside a colour is between the 3 components of a node (the node's 3 x 3
-                    diagonal block, updated with its diagonal). Pre-smoothing sweeps the colours forward, post-smoothing
+                    24 dof colours 3 ((i mod 2) + 2 (j mod 2) + 4 (k mod 2)) + component (and, for S, the extra
+                    unknown alpha as a 25th): x_c += D_c^-1 (b - A x)_c, colour after colour. Nodes of one node
+                    colour share no element, so no two dofs of one colour are coupled and a sweep is point
+                    Gauss-Seidel in the colour ordering. Pre-smoothing sweeps the colours forward, post-smoothing
                     backward, which keeps the V-cycle symmetric.
   * `direct_solve`— sparse LU (scipy SuperLU) or dense solve.
 """
@@ -217,11 +217,12 @@ class Hierarchy:
 
 
 def node_colours(grid: fem.Grid, has_alpha: bool) -> np.ndarray:
-    """Colour of every unknown: the node colour (i mod 2) + 2 (j mod 2) + 4 (k mod 2) for its 3 dofs, 8 for alpha."""
+    """Colour of every unknown: 3 (node colour) + component, the node colour (i mod 2) + 2 (j mod 2) + 4 (k mod 2);
+    24 for alpha."""
     ijk = grid.node_ijk()
     c = (ijk[:, 0] % 2) + 2 * (ijk[:, 1] % 2) + 4 * (ijk[:, 2] % 2)
-    c = np.repeat(c, 3)
-    return np.concatenate([c, [8]]) if has_alpha else c
+    c = (3 * c[:, None] + np.arange(3)[None, :]).ravel()
+    return np.concatenate([c, [24]]) if has_alpha else c
 
 
 def multicolour_gs_sweep(A, D: np.ndarray, b: np.ndarray, x: np.ndarray, colours: np.ndarray, order) -> np.ndarray:

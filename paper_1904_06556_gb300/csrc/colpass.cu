@@ -370,7 +370,7 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
                 if (c1nz) o -= c1T * yp[c];
                 if (want_dot) pdT += o * bv[c];
             } else {
-                o = (node_colour(I, J, K) == P.mode - EPI_GS0) ? xo[c] + (bv[c] - s[c]) * dv[c] : xo[c];
+                o = (3 * node_colour(I, J, K) + c == P.mode - EPI_GS0) ? xo[c] + (bv[c] - s[c]) * dv[c] : xo[c];
                 if (want_dot) pdT += o * bv[c];
             }
             P.y[d0 + c] = o;
@@ -427,7 +427,7 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
             sd += o * bb;
         } else {
             const double bb = double(P.b[n]);
-            o = P.mode == EPI_GS0 + 8 ? double(xa) + (bb - ya) * double(P.idiag[n]) : double(xa);
+            o = P.mode == EPI_GS0 + kGsColours ? double(xa) + (bb - ya) * double(P.idiag[n]) : double(xa);
             sd += o * bb;
         }
         P.y[n] = T(o);

@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
         }
         __syncthreads();  // (b) corner values of plane k complete
         if (owner) {
-            const bool gs_upd = node_colour(I, J, k) == P.mode - EPI_GS0;   // Gauss-Seidel colour step
+            const int gs_c = P.mode - EPI_GS0 - 3 * node_colour(I, J, k);   // Gauss-Seidel: the component updated
             float2 s01 = make_float2(0.0f, 0.0f);
             float s2 = 0.0f;
 #pragma unroll
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
                     if (want_dot) pdT += o * bb;
                 } else {
                     const float bb = __ldg(P.b + d0 + c);
-                    o = gs_upd ? xo[c] + (bb - s[c]) * __ldg(P.idiag + d0 + c) : xo[c];
+                    o = gs_c == c ? xo[c] + (bb - s[c]) * __ldg(P.idiag + d0 + c) : xo[c];
                     if (want_dot) pdT += o * bb;
                 }
                 P.y[d0 + c] = o;
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
             sd += o * bb;
         } else {
             const double bb = double(P.b[n]);
-            o = P.mode == EPI_GS0 + 8 ? double(xa) + (bb - sa) * double(P.idiag[n]) : double(xa);
+            o = P.mode == EPI_GS0 + kGsColours ? double(xa) + (bb - sa) * double(P.idiag[n]) : double(xa);
             sd += o * bb;
         }
         P.y[n] = float(o);
@@ -644,7 +644,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
         if (q < 4) sq[q * EC + col] = make_float4(ob[0], ob[1], ob[2], 0.0f);
         __syncthreads();  // (b) corner values of plane k complete
         if (owner) {
-            const bool gs_upd = node_colour(I, J, k) == P.mode - EPI_GS0;   // Gauss-Seidel colour step
+            const int gs_c = P.mode - EPI_GS0 - 3 * node_colour(I, J, k);   // Gauss-Seidel: the component updated
             float s3[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
             for (int dj = 1; dj >= 0; --dj)
@@ -689,7 +689,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
                     if (want_dot) pdT += o * bb;
                 } else {
                     const float bb = __ldg(P.b + d0 + c);
-                    o = gs_upd ? xo[c] + (bb - s3[c]) * __ldg(P.idiag + d0 + c) : xo[c];
+                    o = gs_c == c ? xo[c] + (bb - s3[c]) * __ldg(P.idiag + d0 + c) : xo[c];
                     if (want_dot) pdT += o * bb;
                 }
                 P.y[d0 + c] = o;
@@ -740,7 +740,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
             sd += o * bb;
         } else {
             const double bb = double(P.b[n]);
-            o = P.mode == EPI_GS0 + 8 ? double(xa) + (bb - ya) * double(P.idiag[n]) : double(xa);
+            o = P.mode == EPI_GS0 + kGsColours ? double(xa) + (bb - ya) * double(P.idiag[n]) : double(xa);
             sd += o * bb;
         }
         P.y[n] = float(o);

@@ -313,10 +313,12 @@ void dfree(void* p);
 // EPI_CHEB: one step of Chebyshev acceleration of Jacobi, y = c0 x - c1 y_prev + c2 D^{-1} (b - A x)
 // with (c0, c1, c2) = (1 + a_s, a_s or 0, b_s) read from ApplyArgs::omega, y_prev the iterate before x,
 // read from y itself before it is overwritten (not read when c1 = 0)
-// EPI_GS0 + c (c = 0 .. 8): one colour step of a multicolour Gauss-Seidel sweep: y = x + D^{-1} (b - A x) on the
-// nodes of colour c = (i & 1) | (j & 1) << 1 | (k & 1) << 2 (c = 8: the alpha entry of S), y = x elsewhere
+// EPI_GS0 + c (c = 0 .. 24): one colour step of a multicolour Gauss-Seidel sweep: y = x + D^{-1} (b - A x) on the
+// dofs of colour c = 3 node_colour + component (c = 24: the alpha entry of S), y = x elsewhere; no two dofs of
+// one colour are coupled, so a sweep is point Gauss-Seidel in the colour ordering
 enum EpiMode { EPI_APPLY = 0, EPI_RESID = 1, EPI_JACOBI = 2, EPI_CHEB = 3, EPI_GS0 = 4 };
 __host__ __device__ inline int node_colour(int i, int j, int k) { return (i & 1) | ((j & 1) << 1) | ((k & 1) << 2); }
+constexpr int kGsColours = 24;   // dof colours; alpha is colour 24
 // slot of step s >= 1 (from_zero: the step after a first step taken from x = 0) in DevScalars::cheb[k]
 constexpr int kChebMaxStep = 8;
 inline int cheb_slot(int s, bool from_zero) { return 4 * (2 * (s - 1) + (from_zero ? 1 : 0)); }

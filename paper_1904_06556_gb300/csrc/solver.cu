@@ -60,7 +60,7 @@ static size_t esz(bool fp32) { return fp32 ? sizeof(float) : sizeof(double); }
 void vcycle(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, void* x, int dot_slot, cudaStream_t st,
             bool first_done);
 
-// V-cycle with multicolour Gauss-Seidel smoothing: every sweep is one operator launch per colour (8 node
+// V-cycle with multicolour Gauss-Seidel smoothing: every sweep is one operator launch per colour (24 dof
 // colours, and alpha last for S) with the EPI_GS0 + c epilogue, forward before the coarse correction and
 // backward after it; pre-smoothing starts from x = 0 (no sweep is fused into the restriction)
 static void vcycle_gs(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, void* x, int dot_slot,
@@ -71,7 +71,7 @@ static void vcycle_gs(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, v
     void* t = fp32 ? (void*)L.t32 : (void*)L.t64;
     void* r = fp32 ? (void*)L.r32 : (void*)L.r64;
     const void* D = fp32 ? (const void*)L.idiag32 : (const void*)L.idiag64;
-    const int ncol = op_s ? 9 : 8;
+    const int ncol = op_s ? kGsColours + 1 : kGsColours;
     const int pre = g->desc.pre_sweeps, post = g->desc.post_sweeps;
     vec_zero(x, nv * es, st);
     void* cur = x;

@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
         if (s_abort) break;
         if (k < kz0) continue;
         if (owner) {
-            const bool gs_upd = node_colour(I, J, k) == mode - EPI_GS0;   // Gauss-Seidel colour step
+            const int gs_c = mode - EPI_GS0 - 3 * node_colour(I, J, k);   // Gauss-Seidel: the component updated
             const float4 o = sq_r[buf * EYT * EXT];
             float s3[3] = {n0[0] + o.x, n0[1] + o.y, n0[2] + o.z};
             if (ofixed) {
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
                     if (want_dot) pdT += o3 * bb;
                 } else {
                     const float bb = __ldg(P.b + d0 + c);
-                    o3 = gs_upd ? xo[c] + (bb - s3[c]) * __ldg(P.idiag + d0 + c) : xo[c];
+                    o3 = gs_c == c ? xo[c] + (bb - s3[c]) * __ldg(P.idiag + d0 + c) : xo[c];
                     if (want_dot) pdT += o3 * bb;
                 }
                 P.y[d0 + c] = o3;
@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
             sd += o * bb;
         } else {
             const double bb = double(P.b[n]);
-            o = mode == EPI_GS0 + 8 ? double(xa) + (bb - sa) * double(P.idiag[n]) : double(xa);
+            o = mode == EPI_GS0 + kGsColours ? double(xa) + (bb - sa) * double(P.idiag[n]) : double(xa);
             sd += o * bb;
         }
         P.y[n] = float(o);

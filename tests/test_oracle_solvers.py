@@ -132,6 +132,32 @@ def test_multicolour_gs_sweep_is_sequential_gauss_seidel_in_colour_order():
     assert np.allclose(x[perm], xp, rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("has_alpha", [False, True])
+def test_dof_colouring_sweep_is_point_gauss_seidel_on_elasticity(has_alpha):
+    """With the 24 dof colours (and alpha as the 25th) no two unknowns of a colour are coupled in K or S, so the
+    multicolour sweep of the V-cycle is exactly point Gauss-Seidel on the unknowns ordered by colour."""
+    if has_alpha:
+        pb, st, A = _S_problem(nx=6, ny=4, nz=4)
+        g = pb.grid
+    else:
+        g = fem.Grid(6, 4, 4, "bridge_corners")
+        w = np.random.default_rng(2).uniform(1e-3, 1.0, g.m)
+        A = fem.assemble_K(g, w, fem.element_stiffness())
+    A = sp.csr_matrix(A)
+    colours = solvers.node_colours(g, has_alpha)
+    same = colours[:, None] == colours[None, :]
+    Ad = A.toarray()
+    assert np.all(Ad[same & ~np.eye(len(colours), dtype=bool)] == 0.0)
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal(A.shape[0])
+    x0 = rng.standard_normal(A.shape[0])
+    x = solvers.multicolour_gs_sweep(A, A.diagonal(), b, x0, colours, range(int(colours.max()) + 1))
+    perm = np.argsort(colours, kind="stable")
+    LD = sp.tril(A[perm][:, perm], format="csr")
+    xp = x0[perm] + spla.spsolve_triangular(LD, (b - A @ x0)[perm], lower=True)
+    assert np.allclose(x[perm], xp, rtol=1e-10, atol=1e-10 * np.abs(xp).max())
+
+
 @pytest.mark.parametrize("levels", [2, 3])
 def test_gauss_seidel_vcycle_is_symmetric_positive_definite(levels):
     pb, st, S = _S_problem(nx=8, ny=4, nz=4)
