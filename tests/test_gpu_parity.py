@@ -440,7 +440,7 @@ def test_vcycle_K_matches_oracle(pkg, dims, bc, levels, smoother, sweeps):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_gauss_seidel_smoother_fp32_and_solves(pkg, precision):
-    """Multicolour Gauss-Seidel smoothing (one launch per colour, alpha as the ninth): the FP32 V-cycle on mixed
+    """Multicolour point Gauss-Seidel smoothing (one launch per dof colour, alpha as the 25th): the FP32 V-cycle on mixed
     grids (fine single pass, coarse kernels, and the tensor-core plan) against the oracle's; MINRES solves reach
     the oracle's direct solution; batches refuse it."""
     dims, bc, levels = (16, 8, 8), "cantilever", 3
