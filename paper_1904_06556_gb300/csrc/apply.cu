@@ -25,7 +25,8 @@ struct MarchParams {
     int nx, ny, nz, support, DZ;
     int64_t n, m;
     const T* x;        // gathered input (n (+1))
-    const T* u;        // second gathered vector (fine S: u; fine diag S: u)
+    const T* u;        // second gathered vector (fine S: u)
+    const T* what_hat; // Khat H u_e of every fine element, [21][m] (fine diag S)
     const T* w;        // element weights (fine)
     const T* d;        // Schur weights (fine S)
     const T* A;        // coarse element matrices (upper triangle, entry-major)
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(32 * BY) k_march(MarchParams<T> P) {
     constexpr int BX = 32;
     constexpr int NT = BX * BY;
     constexpr bool GX = (KIND == K_FINE_K || KIND == K_FINE_S || KIND == K_COARSE);
-    constexpr bool GU = (KIND == K_FINE_S || KIND == K_FINE_DIAG_S);
+    constexpr bool GU = (KIND == K_FINE_S);   // the fine diagonal of S reads K_e u_e from the W_e table
     constexpr bool DIAG = (KIND == K_FINE_DIAG_K || KIND == K_FINE_DIAG_S || KIND == K_COARSE_DIAG);
     __shared__ T sx[GX ? 2 : 1][3][BY + 1][BX + 1];
     __shared__ T su[GU ? 2 : 1][3][BY + 1][BX + 1];
@@ -219,9 +220,13 @@ __global__ void __launch_bounds__(32 * BY) k_march(MarchParams<T> P) {
                     for (int a = 0; a < 8; ++a) ye[c][a] = we * T(P.Kdiag);
             } else if (KIND == K_FINE_DIAG_S) {
                 const T we = ldv(P.w, e), de = ldv(P.d, e);
+                // Khat H u_e from the table of the S pass (built from the masked u just before)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) wht_fwd(ue[c]);
-                khat_apply(P.K, ue, ye);
+                for (int c = 0; c < 3; ++c) {
+                    ye[c][0] = T(0);
+#pragma unroll
+                    for (int q = 1; q < 8; ++q) ye[c][q] = ldv(P.what_hat, int64_t(7 * c + q - 1) * P.m + e);
+                }
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     wht_out(ye[c]);
@@ -488,7 +493,7 @@ void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st, int rset) {
         P.w = op_s ? g->w64 : g->rho;
         if (op_s) {
             P.d = g->d64;
-            P.u = g->u64;
+            P.what_hat = g->what_hat;   // filled by launch_what_hat before the diagonal
             run<double, K_FINE_DIAG_S>(g, 0, P, st, "fine diag S");
         } else {
             run<double, K_FINE_DIAG_K>(g, 0, P, st, "fine diag K");
