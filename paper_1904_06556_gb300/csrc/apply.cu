@@ -1,47 +1,36 @@
-// Operator applications on a structured grid: K(w) x, S x (eq. (S)), explicit coarse Galerkin
-// operators, their Jacobi diagonals, and fused residual / damped-Jacobi epilogues.
+// Jacobi diagonals of the operators on a structured grid (the fine K(w) and S of eq. (S), and the
+// stored coarse Galerkin operators), and the launch wrappers of the operator applications.
 //
-// All of them share one "marching" kernel. A CTA of 32 x BY threads covers 31 x (BY - 1) node
+// The diagonals share one "marching" kernel. A CTA of 32 x BY threads covers 31 x (BY - 1) node
 // columns of the grid and walks up a chunk of node planes in z. Thread (tx, ty) computes the
-// element whose upper corner (in x and y) is its own node column, one element layer per step:
-//   * the node values of the plane just above are staged in shared memory (with a one-node halo
-//     in -x and -y, loaded by the first row / column of threads);
-//   * the element result is split into its 4 bottom and 4 top corners: the top corners are kept in
-//     registers and added to the next layer's bottom corners (same element column), so each node
-//     plane is completed after two element layers;
+// diagonal contributions of the element whose upper corner (in x and y) is its own node column, one
+// element layer per step:
+//   * the element's contributions are split into its 4 bottom and 4 top corners: the top corners are
+//     kept in registers and added to the next layer's bottom corners (same element column), so each
+//     node plane is completed after two element layers;
 //   * the 4 elements around a node column exchange their corner sums through shared memory and the
 //     owning thread writes the node once: no atomics, and a fixed summation order (deterministic).
-// Elements on CTA borders are computed twice (by the two CTAs that share them); the alpha-row sum
-// counts each element once. Every launch finishes with a last-block-done reduction of the per-CTA
-// partial sums in a fixed order.
+// Elements on CTA borders are computed twice (by the two CTAs that share them); the alpha entry of S
+// (sum_i d_i) counts each element once and is finished by the last CTA from the per-CTA partial sums
+// in a fixed order.
 #include "pbm_internal.h"
 
 namespace pbm {
 
-enum Kind { K_FINE_K = 0, K_FINE_S = 1, K_FINE_DIAG_K = 2, K_FINE_DIAG_S = 3, K_COARSE = 4, K_COARSE_DIAG = 5 };
+enum Kind { K_FINE_DIAG_K = 2, K_FINE_DIAG_S = 3, K_COARSE_DIAG = 5 };
 
 template <class T>
 struct MarchParams {
     int nx, ny, nz, support, DZ;
     int64_t n, m;
-    const T* x;        // gathered input (n (+1))
-    const T* u;        // second gathered vector (fine S: u)
-    const T* what_hat; // Khat H u_e of every fine element, [21][m] (fine diag S)
-    const T* w;        // element weights (fine)
-    const T* d;        // Schur weights (fine S)
+    const T* w;        // element weights (fine level)
+    const T* d;        // Schur weights (fine diagonal of S)
+    const T* what_hat; // Khat H u_e of every fine element, [21][m] (fine diagonal of S)
     const T* A;        // coarse element matrices (upper triangle, entry-major)
-    const T* bord;     // coarse alpha border (n)
-    double s_alpha;    // coarse S_alpha,alpha of the diagonal kinds (set-up)
-    const double* s_alpha_dev;  // coarse S_alpha,alpha of the applies (device scalar)
-    T* y;
-    const T* b;
-    const T* diag;     // inverse Jacobi diagonal (JACOBI)
-    const double* omega;
-    int mode;
+    double s_alpha;    // S_alpha,alpha of a coarse level (the alpha entry of its diagonal)
+    T* y;              // the diagonal, n (+ 1) entries
     int with_alpha;
-    int dot_slot;
-    double Kdiag;
-    KeHatT<T> K;
+    double Kdiag;      // K_e[i][i] of the fine element matrix
     double* partials;  // 2 * nblocks
     DevScalars* sc;
     unsigned int* counter;  // last-CTA counter
@@ -81,11 +70,6 @@ template <class T, int BY, int KIND>
 __global__ void __launch_bounds__(32 * BY) k_march(MarchParams<T> P) {
     constexpr int BX = 32;
     constexpr int NT = BX * BY;
-    constexpr bool GX = (KIND == K_FINE_K || KIND == K_FINE_S || KIND == K_COARSE);
-    constexpr bool GU = (KIND == K_FINE_S);   // the fine diagonal of S reads K_e u_e from the W_e table
-    constexpr bool DIAG = (KIND == K_FINE_DIAG_K || KIND == K_FINE_DIAG_S || KIND == K_COARSE_DIAG);
-    __shared__ T sx[GX ? 2 : 1][3][BY + 1][BX + 1];
-    __shared__ T su[GU ? 2 : 1][3][BY + 1][BX + 1];
     __shared__ T sacc[3][3][BY][BX];
     __shared__ double sred[2 * NT / 32];
     __shared__ bool s_last;
@@ -102,117 +86,18 @@ __global__ void __launch_bounds__(32 * BY) k_march(MarchParams<T> P) {
     const int kz1 = min(kz0 + P.DZ, nz + 1);
     const int64_t sxn = nx + 1, sxy = int64_t(nx + 1) * (ny + 1);
 
-    T xa = T(0);
-    if (GX && P.with_alpha) xa = P.x[P.n];
-    const double om = (!DIAG && P.mode == EPI_JACOBI) ? *P.omega : 0.0;
-
-    auto fetch = [&](const T* v, int i, int j, int k, T* out3, bool& fixed) {
-        fixed = false;
-        if (i < 0 || i > nx || j < 0 || j > ny || k < 0 || k > nz) {
-            out3[0] = out3[1] = out3[2] = T(0);
-            return;
-        }
-        fixed = node_fixed(P.support, nx, ny, nz, i, j, k);
-        const int64_t nd = 3 * (i + sxn * j + sxy * k);
-        out3[0] = ldv(v, nd);
-        out3[1] = ldv(v, nd + 1);
-        out3[2] = ldv(v, nd + 2);
-    };
-    // stage plane `pl` of vector v into buffer s[(pl & 1)], masked; own node unmasked into own3
-    auto stage = [&](const T* v, T (*s)[3][BY + 1][BX + 1], int pl, T* own3) {
-        const int bf = pl & 1;
-        T t3[3];
-        bool fx;
-        fetch(v, Ix, Iy, pl, t3, fx);
-        own3[0] = t3[0];
-        own3[1] = t3[1];
-        own3[2] = t3[2];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) s[bf][c][ty + 1][tx + 1] = fx ? T(0) : t3[c];
-        if (tx == 0) {
-            fetch(v, Ix - 1, Iy, pl, t3, fx);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) s[bf][c][ty + 1][0] = fx ? T(0) : t3[c];
-        }
-        if (ty == 0) {
-            fetch(v, Ix, Iy - 1, pl, t3, fx);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) s[bf][c][0][tx + 1] = fx ? T(0) : t3[c];
-        }
-        if (tx == 0 && ty == 0) {
-            fetch(v, Ix - 1, Iy - 1, pl, t3, fx);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) s[bf][c][0][0] = fx ? T(0) : t3[c];
-        }
-    };
-
-    T xown[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
-    T uown[3];
-    if (GX) stage(P.x, sx, kz0 - 1, xown[(kz0 - 1) & 1]);
-    if (GU) stage(P.u, su, kz0 - 1, uown);
-
     T carry[4][3];
 #pragma unroll
     for (int a = 0; a < 4; ++a) carry[a][0] = carry[a][1] = carry[a][2] = T(0);
-    double part_alpha = 0.0, part_dot = 0.0;
+    double part_alpha = 0.0, part_zero = 0.0;
 
     for (int k = kz0 - 1; k < kz1; ++k) {
-        // stage the plane above this element layer
-        if (GX) stage(P.x, sx, k + 1, xown[(k + 1) & 1]);
-        if (GU) stage(P.u, su, k + 1, uown);
-        __syncthreads();
-
+        __syncthreads();   // the owners have read the previous plane's corner sums
         T ye[3][8];
         const bool ev = ecol && k >= 0 && k < nz;
         if (ev) {
             const int64_t e = ex + int64_t(nx) * (ey + int64_t(ny) * k);
-            T xe[3][8], ue[3][8];
-#pragma unroll
-            for (int a = 0; a < 8; ++a) {
-                const int ix = a & 1, iy = (a >> 1) & 1, iz = (a >> 2) & 1;
-                const int bf = (k + iz) & 1;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    if (GX) xe[c][a] = sx[bf][c][ty + iy][tx + ix];
-                    if (GU) ue[c][a] = su[bf][c][ty + iy][tx + ix];
-                }
-            }
-            if (KIND == K_FINE_K) {
-                const T we = ldv(P.w, e);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) wht_fwd(xe[c]);
-                khat_apply(P.K, xe, ye);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) ye[c][q] *= we;
-                    wht_out(ye[c]);
-                }
-            } else if (KIND == K_FINE_S) {
-                const T we = ldv(P.w, e), de = ldv(P.d, e);
-                T W[3][8];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) wht_fwd(ue[c]);
-                khat_apply(P.K, ue, W);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) wht_fwd(xe[c]);
-                T dot = T(0);
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-#pragma unroll
-                    for (int q = 1; q < 8; ++q) dot += W[c][q] * xe[c][q];
-                // H^T Y . H^{-1}: in the transformed basis u . v = (H u) . (H^{-T} v); with
-                // v = H^T V this is U . V, so w_e . x_e = (H^T W) . x_e = W . (H x_e) = W . X
-                const T t = de * (dot - xa);
-                khat_apply(P.K, xe, ye);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) ye[c][q] = we * ye[c][q] + t * W[c][q];
-                    wht_out(ye[c]);
-                }
-                if (designated && k >= kz0) part_alpha -= double(t);
-            } else if (KIND == K_FINE_DIAG_K) {
+            if (KIND == K_FINE_DIAG_K) {
                 const T we = ldv(P.w, e);
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
@@ -234,22 +119,6 @@ __global__ void __launch_bounds__(32 * BY) k_march(MarchParams<T> P) {
                     for (int a = 0; a < 8; ++a) ye[c][a] = we * T(P.Kdiag) + de * ye[c][a] * ye[c][a];
                 }
                 if (designated && k >= kz0) part_alpha += double(de);
-            } else if (KIND == K_COARSE) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-#pragma unroll
-                    for (int a = 0; a < 8; ++a) ye[c][a] = T(0);
-                const T* Ae = P.A + e;
-                const int64_t m = P.m;
-#pragma unroll
-                for (int i = 0; i < 24; ++i) {
-#pragma unroll
-                    for (int j = i; j < 24; ++j) {
-                        const T a = ldv(Ae, int64_t(tri_index(i, j)) * m);
-                        ye[i % 3][i / 3] += a * xe[j % 3][j / 3];
-                        if (i != j) ye[j % 3][j / 3] += a * xe[i % 3][i / 3];
-                    }
-                }
             } else {  // K_COARSE_DIAG
                 const T* Ae = P.A + e;
                 const int64_t m = P.m;
@@ -279,57 +148,22 @@ __global__ void __launch_bounds__(32 * BY) k_march(MarchParams<T> P) {
         __syncthreads();
 
         if (owner && k >= kz0 && k <= nz) {
-            T yv[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                yv[c] = acc[3][c] + sacc[2][c][ty][tx + 1] + sacc[1][c][ty + 1][tx] + sacc[0][c][ty + 1][tx + 1];
             const int64_t nd = 3 * (Ix + sxn * Iy + sxy * k);
             const bool fixed = node_fixed(P.support, nx, ny, nz, Ix, Iy, k);
-            const T* xo = xown[k & 1];
-            if (DIAG) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) P.y[nd + c] = fixed ? T(1) : yv[c];
-            } else {
-                if (KIND == K_COARSE && P.with_alpha) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const T bc = ldv(P.bord, nd + c);
-                        yv[c] += bc * xa;
-                        part_alpha += double(bc) * double(xo[c]);
-                    }
-                }
-                if (fixed) {
-                    yv[0] = xo[0];
-                    yv[1] = xo[1];
-                    yv[2] = xo[2];
-                }
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    T o;
-                    if (P.mode == EPI_APPLY) {
-                        o = yv[c];
-                        part_dot += double(o) * double(xo[c]);
-                    } else if (P.mode == EPI_RESID) {
-                        o = ldv(P.b, nd + c) - yv[c];
-                        part_dot += double(o) * double(o);
-                    } else {
-                        const T bb = ldv(P.b, nd + c);
-                        o = xo[c] + T(om) * ((bb - yv[c]) * ldv(P.diag, nd + c));
-                        part_dot += double(o) * double(bb);
-                    }
-                    P.y[nd + c] = o;
-                }
+            for (int c = 0; c < 3; ++c) {
+                const T yv = acc[3][c] + sacc[2][c][ty][tx + 1] + sacc[1][c][ty + 1][tx] + sacc[0][c][ty + 1][tx + 1];
+                P.y[nd + c] = fixed ? T(1) : yv;   // identity rows of the supported dofs
             }
         }
     }
 
-    // per-CTA partials, then the last CTA reduces them in order and finishes the alpha entry
-    block_sum2<NT>(part_alpha, part_dot, sred);
+    // per-CTA partials, then the last CTA reduces them in order and writes the alpha entry
+    block_sum2<NT>(part_alpha, part_zero, sred);
     const int nblk = gridDim.x * gridDim.y * gridDim.z;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     if (tx == 0 && ty == 0) {
         P.partials[bid] = part_alpha;
-        P.partials[nblk + bid] = part_dot;
         __threadfence();
         const unsigned t = atomicAdd(P.counter, 1u);
         s_last = (t == unsigned(nblk - 1));
@@ -337,38 +171,13 @@ __global__ void __launch_bounds__(32 * BY) k_march(MarchParams<T> P) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    double sa = 0.0, sd = 0.0;
+    double sa = 0.0, sz = 0.0;
     const int tid = tx + BX * ty;
-    for (int i = tid; i < nblk; i += NT) {
-        sa += ((volatile double*)P.partials)[i];
-        sd += ((volatile double*)P.partials)[nblk + i];
-    }
-    block_sum2<NT>(sa, sd, sred);
+    for (int i = tid; i < nblk; i += NT) sa += ((volatile double*)P.partials)[i];
+    block_sum2<NT>(sa, sz, sred);
     if (tid == 0) {
         *P.counter = 0u;
-        const int64_t n = P.n;
-        if (DIAG) {
-            if (P.with_alpha) P.y[n] = T(KIND == K_COARSE_DIAG ? P.s_alpha : (KIND == K_FINE_DIAG_S ? sa : 1.0));
-        } else {
-            if (P.with_alpha) {
-                double ya = sa;
-                if (KIND == K_COARSE) ya += *P.s_alpha_dev * double(xa);
-                double o;
-                if (P.mode == EPI_APPLY) {
-                    o = ya;
-                    sd += o * double(xa);
-                } else if (P.mode == EPI_RESID) {
-                    o = double(P.b[n]) - ya;
-                    sd += o * o;
-                } else {
-                    const double bb = double(P.b[n]);
-                    o = double(xa) + om * ((bb - ya) * double(P.diag[n]));
-                    sd += o * bb;
-                }
-                P.y[n] = T(o);
-            }
-            if (P.dot_slot >= 0) P.sc->red[P.dot_slot] = sd;
-        }
+        if (P.with_alpha) P.y[P.n] = T(KIND == K_COARSE_DIAG ? P.s_alpha : (KIND == K_FINE_DIAG_S ? sa : 1.0));
     }
 }
 
@@ -414,9 +223,7 @@ static MarchParams<T> base_params(pbm_grid* g, int k, int rset = 0) {
     P.partials = r.partials;
     P.sc = g->sc;
     P.counter = r.counter;
-    P.dot_slot = -1;
     P.Kdiag = g->Kdiag;
-    fill_khat(P.K, g->kehat);
     return P;
 }
 
@@ -429,18 +236,6 @@ static void run(pbm_grid* g, int k, MarchParams<T>& P, cudaStream_t st, const ch
     // (every reduction set holds at least 2 max_blocks partial sums)
     k_march<T, BY_, KIND><<<grid, dim3(32, BY_), 0, st>>>(P);
     PBM_LAUNCH(what);
-}
-
-template <class T>
-static void set_epi(MarchParams<T>& P, const ApplyArgs& a) {
-    P.x = (const T*)a.x;
-    P.y = (T*)a.y;
-    P.b = (const T*)a.b;
-    P.diag = (const T*)a.diag;
-    P.omega = a.omega;
-    P.mode = a.mode;
-    P.with_alpha = a.with_alpha ? 1 : 0;
-    P.dot_slot = a.dot_slot;
 }
 
 // Fine-level operator applications: FP64 runs the two-pass column kernels (colpass.cu) with the
@@ -485,7 +280,6 @@ void launch_coarse(pbm_grid* g, int k, bool fp32, const ApplyArgs& a, cudaStream
 void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st, int rset) {
     Level& L = g->L[k];
     auto P = base_params<double>(g, k, rset);
-    P.mode = EPI_APPLY;
     P.with_alpha = 1;
     P.y = L.diag64;
     P.s_alpha = g->s_alpha;

@@ -23,8 +23,6 @@ void launch_dot(pbm_grid* g, bool fp32, const void* a, const void* b, int64_t n,
 int solve(pbm_grid* g, bool op_s, const double* b, double* x, double rtol, int maxit, pbm_solve_info* info,
           cudaStream_t st);
 
-constexpr int VBB = 256;  // threads of the batched vector stages
-
 __device__ __forceinline__ int mr_exit_reason_b(const double* mr, double target, double it, double budget) {
     if (mr[13] == 1.0) return 1;
     if (mr[13] == 2.0 || mr[1] == 0.0) return 2;

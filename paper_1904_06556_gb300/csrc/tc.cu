@@ -51,13 +51,6 @@ namespace {
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
 
-// shared-memory matrix descriptor of tcgen05.mma without swizzling: start address, byte offset of
-// the second core matrix of a K step (LBO) and of the next group of 8 rows (SBO), descriptor version 1
-__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return uint64_t((addr & 0x3FFFFu) >> 4) | (uint64_t(lbo >> 4) << 16) | (uint64_t(sbo >> 4) << 32) |
-           (uint64_t(1) << 46);
-}
-
 // instruction descriptor: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9, 10-12 = 2), both K-major,
 // N / 8 in bits 17-22, M / 16 in bits 24-28; M = 128, N = 32
 constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
@@ -325,8 +318,10 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    // descriptor words: start address / 16 in bits 0-13 of the low word, LBO / 16 in bits 16-29; SBO / 16
-    // in bits 0-13 of the high word and the version (bit 46) in its bit 14. A: LBO 16, SBO 144; B: LBO
+    // shared-memory matrix descriptors of tcgen05.mma without swizzling, as two 32-bit words: start address
+    // / 16 in bits 0-13 of the low word, LBO / 16 (byte offset of the second core matrix of a K step) in
+    // bits 16-29; SBO / 16 (byte offset of the next group of 8 rows) in bits 0-13 of the high word and the
+    // descriptor version 1 (bit 46) in its bit 14. A: LBO 16, SBO 144; B: LBO
     // 128, SBO 1024. Offsets below are in 16-byte units.
     const uint32_t aLo = (smem_addr(stg) >> 4) | (1u << 16), bLo = (smem_addr(sB) >> 4) | (8u << 16);
     constexpr uint32_t aHi = 9u | (1u << 14), bHi = 64u | (1u << 14);
