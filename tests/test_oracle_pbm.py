@@ -179,6 +179,73 @@ def _primal_reference(pb):
     return res.x, res.fun
 
 
+# ---------------------------------------------------------------------------------------------------------------
+# the Newton stopping measure res_PBM (eq. resIP)
+# ---------------------------------------------------------------------------------------------------------------
+
+def test_res_pbm_hand_computed_state():
+    """res_PBM on a 2x1x1 cantilever state whose three terms follow by hand from eq. (resIP), the gradient of
+    eq. (lagr_grad_a) and the log branch of eq. (103.1) (tau_hat = -1/2: phi'(t) = -1/(4t)).
+
+    u = 0, alpha = 1, nu_lo = nu_up = 1, p = q = 1, rho = 0.4, mu = 1, rho_lo = 1e-3, rho_up = 1, V = 0.6:
+      * res_1 = -f (u = 0), so ||res_1|| / ||f|| = 1;
+      * s_i = (0 - 1 + 1 - 1) / 1 = -1, phi'(-1) = 1/4, rho'_i = 0.1; res_2 = V - sum rho' = 0.4, |res_2| / V = 2/3;
+      * mu'_lo = phi'(-1) = 1/4, res_3_i = -rho_lo + rho'_i - mu'_lo = -0.151 for both elements, so
+        ||res_3|| / (||rho_lo e|| + ||rho_up e||) = 0.151 sqrt(2) / (1.001 sqrt(2)).
+    A normalisation by m instead of ||.||_2 of the bound vectors, the +rho_lo sign printed in res_3, or res_4 in
+    place of res_3 each change the value in the third digit."""
+    g = fem.Grid(2, 1, 1, "cantilever")
+    f = synthetic.load_vector(2, 1, 1, "end_edge")
+    pb = pbm.Problem(g, f, 0.6, 1e-3, 1.0)
+    m = g.m
+    st = pbm.State(np.zeros(g.n), 1.0, np.ones(m), np.ones(m), np.full(m, 0.4), np.ones(m), np.ones(m))
+    expected = 1.0 + 2.0 / 3.0 + 0.151 / 1.001
+    assert abs(pbm.res_pbm(pb, st) - expected) < 1e-13 * expected
+
+
+@pytest.mark.parametrize("seed,u_scale", [(0, 1.0), (4, 0.2)])
+def test_res_pbm_from_finite_difference_gradient(seed, u_scale):
+    """eq. (resIP) with res_1, res_2, res_3 taken as central finite differences of the augmented Lagrangian
+    (not from the oracle's gradient): ||dL/du|| / ||f|| + |dL/dalpha| / V + ||dL/dnu_lo|| / (||rho_lo|| + ||rho_up||),
+    the bound vectors of length m with 2-norms sqrt(m) |rho_lo|, sqrt(m) |rho_up|."""
+    pb, st = _tiny(seed=seed, u_scale=u_scale)
+    v, free = _pack(pb, st)
+    h = 1e-6
+    fd = np.empty_like(v)
+    for k in range(v.size):
+        e = np.zeros_like(v)
+        e[k] = h
+        fd[k] = (pbm.lagrangian(pb, _unpack(pb, st, v + e, free))
+                 - pbm.lagrangian(pb, _unpack(pb, st, v - e, free))) / (2 * h)
+    nf, m = free.size, pb.m
+    r1, r2, r3 = fd[:nf], fd[nf], fd[nf + 1:nf + 1 + m]
+    bound_norms = np.linalg.norm(np.full(m, pb.rho_lo)) + np.linalg.norm(np.full(m, pb.rho_up))
+    expected = np.linalg.norm(r1) / np.linalg.norm(pb.f) + abs(r2) / pb.V + np.linalg.norm(r3) / bound_norms
+    assert abs(pbm.res_pbm(pb, st) - expected) < 1e-7 * expected
+
+
+def test_res_pbm_vanishes_at_a_stationary_point():
+    """At a minimiser of the augmented Lagrangian (Newton with direct solves run to convergence) res_PBM is zero up
+    to rounding, and so is the finite-difference gradient of L there."""
+    nx, ny, nz = 4, 2, 2
+    g = fem.Grid(nx, ny, nz, "cantilever")
+    f = synthetic.load_vector(nx, ny, nz, "end_edge")
+    pb = pbm.Problem(g, f, 0.3 * g.m, 1e-3, 1.0)
+    m = g.m
+    st0 = pbm.State(np.zeros(g.n), 1.0, np.ones(m), np.ones(m), np.full(m, 0.3), np.ones(m), np.ones(m))
+    st, info, _ = pbm.newton(pb, st0, eps_nwt=1e-12, eps_mr=None, max_iter=60)
+    assert pbm.res_pbm(pb, st) < 1e-11
+    v, free = _pack(pb, st)
+    h = 1e-6
+    for k in np.random.default_rng(0).choice(v.size, 12, replace=False):
+        e = np.zeros_like(v)
+        e[k] = h
+        d = (pbm.lagrangian(pb, _unpack(pb, st, v + e, free)) - pbm.lagrangian(pb, _unpack(pb, st, v - e, free)))
+        assert abs(d / (2 * h)) < 1e-6
+    # away from it the measure is not small
+    assert pbm.res_pbm(pb, st0) > 0.1
+
+
 @pytest.fixture(scope="module")
 def pbm_run():
     nx, ny, nz = 4, 2, 2
