@@ -468,21 +468,24 @@ int pbm_batch_minres_solve(pbm_batch* b, const double* const* b_dev, double* con
                            pbm_solve_info* infos, void* stream);
 
 /* y = K(w) x, exactly as pbm_apply_K computes it (FP64, supported rows and columns the identity),
- * for callers that cannot allocate device memory and so cannot create a grid handle: code running
- * while a CUDA graph is being captured, loops that must not allocate after start-up, or hosts whose
- * own allocator owns all device memory. The paper has no counterpart; this is an interface for
- * such callers. The call allocates nothing (no cudaMalloc, cudaFree or allocating library routine):
- * the scratch of its kernels is one fixed 32 MiB array in the library's device code, which every
- * GPU that loads the library holds until the process exits.
+ * for callers that cannot allocate device memory and so cannot create a grid handle: loops that must
+ * not allocate after start-up, host frameworks whose own allocator owns all device memory, and
+ * plug-ins running inside such hosts. The paper has no counterpart; this is an interface for such
+ * callers. The call allocates nothing (no cudaMalloc, cudaFree or allocating library routine): the
+ * scratch of its kernels is one fixed 32 MiB array in the library's device code, which every GPU that
+ * loads the library holds until the process exits.
  *   nx, ny, nz, support, E, nu, h: the grid as in pbm_grid_desc (no multigrid levels are needed).
- *   w_dev: m FP64 element weights; x_dev, y_dev: n FP64 entries, caller-owned, not overlapping.
+ *   w_dev: m FP64 element weights; x_dev, y_dev: n FP64 entries, caller-owned, not overlapping, all
+ *   three on the current device (the call runs there; arrays on another device are rejected).
  *   stream: as elsewhere (work is enqueued, nothing synchronises).
- * The first call on a device looks up the array's device address on that device; make that first
- * call before any stream capture. Every call shares the array and finds it as the previous call
- * left it, so calls whose work overlaps on the GPU (other streams, other host threads) race and
- * must be serialised by the caller.
- * Errors: PBM_EINVAL (null pointer, bad sizes or material, or a grid whose scratch exceeds the
- * array: roughly more than 170,000 elements), PBM_ECUDA. */
+ * The first call on a device looks up the array's device address on that device and keeps it; make
+ * that first call before any stream capture, and do not call the library again after a
+ * cudaDeviceReset of that device. Every call shares the array and finds it as the previous call left
+ * it, so calls whose work overlaps on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.
+ * Errors: PBM_EINVAL (null pointer, bad sizes or material, arrays that are not device memory of the
+ * current device, or a grid whose scratch exceeds the array: grids of up to about 170,000 elements always fit),
+ * PBM_ECUDA. */
 int pbm_apply_K_noalloc(int nx, int ny, int nz, int support, double E, double nu, double h, const double* w_dev,
                         const double* x_dev, double* y_dev, void* stream);
 

@@ -34,12 +34,17 @@ def kernel_launches() -> int:
 def apply_K_noalloc(nx: int, ny: int, nz: int, support: str, x: torch.Tensor, w: torch.Tensor,
                     out: torch.Tensor | None = None, E: float = 1.0, nu: float = 0.3, h: float = 1.0) -> torch.Tensor:
     """y = K(w) x like Grid.apply_K, for callers that cannot allocate device memory (pbm_apply_K_noalloc): no grid
-    handle, and the library allocates nothing. Pass `out` to avoid the allocation of the result tensor too."""
+    handle, and the library allocates nothing. Pass `out` to avoid the allocation of the result tensor too. x, w and
+    out must be on one CUDA device; the call runs there, on that device's current stream."""
     L = lib()
     n, m = 3 * (nx + 1) * (ny + 1) * (nz + 1), nx * ny * nz
     y = torch.empty_like(x) if out is None else out
-    rc = L.pbm_apply_K_noalloc(nx, ny, nz, _lib.SUPPORTS[support], float(E), float(nu), float(h),
-                               _ptr(w, n=m, name="w"), _ptr(x, n=n, name="x"), _ptr(y, n=n, name="y"), _stream())
+    for name, t in (("w", w), ("out", y)):
+        if t.device != x.device:
+            raise ValueError(f"{name} is on {t.device}, x on {x.device}: all three must be on one device")
+    with torch.cuda.device(x.device):
+        rc = L.pbm_apply_K_noalloc(nx, ny, nz, _lib.SUPPORTS[support], float(E), float(nu), float(h),
+                                   _ptr(w, n=m, name="w"), _ptr(x, n=n, name="x"), _ptr(y, n=n, name="y"), _stream())
     if rc != 0:
         raise PbmError(rc, L.pbm_last_error().decode())
     return y

@@ -191,7 +191,7 @@ static dim3 march_grid(const Geom& g, int& DZ) {
     const int gy = (g.ny + 1 + BY_ - 2) / (BY_ - 1);
     const int planes = g.nz + 1;
     // aim for about 4 CTAs per SM, chunks of at least 4 planes
-    const int want = 152 * 4;
+    const int want = num_sms() * 4;
     int chunks = (want + gx * gy - 1) / (gx * gy);
     chunks = std::max(1, std::min(chunks, (planes + 3) / 4));
     DZ = (planes + chunks - 1) / chunks;
@@ -344,7 +344,7 @@ void launch_elem_energy(pbm_grid* g, const double* u, const double* v, double* o
     KeHatT<double> K;
     fill_khat(K, g->kehat);
     const int64_t m = G.m();
-    int blocks = int(std::min<int64_t>((m + 255) / 256, 152 * 16));
+    int blocks = int(std::min<int64_t>((m + 255) / 256, num_sms() * 16));
     k_elem_energy<<<blocks, 256, 0, st>>>(G.nx, G.ny, G.nz, G.support, u, v ? v : u, out, K);
     PBM_LAUNCH("elem energy");
 }

@@ -42,6 +42,21 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_launch_add(int64_t delta) { g_launches.fetch_add((long long)delta, std::memory_order_relaxed); }
 int64_t launch_count() { return int64_t(g_launches.load(std::memory_order_relaxed)); }
 
+int num_sms() {
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];   // 0: not queried yet
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDev) fail(PBM_EINVAL, "device ordinal out of range");
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        check_cuda(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev), "SM count");
+        if (v <= 0) fail(PBM_ECUDA, "device reports no SMs");
+        cache[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
 // ------------------------------------------------------------------------------------------------
 // profiling of the fine-level operator kernel: an event pair per launch, folded on read
 // ------------------------------------------------------------------------------------------------

@@ -452,10 +452,10 @@ __global__ void __launch_bounds__(NB2) k_nodes_b(const NodeArgs<T>* __restrict__
 // launch wrappers
 // ------------------------------------------------------------------------------------------------
 // chunk length of the fine pass: the longest of 8, 4, 2, 1 layers that still gives every SM
-// sub-partition (152 x 4) at least two warps of columns
+// sub-partition (4 per SM) at least two warps of columns
 static int fine_chunk(const Geom& G) {
     const int64_t ncol = int64_t(G.nx) * G.ny;
-    const int64_t want = 152LL * 4 * 32 * 2;
+    const int64_t want = int64_t(num_sms()) * 4 * 32 * 2;
     for (int L = 8; L > 1; L >>= 1)
         if (ncol * ((G.nz + L - 1) / L) >= want) return L;
     return 1;
@@ -490,7 +490,7 @@ NodeArgs<T> make_node_args(const ColEnv& env, const Geom& G, const ApplyArgs& a,
     N.sc = env.sc;
     N.counter = env.counter ? env.counter : &env.sc->counter[0];
     const int64_t nn = G.nnode();
-    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nn + NB2 - 1) / NB2, 152 * 8)));
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nn + NB2 - 1) / NB2, int64_t(num_sms()) * kNodeBlocksPerSm)));
     if (off + 2 * blocks > env.partials_len) fail(PBM_EINVAL, "grid too large for the partials buffer");
     *blocks_out = blocks;
     return N;
@@ -874,7 +874,7 @@ void launch_what_hat(pbm_grid* g, cudaStream_t st) {
     KeHatT<double> K;
     fill_khat_t(K, g->kehat);
     const int64_t m = G.m();
-    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((m + 127) / 128, 152 * 16)));
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((m + 127) / 128, num_sms() * 16)));
     k_what_hat<<<blocks, 128, 0, st>>>(G.nx, G.ny, G.nz, G.support, g->u64, g->what_hat, K);
     PBM_LAUNCH("what hat");
 }

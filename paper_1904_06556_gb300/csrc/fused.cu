@@ -779,6 +779,7 @@ FusedPlan fused_plan(const Geom& G, int cand, bool op_s) {
     p.gy = (G.ny + 1 + p.TY - 1) / p.TY;
     const int planes = G.nz + 1;
     const int tiles = p.gx * p.gy;
+    const int sms = num_sms();
     // chunk length: with per_sm resident CTAs per SM a launch takes about waves x (DZ + 1) plane
     // steps; take the shortest, then the fewest CTAs
     double best = 1e300;
@@ -786,7 +787,7 @@ FusedPlan fused_plan(const Geom& G, int cand, bool op_s) {
     for (int dz = std::max(1, std::min(planes, 2)); dz <= planes; ++dz) {
         const int gz = (planes + dz - 1) / dz;
         if (dz > 1 && (planes + dz - 2) / (dz - 1) == gz && dz != planes) continue;  // same split, shorter dz
-        const double waves = double((int64_t(tiles) * gz + 152 * per_sm - 1) / (152 * per_sm));
+        const double waves = double((int64_t(tiles) * gz + sms * per_sm - 1) / (sms * per_sm));
         const double cost = waves * (dz + 1);
         if (cost < best - 1e-9) {
             best = cost;
@@ -810,11 +811,12 @@ int fused_threads(const FusedPlan& p) { return p.var == kFusedNumPlans ? 256 : k
 int fused_default_plan(const Geom& G) {
     int best = 0;
     double bc = 1e300;
+    const int sms = num_sms();
     for (int c = 0; c < kFusedNumPlans; ++c) {
         const FusedPlan p = fused_plan(G, c);
         const int per_sm = kFusedPlans[p.var][1];
         const int blocks = fused_blocks(p);
-        const double waves = double((blocks + 152 * per_sm - 1) / (152 * per_sm));
+        const double waves = double((blocks + sms * per_sm - 1) / (sms * per_sm));
         const double cols = double(p.gx) * (p.TX + 1) * p.gy * (p.TY + 1);
         const double cost = waves * (p.DZ + 1) / per_sm * 1e9 + cols * (p.DZ + 1) / p.DZ;
         if (cost < bc) {
@@ -903,12 +905,13 @@ FusedPlan fused_coarse_plan(const Geom& G, int cand) {
     p.gy = (G.ny + 1 + p.TY - 1) / p.TY;
     const int planes = G.nz + 1;
     const int tiles = p.gx * p.gy;
+    const int sms = num_sms();
     double best = 1e300;
     p.DZ = planes;
     for (int dz = std::max(1, std::min(planes, 2)); dz <= planes; ++dz) {
         const int gz = (planes + dz - 1) / dz;
         if (dz > 1 && (planes + dz - 2) / (dz - 1) == gz && dz != planes) continue;
-        const double waves = double((int64_t(tiles) * gz + 152 * per_sm - 1) / (152 * per_sm));
+        const double waves = double((int64_t(tiles) * gz + sms * per_sm - 1) / (sms * per_sm));
         const double cost = waves * (dz + 1);
         if (cost < best - 1e-9) {
             best = cost;

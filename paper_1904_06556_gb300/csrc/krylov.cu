@@ -8,7 +8,8 @@
 namespace pbm {
 
 constexpr int VB = 256;        // threads per vector CTA
-constexpr int VG = 152 * 4;    // vector CTAs (fixed, so that the summation order is fixed)
+// vector CTAs: 4 per SM, fixed for a device, so that the summation order is fixed
+static int vg() { return num_sms() * 4; }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -60,10 +61,10 @@ __global__ void k_cast(const S* __restrict__ a, D* __restrict__ b, int64_t n) {
 }
 
 void launch_cast(const void* src, bool src32, void* dst, bool dst32, int64_t n, cudaStream_t st) {
-    if (src32 && !dst32) launch_pdl(k_cast<float, double>, dim3(VG), dim3(VB), 0, st, (const float*)src, (double*)dst, n);
-    else if (!src32 && dst32) launch_pdl(k_cast<double, float>, dim3(VG), dim3(VB), 0, st, (const double*)src, (float*)dst, n);
-    else if (src32) launch_pdl(k_cast<float, float>, dim3(VG), dim3(VB), 0, st, (const float*)src, (float*)dst, n);
-    else launch_pdl(k_cast<double, double>, dim3(VG), dim3(VB), 0, st, (const double*)src, (double*)dst, n);
+    if (src32 && !dst32) launch_pdl(k_cast<float, double>, dim3(vg()), dim3(VB), 0, st, (const float*)src, (double*)dst, n);
+    else if (!src32 && dst32) launch_pdl(k_cast<double, float>, dim3(vg()), dim3(VB), 0, st, (const double*)src, (float*)dst, n);
+    else if (src32) launch_pdl(k_cast<float, float>, dim3(vg()), dim3(VB), 0, st, (const float*)src, (float*)dst, n);
+    else launch_pdl(k_cast<double, double>, dim3(vg()), dim3(VB), 0, st, (const double*)src, (double*)dst, n);
     PBM_LAUNCH("cast");
 }
 
@@ -90,11 +91,11 @@ __global__ void k_inverse(const double* __restrict__ x, double* __restrict__ y, 
         y[i] = sq ? 1.0 / sqrt(x[i]) : 1.0 / x[i];
 }
 void launch_inverse(const double* x, double* y, int64_t n, cudaStream_t st) {
-    k_inverse<<<VG, VB, 0, st>>>(x, y, n, 0);
+    k_inverse<<<vg(), VB, 0, st>>>(x, y, n, 0);
     PBM_LAUNCH("inverse");
 }
 void launch_inverse_sqrt(const double* x, double* y, int64_t n, cudaStream_t st) {
-    k_inverse<<<VG, VB, 0, st>>>(x, y, n, 1);
+    k_inverse<<<vg(), VB, 0, st>>>(x, y, n, 1);
     PBM_LAUNCH("inverse sqrt");
 }
 
@@ -103,8 +104,8 @@ void launch_scale_diag_first(pbm_grid* g, int k, bool fp32, const void* b, void*
     Level& L = g->L[k];
     const int64_t n = L.g.n() + (with_alpha ? 1 : 0);
     const double* om = &g->sc->mr[16 + k];
-    if (fp32) launch_pdl(k_first_jacobi<float>, dim3(VG), dim3(VB), 0, st, (const float*)b, L.idiag32, om, (float*)x, n);
-    else launch_pdl(k_first_jacobi<double>, dim3(VG), dim3(VB), 0, st, (const double*)b, L.idiag64, om, (double*)x, n);
+    if (fp32) launch_pdl(k_first_jacobi<float>, dim3(vg()), dim3(VB), 0, st, (const float*)b, L.idiag32, om, (float*)x, n);
+    else launch_pdl(k_first_jacobi<double>, dim3(vg()), dim3(VB), 0, st, (const double*)b, L.idiag64, om, (double*)x, n);
     PBM_LAUNCH("first jacobi");
 }
 
@@ -122,10 +123,10 @@ __global__ void k_dot(const T* __restrict__ a, const T* __restrict__ b, int64_t 
 
 void launch_dot(pbm_grid* g, bool fp32, const void* a, const void* b, int64_t n, int slot, cudaStream_t st) {
     if (fp32)
-        launch_pdl(k_dot<float>, dim3(VG), dim3(VB), 0, st, (const float*)a, (const float*)b, n, g->partials, &g->sc->counter[1],
+        launch_pdl(k_dot<float>, dim3(vg()), dim3(VB), 0, st, (const float*)a, (const float*)b, n, g->partials, &g->sc->counter[1],
                                         &g->sc->red[slot]);
     else
-        launch_pdl(k_dot<double>, dim3(VG), dim3(VB), 0, st, (const double*)a, (const double*)b, n, g->partials, &g->sc->counter[1],
+        launch_pdl(k_dot<double>, dim3(vg()), dim3(VB), 0, st, (const double*)a, (const double*)b, n, g->partials, &g->sc->counter[1],
                                          &g->sc->red[slot]);
     PBM_LAUNCH("dot");
 }
@@ -223,24 +224,24 @@ __global__ void k_cast_dot(const float* __restrict__ src, double* __restrict__ d
 
 void mr_lanczos2(pbm_grid* g, bool fp32, const void* Az, void* v0, void* v1, int64_t n, cudaStream_t st) {
     if (fp32)
-        launch_pdl(k_mr_lanczos2<float>, dim3(VG), dim3(VB), 0, st, (const float*)Az, (float*)v0, (float*)v1, n, g->sc->mr, g->sc->red);
+        launch_pdl(k_mr_lanczos2<float>, dim3(vg()), dim3(VB), 0, st, (const float*)Az, (float*)v0, (float*)v1, n, g->sc->mr, g->sc->red);
     else
-        launch_pdl(k_mr_lanczos2<double>, dim3(VG), dim3(VB), 0, st, (const double*)Az, (double*)v0, (double*)v1, n, g->sc->mr,
+        launch_pdl(k_mr_lanczos2<double>, dim3(vg()), dim3(VB), 0, st, (const double*)Az, (double*)v0, (double*)v1, n, g->sc->mr,
                                                  g->sc->red);
     PBM_LAUNCH("mr lanczos");
 }
 void mr_update2(pbm_grid* g, bool fp32, void* zc, const void* zn, void* d1, void* d2, void* x, int64_t n,
                 cudaStream_t st) {
     if (fp32)
-        launch_pdl(k_mr_update2<float>, dim3(VG), dim3(VB), 0, st, (float*)zc, (const float*)zn, (float*)d1, (float*)d2, (float*)x, n,
+        launch_pdl(k_mr_update2<float>, dim3(vg()), dim3(VB), 0, st, (float*)zc, (const float*)zn, (float*)d1, (float*)d2, (float*)x, n,
                                                g->sc->mr);
     else
-        launch_pdl(k_mr_update2<double>, dim3(VG), dim3(VB), 0, st, (double*)zc, (const double*)zn, (double*)d1, (double*)d2, (double*)x,
+        launch_pdl(k_mr_update2<double>, dim3(vg()), dim3(VB), 0, st, (double*)zc, (const double*)zn, (double*)d1, (double*)d2, (double*)x,
                                                 n, g->sc->mr);
     PBM_LAUNCH("mr update");
 }
 void cast_dot(pbm_grid* g, const float* src, double* dst, const double* other, int64_t n, int slot, cudaStream_t st) {
-    launch_pdl(k_cast_dot, dim3(VG), dim3(VB), 0, st, src, dst, other, n, g->partials, &g->sc->counter[1], &g->sc->red[slot]);
+    launch_pdl(k_cast_dot, dim3(vg()), dim3(VB), 0, st, src, dst, other, n, g->partials, &g->sc->counter[1], &g->sc->red[slot]);
     PBM_LAUNCH("cast dot");
 }
 
@@ -362,7 +363,7 @@ __global__ void k_add_f32(double* __restrict__ x, const float* __restrict__ d, i
         x[i] += sign * double(d[i]);
 }
 void add_f32(double* x, const float* d, int64_t n, cudaStream_t st, double sign) {
-    launch_pdl(k_add_f32, dim3(VG), dim3(VB), 0, st, x, d, n, sign);
+    launch_pdl(k_add_f32, dim3(vg()), dim3(VB), 0, st, x, d, n, sign);
     PBM_LAUNCH("add f32");
 }
 
@@ -413,20 +414,20 @@ __global__ void k_lz_next(const double* __restrict__ w, double* __restrict__ v, 
 }
 
 void lz_start(pbm_grid* g, double* v, double* t, double* vprev, const double* diag, int64_t n, cudaStream_t st) {
-    k_lz_start<<<VG, VB, 0, st>>>(v, t, vprev, diag, n);
+    k_lz_start<<<vg(), VB, 0, st>>>(v, t, vprev, diag, n);
     PBM_LAUNCH("lz start");
 }
 // j: coefficient index in sc->lz_a / lz_b; rset: reduction set of the stream (0: counter[2])
 void lz_b(pbm_grid* g, double* w, const double* v, const double* vprev, const double* sdiag, int64_t n, int j0,
           int j, int rset, cudaStream_t st) {
     const RedSet r = red_set(g, rset);
-    k_lz_b<<<VG, VB, 0, st>>>(w, v, vprev, sdiag, n, &g->sc->lz_a[j0 + j], j > 0 ? &g->sc->lz_b[j0 + j - 1] : nullptr,
+    k_lz_b<<<vg(), VB, 0, st>>>(w, v, vprev, sdiag, n, &g->sc->lz_a[j0 + j], j > 0 ? &g->sc->lz_b[j0 + j - 1] : nullptr,
                               r.partials, rset == 0 ? &g->sc->counter[2] : r.counter, &g->sc->lz_b[j0 + j]);
     PBM_LAUNCH("lz b");
 }
 void lz_next(pbm_grid* g, const double* w, double* v, double* vprev, double* t, const double* diag, int64_t n, int j,
              cudaStream_t st) {
-    k_lz_next<<<VG, VB, 0, st>>>(w, v, vprev, t, diag, n, &g->sc->lz_b[j]);
+    k_lz_next<<<vg(), VB, 0, st>>>(w, v, vprev, t, diag, n, &g->sc->lz_b[j]);
     PBM_LAUNCH("lz next");
 }
 

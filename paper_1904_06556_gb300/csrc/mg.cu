@@ -106,7 +106,7 @@ void launch_restrict(pbm_grid* g, int k, bool fp32, const void* rf, void* bc, bo
     const Geom& F = g->L[k].g;
     Level& C = g->L[k + 1];
     const int64_t nt = 3 * C.g.nnode();
-    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nt + 127) / 128, 152 * 16)));
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nt + 127) / 128, num_sms() * 16)));
     const double* om = &g->sc->mr[16 + k + 1];
     if (fp32)
         launch_pdl(k_restrict<float>, dim3(blocks), dim3(128), 0, st, RestrictArgs<float>{F.nx, F.ny, F.nz, F.support, with_alpha ? 1 : 0,
@@ -174,7 +174,7 @@ __global__ void k_prolong_add_b(const ProlongArgs<T>* __restrict__ A, BatchMap M
 void launch_prolong_add(pbm_grid* g, int k, bool fp32, const void* xc, void* xf, bool with_alpha, cudaStream_t st) {
     const Geom& F = g->L[k].g;
     const int64_t nt = 3 * F.nnode();
-    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nt + 255) / 256, 152 * 16)));
+    const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((nt + 255) / 256, num_sms() * 16)));
     if (fp32)
         launch_pdl(k_prolong_add<float>, dim3(blocks), dim3(256), 0, st, ProlongArgs<float>{F.nx, F.ny, F.nz, F.support,
                                                                         with_alpha ? 1 : 0, (const float*)xc,
@@ -240,7 +240,7 @@ void launch_build_what(pbm_grid* g, cudaStream_t st) {
         K.mu4[b] = g->kehat.mu4[b];
     }
     const int64_t m = G.m();
-    const int blocks = int(std::min<int64_t>((m + 127) / 128, 152 * 16));
+    const int blocks = int(std::min<int64_t>((m + 127) / 128, num_sms() * 16));
     k_build_what<<<blocks, 128, 0, st>>>(G.nx, G.ny, G.nz, G.support, g->u64, g->what, K);
     PBM_LAUNCH("build what");
 }
@@ -598,7 +598,7 @@ RestrictArgs<T> make_restrict_args(pbm_grid* g, int k, const void* rf, void* bc,
     const Geom& F = g->L[k].g;
     Level& C = g->L[k + 1];
     const int64_t nt = 3 * C.g.nnode();
-    *blocks_out = int(std::max<int64_t>(1, std::min<int64_t>((nt + 127) / 128, 152 * 16)));
+    *blocks_out = int(std::max<int64_t>(1, std::min<int64_t>((nt + 127) / 128, num_sms() * 16)));
     const T* idiag = sizeof(T) == 4 ? (const T*)(const void*)C.idiag32 : (const T*)(const void*)C.idiag64;
     return RestrictArgs<T>{F.nx, F.ny, F.nz, F.support, with_alpha ? 1 : 0, (const T*)rf, (T*)bc, scale,
                            (T*)xfirst, idiag, &g->sc->mr[16 + k + 1]};
@@ -607,7 +607,7 @@ template <class T>
 ProlongArgs<T> make_prolong_args(pbm_grid* g, int k, const void* xc, void* xf, bool with_alpha, int* blocks_out) {
     const Geom& F = g->L[k].g;
     const int64_t nt = 3 * F.nnode();
-    *blocks_out = int(std::max<int64_t>(1, std::min<int64_t>((nt + 255) / 256, 152 * 16)));
+    *blocks_out = int(std::max<int64_t>(1, std::min<int64_t>((nt + 255) / 256, num_sms() * 16)));
     return ProlongArgs<T>{F.nx, F.ny, F.nz, F.support, with_alpha ? 1 : 0, (const T*)xc, (T*)xf};
 }
 template <class T>

@@ -18,7 +18,8 @@
 namespace pbm {
 
 constexpr int NB = 256;
-constexpr int NG = 152 * 4;
+// CTAs of the element-wise kernels: 4 per SM, fixed for a device (fixed summation order)
+static int ng() { return num_sms() * 4; }
 
 __device__ __forceinline__ double phi_pb(double t) {
     return t >= -0.5 ? t + 0.5 * t * t : -0.25 * log(-2.0 * t) - 0.375;
@@ -105,7 +106,7 @@ __global__ void k_coeffs(int64_t m, const double* __restrict__ c2, const double*
 
 void launch_coeffs(pbm_grid* g, const pbm_state* s, const double* c2, double* coef, cudaStream_t st) {
     const int64_t m = g->L[0].g.m();
-    k_coeffs<<<NG, NB, 0, st>>>(m, c2, s->rho_dev, s->mu_lo_dev, s->mu_up_dev, s->nu_lo_dev, s->nu_up_dev, s->alpha,
+    k_coeffs<<<ng(), NB, 0, st>>>(m, c2, s->rho_dev, s->mu_lo_dev, s->mu_up_dev, s->nu_lo_dev, s->nu_up_dev, s->alpha,
                                 s->p, s->q_lo, s->q_up, s->rho_lo, s->rho_up, g->w64, g->d64, g->eps64, g->wr64, coef,
                                 g->partials, &g->sc->counter[3], &g->sc->red[8]);
     PBM_LAUNCH("coeffs");
@@ -127,7 +128,7 @@ __global__ void k_check_nonneg(const double* __restrict__ v, int64_t n, double* 
     finish_multi<1>(acc, partials, counter, out);
 }
 void launch_check_nonneg(pbm_grid* g, const double* v, int64_t n, int slot, cudaStream_t st) {
-    k_check_nonneg<<<NG, NB, 0, st>>>(v, n, g->partials, &g->sc->counter[3], &g->sc->red[slot]);
+    k_check_nonneg<<<ng(), NB, 0, st>>>(v, n, g->partials, &g->sc->counter[3], &g->sc->red[slot]);
     PBM_LAUNCH("check");
 }
 
@@ -142,7 +143,7 @@ __global__ void k_mask_copy(int nx, int ny, int nz, int support, const double* _
 }
 void launch_mask_copy(pbm_grid* g, const double* x, double* y, cudaStream_t st) {
     const Geom& G = g->L[0].g;
-    k_mask_copy<<<NG, NB, 0, st>>>(G.nx, G.ny, G.nz, G.support, x, y);
+    k_mask_copy<<<ng(), NB, 0, st>>>(G.nx, G.ny, G.nz, G.support, x, y);
     PBM_LAUNCH("mask copy");
 }
 
@@ -162,7 +163,7 @@ __global__ void k_delta_nu(int64_t m, const double* __restrict__ bq, const doubl
 }
 void launch_delta_nu(pbm_grid* g, const double* bq, const double* coef, const double* dz_alpha, double* dl, double* du,
                      cudaStream_t st) {
-    k_delta_nu<<<NG, NB, 0, st>>>(g->L[0].g.m(), bq, coef, dz_alpha, dl, du);
+    k_delta_nu<<<ng(), NB, 0, st>>>(g->L[0].g.m(), bq, coef, dz_alpha, dl, du);
     PBM_LAUNCH("delta nu");
 }
 
@@ -193,7 +194,7 @@ __global__ void k_lagr_terms(int64_t m, double kappa, const double* __restrict__
 void launch_lagr_terms(pbm_grid* g, double kappa, const double* c2u, const double* bq, const double* qq,
                        const pbm_state* s, const double* dl, const double* dup, double alpha_k, int slot,
                        cudaStream_t st) {
-    k_lagr_terms<<<NG, NB, 0, st>>>(g->L[0].g.m(), kappa, c2u, bq, qq, s->rho_dev, s->mu_lo_dev, s->mu_up_dev,
+    k_lagr_terms<<<ng(), NB, 0, st>>>(g->L[0].g.m(), kappa, c2u, bq, qq, s->rho_dev, s->mu_lo_dev, s->mu_up_dev,
                                     s->nu_lo_dev, s->nu_up_dev, dl, dup, alpha_k, s->p, s->q_lo, s->q_up, g->partials,
                                     &g->sc->counter[3], &g->sc->red[slot]);
     PBM_LAUNCH("lagr terms");
@@ -205,7 +206,7 @@ __global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, dou
         y[i] += kappa * x[i];
 }
 void launch_axpy(double* y, const double* x, double kappa, int64_t n, cudaStream_t st) {
-    k_axpy<<<NG, NB, 0, st>>>(y, x, kappa, n);
+    k_axpy<<<ng(), NB, 0, st>>>(y, x, kappa, n);
     PBM_LAUNCH("axpy");
 }
 
@@ -215,7 +216,7 @@ __global__ void k_scale(const double* __restrict__ a, double* __restrict__ b, do
         b[i] = s * a[i];
 }
 void launch_scale(const double* a, double* b, double s, int64_t n, cudaStream_t st) {
-    k_scale<<<NG, NB, 0, st>>>(a, b, s, n);
+    k_scale<<<ng(), NB, 0, st>>>(a, b, s, n);
     PBM_LAUNCH("scale");
 }
 
@@ -237,7 +238,7 @@ __global__ void k_mult_update(int64_t m, const double* __restrict__ c2, double* 
     }
 }
 void launch_mult_update(pbm_grid* g, const double* c2, pbm_state* s, double beta, bool only_rho, cudaStream_t st) {
-    k_mult_update<<<NG, NB, 0, st>>>(g->L[0].g.m(), c2, s->rho_dev, s->mu_lo_dev, s->mu_up_dev, s->nu_lo_dev,
+    k_mult_update<<<ng(), NB, 0, st>>>(g->L[0].g.m(), c2, s->rho_dev, s->mu_lo_dev, s->mu_up_dev, s->nu_lo_dev,
                                      s->nu_up_dev, s->alpha, s->p, s->q_lo, s->q_up, beta, 1.0 / beta,
                                      only_rho ? 1 : 0);
     PBM_LAUNCH("multiplier update");
@@ -259,7 +260,7 @@ __global__ void k_gap_sums(int64_t m, const double* __restrict__ c2, double alph
     finish_multi<4>(acc, partials, counter, out);
 }
 void launch_gap_sums(pbm_grid* g, const double* c2, const pbm_state* s, int slot, cudaStream_t st) {
-    k_gap_sums<<<NG, NB, 0, st>>>(g->L[0].g.m(), c2, s->alpha, s->rho_lo, s->rho_up, s->nu_lo_dev, s->nu_up_dev,
+    k_gap_sums<<<ng(), NB, 0, st>>>(g->L[0].g.m(), c2, s->alpha, s->rho_lo, s->rho_up, s->nu_lo_dev, s->nu_up_dev,
                                   s->rho_dev, g->partials, &g->sc->counter[3], &g->sc->red[slot]);
     PBM_LAUNCH("gap sums");
 }
@@ -310,7 +311,7 @@ __global__ void k_ip_coeffs(int64_t m, const double* __restrict__ c2, const doub
 
 void launch_ip_coeffs(pbm_grid* g, const pbm_ip_state* s, const double* c2, double* coef, cudaStream_t st) {
     const int64_t m = g->L[0].g.m();
-    k_ip_coeffs<<<NG, NB, 0, st>>>(m, c2, s->rho_dev, s->nu_lo_dev, s->nu_up_dev, s->alpha, s->rho_lo, s->rho_up, s->r,
+    k_ip_coeffs<<<ng(), NB, 0, st>>>(m, c2, s->rho_dev, s->nu_lo_dev, s->nu_up_dev, s->alpha, s->rho_lo, s->rho_up, s->r,
                                    s->s, g->w64, g->d64, g->wr64, coef, g->partials, &g->sc->counter[3],
                                    &g->sc->red[8]);
     PBM_LAUNCH("ip coeffs");
@@ -341,7 +342,7 @@ __global__ void k_ip_recover(int64_t m, const double* __restrict__ wdu, const do
 void launch_ip_recover(pbm_grid* g, const double* wdu, const double* da, const double* coef, double rho_lo,
                        double rho_up, double* drho, double* dnl, double* dnu, cudaStream_t st) {
     const int64_t m = g->L[0].g.m();
-    k_ip_recover<<<NG, NB, 0, st>>>(m, wdu, da, g->w64, g->d64, coef, rho_lo, rho_up, drho, dnl, dnu);
+    k_ip_recover<<<ng(), NB, 0, st>>>(m, wdu, da, g->w64, g->d64, coef, rho_lo, rho_up, drho, dnl, dnu);
     PBM_LAUNCH("ip recover");
 }
 
@@ -447,12 +448,12 @@ void launch_doc(pbm_grid* g, const double* e, double* rho_inout, double V, doubl
                 double tau, double* w, cudaStream_t st) {
     const int64_t m = g->L[0].g.m();
     double* ctl = &g->sc->ctl[0];   // reused: the MINRES loop is not running
-    k_doc_weights<<<NG, NB, 0, st>>>(m, g->rho, e, q, w, ctl, 1e4);
+    k_doc_weights<<<ng(), NB, 0, st>>>(m, g->rho, e, q, w, ctl, 1e4);
     PBM_LAUNCH("doc weights");
     // trials in batches; the host looks at the done flag after each batch
     for (int batch = 0; batch < 8; ++batch) {
         for (int t = 0; t < 16; ++t) {
-            k_doc_trial<<<NG, NB, 0, st>>>(m, w, V, rho_lo, rho_up, tau, ctl, g->partials, &g->sc->counter[3]);
+            k_doc_trial<<<ng(), NB, 0, st>>>(m, w, V, rho_lo, rho_up, tau, ctl, g->partials, &g->sc->counter[3]);
             PBM_LAUNCH("doc trial");
         }
         PBM_CUDA(cudaMemcpyAsync(&g->sc_host->ctl[0], ctl, sizeof(double) * 5, cudaMemcpyDeviceToHost, st));
@@ -460,7 +461,7 @@ void launch_doc(pbm_grid* g, const double* e, double* rho_inout, double V, doubl
         if (g->sc_host->ctl[4] != 0.0) break;
     }
     if (g->sc_host->ctl[4] == 0.0) fail(PBM_ENOTCONV, "DOC bisection did not close its interval in 128 trials");
-    k_doc_update<<<NG, NB, 0, st>>>(m, w, ctl, rho_lo, rho_up, g->rho, rho_inout, g->partials, &g->sc->counter[3],
+    k_doc_update<<<ng(), NB, 0, st>>>(m, w, ctl, rho_lo, rho_up, g->rho, rho_inout, g->partials, &g->sc->counter[3],
                                     &g->sc->red[12]);
     PBM_LAUNCH("doc update");
 }

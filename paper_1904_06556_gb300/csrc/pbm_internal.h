@@ -25,6 +25,12 @@ void check_cuda(cudaError_t e, const char* what);
 void count_launch();  // process-wide counter of the kernels this library launched
 void count_launch_add(int64_t delta);
 int64_t launch_count();
+// Number of SMs of the current device, queried once per device and cached. The launches whose CTA
+// count is fixed (so that their reductions sum in a fixed order) and the wave models of the tile
+// planners size themselves from it: results are bit-reproducible on a given device, and a part with
+// another SM count is filled the same way.
+int num_sms();
+constexpr int kNodeBlocksPerSm = 8;   // CTA cap of the node pass of the two-pass operators, per SM
 #define PBM_CUDA(x) ::pbm::check_cuda((x), #x)
 #define PBM_LAUNCH(what) (::pbm::count_launch(), ::pbm::check_cuda(cudaGetLastError(), what))
 

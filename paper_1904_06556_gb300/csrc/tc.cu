@@ -647,7 +647,7 @@ FusedPlan tc_plan(const Geom& G, bool op_s) {
     for (int dz = std::max(1, std::min(planes, 2)); dz <= planes; ++dz) {
         const int gz = (planes + dz - 1) / dz;
         if (dz > 1 && (planes + dz - 2) / (dz - 1) == gz && dz != planes) continue;  // same split, shorter dz
-        const double waves = double((int64_t(tiles) * gz + 152 * per_sm - 1) / (152 * per_sm));
+        const double waves = double((int64_t(tiles) * gz + num_sms() * per_sm - 1) / (num_sms() * per_sm));
         const double cost = waves * (dz + 1);
         if (cost < best - 1e-9) {
             best = cost;
