@@ -160,6 +160,9 @@ typedef struct pbm_newton_info {
     double slope;          /* grad L^T dxi (must be < 0)                                         */
     double lagrangian_old, lagrangian_new;
     double minres_relres;
+    int resolves;          /* re-solves with a tightened eps_mr after a non-descent direction         */
+    int stalled;           /* 1: no descent direction even at the floor; the step was not taken     */
+    double eps_mr;         /* MINRES tolerance of the last solve                                     */
 } pbm_newton_info;
 
 /* Timing of the fine-level operator kernel (K(w) x or S x with any of its fused epilogues: plain
@@ -210,10 +213,17 @@ int pbm_get_maps(const pbm_grid* g, int level, int which, void* host_dst);
  * value is finite and >= 0 (this synchronises `stream`): PBM_ENONFINITE / PBM_EINVAL. */
 int pbm_set_density(pbm_grid* g, const double* rho_dev, void* stream);
 
-/* y = K(w) x on the fine level, eq. (1): K(w) = sum_i w_i K_i with supported rows/columns the
- * identity. w_dev: m element weights (NULL = the density set by pbm_set_density); x_dev, y_dev:
- * n. x and y must not overlap. FP64 throughout. */
-int pbm_apply_K(pbm_grid* g, const double* w_dev, const double* x_dev, double* y_dev, void* stream);
+/* y = A_level x with A_0 = K(w) on the fine level, eq. (1): K(w) = sum_i w_i K_i with supported
+ * rows/columns the identity; and for level >= 1 the Galerkin operator A_level = R A_{level-1} P of
+ * Section 5.1 (R = P^T, P the trilinear prolongation of Section 5.2) built from K(rho) of the density
+ * set by pbm_set_density, supported rows/columns of that level the identity.
+ *   level 0: w_dev m element weights (NULL = the density set by pbm_set_density); x_dev, y_dev n.
+ *   level k >= 1: w_dev must be NULL; x_dev, y_dev hold 3 (nx/2^k + 1)(ny/2^k + 1)(nz/2^k + 1)
+ *   entries. If the K(rho) hierarchy is not current (no K solve or V-cycle since the last
+ *   pbm_set_density, or an S hierarchy replaced it) it is built first, on `stream`.
+ * x and y must not overlap. FP64 throughout. Errors: PBM_EINVAL (level out of range, weights given
+ * for a coarse level), PBM_ESTATE (no density set and no weights). */
+int pbm_apply_K(pbm_grid* g, const double* w_dev, const double* x_dev, double* y_dev, int level, void* stream);
 
 /* Same operator in FP32 (the kernel the mixed path runs); w_dev must not be NULL. */
 int pbm_apply_K_f32(pbm_grid* g, const float* w_dev, const float* x_dev, float* y_dev, void* stream);
@@ -383,9 +393,30 @@ int pbm_ip_recover(pbm_grid* g, const double* dz_dev, double* drho_dev, double* 
  * solves the reduced system to relative residual eps_mr, recovers (dnu_lo, dnu_up) by
  * eq. (deltanu), backtracks (Armijo, c1 = 1e-4, halving, at most 30 halvings) and updates
  * st->u_dev, st->alpha, st->nu_lo_dev, st->nu_up_dev in place. f_dev: n load vector. Synchronises.
- * Errors: PBM_ELINESEARCH (no acceptable step; state unchanged), PBM_ENOTCONV, PBM_EBREAKDOWN. */
+ * A direction that is not one of descent (grad L^T dxi >= 0: the failure of inexact solves that
+ * Section 6 reports for the largest bridge examples) is solved again from zero with eps_mr / 10, down
+ * to the floor 1e-9 of Section 5.3 (info->resolves counts them); if it is still not a descent
+ * direction there the step is not taken (info->stalled = 1, PBM_ELINESEARCH).
+ * Errors: PBM_ELINESEARCH (no acceptable step; state unchanged), PBM_ENOTCONV (the step was taken
+ * with a solve that did not reach the tolerance), PBM_EBREAKDOWN. */
 int pbm_newton_step(pbm_grid* g, pbm_state* st, const double* f_dev, double eps_mr, pbm_newton_info* info,
                     void* stream);
+
+/* Parameters of one Newton step (pbm_newton_step_ex); pbm_default_newton_params gives the values
+ * pbm_newton_step uses for the ones it does not take. */
+typedef struct pbm_newton_params {
+    double eps_mr;         /* MINRES relative tolerance of the reduced system, > 0                   */
+    double eps_mr_min;     /* floor of the non-descent re-solves (Section 5.3: 1e-9); a value above
+                              eps_mr means no re-solve                                            */
+    int max_halvings;      /* Armijo step halvings before PBM_ELINESEARCH, >= 0 (reading: 30)     */
+    int maxit;             /* MINRES iterations per solve, >= 1 (10000)                            */
+} pbm_newton_params;
+
+int pbm_default_newton_params(pbm_newton_params* p);
+
+/* pbm_newton_step with every parameter given. Errors as pbm_newton_step, and PBM_EINVAL. */
+int pbm_newton_step_ex(pbm_grid* g, pbm_state* st, const double* f_dev, const pbm_newton_params* prm,
+                       pbm_newton_info* info, void* stream);
 
 /* Parameters of Algorithm 1 (PBM outer loop). pbm_default_pbm_params gives the paper's values
  * (Section 3.3, Section 5.3): eps_pbm 1e-5, beta = gamma = 0.3, p_min 1e-8, eps_nwt 1 and its
@@ -399,6 +430,7 @@ typedef struct pbm_pbm_params {
     double eps_nwt, eps_nwt_min;  /* Newton tolerance on res_PBM and its floor                   */
     double eps_mr, eps_mr_min;    /* MINRES relative tolerance (<= 0: 1e-4 sqrt(n)) and floor    */
     int max_outer, max_newton;    /* outer iterations; Newton steps per Newton loop              */
+    int max_halvings;             /* Armijo step halvings per Newton step (30)                   */
 } pbm_pbm_params;
 
 typedef struct pbm_pbm_info {
@@ -408,6 +440,9 @@ typedef struct pbm_pbm_info {
     double compliance;            /* 1/2 f^T u at exit                                           */
     double volume;                /* sum rho at exit                                              */
     double eps_mr;                /* MINRES tolerance in use at exit                              */
+    int resolves;                 /* Newton systems solved again after a non-descent direction    */
+    int stalls;                   /* Newton loops ended early because no descent direction was
+                                     found at eps_mr_min (Section 6: the iterate is accepted)      */
 } pbm_pbm_info;
 
 int pbm_default_pbm_params(pbm_pbm_params* p);
@@ -418,8 +453,11 @@ int pbm_default_pbm_params(pbm_pbm_params* p);
  * evaluates the duality gap delta (eq. (gap)) and d, stops when |delta / d| < eps_pbm, else updates
  * the multipliers (rho, mu_lo, mu_up with the beta safeguard), the penalties and eps_nwt. The run
  * ends with a Newton loop at 10 eps_pbm and a final density update. st is updated in place; st->rho
- * holds the optimal densities on exit. Synchronises. Errors: PBM_ENOTCONV (max_outer or max_newton
- * reached), PBM_ELINESEARCH, PBM_EBREAKDOWN, PBM_EINVAL. */
+ * holds the optimal densities on exit. A Newton direction that is not one of descent is solved again
+ * with eps_mr / 10 (down to eps_mr_min); a Newton loop that finds no descent direction at the floor
+ * ends at its current iterate, which is accepted as Section 6 does for its stalled runs
+ * (info->stalls). Synchronises. Errors: PBM_ENOTCONV (max_outer or max_newton reached),
+ * PBM_ELINESEARCH, PBM_EBREAKDOWN, PBM_EINVAL. */
 int pbm_solve(pbm_grid* g, pbm_state* st, const double* f_dev, const pbm_pbm_params* prm, pbm_pbm_info* info,
               void* stream);
 

@@ -12,6 +12,11 @@ Readings of the paper taken here, where it is silent or inconsistent (the CUDA p
     and with the generic rule eq. (106) (Algorithm 1 prints phi'(nu_lo/q_lo)).
   * Supported dofs are eliminated; u has zeros there and every K_i u is restricted to the free dofs.
   * Armijo constants (not given): c1 = 1e-4, halving, kappa0 = 1, at most 30 halvings.
+  * Non-descent directions (Section 6, the discussion of the BRIDGE examples with 7 levels: inexact solves of eq.
+    (system) stopped being descent directions and the method stalled there). When grad L^T dxi >= 0 the reduced
+    system is solved again from zero with eps_MR tightened tenfold, down to the floor eps_mr_min of Section 5.3; a
+    direction that is still not one of descent at the floor ends the Newton loop at the current iterate (a stall,
+    which the paper accepted as the nearly optimal solution).
 """
 from __future__ import annotations
 
@@ -341,6 +346,9 @@ class NewtonInfo:
     minres_iters: int = 0
     res: float = float("nan")
     kappas: list = field(default_factory=list)
+    resolves: int = 0          # re-solves with a tightened eps_MR after a non-descent direction
+    stalled: bool = False      # no descent direction even at eps_mr_min: the loop ended at the current iterate
+    slopes: list = field(default_factory=list)
 
 
 def solve_reduced(pb: Problem, st: State, cf: Coeffs, rhs: np.ndarray, eps_mr: float | None, levels: int,
@@ -356,9 +364,10 @@ def solve_reduced(pb: Problem, st: State, cf: Coeffs, rhs: np.ndarray, eps_mr: f
 
 def newton(pb: Problem, st: State, eps_nwt: float, eps_mr: float | None = None, levels: int = 2,
            max_iter: int = 100, c1: float = 1e-4, max_halvings: int = 30, adapt_eps_mr: bool = False,
-           info: NewtonInfo | None = None):
+           info: NewtonInfo | None = None, eps_mr_min: float = 1e-9):
     """Algorithm 2: Newton with Armijo backtracking on the augmented Lagrangian until res_PBM < eps_nwt.
-    Returns (state, info, eps_mr)."""
+    Returns (state, info, eps_mr). A direction that is not one of descent is solved again with eps_MR / 10 (down to
+    eps_mr_min); at the floor the loop stops at the current iterate (info.stalled)."""
     info = NewtonInfo() if info is None else info
     st = st.copy()
     res_prev = None
@@ -369,14 +378,23 @@ def newton(pb: Problem, st: State, eps_nwt: float, eps_mr: float | None = None, 
         if res < eps_nwt:
             break
         if adapt_eps_mr and eps_mr is not None and res_prev is not None and res > 0.9 * res_prev:
-            eps_mr = max(0.1 * eps_mr, 1e-9)
+            eps_mr = max(0.1 * eps_mr, eps_mr_min)
         res_prev = res
         rhs = rhs_closed(pb, st, cf)
-        dz, its = solve_reduced(pb, st, cf, rhs, eps_mr, levels)
-        info.minres_iters += its
-        dl, dup = delta_nu(pb, st, cf, dz)
         gu_vec, ga, gl, gu = gradient(pb, st, cf)
-        slope = gu_vec @ masked(pb, dz[:pb.n]) + ga * dz[pb.n] + gl @ dl + gu @ dup
+        while True:
+            dz, its = solve_reduced(pb, st, cf, rhs, eps_mr, levels)
+            info.minres_iters += its
+            dl, dup = delta_nu(pb, st, cf, dz)
+            slope = gu_vec @ masked(pb, dz[:pb.n]) + ga * dz[pb.n] + gl @ dl + gu @ dup
+            if slope < 0.0 or eps_mr is None or eps_mr <= eps_mr_min:
+                break
+            eps_mr = max(0.1 * eps_mr, eps_mr_min)
+            info.resolves += 1
+        info.slopes.append(float(slope))
+        if not slope < 0.0:
+            info.stalled = True
+            break
         L0 = lagrangian(pb, st)
         kappa = 1.0
         for _h in range(max_halvings + 1):

@@ -163,10 +163,14 @@ class Grid:
     def set_density(self, rho: torch.Tensor):
         self._check(self._L.pbm_set_density(self._h, _ptr(rho, n=self.m, name="rho"), _stream()))
 
-    def apply_K(self, x: torch.Tensor, w: torch.Tensor | None = None, out: torch.Tensor | None = None):
+    def apply_K(self, x: torch.Tensor, w: torch.Tensor | None = None, out: torch.Tensor | None = None,
+                level: int = 0):
+        """y = K(w) x on the fine level (w None: the set density), or, for level >= 1, the FP64 Galerkin operator
+        of that level of the K(rho) hierarchy (pbm_apply_K)."""
         y = torch.empty_like(x) if out is None else out
-        self._check(self._L.pbm_apply_K(self._h, _ptr(w, n=self.m, name="w"), _ptr(x, n=self.n, name="x"),
-                                        _ptr(y, n=self.n, name="y"), _stream()))
+        nl = self._level_n[level] if 0 <= level < self.levels else None
+        self._check(self._L.pbm_apply_K(self._h, _ptr(w, n=self.m, name="w"), _ptr(x, n=nl, name="x"),
+                                        _ptr(y, n=nl, name="y"), int(level), _stream()))
         return y
 
     def apply_K_f32(self, x: torch.Tensor, w: torch.Tensor, out: torch.Tensor | None = None):
@@ -331,12 +335,20 @@ class Grid:
         info["rc"] = rc
         return x, info
 
-    def newton_step(self, st: dict, f: torch.Tensor, eps_mr: float, check: bool = True):
-        """One Newton step of Algorithm 2; updates st['u'], st['nu_lo'], st['nu_up'] in place and st['alpha']."""
+    def newton_step(self, st: dict, f: torch.Tensor, eps_mr: float, check: bool = True, **params):
+        """One Newton step of Algorithm 2; updates st['u'], st['nu_lo'], st['nu_up'] in place and st['alpha'].
+        Keyword arguments (eps_mr_min, max_halvings, maxit) override the defaults of pbm_newton_step_ex."""
         s = self._state(st)
         inf = _lib.NewtonInfo()
-        rc = self._L.pbm_newton_step(self._h, C.byref(s), _ptr(f, n=self.n, name="f"), float(eps_mr), C.byref(inf),
-                                     _stream())
+        prm = _lib.NewtonParams()
+        self._check(self._L.pbm_default_newton_params(C.byref(prm)))
+        prm.eps_mr = float(eps_mr)
+        for k, v in params.items():
+            if not hasattr(prm, k):
+                raise TypeError(f"unknown Newton parameter {k}")
+            setattr(prm, k, v)
+        rc = self._L.pbm_newton_step_ex(self._h, C.byref(s), _ptr(f, n=self.n, name="f"), C.byref(prm), C.byref(inf),
+                                        _stream())
         info = {k: getattr(inf, k) for k, _ in _lib.NewtonInfo._fields_}
         info["rc"] = rc
         if check:
@@ -358,7 +370,7 @@ class Grid:
     def pbm_solve(self, st: dict, f: torch.Tensor, check: bool = True, **params):
         """Algorithm 1 from the state `st` (updated in place; st['rho'] holds the densities on exit). Keyword
         arguments override the paper's parameters (eps_pbm, beta, gamma, p_min, eps_nwt, eps_nwt_min, eps_mr,
-        eps_mr_min, max_outer, max_newton)."""
+        eps_mr_min, max_outer, max_newton, max_halvings)."""
         prm = _lib.PbmParams()
         self._check(self._L.pbm_default_pbm_params(C.byref(prm)))
         for k, v in params.items():

@@ -73,13 +73,14 @@ class ProfileStats(C.Structure):
 class PbmParams(C.Structure):
     _fields_ = [("eps_pbm", C.c_double), ("beta", C.c_double), ("gamma", C.c_double), ("p_min", C.c_double),
                 ("eps_nwt", C.c_double), ("eps_nwt_min", C.c_double), ("eps_mr", C.c_double),
-                ("eps_mr_min", C.c_double), ("max_outer", C.c_int), ("max_newton", C.c_int)]
+                ("eps_mr_min", C.c_double), ("max_outer", C.c_int), ("max_newton", C.c_int),
+                ("max_halvings", C.c_int)]
 
 
 class PbmInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("outer", C.c_int), ("newton", C.c_int), ("minres", C.c_int),
                 ("gap_ratio", C.c_double), ("compliance", C.c_double), ("volume", C.c_double),
-                ("eps_mr", C.c_double)]
+                ("eps_mr", C.c_double), ("resolves", C.c_int), ("stalls", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -90,7 +91,12 @@ class SolveInfo(C.Structure):
 class NewtonInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("minres_iterations", C.c_int), ("halvings", C.c_int), ("kappa", C.c_double),
                 ("res_pbm", C.c_double), ("slope", C.c_double), ("lagrangian_old", C.c_double),
-                ("lagrangian_new", C.c_double), ("minres_relres", C.c_double)]
+                ("lagrangian_new", C.c_double), ("minres_relres", C.c_double), ("resolves", C.c_int),
+                ("stalled", C.c_int), ("eps_mr", C.c_double)]
+
+
+class NewtonParams(C.Structure):
+    _fields_ = [("eps_mr", C.c_double), ("eps_mr_min", C.c_double), ("max_halvings", C.c_int), ("maxit", C.c_int)]
 
 
 def header_symbols() -> list[str]:
@@ -114,7 +120,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pbm_grid_info_get": (i, [vp, C.POINTER(GridInfo)]),
         "pbm_get_maps": (i, [vp, i, i, vp]),
         "pbm_set_density": (i, [vp, vp, vp]),
-        "pbm_apply_K": (i, [vp, vp, vp, vp, vp]),
+        "pbm_apply_K": (i, [vp, vp, vp, vp, i, vp]),
         "pbm_apply_K_f32": (i, [vp, vp, vp, vp, vp]),
         "pbm_apply_fine_f32": (i, [vp, i, i, vp, vp, vp, C.POINTER(C.c_double), vp]),
         "pbm_apply_level_f32": (i, [vp, i, i, i, vp, vp, vp, C.POINTER(C.c_double), vp]),
@@ -136,6 +142,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pbm_vcycle": (i, [vp, i, vp, vp, vp]),
         "pbm_minres_solve": (i, [vp, i, vp, vp, d, i, C.POINTER(SolveInfo), vp]),
         "pbm_newton_step": (i, [vp, C.POINTER(State), vp, d, C.POINTER(NewtonInfo), vp]),
+        "pbm_default_newton_params": (i, [C.POINTER(NewtonParams)]),
+        "pbm_newton_step_ex": (i, [vp, C.POINTER(State), vp, C.POINTER(NewtonParams), C.POINTER(NewtonInfo), vp]),
         "pbm_compliance_grad": (i, [vp, vp, vp, vp, C.POINTER(C.c_double), vp]),
         "pbm_kernel_launches": (C.c_int64, []),
         "pbm_batch_create": (i, [C.POINTER(vp), i, i, C.POINTER(vp)]),

@@ -576,17 +576,26 @@ int pbm_set_density(pbm_grid* g, const double* rho_dev, void* stream) {
     PBM_CATCH
 }
 
-int pbm_apply_K(pbm_grid* g, const double* w_dev, const double* x_dev, double* y_dev, void* stream) {
+int pbm_apply_K(pbm_grid* g, const double* w_dev, const double* x_dev, double* y_dev, int level, void* stream) {
     PBM_TRY
     if (!g || !x_dev || !y_dev) fail(PBM_EINVAL, "null argument");
+    if (level < 0 || level >= g->levels) fail(PBM_EINVAL, "level out of range");
+    if (level > 0 && w_dev) fail(PBM_EINVAL, "coarse levels apply the Galerkin operators of the set density: w must be NULL");
     if (!w_dev && !g->rho_set) fail(PBM_ESTATE, "no density set");
     set_device(g);
+    const cudaStream_t st = S(stream);
     ApplyArgs a{};
     a.x = x_dev;
     a.y = y_dev;
     a.mode = EPI_APPLY;
     a.dot_slot = -1;
-    launch_fine(g, false, w_dev ? w_dev : g->rho, nullptr, nullptr, a, S(stream));
+    if (level == 0) {
+        launch_fine(g, false, w_dev ? w_dev : g->rho, nullptr, nullptr, a, st);
+    } else {
+        // the Galerkin chain of K(rho) (Section 5.1): built here if no K solve or V-cycle has built it
+        if (g->op_ready != 1) setup_hierarchy(g, false, st);
+        launch_coarse(g, level, false, a, st);
+    }
     PBM_CATCH
 }
 
@@ -1041,9 +1050,13 @@ int pbm_minres_solve(pbm_grid* g, int op, const double* b_dev, double* x_dev, do
 // status of the step (PBM_OK or PBM_ENOTCONV); throws on every other error.
 // With res_prev >= 0 the MINRES tolerance adapts before the solve (Section 5.3): if res_PBM has not
 // fallen below 0.9 res_prev, *eps_mr = max(*eps_mr / 10, eps_mr_min).
+// A direction with grad L^T dxi >= 0 (not one of descent; Section 6 reports such directions from
+// inexact solves near the end of its largest runs) is solved again from zero with eps_mr / 10, down
+// to eps_mr_min; the tightened tolerance is kept (*eps_mr). If the direction is still not one of
+// descent at the floor the step is not taken: inf.stalled = 1, *stepped = false, PBM_ELINESEARCH.
 static int newton_core(pbm_grid* g, pbm_state* s, const double* f_dev, double* eps_mr_io, double eps_stop,
-                       pbm_newton_info& inf, void* stream, bool* stepped, double res_prev = -1.0,
-                       double eps_mr_min = 0.0) {
+                       pbm_newton_info& inf, void* stream, bool* stepped, double res_prev, double eps_mr_min,
+                       int max_halvings, int maxit) {
     int rc_solve = PBM_OK;
     *stepped = false;
     const cudaStream_t st = S(stream);
@@ -1064,43 +1077,60 @@ static int newton_core(pbm_grid* g, pbm_state* s, const double* f_dev, double* e
     inf.res_pbm = norms[0] / fnorm + std::fabs(norms[1]) / s->V + norms[2] / rho_n;
     if (eps_stop > 0.0 && inf.res_pbm < eps_stop) return PBM_OK;
     if (res_prev >= 0.0 && inf.res_pbm > 0.9 * res_prev) *eps_mr_io = std::max(0.1 * *eps_mr_io, eps_mr_min);
-    const double eps_mr = *eps_mr_io;
-    // reduced Newton system S dz = rhs (eq. (system))
-    PBM_CUDA(cudaMemsetAsync(dz, 0, sizeof(double) * (n + 1), st));
-    pbm_solve_info si{};
-    rc_solve = solve(g, true, rhs, dz, eps_mr, 10000, &si, st);
-    inf.minres_iterations = si.iterations;
-    inf.minres_relres = si.relres;
-    if (rc_solve == PBM_EBREAKDOWN) fail(PBM_EBREAKDOWN, "MINRES breakdown in the Newton system");
-    // per-element forms b = u^T K_e du, q = du^T K_e du; nu-step (eq. (deltanu))
+    double eps_mr = *eps_mr_io;
     double* c2 = g->aux64 + 5 * m;
     double* bq = g->aux64 + 6 * m;
     double* qq = g->aux64 + 7 * m;
-    launch_elem_energy(g, g->u64, dz, bq, st);
-    launch_elem_energy(g, dz, nullptr, qq, st);
-    launch_delta_nu(g, bq, g->aux64, dz + n, dl, dup, st);
-    // directional derivative grad L . dxi; grad_u L = K(rho') u - f = -(f - K(rho') u)
-    ApplyArgs a{};
-    a.x = g->u64;
-    a.y = r;
-    a.b = f_dev;
-    a.mode = EPI_RESID;
-    a.dot_slot = -1;
-    launch_fine(g, false, g->w64, nullptr, nullptr, a, st);
-    launch_dot(g, false, r, dz, n, 21, st);
-    launch_dot(g, false, g->aux64 + 3 * m, dl, m, 22, st);
-    launch_dot(g, false, g->aux64 + 4 * m, dup, m, 23, st);
+    // grad_u L = K(rho') u - f = -(f - K(rho') u), a function of the state only
+    {
+        ApplyArgs a{};
+        a.x = g->u64;
+        a.y = r;
+        a.b = f_dev;
+        a.mode = EPI_RESID;
+        a.dot_slot = -1;
+        launch_fine(g, false, g->w64, nullptr, nullptr, a, st);
+    }
     launch_dot(g, false, f_dev, g->u64, n, 28, st);
-    launch_dot(g, false, f_dev, dz, n, 29, st);
-    PBM_CUDA(cudaMemcpyAsync(&g->sc_host->red[20], &g->sc->red[20], sizeof(double) * 12, cudaMemcpyDeviceToHost, st));
-    PBM_CUDA(cudaStreamSynchronize(st));
-    const double* R = g->sc_host->red;
-    double dalpha = 0.0;
-    PBM_CUDA(cudaMemcpy(&dalpha, dz + n, sizeof(double), cudaMemcpyDeviceToHost));
     const double g_alpha = s->V - g->sum_rho1;
-    const double slope = -R[21] + g_alpha * dalpha + R[22] + R[23];
-    const double fTu = R[28], fTdu = R[29];
+    double slope = 0.0, dalpha = 0.0, fTu = 0.0, fTdu = 0.0;
+    for (;;) {
+        // reduced Newton system S dz = rhs (eq. (system)), from zero
+        PBM_CUDA(cudaMemsetAsync(dz, 0, sizeof(double) * (n + 1), st));
+        pbm_solve_info si{};
+        rc_solve = solve(g, true, rhs, dz, eps_mr, maxit, &si, st);
+        inf.minres_iterations += si.iterations;
+        inf.minres_relres = si.relres;
+        if (rc_solve == PBM_EBREAKDOWN) fail(PBM_EBREAKDOWN, "MINRES breakdown in the Newton system");
+        // per-element forms b = u^T K_e du, q = du^T K_e du; nu-step (eq. (deltanu))
+        launch_elem_energy(g, g->u64, dz, bq, st);
+        launch_elem_energy(g, dz, nullptr, qq, st);
+        launch_delta_nu(g, bq, g->aux64, dz + n, dl, dup, st);
+        // directional derivative grad L . dxi
+        launch_dot(g, false, r, dz, n, 21, st);
+        launch_dot(g, false, g->aux64 + 3 * m, dl, m, 22, st);
+        launch_dot(g, false, g->aux64 + 4 * m, dup, m, 23, st);
+        launch_dot(g, false, f_dev, dz, n, 29, st);
+        PBM_CUDA(cudaMemcpyAsync(&g->sc_host->red[20], &g->sc->red[20], sizeof(double) * 12, cudaMemcpyDeviceToHost,
+                                 st));
+        PBM_CUDA(cudaMemcpyAsync(&g->sc_host->ctl[7], dz + n, sizeof(double), cudaMemcpyDeviceToHost, st));
+        PBM_CUDA(cudaStreamSynchronize(st));
+        const double* R = g->sc_host->red;
+        dalpha = g->sc_host->ctl[7];
+        slope = -R[21] + g_alpha * dalpha + R[22] + R[23];
+        fTu = R[28];
+        fTdu = R[29];
+        if (slope < 0.0 || eps_mr <= eps_mr_min) break;
+        eps_mr = std::max(0.1 * eps_mr, eps_mr_min);
+        inf.resolves += 1;
+    }
+    *eps_mr_io = eps_mr;
+    inf.eps_mr = eps_mr;
     inf.slope = slope;
+    if (!(slope < 0.0)) {
+        inf.stalled = 1;
+        fail(PBM_ELINESEARCH, "no descent direction at the MINRES tolerance floor: the Newton step is not taken");
+    }
     auto lagr = [&](double kappa) {
         launch_lagr_terms(g, kappa, c2, bq, qq, s, dl, dup, s->alpha + kappa * dalpha, 24, st);
         PBM_CUDA(cudaMemcpyAsync(&g->sc_host->red[24], &g->sc->red[24], sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
@@ -1113,7 +1143,7 @@ static int newton_core(pbm_grid* g, pbm_state* s, const double* f_dev, double* e
     inf.lagrangian_old = L0;
     double kappa = 1.0;
     bool ok = false;
-    for (int h = 0; h <= 30; ++h) {
+    for (int h = 0; h <= max_halvings; ++h) {
         const double Lk = lagr(kappa);
         if (std::isfinite(Lk) && Lk <= L0 + 1e-4 * kappa * slope) {
             inf.lagrangian_new = Lk;
@@ -1134,18 +1164,33 @@ static int newton_core(pbm_grid* g, pbm_state* s, const double* f_dev, double* e
     return rc_solve;
 }
 
-int pbm_newton_step(pbm_grid* g, pbm_state* s, const double* f_dev, double eps_mr, pbm_newton_info* info,
-                    void* stream) {
+int pbm_default_newton_params(pbm_newton_params* p) {
+    if (!p) {
+        set_error("null argument");
+        return PBM_EINVAL;
+    }
+    p->eps_mr = 1e-4;
+    p->eps_mr_min = 1e-9;
+    p->max_halvings = 30;
+    p->maxit = 10000;
+    set_error("");
+    return PBM_OK;
+}
+
+int pbm_newton_step_ex(pbm_grid* g, pbm_state* s, const double* f_dev, const pbm_newton_params* prm,
+                       pbm_newton_info* info, void* stream) {
     pbm_newton_info inf{};
     int rc_solve = PBM_OK;
     PBM_TRY
-    if (!g || !f_dev) fail(PBM_EINVAL, "null argument");
+    if (!g || !f_dev || !prm) fail(PBM_EINVAL, "null argument");
     check_state(s);
-    if (!(eps_mr > 0.0)) fail(PBM_EINVAL, "eps_mr must be > 0");
+    if (!(prm->eps_mr > 0.0) || !(prm->eps_mr_min > 0.0) || prm->max_halvings < 0 || prm->maxit < 1)
+        fail(PBM_EINVAL, "eps_mr and eps_mr_min must be > 0, max_halvings >= 0, maxit >= 1");
     set_device(g);
     bool stepped = false;
-    double eps_mr_v = eps_mr;
-    rc_solve = newton_core(g, s, f_dev, &eps_mr_v, -1.0, inf, stream, &stepped);
+    double eps_mr_v = prm->eps_mr;
+    rc_solve = newton_core(g, s, f_dev, &eps_mr_v, -1.0, inf, stream, &stepped, -1.0,
+                           std::min(prm->eps_mr_min, prm->eps_mr), prm->max_halvings, prm->maxit);
     inf.status = rc_solve;
     if (info) *info = inf;
     if (rc_solve != PBM_OK) {
@@ -1163,6 +1208,14 @@ int pbm_newton_step(pbm_grid* g, pbm_state* s, const double* f_dev, double eps_m
     return PBM_OK;
 }
 
+int pbm_newton_step(pbm_grid* g, pbm_state* s, const double* f_dev, double eps_mr, pbm_newton_info* info,
+                    void* stream) {
+    pbm_newton_params prm;
+    pbm_default_newton_params(&prm);
+    prm.eps_mr = eps_mr;
+    return pbm_newton_step_ex(g, s, f_dev, &prm, info, stream);
+}
+
 int pbm_default_pbm_params(pbm_pbm_params* p) {
     if (!p) {
         set_error("null argument");
@@ -1178,6 +1231,7 @@ int pbm_default_pbm_params(pbm_pbm_params* p) {
     p->eps_mr_min = 1e-9;
     p->max_outer = 100;
     p->max_newton = 100;
+    p->max_halvings = 30;
     set_error("");
     return PBM_OK;
 }
@@ -1190,7 +1244,7 @@ int pbm_solve(pbm_grid* g, pbm_state* s, const double* f_dev, const pbm_pbm_para
     check_state(s);
     if (!(prm->beta > 0.0 && prm->beta < 1.0) || !(prm->gamma > 0.0 && prm->gamma < 1.0) || !(prm->p_min > 0.0) ||
         !(prm->eps_pbm > 0.0) || !(prm->eps_nwt > 0.0) || !(prm->eps_nwt_min > 0.0) || prm->max_outer < 1 ||
-        prm->max_newton < 1)
+        prm->max_newton < 1 || prm->max_halvings < 0 || !(prm->eps_mr_min > 0.0))
         fail(PBM_EINVAL, "invalid PBM parameters");
     set_device(g);
     const cudaStream_t st = S(stream);
@@ -1206,11 +1260,25 @@ int pbm_solve(pbm_grid* g, pbm_state* s, const double* f_dev, const pbm_pbm_para
         for (int it = 0; it < prm->max_newton; ++it) {
             pbm_newton_info ni{};
             bool stepped = false;
-            const int rc = newton_core(g, s, f_dev, &eps_mr, eps, ni, stream, &stepped, res_prev, prm->eps_mr_min);
-            (void)rc;   // an inexact solve still gives a descent step; the Newton loop goes on
+            try {
+                // a solve that stopped at maxit still gave a descent direction (checked in newton_core)
+                (void)newton_core(g, s, f_dev, &eps_mr, eps, ni, stream, &stepped, res_prev, prm->eps_mr_min,
+                                  prm->max_halvings, 10000);
+            } catch (const Error& e) {
+                inf.resolves += ni.resolves;
+                inf.minres += ni.minres_iterations;
+                if (e.code == PBM_ELINESEARCH && ni.stalled) {
+                    // no descent direction even at eps_mr_min: the loop ends at the current iterate, which
+                    // Section 6 accepts as the nearly optimal solution of a stalled run
+                    inf.stalls += 1;
+                    return;
+                }
+                throw;
+            }
+            inf.resolves += ni.resolves;
+            inf.minres += ni.minres_iterations;
             if (!stepped) return;
             inf.newton += 1;
-            inf.minres += ni.minres_iterations;
             res_prev = ni.res_pbm;
         }
         fail(PBM_ENOTCONV, "Newton loop reached max_newton steps");

@@ -72,3 +72,14 @@ def test_coarsest_too_large_rejected(lib):
 def test_null_arguments(lib):
     assert lib.pbm_create_grid(None, None) == _lib.PBM_EINVAL
     assert lib.pbm_destroy_grid(None) == 0
+
+
+def test_newton_params_defaults_and_rejection(lib):
+    p = _lib.NewtonParams()
+    assert lib.pbm_default_newton_params(C.byref(p)) == 0
+    assert (p.eps_mr, p.eps_mr_min, p.max_halvings, p.maxit) == (1e-4, 1e-9, 30, 10000)
+    info = _lib.NewtonInfo()
+    assert lib.pbm_newton_step_ex(None, None, None, C.byref(p), C.byref(info), None) == _lib.PBM_EINVAL
+    q = _lib.PbmParams()
+    assert lib.pbm_default_pbm_params(C.byref(q)) == 0
+    assert q.max_halvings == 30 and q.eps_mr_min == 1e-9 and q.max_newton == 100

@@ -246,6 +246,60 @@ def test_res_pbm_vanishes_at_a_stationary_point():
     assert pbm.res_pbm(pb, st0) > 0.1
 
 
+# ---------------------------------------------------------------------------------------------------------------
+# non-descent directions of inexact solves (Section 6) and their recovery
+# ---------------------------------------------------------------------------------------------------------------
+
+def _nondescent_case():
+    """8x4x4 bridge, random state at penalties p = q = 1e-6 (late-PBM conditioning): the MINRES iterate at
+    eps_MR = 0.5 is not a descent direction, the one at 0.05 is."""
+    nx, ny, nz = 8, 4, 4
+    g = fem.Grid(nx, ny, nz, "bridge_corners")
+    f = synthetic.load_vector(nx, ny, nz, "top_traction")
+    d = synthetic.random_state(nx, ny, nz, 9, u_scale=0.5, p=1e-6, q=1e-6, fixed_dofs=g.fixed_dofs())
+    pb = pbm.Problem(g, f, d["V"], d["rho_lo"], d["rho_up"])
+    return pb, pbm.State.from_dict(d)
+
+
+def _fd_directional_derivative(pb, st, dz, dl, dup, h=1e-9):
+    def L(t):
+        s = st.copy()
+        s.u = pbm.masked(pb, st.u + t * dz[:pb.n])
+        s.alpha = st.alpha + t * dz[pb.n]
+        s.nu_lo = st.nu_lo + t * dl
+        s.nu_up = st.nu_up + t * dup
+        return pbm.lagrangian(pb, s)
+    return (L(h) - L(-h)) / (2 * h)
+
+
+def test_loose_solve_gives_a_non_descent_direction():
+    """The premise of the recovery, measured on L itself (central differences along the Newton direction, not the
+    oracle's gradient): ascent at eps_MR = 0.5, descent at eps_MR = 0.05."""
+    pb, st = _nondescent_case()
+    cf = pbm.coeffs(pb, st)
+    rhs = pbm.rhs_closed(pb, st, cf)
+    signs = []
+    for eps in (0.5, 0.05):
+        dz, _ = pbm.solve_reduced(pb, st, cf, rhs, eps, 3)
+        dl, dup = pbm.delta_nu(pb, st, cf, dz)
+        signs.append(np.sign(_fd_directional_derivative(pb, st, dz, dl, dup)))
+    assert signs == [1.0, -1.0]
+
+
+def test_newton_recovers_from_a_non_descent_direction():
+    """Algorithm 2 with the re-solve of Section 6's failure mode: one tightening (0.5 -> 0.05), then a descent
+    step accepted by Armijo that lowers L."""
+    pb, st = _nondescent_case()
+    st1, info, eps = pbm.newton(pb, st, eps_nwt=0.0, eps_mr=0.5, levels=3, max_iter=1)
+    assert info.resolves == 1 and abs(eps - 0.05) < 1e-15 and not info.stalled
+    assert info.iters == 1 and info.slopes[0] < 0
+    assert pbm.lagrangian(pb, st1) < pbm.lagrangian(pb, st)
+    # at the floor there is no recovery: the loop stalls at the current iterate and leaves it unchanged
+    st2, info2, _ = pbm.newton(pb, st, eps_nwt=0.0, eps_mr=0.5, levels=3, max_iter=1, eps_mr_min=0.5)
+    assert info2.stalled and info2.iters == 0 and info2.resolves == 0
+    assert np.array_equal(st2.u, st.u) and st2.alpha == st.alpha
+
+
 @pytest.fixture(scope="module")
 def pbm_run():
     nx, ny, nz = 4, 2, 2
