@@ -3,21 +3,24 @@
 
 One step is one complete reduced Newton system of the synthetic workload, every row of the hot path:
   * Newton state set-up (per-element coefficients rho', rho'', mu'', d, eps; the alpha border; the Galerkin
-    coarse operators of S on every level; Jacobi diagonals; Lanczos estimates of the Jacobi weights; the
+    coarse operators of S on every level; Jacobi diagonals; Lanczos estimates of the smoother weights; the
     Cholesky inverse of the coarsest bordered matrix),
   * the right-hand side of eq. (system),
   * MINRES preconditioned by one V-cycle per iteration, until the true 2-norm relative residual is at most rtol.
 
-Default workload (single-GPU): the 64 x 32 x 32 cantilever in FP64 (5-level V-cycle, rtol 1e-8), densities
-U[1e-3, 1] from seed 0 rescaled to mean 0.3, multipliers and penalties 1, and u the equilibrium displacement
-of K(rho) u = f (computed before timing by the library's own K solve). The JSON line reports whole-job solves
-per second (device-resident inputs, L2 flushed between steps), the same measured end to end through the C ABI
-with the inputs copied from pinned host memory and the solution copied back every step, the roofline of the
-fine-level S kernel (timed live by the library with CUDA events on its launch stream), the clocks sampled
-during the timed region and the CPU oracle's time for the same system.
+Default workload: the 128 x 64 x 64 bridge (four bottom corners fixed, unit top traction, 32-bump density at
+volume fraction 0.2, 6-level V-cycle, rtol 1e-8) at its synthetic Newton state, solved with FP32 inner solves inside
+FP64 refinement ("mixed", the JSON line's value) and, in the same process on the same inputs, with the plain FP64
+solve; both solutions are compared with the oracle's reference solution of the same system
+(tests/golden/bridge128_dz_ref.npy, MG-MINRES to about 2e-14, written by tests/golden/make_bridge128_reference.py).
+The JSON line reports whole-job solves per second (device-resident inputs, L2 flushed between steps), the same
+measured end to end through the C ABI with the inputs copied from pinned host memory and the solution copied back
+every step, the roofline of the fine-level FP32 S kernel (timed live by the library with CUDA events on its launch
+stream), the clocks sampled during the timed region and the CPU oracle's time for a bounded sample of the same
+system.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cant64|bridge128]
-                  [--precision fp64|mixed]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload bridge128|cant64|...]
+                  [--precision mixed|fp64] [--no-compare]
 
 `--impl reference` times the CPU oracle (oracle/, numpy/scipy) on the host cores for the same workload and
 metric. With N > 1 (torchrun) every rank solves its own replica of the workload (weak scaling; the solve itself
@@ -27,8 +30,11 @@ from __future__ import annotations
 
 import os
 
+# dense and factorisation parts of the CPU oracle (BLAS) use every host core; scipy's sparse products are
+# single-threaded whatever this says
+_NCPU = str(os.cpu_count() or 1)
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-    os.environ.setdefault(_v, "1")
+    os.environ.setdefault(_v, _NCPU)
 
 import argparse  # noqa: E402
 import hashlib  # noqa: E402
@@ -64,11 +70,15 @@ FP64_OPS_PEAK = 2.0 * 152 * 2.07e9
 FALLBACK_HBM_GBS = 6800.0
 
 
-def workload_desc(w, precision, smoother="jacobi"):
-    return {"workload": f"{w.name}: {w.nx}x{w.ny}x{w.nz} Q1 hex {w.bc}, {precision}, single reduced-Newton solve",
+def workload_desc(w, precision, smoother="jacobi", compare=None):
+    prec = precision if not compare else f"{precision} (FP32 inner solves in FP64 refinement) vs {compare}"
+    u = w.extra.get("u")
+    return {"workload": f"{w.name}: {w.nx}x{w.ny}x{w.nz} Q1 hex {w.bc}, {prec}, single reduced-Newton solve",
             "smoother": smoother,
             "grid": [w.nx, w.ny, w.nz], "support": w.bc, "load": w.loads[0], "density": w.density,
             "volume_fraction": w.vf, "levels": w.levels, "rtol": w.rtol, "precision": precision,
+            "state_u": (f"seeded smooth field (seed {u[1]}, max |u| = {u[2]})" if u else
+                        "equilibrium displacement of K(rho) u = f (library FP64 solve, untimed)"),
             "n_dofs": w.n, "m_elements": w.m,
             "l2": "flushed: a 256 MiB buffer is written between timed steps (outside the step's events)"}
 
@@ -200,6 +210,26 @@ def profiled_traffic(name: str, precision: str):
 # ------------------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------------------
+REF_DIR = os.path.join(ROOT, "tests", "golden")
+
+
+def oracle_reference(w, rho, f, u):
+    """The oracle's stored reference solution of the workload's reduced system, if one exists and was written for
+    these exact inputs (SHA-256 of rho, f, u); else (None, reason)."""
+    npy = os.path.join(REF_DIR, f"{w.name}_dz_ref.npy")
+    meta_path = os.path.join(REF_DIR, f"{w.name}_dz_ref.json")
+    if not (os.path.exists(npy) and os.path.exists(meta_path)):
+        return None, f"no stored oracle reference for {w.name}"
+    with open(meta_path) as fh:
+        meta = json.load(fh)
+    h = hashlib.sha256()
+    for a in (rho, f, u):
+        h.update(np.ascontiguousarray(a, dtype=np.float64).tobytes())
+    if h.hexdigest() != meta.get("inputs_sha256"):
+        return None, "stored oracle reference was written for other inputs"
+    return (np.load(npy), meta), None
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -215,71 +245,94 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     w = synthetic.WORKLOADS[args.workload]
     precision = args.precision
+    other = "fp64" if (precision == "mixed" and not args.no_compare) else None
 
     def t64(a):
         return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
 
-    # ---- inputs (untimed): density, load, equilibrium displacement, synthetic Newton state ----
+    # ---- inputs (untimed): density, load, the state's displacement, synthetic Newton state ----
     rho = synthetic.density_for(w)
     f_h = synthetic.load_vector(w.nx, w.ny, w.nz, w.loads[0])
     f = t64(f_h)
-    # the input displacement: equilibrium of K(rho) u = f by the library's FP64 K solve, to the
-    # workload's tolerance (untimed; the 4-corner bridge levels off near 1e-8 in FP64)
-    with pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision="fp64") as G64:
-        G64.set_density(t64(rho))
-        u, uinfo = G64.minres_solve("K", f, rtol=w.rtol, maxit=2000, check=False)
-    if not uinfo["relres"] <= 1e-6:
-        raise RuntimeError(f"equilibrium solve of the input state failed: {uinfo}")
-    G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=precision, smoother=args.smoother)
-    G.set_density(t64(rho))
-    st_h = synthetic.synthetic_state(w, np.zeros(w.n))
+    u_h = synthetic.state_displacement(w)
+    uinfo = None
+    if u_h is None:
+        # the equilibrium of K(rho) u = f by the library's FP64 K solve, to the workload's tolerance
+        with pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision="fp64") as G64:
+            G64.set_density(t64(rho))
+            u, uinfo = G64.minres_solve("K", f, rtol=w.rtol, maxit=2000, check=False)
+        if not uinfo["relres"] <= 1e-6:
+            raise RuntimeError(f"equilibrium solve of the input state failed: {uinfo}")
+        u_h = u.cpu().numpy()
+    else:
+        u = t64(u_h)
+    st_h = synthetic.synthetic_state(w, u_h)
     sd = {k: t64(st_h[k]) for k in ("nu_lo", "nu_up", "rho", "mu_lo", "mu_up")}
     sd["u"] = u
     sd.update({k: float(st_h[k]) for k in ("alpha", "p", "q_lo", "q_up", "V", "rho_lo", "rho_up")})
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > 2 x L2
+
+    def make_grid(prec):
+        G = pkg.Grid(w.nx, w.ny, w.nz, w.levels, w.bc, precision=prec, smoother=args.smoother)
+        G.set_density(t64(rho))
+        return G
+
+    def make_step(G, last, ph=None):
+        def step():
+            if ph:
+                ph[0].record(stream)
+            G.set_state(sd)
+            if ph:
+                ph[1].record(stream)
+            rhs = G.reduced_rhs(f)
+            if ph:
+                ph[2].record(stream)
+            x, info = G.minres_solve("S", rhs, rtol=w.rtol, maxit=1000)
+            if ph:
+                ph[3].record(stream)
+            last["info"] = info
+            last["x"] = x
+            return x
+        return step
+
+    def timed(step, last, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        its = []
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            its.append(last["info"]["iterations"])
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev], its
+
+    # ---- the measured precision ----
+    G = make_grid(precision)
     last = {}
-
     ph = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-
-    def step():
-        ph[0].record(stream)
-        G.set_state(sd)
-        ph[1].record(stream)
-        rhs = G.reduced_rhs(f)
-        ph[2].record(stream)
-        x, info = G.minres_solve("S", rhs, rtol=w.rtol, maxit=1000)
-        ph[3].record(stream)
-        last["info"] = info
-        return x
-
+    step = make_step(G, last, ph)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-
-    # ---- device-resident timed region ----
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(torch.cuda.current_device())
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
     n0 = pkg.kernel_launches()
-    iters = []
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        step()
-        ev[i][1].record(stream)
-        iters.append(last["info"]["iterations"])
-    torch.cuda.synchronize()
+    step_ms, iters = timed(step, last, args.steps)
     launches = pkg.kernel_launches() - n0
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     phases = {"set_state_ms": ph[0].elapsed_time(ph[1]), "rhs_ms": ph[1].elapsed_time(ph[2]),
               "minres_ms": ph[2].elapsed_time(ph[3])}
+    x_main = last["x"].detach().cpu().numpy()
+    info_main = last["info"]
+    total_ms = max_over_ranks(float(sum(step_ms)), dev)
+    value = whole_job_rate(world, args.steps, total_ms)
 
     # ---- the same steps again with every fine-level S launch bracketed by CUDA events on its stream
     # (pbm_profile): the roofline's kernel durations. Profiled solves launch eagerly, because an
@@ -287,20 +340,16 @@ def run_ours(args):
     G.profile(True)
     G.profile_read("S")
     G.profile_read("K")
-    for i in range(args.steps):
+    for _ in range(args.steps):
         flush.zero_()
         step()
     torch.cuda.synchronize()
     prof = G.profile_read("S")
     G.profile(False)
-    total_ms = max_over_ranks(float(sum(step_ms)), dev)
-    value = whole_job_rate(world, args.steps, total_ms)
-    relres = last["info"]["relres"]
 
     # ---- end to end through the C ABI: pinned host inputs in, solution out, every step ----
-    host_in = {k: torch.as_tensor(np.ascontiguousarray(st_h[k] if k != "u" else u.cpu().numpy()),
-                                  dtype=torch.float64).pin_memory() for k in ("u", "nu_lo", "nu_up", "rho", "mu_lo",
-                                                                             "mu_up")}
+    host_in = {k: torch.as_tensor(np.ascontiguousarray(st_h[k] if k != "u" else u_h), dtype=torch.float64)
+               .pin_memory() for k in ("u", "nu_lo", "nu_up", "rho", "mu_lo", "mu_up")}
     host_in["f"] = torch.as_tensor(f_h, dtype=torch.float64).pin_memory()
     host_out = torch.empty(w.n + 1, dtype=torch.float64).pin_memory()
     dev_in = {k: torch.empty_like(v, device=dev) for k, v in host_in.items()}
@@ -331,13 +380,53 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in ev2)), dev)
     e2e_value = whole_job_rate(world, args.steps, e2e_ms)
-
-    # ---- standalone K(rho) u applies at the workload size (metric's second half), L2 flushed and warm ----
+    solve = {"minres_iterations": iters[-1], "true_relres": info_main["relres"], "phases_last_step": phases,
+             "mixed_outer_steps": info_main["outer"], "fine_chunk": G.info()["fine_chunk"],
+             "fp32_tile_K_S": G.info()["fp32_tile"], "step_ms_min": min(step_ms),
+             "step_ms_median": statistics.median(step_ms)}
+    if uinfo is not None:
+        solve["equilibrium_u_relres"] = uinfo["relres"]
     kapply = k_apply_rates(G, w, rho, dev, flush)
+    G.close()
+
+    # ---- the other precision on the same inputs, same protocol (the metric's FP32-mixed vs FP64 comparison) ----
+    x_other = None
+    if other:
+        G2 = make_grid(other)
+        last2 = {}
+        step2 = make_step(G2, last2)
+        for _ in range(args.warmup):
+            step2()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms2, its2 = timed(step2, last2, args.steps)
+        tot2 = max_over_ranks(float(sum(ms2)), dev)
+        x_other = last2["x"].detach().cpu().numpy()
+        solve["compare"] = {"precision": other, "systems_per_s": whole_job_rate(world, args.steps, tot2),
+                            "ms_per_step": tot2 / args.steps, "minres_iterations": its2[-1],
+                            "true_relres": last2["info"]["relres"], "step_ms_median": statistics.median(ms2)}
+        solve["speedup_vs_" + other] = (tot2 / args.steps) / (total_ms / args.steps)
+        G2.close()
+
+    # ---- error of each solution against the oracle's reference solution (outside every timed region) ----
+    ref, why = oracle_reference(w, rho, f_h, u_h)
+    if ref is not None:
+        dz_ref, meta = ref
+        nref = float(np.linalg.norm(dz_ref))
+        solve["error_vs_oracle"] = float(np.linalg.norm(x_main - dz_ref) / nref)
+        if x_other is not None:
+            solve["compare"]["error_vs_oracle"] = float(np.linalg.norm(x_other - dz_ref) / nref)
+        solve["oracle_reference"] = {"relres": meta["relres"], "iterations": meta["iterations"],
+                                     "solver": meta["solver"]}
+    else:
+        solve["error_vs_oracle"] = None
+        solve["oracle_reference"] = why
 
     # ---- roofline of the fine-level S kernel ----
     peaks, peak_src = measured_peaks()
     avg_ms = prof["total_ms"] / max(prof["launches"], 1)
+    of = "of measured" if peak_src == "measured" else "of fallback"
     if precision == "fp64":
         achieved = prof["flops"] / (prof["total_ms"] / 1e3) / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_OPS_PEAK / 1e9, "unit": "G FP64 op/s",
@@ -347,30 +436,25 @@ def run_ours(args):
                            "(node sums with the fused residual / Jacobi / dot epilogues), timed as one launch pair")}
         hbm = prof["bytes"] / (prof["total_ms"] / 1e3) / 1e9
         roof["hbm_achieved_gbs"] = hbm
-        roof["hbm_frac_of_measured"] = hbm / peaks["hbm_gbs"]
+        roof["hbm_frac_" + of.replace(" ", "_")] = hbm / peaks["hbm_gbs"]
     else:
         achieved = prof["bytes"] / (prof["total_ms"] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{peak_src} (MEASURED_PEAKS hbm_gbs)",
-                "kernel": ("fine-level S operator: k_fused_f32<2, threads, CTAs per SM> (single pass: element "
-                           "columns with W_e recomputed from u, node sums, fused residual / Jacobi / dot epilogues)")}
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{peak_src} (MEASURED_PEAKS hbm_gbs), {of}",
+                "kernel": "fine-level FP32 S operator (single pass, the autotuned plan in fp32_tile_K_S[1]) with its "
+                          "fused residual / Jacobi / Chebyshev / dot epilogues, every launch of the solve"}
     roof.update({"launches": prof["launches"], "avg_launch_us": avg_ms * 1e3,
                  "bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
                  "ops_per_launch": prof["flops"] / max(prof["launches"], 1)})
-    tr = profiled_traffic(f"fine_S_apply_{precision}_{w.name}.md", precision)
-    roof["traffic"] = tr
+    roof["traffic"] = profiled_traffic(f"fine_S_apply_{precision}_{w.name}.md", precision)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32+f64",
-        "data": "synthetic (seeded; shapes of the paper's cantilever example, Section 6)",
-        "config": workload_desc(w, precision, args.smoother),
-        "solve": {"minres_iterations": iters[-1], "true_relres": relres, "phases_last_step": phases,
-                  "mixed_outer_steps": last["info"]["outer"], "fine_chunk": G.info()["fine_chunk"],
-                  "fp32_tile_K_S": G.info()["fp32_tile"],
-                  "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
-                  "equilibrium_u_relres": uinfo["relres"]},
+        "data": "synthetic (seeded; shapes of the paper's Section 6 examples)",
+        "config": workload_desc(w, precision, args.smoother, other),
+        "solve": solve,
         "k_apply": kapply,
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -737,41 +821,101 @@ def oracle_inputs(w):
     g = fem.Grid(w.nx, w.ny, w.nz, w.bc)
     rho = synthetic.density_for(w)
     f = synthetic.load_vector(w.nx, w.ny, w.nz, w.loads[0])
-    K = fem.assemble_K(g, rho, fem.element_stiffness(w.E, w.nu))
-    h = solvers.Hierarchy(g, K, w.levels, has_alpha=False)
-    u = solvers.minres(lambda v: K @ v, f, h.vcycle, rtol=1e-12, maxit=2000).x
+    u = synthetic.state_displacement(w)
+    if u is None:
+        K = fem.assemble_K(g, rho, fem.element_stiffness(w.E, w.nu))
+        h = solvers.Hierarchy(g, K, w.levels, has_alpha=False)
+        u = solvers.minres(lambda v: K @ v, f, h.vcycle, rtol=1e-12, maxit=2000).x
     d = synthetic.synthetic_state(w, u)
-    pb = pbm.Problem(g, f, d["V"], d["rho_lo"], d["rho_up"], E=w.E, nu=w.nu)
+    pb = pbm.Problem(g, f, d["V"], d["rho_lo"], d["rho_up"])
     return pb, pbm.State.from_dict(d)
 
 
-def oracle_step(w, pb, st, smoother="jacobi"):
-    """One reduced Newton system by the oracle: coefficients, S in CSR, Galerkin hierarchy, rhs, MG-MINRES."""
+def oracle_step(w, pb, st, smoother="jacobi", levels=None, maxit=1000, rtol=None):
+    """One reduced Newton system by the oracle: coefficients, S in CSR, Galerkin hierarchy, rhs, MG-MINRES.
+    Returns (MINRES result, set-up seconds, solve seconds)."""
     from oracle import pbm, solvers
+    t0 = time.perf_counter()
     cf = pbm.coeffs(pb, st)
     S = pbm.assemble_S(pb, st, cf)
     rhs = pbm.rhs_closed(pb, st, cf)
-    h = solvers.Hierarchy(pb.grid, S, w.levels, has_alpha=True, smoother=smoother)
-    r = solvers.minres(lambda v: S @ v, rhs, h.vcycle, rtol=w.rtol, maxit=1000)
-    return r
+    h = solvers.Hierarchy(pb.grid, S, levels or w.levels, has_alpha=True, smoother=smoother)
+    t1 = time.perf_counter()
+    r = solvers.minres(lambda v: S @ v, rhs, h.vcycle, rtol=rtol or w.rtol, maxit=maxit)
+    return r, t1 - t0, time.perf_counter() - t1
+
+
+# workloads whose complete oracle system takes more than a few seconds are sampled: an x-slab of the same grid,
+# densities and state (every element's set-up and every MINRES iteration cost the same per element), timed for its
+# set-up and a few MG-MINRES iterations, scaled to the full element count and to the oracle's own iteration count
+SLAB_NX = {"bridge128": 16, "cant256": 16}
+
+
+def _slab(w, nx_s):
+    """The x-slab [0, nx_s] of workload w: its grid, densities, state displacement and load, as an oracle problem."""
+    from oracle import fem, pbm
+    rho = synthetic.density_for(w).reshape(w.nz, w.ny, w.nx)[:, :, :nx_s].ravel()
+    u_full = synthetic.state_displacement(w)
+    if u_full is None:
+        u_full = synthetic.smooth_displacement(w.nx, w.ny, w.nz, 5, 1.0)
+    u = u_full.reshape(w.nz + 1, w.ny + 1, w.nx + 1, 3)[:, :, :nx_s + 1, :].ravel().copy()
+    g = fem.Grid(nx_s, w.ny, w.nz, w.bc)
+    u[g.fixed_dofs()] = 0.0
+    f = synthetic.load_vector(nx_s, w.ny, w.nz, w.loads[0])
+    m = g.m
+    d = dict(u=u, alpha=1.0, nu_lo=np.ones(m), nu_up=np.ones(m), rho=rho, mu_lo=np.ones(m), mu_up=np.ones(m),
+             p=1.0, q_lo=1.0, q_up=1.0, V=w.vf * m, rho_lo=w.rho_lo, rho_up=w.rho_up)
+    return pbm.Problem(g, f, d["V"], d["rho_lo"], d["rho_up"]), pbm.State.from_dict(d)
+
+
+def oracle_sample_seconds(w, smoother, ctx):
+    """Seconds of one complete reduced Newton system of workload w by the oracle, measured on a bounded sample.
+    ctx caches the sample's inputs across calls. Returns (seconds, description of the sample)."""
+    nx_s = SLAB_NX.get(w.name)
+    if nx_s is None:
+        if "full" not in ctx:
+            ctx["full"] = oracle_inputs(w)
+        pb, st = ctx["full"]
+        r, ts, tm = oracle_step(w, pb, st, smoother)
+        return ts + tm, (f"the complete system (coefficients, CSR S, Galerkin hierarchy, rhs, MG-MINRES to "
+                         f"{w.rtol:g}: {r.iters} iterations)")
+    if "slab" not in ctx:
+        ctx["slab"] = _slab(w, nx_s)
+        meta_path = os.path.join(REF_DIR, f"{w.name}_dz_ref.json")
+        iters = None
+        if os.path.exists(meta_path):
+            with open(meta_path) as fh:
+                iters = json.load(fh).get("iterations_to_1e-8")
+        ctx["iters"] = iters or 40
+    pb, st = ctx["slab"]
+    k = 3
+    levels = min(w.levels, int(np.log2(nx_s)) + 1)
+    r, ts, tm = oracle_step(w, pb, st, smoother, levels=levels, maxit=k, rtol=1e-30)
+    scale = w.m / pb.grid.m
+    per_it = tm / max(r.iters, 1)
+    secs = scale * (ts + ctx["iters"] * per_it)
+    return secs, (f"x-slab {nx_s}x{w.ny}x{w.nz} (1/{scale:g} of the elements) of the same system: set-up "
+                  f"(coefficients, CSR S, {levels}-level Galerkin hierarchy, rhs) and {r.iters} MG-MINRES "
+                  f"iterations timed, scaled by {scale:g} to the full element count and to the "
+                  f"{ctx['iters']} iterations the oracle needs to {w.rtol:g} on the full system")
 
 
 def cpu_baseline(w, budget_s, smoother="jacobi"):
-    pb, st = oracle_inputs(w)
-    times = []
+    ctx = {}
+    times, desc = [], ""
     t_all = time.perf_counter()
     while True:
         t0 = time.perf_counter()
-        r = oracle_step(w, pb, st, smoother)
-        times.append(time.perf_counter() - t0)
-        if time.perf_counter() - t_all + times[-1] > budget_s or len(times) >= 5:
+        secs, desc = oracle_sample_seconds(w, smoother, ctx)
+        times.append(secs)
+        if time.perf_counter() - t_all + (time.perf_counter() - t0) > budget_s or len(times) >= 5:
             break
     tm = statistics.median(times)
-    return {"value": 1.0 / tm, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{len(times)} complete reduced-Newton system(s) of the same workload by the oracle "
-                       f"(numpy/scipy CSR: coefficients, S assembly, Galerkin hierarchy, rhs, MG-MINRES to "
-                       f"{w.rtol:g}: {r.iters} iterations); median {tm:.2f} s; BLAS/OpenMP threads pinned to 1, "
-                       f"scipy sparse products are single-threaded")}
+    return {"value": 1.0 / tm, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "blas_threads": int(os.environ.get("OPENBLAS_NUM_THREADS", "1")),
+            "sample": (f"{len(times)} sample(s): {desc}; median {tm:.2f} s per system; BLAS/OpenMP threads = "
+                       f"{os.environ.get('OPENBLAS_NUM_THREADS')} of {os.cpu_count()} host cores (dense coarsest "
+                       f"factorisation), scipy sparse products single-threaded")}
 
 
 def run_reference(args):
@@ -779,29 +923,30 @@ def run_reference(args):
     if rank != 0:
         return
     w = synthetic.WORKLOADS[args.workload]
-    pb, st = oracle_inputs(w)
+    ctx = {}
     budget = args.cpu_budget_s * 6
     t_start = time.perf_counter()
+    desc = ""
     for _ in range(min(args.warmup, 1)):
-        oracle_step(w, pb, st, args.smoother)
+        _, desc = oracle_sample_seconds(w, args.smoother, ctx)
     times = []
-    r = None
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        r = oracle_step(w, pb, st, args.smoother)
-        times.append(time.perf_counter() - t0)
-        if time.perf_counter() - t_start + times[-1] > budget:
+        secs, desc = oracle_sample_seconds(w, args.smoother, ctx)
+        times.append(secs)
+        if time.perf_counter() - t_start + (time.perf_counter() - t0) > budget:
             break
     total = sum(times)
     value = len(times) / total
+    other = "fp64" if (args.precision == "mixed" and not args.no_compare) else None
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": len(times), "steps_requested": args.steps, "warmup": min(args.warmup, 1),
            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-           "config": workload_desc(w, "fp64", args.smoother),
-           "solve": {"minres_iterations": r.iters, "true_relres": r.relres},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"{len(times)} complete reduced-Newton systems of the workload by the oracle"},
+           "config": workload_desc(w, args.precision, args.smoother, other),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "blas_threads": int(os.environ.get("OPENBLAS_NUM_THREADS", "1")),
+                            "sample": f"every step: {desc}"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -812,7 +957,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="cant64",
+    ap.add_argument("--workload", default="bridge128",
                     choices=["cant64", "bridge128", "cant32", "cant16", "cant256", "batch48"])
     ap.add_argument("--pbm", action="store_true", help="time one complete PBM run (Algorithm 1) on the workload")
     ap.add_argument("--ip", action="store_true", help="time interior-point Newton systems (Section 4.1)")
@@ -820,7 +965,9 @@ def main():
     ap.add_argument("--compare-fp64", action="store_true", help="with --pbm: also run the other precision")
     ap.add_argument("--fp32-plans", action="store_true",
                     help="time every tile plan of the FP32 fine operator on the workload's grid")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-compare", action="store_true",
+                    help="with --precision mixed: skip the FP64 solve of the same system")
     ap.add_argument("--smoother", default="chebyshev", choices=["jacobi", "chebyshev", "gauss_seidel"],
                     help="V-cycle smoothing: Chebyshev acceleration of Jacobi (default; fewer MINRES iterations "
                          "for the same operator applications) or damped Jacobi")

@@ -20,55 +20,12 @@
 // in a fixed order, so results are bit-reproducible for a given tile plan.
 #include <algorithm>
 
+#include "fp32_elem.h"
 #include "pbm_internal.h"
 
 namespace pbm {
 
 constexpr int FSLOT = 4;   // staging slots per thread: 3 (TX + 2)(TY + 2) <= FSLOT * NT
-
-// The element arithmetic keeps displacement components x and y of a coefficient as one float2 and
-// runs it with the paired FP32 instructions (one instruction for two operations), component z alone.
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
-// Khat of pbm_internal.h with the diagonal of components x, y as pairs
-struct KeHat2 {
-    float2 dg01[8];
-    float dg2[8];
-    float lam4[2];
-    float mu4[2];
-};
-
-// Y = Khat X on (x, y) pairs and z: the diagonal in pairs, the couplings per component
-__device__ __forceinline__ void khat_apply2(const KeHat2& K, const float2 (&X01)[8], const float (&X2)[8],
-                                            float2 (&Y01)[8], float (&Y2)[8]) {
-    auto get = [&](int d, int i) -> float { return d == 0 ? X01[i].x : (d == 1 ? X01[i].y : X2[i]); };
-#pragma unroll
-    for (int q = 1; q < 8; ++q) {
-        Y01[q] = mul2(K.dg01[q], X01[q]);
-        Y2[q] = K.dg2[q] * X2[q];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float acc = c == 0 ? Y01[q].x : (c == 1 ? Y01[q].y : Y2[q]);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                if (d == c) continue;
-                const int r = 3 - c - d;
-                const int br = (q >> r) & 1;
-                const int qc = (q >> c) & 1, qd = (q >> d) & 1;
-                if (qc == 1 && qd == 0) acc = fmaf(K.lam4[br], get(d, (q & ~(1 << c)) | (1 << d)), acc);
-                if (qd == 1 && qc == 0) acc = fmaf(K.mu4[br], get(d, (q & ~(1 << d)) | (1 << c)), acc);
-            }
-            if (c == 0) Y01[q].x = acc;
-            else if (c == 1) Y01[q].y = acc;
-            else Y2[q] = acc;
-        }
-    }
-    Y01[0] = make_float2(0.0f, 0.0f);
-    Y2[0] = 0.0f;
-}
 
 struct FusedArgs {
     int nx, ny, nz, support;
@@ -113,20 +70,6 @@ __device__ __forceinline__ void fused_quad2(const float4* __restrict__ s, int NW
     Q2[1] = e0 + e1;
     Q2[2] = t1 - t0;
     Q2[3] = e1 - e0;
-}
-
-template <int NT>
-__device__ __forceinline__ double fused_cta_sum(double v, double* sh) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < NT / 32; ++w) s += sh[w];
-    __syncthreads();
-    return s;
 }
 
 // MODE 0: K(w) x. MODE 2: S x with W_e = Khat H u_e recomputed from the staged u. NT threads per
@@ -764,9 +707,18 @@ static const int kFusedPlans[][4] = {PBM_FUSED_PLANS(PBM_PLAN_ROW)};
 #undef PBM_PLAN_ROW
 constexpr int kFusedNumPlans = int(sizeof(kFusedPlans) / sizeof(kFusedPlans[0]));
 
+// Plan numbers: 0 .. kFusedNumPlans - 1 this file's tiles, kFusedNumPlans the tensor-core kernel (tc.cu), then
+// the lane-strip kernel's plans (strip.cu).
+static bool is_strip(int cand) { return cand > kFusedNumPlans; }
+
 FusedPlan fused_plan(const Geom& G, int cand, bool op_s) {
     if (cand == kFusedNumPlans) {
         FusedPlan p = tc_plan(G, op_s);
+        p.var = cand;
+        return p;
+    }
+    if (is_strip(cand)) {
+        FusedPlan p = strip_plan(G, cand - kFusedNumPlans - 1);
         p.var = cand;
         return p;
     }
@@ -798,13 +750,16 @@ FusedPlan fused_plan(const Geom& G, int cand, bool op_s) {
     return p;
 }
 
-int fused_num_plans() { return kFusedNumPlans + 1; }
+int fused_num_plans() { return kFusedNumPlans + 1 + strip_num_plans(); }
 
 int fused_tc_plan() { return kFusedNumPlans; }
 
 int fused_blocks(const FusedPlan& p) { return p.gx * p.gy * p.gz; }
 
-int fused_threads(const FusedPlan& p) { return p.var == kFusedNumPlans ? 256 : kFusedPlans[p.var][0]; }
+int fused_threads(const FusedPlan& p) {
+    if (is_strip(p.var)) return strip_threads(p.var - kFusedNumPlans - 1);
+    return p.var == kFusedNumPlans ? 256 : kFusedPlans[p.var][0];
+}
 
 // plan used until the autotuner has timed the candidates (and for grids it does not tune): fewest
 // plane steps per SM (waves x (DZ + 1) / resident CTAs), then fewest element columns computed
@@ -842,6 +797,10 @@ void fused_fine_f32(const FusedPlan& p, const RedSet& r, const Geom& G, const Ke
                     const float* w, const float* d, const float* u, const ApplyArgs& a, cudaStream_t st) {
     if (p.var == kFusedNumPlans) {
         tc_fine_f32(p, r, G, tm, w, d, u, a, st);
+        return;
+    }
+    if (is_strip(p.var)) {
+        strip_fine_f32(p.var - kFusedNumPlans - 1, p, r, G, kh, w, d, u, a, st);
         return;
     }
     const bool s = d != nullptr;

@@ -544,6 +544,12 @@ void tc_build(const double* Ke, std::vector<float>& B, int& terms, float& scale)
 FusedPlan tc_plan(const Geom& G, bool op_s);
 void tc_fine_f32(const FusedPlan& p, const RedSet& r, const Geom& G, const TcMatrix& tm, const float* w,
                  const float* d, const float* u, const ApplyArgs& a, cudaStream_t st);
+// lane-strip FP32 fine operator (strip.cu): plans cand = 0 .. strip_num_plans() - 1
+int strip_num_plans();
+int strip_threads(int cand);
+FusedPlan strip_plan(const Geom& G, int cand);
+void strip_fine_f32(int cand, const FusedPlan& p, const RedSet& r, const Geom& G, const KeHat& kh, const float* w,
+                    const float* d, const float* u, const ApplyArgs& a, cudaStream_t st);
 // single-pass FP32 coarse-level operator (stored Galerkin matrices; fused.cu)
 int fused_coarse_num_plans();
 FusedPlan fused_coarse_plan(const Geom& G, int cand);

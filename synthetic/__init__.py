@@ -22,6 +22,7 @@ import numpy as np
 __all__ = [
     "Workload", "WORKLOADS", "BATCH_WORKLOADS", "load_vector", "density_uniform_rescaled", "density_bumps",
     "density_for", "synthetic_state", "random_state", "smooth_displacement", "node_count", "dof_count", "elem_count",
+    "supported_dofs", "state_displacement",
 ]
 
 
@@ -35,6 +36,26 @@ def dof_count(nx: int, ny: int, nz: int) -> int:
 
 def elem_count(nx: int, ny: int, nz: int) -> int:
     return nx * ny * nz
+
+
+def supported_dofs(nx: int, ny: int, nz: int, bc: str) -> np.ndarray:
+    """Boolean (n,) mask of the supported dofs of a workload's boundary condition (the placement of the supports,
+    like the placement of the loads below): "cantilever" every node of the face x = 0; "bridge_corners" the four
+    corner nodes of the bottom face z = 0; "bridge_edges" the two bottom edges {x = 0, z = 0} and {x = nx, z = 0};
+    "free" none. All three dofs of a supported node are supported."""
+    k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    i, j, k = i.ravel(), j.ravel(), k.ravel()
+    if bc == "cantilever":
+        node = i == 0
+    elif bc == "bridge_corners":
+        node = (k == 0) & ((i == 0) | (i == nx)) & ((j == 0) | (j == ny))
+    elif bc == "bridge_edges":
+        node = (k == 0) & ((i == 0) | (i == nx))
+    elif bc == "free":
+        node = np.zeros(i.size, dtype=bool)
+    else:
+        raise ValueError(f"unknown support {bc!r}")
+    return np.repeat(node, 3)
 
 
 def _face_weights(n: int) -> np.ndarray:
@@ -178,8 +199,10 @@ WORKLOADS = {
     "cant16": Workload("cant16", 16, 8, 8, "cantilever", ("end_edge",), 0.3, "uniform", 0, 3, 1e-10),
     # 64x32x32 cantilever, single reduced-Newton solve, 5 levels, rtol 1e-8
     "cant64": Workload("cant64", 64, 32, 32, "cantilever", ("end_edge",), 0.3, "uniform_rescaled", 0, 5, 1e-8),
-    # 128x64x64 bridge (four bottom corners), top traction, Gaussian-bump density at vf 0.2, 6 levels (4x2x2 coarse)
-    "bridge128": Workload("bridge128", 128, 64, 64, "bridge_corners", ("top_traction",), 0.2, "bumps", 0, 6, 1e-8),
+    # 128x64x64 bridge (four bottom corners), top traction, Gaussian-bump density at vf 0.2, 6 levels (4x2x2 coarse);
+    # its Newton state's displacement is the seeded smooth field (seed 5, max |u| = 1)
+    "bridge128": Workload("bridge128", 128, 64, 64, "bridge_corners", ("top_traction",), 0.2, "bumps", 0, 6, 1e-8,
+                          extra={"u": ("smooth", 5, 1.0)}),
     # 256x128x128 cantilever, distributed end load, vf 0.15, 7 levels
     "cant256": Workload("cant256", 256, 128, 128, "cantilever", ("end_face",), 0.15, "uniform", 0, 7, 1e-8),
     # small cases used by parity tests
@@ -207,10 +230,23 @@ def density_for(w: Workload) -> np.ndarray:
     raise ValueError(w.density)
 
 
+def state_displacement(w: Workload) -> np.ndarray | None:
+    """The displacement of a single-solve workload's synthetic Newton state when the recipe fixes it (the seeded
+    smooth field of `smooth_displacement`, zero on the supported dofs); None when the state uses the equilibrium
+    displacement of K(rho) u = f, which the caller computes."""
+    spec = w.extra.get("u")
+    if spec is None:
+        return None
+    kind, seed, amplitude = spec
+    if kind != "smooth":
+        raise ValueError(kind)
+    return smooth_displacement(w.nx, w.ny, w.nz, seed, amplitude, supported_dofs(w.nx, w.ny, w.nz, w.bc))
+
+
 def synthetic_state(w: Workload, u: np.ndarray) -> dict:
     """The synthetic Newton state of a single-solve workload: PBM multipliers all 1 (mu_lo = mu_up = 1), penalty
     parameters all 1, alpha = 1 and nu_lo = nu_up = 1 (the paper's initial values), rho from the density recipe,
-    and u supplied by the caller (the equilibrium displacement of K(rho) u = f)."""
+    and u supplied by the caller (`state_displacement`, else the equilibrium displacement of K(rho) u = f)."""
     m = w.m
     return dict(u=np.asarray(u, dtype=np.float64), alpha=1.0, nu_lo=np.ones(m), nu_up=np.ones(m),
                 rho=density_for(w), mu_lo=np.ones(m), mu_up=np.ones(m), p=1.0, q_lo=1.0, q_up=1.0,

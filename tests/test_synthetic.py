@@ -72,3 +72,18 @@ def test_workload_sizes_match_their_grids():
         assert w.nx % f == 0 and w.ny % f == 0 and w.nz % f == 0
         # the coarsest grid of every workload stays small enough for the dense bordered solve
         assert 3 * (w.nx // f + 1) * (w.ny // f + 1) * (w.nz // f + 1) <= 1500
+
+
+@pytest.mark.parametrize("bc", ["cantilever", "bridge_corners", "bridge_edges", "free"])
+def test_supported_dofs_match_the_oracle_grid(bc):
+    for dims in ((8, 4, 4), (5, 3, 2)):
+        assert np.array_equal(synthetic.supported_dofs(*dims, bc), fem.Grid(*dims, bc).fixed_dofs())
+
+
+def test_state_displacement_recipes():
+    w = synthetic.WORKLOADS["bridge128"]
+    u = synthetic.state_displacement(w)
+    assert u.shape == (w.n,) and abs(np.abs(u).max() - 1.0) < 1e-15
+    assert np.all(u[synthetic.supported_dofs(w.nx, w.ny, w.nz, w.bc)] == 0.0)
+    assert np.array_equal(u, synthetic.state_displacement(w))
+    assert synthetic.state_displacement(synthetic.WORKLOADS["cant64"]) is None
