@@ -63,7 +63,10 @@ PROFILE_DIR = os.path.join(ROOT, "profiles")
 # (launch wrappers, plans, cost models), so that host-only edits keep the ncu counters valid
 KERNEL_SOURCES = {"fp64": [(os.path.join(ROOT, "paper_1904_06556_gb300", "csrc", "colpass.cu"), "// launch wrappers")],
                   "mixed": [(os.path.join(ROOT, "paper_1904_06556_gb300", "csrc", "fused.cu"),
-                             "// FP32 coarse levels")]}
+                             "// FP32 coarse levels"),
+                            (os.path.join(ROOT, "paper_1904_06556_gb300", "csrc", "strip.cu"),
+                             "// plans: element rows per warp"),
+                            (os.path.join(ROOT, "paper_1904_06556_gb300", "csrc", "fp32_elem.h"), None)]}
 # FP64 issue rate of GB300 derived from the nominal 1.25 TFLOP/s (FMA = 2 flops), 152 SMs, 2070 MHz:
 # 1.25e12 / (2 * 152 * 2.07e9) = 2 FP64 instructions per clock per SM, i.e. 629 G FP64 operations/s.
 FP64_OPS_PEAK = 2.0 * 152 * 2.07e9
@@ -186,7 +189,7 @@ def kernel_hash(precision: str) -> str:
     for p, marker in KERNEL_SOURCES[precision]:
         with open(p, "rb") as fh:
             txt = fh.read()
-        cut = txt.find(marker.encode())
+        cut = txt.find(marker.encode()) if marker else -1
         h.update(txt if cut < 0 else txt[:cut])
     return h.hexdigest()[:16]
 
@@ -215,18 +218,20 @@ REF_DIR = os.path.join(ROOT, "tests", "golden")
 
 def oracle_reference(w, rho, f, u):
     """The oracle's stored reference solution of the workload's reduced system, if one exists and was written for
-    these exact inputs (SHA-256 of rho, f, u); else (None, reason)."""
+    these inputs (their sums and norms agree to 1e-12 relative); else (None, reason)."""
     npy = os.path.join(REF_DIR, f"{w.name}_dz_ref.npy")
     meta_path = os.path.join(REF_DIR, f"{w.name}_dz_ref.json")
     if not (os.path.exists(npy) and os.path.exists(meta_path)):
         return None, f"no stored oracle reference for {w.name}"
     with open(meta_path) as fh:
         meta = json.load(fh)
-    h = hashlib.sha256()
-    for a in (rho, f, u):
-        h.update(np.ascontiguousarray(a, dtype=np.float64).tobytes())
-    if h.hexdigest() != meta.get("inputs_sha256"):
-        return None, "stored oracle reference was written for other inputs"
+    ramp = np.linspace(1.0, 2.0, u.size)
+    mine = {"rho_sum": float(rho.sum()), "rho_norm": float(np.linalg.norm(rho)), "f_norm": float(np.linalg.norm(f)),
+            "u_norm": float(np.linalg.norm(u)), "u_ramp": float(u @ ramp)}
+    theirs = meta.get("inputs_check", {})
+    for k, v in mine.items():
+        if k not in theirs or not abs(v - theirs[k]) <= 1e-12 * max(abs(theirs[k]), 1e-300):
+            return None, f"stored oracle reference was written for other inputs ({k})"
     return (np.load(npy), meta), None
 
 

@@ -7,11 +7,10 @@ volume fraction 0.2 (seed 0), mu = nu = 1, alpha = 1, p = q = 1, and the displac
 (seed 5, max |u| = 1, zero on the supported dofs). The oracle assembles S and the right-hand side in CSR and solves
 with its own MG-MINRES (6-level Galerkin V-cycle, Chebyshev smoothing) driven toward a true relative residual of
 1e-14 for at most 80 iterations (FP64 levels off near 2e-14 on this system); anything above 1e-13 is refused. Only oracle/ and synthetic/ are used. The JSON records the residual
-reached, the iteration counts to 1e-8 and to the reference, and a SHA-256 of the inputs (rho, f, u as float64) so
-that readers can check they hold the same system. Run from the repository root (about three minutes):
+reached, the iteration counts to 1e-8 and to the reference, and sums and norms of the inputs (rho, f, u) so that
+readers can check they hold the same system. Run from the repository root (about three minutes):
     python tests/golden/make_bridge128_reference.py
 """
-import hashlib
 import json
 import os
 import sys
@@ -40,11 +39,12 @@ def inputs():
     return w, g, rho, f, u, synthetic.synthetic_state(w, u)
 
 
-def input_digest(rho, f, u) -> str:
-    h = hashlib.sha256()
-    for a in (rho, f, u):
-        h.update(np.ascontiguousarray(a, dtype=np.float64).tobytes())
-    return h.hexdigest()
+def input_check(rho, f, u) -> dict:
+    """Sums and norms of the inputs (float64): a reader regenerates the inputs from synthetic/ and compares these
+    to 1e-12 relative (the platforms' exp and sin may differ in the last bit, so no bitwise digest)."""
+    ramp = np.linspace(1.0, 2.0, u.size)
+    return {"rho_sum": float(rho.sum()), "rho_norm": float(np.linalg.norm(rho)), "f_norm": float(np.linalg.norm(f)),
+            "u_norm": float(np.linalg.norm(u)), "u_ramp": float(u @ ramp)}
 
 
 def main():
@@ -66,7 +66,7 @@ def main():
         "state": {"u": f"synthetic.smooth_displacement(seed={U_SEED}, amplitude={U_AMPLITUDE}), supported dofs 0",
                   "rho": "synthetic.density_bumps(vf=0.2, seed=0)", "mu_lo": 1, "mu_up": 1, "nu_lo": 1, "nu_up": 1,
                   "alpha": 1, "p": 1, "q": 1, "V": w.V, "rho_lo": w.rho_lo, "rho_up": w.rho_up},
-        "inputs_sha256": input_digest(rho, f, u),
+        "inputs_check": input_check(rho, f, u),
         "n_plus_1": int(ref.x.size),
         "solver": "oracle MINRES + 6-level Galerkin V-cycle, Chebyshev smoothing",
         "relres": ref.relres, "iterations": ref.iters,
