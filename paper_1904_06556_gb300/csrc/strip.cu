@@ -1,6 +1,7 @@
 // Single-pass FP32 fine-level operator in lane strips: K(w) x and the S operator of eq. (S) with the fused
 // apply / residual / damped-Jacobi / Chebyshev / Gauss-Seidel epilogues (Section 5.1) and the Krylov dot
-// products, organised so that almost every value an element shares with its neighbours stays in registers.
+// products, organised so that almost every value an element shares with its neighbours stays in registers and
+// every floating-point instruction does the work of two elements.
 //
 // A warp's 32 lanes are 32 consecutive node columns i = X0 - 1 + lane (consecutive lanes read consecutive
 // nodes: every global access is coalesced). Lane l <= 30 owns the element column i, between its node column
@@ -12,13 +13,15 @@
 //     by the two element rows and the two layers that touch them;
 //   * y: the element's face quad (sum / difference of its two x-pairs) is formed per element and plane;
 //   * z: the element's 24 transformed coefficients are the sum and difference of its two face quads.
-// The output goes back the same way: each element's bottom and top faces are split into the x-pair form of
-// their node rows and accumulated per row (the top faces are the carry into the next plane), and a node's
-// value is its own column's part plus the part the lane on its left computed (one shuffle per value). The
-// node row between two warps is completed through shared memory (one float4 per lane and plane, double
-// buffered so that one barrier per plane suffices). Nothing but the inputs and the output goes through
-// global memory, and no element value is recomputed except on the CTA's one-column and one-row halo and on
-// the layer below each plane chunk.
+// Two vertically adjacent elements of the strip are processed together: every per-element quantity is a float2
+// (lower element, upper element), so the paired FP32 instructions (FADD2 / FMUL2 / FFMA2) do all arithmetic of
+// the transform and of Khat for both at once. The output goes back the same way: each element's bottom face
+// plus the top face of the element below it in the previous layer (carried in transformed form) is split into
+// the x-pair form of its two node rows, and a node's value is its own column's part plus the part the lane on
+// its left computed (one shuffle per value). The node row between two warps is completed through shared memory
+// (one float4 per lane and plane, double buffered so that one barrier per plane suffices). Nothing but the
+// inputs and the output goes through global memory, and no element value is recomputed except on the CTA's
+// one-column and one-row halo and on the layer below each plane chunk.
 //
 // The alpha row of S counts every element once (in the CTA and chunk that own its upper corner node). Per-CTA
 // partial sums of the dot product and of the alpha row are finished by the last CTA in a fixed order, so the
@@ -34,19 +37,64 @@ namespace {
 
 constexpr int kStripOwnedX = 30;   // owned node columns per warp (lanes 1 .. 30)
 
-// a 3-vector with components (x, y) paired for the packed instructions and z alone
-struct V3 {
-    float2 a;
-    float b;
+// Khat of pbm_internal.h with every coefficient repeated in both halves of a float2 (the two elements of a pair)
+struct KeHatP {
+    float2 dg[3][8];
+    float2 lam4[2];
+    float2 mu4[2];
 };
-__device__ __forceinline__ V3 v3zero() { return V3{make_float2(0.0f, 0.0f), 0.0f}; }
-__device__ __forceinline__ V3 operator+(V3 p, V3 q) { return V3{add2(p.a, q.a), p.b + q.b}; }
-__device__ __forceinline__ V3 operator-(V3 p, V3 q) { return V3{sub2(p.a, q.a), p.b - q.b}; }
 
-// the x-pair of a node row: s = v(i + 1) + v(i), d = v(i + 1) - v(i)
-struct XP {
-    V3 s, d;
+// Y = Khat X for two elements at once (X, Y: [component][pattern], patterns 1 .. 7; Y[.][0] is zero)
+__device__ __forceinline__ void khat_pair(const KeHatP& K, const float2 (&X)[3][8], float2 (&Y)[3][8]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        Y[c][0] = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int q = 1; q < 8; ++q) {
+            float2 acc = mul2(K.dg[c][q], X[c][q]);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (d == c) continue;
+                const int r = 3 - c - d;
+                const int br = (q >> r) & 1;
+                const int qc = (q >> c) & 1, qd = (q >> d) & 1;
+                if (qc == 1 && qd == 0) acc = fma2(K.lam4[br], X[d][(q & ~(1 << c)) | (1 << d)], acc);
+                if (qd == 1 && qc == 0) acc = fma2(K.mu4[br], X[d][(q & ~(1 << d)) | (1 << c)], acc);
+            }
+            Y[c][q] = acc;
+        }
+    }
+}
+
+// x-pairs of the two node rows of each element of a pair, per component: s = v(i + 1) + v(i), d = v(i + 1) - v(i),
+// as (lower element, upper element)
+struct XPP {
+    float2 ls[3], ld[3];   // low rows (rows 2p, 2p + 1)
+    float2 hs[3], hd[3];   // high rows (rows 2p + 1, 2p + 2)
 };
+
+// the 24 transformed coefficients of the two elements from the x-pairs of their bottom and top planes
+__device__ __forceinline__ void pair_coeffs(const XPP& b, const XPP& t, float2 (&X)[3][8]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        // face quads (fused.cu's convention: 0 sum, 1 x-difference, 2 y-difference, 3 both)
+        const float2 b0 = add2(b.ls[c], b.hs[c]), b1 = add2(b.ld[c], b.hd[c]);
+        const float2 b2 = sub2(b.hs[c], b.ls[c]), b3 = sub2(b.hd[c], b.ld[c]);
+        const float2 t0 = add2(t.ls[c], t.hs[c]), t1 = add2(t.ld[c], t.hd[c]);
+        const float2 t2 = sub2(t.hs[c], t.ls[c]), t3 = sub2(t.hd[c], t.ld[c]);
+        X[c][0] = add2(b0, t0);
+        X[c][1] = add2(b1, t1);
+        X[c][2] = add2(b2, t2);
+        X[c][3] = add2(b3, t3);
+        X[c][4] = sub2(t0, b0);
+        X[c][5] = sub2(t1, b1);
+        X[c][6] = sub2(t2, b2);
+        X[c][7] = sub2(t3, b3);
+    }
+}
+
+__device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 
 struct StripArgs {
     int nx, ny, nz, support;
@@ -61,64 +109,25 @@ struct StripArgs {
     const float* idiag;
     const double* omega;
     int mode, with_alpha, dot_slot;
-    KeHat2 K;
+    KeHatP K;
     double* partials;     // 2 * gridDim.x
     DevScalars* sc;
     unsigned int* counter;
 };
 
-// face quad of element row r from the x-pairs of its two node rows (fused.cu's fused_quad2 convention:
-// Q0 = sum, Q1 = x-difference, Q2 = y-difference, Q3 = both)
-__device__ __forceinline__ void face_quad(const XP& lo, const XP& hi, V3 (&Q)[4]) {
-    Q[0] = lo.s + hi.s;
-    Q[1] = lo.d + hi.d;
-    Q[2] = hi.s - lo.s;
-    Q[3] = hi.d - lo.d;
-}
-
-// the 24 transformed coefficients of an element from the face quads of its bottom and top planes
-__device__ __forceinline__ void element_coeffs(const V3 (&Qb)[4], const V3 (&Qt)[4], float2 (&X01)[8], float (&X2)[8]) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const V3 p = Qb[q] + Qt[q], m = Qt[q] - Qb[q];
-        X01[q] = p.a;
-        X2[q] = p.b;
-        X01[q + 4] = m.a;
-        X2[q + 4] = m.b;
-    }
-}
-
-// adds a face F (transformed, 4 q-values) to the x-pair accumulators of its low and high node rows
-__device__ __forceinline__ void face_to_rows(const V3 (&F)[4], XP& low, XP& high) {
-    low.s = low.s + (F[0] - F[2]);
-    low.d = low.d + (F[1] - F[3]);
-    high.s = high.s + (F[0] + F[2]);
-    high.d = high.d + (F[1] + F[3]);
-}
-
-__device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
-__device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
-
-// node value of a row from its x-pair accumulator: the left part of the own column plus the right part the
-// lane on the left computed (lane 0's value is incomplete; it is never owned)
-__device__ __forceinline__ V3 row_total(const XP& a) {
-    const V3 L = a.s - a.d, Rt = a.s + a.d;
-    V3 Rp;
-    Rp.a = make_float2(shfl_up1(Rt.a.x), shfl_up1(Rt.a.y));
-    Rp.b = shfl_up1(Rt.b);
-    return L + Rp;
-}
-
 }  // namespace
 
-// MODE 0: K(w) x. MODE 2: S x with W_e = Khat H u_e recomputed from u. NW warps per CTA, NYB element rows per
-// warp, MINB resident CTAs per SM asked of the register allocator.
-template <int MODE, int NYB, int NW, int MINB>
+// MODE 0: K(w) x. MODE 2: S x with W_e = Khat H u_e recomputed from u. EPI: the epilogue (EPI_APPLY, EPI_RESID,
+// EPI_JACOBI, EPI_CHEB, or EPI_GS0 for every Gauss-Seidel colour, the colour read from P.mode). NW warps per CTA,
+// NYB (even) element rows per warp, MINB resident CTAs per SM asked of the register allocator.
+template <int MODE, int EPI, int NYB, int NW, int MINB>
 __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     pdl_wait();
     constexpr bool S = MODE == 2;
     constexpr int NT = 32 * NW;
     constexpr int R = NW * NYB;            // element rows of the CTA
+    constexpr int NP = NYB / 2;            // element pairs per lane
+    static_assert(NYB % 2 == 0, "element rows come in pairs");
     __shared__ float4 sy[2][NW][32];       // node totals of each warp's top row, by plane parity
     __shared__ double sred[NW];
     __shared__ bool s_last;
@@ -135,8 +144,9 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     const int64_t plane = 3 * int64_t(nx + 1) * (ny + 1);
     const int64_t elayer = int64_t(nx) * ny;
 
-    // per node row r = 0 .. NYB: in range and not supported, for planes k >= 1 (bit r) and plane 0 (bit 16 + r)
-    unsigned okm = 0, fixm = 0;
+    // node rows r = 0 .. NYB: in range and not supported (bit r for planes k >= 1, bit 16 + r for plane 0),
+    // supported (same layout), owned by this lane (bit r)
+    unsigned okm = 0, fixm = 0, ownm = 0;
     int noff[NYB + 1];                     // node offsets (floats) within a plane
 #pragma unroll
     for (int r = 0; r <= NYB; ++r) {
@@ -149,6 +159,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
             if (!(fb & 2)) okm |= 1u << (16 + r);
             fixm |= unsigned(fb & 1) << r;
             fixm |= unsigned((fb >> 1) & 1) << (16 + r);
+            if (lane >= 1 && lane <= 30 && r < NYB && (r >= 1 || wid >= 1)) ownm |= 1u << r;
         }
     }
     // element rows r = 0 .. NYB - 1 that exist (lanes 0 .. 30), and those whose alpha term this CTA counts
@@ -166,8 +177,8 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     const float xa = S ? P.x[P.n] : 0.0f;
     float omF = 0.0f, c0F = 0.0f, c1F = 0.0f, c2F = 0.0f;
     bool c1nz = false;
-    if (P.mode == EPI_JACOBI) omF = float(*P.omega);
-    if (P.mode == EPI_CHEB) {
+    if (EPI == EPI_JACOBI) omF = float(*P.omega);
+    if (EPI == EPI_CHEB) {
         c0F = float(P.omega[0]);
         c1F = float(P.omega[1]);
         c2F = float(P.omega[2]);
@@ -177,7 +188,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     float pdT = 0.0f, paT = 0.0f;
 
     // raw node values of the lane's column (rows 0 .. NYB) of one plane, zero where not in range or supported
-    float rx[NYB + 1][3], ru[S ? NYB + 1 : 1][3];
+    float rx[NYB + 1][3], ru[NYB + 1][3];   // ru: S only (dead code for K)
     auto fetch = [&](int k) {
         const unsigned ok = k == 0 ? (okm >> 16) : okm;
         const float* xs = P.x + int64_t(k) * plane;
@@ -192,174 +203,216 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
             }
         }
     };
-    // x-pairs of one node row from the lane's column and the right neighbour's
-    auto xpair = [&](const float (&v)[3]) {
-        const float r0 = shfl_dn1(v[0]), r1 = shfl_dn1(v[1]), r2 = shfl_dn1(v[2]);
-        XP p;
-        p.s = V3{make_float2(r0 + v[0], r1 + v[1]), r2 + v[2]};
-        p.d = V3{make_float2(r0 - v[0], r1 - v[1]), r2 - v[2]};
-        return p;
+    // x-pairs of a plane from the lane's raw column values and the right neighbour's
+    auto xpairs = [&](const float (&v)[NYB + 1][3], XPP (&o)[NP]) {
+        float rt[NYB + 1][3];
+#pragma unroll
+        for (int r = 0; r <= NYB; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) rt[r][c] = shfl_dn1(v[r][c]);
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float2 ownL = make_float2(v[2 * p][c], v[2 * p + 1][c]);
+                const float2 ownH = make_float2(v[2 * p + 1][c], v[2 * p + 2][c]);
+                const float2 rgtL = make_float2(rt[2 * p][c], rt[2 * p + 1][c]);
+                const float2 rgtH = make_float2(rt[2 * p + 1][c], rt[2 * p + 2][c]);
+                o[p].ls[c] = add2(rgtL, ownL);
+                o[p].ld[c] = sub2(rgtL, ownL);
+                o[p].hs[c] = add2(rgtH, ownH);
+                o[p].hd[c] = sub2(rgtH, ownH);
+            }
     };
 
-    const int kstart = max(kz0 - 1, 0);
-    XP xl[NYB + 1], ul[S ? NYB + 1 : 1];   // x-pairs of the plane below the current layer
-    XP acc[NYB + 1];                       // x-pair accumulators of the current plane's node rows
-    fetch(kstart);
-#pragma unroll
-    for (int r = 0; r <= NYB; ++r) {
-        xl[r] = xpair(rx[r]);
-        if (S) ul[r] = xpair(ru[r]);
-        acc[r].s = acc[r].d = v3zero();
-    }
-    if (kstart + 1 <= nz) fetch(kstart + 1);
-    float wn[NYB], dn[S ? NYB : 1];
+    // element weights of the next layer, as (lower, upper) element of each pair
+    float2 wn[NP], dn[NP];
     auto fetch_w = [&](int k) {
 #pragma unroll
-        for (int r = 0; r < NYB; ++r) {
-            const bool e = (em >> r) & 1u;
-            wn[r] = e ? __ldg(P.w + int64_t(k) * elayer + eoff[r]) : 0.0f;
-            if (S) dn[r] = e ? __ldg(P.d + int64_t(k) * elayer + eoff[r]) : 0.0f;
+        for (int p = 0; p < NP; ++p) {
+            const bool e0 = (em >> (2 * p)) & 1u, e1 = (em >> (2 * p + 1)) & 1u;
+            const float* wl = P.w + int64_t(k) * elayer;
+            wn[p] = make_float2(e0 ? __ldg(wl + eoff[2 * p]) : 0.0f, e1 ? __ldg(wl + eoff[2 * p + 1]) : 0.0f);
+            if (S) {
+                const float* dl = P.d + int64_t(k) * elayer;
+                dn[p] = make_float2(e0 ? __ldg(dl + eoff[2 * p]) : 0.0f, e1 ? __ldg(dl + eoff[2 * p + 1]) : 0.0f);
+            }
         }
     };
-    if (kstart < nz) fetch_w(kstart);
 
-    for (int k = kstart; k < kz1; ++k) {
-        const bool layer = k < nz;
-        XP nxt[NYB + 1];                   // x-pair accumulators of plane k + 1 (the top faces)
+    // epilogue of the owned node of row r of plane k with the operator value s
+    auto epilogue = [&](int k, int r, float s0, float s1, float s2) {
+        if (!((ownm >> r) & 1u)) return;
+        const int j = jb + r;
+        const int64_t d0 = int64_t(k) * plane + noff[r];
+        const bool ofixed = ((k == 0 ? (fixm >> 16) : fixm) >> r) & 1u;
+        float sv[3] = {s0, s1, s2};
+        float xo[3] = {0.0f, 0.0f, 0.0f};
+        const bool need_x = ofixed || EPI == EPI_JACOBI || EPI == EPI_CHEB || EPI == EPI_GS0 ||
+                            (EPI == EPI_APPLY && want_dot);
+        if (need_x) {
 #pragma unroll
-        for (int r = 0; r <= NYB; ++r) nxt[r].s = nxt[r].d = v3zero();
-        if (layer) {
-            XP xh[NYB + 1], uh[S ? NYB + 1 : 1];
+            for (int c = 0; c < 3; ++c) xo[c] = __ldg(P.x + d0 + c);
+        }
+        if (ofixed) {
 #pragma unroll
-            for (int r = 0; r <= NYB; ++r) {
-                xh[r] = xpair(rx[r]);
-                if (S) uh[r] = xpair(ru[r]);
+            for (int c = 0; c < 3; ++c) sv[c] = xo[c];
+        }
+        const int gs_c = EPI == EPI_GS0 ? P.mode - EPI_GS0 - 3 * node_colour(i, j, k) : 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float o;
+            if (EPI == EPI_APPLY) {
+                o = sv[c];
+                if (want_dot) pdT += o * xo[c];
+            } else if (EPI == EPI_RESID) {
+                o = __ldg(P.b + d0 + c) - sv[c];
+                if (want_dot) pdT += o * o;
+            } else if (EPI == EPI_JACOBI) {
+                const float bb = __ldg(P.b + d0 + c);
+                o = xo[c] + omF * ((bb - sv[c]) * __ldg(P.idiag + d0 + c));
+                if (want_dot) pdT += o * bb;
+            } else if (EPI == EPI_CHEB) {
+                const float bb = __ldg(P.b + d0 + c);
+                o = c0F * xo[c] + c2F * ((bb - sv[c]) * __ldg(P.idiag + d0 + c));
+                if (c1nz) o -= c1F * P.y[d0 + c];
+                if (want_dot) pdT += o * bb;
+            } else {
+                const float bb = __ldg(P.b + d0 + c);
+                o = gs_c == c ? xo[c] + (bb - sv[c]) * __ldg(P.idiag + d0 + c) : xo[c];
+                if (want_dot) pdT += o * bb;
             }
-            if (k + 2 <= nz && k + 1 < kz1) fetch(k + 2);
-            float we[NYB], de[S ? NYB : 1];
+            P.y[d0 + c] = o;
+        }
+    };
+
+    // One layer k (planes k and k + 1): lo holds the x-pairs of plane k (x and u), carry the transformed top
+    // faces of layer k - 1 (zero below the first layer); hi receives those of plane k + 1 and carry the top
+    // faces of layer k. Then the node values of plane k are finished (k >= kz0). Called with the lo / hi roles
+    // swapped on alternate layers, so nothing is copied between layers.
+    auto layer_step = [&](int k, XPP (&xlo)[NP], XPP (&xhi)[NP], XPP (&ulo)[NP], XPP (&uhi)[NP],
+                          float2 (&carry)[NP][4][3]) {
+        const bool layer = k < nz;
+        // node-row accumulators of plane k in x-pair form (s, d per component), rows 0 .. NYB
+        float as[NYB + 1][3], ad[NYB + 1][3];
 #pragma unroll
-            for (int r = 0; r < NYB; ++r) {
-                we[r] = wn[r];
-                if (S) de[r] = dn[r];
+        for (int r = 0; r <= NYB; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) as[r][c] = ad[r][c] = 0.0f;
+        if (layer) {
+            xpairs(rx, xhi);
+            if (S) xpairs(ru, uhi);
+            if (k + 2 <= nz && k + 1 < kz1) fetch(k + 2);
+            float2 we[NP], de[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                we[p] = wn[p];
+                if (S) de[p] = dn[p];
             }
             if (k + 1 < nz && k + 1 < kz1) fetch_w(k + 1);
             const bool count_alpha = k + 1 >= kz0 && k + 1 < kz1;
 #pragma unroll
-            for (int r = 0; r < NYB; ++r) {
-                V3 Qb[4], Qt[4];
-                face_quad(xl[r], xl[r + 1], Qb);
-                face_quad(xh[r], xh[r + 1], Qt);
-                float2 X01[8], Y01[8];
-                float X2[8], Y2[8];
-                element_coeffs(Qb, Qt, X01, X2);
-                khat_apply2(P.K, X01, X2, Y01, Y2);
-                const float2 we2 = make_float2(we[r], we[r]);
+            for (int p = 0; p < NP; ++p) {
+                float2 X[3][8], Y[3][8];
+                pair_coeffs(xlo[p], xhi[p], X);
                 if (S) {
-                    V3 Ub[4], Ut[4];
-                    face_quad(ul[r], ul[r + 1], Ub);
-                    face_quad(uh[r], uh[r + 1], Ut);
-                    float2 U01[8], W01[8];
-                    float U2[8], W2[8];
-                    element_coeffs(Ub, Ut, U01, U2);
-                    khat_apply2(P.K, U01, U2, W01, W2);
-                    float2 dot01 = make_float2(0.0f, 0.0f);
-                    float dot2 = 0.0f;
+                    // t_e = d_e (u_e^T K_e x_e - x_alpha) with u_e^T K_e x_e = (H u_e) . Khat (H x_e); then
+                    // Y = Khat (w_e X + t_e H u_e) (linearity: the two products of eq. (S) share one Khat)
+                    float2 U[3][8];
+                    pair_coeffs(ulo[p], uhi[p], U);
+                    khat_pair(P.K, X, Y);
+                    float2 dot = make_float2(0.0f, 0.0f);
 #pragma unroll
-                    for (int q = 1; q < 8; ++q) {
-                        dot01 = fma2(W01[q], X01[q], dot01);
-                        dot2 = fmaf(W2[q], X2[q], dot2);
-                    }
-                    const float te = de[r] * ((dot01.x + dot01.y + dot2) - xa);
-                    if (count_alpha && ((am >> r) & 1u)) paT -= te;
-                    const float2 te2 = make_float2(te, te);
+                    for (int c = 0; c < 3; ++c)
 #pragma unroll
-                    for (int q = 1; q < 8; ++q) {
-                        Y01[q] = fma2(te2, W01[q], mul2(we2, Y01[q]));
-                        Y2[q] = fmaf(te, W2[q], we[r] * Y2[q]);
+                        for (int q = 1; q < 8; ++q) dot = fma2(U[c][q], Y[c][q], dot);
+                    const float2 te = mul2(de[p], make_float2(dot.x - xa, dot.y - xa));
+                    if (count_alpha) {
+                        if ((am >> (2 * p)) & 1u) paT -= te.x;
+                        if ((am >> (2 * p + 1)) & 1u) paT -= te.y;
                     }
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+#pragma unroll
+                        for (int q = 1; q < 8; ++q) X[c][q] = fma2(te, U[c][q], mul2(we[p], X[c][q]));
+                    khat_pair(P.K, X, Y);
                 } else {
+                    khat_pair(P.K, X, Y);
 #pragma unroll
-                    for (int q = 1; q < 8; ++q) {
-                        Y01[q] = mul2(we2, Y01[q]);
-                        Y2[q] *= we[r];
-                    }
+                    for (int c = 0; c < 3; ++c)
+#pragma unroll
+                        for (int q = 1; q < 8; ++q) Y[c][q] = mul2(we[p], Y[c][q]);
                 }
-                V3 B[4], T[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const V3 lo = V3{Y01[q], Y2[q]}, hi = V3{Y01[q + 4], Y2[q + 4]};
-                    B[q] = lo - hi;
-                    T[q] = lo + hi;
-                }
-                face_to_rows(B, acc[r], acc[r + 1]);
-                face_to_rows(T, nxt[r], nxt[r + 1]);
-            }
-#pragma unroll
-            for (int r = 0; r <= NYB; ++r) {
-                xl[r] = xh[r];
-                if (S) ul[r] = uh[r];
-            }
-        }
-        if (k >= kz0) {
-            // node totals of plane k: rows 1 .. NYB - 1 complete in the warp, row NYB shared with the warp above,
-            // row 0 with the warp below
-            const int64_t pbase = int64_t(k) * plane;
-            auto epilogue = [&](int r, V3 s) {
-                const int j = jb + r;
-                if (lane < 1 || lane > 30 || i > nx || j < 0 || j > ny) return;
-                const int64_t d0 = pbase + noff[r];
-                const bool ofixed = ((k == 0 ? (fixm >> 16) : fixm) >> r) & 1u;
-                float sv[3] = {s.a.x, s.a.y, s.b};
-                float xo[3] = {0.0f, 0.0f, 0.0f};
-                if (ofixed || P.mode != EPI_RESID) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) xo[c] = __ldg(P.x + d0 + c);
-                }
-                if (ofixed) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) sv[c] = xo[c];
-                }
-                const int gs_c = P.mode - EPI_GS0 - 3 * node_colour(i, j, k);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    float o;
-                    if (P.mode == EPI_APPLY) {
-                        o = sv[c];
-                        if (want_dot) pdT += o * xo[c];
-                    } else if (P.mode == EPI_RESID) {
-                        o = __ldg(P.b + d0 + c) - sv[c];
-                        if (want_dot) pdT += o * o;
-                    } else if (P.mode == EPI_JACOBI) {
-                        const float bb = __ldg(P.b + d0 + c);
-                        o = xo[c] + omF * ((bb - sv[c]) * __ldg(P.idiag + d0 + c));
-                        if (want_dot) pdT += o * bb;
-                    } else if (P.mode == EPI_CHEB) {
-                        const float bb = __ldg(P.b + d0 + c);
-                        o = c0F * xo[c] + c2F * ((bb - sv[c]) * __ldg(P.idiag + d0 + c));
-                        if (c1nz) o -= c1F * P.y[d0 + c];
-                        if (want_dot) pdT += o * bb;
-                    } else {
-                        const float bb = __ldg(P.b + d0 + c);
-                        o = gs_c == c ? xo[c] + (bb - sv[c]) * __ldg(P.idiag + d0 + c) : xo[c];
-                        if (want_dot) pdT += o * bb;
+                    // bottom face plus the carried top face of the layer below; the new top face is carried
+                    float2 F[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        F[q] = add2(carry[p][q][c], sub2(Y[c][q], Y[c][q + 4]));
+                        carry[p][q][c] = add2(Y[c][q], Y[c][q + 4]);
                     }
-                    P.y[d0 + c] = o;
+                    // the face split into the x-pair form of its low and high node rows, per element
+                    const float2 lo_s = sub2(F[0], F[2]), lo_d = sub2(F[1], F[3]);
+                    const float2 hi_s = add2(F[0], F[2]), hi_d = add2(F[1], F[3]);
+                    as[2 * p][c] += lo_s.x;
+                    ad[2 * p][c] += lo_d.x;
+                    as[2 * p + 1][c] += hi_s.x + lo_s.y;
+                    ad[2 * p + 1][c] += hi_d.x + lo_d.y;
+                    as[2 * p + 2][c] += hi_s.y;
+                    ad[2 * p + 2][c] += hi_d.y;
                 }
-            };
-            const V3 top = row_total(acc[NYB]);
-            sy[k & 1][wid][lane] = make_float4(top.a.x, top.a.y, top.b, 0.0f);
-#pragma unroll
-            for (int r = 1; r < NYB; ++r) epilogue(r, row_total(acc[r]));
-            V3 bot = row_total(acc[0]);
-            __syncthreads();   // every warp's top row of plane k is in shared memory
-            if (wid >= 1) {
-                const float4 v = sy[k & 1][wid - 1][lane];
-                bot = bot + V3{make_float2(v.x, v.y), v.z};
-                epilogue(0, bot);
             }
-        }
+        } else {
+            // above the last layer: plane k = nz holds only the top faces of layer nz - 1
 #pragma unroll
-        for (int r = 0; r <= NYB; ++r) acc[r] = nxt[r];
+            for (int p = 0; p < NP; ++p)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float2 lo_s = sub2(carry[p][0][c], carry[p][2][c]), lo_d = sub2(carry[p][1][c], carry[p][3][c]);
+                    const float2 hi_s = add2(carry[p][0][c], carry[p][2][c]), hi_d = add2(carry[p][1][c], carry[p][3][c]);
+                    as[2 * p][c] += lo_s.x;
+                    ad[2 * p][c] += lo_d.x;
+                    as[2 * p + 1][c] += hi_s.x + lo_s.y;
+                    ad[2 * p + 1][c] += hi_d.x + lo_d.y;
+                    as[2 * p + 2][c] += hi_s.y;
+                    ad[2 * p + 2][c] += hi_d.y;
+                }
+        }
+        if (k < kz0) return;   // the layer below the chunk: only its top faces are kept
+        // node totals: the own column's left part plus the left lane's right part
+        float tot[NYB + 1][3];
+#pragma unroll
+        for (int r = 0; r <= NYB; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) tot[r][c] = (as[r][c] - ad[r][c]) + shfl_up1(as[r][c] + ad[r][c]);
+        sy[k & 1][wid][lane] = make_float4(tot[NYB][0], tot[NYB][1], tot[NYB][2], 0.0f);
+#pragma unroll
+        for (int r = 1; r < NYB; ++r) epilogue(k, r, tot[r][0], tot[r][1], tot[r][2]);
+        __syncthreads();   // every warp's top row of plane k is in shared memory
+        if (wid >= 1) {
+            const float4 v = sy[k & 1][wid - 1][lane];
+            epilogue(k, 0, tot[0][0] + v.x, tot[0][1] + v.y, tot[0][2] + v.z);
+        }
+    };
+
+    const int kstart = max(kz0 - 1, 0);
+    XPP xa_[NP], xb_[NP], ua_[NP], ub_[NP];   // ua_, ub_: S only
+    float2 carry[NP][4][3];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) carry[p][q][c] = make_float2(0.0f, 0.0f);
+    fetch(kstart);
+    xpairs(rx, xa_);
+    if (S) xpairs(ru, ua_);
+    if (kstart + 1 <= nz) fetch(kstart + 1);
+    if (kstart < nz) fetch_w(kstart);
+    for (int k = kstart; k < kz1; k += 2) {
+        layer_step(k, xa_, xb_, ua_, ub_, carry);
+        if (k + 1 < kz1) layer_step(k + 1, xb_, xa_, ub_, ua_, carry);
     }
 
     // per-CTA partials; the last CTA finishes the dot and the alpha entry in a fixed order
@@ -389,17 +442,17 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     if (P.with_alpha) {
         const int64_t n = P.n;
         double o;
-        if (P.mode == EPI_APPLY) {
+        if (EPI == EPI_APPLY) {
             o = sa;
             sd += o * double(xa);
-        } else if (P.mode == EPI_RESID) {
+        } else if (EPI == EPI_RESID) {
             o = double(P.b[n]) - sa;
             sd += o * o;
-        } else if (P.mode == EPI_JACOBI) {
+        } else if (EPI == EPI_JACOBI) {
             const double bb = double(P.b[n]);
             o = double(xa) + *P.omega * ((bb - sa) * double(P.idiag[n]));
             sd += o * bb;
-        } else if (P.mode == EPI_CHEB) {
+        } else if (EPI == EPI_CHEB) {
             const double bb = double(P.b[n]);
             o = P.omega[0] * double(xa) + P.omega[2] * ((bb - sa) * double(P.idiag[n]));
             if (P.omega[1] != 0.0) o -= P.omega[1] * double(P.y[n]);
@@ -417,8 +470,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
 // ------------------------------------------------------------------------------------------------
 // plans: element rows per warp, warps per CTA, resident CTAs per SM asked of the register allocator
 // ------------------------------------------------------------------------------------------------
-#define PBM_STRIP_PLANS(X) \
-    X(0, 4, 8, 1) X(1, 4, 4, 2) X(2, 3, 8, 1) X(3, 2, 8, 1) X(4, 2, 4, 2) X(5, 3, 4, 2)
+#define PBM_STRIP_PLANS(X) X(0, 2, 4, 2) X(1, 2, 8, 1) X(2, 2, 4, 3) X(3, 4, 4, 1)
 #define PBM_STRIP_ROW(id, nyb, nw, minb) {nyb, nw, minb},
 static const int kStripPlans[][3] = {PBM_STRIP_PLANS(PBM_STRIP_ROW)};
 #undef PBM_STRIP_ROW
@@ -456,14 +508,27 @@ FusedPlan strip_plan(const Geom& G, int cand) {
     return p;
 }
 
-template <int MODE>
-static void strip_launch(int cand, int blocks, const StripArgs& P, cudaStream_t st) {
+template <int MODE, int EPI>
+static void strip_launch_epi(int cand, int blocks, const StripArgs& P, cudaStream_t st) {
     switch (cand) {
 #define PBM_STRIP_CASE(id, nyb, nw, minb) \
-    case id: launch_pdl(k_strip_f32<MODE, nyb, nw, minb>, dim3(blocks), dim3(32 * nw), 0, st, P); break;
+    case id: launch_pdl(k_strip_f32<MODE, EPI, nyb, nw, minb>, dim3(blocks), dim3(32 * nw), 0, st, P); break;
         PBM_STRIP_PLANS(PBM_STRIP_CASE)
 #undef PBM_STRIP_CASE
         default: fail(PBM_EINVAL, "strip operator: unknown plan");
+    }
+}
+
+template <int MODE>
+static void strip_launch(int cand, int blocks, const StripArgs& P, cudaStream_t st) {
+    switch (P.mode) {
+        case EPI_APPLY: strip_launch_epi<MODE, EPI_APPLY>(cand, blocks, P, st); break;
+        case EPI_RESID: strip_launch_epi<MODE, EPI_RESID>(cand, blocks, P, st); break;
+        case EPI_JACOBI: strip_launch_epi<MODE, EPI_JACOBI>(cand, blocks, P, st); break;
+        case EPI_CHEB: strip_launch_epi<MODE, EPI_CHEB>(cand, blocks, P, st); break;
+        default:
+            if (P.mode < EPI_GS0 || P.mode > EPI_GS0 + kGsColours) fail(PBM_EINVAL, "strip operator: unknown epilogue");
+            strip_launch_epi<MODE, EPI_GS0>(cand, blocks, P, st);
     }
 }
 
@@ -492,13 +557,11 @@ void strip_fine_f32(int cand, const FusedPlan& p, const RedSet& r, const Geom& G
     P.mode = a.mode;
     P.with_alpha = (s && a.with_alpha) ? 1 : 0;
     P.dot_slot = a.dot_slot;
-    for (int q = 0; q < 8; ++q) {
-        P.K.dg01[q] = make_float2(float(kh.dg[0][q]), float(kh.dg[1][q]));
-        P.K.dg2[q] = float(kh.dg[2][q]);
-    }
+    for (int c = 0; c < 3; ++c)
+        for (int q = 0; q < 8; ++q) P.K.dg[c][q] = make_float2(float(kh.dg[c][q]), float(kh.dg[c][q]));
     for (int b = 0; b < 2; ++b) {
-        P.K.lam4[b] = float(kh.lam4[b]);
-        P.K.mu4[b] = float(kh.mu4[b]);
+        P.K.lam4[b] = make_float2(float(kh.lam4[b]), float(kh.lam4[b]));
+        P.K.mu4[b] = make_float2(float(kh.mu4[b]), float(kh.mu4[b]));
     }
     P.partials = r.partials;
     P.sc = r.sc;
