@@ -93,6 +93,14 @@ __device__ __forceinline__ void pair_coeffs(const XPP& b, const XPP& t, float2 (
     }
 }
 
+// 4-byte asynchronous global -> shared copy, the bytes beyond src_bytes (0 or 4) zero-filled
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 __device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 
@@ -187,20 +195,62 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     const bool want_dot = P.dot_slot >= 0;
     float pdT = 0.0f, paT = 0.0f;
 
-    // raw node values of the lane's column (rows 0 .. NYB) of one plane, zero where not in range or supported
-    float rx[NYB + 1][3], ru[NYB + 1][3];   // ru: S only (dead code for K)
-    auto fetch = [&](int k) {
-        const unsigned ok = k == 0 ? (okm >> 16) : okm;
-        const float* xs = P.x + int64_t(k) * plane;
-        const float* us = S ? P.u + int64_t(k) * plane : nullptr;
+    // Asynchronous staging (cp.async): every lane copies its own column's values into a private ring of D stages
+    // in shared memory, D - 1 planes ahead of the layer it computes. Stage p holds x (and u) of plane p, rows
+    // 0 .. NYB (zero where not in range or supported, by the copies' zero fill), and the weights of layer p - 1.
+    // A lane only reads what it copied itself, so waiting for its own copies suffices (no barrier).
+    constexpr int D = S ? 3 : 4;
+    constexpr int NV = 3 * (NYB + 1);
+    constexpr int WOFF = S ? 2 * NV : NV;
+    constexpr int PER = WOFF + (S ? 2 * NYB : NYB);
+    __shared__ float ring[D * PER * NT];
+    const int tid = threadIdx.x;
+    const int pmax = min(kz1, nz);   // last plane a layer of this chunk reads
+    auto issue = [&](int p) {
+        if (p <= pmax) {
+            const int slot = p % D;
+            const uint32_t st = uint32_t(__cvta_generic_to_shared(ring + slot * PER * NT + tid));
+            const unsigned ok = p == 0 ? (okm >> 16) : okm;
+            const float* xs = P.x + int64_t(p) * plane;
+            const float* us = S ? P.u + int64_t(p) * plane : nullptr;
 #pragma unroll
-        for (int r = 0; r <= NYB; ++r) {
-            const bool v = (ok >> r) & 1u;
+            for (int r = 0; r <= NYB; ++r) {
+                const bool v = (ok >> r) & 1u;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    cp_async4(st + 4u * uint32_t((3 * r + c) * NT), v ? xs + noff[r] + c : P.x, v ? 4u : 0u);
+                    if (S) cp_async4(st + 4u * uint32_t((NV + 3 * r + c) * NT), v ? us + noff[r] + c : P.x, v ? 4u : 0u);
+                }
+            }
+            if (p >= 1) {
+                const float* wl = P.w + int64_t(p - 1) * elayer;
+                const float* dl = S ? P.d + int64_t(p - 1) * elayer : nullptr;
+#pragma unroll
+                for (int r = 0; r < NYB; ++r) {
+                    const bool e = (em >> r) & 1u;
+                    cp_async4(st + 4u * uint32_t((WOFF + r) * NT), e ? wl + eoff[r] : P.w, e ? 4u : 0u);
+                    if (S) cp_async4(st + 4u * uint32_t((WOFF + NYB + r) * NT), e ? dl + eoff[r] : P.w, e ? 4u : 0u);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    // raw values of plane p and the weights of layer p - 1, from the lane's ring
+    float rx[NYB + 1][3], ru[NYB + 1][3];   // ru: S only (dead code for K)
+    float2 wn[NP], dn[NP];
+    auto consume = [&](int p) {
+        const float* st = ring + (p % D) * PER * NT + tid;
+#pragma unroll
+        for (int r = 0; r <= NYB; ++r)
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                rx[r][c] = v ? __ldg(xs + noff[r] + c) : 0.0f;
-                if (S) ru[r][c] = v ? __ldg(us + noff[r] + c) : 0.0f;
+                rx[r][c] = st[(3 * r + c) * NT];
+                if (S) ru[r][c] = st[(NV + 3 * r + c) * NT];
             }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            wn[q] = make_float2(st[(WOFF + 2 * q) * NT], st[(WOFF + 2 * q + 1) * NT]);
+            if (S) dn[q] = make_float2(st[(WOFF + NYB + 2 * q) * NT], st[(WOFF + NYB + 2 * q + 1) * NT]);
         }
     };
     // x-pairs of a plane from the lane's raw column values and the right neighbour's
@@ -223,21 +273,6 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
                 o[p].hs[c] = add2(rgtH, ownH);
                 o[p].hd[c] = sub2(rgtH, ownH);
             }
-    };
-
-    // element weights of the next layer, as (lower, upper) element of each pair
-    float2 wn[NP], dn[NP];
-    auto fetch_w = [&](int k) {
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            const bool e0 = (em >> (2 * p)) & 1u, e1 = (em >> (2 * p + 1)) & 1u;
-            const float* wl = P.w + int64_t(k) * elayer;
-            wn[p] = make_float2(e0 ? __ldg(wl + eoff[2 * p]) : 0.0f, e1 ? __ldg(wl + eoff[2 * p + 1]) : 0.0f);
-            if (S) {
-                const float* dl = P.d + int64_t(k) * elayer;
-                dn[p] = make_float2(e0 ? __ldg(dl + eoff[2 * p]) : 0.0f, e1 ? __ldg(dl + eoff[2 * p + 1]) : 0.0f);
-            }
-        }
     };
 
     // epilogue of the owned node of row r of plane k with the operator value s
@@ -300,16 +335,13 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) as[r][c] = ad[r][c] = 0.0f;
         if (layer) {
+            issue(k + D);           // into the slot of plane k, read in the previous layer
+            cp_async_wait<D - 1>();  // plane k + 1 and the weights of layer k have landed
+            consume(k + 1);
             xpairs(rx, xhi);
             if (S) xpairs(ru, uhi);
-            if (k + 2 <= nz && k + 1 < kz1) fetch(k + 2);
-            float2 we[NP], de[NP];
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                we[p] = wn[p];
-                if (S) de[p] = dn[p];
-            }
-            if (k + 1 < nz && k + 1 < kz1) fetch_w(k + 1);
+            const float2 (&we)[NP] = wn;
+            const float2 (&de)[NP] = dn;
             const bool count_alpha = k + 1 >= kz0 && k + 1 < kz1;
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
@@ -405,15 +437,17 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int c = 0; c < 3; ++c) carry[p][q][c] = make_float2(0.0f, 0.0f);
-    fetch(kstart);
+#pragma unroll
+    for (int q = 0; q < D; ++q) issue(kstart + q);
+    cp_async_wait<D - 1>();
+    consume(kstart);
     xpairs(rx, xa_);
     if (S) xpairs(ru, ua_);
-    if (kstart + 1 <= nz) fetch(kstart + 1);
-    if (kstart < nz) fetch_w(kstart);
     for (int k = kstart; k < kz1; k += 2) {
         layer_step(k, xa_, xb_, ua_, ub_, carry);
         if (k + 1 < kz1) layer_step(k + 1, xb_, xa_, ub_, ua_, carry);
     }
+    cp_async_wait<0>();
 
     // per-CTA partials; the last CTA finishes the dot and the alpha entry in a fixed order
     if (!want_dot && !P.with_alpha) return;
