@@ -19,7 +19,8 @@
 // plus the top face of the element below it in the previous layer (carried in transformed form) is split into
 // the x-pair form of its two node rows, and a node's value is its own column's part plus the part the lane on
 // its left computed (one shuffle per value). The node row between two warps is completed through shared memory
-// (one float4 per lane and plane, double buffered so that one barrier per plane suffices). Nothing but the
+// (one float4 per lane and plane), handed from the lower warp to the upper one with a pair of named barriers, so
+// that every warp waits only for its neighbours. Nothing but the
 // inputs and the output goes through global memory, and no element value is recomputed except on the CTA's
 // one-column and one-row halo and on the layer below each plane chunk.
 //
@@ -101,6 +102,10 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// named barriers between two adjacent warps (64 threads): one warp waits, the other arrives
+__device__ __forceinline__ void bar_sync(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+__device__ __forceinline__ void bar_arrive(int id) { asm volatile("bar.arrive %0, 64;" ::"r"(id) : "memory"); }
+
 __device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 __device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 
@@ -136,7 +141,8 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     constexpr int R = NW * NYB;            // element rows of the CTA
     constexpr int NP = NYB / 2;            // element pairs per lane
     static_assert(NYB % 2 == 0, "element rows come in pairs");
-    __shared__ float4 sy[2][NW][32];       // node totals of each warp's top row, by plane parity
+    __shared__ float4 sy[NW][32];          // node totals of each warp's top row for the warp above
+    static_assert(2 * NW - 2 <= 15, "named barriers: 1 .. NW - 1 (row written), NW .. 2 NW - 2 (row read)");
     __shared__ double sred[NW];
     __shared__ bool s_last;
 
@@ -156,11 +162,12 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     // supported (same layout), owned by this lane (bit r)
     unsigned okm = 0, fixm = 0, ownm = 0;
     int noff[NYB + 1];                     // node offsets (floats) within a plane
+    const int ic = min(max(i, 0), nx);     // clamped coordinates: every address formed stays inside the arrays
 #pragma unroll
     for (int r = 0; r <= NYB; ++r) {
         const int j = jb + r;
         const bool in = i >= 0 && i <= nx && j >= 0 && j <= ny;
-        noff[r] = in ? 3 * (i + (nx + 1) * j) : 0;
+        noff[r] = 3 * (ic + (nx + 1) * min(max(j, 0), ny));
         if (in) {
             const int fb = fixed_bits(support, nx, ny, nz, i, j);
             if (!(fb & 1)) okm |= 1u << r;
@@ -177,7 +184,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     for (int r = 0; r < NYB; ++r) {
         const int j = jb + r;
         const bool e = lane <= 30 && i >= 0 && i < nx && j >= 0 && j < ny;
-        eoff[r] = e ? i + nx * j : 0;
+        eoff[r] = min(max(i, 0), nx - 1) + nx * min(max(j, 0), ny - 1);
         if (e) em |= 1u << r;
         if (e && lane >= 1 && j >= Y0) am |= 1u << r;
     }
@@ -206,20 +213,24 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     __shared__ float ring[D * PER * NT];
     const int tid = threadIdx.x;
     const int pmax = min(kz1, nz);   // last plane a layer of this chunk reads
+    const uint32_t ring0 = uint32_t(__cvta_generic_to_shared(ring + tid));
+    int islot = 0;   // ring slot of the next stage issued
     auto issue = [&](int p) {
         if (p <= pmax) {
-            const int slot = p % D;
-            const uint32_t st = uint32_t(__cvta_generic_to_shared(ring + slot * PER * NT + tid));
+            const uint32_t st = ring0 + uint32_t(islot * PER * NT * 4);
             const unsigned ok = p == 0 ? (okm >> 16) : okm;
             const float* xs = P.x + int64_t(p) * plane;
             const float* us = S ? P.u + int64_t(p) * plane : nullptr;
 #pragma unroll
             for (int r = 0; r <= NYB; ++r) {
-                const bool v = (ok >> r) & 1u;
+                const uint32_t nb = ((ok >> r) & 1u) ? 4u : 0u;   // zero fill where not in range or supported
+                const float* xr = xs + noff[r];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    cp_async4(st + 4u * uint32_t((3 * r + c) * NT), v ? xs + noff[r] + c : P.x, v ? 4u : 0u);
-                    if (S) cp_async4(st + 4u * uint32_t((NV + 3 * r + c) * NT), v ? us + noff[r] + c : P.x, v ? 4u : 0u);
+                for (int c = 0; c < 3; ++c) cp_async4(st + 4u * uint32_t((3 * r + c) * NT), xr + c, nb);
+                if (S) {
+                    const float* ur = us + noff[r];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) cp_async4(st + 4u * uint32_t((NV + 3 * r + c) * NT), ur + c, nb);
                 }
             }
             if (p >= 1) {
@@ -227,19 +238,21 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
                 const float* dl = S ? P.d + int64_t(p - 1) * elayer : nullptr;
 #pragma unroll
                 for (int r = 0; r < NYB; ++r) {
-                    const bool e = (em >> r) & 1u;
-                    cp_async4(st + 4u * uint32_t((WOFF + r) * NT), e ? wl + eoff[r] : P.w, e ? 4u : 0u);
-                    if (S) cp_async4(st + 4u * uint32_t((WOFF + NYB + r) * NT), e ? dl + eoff[r] : P.w, e ? 4u : 0u);
+                    const uint32_t nb = ((em >> r) & 1u) ? 4u : 0u;
+                    cp_async4(st + 4u * uint32_t((WOFF + r) * NT), wl + eoff[r], nb);
+                    if (S) cp_async4(st + 4u * uint32_t((WOFF + NYB + r) * NT), dl + eoff[r], nb);
                 }
             }
         }
         cp_async_commit();
+        islot = islot == D - 1 ? 0 : islot + 1;
     };
     // raw values of plane p and the weights of layer p - 1, from the lane's ring
     float rx[NYB + 1][3], ru[NYB + 1][3];   // ru: S only (dead code for K)
     float2 wn[NP], dn[NP];
-    auto consume = [&](int p) {
-        const float* st = ring + (p % D) * PER * NT + tid;
+    int cslot = 0;   // ring slot of the next stage consumed
+    auto consume = [&]() {
+        const float* st = ring + cslot * PER * NT + tid;
 #pragma unroll
         for (int r = 0; r <= NYB; ++r)
 #pragma unroll
@@ -252,6 +265,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
             wn[q] = make_float2(st[(WOFF + 2 * q) * NT], st[(WOFF + 2 * q + 1) * NT]);
             if (S) dn[q] = make_float2(st[(WOFF + NYB + 2 * q) * NT], st[(WOFF + NYB + 2 * q + 1) * NT]);
         }
+        cslot = cslot == D - 1 ? 0 : cslot + 1;
     };
     // x-pairs of a plane from the lane's raw column values and the right neighbour's
     auto xpairs = [&](const float (&v)[NYB + 1][3], XPP (&o)[NP]) {
@@ -275,17 +289,17 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
             }
     };
 
-    // epilogue of the owned node of row r of plane k with the operator value s
+    // epilogue of the node of row r of plane k with the operator value s: stored (and counted in the dot) where
+    // the lane owns it; the loads use the clamped, always valid addresses, so no lane branches
     auto epilogue = [&](int k, int r, float s0, float s1, float s2) {
-        if (!((ownm >> r) & 1u)) return;
+        const bool own = (ownm >> r) & 1u;
         const int j = jb + r;
         const int64_t d0 = int64_t(k) * plane + noff[r];
         const bool ofixed = ((k == 0 ? (fixm >> 16) : fixm) >> r) & 1u;
         float sv[3] = {s0, s1, s2};
         float xo[3] = {0.0f, 0.0f, 0.0f};
-        const bool need_x = ofixed || EPI == EPI_JACOBI || EPI == EPI_CHEB || EPI == EPI_GS0 ||
-                            (EPI == EPI_APPLY && want_dot);
-        if (need_x) {
+        constexpr bool always_x = EPI == EPI_JACOBI || EPI == EPI_CHEB || EPI == EPI_GS0;
+        if (always_x || (EPI == EPI_APPLY && want_dot) || ofixed) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) xo[c] = __ldg(P.x + d0 + c);
         }
@@ -294,31 +308,33 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
             for (int c = 0; c < 3; ++c) sv[c] = xo[c];
         }
         const int gs_c = EPI == EPI_GS0 ? P.mode - EPI_GS0 - 3 * node_colour(i, j, k) : 0;
+        float dsum = 0.0f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             float o;
             if (EPI == EPI_APPLY) {
                 o = sv[c];
-                if (want_dot) pdT += o * xo[c];
+                dsum += o * xo[c];
             } else if (EPI == EPI_RESID) {
                 o = __ldg(P.b + d0 + c) - sv[c];
-                if (want_dot) pdT += o * o;
+                dsum += o * o;
             } else if (EPI == EPI_JACOBI) {
                 const float bb = __ldg(P.b + d0 + c);
                 o = xo[c] + omF * ((bb - sv[c]) * __ldg(P.idiag + d0 + c));
-                if (want_dot) pdT += o * bb;
+                dsum += o * bb;
             } else if (EPI == EPI_CHEB) {
                 const float bb = __ldg(P.b + d0 + c);
                 o = c0F * xo[c] + c2F * ((bb - sv[c]) * __ldg(P.idiag + d0 + c));
                 if (c1nz) o -= c1F * P.y[d0 + c];
-                if (want_dot) pdT += o * bb;
+                dsum += o * bb;
             } else {
                 const float bb = __ldg(P.b + d0 + c);
                 o = gs_c == c ? xo[c] + (bb - sv[c]) * __ldg(P.idiag + d0 + c) : xo[c];
-                if (want_dot) pdT += o * bb;
+                dsum += o * bb;
             }
-            P.y[d0 + c] = o;
+            if (own) P.y[d0 + c] = o;
         }
+        if (want_dot && own) pdT += dsum;
     };
 
     // One layer k (planes k and k + 1): lo holds the x-pairs of plane k (x and u), carry the transformed top
@@ -328,16 +344,30 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     auto layer_step = [&](int k, XPP (&xlo)[NP], XPP (&xhi)[NP], XPP (&ulo)[NP], XPP (&uhi)[NP],
                           float2 (&carry)[NP][4][3]) {
         const bool layer = k < nz;
-        // node-row accumulators of plane k in x-pair form (s, d per component), rows 0 .. NYB
-        float as[NYB + 1][3], ad[NYB + 1][3];
+        // node-row accumulators of plane k: the left (own column) and right (next column) parts per component,
+        // rows 0 .. NYB
+        float aL[NYB + 1][3], aR[NYB + 1][3];
 #pragma unroll
         for (int r = 0; r <= NYB; ++r)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) as[r][c] = ad[r][c] = 0.0f;
+            for (int c = 0; c < 3; ++c) aL[r][c] = aR[r][c] = 0.0f;
+        // a face of element pair p (transformed, 4 q-values per element) split into its low and high node rows and
+        // into the left and right columns: low row (F0 - F2) -/+ (F1 - F3), high row (F0 + F2) -/+ (F1 + F3)
+        auto face_rows = [&](float2 F0, float2 F1, float2 F2, float2 F3, int p, int c) {
+            const float2 ls = sub2(F0, F2), ld = sub2(F1, F3);
+            const float2 hs = add2(F0, F2), hd = add2(F1, F3);
+            const float2 lL = sub2(ls, ld), lR = add2(ls, ld), hL = sub2(hs, hd), hR = add2(hs, hd);
+            aL[2 * p][c] += lL.x;
+            aR[2 * p][c] += lR.x;
+            aL[2 * p + 1][c] += hL.x + lL.y;
+            aR[2 * p + 1][c] += hR.x + lR.y;
+            aL[2 * p + 2][c] += hL.y;
+            aR[2 * p + 2][c] += hR.y;
+        };
         if (layer) {
             issue(k + D);           // into the slot of plane k, read in the previous layer
             cp_async_wait<D - 1>();  // plane k + 1 and the weights of layer k have landed
-            consume(k + 1);
+            consume();   // plane k + 1
             xpairs(rx, xhi);
             if (S) xpairs(ru, uhi);
             const float2 (&we)[NP] = wn;
@@ -384,15 +414,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
                         F[q] = add2(carry[p][q][c], sub2(Y[c][q], Y[c][q + 4]));
                         carry[p][q][c] = add2(Y[c][q], Y[c][q + 4]);
                     }
-                    // the face split into the x-pair form of its low and high node rows, per element
-                    const float2 lo_s = sub2(F[0], F[2]), lo_d = sub2(F[1], F[3]);
-                    const float2 hi_s = add2(F[0], F[2]), hi_d = add2(F[1], F[3]);
-                    as[2 * p][c] += lo_s.x;
-                    ad[2 * p][c] += lo_d.x;
-                    as[2 * p + 1][c] += hi_s.x + lo_s.y;
-                    ad[2 * p + 1][c] += hi_d.x + lo_d.y;
-                    as[2 * p + 2][c] += hi_s.y;
-                    ad[2 * p + 2][c] += hi_d.y;
+                    face_rows(F[0], F[1], F[2], F[3], p, c);
                 }
             }
         } else {
@@ -400,16 +422,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
 #pragma unroll
             for (int p = 0; p < NP; ++p)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float2 lo_s = sub2(carry[p][0][c], carry[p][2][c]), lo_d = sub2(carry[p][1][c], carry[p][3][c]);
-                    const float2 hi_s = add2(carry[p][0][c], carry[p][2][c]), hi_d = add2(carry[p][1][c], carry[p][3][c]);
-                    as[2 * p][c] += lo_s.x;
-                    ad[2 * p][c] += lo_d.x;
-                    as[2 * p + 1][c] += hi_s.x + lo_s.y;
-                    ad[2 * p + 1][c] += hi_d.x + lo_d.y;
-                    as[2 * p + 2][c] += hi_s.y;
-                    ad[2 * p + 2][c] += hi_d.y;
-                }
+                for (int c = 0; c < 3; ++c) face_rows(carry[p][0][c], carry[p][1][c], carry[p][2][c], carry[p][3][c], p, c);
         }
         if (k < kz0) return;   // the layer below the chunk: only its top faces are kept
         // node totals: the own column's left part plus the left lane's right part
@@ -417,13 +430,20 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
 #pragma unroll
         for (int r = 0; r <= NYB; ++r)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) tot[r][c] = (as[r][c] - ad[r][c]) + shfl_up1(as[r][c] + ad[r][c]);
-        sy[k & 1][wid][lane] = make_float4(tot[NYB][0], tot[NYB][1], tot[NYB][2], 0.0f);
+            for (int c = 0; c < 3; ++c) tot[r][c] = aL[r][c] + shfl_up1(aR[r][c]);
+        // the top row goes to the warp above through its slot: wait until that warp has read the previous plane's
+        // value, write, signal; rows 1 .. NYB - 1 meanwhile; then the bottom row from the warp below
+        if (wid + 1 < NW) {
+            bar_sync(NW + wid);
+            sy[wid][lane] = make_float4(tot[NYB][0], tot[NYB][1], tot[NYB][2], 0.0f);
+            bar_arrive(1 + wid);
+        }
 #pragma unroll
         for (int r = 1; r < NYB; ++r) epilogue(k, r, tot[r][0], tot[r][1], tot[r][2]);
-        __syncthreads();   // every warp's top row of plane k is in shared memory
         if (wid >= 1) {
-            const float4 v = sy[k & 1][wid - 1][lane];
+            bar_sync(1 + wid - 1);
+            const float4 v = sy[wid - 1][lane];
+            bar_arrive(NW + wid - 1);
             epilogue(k, 0, tot[0][0] + v.x, tot[0][1] + v.y, tot[0][2] + v.z);
         }
     };
@@ -440,13 +460,17 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
 #pragma unroll
     for (int q = 0; q < D; ++q) issue(kstart + q);
     cp_async_wait<D - 1>();
-    consume(kstart);
+    consume();   // plane kstart
     xpairs(rx, xa_);
     if (S) xpairs(ru, ua_);
+    // the slot between warps w and w + 1 starts free: the reader's first "read done" is signalled up front, and
+    // the writer's last wait matches the reader's last signal, so every barrier phase completes
+    if (wid >= 1) bar_arrive(NW + wid - 1);
     for (int k = kstart; k < kz1; k += 2) {
         layer_step(k, xa_, xb_, ua_, ub_, carry);
         if (k + 1 < kz1) layer_step(k + 1, xb_, xa_, ub_, ua_, carry);
     }
+    if (wid + 1 < NW) bar_sync(NW + wid);
     cp_async_wait<0>();
 
     // per-CTA partials; the last CTA finishes the dot and the alpha entry in a fixed order
@@ -504,7 +528,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
 // ------------------------------------------------------------------------------------------------
 // plans: element rows per warp, warps per CTA, resident CTAs per SM asked of the register allocator
 // ------------------------------------------------------------------------------------------------
-#define PBM_STRIP_PLANS(X) X(0, 2, 4, 2) X(1, 2, 8, 1) X(2, 2, 4, 3) X(3, 4, 4, 1)
+#define PBM_STRIP_PLANS(X) X(0, 2, 4, 2) X(1, 2, 8, 1) X(2, 2, 4, 3) X(3, 2, 6, 2)
 #define PBM_STRIP_ROW(id, nyb, nw, minb) {nyb, nw, minb},
 static const int kStripPlans[][3] = {PBM_STRIP_PLANS(PBM_STRIP_ROW)};
 #undef PBM_STRIP_ROW
@@ -524,8 +548,8 @@ FusedPlan strip_plan(const Geom& G, int cand) {
     const int planes = G.nz + 1;
     const int tiles = p.gx * p.gy;
     const int sms = num_sms();
-    // a launch takes about waves x (DZ + 1) plane steps with per_sm resident CTAs per SM: the shortest, then the
-    // fewest CTAs
+    // a launch takes about waves x (DZ + 1) plane steps with per_sm resident CTAs per SM: the shortest, and of
+    // equally short ones the one with the fewest CTAs (the least halo work)
     double best = 1e300;
     p.DZ = planes;
     for (int dz = std::max(1, std::min(planes, 2)); dz <= planes; ++dz) {
@@ -533,7 +557,7 @@ FusedPlan strip_plan(const Geom& G, int cand) {
         if (dz > 1 && (planes + dz - 2) / (dz - 1) == gz && dz != planes) continue;
         const double waves = double((int64_t(tiles) * gz + sms * per_sm - 1) / (sms * per_sm));
         const double cost = waves * (dz + 1);
-        if (cost < best - 1e-9) {
+        if (cost <= best + 1e-9) {
             best = cost;
             p.DZ = dz;
         }
