@@ -28,6 +28,7 @@
 // partial sums of the dot product and of the alpha row are finished by the last CTA in a fixed order, so the
 // results are bit-reproducible for a given plan.
 #include <algorithm>
+#include <atomic>
 
 #include "fp32_elem.h"
 #include "pbm_internal.h"
@@ -67,31 +68,21 @@ __device__ __forceinline__ void khat_pair(const KeHatP& K, const float2 (&X)[3][
     }
 }
 
-// x-pairs of the two node rows of each element of a pair, per component: s = v(i + 1) + v(i), d = v(i + 1) - v(i),
-// as (lower element, upper element)
-struct XPP {
-    float2 ls[3], ld[3];   // low rows (rows 2p, 2p + 1)
-    float2 hs[3], hd[3];   // high rows (rows 2p + 1, 2p + 2)
+// face quads of the two elements of a pair on one plane, per pattern q and component c, as (lower element, upper
+// element): fused.cu's convention, q = 0 sum, 1 x-difference, 2 y-difference, 3 both
+struct FQ {
+    float2 q[4][3];
 };
 
-// the 24 transformed coefficients of the two elements from the x-pairs of their bottom and top planes
-__device__ __forceinline__ void pair_coeffs(const XPP& b, const XPP& t, float2 (&X)[3][8]) {
+// the 24 transformed coefficients of the two elements from the face quads of their bottom and top planes
+__device__ __forceinline__ void pair_coeffs(const FQ& b, const FQ& t, float2 (&X)[3][8]) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        // face quads (fused.cu's convention: 0 sum, 1 x-difference, 2 y-difference, 3 both)
-        const float2 b0 = add2(b.ls[c], b.hs[c]), b1 = add2(b.ld[c], b.hd[c]);
-        const float2 b2 = sub2(b.hs[c], b.ls[c]), b3 = sub2(b.hd[c], b.ld[c]);
-        const float2 t0 = add2(t.ls[c], t.hs[c]), t1 = add2(t.ld[c], t.hd[c]);
-        const float2 t2 = sub2(t.hs[c], t.ls[c]), t3 = sub2(t.hd[c], t.ld[c]);
-        X[c][0] = add2(b0, t0);
-        X[c][1] = add2(b1, t1);
-        X[c][2] = add2(b2, t2);
-        X[c][3] = add2(b3, t3);
-        X[c][4] = sub2(t0, b0);
-        X[c][5] = sub2(t1, b1);
-        X[c][6] = sub2(t2, b2);
-        X[c][7] = sub2(t3, b3);
-    }
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            X[c][q] = add2(b.q[q][c], t.q[q][c]);
+            X[c][q + 4] = sub2(t.q[q][c], b.q[q][c]);
+        }
 }
 
 // 4-byte asynchronous global -> shared copy, the bytes beyond src_bytes (0 or 4) zero-filled
@@ -203,14 +194,16 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     float pdT = 0.0f, paT = 0.0f;
 
     // Asynchronous staging (cp.async): every lane copies its own column's values into a private ring of D stages
-    // in shared memory, D - 1 planes ahead of the layer it computes. Stage p holds x (and u) of plane p, rows
-    // 0 .. NYB (zero where not in range or supported, by the copies' zero fill), and the weights of layer p - 1.
-    // A lane only reads what it copied itself, so waiting for its own copies suffices (no barrier).
-    constexpr int D = S ? 3 : 4;
+    // in shared memory. Stage p holds x (and u) of plane p, rows 0 .. NYB (zero where not in range or supported,
+    // by the copies' zero fill), and the weights of layer p - 1. Layer k reads planes k and k + 1 from the ring
+    // (both stay resident while it runs, so no plane's transform is kept in registers across layers) and then
+    // issues plane k + D - 1 into the slot of plane k - 1. A lane only reads what it copied itself, so waiting for
+    // its own copies suffices (no barrier).
+    constexpr int D = S ? 4 : 5;
     constexpr int NV = 3 * (NYB + 1);
     constexpr int WOFF = S ? 2 * NV : NV;
     constexpr int PER = WOFF + (S ? 2 * NYB : NYB);
-    __shared__ float ring[D * PER * NT];
+    extern __shared__ float ring[];   // D * PER * NT floats (dynamic: strip_ring_bytes)
     const int tid = threadIdx.x;
     const int pmax = min(kz1, nz);   // last plane a layer of this chunk reads
     const uint32_t ring0 = uint32_t(__cvta_generic_to_shared(ring + tid));
@@ -250,9 +243,8 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     // raw values of plane p and the weights of layer p - 1, from the lane's ring
     float rx[NYB + 1][3], ru[NYB + 1][3];   // ru: S only (dead code for K)
     float2 wn[NP], dn[NP];
-    int cslot = 0;   // ring slot of the next stage consumed
-    auto consume = [&]() {
-        const float* st = ring + cslot * PER * NT + tid;
+    auto read_plane = [&](int slot) {
+        const float* st = ring + slot * PER * NT + tid;
 #pragma unroll
         for (int r = 0; r <= NYB; ++r)
 #pragma unroll
@@ -260,15 +252,21 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
                 rx[r][c] = st[(3 * r + c) * NT];
                 if (S) ru[r][c] = st[(NV + 3 * r + c) * NT];
             }
+    };
+    auto read_w = [&](int slot) {
+        const float* st = ring + slot * PER * NT + tid;
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             wn[q] = make_float2(st[(WOFF + 2 * q) * NT], st[(WOFF + 2 * q + 1) * NT]);
             if (S) dn[q] = make_float2(st[(WOFF + NYB + 2 * q) * NT], st[(WOFF + NYB + 2 * q + 1) * NT]);
         }
-        cslot = cslot == D - 1 ? 0 : cslot + 1;
     };
-    // x-pairs of a plane from the lane's raw column values and the right neighbour's
-    auto xpairs = [&](const float (&v)[NYB + 1][3], XPP (&o)[NP]) {
+    int cslot = 0;   // ring slot of plane k of the current layer
+
+    // face quads of a plane from the lane's raw column values and the right neighbour's: the x-pairs (sum and
+    // difference of the two node columns) of the element pair's low rows (2p, 2p + 1) and high rows (2p + 1, 2p + 2),
+    // then their sum and difference along y
+    auto plane_quads = [&](const float (&v)[NYB + 1][3], FQ (&o)[NP]) {
         float rt[NYB + 1][3];
 #pragma unroll
         for (int r = 0; r <= NYB; ++r)
@@ -282,10 +280,12 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
                 const float2 ownH = make_float2(v[2 * p + 1][c], v[2 * p + 2][c]);
                 const float2 rgtL = make_float2(rt[2 * p][c], rt[2 * p + 1][c]);
                 const float2 rgtH = make_float2(rt[2 * p + 1][c], rt[2 * p + 2][c]);
-                o[p].ls[c] = add2(rgtL, ownL);
-                o[p].ld[c] = sub2(rgtL, ownL);
-                o[p].hs[c] = add2(rgtH, ownH);
-                o[p].hd[c] = sub2(rgtH, ownH);
+                const float2 ls = add2(rgtL, ownL), ld = sub2(rgtL, ownL);
+                const float2 hs = add2(rgtH, ownH), hd = sub2(rgtH, ownH);
+                o[p].q[0][c] = add2(ls, hs);
+                o[p].q[1][c] = add2(ld, hd);
+                o[p].q[2][c] = sub2(hs, ls);
+                o[p].q[3][c] = sub2(hd, ld);
             }
     };
 
@@ -341,8 +341,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     // faces of layer k - 1 (zero below the first layer); hi receives those of plane k + 1 and carry the top
     // faces of layer k. Then the node values of plane k are finished (k >= kz0). Called with the lo / hi roles
     // swapped on alternate layers, so nothing is copied between layers.
-    auto layer_step = [&](int k, XPP (&xlo)[NP], XPP (&xhi)[NP], XPP (&ulo)[NP], XPP (&uhi)[NP],
-                          float2 (&carry)[NP][4][3]) {
+    auto layer_step = [&](int k, float2 (&carry)[NP][4][3]) {
         const bool layer = k < nz;
         // node-row accumulators of plane k: the left (own column) and right (next column) parts per component,
         // rows 0 .. NYB
@@ -364,12 +363,17 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
             aL[2 * p + 2][c] += hL.y;
             aR[2 * p + 2][c] += hR.y;
         };
+        const int hslot = cslot == D - 1 ? 0 : cslot + 1;
         if (layer) {
-            issue(k + D);           // into the slot of plane k, read in the previous layer
-            cp_async_wait<D - 1>();  // plane k + 1 and the weights of layer k have landed
-            consume();   // plane k + 1
-            xpairs(rx, xhi);
-            if (S) xpairs(ru, uhi);
+            cp_async_wait<D - 3>();  // plane k + 1 and the weights of layer k have landed
+            FQ xlo[NP], xhi[NP], ulo[NP], uhi[NP];   // ulo, uhi: S only
+            read_plane(cslot);
+            plane_quads(rx, xlo);
+            if (S) plane_quads(ru, ulo);
+            read_plane(hslot);
+            read_w(hslot);
+            plane_quads(rx, xhi);
+            if (S) plane_quads(ru, uhi);
             const float2 (&we)[NP] = wn;
             const float2 (&de)[NP] = dn;
             const bool count_alpha = k + 1 >= kz0 && k + 1 < kz1;
@@ -383,11 +387,14 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
                     float2 U[3][8];
                     pair_coeffs(ulo[p], uhi[p], U);
                     khat_pair(P.K, X, Y);
-                    float2 dot = make_float2(0.0f, 0.0f);
+                    float2 dc[3];   // one partial sum per component: short dependency chains
 #pragma unroll
-                    for (int c = 0; c < 3; ++c)
+                    for (int c = 0; c < 3; ++c) {
+                        dc[c] = mul2(U[c][1], Y[c][1]);
 #pragma unroll
-                        for (int q = 1; q < 8; ++q) dot = fma2(U[c][q], Y[c][q], dot);
+                        for (int q = 2; q < 8; ++q) dc[c] = fma2(U[c][q], Y[c][q], dc[c]);
+                    }
+                    const float2 dot = add2(add2(dc[0], dc[1]), dc[2]);
                     const float2 te = mul2(de[p], make_float2(dot.x - xa, dot.y - xa));
                     if (count_alpha) {
                         if ((am >> (2 * p)) & 1u) paT -= te.x;
@@ -398,25 +405,38 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
 #pragma unroll
                         for (int q = 1; q < 8; ++q) X[c][q] = fma2(te, U[c][q], mul2(we[p], X[c][q]));
                     khat_pair(P.K, X, Y);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        // bottom face plus the carried top face of the layer below; the new top face is carried
+                        float2 F[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            F[q] = add2(carry[p][q][c], sub2(Y[c][q], Y[c][q + 4]));
+                            carry[p][q][c] = add2(Y[c][q], Y[c][q + 4]);
+                        }
+                        face_rows(F[0], F[1], F[2], F[3], p, c);
+                    }
                 } else {
                     khat_pair(P.K, X, Y);
+                    // the element weight enters with the faces: top w (Y_q + Y_q+4), bottom plus carry
+                    // carry + w (Y_q - Y_q+4); Y_0 = 0
 #pragma unroll
-                    for (int c = 0; c < 3; ++c)
+                    for (int c = 0; c < 3; ++c) {
+                        float2 F[4];
+                        const float2 wy4 = mul2(we[p], Y[c][4]);
+                        F[0] = sub2(carry[p][0][c], wy4);
+                        carry[p][0][c] = wy4;
 #pragma unroll
-                        for (int q = 1; q < 8; ++q) Y[c][q] = mul2(we[p], Y[c][q]);
-                }
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    // bottom face plus the carried top face of the layer below; the new top face is carried
-                    float2 F[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        F[q] = add2(carry[p][q][c], sub2(Y[c][q], Y[c][q + 4]));
-                        carry[p][q][c] = add2(Y[c][q], Y[c][q + 4]);
+                        for (int q = 1; q < 4; ++q) {
+                            const float2 wyq4 = mul2(we[p], Y[c][q + 4]);
+                            F[q] = sub2(fma2(we[p], Y[c][q], carry[p][q][c]), wyq4);
+                            carry[p][q][c] = fma2(we[p], Y[c][q], wyq4);
+                        }
+                        face_rows(F[0], F[1], F[2], F[3], p, c);
                     }
-                    face_rows(F[0], F[1], F[2], F[3], p, c);
                 }
             }
+            issue(k + D - 1);        // into the slot of plane k - 1
         } else {
             // above the last layer: plane k = nz holds only the top faces of layer nz - 1
 #pragma unroll
@@ -424,6 +444,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) face_rows(carry[p][0][c], carry[p][1][c], carry[p][2][c], carry[p][3][c], p, c);
         }
+        cslot = hslot;
         if (k < kz0) return;   // the layer below the chunk: only its top faces are kept
         // node totals: the own column's left part plus the left lane's right part
         float tot[NYB + 1][3];
@@ -449,7 +470,6 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     };
 
     const int kstart = max(kz0 - 1, 0);
-    XPP xa_[NP], xb_[NP], ua_[NP], ub_[NP];   // ua_, ub_: S only
     float2 carry[NP][4][3];
 #pragma unroll
     for (int p = 0; p < NP; ++p)
@@ -458,17 +478,13 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) carry[p][q][c] = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int q = 0; q < D; ++q) issue(kstart + q);
-    cp_async_wait<D - 1>();
-    consume();   // plane kstart
-    xpairs(rx, xa_);
-    if (S) xpairs(ru, ua_);
+    for (int q = 0; q < D - 1; ++q) issue(kstart + q);
     // the slot between warps w and w + 1 starts free: the reader's first "read done" is signalled up front, and
     // the writer's last wait matches the reader's last signal, so every barrier phase completes
     if (wid >= 1) bar_arrive(NW + wid - 1);
     for (int k = kstart; k < kz1; k += 2) {
-        layer_step(k, xa_, xb_, ua_, ub_, carry);
-        if (k + 1 < kz1) layer_step(k + 1, xb_, xa_, ub_, ua_, carry);
+        layer_step(k, carry);
+        if (k + 1 < kz1) layer_step(k + 1, carry);
     }
     if (wid + 1 < NW) bar_sync(NW + wid);
     cp_async_wait<0>();
@@ -528,7 +544,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
 // ------------------------------------------------------------------------------------------------
 // plans: element rows per warp, warps per CTA, resident CTAs per SM asked of the register allocator
 // ------------------------------------------------------------------------------------------------
-#define PBM_STRIP_PLANS(X) X(0, 2, 4, 2) X(1, 2, 8, 1) X(2, 2, 4, 3) X(3, 2, 6, 2)
+#define PBM_STRIP_PLANS(X) X(0, 2, 4, 2) X(1, 2, 8, 2) X(2, 2, 4, 3) X(3, 2, 6, 2)
 #define PBM_STRIP_ROW(id, nyb, nw, minb) {nyb, nw, minb},
 static const int kStripPlans[][3] = {PBM_STRIP_PLANS(PBM_STRIP_ROW)};
 #undef PBM_STRIP_ROW
@@ -566,11 +582,36 @@ FusedPlan strip_plan(const Geom& G, int cand) {
     return p;
 }
 
+// bytes of the staging ring of the kernel: D stages of x (and u) of NYB + 1 node rows and the weights of NYB
+// element rows, per thread
+static size_t strip_ring_bytes(int mode, int nyb, int nw) {
+    const bool s = mode == 2;
+    const int D = s ? 4 : 5, NV = 3 * (nyb + 1);
+    const int per = (s ? 2 * NV : NV) + (s ? 2 * nyb : nyb);
+    return sizeof(float) * size_t(D) * size_t(per) * size_t(32 * nw);
+}
+
+// launch with the ring in dynamic shared memory (the opt-in above 48 KB set once per kernel and device)
+template <int MODE, int EPI, int NYB, int NW, int MINB>
+static void strip_launch_one(int blocks, const StripArgs& P, cudaStream_t st) {
+    auto kern = k_strip_f32<MODE, EPI, NYB, NW, MINB>;
+    const size_t smem = strip_ring_bytes(MODE, NYB, NW);
+    static std::atomic<uint64_t> set_on{0};   // bit per device ordinal < 64
+    int dev = 0;
+    PBM_CUDA(cudaGetDevice(&dev));
+    const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+    if (!bit || !(set_on.load() & bit)) {
+        PBM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        if (bit) set_on.fetch_or(bit);
+    }
+    launch_pdl(kern, dim3(blocks), dim3(32 * NW), smem, st, P);
+}
+
 template <int MODE, int EPI>
 static void strip_launch_epi(int cand, int blocks, const StripArgs& P, cudaStream_t st) {
     switch (cand) {
 #define PBM_STRIP_CASE(id, nyb, nw, minb) \
-    case id: launch_pdl(k_strip_f32<MODE, EPI, nyb, nw, minb>, dim3(blocks), dim3(32 * nw), 0, st, P); break;
+    case id: strip_launch_one<MODE, EPI, nyb, nw, minb>(blocks, P, st); break;
         PBM_STRIP_PLANS(PBM_STRIP_CASE)
 #undef PBM_STRIP_CASE
         default: fail(PBM_EINVAL, "strip operator: unknown plan");
