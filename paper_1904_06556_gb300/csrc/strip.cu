@@ -299,14 +299,15 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
         float sv[3] = {s0, s1, s2};
         float xo[3] = {0.0f, 0.0f, 0.0f};
         constexpr bool always_x = EPI == EPI_JACOBI || EPI == EPI_CHEB || EPI == EPI_GS0;
-        if (always_x || (EPI == EPI_APPLY && want_dot) || ofixed) {
+        if (always_x || (EPI == EPI_APPLY && want_dot)) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) xo[c] = __ldg(P.x + d0 + c);
-        }
-        if (ofixed) {
+        } else {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) sv[c] = xo[c];
+            for (int c = 0; c < 3; ++c) xo[c] = ofixed ? __ldg(P.x + d0 + c) : 0.0f;   // supported nodes only
         }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sv[c] = ofixed ? xo[c] : sv[c];
         const int gs_c = EPI == EPI_GS0 ? P.mode - EPI_GS0 - 3 * node_colour(i, j, k) : 0;
         float dsum = 0.0f;
 #pragma unroll
