@@ -387,7 +387,8 @@ def run_ours(args):
     e2e_value = whole_job_rate(world, args.steps, e2e_ms)
     solve = {"minres_iterations": iters[-1], "true_relres": info_main["relres"], "phases_last_step": phases,
              "mixed_outer_steps": info_main["outer"], "fine_chunk": G.info()["fine_chunk"],
-             "fp32_tile_K_S": G.info()["fp32_tile"], "step_ms_min": min(step_ms),
+             "fp32_tile_K_S": G.info()["fp32_tile"], "fp32_coarse_plans_K_S": G.info()["coarse_plan"],
+             "step_ms_min": min(step_ms),
              "step_ms_median": statistics.median(step_ms)}
     if uinfo is not None:
         solve["equilibrium_u_relres"] = uinfo["relres"]

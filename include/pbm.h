@@ -125,6 +125,9 @@ typedef struct pbm_grid_info {
     int fp32_tile[2][5];          /* plan of the single-pass FP32 fine operator, for K and for S:
                                      {TX, TY, DZ} node columns x node columns x planes per CTA,
                                      threads per CTA, plan index (pbm_set_fp32_plan)               */
+    int coarse_plan[2][16];       /* form of the FP32 operator of coarse level k, for K and for S
+                                     (pbm_set_fp32_coarse_plan): set for 1 <= k <= levels - 2 on
+                                     PBM_MIXED grids, 0 elsewhere                                 */
 } pbm_grid_info;
 
 /* Newton state of the dual VTS problem (eq. (aug_lagr)): variables xi = (u, alpha, nu_lo, nu_up),
@@ -263,6 +266,18 @@ int pbm_apply_level_f32(pbm_grid* g, int level, int op, int epilogue, const floa
 int pbm_fp32_plan_count(void);
 int pbm_fp32_tc_plan(void);
 int pbm_set_fp32_plan(pbm_grid* g, int op, int plan);
+
+/* Forms of the FP32 operator of a coarse level 1 <= level <= levels - 2 (the Galerkin element
+ * matrices of Section 5.1, stored; the coarsest level is solved directly): plan -1 is two passes
+ * (element rows, then node sums) with the 24 rows of each element split over eight threads, -2
+ * the two passes with one thread per element (each stored entry loaded once), and
+ * 0 <= plan < pbm_fp32_coarse_plan_count() a tile plan of the single marching pass.
+ * pbm_create_grid times them on PBM_MIXED grids per level and operator (levels of 32768 elements
+ * or more: the two-pass forms only) and keeps the fastest; pbm_set_fp32_coarse_plan overrides the
+ * choice for `op` on `level`. Every form computes the same operator; only the summation order
+ * differs. Errors: PBM_EINVAL (op, level or plan out of range), PBM_ESTATE (not a PBM_MIXED grid). */
+int pbm_fp32_coarse_plan_count(void);
+int pbm_set_fp32_coarse_plan(pbm_grid* g, int op, int level, int plan);
 
 /* Copies the Jacobi diagonal of level `level` of the current hierarchy (K or S, the last one set
  * up) into diag_dev: n_level + 1 FP64 entries (the last is the alpha entry of S, 1 for K);

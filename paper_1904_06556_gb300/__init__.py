@@ -60,6 +60,12 @@ def fp32_tc_plan() -> int:
     return int(lib().pbm_fp32_tc_plan())
 
 
+def fp32_coarse_plan_count() -> int:
+    """Number of tile plans of the single-pass FP32 coarse operator (pbm_fp32_coarse_plan_count); the
+    two-pass forms are plans -1 (rows split over eight threads) and -2 (one thread per element)."""
+    return int(lib().pbm_fp32_coarse_plan_count())
+
+
 def _ptr(t: torch.Tensor | None, dtype=torch.float64, n: int | None = None, name: str = "tensor"):
     if t is None:
         return None
@@ -135,7 +141,8 @@ class Grid:
         return dict(levels=L, dims=[(gi.nx[k], gi.ny[k], gi.nz[k]) for k in range(L)], n=list(gi.n[:L]),
                     m=list(gi.m[:L]), n_free=gi.n_free, omega=list(gi.omega[:L]), lambda_max=list(gi.lambda_max[:L]),
                     device_bytes=gi.device_bytes, fine_chunk=list(gi.fine_chunk),
-                    fp32_tile=[list(gi.fp32_tile[0]), list(gi.fp32_tile[1])])
+                    fp32_tile=[list(gi.fp32_tile[0]), list(gi.fp32_tile[1])],
+                    coarse_plan=[list(gi.coarse_plan[0][1:max(1, L - 1)]), list(gi.coarse_plan[1][1:max(1, L - 1)])])
 
     def maps(self, level: int, which: str):
         import numpy as np
@@ -280,6 +287,10 @@ class Grid:
     def set_fp32_plan(self, op: str, plan: int):
         """Overrides the autotuned tile plan of the FP32 fine operator for op (pbm_set_fp32_plan)."""
         self._check(self._L.pbm_set_fp32_plan(self._h, _lib.OPS[op], int(plan)))
+
+    def set_fp32_coarse_plan(self, op: str, level: int, plan: int):
+        """Overrides the autotuned form of the FP32 operator of coarse level `level` (pbm_set_fp32_coarse_plan)."""
+        self._check(self._L.pbm_set_fp32_coarse_plan(self._h, _lib.OPS[op], int(level), int(plan)))
 
     def diag(self, level: int = 0) -> torch.Tensor:
         """Jacobi diagonal (n_level + 1 FP64 entries) of a level of the current hierarchy (pbm_get_diag)."""

@@ -38,7 +38,7 @@ class GridInfo(C.Structure):
     _fields_ = [("levels", C.c_int), ("nx", C.c_int * 16), ("ny", C.c_int * 16), ("nz", C.c_int * 16),
                 ("n", C.c_int64 * 16), ("m", C.c_int64 * 16), ("n_free", C.c_int64), ("omega", C.c_double * 16),
                 ("lambda_max", C.c_double * 16), ("device_bytes", C.c_int64), ("fine_chunk", C.c_int * 4),
-                ("fp32_tile", (C.c_int * 5) * 2)]
+                ("fp32_tile", (C.c_int * 5) * 2), ("coarse_plan", (C.c_int * 16) * 2)]
 
 
 class State(C.Structure):
@@ -136,6 +136,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pbm_ip_solve": (i, [vp, vp, vp, d, i, C.POINTER(SolveInfo), vp]),
         "pbm_ip_recover": (i, [vp, vp, vp, vp, vp, vp]),
         "pbm_set_fp32_plan": (i, [vp, i, i]),
+        "pbm_fp32_coarse_plan_count": (i, []),
+        "pbm_set_fp32_coarse_plan": (i, [vp, i, i, i]),
         "pbm_set_state": (i, [vp, C.POINTER(State), vp]),
         "pbm_apply_S": (i, [vp, vp, vp, vp]),
         "pbm_reduced_rhs": (i, [vp, vp, vp, C.POINTER(C.c_double), vp]),

@@ -262,9 +262,9 @@ void launch_fine(pbm_grid* g, bool fp32, const void* w, const void* d, const voi
 
 // Coarse levels. FP64 runs the two column passes (colpass.cu), whose finer split (eight threads per
 // element) keeps the narrow FP64 pipe of every SM busy. FP32 runs, per level, whichever the grid's
-// autotuner found faster: the single pass (fused.cu; one launch, tile halos read their element
-// matrices twice) or the two passes (no recomputation; the better choice where the matrices'
-// traffic dominates, on the larger levels).
+// autotuner found faster: the single marching pass (fused.cu; one launch, tile halos read their
+// element matrices twice) or the two passes with eight threads or one thread per element (no
+// recomputation; the larger levels, where the matrices' traffic dominates).
 void launch_coarse(pbm_grid* g, int k, bool fp32, const ApplyArgs& a, cudaStream_t st) {
     Level& L = g->L[k];
     const int plan = g->coarseP[a.with_alpha ? 1 : 0][k];
@@ -272,7 +272,7 @@ void launch_coarse(pbm_grid* g, int k, bool fp32, const ApplyArgs& a, cudaStream
         fused_coarse_f32(fused_coarse_plan(L.g, plan), red_set(g, a.rset), L.g, L.A32, L.bord32, &g->sc->salpha, a,
                          st);
     else if (fp32)
-        cols_coarse<float>(g, k, L.A32, L.bord32, a, st);
+        cols_coarse<float>(g, k, L.A32, L.bord32, a, st, plan == -2);
     else
         cols_coarse<double>(g, k, L.A64, L.bord64, a, st);
 }

@@ -501,6 +501,8 @@ int pbm_grid_info_get(const pbm_grid* g, pbm_grid_info* out) {
         out->fp32_tile[op][2] = fp.DZ;
         out->fp32_tile[op][3] = fused_threads(fp);
         out->fp32_tile[op][4] = g->fusedP[op];
+        if (g->desc.precision == PBM_MIXED)
+            for (int k = 1; k + 1 < g->levels; ++k) out->coarse_plan[op][k] = g->coarseP[op][k];
     }
     PBM_CATCH
 }
@@ -652,6 +654,19 @@ int pbm_set_fp32_plan(pbm_grid* g, int op, int plan) {
     if (op != PBM_OP_K && op != PBM_OP_S) fail(PBM_EINVAL, "unknown operator");
     if (plan < 0 || plan >= fused_num_plans()) fail(PBM_EINVAL, "plan out of range");
     g->fusedP[op == PBM_OP_S ? 1 : 0] = plan;
+    PBM_CATCH
+}
+
+int pbm_fp32_coarse_plan_count(void) { return fused_coarse_num_plans(); }
+
+int pbm_set_fp32_coarse_plan(pbm_grid* g, int op, int level, int plan) {
+    PBM_TRY
+    if (!g) fail(PBM_EINVAL, "null grid");
+    if (op != PBM_OP_K && op != PBM_OP_S) fail(PBM_EINVAL, "unknown operator");
+    if (g->desc.precision != PBM_MIXED) fail(PBM_ESTATE, "FP32 operators need a PBM_MIXED grid");
+    if (level < 1 || level > g->levels - 2) fail(PBM_EINVAL, "not a coarse level with an operator");
+    if (plan < -2 || plan >= fused_coarse_num_plans()) fail(PBM_EINVAL, "plan out of range");
+    g->coarseP[op == PBM_OP_S ? 1 : 0][level] = plan;
     PBM_CATCH
 }
 

@@ -1,7 +1,8 @@
 // Two-pass operator application: element columns, then nodes.
 //
 // Pass 1 gives every thread one element column (i, j) and a chunk of L element layers of it (the
-// coarse levels use L = 1 and split each element's 24 rows over eight threads). For each layer it
+// coarse levels use L = 1 and split each element's 24 rows over eight threads, or, on FP32 levels
+// where the autotuner finds it faster, give each thread one element). For each layer it
 // forms the element's contribution to the 8 corner nodes and writes, per node plane, the 4 corner
 // values of the column ("plane quads") to scratch:
 //   QA[k]  plane k as bottom face of layer k (plus, inside a chunk, the top face of layer k - 1),
@@ -264,6 +265,56 @@ template <class T>
 __global__ void __launch_bounds__(CB) k_cols_coarse(ColArgs<T> P) {
     pdl_wait();
     cols_coarse_body<T>(P, blockIdx.x);
+}
+
+// The same pass with one thread per element (FP32 levels whose matrices dominate the traffic):
+// each stored entry (r, s), r <= s, is loaded once and used twice (y_r += a x_s, y_s += a x_r), so
+// the SMs load 300 values per element instead of the 576 the row-wise split reads (every entry
+// off the diagonal by two threads). Lanes are consecutive elements, so every load of an entry is
+// one coalesced row of the entry-major array; the eight corner rows go to the same plane-quad
+// scratch as the split pass, and the node pass is shared.
+template <class T>
+__global__ void __launch_bounds__(CB) k_cols_coarse_e(ColArgs<T> P) {
+    pdl_wait();
+    const unsigned mu = unsigned(P.m), ncol = unsigned(P.ncol), nxu = unsigned(P.nx);
+    const unsigned eu = blockIdx.x * CB + threadIdx.x;
+    if (eu >= mu) return;
+    const unsigned ku = eu / ncol, colu = eu - ku * ncol;
+    const int k = int(ku);
+    const int j = int(colu / nxu), i = int(colu - unsigned(j) * nxu);
+    const int64_t sxn = P.nx + 1, sxy = int64_t(P.nx + 1) * (P.ny + 1);
+    T xe[24], y[24];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int ii = i + (b & 1), jj = j + ((b >> 1) & 1), kk = k + (b >> 2);
+        const bool fx = node_fixed(P.support, P.nx, P.ny, P.nz, ii, jj, kk);
+        const int64_t nd = 3 * (ii + sxn * jj + sxy * kk);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xe[3 * b + c] = fx ? T(0) : __ldg(P.x + nd + c);
+    }
+#pragma unroll
+    for (int r = 0; r < 24; ++r) y[r] = T(0);
+    const T* Ae = P.A + eu;
+#pragma unroll
+    for (int r = 0; r < 24; ++r) {
+        // row r of the upper triangle: its entries are consecutive in the entry order
+        T a[24];
+#pragma unroll
+        for (int s = r; s < 24; ++s) a[s] = __ldg(Ae + int64_t(tri_index(r, s)) * mu);
+        y[r] += a[r] * xe[r];
+#pragma unroll
+        for (int s = r + 1; s < 24; ++s) {
+            y[r] += a[s] * xe[s];
+            y[s] += a[s] * xe[r];
+        }
+    }
+    const int64_t col = colu;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        T* Q = (b < 4 ? P.QA : P.QB) + (int64_t(k) * 12 + 3 * (b & 3)) * P.ncol + col;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Q[c * P.ncol] = y[3 * b + c];
+    }
 }
 
 template <class T>
@@ -714,16 +765,14 @@ void autotune_fine(pbm_grid* g) {
                 }
                 g->fusedP[op] = bestP;
             }
-        // plans of the single-pass FP32 coarse operator, per level that is ever applied. Levels of
-        // 32768 elements or more keep the two passes without timing: their element matrices (1.2 KB
-        // per element) dominate and the single pass reads those of its tile halos twice.
+        // FP32 coarse operator per level that is ever applied: the two passes with eight threads per
+        // element (-1) or one (-2), or a plan of the single pass. Levels of 32768 elements or more
+        // time only the two-pass forms: their element matrices (1.2 KB per element) dominate and the
+        // single pass reads those of its tile halos twice.
         if (mixed)
             for (int k = 1; k + 1 < g->levels; ++k) {
                 const Level& L = g->L[k];
-                if (L.g.m() >= 32768) {
-                    g->coarseP[0][k] = g->coarseP[1][k] = -1;
-                    continue;
-                }
+                const int last = L.g.m() >= 32768 ? 0 : fused_coarse_num_plans();
                 PBM_CUDA(cudaMemset(L.A32, 0, sizeof(float) * NTRI * L.g.m()));
                 PBM_CUDA(cudaMemset(L.bord32, 0, sizeof(float) * (L.g.n() + 1)));
                 for (int op = 0; op < 2; ++op) {
@@ -735,12 +784,11 @@ void autotune_fine(pbm_grid* g) {
                     a.dot_slot = -1;
                     float best = 3.4e38f;
                     int bestP = -1;
-                    // candidate -1: the two column passes
-                    for (int c = -1; c < fused_coarse_num_plans(); ++c) {
+                    for (int c = -2; c < last; ++c) {
                         for (int rep = 0; rep < 4; ++rep) {
                             if (rep == 1) PBM_CUDA(cudaEventRecord(e0, 0));
                             if (c < 0)
-                                cols_coarse<float>(g, k, L.A32, L.bord32, a, 0);
+                                cols_coarse<float>(g, k, L.A32, L.bord32, a, 0, c == -2);
                             else
                                 fused_coarse_f32(fused_coarse_plan(L.g, c), red_set(g, 0), L.g, L.A32, L.bord32,
                                                  &g->sc->salpha, a, 0);
@@ -787,7 +835,8 @@ ColArgs<T> make_coarse_args(const ColEnv& env, const Geom& G, const T* A, const 
 }
 
 template <class T>
-void cols_coarse(pbm_grid* g, int k, const T* A, const T* bord, const ApplyArgs& a, cudaStream_t st) {
+void cols_coarse(pbm_grid* g, int k, const T* A, const T* bord, const ApplyArgs& a, cudaStream_t st,
+                 bool per_element) {
     const Geom& G = g->L[k].g;
     ColEnv env = env_of(g, a.rset);
     if (g->L[k].qa) {
@@ -796,7 +845,10 @@ void cols_coarse(pbm_grid* g, int k, const T* A, const T* bord, const ApplyArgs&
     }
     int blocks = 0;
     const ColArgs<T> P = make_coarse_args<T>(env, G, A, a.x, &blocks);
-    launch_pdl(k_cols_coarse<T>, dim3(blocks), dim3(CB), 0, st, P);
+    if (per_element)
+        launch_pdl(k_cols_coarse_e<T>, dim3(unsigned((P.m + CB - 1) / CB)), dim3(CB), 0, st, P);
+    else
+        launch_pdl(k_cols_coarse<T>, dim3(blocks), dim3(CB), 0, st, P);
     PBM_LAUNCH("coarse column pass");
     node_pass<T>(env, G, a, 1, bord, &g->sc->salpha, nullptr, 0, 0, st);
 }
@@ -836,8 +888,8 @@ template void cols_fine<double>(pbm_grid*, const double*, const double*, const d
                                 const ApplyArgs&, cudaStream_t);
 template void cols_fine<float>(pbm_grid*, const float*, const float*, const float*, const float*, const ApplyArgs&,
                                cudaStream_t);
-template void cols_coarse<double>(pbm_grid*, int, const double*, const double*, const ApplyArgs&, cudaStream_t);
-template void cols_coarse<float>(pbm_grid*, int, const float*, const float*, const ApplyArgs&, cudaStream_t);
+template void cols_coarse<double>(pbm_grid*, int, const double*, const double*, const ApplyArgs&, cudaStream_t, bool);
+template void cols_coarse<float>(pbm_grid*, int, const float*, const float*, const ApplyArgs&, cudaStream_t, bool);
 template void cols_fine_env<double>(const ColEnv&, const Geom&, const KeHat&, const double*, const double*,
                                     const double*, const double*, const ApplyArgs&, cudaStream_t);
 

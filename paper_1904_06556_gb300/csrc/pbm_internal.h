@@ -300,8 +300,9 @@ struct pbm_grid {
     cudaGraphExec_t mr_graph[8] = {};
     int fineL[2][2] = {};                  // autotuned chunk length [fp32][op_s] of the fine column pass
     int fusedP[2] = {};                    // autotuned tile plan [op_s] of the single-pass FP32 operator
-    int coarseP[2][16] = {};               // autotuned FP32 coarse operator [op_s][level]: -1 two passes,
-                                           // >= 0 plan of the single pass
+    int coarseP[2][16] = {};               // autotuned FP32 coarse operator [op_s][level]: -1 two passes
+                                           // (eight threads per element), -2 two passes (a thread per
+                                           // element), >= 0 plan of the single pass
     int64_t mr_graph_kernels[8] = {};      // kernels in one iteration of each graph (launch counting)
     std::vector<int> prof_op;              // operator of every recorded launch
     // set-up streams: the coarsest factorisation and the Lanczos estimates of the coarse levels run
@@ -523,7 +524,8 @@ void cols_fine_env(const ColEnv& env, const Geom& G, const KeHat& kh, const T* w
 template <class T>
 void cols_fine(pbm_grid* g, const T* w, const T* d, const T* what, const T* u, const ApplyArgs& a, cudaStream_t st);
 template <class T>
-void cols_coarse(pbm_grid* g, int k, const T* A, const T* bord, const ApplyArgs& a, cudaStream_t st);
+void cols_coarse(pbm_grid* g, int k, const T* A, const T* bord, const ApplyArgs& a, cudaStream_t st,
+                 bool per_element = false);
 void launch_what_hat(pbm_grid* g, cudaStream_t st);
 // single-pass FP32 fine operator (fused.cu): tile plan of candidate `cand` for a grid (of the K or the S
 // operator), and the launch. The last plan is the tensor-core kernel (tc.cu).

@@ -287,6 +287,31 @@ def test_fused_fp32_coarse_levels_match_oracle_galerkin(pkg, dims, bc, levels, o
         if k < levels - 1:
             j, _ = G.apply_level_f32(k, op, "jacobi", dev(x, torch.float32), dev(b, torch.float32))
             assert close(host(j), xr + omega * (br - Ak @ xr) / Ak.diagonal()) < 1e-5, k
+    # every form of the coarse operator (two passes split by rows or per element, each single-pass plan) on
+    # every level that has one, element by element against the oracle's Galerkin matrix
+    tuned = G.info()["coarse_plan"][1 if op == "S" else 0]
+    assert len(tuned) == levels - 2
+    assert all(-2 <= p < pkg.fp32_coarse_plan_count() for p in tuned)
+    for k in range(1, levels - 1):
+        Ak = h.A[k]
+        x, b = rng.standard_normal(Ak.shape[0]), rng.standard_normal(Ak.shape[0])
+        xr, br = _f32(x), _f32(b)
+        omega = G.info()["omega"][k]
+        for plan in range(-2, pkg.fp32_coarse_plan_count()):
+            G.set_fp32_coarse_plan(op, k, plan)
+            assert G.info()["coarse_plan"][1 if op == "S" else 0][k - 1] == plan
+            y, dot = G.apply_level_f32(k, op, "apply", dev(x, torch.float32), dot=True)
+            y = host(y)
+            assert close(y, Ak @ xr) < 1e-5, (k, plan)
+            assert abs(dot - y @ xr) <= 1e-5 * np.abs(y * xr).sum(), (k, plan)
+            r, _ = G.apply_level_f32(k, op, "resid", dev(x, torch.float32), dev(b, torch.float32))
+            assert close(host(r), br - Ak @ xr) < 1e-5, (k, plan)
+            j, _ = G.apply_level_f32(k, op, "jacobi", dev(x, torch.float32), dev(b, torch.float32))
+            assert close(host(j), xr + omega * (br - Ak @ xr) / Ak.diagonal()) < 1e-5, (k, plan)
+        G.set_fp32_coarse_plan(op, k, tuned[k - 1])
+    for bad in ((0, -1), (levels - 1, -1), (1, -3), (1, pkg.fp32_coarse_plan_count())):
+        with pytest.raises(pkg.PbmError):
+            G.set_fp32_coarse_plan(op, *bad)
 
 
 # ------------------------------------------------------------------------------------------------
