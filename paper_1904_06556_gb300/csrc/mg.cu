@@ -57,25 +57,35 @@ __device__ __forceinline__ void restrict_body(const RestrictArgs<T>& P, unsigned
         const int I = int(cn - r * unsigned(nxc + 1));
         const int J = int(r % unsigned(nyc + 1));
         const int K = int(r / unsigned(nyc + 1));
-        T acc = T(0);   // accumulated in the vector type (no FP64 work per entry for FP32)
-        if (!node_fixed(support, nxc, nyc, nzc, I, J, K)) {
+        // the 27 fine values first (clamped, always valid addresses: the loads do not wait on each
+        // other), then the sum over the unmasked ones in a fixed order
+        const bool cfix = node_fixed(support, nxc, nyc, nzc, I, J, K);
+        T v[27];
+        bool ok[27];
 #pragma unroll
-            for (int dz = -1; dz <= 1; ++dz) {
-                const int kf = 2 * K + dz;
+        for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
-                for (int dy = -1; dy <= 1; ++dy) {
-                    const int jf = 2 * J + dy;
+            for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        const int if_ = 2 * I + dx;
-                        if (if_ < 0 || if_ > nxf || jf < 0 || jf > nyf || kf < 0 || kf > nzf) continue;
-                        if (node_fixed(support, nxf, nyf, nzf, if_, jf, kf)) continue;
-                        const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
-                        acc += w * rf[3 * (if_ + sxf * jf + sxyf * kf) + c];
-                    }
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int o = 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1);
+                    const int kf = 2 * K + dz, jf = 2 * J + dy, if_ = 2 * I + dx;
+                    const bool in = if_ >= 0 && if_ <= nxf && jf >= 0 && jf <= nyf && kf >= 0 && kf <= nzf;
+                    ok[o] = in && !cfix && !node_fixed(support, nxf, nyf, nzf, if_, jf, kf);
+                    const int ci = min(max(if_, 0), nxf), cj = min(max(jf, 0), nyf), ck = min(max(kf, 0), nzf);
+                    v[o] = rf[3 * (ci + sxf * cj + sxyf * ck) + c];
                 }
-            }
-        }
+        T acc = T(0);   // accumulated in the vector type (no FP64 work per entry for FP32)
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int o = 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1);
+                    const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
+                    if (ok[o]) acc += w * v[o];
+                }
         const T bv = T(scale) * acc;
         bc[t] = bv;
         if (xfirst) xfirst[t] = T(w_first) * (bv * idiag[t]);
@@ -141,17 +151,27 @@ __device__ __forceinline__ void prolong_body(const ProlongArgs<T>& P, unsigned b
         const int J = int(r % unsigned(nyf + 1));
         const int K = int(r / unsigned(nyf + 1));
         if (node_fixed(support, nxf, nyf, nzf, I, J, K)) continue;
-        const int i0 = I >> 1, i1 = (I + 1) >> 1, j0 = J >> 1, j1 = (J + 1) >> 1, k0 = K >> 1, k1 = (K + 1) >> 1;
+        // parents per direction: I / 2 for even I, (I - 1) / 2 and (I + 1) / 2 for odd I; every load
+        // first, then the sum in the order z, y, x ascending
+        const int pi[2] = {I >> 1, (I + 1) >> 1}, pj[2] = {J >> 1, (J + 1) >> 1}, pk[2] = {K >> 1, (K + 1) >> 1};
+        const bool oi = (I & 1) != 0, oj = (J & 1) != 0, ok_ = (K & 1) != 0;
+        const T xo = xf[t];
+        T v[8];
+        bool ok[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int bx = b & 1, by = (b >> 1) & 1, bz = b >> 2;
+            const int ic = pi[bx], jc = pj[by], kc = pk[bz];
+            ok[b] = (!bx || oi) && (!by || oj) && (!bz || ok_) && !node_fixed(support, nxc, nyc, nzc, ic, jc, kc);
+            v[b] = xc[3 * (ic + sxc * jc + sxyc * kc) + c];
+        }
         T acc = T(0);
-        for (int kc = k0; kc <= k1; ++kc)
-            for (int jc = j0; jc <= j1; ++jc)
-                for (int ic = i0; ic <= i1; ++ic) {
-                    if (node_fixed(support, nxc, nyc, nzc, ic, jc, kc)) continue;
-                    acc += xc[3 * (ic + sxc * jc + sxyc * kc) + c];
-                }
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            if (ok[b]) acc += v[b];
         const int nodd = (I & 1) + (J & 1) + (K & 1);
         const T w = T(__longlong_as_double(static_cast<long long>(1023 - nodd) << 52));  // 2^-nodd, exact
-        xf[t] += w * acc;
+        xf[t] = xo + w * acc;
     }
     if (with_alpha && blk == 0 && threadIdx.x == 0) {
         const int64_t nc = 3 * int64_t(nxc + 1) * (nyc + 1) * (nzc + 1);
