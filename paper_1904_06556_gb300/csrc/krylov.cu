@@ -70,6 +70,12 @@ void launch_cast(const void* src, bool src32, void* dst, bool dst32, int64_t n, 
 
 void vec_zero(void* p, size_t bytes, cudaStream_t st) { PBM_CUDA(cudaMemsetAsync(p, 0, bytes, st)); }
 
+// FP32 vectors whose base addresses are all 16-byte aligned are processed four entries per access
+template <class... P>
+__device__ __forceinline__ bool vec4_ok(const P*... p) {
+    return ((((uintptr_t)p) & 15u) | ...) == 0;
+}
+
 // x = omega D^{-1} b (idiag = D^{-1})
 template <class T>
 __device__ __forceinline__ void first_jacobi_body(const T* __restrict__ b, const T* __restrict__ idiag,
@@ -165,10 +171,33 @@ __device__ __forceinline__ void mr_lanczos2_body(const T* __restrict__ Az, T* __
     }
     __syncthreads();
     const T c1 = T(cs[0]), c2 = T(cs[1]), c3 = T(cs[2]);   // vector arithmetic in the vector type
-    for (int64_t i = blk * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(nblk) * blockDim.x) {
-        const T vc = v1[i];
-        v1[i] = c1 * Az[i] - c2 * vc - c3 * v0[i];
-        v0[i] = vc;
+    auto one = [&](T az, T v0i, T& vn, T& vo) {
+        const T vc = vn;
+        vn = c1 * az - c2 * vc - c3 * v0i;
+        vo = vc;
+    };
+    int64_t i0 = 0;
+    if constexpr (std::is_same<T, float>::value)
+    if (vec4_ok(Az, v0, v1)) {   // FP32: four entries per 16-byte access, the same arithmetic per entry
+        const int64_t n4 = n / 4;
+        for (int64_t q = blk * int64_t(blockDim.x) + threadIdx.x; q < n4; q += int64_t(nblk) * blockDim.x) {
+            const float4 a = reinterpret_cast<const float4*>(Az)[q];
+            const float4 p = reinterpret_cast<const float4*>(v0)[q];
+            float4 c = reinterpret_cast<const float4*>(v1)[q], o;
+            one(a.x, p.x, c.x, o.x);
+            one(a.y, p.y, c.y, o.y);
+            one(a.z, p.z, c.z, o.z);
+            one(a.w, p.w, c.w, o.w);
+            reinterpret_cast<float4*>(v1)[q] = c;
+            reinterpret_cast<float4*>(v0)[q] = o;
+        }
+        i0 = 4 * n4;
+    }
+    for (int64_t i = i0 + blk * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(nblk) * blockDim.x) {
+        T vn = v1[i], vo;
+        one(Az[i], v0[i], vn, vo);
+        v1[i] = vn;
+        v0[i] = vo;
     }
     if (blk == 0 && threadIdx.x == 0) mr[8] = cs[3];
 }
@@ -191,12 +220,41 @@ __device__ __forceinline__ void mr_update2_body(T* __restrict__ zc, const T* __r
     __syncthreads();
     const T e = T(mr[10]), f = T(mr[11]), step = T(mr[9]);
     const T ib = T(cs[0]), ir = T(cs[1]);
-    for (int64_t i = blk * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(nblk) * blockDim.x) {
-        const T dp = d1[i];
-        const T dn = (zc[i] * ib - e * d2[i] - f * dp) * ir;
-        d2[i] = dp;
-        d1[i] = dn;
-        x[i] = x[i] + step * dn;
+    // per entry: (d2, d1, x, z) <- (d1, dn, x + step dn, z_next), dn = (z / beta - e d2 - f d1) / r
+    auto one = [&](T z, T d2i, T d1i, T xi, T& o2, T& o1, T& ox) {
+        const T dn = (z * ib - e * d2i - f * d1i) * ir;
+        o2 = d1i;
+        o1 = dn;
+        ox = xi + step * dn;
+    };
+    int64_t i0 = 0;
+    if constexpr (std::is_same<T, float>::value)
+    if (vec4_ok(zc, zn, d1, d2, x)) {   // FP32: four entries per 16-byte access
+        const int64_t n4 = n / 4;
+        for (int64_t q = blk * int64_t(blockDim.x) + threadIdx.x; q < n4; q += int64_t(nblk) * blockDim.x) {
+            const float4 z = reinterpret_cast<const float4*>(zc)[q];
+            const float4 a2 = reinterpret_cast<const float4*>(d2)[q];
+            const float4 a1 = reinterpret_cast<const float4*>(d1)[q];
+            const float4 xv = reinterpret_cast<const float4*>(x)[q];
+            const float4 zz = reinterpret_cast<const float4*>(zn)[q];
+            float4 o2, o1, ox;
+            one(z.x, a2.x, a1.x, xv.x, o2.x, o1.x, ox.x);
+            one(z.y, a2.y, a1.y, xv.y, o2.y, o1.y, ox.y);
+            one(z.z, a2.z, a1.z, xv.z, o2.z, o1.z, ox.z);
+            one(z.w, a2.w, a1.w, xv.w, o2.w, o1.w, ox.w);
+            reinterpret_cast<float4*>(d2)[q] = o2;
+            reinterpret_cast<float4*>(d1)[q] = o1;
+            reinterpret_cast<float4*>(x)[q] = ox;
+            reinterpret_cast<float4*>(zc)[q] = zz;
+        }
+        i0 = 4 * n4;
+    }
+    for (int64_t i = i0 + blk * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(nblk) * blockDim.x) {
+        T o2, o1, ox;
+        one(zc[i], d2[i], d1[i], x[i], o2, o1, ox);
+        d2[i] = o2;
+        d1[i] = o1;
+        x[i] = ox;
         zc[i] = zn[i];
     }
 }

@@ -585,7 +585,20 @@ __device__ __forceinline__ void coarsest_solve_body(const CoarsestArgs<T>& P, un
     const int row = int((blk * blockDim.x + threadIdx.x) >> 5);
     if (row >= n_vec) return;
     double s = 0.0;
-    for (int c = lane; c < n_vec; c += 32) s += Inv[row * N + c] * double(b[c]);
+    // the lane's terms c = lane, lane + 32, ... in ascending order, eight loads of each operand ahead
+    for (int c0 = 0; c0 < n_vec; c0 += 256) {
+        double iv[8], bv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = c0 + 32 * u + lane;
+            const int cc = c < n_vec ? c : 0;
+            iv[u] = Inv[row * N + cc];
+            bv[u] = double(b[cc]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (c0 + 32 * u + lane < n_vec) s += iv[u] * bv[u];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) x[row] = T(s);
