@@ -620,7 +620,7 @@ def run_ip(args):
            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
            "data": "synthetic (seeded; strictly feasible interior point on the workload's grid)",
-           "config": dict(workload_desc(w, args.precision),
+           "config": dict(workload_desc(w, args.precision, args.smoother),
                           workload=f"{w.name}: {w.nx}x{w.ny}x{w.nz} Q1 hex {w.bc}, {args.precision}, one "
                                    f"interior-point Newton system (set-up, rhs, MG-MINRES, recovery)"),
            "solve": {"minres_iterations": last["info"]["iterations"], "true_relres": last["info"]["relres"],
@@ -659,7 +659,7 @@ def run_doc(args):
            "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64" if args.precision == "mixed" else "f64",
            "data": "synthetic (seeded; the paper's cantilever example, Section 6)",
-           "config": dict(workload_desc(w, args.precision),
+           "config": dict(workload_desc(w, args.precision, args.smoother),
                           workload=f"{w.name}: {w.nx}x{w.ny}x{w.nz} Q1 hex {w.bc}, {args.precision}, complete DOC "
                                    f"run (q 1/2, eps_DOC 1e-3, MINRES 1e-4)"),
            "doc": info}
@@ -706,7 +706,7 @@ def run_pbm(args):
            "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64" if args.precision == "mixed" else "f64",
            "data": "synthetic (seeded; the paper's cantilever example, Section 6)",
-           "config": dict(workload_desc(w, args.precision),
+           "config": dict(workload_desc(w, args.precision, args.smoother),
                           workload=f"{w.name}: {w.nx}x{w.ny}x{w.nz} Q1 hex {w.bc}, {args.precision}, complete PBM "
                                    f"run from the paper's initial point (eps_pbm 1e-5)"),
            "pbm": {k: info[k] for k in ("rc", "status", "outer", "newton", "minres", "gap_ratio", "compliance",

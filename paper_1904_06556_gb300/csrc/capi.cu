@@ -10,7 +10,6 @@
 
 namespace pbm {
 
-void upload_tri_tables();
 void setup_hierarchy(pbm_grid* g, bool op_s, cudaStream_t st);
 void vcycle(pbm_grid* g, int k, bool fp32, bool op_s, const void* b, void* x, int dot_slot, cudaStream_t st,
             bool first_done = false);
@@ -309,7 +308,6 @@ int pbm_create_grid(const pbm_grid_desc* d, pbm_grid** out) {
         for (int i = 0; i < 24; ++i)
             for (int j = i; j < 24; ++j) Gtri[c * NTRI + tri_index(i, j)] = g->G[c][i * 24 + j];
     }
-    upload_tri_tables();
     g->G_dev = (double*)dalloc(g, sizeof(double) * 8 * NTRI);
     PBM_CUDA(cudaMemcpy(g->G_dev, Gtri.data(), sizeof(double) * 8 * NTRI, cudaMemcpyHostToDevice));
     {

@@ -266,39 +266,45 @@ void launch_build_what(pbm_grid* g, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// level 1 element matrices: sum_c w_c G_c (+ d_c what_c what_c^T); one thread per (element, entry)
+// level 1 element matrices: sum_c w_c G_c (+ d_c what_c what_c^T); one thread per (coarse element E,
+// row i) forms the row's entries (i, j), j >= i: the children's weights and d_c what_i,c are loaded
+// (formed) once per thread, so every entry costs two FMAs per child and one load of what_j,c.
+// Warps hold 32 consecutive elements of one row: every load and store is coalesced.
 // ------------------------------------------------------------------------------------------------
-__constant__ int c_tri_i[NTRI];
-__constant__ int c_tri_j[NTRI];
-
 __global__ void k_build_level1(int nxf, int nyf, int nzf, const double* __restrict__ w, const double* __restrict__ d,
                                const double* __restrict__ what, const double* __restrict__ G, double* __restrict__ A) {
     const int nxc = nxf / 2, nyc = nyf / 2, nzc = nzf / 2;
     const int64_t mc = int64_t(nxc) * nyc * nzc, mf = int64_t(nxf) * nyf * nzf;
-    const int t = blockIdx.y;
-    const int ii = c_tri_i[t], jj = c_tri_j[t];
-    double Gc[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) Gc[c] = G[c * NTRI + t];
+    const int ii = blockIdx.y;
     for (int64_t E = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; E < mc; E += int64_t(gridDim.x) * blockDim.x) {
         const int I = int(E % nxc);
         const int J = int((E / nxc) % nyc);
         const int K = int(E / (int64_t(nxc) * nyc));
-        double acc = 0.0;
+        int64_t e[8];
+        double wc[8], dwi[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const int64_t e = (2 * I + (c & 1)) + int64_t(nxf) * ((2 * J + ((c >> 1) & 1)) + int64_t(nyf) * (2 * K + (c >> 2)));
-            acc += w[e] * Gc[c];
-            if (d) acc += d[e] * what[ii * mf + e] * what[jj * mf + e];
+            e[c] = (2 * I + (c & 1)) + int64_t(nxf) * ((2 * J + ((c >> 1) & 1)) + int64_t(nyf) * (2 * K + (c >> 2)));
+            wc[c] = w[e[c]];
+            dwi[c] = d ? d[e[c]] * what[ii * mf + e[c]] : 0.0;
         }
-        A[t * mc + E] = acc;
+        for (int jj = ii; jj < 24; ++jj) {
+            const int t = tri_index(ii, jj);
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                acc += wc[c] * G[c * NTRI + t];
+                if (d) acc += dwi[c] * what[jj * mf + e[c]];
+            }
+            A[t * mc + E] = acc;
+        }
     }
 }
 
 void launch_build_level1(pbm_grid* g, bool op_s, cudaStream_t st) {
     const Geom& F = g->L[0].g;
     const int64_t mc = g->L[1].g.m();
-    dim3 grid(unsigned(std::max<int64_t>(1, std::min<int64_t>((mc + 127) / 128, 64))), NTRI);
+    dim3 grid(unsigned(std::max<int64_t>(1, std::min<int64_t>((mc + 127) / 128, 1024))), 24);
     k_build_level1<<<grid, 128, 0, st>>>(F.nx, F.ny, F.nz, op_s ? g->w64 : g->rho, op_s ? g->d64 : nullptr, g->what, g->G_dev,
                                           g->L[1].A64);
     PBM_LAUNCH("build level1");
@@ -407,20 +413,6 @@ void launch_coarse_to_f32(pbm_grid* g, int k, cudaStream_t st) {
     Level& L = g->L[k];
     if (L.A32) launch_cast(L.A64, false, L.A32, true, int64_t(NTRI) * L.g.m(), st);
     if (L.bord32) launch_cast(L.bord64, false, L.bord32, true, L.g.n(), st);
-}
-
-void upload_tri_tables() {
-    static bool done = false;
-    if (done) return;
-    int ti[NTRI], tj[NTRI];
-    for (int i = 0; i < 24; ++i)
-        for (int j = i; j < 24; ++j) {
-            ti[tri_index(i, j)] = i;
-            tj[tri_index(i, j)] = j;
-        }
-    PBM_CUDA(cudaMemcpyToSymbol(c_tri_i, ti, sizeof(ti)));
-    PBM_CUDA(cudaMemcpyToSymbol(c_tri_j, tj, sizeof(tj)));
-    done = true;
 }
 
 // ------------------------------------------------------------------------------------------------

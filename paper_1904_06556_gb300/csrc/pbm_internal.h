@@ -308,7 +308,8 @@ struct pbm_grid {
     // set-up streams: the coarsest factorisation and the Lanczos estimates of the coarse levels run
     // beside the fine level's (created on first use)
     cudaStream_t side[16] = {};
-    cudaEvent_t side_ev[18] = {};          // [k]: level k's stream done, [16]: fork, [17]: Galerkin chain done
+    cudaEvent_t side_ev[19] = {};          // [k]: level k's stream done, [16]: fork, [17]: Galerkin chain done,
+                                           // [18]: fine-level border done
 };
 
 namespace pbm {

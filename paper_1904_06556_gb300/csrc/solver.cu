@@ -304,15 +304,25 @@ void setup_hierarchy(pbm_grid* g, bool op_s, cudaStream_t st) {
     const int steps = g->desc.lanczos_steps;
     if (steps * std::max(1, nl - 1) > 128) fail(PBM_EINVAL, "lanczos_steps x levels exceeds 128");
     if (nl > 16) fail(PBM_EINVAL, "more than 16 levels");
-    for (int i = 0; i < 18; ++i) {
+    for (int i = 0; i < 19; ++i) {
         if (i < 16 && !g->side[i]) PBM_CUDA(cudaStreamCreateWithFlags(&g->side[i], cudaStreamNonBlocking));
         if (!g->side_ev[i]) PBM_CUDA(cudaEventCreateWithFlags(&g->side_ev[i], cudaEventDisableTiming));
     }
-    // fine-level data: alpha border b_0 = -sum_i d_i K_i u, the tables of the Galerkin products and of
-    // the S pass, the Jacobi diagonal, and the FP32 copies of mixed grids
+    // The Galerkin chain of the coarse levels needs only the element weights (and, for S, the table
+    // of P_c^T K_e u_e), so it starts at once on side[1], beside the rest of the fine level's data on
+    // `st`: the alpha border b_0 = -sum_i d_i K_i u (the chain waits for it before restricting it), the
+    // W_e table of the S pass, the Jacobi diagonal and the FP32 copies of mixed grids.
+    cudaEvent_t fork = g->side_ev[16], chain = g->side_ev[17], border = g->side_ev[18];
+    PBM_CUDA(cudaEventRecord(fork, st));
+    const cudaStream_t sg = g->side[1];
+    if (nl >= 2) {
+        PBM_CUDA(cudaStreamWaitEvent(sg, fork, 0));
+        if (op_s) launch_build_what(g, sg);
+        launch_build_level1(g, op_s, sg);
+    }
     if (op_s) {
         launch_fine(g, false, g->d64, nullptr, nullptr, args(g->u64, F.bord64, EPI_APPLY), st);
-        launch_build_what(g, st);
+        PBM_CUDA(cudaEventRecord(border, st));
         launch_what_hat(g, st);
     }
     launch_diag(g, 0, op_s, st);
@@ -329,13 +339,11 @@ void setup_hierarchy(pbm_grid* g, bool op_s, cudaStream_t st) {
     // chain of the coarse levels on side[1], followed there by level 1's Lanczos; once the chain is
     // done, the coarsest factorisation on side[0] and the Lanczos of levels 2 .. nl - 2 on side[k].
     // Each stream has its own reduction set, vectors and slots; one synchronisation reads everything.
-    cudaEvent_t fork = g->side_ev[16], chain = g->side_ev[17];
-    PBM_CUDA(cudaEventRecord(fork, st));
     if (nl >= 2) {
-        const cudaStream_t sg = g->side[1];
-        PBM_CUDA(cudaStreamWaitEvent(sg, fork, 0));
-        launch_build_level1(g, op_s, sg);
-        if (op_s) launch_restrict(g, 0, false, F.bord64, g->L[1].bord64, false, -1.0, sg);
+        if (op_s) {
+            PBM_CUDA(cudaStreamWaitEvent(sg, border, 0));
+            launch_restrict(g, 0, false, F.bord64, g->L[1].bord64, false, -1.0, sg);
+        }
         for (int k = 1; k + 1 < nl; ++k) {
             launch_build_coarser(g, k, sg);
             if (op_s) launch_restrict(g, k, false, g->L[k].bord64, g->L[k + 1].bord64, false, 1.0, sg);
