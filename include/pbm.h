@@ -223,7 +223,9 @@ int pbm_set_density(pbm_grid* g, const double* rho_dev, void* stream);
  *   level 0: w_dev m element weights (NULL = the density set by pbm_set_density); x_dev, y_dev n.
  *   level k >= 1: w_dev must be NULL; x_dev, y_dev hold 3 (nx/2^k + 1)(ny/2^k + 1)(nz/2^k + 1)
  *   entries. If the K(rho) hierarchy is not current (no K solve or V-cycle since the last
- *   pbm_set_density, or an S hierarchy replaced it) it is built first, on `stream`.
+ *   pbm_set_density, or an S hierarchy replaced it) it is built first, on `stream`. (The set-up of
+ *   a PBM_MIXED grid builds its coarse operators in FP32, for the FP32 V-cycle; the first FP64 read
+ *   of a coarse level after a set-up builds the FP64 ones on `stream`.)
  * x and y must not overlap. FP64 throughout. Errors: PBM_EINVAL (level out of range, weights given
  * for a coarse level), PBM_ESTATE (no density set and no weights). */
 int pbm_apply_K(pbm_grid* g, const double* w_dev, const double* x_dev, double* y_dev, int level, void* stream);
@@ -246,9 +248,10 @@ int pbm_apply_K_f32(pbm_grid* g, const float* w_dev, const float* x_dev, float* 
 int pbm_apply_fine_f32(pbm_grid* g, int op, int epilogue, const float* x_dev, const float* b_dev, float* y_dev,
                        double* dot_host, void* stream);
 
-/* The same on level `level` of the current hierarchy (0 = fine; level >= 1: the FP32 copy of the
- * Galerkin operator A_level = P^T A_(level-1) P of Section 5.1, with the alpha border for S, and
- * that level's Jacobi weight and diagonal). Vectors have n_level (+ 1 for S) entries. Errors as
+/* The same on level `level` of the current hierarchy (0 = fine; level >= 1: the Galerkin operator
+ * A_level = P^T A_(level-1) P of Section 5.1 as the FP32 V-cycle applies it (built in FP32 from the
+ * FP32 copies of the weights and u), with the alpha border for S, and that level's Jacobi weight and
+ * diagonal). Vectors have n_level (+ 1 for S) entries. Errors as
  * above, and PBM_EINVAL for a level out of range. */
 int pbm_apply_level_f32(pbm_grid* g, int level, int op, int epilogue, const float* x_dev, const float* b_dev,
                         float* y_dev, double* dot_host, void* stream);
@@ -281,7 +284,9 @@ int pbm_set_fp32_coarse_plan(pbm_grid* g, int op, int level, int plan);
 
 /* Copies the Jacobi diagonal of level `level` of the current hierarchy (K or S, the last one set
  * up) into diag_dev: n_level + 1 FP64 entries (the last is the alpha entry of S, 1 for K);
- * supported dofs hold 1. Errors: PBM_EINVAL, PBM_ESTATE (no hierarchy). */
+ * supported dofs hold 1. On a PBM_MIXED grid a coarse level's FP64 diagonal comes from its FP64
+ * matrices, built by the first such call after a set-up (on `stream`). Errors: PBM_EINVAL,
+ * PBM_ESTATE (no hierarchy). */
 int pbm_get_diag(const pbm_grid* g, int level, double* diag_dev, void* stream);
 
 /* Sets the Newton state and builds what S needs (Section 3.2): the per-element factors rho', rho'',

@@ -277,13 +277,26 @@ void launch_coarse(pbm_grid* g, int k, bool fp32, const ApplyArgs& a, cudaStream
         cols_coarse<double>(g, k, L.A64, L.bord64, a, st);
 }
 
-void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st, int rset) {
+// FP64 Jacobi diagonal of coarse level k from its FP64 matrices into diag64
+static void coarse_diag64(pbm_grid* g, int k, bool op_s, cudaStream_t st, int rset) {
     Level& L = g->L[k];
     auto P = base_params<double>(g, k, rset);
     P.with_alpha = 1;
     P.y = L.diag64;
-    P.s_alpha = g->s_alpha;
+    P.s_alpha = op_s ? g->s_alpha : 1.0;
+    P.A = L.A64;
+    run<double, K_COARSE_DIAG>(g, k, P, st, "coarse diag");
+}
+
+// from32: a coarse level of a mixed grid whose set-up built only the FP32 matrices (the diagonal is
+// summed in FP32 and widened)
+void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st, int rset, bool from32) {
+    Level& L = g->L[k];
     if (k == 0) {
+        auto P = base_params<double>(g, k, rset);
+        P.with_alpha = 1;
+        P.y = L.diag64;
+        P.s_alpha = g->s_alpha;
         P.w = op_s ? g->w64 : g->rho;
         if (op_s) {
             P.d = g->d64;
@@ -292,13 +305,30 @@ void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st, int rset) {
         } else {
             run<double, K_FINE_DIAG_K>(g, 0, P, st, "fine diag K");
         }
+    } else if (from32) {
+        auto P = base_params<float>(g, k, rset);
+        P.with_alpha = 1;
+        P.y = L.t32;
+        P.s_alpha = op_s ? g->s_alpha : 1.0;
+        P.A = L.A32;
+        run<float, K_COARSE_DIAG>(g, k, P, st, "coarse diag");
+        launch_cast(L.t32, true, L.diag64, false, L.g.n() + 1, st);
     } else {
-        P.A = L.A64;
-        if (!op_s) P.s_alpha = 1.0;
-        run<double, K_COARSE_DIAG>(g, k, P, st, "coarse diag");
+        coarse_diag64(g, k, op_s, st, rset);
     }
     launch_inverse(L.diag64, L.idiag64, L.g.n() + 1, st);
     if (L.idiag32) launch_cast(L.idiag64, false, L.idiag32, true, L.g.n() + 1, st);
+}
+
+void ensure_coarse64(pbm_grid* g, cudaStream_t st) {
+    if (g->desc.precision != PBM_MIXED || g->coarse64_ready || g->levels < 2 || g->op_ready == 0) return;
+    const bool op_s = g->op_ready == 2;
+    if (op_s) launch_build_what(g, st, false);
+    launch_build_level1(g, op_s, st, false);
+    for (int k = 1; k + 1 < g->levels; ++k) launch_build_coarser(g, k, st, false);
+    // the FP64 diagonals only: the FP32 smoother keeps the weights and inverse diagonals of its set-up
+    for (int k = 1; k < g->levels; ++k) coarse_diag64(g, k, op_s, st, 0);
+    g->coarse64_ready = true;
 }
 
 // ------------------------------------------------------------------------------------------------

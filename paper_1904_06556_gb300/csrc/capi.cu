@@ -310,6 +310,11 @@ int pbm_create_grid(const pbm_grid_desc* d, pbm_grid** out) {
     }
     g->G_dev = (double*)dalloc(g, sizeof(double) * 8 * NTRI);
     PBM_CUDA(cudaMemcpy(g->G_dev, Gtri.data(), sizeof(double) * 8 * NTRI, cudaMemcpyHostToDevice));
+    if (g->desc.precision == PBM_MIXED) {
+        std::vector<float> G32(Gtri.begin(), Gtri.end());
+        g->G32 = (float*)dalloc(g, sizeof(float) * 8 * NTRI);
+        PBM_CUDA(cudaMemcpy(g->G32, G32.data(), sizeof(float) * 8 * NTRI, cudaMemcpyHostToDevice));
+    }
     {
         std::vector<float> B;
         tc_build(g->Ke, B, g->tc.terms, g->tc.scale);
@@ -425,6 +430,7 @@ int pbm_destroy_grid(pbm_grid* g) {
         dfree(L.t32);
     }
     dfree(g->G_dev);
+    dfree(g->G32);
     dfree(g->tcB);
     dfree(g->rho);
     dfree(g->w64);
@@ -594,6 +600,7 @@ int pbm_apply_K(pbm_grid* g, const double* w_dev, const double* x_dev, double* y
     } else {
         // the Galerkin chain of K(rho) (Section 5.1): built here if no K solve or V-cycle has built it
         if (g->op_ready != 1) setup_hierarchy(g, false, st);
+        ensure_coarse64(g, st);
         launch_coarse(g, level, false, a, st);
     }
     PBM_CATCH
@@ -675,6 +682,7 @@ int pbm_get_diag(const pbm_grid* g, int level, double* diag_dev, void* stream) {
     if (g->op_ready == 0) fail(PBM_ESTATE, "no hierarchy has been set up");
     set_device(const_cast<pbm_grid*>(g));
     const Level& L = g->L[level];
+    if (level >= 1) ensure_coarse64(const_cast<pbm_grid*>(g), S(stream));
     PBM_CUDA(cudaMemcpyAsync(diag_dev, L.diag64, sizeof(double) * (L.g.n() + 1), cudaMemcpyDeviceToDevice,
                              S(stream)));
     PBM_CATCH

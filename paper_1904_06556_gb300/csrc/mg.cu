@@ -23,10 +23,12 @@ __host__ __device__ inline double wt1(int A, int s) {
     if (s == 0) return A == 0 ? 1.0 : 0.0;
     return A == 1 ? 1.0 : 0.0;
 }
-// P_c[a][A]: child c, child-local node a, coarse-local node A
-__host__ __device__ inline double pc_weight(int c, int a, int A) {
-    double w = 1.0;
-    for (int k = 0; k < 3; ++k) w *= wt1((A >> k) & 1, ((c >> k) & 1) + ((a >> k) & 1));
+// P_c[a][A]: child c, child-local node a, coarse-local node A (a product of 0, 1/2 and 1: exact in
+// either precision)
+template <class T = double>
+__host__ __device__ inline T pc_weight(int c, int a, int A) {
+    T w = T(1);
+    for (int k = 0; k < 3; ++k) w *= T(wt1((A >> k) & 1, ((c >> k) & 1) + ((a >> k) & 1)));
     return w;
 }
 
@@ -209,8 +211,9 @@ void launch_prolong_add(pbm_grid* g, int k, bool fp32, const void* xc, void* xf,
 // ------------------------------------------------------------------------------------------------
 // what[i][e] = (P_c^T K_e u_e)[i] for every fine element e (child c = parities of its indices)
 // ------------------------------------------------------------------------------------------------
-__global__ void k_build_what(int nx, int ny, int nz, int support, const double* __restrict__ u,
-                             double* __restrict__ what, KeHatT<double> K) {
+template <class T>
+__global__ void k_build_what(int nx, int ny, int nz, int support, const T* __restrict__ u, T* __restrict__ what,
+                             KeHatT<T> K) {
     const int64_t m = int64_t(nx) * ny * nz;
     const int64_t sxn = nx + 1, sxy = int64_t(nx + 1) * (ny + 1);
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m; e += int64_t(gridDim.x) * blockDim.x) {
@@ -218,14 +221,14 @@ __global__ void k_build_what(int nx, int ny, int nz, int support, const double* 
         const int j = int((e / nx) % ny);
         const int k = int(e / (int64_t(nx) * ny));
         const int c = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
-        double U[3][8], W[3][8];
+        T U[3][8], W[3][8];
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
             const int ii = i + (a & 1), jj = j + ((a >> 1) & 1), kk = k + ((a >> 2) & 1);
             const bool fx = node_fixed(support, nx, ny, nz, ii, jj, kk);
             const int64_t nd = 3 * (ii + sxn * jj + sxy * kk);
 #pragma unroll
-            for (int cc = 0; cc < 3; ++cc) U[cc][a] = fx ? 0.0 : u[nd + cc];
+            for (int cc = 0; cc < 3; ++cc) U[cc][a] = fx ? T(0) : u[nd + cc];
         }
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) wht_fwd(U[cc]);
@@ -235,10 +238,10 @@ __global__ void k_build_what(int nx, int ny, int nz, int support, const double* 
         // W[cc][a] = (K_e u_e)[3a + cc]; project with P_c^T
 #pragma unroll
         for (int A = 0; A < 8; ++A) {
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+            T s0 = T(0), s1 = T(0), s2 = T(0);
 #pragma unroll
             for (int a = 0; a < 8; ++a) {
-                const double p = pc_weight(c, a, A);
+                const T p = pc_weight<T>(c, a, A);
                 s0 += p * W[0][a];
                 s1 += p * W[1][a];
                 s2 += p * W[2][a];
@@ -250,18 +253,31 @@ __global__ void k_build_what(int nx, int ny, int nz, int support, const double* 
     }
 }
 
-void launch_build_what(pbm_grid* g, cudaStream_t st) {
+// fp32: the table in FP32 from the FP32 copy of u, into the first half of the FP64 table's buffer
+// (mixed grids: it only feeds the FP32 Galerkin chain of the set-up)
+void launch_build_what(pbm_grid* g, cudaStream_t st, bool fp32) {
     const Geom& G = g->L[0].g;
-    KeHatT<double> K;
-    for (int c = 0; c < 3; ++c)
-        for (int q = 0; q < 8; ++q) K.dg[c][q] = g->kehat.dg[c][q];
-    for (int b = 0; b < 2; ++b) {
-        K.lam4[b] = g->kehat.lam4[b];
-        K.mu4[b] = g->kehat.mu4[b];
-    }
     const int64_t m = G.m();
     const int blocks = int(std::min<int64_t>((m + 127) / 128, num_sms() * 16));
-    k_build_what<<<blocks, 128, 0, st>>>(G.nx, G.ny, G.nz, G.support, g->u64, g->what, K);
+    if (fp32) {
+        KeHatT<float> K;
+        for (int c = 0; c < 3; ++c)
+            for (int q = 0; q < 8; ++q) K.dg[c][q] = float(g->kehat.dg[c][q]);
+        for (int b = 0; b < 2; ++b) {
+            K.lam4[b] = float(g->kehat.lam4[b]);
+            K.mu4[b] = float(g->kehat.mu4[b]);
+        }
+        k_build_what<float><<<blocks, 128, 0, st>>>(G.nx, G.ny, G.nz, G.support, g->u32, (float*)g->what, K);
+    } else {
+        KeHatT<double> K;
+        for (int c = 0; c < 3; ++c)
+            for (int q = 0; q < 8; ++q) K.dg[c][q] = g->kehat.dg[c][q];
+        for (int b = 0; b < 2; ++b) {
+            K.lam4[b] = g->kehat.lam4[b];
+            K.mu4[b] = g->kehat.mu4[b];
+        }
+        k_build_what<double><<<blocks, 128, 0, st>>>(G.nx, G.ny, G.nz, G.support, g->u64, g->what, K);
+    }
     PBM_LAUNCH("build what");
 }
 
@@ -271,8 +287,9 @@ void launch_build_what(pbm_grid* g, cudaStream_t st) {
 // (formed) once per thread, so every entry costs two FMAs per child and one load of what_j,c.
 // Warps hold 32 consecutive elements of one row: every load and store is coalesced.
 // ------------------------------------------------------------------------------------------------
-__global__ void k_build_level1(int nxf, int nyf, int nzf, const double* __restrict__ w, const double* __restrict__ d,
-                               const double* __restrict__ what, const double* __restrict__ G, double* __restrict__ A) {
+template <class T>
+__global__ void k_build_level1(int nxf, int nyf, int nzf, const T* __restrict__ w, const T* __restrict__ d,
+                               const T* __restrict__ what, const T* __restrict__ G, T* __restrict__ A) {
     const int nxc = nxf / 2, nyc = nyf / 2, nzc = nzf / 2;
     const int64_t mc = int64_t(nxc) * nyc * nzc, mf = int64_t(nxf) * nyf * nzf;
     const int ii = blockIdx.y;
@@ -281,16 +298,16 @@ __global__ void k_build_level1(int nxf, int nyf, int nzf, const double* __restri
         const int J = int((E / nxc) % nyc);
         const int K = int(E / (int64_t(nxc) * nyc));
         int64_t e[8];
-        double wc[8], dwi[8];
+        T wc[8], dwi[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             e[c] = (2 * I + (c & 1)) + int64_t(nxf) * ((2 * J + ((c >> 1) & 1)) + int64_t(nyf) * (2 * K + (c >> 2)));
             wc[c] = w[e[c]];
-            dwi[c] = d ? d[e[c]] * what[ii * mf + e[c]] : 0.0;
+            dwi[c] = d ? d[e[c]] * what[ii * mf + e[c]] : T(0);
         }
         for (int jj = ii; jj < 24; ++jj) {
             const int t = tri_index(ii, jj);
-            double acc = 0.0;
+            T acc = T(0);
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 acc += wc[c] * G[c * NTRI + t];
@@ -301,12 +318,18 @@ __global__ void k_build_level1(int nxf, int nyf, int nzf, const double* __restri
     }
 }
 
-void launch_build_level1(pbm_grid* g, bool op_s, cudaStream_t st) {
+// fp32 (mixed grids): from the FP32 weights and table into the FP32 matrices the V-cycle applies
+void launch_build_level1(pbm_grid* g, bool op_s, cudaStream_t st, bool fp32) {
     const Geom& F = g->L[0].g;
     const int64_t mc = g->L[1].g.m();
     dim3 grid(unsigned(std::max<int64_t>(1, std::min<int64_t>((mc + 127) / 128, 1024))), 24);
-    k_build_level1<<<grid, 128, 0, st>>>(F.nx, F.ny, F.nz, op_s ? g->w64 : g->rho, op_s ? g->d64 : nullptr, g->what, g->G_dev,
-                                          g->L[1].A64);
+    if (fp32)
+        k_build_level1<float><<<grid, 128, 0, st>>>(F.nx, F.ny, F.nz, op_s ? g->w32 : g->rho32,
+                                                    op_s ? g->d32 : nullptr, (const float*)g->what, g->G32,
+                                                    g->L[1].A32);
+    else
+        k_build_level1<double><<<grid, 128, 0, st>>>(F.nx, F.ny, F.nz, op_s ? g->w64 : g->rho,
+                                                     op_s ? g->d64 : nullptr, g->what, g->G_dev, g->L[1].A64);
     PBM_LAUNCH("build level1");
 }
 
@@ -322,14 +345,16 @@ void launch_build_level1(pbm_grid* g, bool op_s, cudaStream_t st) {
 // entry (r, s), r <= s, belongs to block (r % 3, s % 3) if r % 3 <= s % 3, else to the transposed
 // position of block (s % 3, r % 3)).
 // ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ void interp_pair(double& v0, double& v1, int cb) {
-    const double h = 0.5 * (cb ? v0 : v1);
-    const double sum = (cb ? v1 : v0) + h;
+template <class T>
+__device__ __forceinline__ void interp_pair(T& v0, T& v1, int cb) {
+    const T h = T(0.5) * (cb ? v0 : v1);
+    const T sum = (cb ? v1 : v0) + h;
     v0 = cb ? h : sum;
     v1 = cb ? sum : h;
 }
 
-__device__ __forceinline__ void interp8(double (&v)[8], int c) {
+template <class T>
+__device__ __forceinline__ void interp8(T (&v)[8], int c) {
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         const int cb = (c >> ax) & 1;
@@ -339,8 +364,9 @@ __device__ __forceinline__ void interp8(double (&v)[8], int c) {
     }
 }
 
-__global__ void __launch_bounds__(128) k_build_coarser(int nxf, int nyf, int nzf, const double* __restrict__ Af,
-                                                       double* __restrict__ Ac) {
+template <class T>
+__global__ void __launch_bounds__(128) k_build_coarser(int nxf, int nyf, int nzf, const T* __restrict__ Af,
+                                                       T* __restrict__ Ac) {
     const int nxc = nxf / 2, nyc = nyf / 2, nzc = nzf / 2;
     const int64_t mc = int64_t(nxc) * nyc * nzc, mf = int64_t(nxf) * nyf * nzf;
     const int64_t tid = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -354,7 +380,7 @@ __global__ void __launch_bounds__(128) k_build_coarser(int nxf, int nyf, int nzf
     const int bj = blk < 3 ? blk : (blk < 5 ? blk - 2 : 2);
     const int ex = int(E % nxc), ey = int((E / nxc) % nyc), ez = int(E / (int64_t(nxc) * nyc));
     const int64_t e = (2 * ex + (c & 1)) + int64_t(nxf) * ((2 * ey + ((c >> 1) & 1)) + int64_t(nyf) * (2 * ez + (c >> 2)));
-    double M[8][8];
+    T M[8][8];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
@@ -368,7 +394,7 @@ __global__ void __launch_bounds__(128) k_build_coarser(int nxf, int nyf, int nzf
     for (int a = 0; a < 8; ++a) interp8(M[a], c);
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
-        double col[8];
+        T col[8];
 #pragma unroll
         for (int a = 0; a < 8; ++a) col[a] = M[a][b];
         interp8(col, c);
@@ -380,7 +406,7 @@ __global__ void __launch_bounds__(128) k_build_coarser(int nxf, int nyf, int nzf
     for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
-            double v = M[a][b];
+            T v = M[a][b];
             v += __shfl_xor_sync(0xffffffffu, v, 1, 8);
             v += __shfl_xor_sync(0xffffffffu, v, 2, 8);
             v += __shfl_xor_sync(0xffffffffu, v, 4, 8);
@@ -401,18 +427,29 @@ __global__ void __launch_bounds__(128) k_build_coarser(int nxf, int nyf, int nzf
     }
 }
 
-void launch_build_coarser(pbm_grid* g, int k, cudaStream_t st) {
+void launch_build_coarser(pbm_grid* g, int k, cudaStream_t st, bool fp32) {
     const Geom& F = g->L[k].g;
     const int64_t mc = g->L[k + 1].g.m();
-    const int64_t threads = mc * 48;
-    k_build_coarser<<<int((threads + 127) / 128), 128, 0, st>>>(F.nx, F.ny, F.nz, g->L[k].A64, g->L[k + 1].A64);
+    const int blocks = int((mc * 48 + 127) / 128);
+    if (fp32)
+        k_build_coarser<float><<<blocks, 128, 0, st>>>(F.nx, F.ny, F.nz, g->L[k].A32, g->L[k + 1].A32);
+    else
+        k_build_coarser<double><<<blocks, 128, 0, st>>>(F.nx, F.ny, F.nz, g->L[k].A64, g->L[k + 1].A64);
     PBM_LAUNCH("build coarser");
 }
 
-void launch_coarse_to_f32(pbm_grid* g, int k, cudaStream_t st) {
+// FP32 copies of level k's alpha border and, when built in FP64, its matrices (mixed grids)
+void launch_coarse_to_f32(pbm_grid* g, int k, cudaStream_t st, bool matrices) {
     Level& L = g->L[k];
-    if (L.A32) launch_cast(L.A64, false, L.A32, true, int64_t(NTRI) * L.g.m(), st);
+    if (matrices && L.A32) launch_cast(L.A64, false, L.A32, true, int64_t(NTRI) * L.g.m(), st);
     if (L.bord32) launch_cast(L.bord64, false, L.bord32, true, L.g.n(), st);
+}
+
+// FP64 matrices of level k from its FP32 ones (the coarsest level of a mixed grid, for its FP64
+// Cholesky factorisation: the factor then inverts exactly the matrix the FP32 V-cycle restricts to)
+void launch_coarse_to_f64(pbm_grid* g, int k, cudaStream_t st) {
+    Level& L = g->L[k];
+    launch_cast(L.A32, true, L.A64, false, int64_t(NTRI) * L.g.m(), st);
 }
 
 // ------------------------------------------------------------------------------------------------

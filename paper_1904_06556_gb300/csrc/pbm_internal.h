@@ -245,6 +245,7 @@ struct pbm_grid {
     double Kdiag;                     // K_e[i][i] (all equal for the isotropic cube)
     double G[8][576];                 // P_c^T K_e P_c for the 8 children (coarse local dofs)
     double* G_dev = nullptr;          // 8 x NTRI upper triangles, [c][t]
+    float* G32 = nullptr;             // the same rounded to FP32, for the FP32 Galerkin chain of mixed grids
     float* tcB = nullptr;             // element matrix as the tensor-core operand (2 x 1024 floats)
     pbm::TcMatrix tc;
     // fine-level element data
@@ -300,6 +301,8 @@ struct pbm_grid {
     cudaGraphExec_t mr_graph[8] = {};
     int fineL[2][2] = {};                  // autotuned chunk length [fp32][op_s] of the fine column pass
     int fusedP[2] = {};                    // autotuned tile plan [op_s] of the single-pass FP32 operator
+    bool coarse64_ready = false;           // FP64 coarse matrices and diagonals current (mixed grids build
+                                           // them on first use, ensure_coarse64)
     int coarseP[2][16] = {};               // autotuned FP32 coarse operator [op_s][level]: -1 two passes
                                            // (eight threads per element), -2 two passes (a thread per
                                            // element), >= 0 plan of the single pass
@@ -365,7 +368,7 @@ void level_apply(pbm_grid* g, int k, bool fp32, bool op_s, const ApplyArgs& a0, 
 // coarse level k >= 1: explicit element matrices (+ border for S)
 void launch_coarse(pbm_grid* g, int k, bool fp32, const ApplyArgs& a, cudaStream_t st);
 // Jacobi diagonal of a level (S or K), written to L[k].diag64 / diag32 (n + 1, last = alpha)
-void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st, int rset = 0);
+void launch_diag(pbm_grid* g, int k, bool op_s, cudaStream_t st, int rset = 0, bool from32 = false);
 // ------------------------------------------------------------------------------------------------
 // batched launches: one launch covers several systems (grid handles); first[s] is the first CTA of
 // system s (first[nsys] = total CTAs), sc[s] its scalar block; flags[1] == 0 marks a system whose
@@ -578,10 +581,14 @@ void prof_fold(pbm_grid* g);
 void launch_restrict(pbm_grid* g, int k, bool fp32, const void* rf, void* bc, bool with_alpha, double scale,
                      cudaStream_t st, void* xfirst = nullptr);
 void launch_prolong_add(pbm_grid* g, int k, bool fp32, const void* xc, void* xf, bool with_alpha, cudaStream_t st);
-void launch_build_what(pbm_grid* g, cudaStream_t st);
-void launch_build_level1(pbm_grid* g, bool op_s, cudaStream_t st);
-void launch_build_coarser(pbm_grid* g, int k, cudaStream_t st);
-void launch_coarse_to_f32(pbm_grid* g, int k, cudaStream_t st);
+void launch_build_what(pbm_grid* g, cudaStream_t st, bool fp32);
+void launch_build_level1(pbm_grid* g, bool op_s, cudaStream_t st, bool fp32);
+void launch_build_coarser(pbm_grid* g, int k, cudaStream_t st, bool fp32);
+void launch_coarse_to_f32(pbm_grid* g, int k, cudaStream_t st, bool matrices);
+void launch_coarse_to_f64(pbm_grid* g, int k, cudaStream_t st);
+// the FP64 Galerkin matrices and Jacobi diagonals of the coarse levels of a mixed grid (whose set-up
+// builds them in FP32), built on first use by the calls that read them in FP64
+void ensure_coarse64(pbm_grid* g, cudaStream_t st);
 void build_coarsest(pbm_grid* g, bool op_s, cudaStream_t st);
 void launch_coarsest_solve(pbm_grid* g, bool fp32, const void* b, void* x, bool with_alpha, cudaStream_t st);
 

@@ -311,21 +311,9 @@ void setup_hierarchy(pbm_grid* g, bool op_s, cudaStream_t st) {
     // The Galerkin chain of the coarse levels needs only the element weights (and, for S, the table
     // of P_c^T K_e u_e), so it starts at once on side[1], beside the rest of the fine level's data on
     // `st`: the alpha border b_0 = -sum_i d_i K_i u (the chain waits for it before restricting it), the
-    // W_e table of the S pass, the Jacobi diagonal and the FP32 copies of mixed grids.
-    cudaEvent_t fork = g->side_ev[16], chain = g->side_ev[17], border = g->side_ev[18];
-    PBM_CUDA(cudaEventRecord(fork, st));
-    const cudaStream_t sg = g->side[1];
-    if (nl >= 2) {
-        PBM_CUDA(cudaStreamWaitEvent(sg, fork, 0));
-        if (op_s) launch_build_what(g, sg);
-        launch_build_level1(g, op_s, sg);
-    }
-    if (op_s) {
-        launch_fine(g, false, g->d64, nullptr, nullptr, args(g->u64, F.bord64, EPI_APPLY), st);
-        PBM_CUDA(cudaEventRecord(border, st));
-        launch_what_hat(g, st);
-    }
-    launch_diag(g, 0, op_s, st);
+    // W_e table of the S pass and the Jacobi diagonal. Mixed grids build the chain in FP32 from the
+    // FP32 copies of the weights and u (made first): it only feeds the FP32 V-cycle, and the FP64
+    // matrices are built when a call reads them (ensure_coarse64).
     if (mixed) {
         if (op_s) {
             launch_cast(g->w64, false, g->w32, true, F.g.m(), st);
@@ -335,6 +323,21 @@ void setup_hierarchy(pbm_grid* g, bool op_s, cudaStream_t st) {
             launch_cast(g->rho, false, g->rho32, true, F.g.m(), st);
         }
     }
+    g->coarse64_ready = !mixed;
+    cudaEvent_t fork = g->side_ev[16], chain = g->side_ev[17], border = g->side_ev[18];
+    PBM_CUDA(cudaEventRecord(fork, st));
+    const cudaStream_t sg = g->side[1];
+    if (nl >= 2) {
+        PBM_CUDA(cudaStreamWaitEvent(sg, fork, 0));
+        if (op_s) launch_build_what(g, sg, mixed);
+        launch_build_level1(g, op_s, sg, mixed);
+    }
+    if (op_s) {
+        launch_fine(g, false, g->d64, nullptr, nullptr, args(g->u64, F.bord64, EPI_APPLY), st);
+        PBM_CUDA(cudaEventRecord(border, st));
+        launch_what_hat(g, st);
+    }
+    launch_diag(g, 0, op_s, st);
     // From here three kinds of work overlap: the fine level's Lanczos estimate on `st`; the Galerkin
     // chain of the coarse levels on side[1], followed there by level 1's Lanczos; once the chain is
     // done, the coarsest factorisation on side[0] and the Lanczos of levels 2 .. nl - 2 on side[k].
@@ -345,12 +348,14 @@ void setup_hierarchy(pbm_grid* g, bool op_s, cudaStream_t st) {
             launch_restrict(g, 0, false, F.bord64, g->L[1].bord64, false, -1.0, sg);
         }
         for (int k = 1; k + 1 < nl; ++k) {
-            launch_build_coarser(g, k, sg);
+            launch_build_coarser(g, k, sg, mixed);
             if (op_s) launch_restrict(g, k, false, g->L[k].bord64, g->L[k + 1].bord64, false, 1.0, sg);
         }
-        for (int k = 1; k < nl; ++k) launch_diag(g, k, op_s, sg, 1);
-        if (mixed)
-            for (int k = 1; k < nl; ++k) launch_coarse_to_f32(g, k, sg);
+        for (int k = 1; k < nl; ++k) launch_diag(g, k, op_s, sg, 1, mixed);
+        if (mixed) {
+            for (int k = 1; k < nl; ++k) launch_coarse_to_f32(g, k, sg, false);
+            launch_coarse_to_f64(g, nl - 1, sg);   // the coarsest level's FP64 factorisation
+        }
         PBM_CUDA(cudaEventRecord(chain, sg));
         PBM_CUDA(cudaStreamWaitEvent(g->side[0], chain, 0));
         build_coarsest(g, op_s, g->side[0]);
