@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(32 * BY) k_march(MarchParams<T> P) {
     __threadfence();
     double sa = 0.0, sz = 0.0;
     const int tid = tx + BX * ty;
-    for (int i = tid; i < nblk; i += NT) sa += ((volatile double*)P.partials)[i];
+    sa = l2_strided_sum(P.partials, nblk, tid, NT);
     block_sum2<NT>(sa, sz, sred);
     if (tid == 0) {
         *P.counter = 0u;

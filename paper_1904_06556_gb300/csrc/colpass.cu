@@ -445,12 +445,19 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
     __threadfence();
     // every thread of the last CTA sums a fixed strided subset; the CTA sum has a fixed tree order
     double td = 0.0, ta = 0.0;
-    for (int q = threadIdx.x; q < int(nblk); q += NB2) {
-        td += ((volatile double*)P.partials)[q];
-        ta += ((volatile double*)P.partials)[nblk + q];
+    td = l2_strided_sum(P.partials, int(nblk), threadIdx.x, NB2);
+    ta = l2_strided_sum(P.partials + nblk, int(nblk), threadIdx.x, NB2);
+    if (P.apart) {
+        // continues this thread's alpha share in the same order
+        for (int q0 = threadIdx.x; q0 < P.napart; q0 += 8 * NB2) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = q0 + u * NB2 < P.napart ? __ldcg(P.apart + q0 + u * NB2) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (q0 + u * NB2 < P.napart) ta += v[u];
+        }
     }
-    if (P.apart)
-        for (int q = threadIdx.x; q < P.napart; q += NB2) ta += ((volatile const double*)P.apart)[q];
     __syncthreads();
     double sd = cta_sum1<NB2>(td, sh);
     __syncthreads();

@@ -375,10 +375,8 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_f32(FusedArgs P) {
     if (!s_last) return;
     __threadfence();
     double td = 0.0, ta = 0.0;
-    for (int q = t; q < int(nblk); q += NT) {
-        td += ((volatile double*)P.partials)[q];
-        ta += ((volatile double*)P.partials)[nblk + q];
-    }
+    td = l2_strided_sum(P.partials, int(nblk), t, NT);
+    ta = l2_strided_sum(P.partials + nblk, int(nblk), t, NT);
     double sd = fused_cta_sum<NT>(td, sred);
     const double sa = fused_cta_sum<NT>(ta, sred);
     if (t != 0) return;
@@ -654,10 +652,8 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
     if (!s_last) return;
     __threadfence();
     double td = 0.0, ta = 0.0;
-    for (int i = t; i < int(nblk); i += NT) {
-        td += ((volatile double*)P.partials)[i];
-        ta += ((volatile double*)P.partials)[nblk + i];
-    }
+    td = l2_strided_sum(P.partials, int(nblk), t, NT);
+    ta = l2_strided_sum(P.partials + nblk, int(nblk), t, NT);
     double sd = fused_cta_sum<NT>(td, sred);
     const double sa = fused_cta_sum<NT>(ta, sred);
     if (t != 0) return;

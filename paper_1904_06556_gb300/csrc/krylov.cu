@@ -42,7 +42,7 @@ __device__ bool finish_sum(double part, double* partials, unsigned* counter, dou
     if (!last) return false;
     __threadfence();
     double s = 0.0;
-    for (int i = threadIdx.x; i < int(gridDim.x); i += blockDim.x) s += ((volatile double*)partials)[i];
+    s = l2_strided_sum(partials, int(gridDim.x), threadIdx.x, blockDim.x);
     s = cta_sum(s, sh);
     if (threadIdx.x == 0) {
         *counter = 0u;

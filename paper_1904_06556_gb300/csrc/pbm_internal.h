@@ -45,6 +45,26 @@ constexpr int kNodeBlocksPerSm = 8;   // CTA cap of the node pass of the two-pas
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Last-CTA completion of the ordered reductions: this thread's share a[t], a[t + stride], ... of the per-CTA
+// partials a[0 .. n) summed in that order. The partials were written by other CTAs before their fence, so they are
+// read from L2 (ld.global.cg); the loads are issued eight at a time, so a long share costs one L2 round trip per
+// eight entries instead of one per entry, with the same additions in the same order.
+__device__ __forceinline__ double l2_strided_sum(const double* a, int n, int t, int stride) {
+    double s = 0.0;
+    for (int q0 = t; q0 < n; q0 += 8 * stride) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u * stride;
+            v[u] = q < n ? __ldcg(a + q) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (q0 + u * stride < n) s += v[u];
+    }
+    return s;
+}
+
 template <typename... KArgs, typename... Args>
 void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args&&... args) {
     cudaLaunchConfig_t cfg = {};

@@ -100,6 +100,29 @@ __device__ __forceinline__ void bar_arrive(int id) { asm volatile("bar.arrive %0
 __device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 __device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 
+// Layout of a lane's staging ring (floats per stage, in units of the CTA's thread count): x of node rows 0 .. NYB
+// (and u for S), the element weights of NYB rows (and the Schur weights for S), then NE epilogue operands of the
+// owned node rows 0 .. NYB - 1 (b; the inverse diagonal; the previous Chebyshev iterate). D stages: as many as
+// fit MINB CTAs per SM (5 or 4 for plain applies, at least 3).
+struct StripRing {
+    int D, NV, WOFF, EOFF, NE, PER;
+};
+__host__ __device__ constexpr int strip_epi_operands(int epi) {
+    return epi == EPI_APPLY ? 0 : (epi == EPI_RESID ? 1 : (epi == EPI_CHEB ? 3 : 2));
+}
+__host__ __device__ constexpr StripRing strip_ring(int mode, int epi, int nyb, int nw, int minb) {
+    const bool s = mode == 2;
+    const int nv = 3 * (nyb + 1);
+    const int woff = s ? 2 * nv : nv;
+    const int eoff = woff + (s ? 2 * nyb : nyb);
+    const int ne = strip_epi_operands(epi);
+    const int per = eoff + 3 * nyb * ne;
+    int d = s ? 4 : 5;
+    // shared memory per SM: 228 KB, less about 3 KB per CTA for the static arrays and the reserved block
+    while (d > 3 && minb * (d * per * 32 * nw * 4 + 3 * 1024) > 228 * 1024) --d;
+    return StripRing{d, nv, woff, eoff, ne, per};
+}
+
 struct StripArgs {
     int nx, ny, nz, support;
     int DZ, gx, gy;
@@ -151,7 +174,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
 
     // node rows r = 0 .. NYB: in range and not supported (bit r for planes k >= 1, bit 16 + r for plane 0),
     // supported (same layout), owned by this lane (bit r)
-    unsigned okm = 0, fixm = 0, ownm = 0;
+    unsigned okm = 0, fixm = 0, ownm = 0, inm = 0;
     int noff[NYB + 1];                     // node offsets (floats) within a plane
     const int ic = min(max(i, 0), nx);     // clamped coordinates: every address formed stays inside the arrays
 #pragma unroll
@@ -160,6 +183,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
         const bool in = i >= 0 && i <= nx && j >= 0 && j <= ny;
         noff[r] = 3 * (ic + (nx + 1) * min(max(j, 0), ny));
         if (in) {
+            inm |= 1u << r;
             const int fb = fixed_bits(support, nx, ny, nz, i, j);
             if (!(fb & 1)) okm |= 1u << r;
             if (!(fb & 2)) okm |= 1u << (16 + r);
@@ -199,10 +223,8 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     // (both stay resident while it runs, so no plane's transform is kept in registers across layers) and then
     // issues plane k + D - 1 into the slot of plane k - 1. A lane only reads what it copied itself, so waiting for
     // its own copies suffices (no barrier).
-    constexpr int D = S ? 4 : 5;
-    constexpr int NV = 3 * (NYB + 1);
-    constexpr int WOFF = S ? 2 * NV : NV;
-    constexpr int PER = WOFF + (S ? 2 * NYB : NYB);
+    constexpr StripRing RG = strip_ring(MODE, EPI, NYB, NW, MINB);
+    constexpr int D = RG.D, NV = RG.NV, WOFF = RG.WOFF, EOFF = RG.EOFF, PER = RG.PER;
     extern __shared__ float ring[];   // D * PER * NT floats (dynamic: strip_ring_bytes)
     const int tid = threadIdx.x;
     const int pmax = min(kz1, nz);   // last plane a layer of this chunk reads
@@ -224,6 +246,26 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
                     const float* ur = us + noff[r];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) cp_async4(st + 4u * uint32_t((NV + 3 * r + c) * NT), ur + c, nb);
+                }
+            }
+            if (RG.NE > 0) {
+                // the epilogue's operands of the owned node rows 0 .. NYB - 1 of plane p (zero outside the grid; the
+                // previous Chebyshev iterate only when its coefficient is not zero)
+                const float* bs = P.b + int64_t(p) * plane;
+                const float* ds = P.idiag + int64_t(p) * plane;
+                const float* ys = P.y + int64_t(p) * plane;
+#pragma unroll
+                for (int r = 0; r < NYB; ++r) {
+                    const uint32_t nb = ((inm >> r) & 1u) ? 4u : 0u;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        cp_async4(st + 4u * uint32_t((EOFF + 3 * r + c) * NT), bs + noff[r] + c, nb);
+                        if (RG.NE >= 2)
+                            cp_async4(st + 4u * uint32_t((EOFF + 3 * (NYB + r) + c) * NT), ds + noff[r] + c, nb);
+                        if (RG.NE >= 3)
+                            cp_async4(st + 4u * uint32_t((EOFF + 3 * (2 * NYB + r) + c) * NT), ys + noff[r] + c,
+                                      c1nz ? nb : 0u);
+                    }
                 }
             }
             if (p >= 1) {
@@ -291,23 +333,28 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
 
     // epilogue of the node of row r of plane k with the operator value s: stored (and counted in the dot) where
     // the lane owns it; the loads use the clamped, always valid addresses, so no lane branches
-    auto epilogue = [&](int k, int r, float s0, float s1, float s2) {
+    // epilogue of the node of row r of plane k with the operator value s: stored (and counted in the dot) where
+    // the lane owns it. x and the epilogue's operands come from the lane's ring stage of plane k (slot es); x is
+    // zero there at supported nodes, whose output is x itself, read from global memory (predicated: only lanes of
+    // supported nodes load). The store uses the clamped, always valid address, so no lane branches.
+    auto epilogue = [&](int es, int k, int r, float s0, float s1, float s2) {
         const bool own = (ownm >> r) & 1u;
         const int j = jb + r;
         const int64_t d0 = int64_t(k) * plane + noff[r];
         const bool ofixed = ((k == 0 ? (fixm >> 16) : fixm) >> r) & 1u;
+        const float* st = ring + es * PER * NT + tid;
         float sv[3] = {s0, s1, s2};
         float xo[3] = {0.0f, 0.0f, 0.0f};
         constexpr bool always_x = EPI == EPI_JACOBI || EPI == EPI_CHEB || EPI == EPI_GS0;
         if (always_x || (EPI == EPI_APPLY && want_dot)) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) xo[c] = __ldg(P.x + d0 + c);
-        } else {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) xo[c] = ofixed ? __ldg(P.x + d0 + c) : 0.0f;   // supported nodes only
+            for (int c = 0; c < 3; ++c) xo[c] = st[(3 * r + c) * NT];
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) sv[c] = ofixed ? xo[c] : sv[c];
+        for (int c = 0; c < 3; ++c) {
+            if (ofixed) xo[c] = __ldg(P.x + d0 + c);   // supported nodes only
+            sv[c] = ofixed ? xo[c] : sv[c];
+        }
         const int gs_c = EPI == EPI_GS0 ? P.mode - EPI_GS0 - 3 * node_colour(i, j, k) : 0;
         float dsum = 0.0f;
 #pragma unroll
@@ -317,20 +364,20 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
                 o = sv[c];
                 dsum += o * xo[c];
             } else if (EPI == EPI_RESID) {
-                o = __ldg(P.b + d0 + c) - sv[c];
+                o = st[(EOFF + 3 * r + c) * NT] - sv[c];
                 dsum += o * o;
             } else if (EPI == EPI_JACOBI) {
-                const float bb = __ldg(P.b + d0 + c);
-                o = xo[c] + omF * ((bb - sv[c]) * __ldg(P.idiag + d0 + c));
+                const float bb = st[(EOFF + 3 * r + c) * NT];
+                o = xo[c] + omF * ((bb - sv[c]) * st[(EOFF + 3 * (NYB + r) + c) * NT]);
                 dsum += o * bb;
             } else if (EPI == EPI_CHEB) {
-                const float bb = __ldg(P.b + d0 + c);
-                o = c0F * xo[c] + c2F * ((bb - sv[c]) * __ldg(P.idiag + d0 + c));
-                if (c1nz) o -= c1F * P.y[d0 + c];
+                const float bb = st[(EOFF + 3 * r + c) * NT];
+                o = c0F * xo[c] + c2F * ((bb - sv[c]) * st[(EOFF + 3 * (NYB + r) + c) * NT]);
+                o -= c1F * st[(EOFF + 3 * (2 * NYB + r) + c) * NT];   // staged as zero when c1 is zero
                 dsum += o * bb;
             } else {
-                const float bb = __ldg(P.b + d0 + c);
-                o = gs_c == c ? xo[c] + (bb - sv[c]) * __ldg(P.idiag + d0 + c) : xo[c];
+                const float bb = st[(EOFF + 3 * r + c) * NT];
+                o = gs_c == c ? xo[c] + (bb - sv[c]) * st[(EOFF + 3 * (NYB + r) + c) * NT] : xo[c];
                 dsum += o * bb;
             }
             if (own) P.y[d0 + c] = o;
@@ -338,11 +385,13 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
         if (want_dot && own) pdT += dsum;
     };
 
-    // One layer k (planes k and k + 1): lo holds the x-pairs of plane k (x and u), carry the transformed top
-    // faces of layer k - 1 (zero below the first layer); hi receives those of plane k + 1 and carry the top
-    // faces of layer k. Then the node values of plane k are finished (k >= kz0). Called with the lo / hi roles
-    // swapped on alternate layers, so nothing is copied between layers.
-    auto layer_step = [&](int k, float2 (&carry)[NP][4][3]) {
+    // One layer k (planes k and k + 1): xlo / ulo hold the face quads of plane k (x and u), carry the
+    // transformed top faces of layer k - 1 (zero below the first layer); xhi / uhi receive those of plane k + 1,
+    // which the next layer takes as its lo, and carry the top faces of layer k. Then the node values of plane k
+    // are finished (k >= kz0). Called with the lo / hi roles swapped on alternate layers, so every plane is read
+    // from the ring and transformed once and nothing is copied between layers.
+    auto layer_step = [&](int k, float2 (&carry)[NP][4][3], FQ (&xlo)[NP], FQ (&ulo)[NP], FQ (&xhi)[NP],
+                          FQ (&uhi)[NP]) {
         const bool layer = k < nz;
         // node-row accumulators of plane k: the left (own column) and right (next column) parts per component,
         // rows 0 .. NYB
@@ -364,13 +413,10 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
             aL[2 * p + 2][c] += hL.y;
             aR[2 * p + 2][c] += hR.y;
         };
+        const int es = cslot;   // ring slot of plane k: its epilogue operands
         const int hslot = cslot == D - 1 ? 0 : cslot + 1;
         if (layer) {
             cp_async_wait<D - 3>();  // plane k + 1 and the weights of layer k have landed
-            FQ xlo[NP], xhi[NP], ulo[NP], uhi[NP];   // ulo, uhi: S only
-            read_plane(cslot);
-            plane_quads(rx, xlo);
-            if (S) plane_quads(ru, ulo);
             read_plane(hslot);
             read_w(hslot);
             plane_quads(rx, xhi);
@@ -461,12 +507,12 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
             bar_arrive(1 + wid);
         }
 #pragma unroll
-        for (int r = 1; r < NYB; ++r) epilogue(k, r, tot[r][0], tot[r][1], tot[r][2]);
+        for (int r = 1; r < NYB; ++r) epilogue(es, k, r, tot[r][0], tot[r][1], tot[r][2]);
         if (wid >= 1) {
             bar_sync(1 + wid - 1);
             const float4 v = sy[wid - 1][lane];
             bar_arrive(NW + wid - 1);
-            epilogue(k, 0, tot[0][0] + v.x, tot[0][1] + v.y, tot[0][2] + v.z);
+            epilogue(es, k, 0, tot[0][0] + v.x, tot[0][1] + v.y, tot[0][2] + v.z);
         }
     };
 
@@ -483,9 +529,15 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     // the slot between warps w and w + 1 starts free: the reader's first "read done" is signalled up front, and
     // the writer's last wait matches the reader's last signal, so every barrier phase completes
     if (wid >= 1) bar_arrive(NW + wid - 1);
+    // face quads of the first plane; from then on every layer transforms only its upper plane
+    FQ xa_[NP], ua_[NP], xb_[NP], ub_[NP];   // ua_, ub_: S only
+    cp_async_wait<D - 2>();
+    read_plane(0);
+    plane_quads(rx, xa_);
+    if (S) plane_quads(ru, ua_);
     for (int k = kstart; k < kz1; k += 2) {
-        layer_step(k, carry);
-        if (k + 1 < kz1) layer_step(k + 1, carry);
+        layer_step(k, carry, xa_, ua_, xb_, ub_);
+        if (k + 1 < kz1) layer_step(k + 1, carry, xb_, ub_, xa_, ua_);
     }
     if (wid + 1 < NW) bar_sync(NW + wid);
     cp_async_wait<0>();
@@ -506,10 +558,8 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     if (!s_last) return;
     __threadfence();
     double td = 0.0, ta = 0.0;
-    for (int q = t; q < int(nblk); q += NT) {
-        td += ((volatile double*)P.partials)[q];
-        ta += ((volatile double*)P.partials)[nblk + q];
-    }
+    td = l2_strided_sum(P.partials, int(nblk), t, NT);
+    ta = l2_strided_sum(P.partials + nblk, int(nblk), t, NT);
     double sd = fused_cta_sum<NT>(td, sred);
     const double sa = fused_cta_sum<NT>(ta, sred);
     if (t != 0) return;
@@ -583,20 +633,18 @@ FusedPlan strip_plan(const Geom& G, int cand) {
     return p;
 }
 
-// bytes of the staging ring of the kernel: D stages of x (and u) of NYB + 1 node rows and the weights of NYB
-// element rows, per thread
-static size_t strip_ring_bytes(int mode, int nyb, int nw) {
-    const bool s = mode == 2;
-    const int D = s ? 4 : 5, NV = 3 * (nyb + 1);
-    const int per = (s ? 2 * NV : NV) + (s ? 2 * nyb : nyb);
-    return sizeof(float) * size_t(D) * size_t(per) * size_t(32 * nw);
+// bytes of the staging ring of the kernel: D stages of x (and u) of NYB + 1 node rows, the weights of NYB element
+// rows and the epilogue's operands, per thread
+static size_t strip_ring_bytes(int mode, int epi, int nyb, int nw, int minb) {
+    const StripRing rg = strip_ring(mode, epi, nyb, nw, minb);
+    return sizeof(float) * size_t(rg.D) * size_t(rg.PER) * size_t(32 * nw);
 }
 
 // launch with the ring in dynamic shared memory (the opt-in above 48 KB set once per kernel and device)
 template <int MODE, int EPI, int NYB, int NW, int MINB>
 static void strip_launch_one(int blocks, const StripArgs& P, cudaStream_t st) {
     auto kern = k_strip_f32<MODE, EPI, NYB, NW, MINB>;
-    const size_t smem = strip_ring_bytes(MODE, NYB, NW);
+    const size_t smem = strip_ring_bytes(MODE, EPI, NYB, NW, MINB);
     static std::atomic<uint64_t> set_on{0};   // bit per device ordinal < 64
     int dev = 0;
     PBM_CUDA(cudaGetDevice(&dev));

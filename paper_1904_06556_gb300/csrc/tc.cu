@@ -536,10 +536,8 @@ __global__ void __launch_bounds__(tc::NT, MINB) k_tc_f32(TcArgs P) {
     if (!s_last) return;
     __threadfence();
     double td = 0.0, ta = 0.0;
-    for (int q = t; q < int(nblk); q += NT) {
-        td += ((volatile double*)P.partials)[q];
-        ta += ((volatile double*)P.partials)[nblk + q];
-    }
+    td = l2_strided_sum(P.partials, int(nblk), t, NT);
+    ta = l2_strided_sum(P.partials + nblk, int(nblk), t, NT);
     double sd = tc_cta_sum<NT>(td, sred);
     const double sa = tc_cta_sum<NT>(ta, sred);
     if (t != 0) return;
