@@ -155,6 +155,9 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
     constexpr int R = NW * NYB;            // element rows of the CTA
     constexpr int NP = NYB / 2;            // element pairs per lane
     static_assert(NYB % 2 == 0, "element rows come in pairs");
+    // the face quads of a layer's upper plane are kept for the next layer where the registers allow it (one pair
+    // per lane, and for S only with the two 4-warp CTAs per SM); otherwise every layer transforms both planes
+    constexpr bool CARRY = NP == 1 && (!S || (NW == 4 && MINB == 2));
     __shared__ float4 sy[NW][32];          // node totals of each warp's top row for the warp above
     static_assert(2 * NW - 2 <= 15, "named barriers: 1 .. NW - 1 (row written), NW .. 2 NW - 2 (row read)");
     __shared__ double sred[NW];
@@ -417,6 +420,11 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
         const int hslot = cslot == D - 1 ? 0 : cslot + 1;
         if (layer) {
             cp_async_wait<D - 3>();  // plane k + 1 and the weights of layer k have landed
+            if (!CARRY) {
+                read_plane(cslot);
+                plane_quads(rx, xlo);
+                if (S) plane_quads(ru, ulo);
+            }
             read_plane(hslot);
             read_w(hslot);
             plane_quads(rx, xhi);
