@@ -906,6 +906,27 @@ def oracle_sample_seconds(w, smoother, ctx):
                   f"{ctx['iters']} iterations the oracle needs to {w.rtol:g} on the full system")
 
 
+def oracle_spmv(w, ctx):
+    """The oracle's CSR product K(rho) x on the sample's grid (scipy, single-threaded): seconds per product scaled
+    to the full element count, and its rate in algorithmic bytes ((2n + m) 8 per product, the FP64 K(w) x bytes)."""
+    from oracle import fem
+    pb, st = ctx.get("slab") or ctx["full"]
+    g = pb.grid
+    K = fem.assemble_K(g, st.rho, fem.element_stiffness(w.E, w.nu))
+    x = np.random.default_rng(0).standard_normal(g.n)
+    y = K @ x
+    ts = []
+    for _ in range(10):
+        t0 = time.perf_counter()
+        y = K @ x
+        ts.append(time.perf_counter() - t0)
+    t = statistics.median(ts)
+    scale = w.m / g.m
+    return {"ms_per_product_full_size": 1e3 * t * scale, "gbs_algorithmic": (2 * g.n + g.m) * 8 / t / 1e9,
+            "csr_nonzeros": int(K.nnz), "threads": 1,
+            "sample": f"K(rho) x on the {g.nx}x{g.ny}x{g.nz} sample grid, median of 10, scaled by {scale:g}"}
+
+
 def cpu_baseline(w, budget_s, smoother="jacobi"):
     ctx = {}
     times, desc = [], ""
@@ -917,7 +938,8 @@ def cpu_baseline(w, budget_s, smoother="jacobi"):
         if time.perf_counter() - t_all + (time.perf_counter() - t0) > budget_s or len(times) >= 5:
             break
     tm = statistics.median(times)
-    return {"value": 1.0 / tm, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    spmv = oracle_spmv(w, ctx)
+    return {"value": 1.0 / tm, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "spmv_K": spmv,
             "blas_threads": int(os.environ.get("OPENBLAS_NUM_THREADS", "1")),
             "sample": (f"{len(times)} sample(s): {desc}; median {tm:.2f} s per system; BLAS/OpenMP threads = "
                        f"{os.environ.get('OPENBLAS_NUM_THREADS')} of {os.cpu_count()} host cores (dense coarsest "
