@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(CB) k_cols_coarse(ColArgs<T> P) {
 // one coalesced row of the entry-major array; the eight corner rows go to the same plane-quad
 // scratch as the split pass, and the node pass is shared.
 template <class T>
-__global__ void __launch_bounds__(CB) k_cols_coarse_e(ColArgs<T> P) {
+__global__ void __launch_bounds__(CB, 4) k_cols_coarse_e(ColArgs<T> P) {
     pdl_wait();
     const unsigned mu = unsigned(P.m), ncol = unsigned(P.ncol), nxu = unsigned(P.nx);
     const unsigned eu = blockIdx.x * CB + threadIdx.x;
@@ -295,17 +295,25 @@ __global__ void __launch_bounds__(CB) k_cols_coarse_e(ColArgs<T> P) {
 #pragma unroll
     for (int r = 0; r < 24; ++r) y[r] = T(0);
     const T* Ae = P.A + eu;
+    // row r of the upper triangle (its entries are consecutive in the entry order) is loaded two rows ahead of
+    // its use, so that about two rows of loads per thread are in flight while a row is multiplied (the matrices
+    // are read once, from DRAM: the pass is bound by how many loads the SM keeps in flight)
+    T a[3][24];
+    auto load_row = [&](int r, T (&dst)[24]) {
+#pragma unroll
+        for (int s = r; s < 24; ++s) dst[s] = __ldg(Ae + int64_t(tri_index(r, s)) * mu);
+    };
+    load_row(0, a[0]);
+    load_row(1, a[1]);
 #pragma unroll
     for (int r = 0; r < 24; ++r) {
-        // row r of the upper triangle: its entries are consecutive in the entry order
-        T a[24];
-#pragma unroll
-        for (int s = r; s < 24; ++s) a[s] = __ldg(Ae + int64_t(tri_index(r, s)) * mu);
-        y[r] += a[r] * xe[r];
+        if (r + 2 < 24) load_row(r + 2, a[(r + 2) % 3]);
+        const T (&ar)[24] = a[r % 3];
+        y[r] += ar[r] * xe[r];
 #pragma unroll
         for (int s = r + 1; s < 24; ++s) {
-            y[r] += a[s] * xe[s];
-            y[s] += a[s] * xe[r];
+            y[r] += ar[s] * xe[s];
+            y[s] += ar[s] * xe[r];
         }
     }
     const int64_t col = colu;
