@@ -210,15 +210,23 @@ __global__ void __launch_bounds__(CB) k_cols_fine_b(const ColArgs<T>* __restrict
 // ------------------------------------------------------------------------------------------------
 template <class T, int A>
 __device__ __forceinline__ void coarse_node_rows(const T* __restrict__ Ae, int64_t m, const T (&xe)[24], T (&y)[3]) {
+    // all 72 entries are loaded before the sums (one round of loads: on the small coarse levels the pass is bound
+    // by load latency), then summed in the fixed order
+    T av[3][24];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const int r = 3 * A + c;
-        T acc = T(0);
 #pragma unroll
         for (int s = 0; s < 24; ++s) {
             const int t = r <= s ? tri_index(r, s) : tri_index(s, r);
-            acc += __ldg(Ae + int64_t(t) * m) * xe[s];
+            av[c][s] = __ldg(Ae + int64_t(t) * m);
         }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        T acc = T(0);
+#pragma unroll
+        for (int s = 0; s < 24; ++s) acc += av[c][s] * xe[s];
         y[c] = acc;
     }
 }
@@ -262,7 +270,7 @@ __device__ __forceinline__ void cols_coarse_body(const ColArgs<T>& P, unsigned b
 }
 
 template <class T>
-__global__ void __launch_bounds__(CB) k_cols_coarse(ColArgs<T> P) {
+__global__ void __launch_bounds__(CB, 4) k_cols_coarse(ColArgs<T> P) {
     pdl_wait();
     cols_coarse_body<T>(P, blockIdx.x);
 }
@@ -326,7 +334,7 @@ __global__ void __launch_bounds__(CB, 4) k_cols_coarse_e(ColArgs<T> P) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(CB) k_cols_coarse_b(const ColArgs<T>* __restrict__ A, BatchMap M) {
+__global__ void __launch_bounds__(CB, 4) k_cols_coarse_b(const ColArgs<T>* __restrict__ A, BatchMap M) {
     const int s = batch_system(M, blockIdx.x);
     if (!batch_active(M, s)) return;
     cols_coarse_body<T>(A[s], blockIdx.x - M.first[s]);
