@@ -506,15 +506,28 @@ static MrResult minres(pbm_grid* g, bool fp32, bool op_s, const void* b, void* x
     void* const* V = fp32 ? (void* const*)g->kv32 : (void* const*)g->kv64;
     void* X = V[10];
     const size_t bytes = nv * esz(fp32);
+    // |b|^2 and |x|^2 of the initial guess in one read; from x = 0 the starting residual is b itself (bit for bit)
+    // and the operator application is skipped
     launch_dot(g, fp32, b, b, nv, 3, st);
-    const double bnorm = std::sqrt(read_slot(g, 3, st));
+    launch_dot(g, fp32, x, x, nv, 57, st);
+    PBM_CUDA(cudaMemcpyAsync(&g->sc_host->red[3], &g->sc->red[3], sizeof(double), cudaMemcpyDeviceToHost, st));
+    PBM_CUDA(cudaMemcpyAsync(&g->sc_host->red[57], &g->sc->red[57], sizeof(double), cudaMemcpyDeviceToHost, st));
+    PBM_CUDA(cudaStreamSynchronize(st));
+    const double bnorm = std::sqrt(g->sc_host->red[3]);
+    const bool x_zero = g->sc_host->red[57] == 0.0;
     if (bnorm == 0.0) {
         vec_zero(x, bytes, st);
         return res;
     }
-    PBM_CUDA(cudaMemcpyAsync(X, x, bytes, cudaMemcpyDeviceToDevice, st));
     auto finish = [&]() { PBM_CUDA(cudaMemcpyAsync(x, X, bytes, cudaMemcpyDeviceToDevice, st)); };
-    level_apply(g, 0, fp32, op_s, args(X, V[1], EPI_RESID, b, nullptr, nullptr, 2), st);
+    if (x_zero) {
+        // (a guess whose squares all underflow counts as zero: the iterate starts from exactly zero)
+        vec_zero(X, bytes, st);
+        PBM_CUDA(cudaMemcpyAsync(V[1], b, bytes, cudaMemcpyDeviceToDevice, st));
+    } else {
+        PBM_CUDA(cudaMemcpyAsync(X, x, bytes, cudaMemcpyDeviceToDevice, st));
+        level_apply(g, 0, fp32, op_s, args(X, V[1], EPI_RESID, b, nullptr, nullptr, 2), st);
+    }
     precondition(g, fp32, pc32, op_s, V[1], V[2], nv, st);
     mr_init(g, st);
     vec_zero(V[0], bytes, st);
@@ -623,14 +636,27 @@ int solve(pbm_grid* g, bool op_s, const double* b, double* x, double rtol, int m
         double* r64 = g->kv64[7];
         float* r32 = g->kv32[7];
         float* dx32 = g->kv32[8];
+        // |b|^2 and |x|^2 of the initial guess in one read: from x = 0 the first FP64 residual is b itself (bit for
+        // bit: the operator of zero is zero, supported rows give b - 0), so the FP64 apply is skipped
         launch_dot(g, false, b, b, nv, 3, st);
-        const double bnorm = std::sqrt(read_slot(g, 3, st));
+        launch_dot(g, false, x, x, nv, 57, st);
+        PBM_CUDA(cudaMemcpyAsync(&g->sc_host->red[3], &g->sc->red[3], sizeof(double), cudaMemcpyDeviceToHost, st));
+        PBM_CUDA(cudaMemcpyAsync(&g->sc_host->red[57], &g->sc->red[57], sizeof(double), cudaMemcpyDeviceToHost, st));
+        PBM_CUDA(cudaStreamSynchronize(st));
+        const double bnorm = std::sqrt(g->sc_host->red[3]);
+        const bool x_zero = g->sc_host->red[57] == 0.0;
         inf.status = PBM_OK;
         if (bnorm == 0.0) {
             vec_zero(x, nv * sizeof(double), st);
         } else {
             int total = 0, outer = 0;
-            double rel = true_relres(g, op_s, b, x, r64, bnorm, st);
+            double rel;
+            if (x_zero) {
+                PBM_CUDA(cudaMemcpyAsync(r64, b, nv * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                rel = 1.0;
+            } else {
+                rel = true_relres(g, op_s, b, x, r64, bnorm, st);
+            }
             bool robust = false;
             while (rel > rtol && !robust) {
                 if (total >= maxit || outer >= 60) break;
