@@ -915,6 +915,18 @@ def test_full_size_cant256_K_apply_sampled_rows(pkg):
         G.set_fp32_plan("K", plan)
         y, _ = G.apply_fine_f32("K", "apply", dev(x, torch.float32))
         assert close(host(y).reshape(-1, 3)[nodes], ref32) < 2e-6, plan
+    # the fused dot product of the 4-warp lane-strip plan (the first plan after the tensor-core plan) at this size:
+    # its last CTA sums more than eight per-CTA partials per thread, in several rounds of loads; the result is
+    # y . x of the kernel's own output, formed here in FP64
+    G.set_fp32_plan("K", pkg.fp32_tc_plan() + 1)
+    tx, ty, dz, nt = G.info()["fp32_tile"][0][:4]
+    ctas = -(-(X + 1) // tx) * -(-(Y + 1) // ty) * -(-(Z + 1) // dz)
+    assert ctas > 8 * nt, (ctas, nt)
+    x32 = dev(x, torch.float32)
+    y, d = G.apply_fine_f32("K", "apply", x32, dot=True)
+    assert close(host(y).reshape(-1, 3)[nodes], ref32) < 2e-6
+    ref_dot = float(torch.dot(y.double(), x32.double()))
+    assert abs(d - ref_dot) <= 1e-5 * abs(ref_dot), (d, ref_dot)
 
 
 # ------------------------------------------------------------------------------------------------
