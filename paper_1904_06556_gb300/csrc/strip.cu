@@ -255,8 +255,8 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_strip_f32(StripArgs P) {
                 // the epilogue's operands of the owned node rows 0 .. NYB - 1 of plane p (zero outside the grid; the
                 // previous Chebyshev iterate only when its coefficient is not zero)
                 const float* bs = P.b + int64_t(p) * plane;
-                const float* ds = P.idiag + int64_t(p) * plane;
-                const float* ys = P.y + int64_t(p) * plane;
+                const float* ds = RG.NE >= 2 ? P.idiag + int64_t(p) * plane : nullptr;   // only where staged
+                const float* ys = RG.NE >= 3 ? P.y + int64_t(p) * plane : nullptr;
 #pragma unroll
                 for (int r = 0; r < NYB; ++r) {
                     const uint32_t nb = ((inm >> r) & 1u) ? 4u : 0u;
