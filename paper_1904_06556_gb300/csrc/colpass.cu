@@ -272,6 +272,7 @@ __device__ __forceinline__ void cols_coarse_body(const ColArgs<T>& P, unsigned b
 template <class T>
 __global__ void __launch_bounds__(CB, 4) k_cols_coarse(ColArgs<T> P) {
     pdl_wait();
+    pdl_launch_if_small();
     cols_coarse_body<T>(P, blockIdx.x);
 }
 
@@ -284,6 +285,7 @@ __global__ void __launch_bounds__(CB, 4) k_cols_coarse(ColArgs<T> P) {
 template <class T>
 __global__ void __launch_bounds__(CB, 4) k_cols_coarse_e(ColArgs<T> P) {
     pdl_wait();
+    pdl_launch_if_small();
     const unsigned mu = unsigned(P.m), ncol = unsigned(P.ncol), nxu = unsigned(P.nx);
     const unsigned eu = blockIdx.x * CB + threadIdx.x;
     if (eu >= mu) return;
@@ -512,6 +514,7 @@ __device__ __forceinline__ void nodes_body(const NodeArgs<T>& P, unsigned blk, u
 template <class T>
 __global__ void __launch_bounds__(NB2) k_nodes(NodeArgs<T> P) {
     pdl_wait();
+    pdl_launch_if_small();
     nodes_body<T>(P, blockIdx.x, gridDim.x);
 }
 

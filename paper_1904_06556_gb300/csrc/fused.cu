@@ -459,6 +459,7 @@ __device__ __forceinline__ void coarse_rows6(const float* __restrict__ Ae, int64
 template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_fused_coarse_f32(CoarseArgs P) {
     pdl_wait();
+    pdl_launch_if_small();
     extern __shared__ float4 fused_smem4[];
     __shared__ double sred[NT / 32];
     __shared__ bool s_last;

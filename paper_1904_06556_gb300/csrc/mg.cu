@@ -103,6 +103,7 @@ __device__ __forceinline__ void restrict_body(const RestrictArgs<T>& P, unsigned
 template <class T>
 __global__ void k_restrict(RestrictArgs<T> P) {
     pdl_wait();
+    pdl_launch_if_small();
     restrict_body<T>(P, blockIdx.x, gridDim.x);
 }
 template <class T>
@@ -184,6 +185,7 @@ __device__ __forceinline__ void prolong_body(const ProlongArgs<T>& P, unsigned b
 template <class T>
 __global__ void k_prolong_add(ProlongArgs<T> P) {
     pdl_wait();
+    pdl_launch_if_small();
     prolong_body<T>(P, blockIdx.x, gridDim.x);
 }
 template <class T>
@@ -636,6 +638,7 @@ __device__ __forceinline__ void coarsest_solve_body(const CoarsestArgs<T>& P, un
 template <class T>
 __global__ void k_coarsest_solve(CoarsestArgs<T> P) {
     pdl_wait();
+    pdl_launch_if_small();
     coarsest_solve_body<T>(P, blockIdx.x);
 }
 template <class T>

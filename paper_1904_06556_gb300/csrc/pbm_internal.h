@@ -44,6 +44,15 @@ constexpr int kNodeBlocksPerSm = 8;   // CTA cap of the node pass of the two-pas
 // ------------------------------------------------------------------------------------------------
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// The exception: a grid of at most one CTA per SM (the coarse levels, the transfers to them, the coarsest solve)
+// lets the next kernel of the stream launch once its own predecessor has completed (call after pdl_wait()): the
+// waiting CTAs of the next kernel sit on SMs this grid leaves idle, and the launch gaps of the V-cycle's chains
+// of small kernels overlap the running kernel.
+__device__ __forceinline__ void pdl_launch_if_small() {
+    unsigned nsm;
+    asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
+    if (gridDim.x * gridDim.y * gridDim.z <= nsm) pdl_launch();
+}
 
 // Last-CTA completion of the ordered reductions: this thread's share a[t], a[t + stride], ... of the per-CTA
 // partials a[0 .. n) summed in that order. The partials were written by other CTAs before their fence, so they are
