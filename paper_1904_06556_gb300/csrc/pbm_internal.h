@@ -37,10 +37,10 @@ constexpr int kNodeBlocksPerSm = 8;   // CTA cap of the node pass of the two-pas
 // ------------------------------------------------------------------------------------------------
 // programmatic dependent launch on the solve path: launch_pdl lets the launch of the next kernel of
 // the stream overlap the end of this one; every kernel launched that way begins with pdl_wait() (its
-// predecessor has completed and its writes are visible after it). The kernels do not trigger their
-// successors early (pdl_launch): waiting CTAs of the next kernel would take registers and warp slots
-// from the running one, which slowed the FP64 solve down by a quarter. In a kernel launched normally
-// pdl_wait() is a no-op.
+// predecessor has completed and its writes are visible after it). Kernels of more than one CTA per SM
+// do not trigger their successors early (pdl_launch): waiting CTAs of the next kernel would take
+// registers and warp slots from the running one, which slowed the FP64 solve down by a quarter. In a
+// kernel launched normally pdl_wait() is a no-op.
 // ------------------------------------------------------------------------------------------------
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
